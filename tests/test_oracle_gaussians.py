@@ -1,0 +1,224 @@
+"""Pins for the oracle's Gaussian projection, footprint and rasterisation
+(Sec. 4.4; EWA splatting of [kerbl20233d] with the dilation of
+Eq. (gs_prefilter_fix))."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2508_18540_gb300 import synth as S
+from tests import helpers as H
+
+
+def _rand_scene(n, seed, rot=True):
+    rng = np.random.default_rng(seed)
+    means = np.stack([rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), rng.uniform(1.5, 6, n)], 1)
+    scales = np.exp(rng.normal(math.log(0.05), 0.6, (n, 3)))
+    q = rng.normal(size=(n, 4)) if rot else np.tile([1.0, 0, 0, 0], (n, 1))
+    f = np.float32
+    return S.GaussianScene(means.astype(f), scales.astype(f), q.astype(f), rng.uniform(0.1, 0.9, n).astype(f),
+                           rng.uniform(0, 1, (n, 3)).astype(f))
+
+
+def _rotated_camera(N=96):
+    # a camera rotated about y and x, translated
+    a, b = 0.3, -0.2
+    Ry = np.array([[math.cos(a), 0, math.sin(a)], [0, 1, 0], [-math.sin(a), 0, math.cos(a)]])
+    Rx = np.array([[1, 0, 0], [0, math.cos(b), -math.sin(b)], [0, math.sin(b), math.cos(b)]])
+    cam = S.identity_camera(N, 50.0, t=(0.2, -0.1, 0.5))
+    cam.R = Rx @ Ry
+    return cam
+
+
+def test_ewa_covariance_matches_numeric_jacobian(orc):
+    # Sigma_2 = J W Sigma_3 W^T J^T + f' I with J the Jacobian of the
+    # perspective projection (taken here by central differences) and
+    # Sigma_3 built from quaternion products.
+    cam = _rotated_camera()
+    disp = S.display_for(3.0, 0.1, D_shift=0.1)
+    r = orc.make_ref(cam, disp)
+    sc = _rand_scene(40, 3)
+    mean2d, conic, cov2d = orc.gauss_values(r, sc)
+    R = np.asarray(cam.R)
+    t = np.asarray(cam.t)
+
+    def proj(pc):
+        return np.array([r.fx * pc[0] / pc[2] + r.cx, r.fy * pc[1] / pc[2] + r.cy])
+
+    for g in range(sc.n):
+        pc = R @ sc.means[g].astype(np.float64) + t - np.array([0, 0, r.D_forward])
+        if pc[2] < 0.3:
+            continue
+        J = np.zeros((2, 3))
+        h = 1e-6
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = h
+            J[:, a] = (proj(pc + e) - proj(pc - e)) / (2 * h)
+        S3 = H.sigma3_from_quat(sc.quats[g], sc.scales[g])
+        S2 = J @ R @ S3 @ R.T @ J.T + r.f_prime * np.eye(2)
+        got = np.array([[cov2d[g, 0], cov2d[g, 1]], [cov2d[g, 1], cov2d[g, 2]]])
+        assert np.allclose(got, S2, rtol=1e-6, atol=1e-9)
+        assert np.allclose(mean2d[g], proj(pc), rtol=1e-12, atol=1e-9)
+        C = np.linalg.inv(got)
+        assert np.allclose(conic[g], [C[0, 0], C[0, 1], C[1, 1]], rtol=1e-10)
+
+
+def test_flat_gaussian_projection_is_exact(orc):
+    # A flat fronto-parallel Gaussian maps affinely under perspective; with
+    # f = 0 its plane texels are its world-plane density at the ray hit point.
+    cam = S.identity_camera(64, 50.0)
+    disp = S.display_for(3.0, 0.1, f_aa=0.0)
+    r = orc.make_ref(cam, disp)
+    sc = H.flat_scene([((0.1, -0.05, 3.5), (0.08, 0.03), 0.7, 0.8, (1, 1, 1))])
+    out = orc.render(scene=sc, camera=cam, display=disp, views=S.ViewSet(1), N=1, binning="quantile",
+                     with_views=False)
+    A = out["planes"][0, :, :, 3]
+    x0, y0, x1, y1 = out["rect"][0]
+    assert out["valid"][0] == 1
+    m = sc.means[0].astype(np.float64)
+    s = sc.scales[0, :2].astype(np.float64)               # the stored FP32 inputs
+    q = sc.quats[0].astype(np.float64)
+    ang = 2 * math.atan2(q[3], q[0])
+    for y in range(r.H):
+        for x in range(r.W):
+            if x0 <= x <= x1 and y0 <= y <= y1:
+                o, d = H.ref_pixel_ray(r, x, y)
+                P = H.hit_plane_z(o, d, m[2])
+                a = H.flat_gauss_alpha(P, m, H.rot2(ang), s, float(sc.opacity[0]))
+                assert A[y, x] == pytest.approx(a, abs=1e-12)
+            else:
+                assert A[y, x] == 0.0
+
+
+def test_footprint_contains_three_sigma_ellipse(orc):
+    # Every plane pixel inside the 3-sigma ellipse of the projected Gaussian
+    # (q <= 9) lies inside the FP32 footprint rectangle.
+    cam = _rotated_camera(80)
+    disp = S.display_for(3.0, 0.1)
+    r = orc.make_ref(cam, disp)
+    sc = _rand_scene(300, 5)
+    z, valid, rect = orc.gauss_decide(r, sc)
+    mean2d, conic, _ = orc.gauss_values(r, sc)
+    ys, xs = np.mgrid[0:r.H, 0:r.W]
+    checked = 0
+    for g in range(sc.n):
+        dx = xs - mean2d[g, 0]
+        dy = ys - mean2d[g, 1]
+        q = conic[g, 0] * dx * dx + 2 * conic[g, 1] * dx * dy + conic[g, 2] * dy * dy
+        inside = q <= 9.0 * (1 - 1e-5)
+        if not valid[g]:
+            if z[g] > disp.z_near:
+                assert not inside.any()
+            continue
+        x0, y0, x1, y1 = rect[g]
+        inrect = (xs >= x0) & (xs <= x1) & (ys >= y0) & (ys <= y1)
+        assert not (inside & ~inrect).any()
+        checked += 1
+    assert checked > 100
+
+
+def test_fp32_footprint_agrees_with_fp64(orc):
+    # The FP32 decision path equals the same rectangle computed in FP64
+    # except for rare half-pixel ties, where it differs by one pixel.
+    cam = S.identity_camera(256, 50.0)
+    disp = S.display_for(2.6, 0.15)
+    r = orc.make_ref(cam, disp)
+    sc = _rand_scene(3000, 6)
+    z, valid, rect = orc.gauss_decide(r, sc)
+    mean2d, conic, cov2d = orc.gauss_values(r, sc)
+    diffs = 0
+    n_ok = 0
+    for g in np.nonzero(valid)[0]:
+        a, b, c = cov2d[g]
+        det = a * c - b * b
+        mid = 0.5 * (a + c)
+        lam = mid + math.sqrt(max(mid * mid - det, 0.0))
+        rad = math.ceil(3 * math.sqrt(lam))
+        px, py = mean2d[g]
+        ref = [max(0, math.ceil(px - rad)), max(0, math.ceil(py - rad)),
+               min(r.W - 1, math.floor(px + rad)), min(r.H - 1, math.floor(py + rad))]
+        d = np.abs(np.asarray(ref) - rect[g])
+        assert d.max() <= 1
+        diffs += int(d.max() > 0)
+        n_ok += 1
+    assert n_ok > 1000
+    assert diffs <= 0.01 * n_ok
+
+
+def test_culling(orc):
+    cam = S.identity_camera(64, 50.0)
+    disp = S.display_for(3.0, 0.1)
+    r = orc.make_ref(cam, disp)
+    sc = _rand_scene(4, 7)
+    sc.means[0] = [0.0, 0.0, 0.1]       # behind the near plane (after D_forward)
+    sc.means[1] = [50.0, 0.0, 3.0]      # far outside the frustum
+    sc.means[2] = [0.0, 0.0, 3.0]       # centre
+    sc.means[3] = [0.0, 0.0, -2.0]      # behind the camera
+    z, valid, rect = orc.gauss_decide(r, sc)
+    assert valid.tolist() == [0, 0, 1, 0]
+    assert z[2] == pytest.approx(3.0 - r.D_forward, rel=1e-15)
+
+
+def test_depth_order_and_ties(orc):
+    # Front-to-back within a chunk: the nearer opaque Gaussian dominates;
+    # equal depths are ordered by index.
+    cam = S.identity_camera(32, 50.0)
+    disp = S.display_for(3.0, 0.1, f_aa=0.0)
+    r = orc.make_ref(cam, disp)
+    sc = H.flat_scene([((0, 0, 3.0), (0.3, 0.3), 0.0, 0.9, (1, 0, 0)),
+                       ((0, 0, 3.0), (0.3, 0.3), 0.0, 0.9, (0, 1, 0)),
+                       ((0, 0, 2.5), (0.3, 0.3), 0.0, 0.9, (0, 0, 1))])
+    out = orc.render(scene=sc, camera=cam, display=disp, views=S.ViewSet(1), N=1, binning="quantile",
+                     with_views=False)
+    assert out["order"].tolist() == [2, 0, 1]
+    c = out["planes"][0, r.H // 2, r.W // 2]
+    # blue (nearest) first, then red before green (equal depth, lower index)
+    assert c[2] > 0.85 and c[2] > c[0] > c[1] > 0.0
+    a_r = c[0] / (1 - c[2])
+    assert c[1] == pytest.approx((1 - c[2]) * (1 - a_r) * a_r, rel=1e-9)
+
+
+def test_chunk_invariance_is_plain_alpha_blending(orc):
+    # No parallax between planes (phi = 0): compositing the chunked planes of
+    # any N gives the plain depth-sorted alpha blending of all primitives,
+    # i.e. the single-chunk plane (Eq. (alpha_blend) is associative).
+    cam = S.identity_camera(48, 50.0)
+    disp = S.Display(D_focal=3.0, phi_x=0.0)
+    sc = _rand_scene(400, 8)
+    one = orc.render(scene=sc, camera=cam, display=disp, views=S.ViewSet(1), N=1, binning="quantile")
+    # independent front-to-back blend from the oracle's per-primitive values
+    r = one["ref"]
+    ys, xs = np.mgrid[0:r.H, 0:r.W]
+    C = np.zeros((r.H, r.W, 3))
+    T = np.ones((r.H, r.W))
+    for g in one["order"]:
+        x0, y0, x1, y1 = one["rect"][g]
+        m = one["mean2d"][g]
+        a, b, c = one["conic"][g]
+        dx, dy = xs - m[0], ys - m[1]
+        al = np.minimum(0.99, sc.opacity[g] * np.exp(-0.5 * (a * dx * dx + 2 * b * dx * dy + c * dy * dy)))
+        al = np.where((xs >= x0) & (xs <= x1) & (ys >= y0) & (ys <= y1), al, 0.0)
+        C += (T * al)[..., None] * sc.rgb[g]
+        T *= 1 - al
+    assert np.allclose(one["planes"][0, ..., :3], C, atol=1e-12)
+    assert np.allclose(one["planes"][0, ..., 3], 1 - T, atol=1e-12)
+    assert np.allclose(one["views"][0], one["planes"][0], atol=1e-12)
+    for N in (2, 7, 16, 64):
+        for mode in ("quantile", "disparity"):
+            many = orc.render(scene=sc, camera=cam, display=disp, views=S.ViewSet(1), N=N, binning=mode)
+            assert np.allclose(many["views"], one["views"], atol=1e-12), (N, mode)
+
+
+def test_chunk_invariance_with_shifted_reference(orc):
+    # D_shift = D_forward0 puts the reference camera at the base camera:
+    # every plane maps the centre view identically, so the centre view is
+    # independent of N even with a viewing angle.
+    cam = S.identity_camera(48, 50.0)
+    d0 = orc.make_ref(cam, S.display_for(3.0, 0.1)).D_forward0
+    disp = S.display_for(3.0, 0.1, D_shift=d0)
+    sc = _rand_scene(400, 9)
+    base = orc.render(scene=sc, camera=cam, display=disp, views=S.ViewSet(1), N=1, binning="quantile")
+    for N in (3, 16):
+        many = orc.render(scene=sc, camera=cam, display=disp, views=S.ViewSet(1), N=N, binning="quantile")
+        assert np.allclose(many["views"], base["views"], atol=1e-12)
