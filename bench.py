@@ -1,0 +1,332 @@
+"""Benchmark: light-field frames/s of the G2LF hot path on the display-scale
+workload (1M anisotropic Gaussians in 200 blobs, 512x512 reference planes,
+N_chunk = 64 quantile planes, 45 views over +-0.15), one step = one LF frame:
+lf_build_mpi_gaussians (project, depth sort, bin, tile lists, rasterise)
++ lf_composite (45 views), all inputs resident in HBM.
+
+Prints one JSON line (rank 0). FP32 planes are the primary number; FP16 and
+BF16 planes are reported beside it. See the design doc for the roofline figures.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(n=1_000_000, res=512, N=64, V=45, seed=2)
+METRIC = "LF frames/s (45 views, 512p, 1M Gaussians) FP16 vs FP32 planes; % HBM roofline"
+UNIT = "LF frames/s"
+L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _config(extra=None):
+    c = {"workload": "g2lf_display_1M_512px_N64_45v",
+         "gaussians": WORKLOAD["n"], "plane_res": [WORKLOAD["res"], WORKLOAD["res"]],
+         "view_res": [WORKLOAD["res"], WORKLOAD["res"]], "N_chunk": WORKLOAD["N"], "views": WORKLOAD["V"],
+         "binning": "quantile", "sampling": "nearest", "P_s": 1,
+         "l2": "flushed between timed steps (512 MB write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2508_18540_gb300 import api
+    from paper_2508_18540_gb300 import synth as S
+
+    rank, world, local = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    # replicas: every rank renders its own frame stream of the same-sized workload
+    wl = S.workload_display(seed=WORKLOAD["seed"] + rank, n=WORKLOAD["n"], res=WORKLOAD["res"], N=WORKLOAD["N"],
+                            V=WORKLOAD["V"])
+    g = api.DeviceGaussians.from_scene(wl.scene, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(renderer, steps, warmup, trace=False):
+        for _ in range(warmup):
+            renderer.render(g)
+        st, needed, M = renderer.status()
+        if st != 0:
+            raise RuntimeError("build failed with status %d (pairs needed %d)" % (st, needed))
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if trace:
+            api.lf_trace_collect()
+            api.lf_trace_enable(True)
+        l0 = api.lf_launch_count()
+        for a, b in ev:
+            flush.zero_()                  # L2 flush, outside the timed events
+            a.record(stream)
+            renderer.render(g)
+            b.record(stream)
+        launches = api.lf_launch_count() - l0
+        barrier()
+        stages = {}
+        if trace:
+            api.lf_trace_enable(False)
+            stages = api.lf_trace_collect()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item()) / steps, launches // steps, stages
+
+    res = {}
+    clocks = ClockSampler(local)
+    for dtype in ("f32", "f16", "bf16"):
+        r = api.LightFieldRenderer(wl.camera, wl.display, wl.views, wl.N, wl.binning, dtype, device=dev)
+        if dtype == "f32":
+            clocks.start()
+        ms, launches, stages = timed(r, args.steps, args.warmup, trace=True)
+        if dtype == "f32":
+            clk = clocks.stop()
+        res[dtype] = dict(ms=ms, launches=launches, stages=stages, renderer=r)
+
+    # end to end through the public API with host buffers (pinned), f32 planes
+    r32 = res["f32"]["renderer"]
+    host_in = api.DeviceGaussians.from_scene(wl.scene, pin=True)
+    host_out = torch.empty(r32.out.shape, dtype=torch.float32, pin_memory=True)
+    h2d = sum(t.numel() * t.element_size() for t in (host_in.means, host_in.scales, host_in.quats,
+                                                     host_in.opacity, host_in.rgb))
+    d2h = host_out.numel() * host_out.element_size()
+
+    def e2e_step():
+        for dst, src in ((g.means, host_in.means), (g.scales, host_in.scales), (g.quats, host_in.quats),
+                         (g.opacity, host_in.opacity), (g.rgb, host_in.rgb)):
+            dst.copy_(src, non_blocking=True)
+        r32.render(g)
+        host_out.copy_(r32.out, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    barrier()
+    e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in e_ev:
+        flush.zero_()
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+    barrier()
+    e_ms = sum(a.elapsed_time(b) for a, b in e_ev) / args.steps
+    t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e_ms = float(t.item())
+
+    # per-kernel roofline of the dominant stage (live event times above)
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    rect = r32.planes.rect[: wl.scene.n].to(torch.int64)
+    area = ((rect[:, 2] - rect[:, 0] + 1).clamp(min=0) * (rect[:, 3] - rect[:, 1] + 1).clamp(min=0))
+    pairs = int(area.sum().item())
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+
+    def roof(dtype):
+        st = res[dtype]["stages"]
+        bp = {"f32": 4, "f16": 2, "bf16": 2}[dtype]
+        out = {}
+        if "composite" in st:
+            ms_c = st["composite"][0] / st["composite"][1]
+            byt = WORKLOAD["N"] * WORKLOAD["res"] ** 2 * 4 * bp + WORKLOAD["V"] * WORKLOAD["res"] ** 2 * 16
+            ach = byt / (ms_c * 1e-3) / 1e9
+            out["composite"] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                                "frac": round(ach / hbm, 4), "traffic": None, "ms": round(ms_c, 4),
+                                "algorithmic_bytes": byt, "peak_source": "measured"}
+        if "raster_gaussians" in st:
+            ms_r = st["raster_gaussians"][0] / st["raster_gaussians"][1]
+            flops = pairs * 15
+            peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+            ach = flops / (ms_r * 1e-3) / 1e12
+            out["raster_gaussians"] = {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2),
+                                       "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                                       "ms": round(ms_r, 4), "pairs": pairs, "flops_per_pair": 15,
+                                       "peak_source": "SMs x 128 FP32 lanes x 2 x sampled median SM clock"}
+        return out
+
+    roofs = {d: roof(d) for d in res}
+    dom = max(res["f32"]["stages"].items(), key=lambda kv: kv[1][0])[0] if res["f32"]["stages"] else None
+    primary = roofs["f32"].get(dom) or roofs["f32"].get("composite")
+
+    line = None
+    if rank == 0:
+        fps = 1000.0 / res["f32"]["ms"] * world
+        line = {
+            "metric": METRIC, "value": round(fps, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(res["f32"]["ms"], 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config({"planes": "f32", "parallelism": "replicas" if world > 1 else "single"}),
+            "views_per_s": round(fps * WORKLOAD["V"], 1),
+            "variants": {d: {"planes": d, "value": round(1000.0 / res[d]["ms"] * world, 2),
+                             "ms_per_step": round(res[d]["ms"], 4), "roofline": roofs[d]}
+                         for d in ("f16", "bf16")},
+            "stages_ms": {d: {k: round(v[0] / v[1], 4) for k, v in res[d]["stages"].items()} for d in res},
+            "e2e": {"value": round(1000.0 / e_ms * world, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e_ms, 4)},
+            "gpu_launches": res["f32"]["launches"] * args.steps,
+            "roofline": dict(primary, kernel=dom if dom in roofs["f32"] else "composite") if primary else None,
+            "roofline_by_kernel": roofs["f32"],
+            "clocks": clk,
+        }
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+def cpu_baseline(n_frames=1):
+    """The FP64 oracle, as it stands, on the host cores: one full LF frame of
+    the same workload (all 1M Gaussians splatted into 64 planes, 45 views
+    composited)."""
+    import oracle
+    from paper_2508_18540_gb300 import synth as S
+    wl = S.workload_display(seed=WORKLOAD["seed"], n=WORKLOAD["n"], res=WORKLOAD["res"], N=WORKLOAD["N"],
+                            V=WORKLOAD["V"])
+    oracle.lib()
+    t0 = time.perf_counter()
+    for _ in range(n_frames):
+        oracle.render(wl)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(n_frames / dt, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d full LF frame(s) of the 1M-Gaussian 512px N64 45-view workload, FP64, OpenMP" % n_frames,
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return None
+    import oracle
+    from paper_2508_18540_gb300 import synth as S
+    wl = S.workload_display(seed=WORKLOAD["seed"], n=WORKLOAD["n"], res=WORKLOAD["res"], N=WORKLOAD["N"],
+                            V=WORKLOAD["V"])
+    oracle.lib()
+    for _ in range(args.warmup):
+        oracle.render(wl, with_views=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.render(wl)
+    dt = (time.perf_counter() - t0) / args.steps
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    v = round(1.0 / dt, 4)
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config({"planes": "f64", "parallelism": "host cores"}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one full LF frame per step (warm-up steps splat only)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    import __graft_entry__
+    __graft_entry__.build()
+    if args.impl == "reference":
+        line = run_reference(args)
+    else:
+        line = run_ours(args)
+        rank, world, _ = _env_rank()
+        if line is not None and world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

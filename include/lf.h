@@ -1,0 +1,249 @@
+/*
+ * lf.h -- C ABI of the GB300 (sm_103a) G2LF / V2LF library (liblf.so).
+ *
+ * Implements the hot path of "Real-time 3D Visualization of Radiance Fields
+ * on Light Field Displays" (arXiv 2508.18540): a radiance field (3D Gaussians
+ * with DC colour, or sparse voxels) is splatted once into N_chunk
+ * depth-binned RGBA sweeping planes seen from a reference camera
+ * (Sec. 4.2, 4.4, 4.5; Algorithm 1 lines 1-5), and the planes are composited
+ * into every light-field view in one pass ("swizzle blending", Sec. 4.3,
+ * Eq. (u_prime), Eq. (alpha_blend); Algorithm 1 lines 6-11).
+ *
+ * Conventions shared by every entry point
+ *  - Camera frame: +x right, +y down, +z forward. The base camera maps a world
+ *    point p to R p + t. The reference camera is the base camera moved
+ *    D_forward along +z (Sec. 4.2).
+ *  - Planes are W x H = (P_s Nx) x (P_s Ny) (Sec. 4.2); texel (x, y) has its
+ *    centre at normalised coordinate ((2x+1)/W - 1, (2y+1)/H - 1).
+ *  - Every texel and view pixel is RGBA: premultiplied colour, A = 1 - T.
+ *  - Memory: every pointer documented "device" is caller-owned device memory
+ *    on the current CUDA device; "host" pointers are caller-owned host memory.
+ *    The library allocates nothing: scratch lives in a caller-provided
+ *    workspace whose size is returned by the matching *_workspace_size call.
+ *  - Streams: compute entry points enqueue work on the given stream and return
+ *    without synchronising. Their argument checks happen on the host before
+ *    anything is enqueued. Data-dependent failures (tile-list overflow) are
+ *    recorded in the workspace and read back with lf_mpi_status().
+ *  - Errors: every call returns an lf_status; lf_last_error() gives a
+ *    thread-local message for the last failing call on this thread.
+ */
+#ifndef LF_H
+#define LF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LF_OK = 0,
+    LF_ERR_INVALID_ARG = 1,   /* bad pointer, size, layout or parameter */
+    LF_ERR_WORKSPACE = 2,     /* workspace missing or too small */
+    LF_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has it) */
+    LF_ERR_OVERFLOW = 4,      /* tile list larger than the workspace capacity */
+    LF_ERR_UNSUPPORTED = 5,   /* valid request this build does not implement */
+    LF_ERR_TIMEOUT = 6        /* a bounded device-side wait gave up */
+} lf_status;
+
+typedef enum { LF_F32 = 0, LF_F16 = 1, LF_BF16 = 2 } lf_dtype;
+
+typedef enum {
+    LF_BIN_QUANTILE = 0,      /* Sec. 4.4: equal-count chunks, d_k = median depth */
+    LF_BIN_DISPARITY = 1      /* N equal bins in 1/z between nearest and farthest */
+} lf_binning;
+
+/* Base camera (Sec. 4.2): world -> camera R (row-major), t; full fields of
+ * view theta_x, theta_y in radians; per-view resolution Nx x Ny. */
+typedef struct {
+    double R[9];
+    double t[3];
+    double theta_x, theta_y;
+    int32_t Nx, Ny;
+} lf_camera;
+
+/* Display set-up (Sec. 4.2, 4.3): focal distance D_focal, viewing angles
+ * phi_x, phi_y (radians), backward shift D_shift, plane resolution scale P_s
+ * (positive integer), 3DGS dilation f (f_aa, 0.3 px^2 in 3DGS), near clip
+ * z_near (> 0) on reference depth. */
+typedef struct {
+    double D_focal, phi_x, phi_y, D_shift;
+    int32_t P_s;
+    double f_aa, z_near;
+} lf_display;
+
+/* Reference camera, filled by lf_make_ref_camera (all FP64):
+ *  tth = tan(theta/2), tphi = tan(phi/2);
+ *  D_forward0 = Eq. (1); D_forward = D_forward0 - D_shift;
+ *  tthp = tan(theta'/2) from Eq. (2) with D_forward0; theta_p = theta';
+ *  fx = W / (2 tthp_x), cx = (W - 1)/2 (plane pixels), same for y;
+ *  f_prime = Eq. (gs_prefilter_fix) with the shifted D_forward. */
+typedef struct {
+    lf_camera base;
+    lf_display disp;
+    double tth_x, tth_y, tphi_x, tphi_y;
+    double D_forward0, D_forward;
+    double tthp_x, tthp_y, theta_px, theta_py;
+    double fx, fy, cx, cy;
+    double f_prime;
+    int32_t W, H;
+} lf_ref_camera;
+
+/* 3D Gaussians, structure of arrays, device, FP32, activated values:
+ * means [n][3], scales [n][3] (standard deviations), quats [n][4] (w, x, y, z;
+ * normalised inside), opacity [n] in (0, 1), rgb [n][3] (DC colour). */
+typedef struct {
+    int64_t n;
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* opacity;
+    const float* rgb;
+} lf_gaussians;
+
+/* Sparse voxels (Sec. 4.5): voxel v is the axis-aligned cube with low corner
+ * origin + ijk[v] * s_v and side s_v = base_size * 2^-level[v].
+ * ijk [n][3] int32, level [n] uint8, density8 [n][8] FP32 (activated,
+ * corner c = i + 2j + 4k at offset (i, j, k)), rgb [n][3] FP32; device. */
+typedef struct {
+    int64_t n;
+    const int32_t* ijk;
+    const uint8_t* level;
+    double origin[3];
+    double base_size;
+    const float* density8;
+    const float* rgb;
+} lf_voxels;
+
+/* Sweeping planes (Sec. 4.2 C and T), caller-allocated device memory:
+ *  rgba  [N][H][W][4] of dtype (premultiplied RGB, A = 1 - T);
+ *  d     [N] FP64 plane distances in the base camera frame (0 if empty);
+ *  count [N] int32 members per chunk;
+ *  chunk [n] int32 chunk of every primitive (-1 = culled);
+ *  rect  [n][4] int32 inclusive footprint {x0, y0, x1, y1} ({0,0,-1,-1} if culled).
+ * N, H, W, dtype describe rgba; H, W must equal the reference camera's. */
+typedef struct {
+    int32_t N, H, W;
+    int32_t dtype;
+    void* rgba;
+    double* d;
+    int32_t* count;
+    int32_t* chunk;
+    int32_t* rect;
+} lf_planes;
+
+/* Quilt views (Sec. 4.3): Vx x Vy views, view index i * Vx + j; nearest
+ * (bilinear = 0, the paper's default) or bilinear sampling; background
+ * colour bg under the remaining transmittance (0 in the paper). */
+typedef struct {
+    int32_t Vx, Vy;
+    int32_t bilinear;
+    float bg[3];
+} lf_view_set;
+
+/* ---- set-up ------------------------------------------------------------ */
+
+/* Sec. 4.2 Eqs. (1)-(2), the D_shift update and Eq. (gs_prefilter_fix).
+ * cam, disp, out: host. Fails with LF_ERR_INVALID_ARG for non-positive sizes,
+ * fields of view outside (0, pi), D_focal or z_near <= 0, P_s < 1, or a
+ * shift that leaves D_forward >= D_focal. */
+lf_status lf_make_ref_camera(const lf_camera* cam, const lf_display* disp, lf_ref_camera* out);
+
+/* ---- splat: radiance field -> sweeping planes (Algorithm 1 lines 1-5) --- */
+
+/* Workspace bytes for lf_build_mpi_* on n primitives into N planes of the
+ * reference camera ref, with room for dup_capacity (primitive, 16x16 tile)
+ * pairs (0 = 8 n + 2^20). */
+size_t lf_build_mpi_workspace_size(const lf_ref_camera* ref, int64_t n, int32_t N, int64_t dup_capacity);
+
+/* Sec. 4.4 (G2LF). Culls Gaussians to the reference frustum (reference depth
+ * > z_near, non-empty footprint), sorts them by (FP64 depth, index), bins
+ * them (quantile: chunk = floor(rank N / M), d_k = median depth; disparity:
+ * equal bins in 1/z), and rasterises each chunk into its plane with the EWA
+ * projection of 3DGS plus the dilation f' (alpha = min(0.99, o e^{-q/2}),
+ * front to back, no early stop). All planes are written (empty ones with 0).
+ * g: host struct of device pointers; ref, out: host structs; ws: device
+ * workspace of ws_bytes; stream: the CUDA stream to enqueue on.
+ * Errors: LF_ERR_INVALID_ARG (null pointer, N < 1 or > 65535, plane size not
+ * the reference camera's, unknown dtype or binning), LF_ERR_WORKSPACE,
+ * LF_ERR_CUDA (launch failure). Tile-list overflow is reported by
+ * lf_mpi_status after the stream has run. */
+lf_status lf_build_mpi_gaussians(const lf_gaussians* g, const lf_ref_camera* ref, int32_t N, int32_t binning,
+                                 void* ws, size_t ws_bytes, lf_planes* out, cudaStream_t stream);
+
+/* Sec. 4.5 (V2LF). Same pipeline for sparse voxels: depth = cube centre,
+ * culled unless the whole cube lies past z_near; footprint = bounding box of
+ * the 8 projected corners; alpha = 1 - exp(-integral of the trilinear
+ * density over the pixel's reference-ray segment in the cube) (exact
+ * Simpson rule). Arguments and errors as lf_build_mpi_gaussians. */
+lf_status lf_build_mpi_voxels(const lf_voxels* v, const lf_ref_camera* ref, int32_t N, int32_t binning,
+                              void* ws, size_t ws_bytes, lf_planes* out, cudaStream_t stream);
+
+/* Synchronises with the stream the last build on ws was enqueued on and
+ * returns LF_ERR_OVERFLOW if its tile list exceeded the capacity (the planes
+ * are then all zero); *needed (host, may be NULL) receives the pair count
+ * and *culled_in (host, may be NULL) the number M of primitives kept. */
+lf_status lf_mpi_status(const void* ws, int64_t* needed, int64_t* culled_in);
+
+/* Copies the build's sorted order and tile lists out of ws (synchronous).
+ * order [n] int32 (host): primitive index of ranks 0..M-1; tile_prims
+ * [cap] int32 (host): primitive of every (tile, chunk) entry in list order;
+ * seg [tiles * N][2] int32 (host): [start, end) of every (tile, chunk) list,
+ * tiles = ceil(W/16) * ceil(H/16), segment index tile * N + chunk. Any output
+ * may be NULL. Fails with LF_ERR_INVALID_ARG if cap is smaller than the pair
+ * count. For tests and inspection. */
+lf_status lf_mpi_tile_lists(const void* ws, int32_t* order, int64_t n, int32_t* tile_prims, int64_t cap,
+                            int32_t* seg);
+
+/* ---- composite: planes -> quilt views (Algorithm 1 lines 6-11) --------- */
+
+/* Workspace bytes for lf_composite / lf_composite_backward. */
+size_t lf_composite_workspace_size(int32_t N, const lf_view_set* views);
+
+/* Sec. 4.3 swizzle blending. For every view (i, j) and pixel (x, y), planes
+ * are visited front to back; plane k is sampled at the Eq. (u_prime)
+ * position X = ((u'+1) W - 1)/2 (nearest: floor(X + 1/2); bilinear with
+ * transparent zero padding), and composited Q += T c_k, T *= 1 - A_k
+ * (Eq. (alpha_blend)); empty planes (count 0) are skipped. Output
+ * views [Vy*Vx][Ny][Nx][4] FP32 device = (Q + T bg, 1 - T).
+ * The nearest index is decided in FP32 from per-(view, plane) coefficients
+ * computed in FP64 (same decision as the CPU reference).
+ * Errors: LF_ERR_INVALID_ARG, LF_ERR_WORKSPACE, LF_ERR_CUDA. */
+lf_status lf_composite(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views, float* out,
+                       void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---- tracing -------------------------------------------------------------- */
+
+/* Number of kernels the library has launched in this process so far. */
+int64_t lf_launch_count(void);
+
+/* Turns stage tracing on or off for calls made from this thread: while on,
+ * every pipeline stage of lf_build_mpi_* and lf_composite (project,
+ * depth_sort, bin, duplicate, tile_sort, ranges, raster_*, comp_coeffs,
+ * composite) is bracketed by a CUDA event pair recorded on the call's stream.
+ * Always returns LF_OK. */
+lf_status lf_trace_enable(int32_t on);
+
+/* Waits for the recorded events, then returns the number of distinct stages
+ * (at most max_stages) and for each, in first-seen order: its name in
+ * names[32*k .. 32*k+31] (host, NUL-terminated), total milliseconds
+ * total_ms[k] and number of traced calls launches[k] (host); any output may
+ * be NULL. Clears the record. */
+int32_t lf_trace_collect(char* names, double* total_ms, int64_t* launches, int32_t max_stages);
+
+/* ---- misc --------------------------------------------------------------- */
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* lf_last_error(void);
+
+/* Library version string. */
+const char* lf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LF_H */

@@ -1,0 +1,315 @@
+"""Thin PyTorch-facing binding of liblf (same names as the C ABI in include/lf.h).
+
+PyTorch supplies device memory and streams; every computation of the path
+runs in liblf's kernels. Tensors are passed by data pointer; shapes, dtypes,
+devices and contiguity are checked here before the call.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from ._lib import check, load
+
+DTYPES = {"f32": L.LF_F32, "f16": L.LF_F16, "bf16": L.LF_BF16}
+TORCH_DTYPES = {L.LF_F32: torch.float32, L.LF_F16: torch.float16, L.LF_BF16: torch.bfloat16}
+BINNING = {"quantile": L.LF_BIN_QUANTILE, "disparity": L.LF_BIN_DISPARITY}
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _need(t: torch.Tensor, shape, dtype, name):
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
+# ---------------------------------------------------------------------------
+# set-up
+# ---------------------------------------------------------------------------
+
+def lf_make_ref_camera(camera, display) -> L.LfRefCamera:
+    """Sec. 4.2: reference camera (Eqs. (1)-(2), D_shift, Eq. (gs_prefilter_fix))."""
+    lib = load()
+    cam = L.LfCamera()
+    cam.R[:] = [float(v) for v in np.asarray(camera.R, np.float64).reshape(9)]
+    cam.t[:] = [float(v) for v in np.asarray(camera.t, np.float64).reshape(3)]
+    cam.theta_x, cam.theta_y = float(camera.theta_x), float(camera.theta_y)
+    cam.Nx, cam.Ny = int(camera.Nx), int(camera.Ny)
+    disp = L.LfDisplay(float(display.D_focal), float(display.phi_x), float(display.phi_y), float(display.D_shift),
+                       int(display.P_s), float(display.f_aa), float(display.z_near))
+    ref = L.LfRefCamera()
+    check(lib.lf_make_ref_camera(ctypes.byref(cam), ctypes.byref(disp), ctypes.byref(ref)))
+    return ref
+
+
+# ---------------------------------------------------------------------------
+# device-resident inputs and outputs
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class DeviceGaussians:
+    means: torch.Tensor
+    scales: torch.Tensor
+    quats: torch.Tensor
+    opacity: torch.Tensor
+    rgb: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @classmethod
+    def from_scene(cls, scene, device="cuda", pin: bool = False):
+        def put(a):
+            t = torch.from_numpy(np.ascontiguousarray(a, np.float32))
+            return t.pin_memory() if pin else t.to(device)
+        return cls(put(scene.means), put(scene.scales), put(scene.quats), put(scene.opacity), put(scene.rgb))
+
+    def c_struct(self) -> L.LfGaussians:
+        n = self.n
+        for name, t, w in (("means", self.means, 3), ("scales", self.scales, 3), ("quats", self.quats, 4),
+                           ("rgb", self.rgb, 3)):
+            _need(t, (n, w), torch.float32, name)
+        _need(self.opacity, (n,), torch.float32, "opacity")
+        return L.LfGaussians(n, self.means.data_ptr(), self.scales.data_ptr(), self.quats.data_ptr(),
+                             self.opacity.data_ptr(), self.rgb.data_ptr())
+
+
+@dataclasses.dataclass
+class DeviceVoxels:
+    ijk: torch.Tensor
+    level: torch.Tensor
+    density8: torch.Tensor
+    rgb: torch.Tensor
+    origin: tuple
+    base_size: float
+
+    @property
+    def n(self) -> int:
+        return int(self.ijk.shape[0])
+
+    @classmethod
+    def from_scene(cls, scene, device="cuda"):
+        return cls(torch.from_numpy(np.ascontiguousarray(scene.ijk, np.int32)).to(device),
+                   torch.from_numpy(np.ascontiguousarray(scene.level, np.uint8)).to(device),
+                   torch.from_numpy(np.ascontiguousarray(scene.density8, np.float32)).to(device),
+                   torch.from_numpy(np.ascontiguousarray(scene.rgb, np.float32)).to(device),
+                   tuple(float(v) for v in scene.origin), float(scene.base_size))
+
+    def c_struct(self) -> L.LfVoxels:
+        n = self.n
+        _need(self.ijk, (n, 3), torch.int32, "ijk")
+        _need(self.level, (n,), torch.uint8, "level")
+        _need(self.density8, (n, 8), torch.float32, "density8")
+        _need(self.rgb, (n, 3), torch.float32, "rgb")
+        v = L.LfVoxels()
+        v.n = n
+        v.ijk, v.level = self.ijk.data_ptr(), self.level.data_ptr()
+        v.origin[:] = list(self.origin)
+        v.base_size = self.base_size
+        v.density8, v.rgb = self.density8.data_ptr(), self.rgb.data_ptr()
+        return v
+
+
+@dataclasses.dataclass
+class Planes:
+    """Sweeping planes and the per-primitive build outputs (device)."""
+    rgba: torch.Tensor       # [N][H][W][4] dtype
+    d: torch.Tensor          # [N] float64
+    count: torch.Tensor      # [N] int32
+    chunk: torch.Tensor      # [n] int32
+    rect: torch.Tensor       # [n][4] int32
+    dtype_code: int
+
+    @classmethod
+    def empty(cls, ref: L.LfRefCamera, N: int, n: int, dtype: str = "f32", device="cuda"):
+        code = DTYPES[dtype]
+        return cls(torch.empty((N, ref.H, ref.W, 4), dtype=TORCH_DTYPES[code], device=device),
+                   torch.empty(N, dtype=torch.float64, device=device),
+                   torch.empty(N, dtype=torch.int32, device=device),
+                   torch.empty(max(n, 1), dtype=torch.int32, device=device),
+                   torch.empty((max(n, 1), 4), dtype=torch.int32, device=device), code)
+
+    @property
+    def N(self) -> int:
+        return int(self.rgba.shape[0])
+
+    def c_struct(self) -> L.LfPlanes:
+        N, H, W = (int(v) for v in self.rgba.shape[:3])
+        _need(self.rgba, (N, H, W, 4), TORCH_DTYPES[self.dtype_code], "planes.rgba")
+        return L.LfPlanes(N, H, W, self.dtype_code, self.rgba.data_ptr(), self.d.data_ptr(),
+                          self.count.data_ptr(), self.chunk.data_ptr(), self.rect.data_ptr())
+
+
+def view_set(views) -> L.LfViewSet:
+    vs = L.LfViewSet()
+    vs.Vx, vs.Vy, vs.bilinear = int(views.Vx), int(views.Vy), int(bool(views.bilinear))
+    vs.bg[:] = [float(c) for c in views.bg]
+    return vs
+
+
+def alloc_workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    """Device workspace (caching-allocator blocks are 512-byte aligned)."""
+    ws = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    assert ws.data_ptr() % 256 == 0
+    return ws
+
+
+# ---------------------------------------------------------------------------
+# splat
+# ---------------------------------------------------------------------------
+
+def lf_build_mpi_workspace_size(ref: L.LfRefCamera, n: int, N: int, dup_capacity: int = 0) -> int:
+    return int(load().lf_build_mpi_workspace_size(ctypes.byref(ref), int(n), int(N), int(dup_capacity)))
+
+
+def lf_build_mpi_gaussians(g: DeviceGaussians, ref: L.LfRefCamera, N: int, binning: str, ws: torch.Tensor,
+                           planes: Planes, stream=None):
+    """Sec. 4.4 / Algorithm 1 lines 1-5 for 3D Gaussians (asynchronous)."""
+    gs = g.c_struct()
+    ps = planes.c_struct()
+    check(load().lf_build_mpi_gaussians(ctypes.byref(gs), ctypes.byref(ref), int(N), BINNING[binning],
+                                        _ptr(ws), ws.numel(), ctypes.byref(ps), _stream_ptr(stream)))
+
+
+def lf_build_mpi_voxels(v: DeviceVoxels, ref: L.LfRefCamera, N: int, binning: str, ws: torch.Tensor,
+                        planes: Planes, stream=None):
+    """Sec. 4.5 / Algorithm 1 lines 1-5 for sparse voxels (asynchronous)."""
+    vs = v.c_struct()
+    ps = planes.c_struct()
+    check(load().lf_build_mpi_voxels(ctypes.byref(vs), ctypes.byref(ref), int(N), BINNING[binning],
+                                     _ptr(ws), ws.numel(), ctypes.byref(ps), _stream_ptr(stream)))
+
+
+def lf_mpi_status(ws: torch.Tensor):
+    """(status, pairs needed, culled-in count) of the last build on ws (synchronising)."""
+    needed = ctypes.c_int64(0)
+    M = ctypes.c_int64(0)
+    st = load().lf_mpi_status(_ptr(ws), ctypes.byref(needed), ctypes.byref(M))
+    return st, needed.value, M.value
+
+
+def lf_mpi_tile_lists(ws: torch.Tensor, n: int, n_tiles: int, N: int):
+    """Sorted order, tile-list entries and (tile, chunk) segments (numpy)."""
+    st, needed, M = lf_mpi_status(ws)
+    check(st)
+    order = np.zeros(max(n, 1), np.int32)
+    prims = np.zeros(max(needed, 1), np.int32)
+    seg = np.zeros((n_tiles * N, 2), np.int32)
+    check(load().lf_mpi_tile_lists(_ptr(ws), order.ctypes.data_as(ctypes.c_void_p), int(n),
+                                   prims.ctypes.data_as(ctypes.c_void_p), int(prims.shape[0]),
+                                   seg.ctypes.data_as(ctypes.c_void_p)))
+    return order[:M], prims[:needed], seg
+
+
+# ---------------------------------------------------------------------------
+# composite
+# ---------------------------------------------------------------------------
+
+def lf_composite_workspace_size(N: int, views) -> int:
+    vs = view_set(views)
+    return int(load().lf_composite_workspace_size(int(N), ctypes.byref(vs)))
+
+
+def lf_composite(planes: Planes, ref: L.LfRefCamera, views, out: torch.Tensor, ws: torch.Tensor, stream=None):
+    """Sec. 4.3 swizzle blending into out [Vy*Vx][Ny][Nx][4] float32 (asynchronous)."""
+    vs = view_set(views)
+    _need(out, (vs.Vx * vs.Vy, ref.base.Ny, ref.base.Nx, 4), torch.float32, "views")
+    ps = planes.c_struct()
+    check(load().lf_composite(ctypes.byref(ps), ctypes.byref(ref), ctypes.byref(vs), _ptr(out), _ptr(ws),
+                              ws.numel(), _stream_ptr(stream)))
+
+
+# ---------------------------------------------------------------------------
+# convenience: one object holding every buffer of a workload
+# ---------------------------------------------------------------------------
+
+class LightFieldRenderer:
+    """Owns the device buffers for one (camera, display, views, N) set-up and
+    runs splat + composite through the C ABI."""
+
+    def __init__(self, camera, display, views, N: int, binning: str = "quantile", dtype: str = "f32",
+                 n_capacity: int = 0, dup_capacity: int = 0, device="cuda"):
+        self.camera, self.display, self.views = camera, display, views
+        self.N, self.binning, self.dtype = int(N), binning, dtype
+        self.ref = lf_make_ref_camera(camera, display)
+        self.device = device
+        self.n_capacity = int(n_capacity)
+        self.dup_capacity = int(dup_capacity)
+        self.planes = None
+        self.ws = None
+        self.cws = alloc_workspace(lf_composite_workspace_size(self.N, views), device)
+        self.out = torch.empty((views.Vx * views.Vy, camera.Ny, camera.Nx, 4), dtype=torch.float32, device=device)
+
+    def _ensure(self, n: int):
+        if self.planes is None or n > self.n_capacity:
+            self.n_capacity = max(n, self.n_capacity)
+            self.planes = Planes.empty(self.ref, self.N, self.n_capacity, self.dtype, self.device)
+            cap = self.dup_capacity if self.dup_capacity > 0 else 8 * self.n_capacity + (1 << 20)
+            self.ws = alloc_workspace(lf_build_mpi_workspace_size(self.ref, self.n_capacity, self.N, cap),
+                                      self.device)
+
+    def build(self, prims, stream=None):
+        self._ensure(prims.n)
+        pl = self.planes
+        view = Planes(pl.rgba, pl.d, pl.count, pl.chunk[: max(prims.n, 1)], pl.rect[: max(prims.n, 1)], pl.dtype_code)
+        if isinstance(prims, DeviceGaussians):
+            lf_build_mpi_gaussians(prims, self.ref, self.N, self.binning, self.ws, view, stream)
+        else:
+            lf_build_mpi_voxels(prims, self.ref, self.N, self.binning, self.ws, view, stream)
+        return view
+
+    def composite(self, stream=None, out: Optional[torch.Tensor] = None):
+        out = self.out if out is None else out
+        lf_composite(self.planes, self.ref, self.views, out, self.cws, stream)
+        return out
+
+    def render(self, prims, stream=None):
+        self.build(prims, stream)
+        return self.composite(stream)
+
+    def status(self):
+        return lf_mpi_status(self.ws)
+
+
+# ---------------------------------------------------------------------------
+# tracing
+# ---------------------------------------------------------------------------
+
+def lf_launch_count() -> int:
+    return int(load().lf_launch_count())
+
+
+def lf_trace_enable(on: bool):
+    check(load().lf_trace_enable(int(bool(on))))
+
+
+def lf_trace_collect(max_stages: int = 64) -> dict:
+    """{stage: (total_ms, calls)} of the traced stages since the last collect."""
+    names = ctypes.create_string_buffer(32 * max_stages)
+    ms = (ctypes.c_double * max_stages)()
+    calls = (ctypes.c_int64 * max_stages)()
+    k = load().lf_trace_collect(names, ms, calls, max_stages)
+    out = {}
+    for i in range(k):
+        nm = names.raw[32 * i:32 * i + 32].split(b"\0", 1)[0].decode()
+        out[nm] = (float(ms[i]), int(calls[i]))
+    return out

@@ -1,0 +1,558 @@
+// lf_api.cu -- C ABI entry points of liblf (declared in include/lf.h):
+// argument checks, host-side FP64 set-up, workspace carving and the launch
+// sequence of each stage. All arithmetic of the path runs in the kernels of
+// the other translation units.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "lf_internal.cuh"
+
+namespace lf {
+
+static thread_local std::string g_last_error;
+
+// ---- launch counting / stage tracing ------------------------------------
+static std::atomic<long long> g_launches{0};
+static thread_local bool g_trace_on = false;
+struct TraceRec {
+    std::string stage;
+    cudaEvent_t a, b;
+};
+static thread_local std::vector<TraceRec> g_trace;
+static thread_local std::vector<cudaEvent_t> g_event_pool;
+static thread_local int g_trace_open = -1;
+
+void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+static cudaEvent_t pool_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void trace_begin(const char* stage, cudaStream_t s)
+{
+    if (!g_trace_on) return;
+    TraceRec r{stage, pool_event(), pool_event()};
+    cudaEventRecord(r.a, s);
+    g_trace.push_back(r);
+    g_trace_open = (int)g_trace.size() - 1;
+}
+
+void trace_end(cudaStream_t s)
+{
+    if (!g_trace_on || g_trace_open < 0) return;
+    cudaEventRecord(g_trace[g_trace_open].b, s);
+    g_trace_open = -1;
+}
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+lf_status fail(lf_status st, const std::string& msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+lf_status check_launch(const char* what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(LF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return LF_OK;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+template <typename T>
+static T* carve(char* base, size_t& off, size_t count)
+{
+    off = align_up(off, 256);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += sizeof(T) * count;
+    return p;
+}
+
+size_t build_ws_layout(int64_t n, int32_t N, int32_t W, int32_t H, int64_t cap, void* basev, BuildWs* o)
+{
+    char* base = static_cast<char*>(basev);
+    const long long tiles = (long long)((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
+    const long long nmax = n > cap ? n : cap;
+    const long long nb = (nmax + kSortTile - 1) / kSortTile + 1;
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    const size_t cc = (size_t)(cap > 0 ? cap : 1);
+    size_t off = 0;
+    BuildWs w;
+    w.hdr = carve<WsHeader>(base, off, 1);
+    w.keyA = carve<unsigned long long>(base, off, nn);
+    w.keyB = carve<unsigned long long>(base, off, nn);
+    w.valA = carve<uint32_t>(base, off, nn);
+    w.valB = carve<uint32_t>(base, off, nn);
+    w.mean2d = carve<float2>(base, off, nn);
+    w.conic_o = carve<float4>(base, off, nn);
+    w.hist = carve<uint32_t>(base, off, (size_t)kRadix * nb + 1);
+    w.bsum = carve<uint32_t>(base, off, (size_t)nb + 1);
+    w.chunk_start = carve<int32_t>(base, off, (size_t)N + 1);
+    w.dkeyA = carve<uint32_t>(base, off, cc);
+    w.dkeyB = carve<uint32_t>(base, off, cc);
+    w.dvalA = carve<uint32_t>(base, off, cc);
+    w.dvalB = carve<uint32_t>(base, off, cc);
+    w.seg = carve<int2>(base, off, (size_t)tiles * N);
+    w.bytes = align_up(off, 256);
+    w.nb_max = nb;
+    if (o) *o = w;
+    return w.bytes;
+}
+
+size_t comp_ws_layout(int32_t N, int32_t Vx, int32_t Vy, void* basev, CompWs* o)
+{
+    char* base = static_cast<char*>(basev);
+    size_t off = 0;
+    CompWs w;
+    w.cx = carve<float>(base, off, (size_t)Vx * N * 3);
+    w.cy = carve<float>(base, off, (size_t)Vy * N * 3);
+    w.bytes = align_up(off, 256);
+    if (o) *o = w;
+    return w.bytes;
+}
+
+// stream each build workspace was last used on (for lf_mpi_status)
+static std::mutex g_ws_mu;
+static std::map<const void*, cudaStream_t> g_ws_stream;
+
+static int64_t default_cap(int64_t n) { return 8 * n + (1ll << 20); }
+
+static int tile_bits_for(long long tiles)
+{
+    int b = 1;
+    while ((1ll << b) < tiles) ++b;
+    return b;
+}
+
+// number of radix passes of the tile sort (its result is in the A buffers
+// after an even count, in the B buffers after an odd one)
+static int tile_sort_passes(long long tiles) { return (tile_bits_for(tiles) + kRadixBits - 1) / kRadixBits; }
+
+static lf_status check_ref(const lf_ref_camera* r)
+{
+    if (!r) return fail(LF_ERR_INVALID_ARG, "ref camera is NULL");
+    if (r->W <= 0 || r->H <= 0 || r->W > 32768 || r->H > 32768)
+        return fail(LF_ERR_INVALID_ARG, "reference plane size out of range (1..32768)");
+    if (!(r->fx > 0) || !(r->fy > 0)) return fail(LF_ERR_INVALID_ARG, "ref camera not initialised");
+    return LF_OK;
+}
+
+static lf_status check_planes(const lf_planes* p, const lf_ref_camera* r, int32_t N)
+{
+    if (!p) return fail(LF_ERR_INVALID_ARG, "planes is NULL");
+    if (N < 1 || N > 65535) return fail(LF_ERR_INVALID_ARG, "N_chunk must be in 1..65535");
+    if (p->N != N || p->W != r->W || p->H != r->H)
+        return fail(LF_ERR_INVALID_ARG, "plane array shape does not match N / reference camera");
+    if (p->dtype < LF_F32 || p->dtype > LF_BF16) return fail(LF_ERR_INVALID_ARG, "unknown plane dtype");
+    if (!p->rgba || !p->d || !p->count || !p->chunk || !p->rect)
+        return fail(LF_ERR_INVALID_ARG, "a plane output pointer is NULL");
+    return LF_OK;
+}
+
+static void fill_proj_params(const lf_ref_camera* r, int64_t n, ProjParams* p)
+{
+    std::memset(p, 0, sizeof(*p));
+    for (int i = 0; i < 9; ++i) {
+        p->R[i] = r->base.R[i];
+        p->Rf[i] = (float)r->base.R[i];
+    }
+    for (int i = 0; i < 3; ++i) p->t[i] = r->base.t[i];
+    p->D_forward = r->D_forward;
+    p->z_near = r->disp.z_near;
+    p->rho = std::fabs(r->base.R[6]) + std::fabs(r->base.R[7]) + std::fabs(r->base.R[8]);
+    p->t0f = (float)r->base.t[0];
+    p->t1f = (float)r->base.t[1];
+    p->t2rf = (float)(r->base.t[2] - r->D_forward);
+    p->fxf = (float)r->fx;
+    p->fyf = (float)r->fy;
+    p->cxf = (float)r->cx;
+    p->cyf = (float)r->cy;
+    p->fpf = (float)r->f_prime;
+    p->wmax = (float)(r->W - 1);
+    p->hmax = (float)(r->H - 1);
+    p->W = r->W;
+    p->H = r->H;
+    p->n = n;
+    // reference centre in world coordinates: R o + t - D_forward e_z = 0
+    const double b[3] = {-r->base.t[0], -r->base.t[1], r->D_forward - r->base.t[2]};
+    for (int i = 0; i < 3; ++i)
+        p->cam_o[i] = r->base.R[i] * b[0] + r->base.R[3 + i] * b[1] + r->base.R[6 + i] * b[2];
+}
+
+static void fill_raster_params(const lf_ref_camera* r, int32_t N, int32_t dtype, RasterParams* p)
+{
+    std::memset(p, 0, sizeof(*p));
+    p->W = r->W;
+    p->H = r->H;
+    p->N = N;
+    p->tiles_x = (r->W + kTile - 1) / kTile;
+    p->tiles_y = (r->H + kTile - 1) / kTile;
+    p->dtype = dtype;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) p->Rt[3 * i + j] = (float)r->base.R[3 * j + i];
+    p->fx = (float)r->fx;
+    p->fy = (float)r->fy;
+    p->cx = (float)r->cx;
+    p->cy = (float)r->cy;
+}
+
+template <typename Launch>
+static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, int32_t binning, void* ws,
+                              size_t ws_bytes, lf_planes* out, cudaStream_t stream, int kind, Launch project,
+                              const void* raster_arg)
+{
+    lf_status st = check_ref(ref);
+    if (st != LF_OK) return st;
+    st = check_planes(out, ref, N);
+    if (st != LF_OK) return st;
+    if (binning != LF_BIN_QUANTILE && binning != LF_BIN_DISPARITY)
+        return fail(LF_ERR_INVALID_ARG, "unknown binning mode");
+    if (n < 0 || n > (int64_t)0x7fffffff) return fail(LF_ERR_INVALID_ARG, "primitive count out of range");
+    if (!ws) return fail(LF_ERR_WORKSPACE, "workspace is NULL");
+    if (((uintptr_t)ws) % 256) return fail(LF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+
+    // pair capacity: the largest one the given workspace holds (the layout
+    // size grows monotonically with it)
+    int64_t lo = 0, hi = (1ll << 31) - 1;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (build_ws_layout(n, N, ref->W, ref->H, mid, nullptr, nullptr) <= ws_bytes)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    if (lo < 1) {
+        const size_t need = build_ws_layout(n, N, ref->W, ref->H, default_cap(n), nullptr, nullptr);
+        return fail(LF_ERR_WORKSPACE, "workspace too small (default capacity needs " + std::to_string(need) +
+                                          " bytes)");
+    }
+    const int64_t cap = lo;
+    BuildWs w;
+    build_ws_layout(n, N, ref->W, ref->H, cap, ws, &w);
+
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        g_ws_stream[ws] = stream;
+    }
+
+    WsHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.kmin = ~0ull;
+    h.kmax = 0;
+    h.kind = kind;
+    h.n = n;
+    h.dup_capacity = cap;
+    h.N = N;
+    h.W = ref->W;
+    h.H = ref->H;
+    h.tiles_x = (ref->W + kTile - 1) / kTile;
+    h.tiles_y = (ref->H + kTile - 1) / kTile;
+    h.binning = binning;
+    // the header is written by a kernel so the whole build stays on the stream
+    launch_init_header(h, w.hdr, stream);
+    if ((st = check_launch("header init")) != LF_OK) return st;
+    const long long n_tiles = (long long)h.tiles_x * h.tiles_y;
+    if (cudaMemsetAsync(w.seg, 0, sizeof(int2) * (size_t)n_tiles * N, stream) != cudaSuccess)
+        return check_launch("segment reset");
+
+    ProjParams pp;
+    fill_proj_params(ref, n, &pp);
+    trace_begin("project", stream);
+    project(pp, w, stream);
+    trace_end(stream);
+    if ((st = check_launch("project")) != LF_OK) return st;
+
+    trace_begin("depth_sort", stream);
+    sort_depth_keys(w, n, stream);
+    trace_end(stream);
+    if ((st = check_launch("depth sort")) != LF_OK) return st;
+
+    BinParams bp;
+    bp.N = N;
+    bp.binning = binning;
+    bp.D_forward = ref->D_forward;
+    trace_begin("bin", stream);
+    launch_bin(w, bp, n, out->chunk, out->d, out->count, stream);
+    trace_end(stream);
+    if ((st = check_launch("bin")) != LF_OK) return st;
+
+    trace_begin("duplicate", stream);
+    launch_duplicate(w, n, out->rect, h.tiles_x, stream);
+    trace_end(stream);
+    if ((st = check_launch("duplicate")) != LF_OK) return st;
+
+    uint32_t* tkeys = nullptr;
+    uint32_t* tvals = nullptr;
+    trace_begin("tile_sort", stream);
+    sort_tile_keys(w, cap, tile_bits_for(n_tiles), stream, &tkeys, &tvals);
+    trace_end(stream);
+    if ((st = check_launch("tile sort")) != LF_OK) return st;
+
+    trace_begin("ranges", stream);
+    launch_ranges(w, cap, tkeys, tvals, out->chunk, N, stream);
+    trace_end(stream);
+    if ((st = check_launch("ranges")) != LF_OK) return st;
+
+    RasterParams rp;
+    fill_raster_params(ref, N, out->dtype, &rp);
+    trace_begin(kind == 0 ? "raster_gaussians" : "raster_voxels", stream);
+    if (kind == 0)
+        launch_raster_gaussians(w, rp, tvals, static_cast<const lf_gaussians*>(raster_arg)->rgb, out->rect,
+                                out->rgba, stream);
+    else
+        launch_raster_voxels(w, rp, tvals, *static_cast<const lf_voxels*>(raster_arg), out->rect, out->rgba, stream);
+    trace_end(stream);
+    return check_launch("rasterise");
+}
+
+}  // namespace lf
+
+using namespace lf;
+
+extern "C" {
+
+const char* lf_last_error(void) { return lf::g_last_error.c_str(); }
+
+const char* lf_version(void) { return "liblf 0.1 (sm_103a)"; }
+
+int64_t lf_launch_count(void) { return (int64_t)g_launches.load(); }
+
+lf_status lf_trace_enable(int32_t on)
+{
+    g_trace_on = on != 0;
+    return LF_OK;
+}
+
+int32_t lf_trace_collect(char* names, double* total_ms, int64_t* launches, int32_t max_stages)
+{
+    std::vector<std::string> order;
+    std::map<std::string, std::pair<double, int64_t>> acc;
+    for (auto& r : g_trace) {
+        float ms = 0.f;
+        cudaEventSynchronize(r.b);
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        if (!acc.count(r.stage)) order.push_back(r.stage);
+        acc[r.stage].first += ms;
+        acc[r.stage].second += 1;
+        g_event_pool.push_back(r.a);
+        g_event_pool.push_back(r.b);
+    }
+    g_trace.clear();
+    int32_t k = 0;
+    for (auto& nm : order) {
+        if (k >= max_stages) break;
+        if (names) {
+            std::strncpy(names + 32 * k, nm.c_str(), 31);
+            names[32 * k + 31] = 0;
+        }
+        if (total_ms) total_ms[k] = acc[nm].first;
+        if (launches) launches[k] = acc[nm].second;
+        ++k;
+    }
+    return k;
+}
+
+lf_status lf_make_ref_camera(const lf_camera* cam, const lf_display* disp, lf_ref_camera* r)
+{
+    if (!cam || !disp || !r) return fail(LF_ERR_INVALID_ARG, "NULL argument");
+    std::memset(r, 0, sizeof(*r));
+    r->base = *cam;
+    r->disp = *disp;
+    if (cam->Nx <= 0 || cam->Ny <= 0 || disp->P_s <= 0) return fail(LF_ERR_INVALID_ARG, "sizes must be positive");
+    if (!(disp->D_focal > 0.0) || !(disp->z_near > 0.0))
+        return fail(LF_ERR_INVALID_ARG, "D_focal and z_near must be positive");
+    if (!(cam->theta_x > 0.0 && cam->theta_x < M_PI) || !(cam->theta_y > 0.0 && cam->theta_y < M_PI))
+        return fail(LF_ERR_INVALID_ARG, "field of view must be in (0, pi)");
+    if (disp->phi_x < 0.0 || disp->phi_y < 0.0) return fail(LF_ERR_INVALID_ARG, "viewing angle must be >= 0");
+    if ((int64_t)cam->Nx * disp->P_s > 32768 || (int64_t)cam->Ny * disp->P_s > 32768)
+        return fail(LF_ERR_INVALID_ARG, "plane resolution too large");
+
+    const double Df = disp->D_focal;
+    r->tth_x = std::tan(0.5 * cam->theta_x);
+    r->tth_y = std::tan(0.5 * cam->theta_y);
+    r->tphi_x = std::tan(0.5 * disp->phi_x);
+    r->tphi_y = std::tan(0.5 * disp->phi_y);
+    // Eq. (1), maximum over the axes that have a viewing angle
+    double fwd_x = 0.0, fwd_y = 0.0;
+    if (r->tphi_x > 0.0) fwd_x = Df * r->tphi_x / (r->tphi_x + r->tth_x);
+    if (r->tphi_y > 0.0) fwd_y = Df * r->tphi_y / (r->tphi_y + r->tth_y);
+    r->D_forward0 = fwd_x > fwd_y ? fwd_x : fwd_y;
+    // Eq. (2) with the unshifted forward distance
+    r->tthp_x = Df * r->tth_x / (Df - r->D_forward0);
+    r->tthp_y = Df * r->tth_y / (Df - r->D_forward0);
+    r->theta_px = 2.0 * std::atan(r->tthp_x);
+    r->theta_py = 2.0 * std::atan(r->tthp_y);
+    // near-field shift
+    r->D_forward = r->D_forward0 - disp->D_shift;
+    if (!(r->D_forward < Df)) return fail(LF_ERR_INVALID_ARG, "D_shift leaves D_forward >= D_focal");
+    r->W = cam->Nx * disp->P_s;
+    r->H = cam->Ny * disp->P_s;
+    r->fx = (double)r->W / (2.0 * r->tthp_x);
+    r->fy = (double)r->H / (2.0 * r->tthp_y);
+    r->cx = 0.5 * (double)(r->W - 1);
+    r->cy = 0.5 * (double)(r->H - 1);
+    // Eq. (gs_prefilter_fix) with the shifted forward distance
+    const double ratio = Df * r->tth_x / ((Df - r->D_forward) * r->tthp_x) * (double)disp->P_s;
+    r->f_prime = disp->f_aa * ratio * ratio;
+    return LF_OK;
+}
+
+size_t lf_build_mpi_workspace_size(const lf_ref_camera* ref, int64_t n, int32_t N, int64_t dup_capacity)
+{
+    if (!ref || n < 0 || N < 1) return 0;
+    if (dup_capacity <= 0) dup_capacity = default_cap(n);
+    return build_ws_layout(n, N, ref->W, ref->H, dup_capacity, nullptr, nullptr);
+}
+
+lf_status lf_build_mpi_gaussians(const lf_gaussians* g, const lf_ref_camera* ref, int32_t N, int32_t binning,
+                                 void* ws, size_t ws_bytes, lf_planes* out, cudaStream_t stream)
+{
+    if (!g) return fail(LF_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n > 0 && (!g->means || !g->scales || !g->quats || !g->opacity || !g->rgb))
+        return fail(LF_ERR_INVALID_ARG, "a Gaussian attribute pointer is NULL");
+    const lf_gaussians gc = *g;
+    auto project = [&](const ProjParams& pp, const BuildWs& w, cudaStream_t s) {
+        launch_project_gaussians(gc, pp, w, out->rect, out->chunk, s);
+    };
+    return build_common(g->n, ref, N, binning, ws, ws_bytes, out, stream, 0, project, &gc);
+}
+
+lf_status lf_build_mpi_voxels(const lf_voxels* v, const lf_ref_camera* ref, int32_t N, int32_t binning, void* ws,
+                              size_t ws_bytes, lf_planes* out, cudaStream_t stream)
+{
+    if (!v) return fail(LF_ERR_INVALID_ARG, "voxels is NULL");
+    if (v->n > 0 && (!v->ijk || !v->level || !v->density8 || !v->rgb))
+        return fail(LF_ERR_INVALID_ARG, "a voxel attribute pointer is NULL");
+    if (!(v->base_size > 0.0)) return fail(LF_ERR_INVALID_ARG, "voxel base_size must be positive");
+    const lf_voxels vc = *v;
+    auto project = [&](const ProjParams& pp0, const BuildWs& w, cudaStream_t s) {
+        ProjParams pp = pp0;
+        for (int i = 0; i < 3; ++i) pp.origin[i] = vc.origin[i];
+        pp.base_size = vc.base_size;
+        launch_project_voxels(vc, pp, w, out->rect, out->chunk, s);
+    };
+    return build_common(v->n, ref, N, binning, ws, ws_bytes, out, stream, 1, project, &vc);
+}
+
+lf_status lf_mpi_status(const void* ws, int64_t* needed, int64_t* culled_in)
+{
+    if (!ws) return fail(LF_ERR_INVALID_ARG, "workspace is NULL");
+    cudaStream_t s = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        auto it = g_ws_stream.find(ws);
+        if (it == g_ws_stream.end()) return fail(LF_ERR_INVALID_ARG, "no build was run on this workspace");
+        s = it->second;
+    }
+    WsHeader h;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return check_launch("stream synchronise");
+    if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return check_launch("header read");
+    if (needed) *needed = (int64_t)h.total_dups;
+    if (culled_in) *culled_in = (int64_t)h.M;
+    if (h.overflow)
+        return fail(LF_ERR_OVERFLOW, "tile list needs " + std::to_string(h.total_dups) + " pairs, capacity " +
+                                         std::to_string(h.dup_capacity));
+    return LF_OK;
+}
+
+lf_status lf_mpi_tile_lists(const void* ws, int32_t* order, int64_t n, int32_t* tile_prims, int64_t cap,
+                            int32_t* seg)
+{
+    int64_t needed = 0, M = 0;
+    lf_status st = lf_mpi_status(ws, &needed, &M);
+    if (st != LF_OK) return st;
+    WsHeader h;
+    if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return check_launch("header read");
+    BuildWs w;
+    build_ws_layout(h.n, h.N, h.W, h.H, h.dup_capacity, const_cast<void*>(ws), &w);
+    if (order) {
+        if (n < M) return fail(LF_ERR_INVALID_ARG, "order buffer too small");
+        if (M > 0 && cudaMemcpy(order, w.valA, sizeof(uint32_t) * (size_t)M, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return check_launch("order read");
+    }
+    if (tile_prims) {
+        if (cap < needed) return fail(LF_ERR_INVALID_ARG, "tile list buffer too small");
+        if (needed > 0 &&
+            cudaMemcpy(tile_prims, tile_sort_passes((long long)h.tiles_x * h.tiles_y) % 2 ? w.dvalB : w.dvalA,
+                       sizeof(uint32_t) * (size_t)needed, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return check_launch("tile list read");
+    }
+    if (seg) {
+        const size_t ns = (size_t)h.tiles_x * h.tiles_y * h.N;
+        if (cudaMemcpy(seg, w.seg, sizeof(int2) * ns, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return check_launch("segment read");
+    }
+    return LF_OK;
+}
+
+size_t lf_composite_workspace_size(int32_t N, const lf_view_set* views)
+{
+    if (!views || N < 1 || views->Vx < 1 || views->Vy < 1) return 0;
+    return comp_ws_layout(N, views->Vx, views->Vy, nullptr, nullptr);
+}
+
+lf_status lf_composite(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views, float* out,
+                       void* ws, size_t ws_bytes, cudaStream_t stream)
+{
+    lf_status st = check_ref(ref);
+    if (st != LF_OK) return st;
+    if (!planes || !views || !out) return fail(LF_ERR_INVALID_ARG, "NULL argument");
+    if (planes->N < 1 || planes->W != ref->W || planes->H != ref->H)
+        return fail(LF_ERR_INVALID_ARG, "plane array shape does not match the reference camera");
+    if (planes->dtype < LF_F32 || planes->dtype > LF_BF16) return fail(LF_ERR_INVALID_ARG, "unknown plane dtype");
+    if (!planes->rgba || !planes->d || !planes->count) return fail(LF_ERR_INVALID_ARG, "plane pointer is NULL");
+    if (views->Vx < 1 || views->Vy < 1 || views->Vx > 65535 || views->Vy > 65535)
+        return fail(LF_ERR_INVALID_ARG, "view counts must be in 1..65535");
+    if (!ws) return fail(LF_ERR_WORKSPACE, "workspace is NULL");
+    if (((uintptr_t)ws) % 256) return fail(LF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+    CompWs cw;
+    if (comp_ws_layout(planes->N, views->Vx, views->Vy, ws, &cw) > ws_bytes)
+        return fail(LF_ERR_WORKSPACE, "composite workspace too small");
+    CompParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.N = planes->N;
+    p.W = ref->W;
+    p.H = ref->H;
+    p.Nx = ref->base.Nx;
+    p.Ny = ref->base.Ny;
+    p.Vx = views->Vx;
+    p.Vy = views->Vy;
+    p.P_s = ref->disp.P_s;
+    p.bilinear = views->bilinear ? 1 : 0;
+    p.dtype = planes->dtype;
+    for (int c = 0; c < 3; ++c) p.bg[c] = views->bg[c];
+    p.D_focal = ref->disp.D_focal;
+    p.D_forward = ref->D_forward;
+    p.tth_x = ref->tth_x;
+    p.tth_y = ref->tth_y;
+    p.tthp_x = ref->tthp_x;
+    p.tthp_y = ref->tthp_y;
+    p.tphi_x = ref->tphi_x;
+    p.tphi_y = ref->tphi_y;
+    trace_begin("comp_coeffs", stream);
+    launch_comp_coeffs(p, planes->d, planes->count, cw, stream);
+    trace_end(stream);
+    if ((st = check_launch("composite coefficients")) != LF_OK) return st;
+    trace_begin("composite", stream);
+    launch_composite(p, planes->rgba, planes->count, cw, out, stream);
+    trace_end(stream);
+    return check_launch("composite");
+}
+
+}  // extern "C"

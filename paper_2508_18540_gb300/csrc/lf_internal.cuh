@@ -1,0 +1,156 @@
+// lf_internal.cuh -- shared declarations of the liblf implementation units.
+//
+// Not part of the public ABI (include/lf.h is). Holds the workspace layout,
+// the per-launch parameter blocks derived on the host, error plumbing and
+// the launchers each translation unit exports to lf_api.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <string>
+
+#include "lf.h"
+
+namespace lf {
+
+constexpr int kTile = 16;                 // splat tile edge (pixels)
+constexpr int kTilePix = kTile * kTile;   // threads per rasterisation CTA
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;            // keys per thread per radix block
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr uint64_t kInvalidKey = ~0ull;
+
+// ---- launch counting and stage tracing ------------------------------------
+// Every kernel launch of the library bumps a process-wide counter; when
+// tracing is on, each pipeline stage is bracketed by a CUDA event pair on the
+// stream it runs on (see lf_trace_* in lf.h).
+void note_launches(int k);
+void trace_begin(const char* stage, cudaStream_t s);
+void trace_end(cudaStream_t s);
+
+// ---- error plumbing ------------------------------------------------------
+void set_error(const std::string& msg);
+lf_status fail(lf_status st, const std::string& msg);
+lf_status check_launch(const char* what);
+
+// ---- device-side state kept at the front of a build workspace -----------
+struct WsHeader {
+    unsigned long long kmin;      // smallest / largest valid depth key
+    unsigned long long kmax;
+    unsigned long long M;         // culled-in primitives
+    unsigned long long total_dups;
+    unsigned long long tile_n;    // pairs to sort (0 after an overflow)
+    int overflow;                 // 1 if total_dups > dup_capacity
+    int kind;                     // 0 gaussians, 1 voxels
+    long long n;
+    long long dup_capacity;
+    int N, W, H, tiles_x, tiles_y;
+    int binning;
+};
+
+// Carved build workspace (all device pointers).
+struct BuildWs {
+    WsHeader* hdr;
+    unsigned long long* keyA;     // [n] depth keys
+    unsigned long long* keyB;
+    uint32_t* valA;               // [n] primitive ids
+    uint32_t* valB;
+    float2* mean2d;               // [n]
+    float4* conic_o;              // [n] (a, b, c, opacity) / voxel (lo_rel xyz, side)
+    uint32_t* hist;               // [kRadix * nb_max] radix histograms
+    uint32_t* bsum;               // [nb_max + 1] block sums / offsets
+    int32_t* chunk_start;         // [N + 1]
+    uint32_t* dkeyA;              // [cap] tile ids
+    uint32_t* dkeyB;
+    uint32_t* dvalA;              // [cap] primitive ids
+    uint32_t* dvalB;
+    int2* seg;                    // [tiles * N] (start, end)
+    size_t bytes;
+    long long nb_max;
+};
+
+size_t build_ws_layout(int64_t n, int32_t N, int32_t W, int32_t H, int64_t cap, void* base, BuildWs* out);
+
+// ---- per-launch parameters computed on the host -------------------------
+struct ProjParams {
+    double R[9];
+    double t[3];
+    double D_forward;
+    double z_near;
+    double rho;                    // |R20| + |R21| + |R22|
+    double origin[3];              // voxels
+    double base_size;              // voxels
+    double cam_o[3];               // reference centre in world coordinates (FP64)
+    float Rf[9];
+    float t0f, t1f, t2rf;          // t2rf = (float)(t2 - D_forward)
+    float fxf, fyf, cxf, cyf, fpf;
+    float wmax, hmax;
+    int W, H;
+    long long n;
+};
+
+struct RasterParams {
+    int W, H, N, tiles_x, tiles_y, dtype;
+    // voxels: world-frame reference rays
+    float Rt[9];                    // R^T row-major (camera -> world)
+    float fx, fy, cx, cy;
+};
+
+struct BinParams {
+    int N;
+    int binning;
+    double D_forward;
+};
+
+// ---- launchers ----------------------------------------------------------
+void launch_init_header(const WsHeader& h, WsHeader* d, cudaStream_t s);
+void launch_project_gaussians(const lf_gaussians& g, const ProjParams& p, const BuildWs& ws, int32_t* rect,
+                              int32_t* chunk, cudaStream_t s);
+void launch_project_voxels(const lf_voxels& v, const ProjParams& p, const BuildWs& ws, int32_t* rect,
+                           int32_t* chunk, cudaStream_t s);
+
+// LSD radix sort of (key, value) pairs, stable. 64-bit depth keys: the first
+// pass drops kInvalidKey entries (culled primitives); the count after it is
+// hdr->M. Result ends in (keyA, valA).
+void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s);
+// Stable sort of (tile id, primitive id) pairs by tile id (tile_bits bits);
+// count in hdr->total_dups. Result ends in (dkeyA, dvalA).
+void sort_tile_keys(const BuildWs& ws, long long cap, int tile_bits, cudaStream_t s, uint32_t** keys_out,
+                    uint32_t** vals_out);
+
+void launch_bin(const BuildWs& ws, const BinParams& p, long long n, int32_t* chunk, double* d, int32_t* count,
+                cudaStream_t s);
+void launch_duplicate(const BuildWs& ws, long long n, const int32_t* rect, int tiles_x, cudaStream_t s);
+void launch_ranges(const BuildWs& ws, long long cap, const uint32_t* tkeys, const uint32_t* tvals,
+                   const int32_t* chunk, int N, cudaStream_t s);
+
+void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uint32_t* tvals, const float* rgb,
+                             const int32_t* rect, void* planes, cudaStream_t s);
+void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32_t* tvals, const lf_voxels& v,
+                          const int32_t* rect, void* planes, cudaStream_t s);
+
+// ---- composite ----------------------------------------------------------
+struct CompWs {
+    float* cx;      // [Vx][N][3] (gm, hn, hb) along x
+    float* cy;      // [Vy][N][3] along y
+    size_t bytes;
+};
+size_t comp_ws_layout(int32_t N, int32_t Vx, int32_t Vy, void* base, CompWs* out);
+
+struct CompParams {
+    int N, W, H, Nx, Ny, Vx, Vy, P_s, bilinear, dtype;
+    float bg[3];
+    // FP64 set-up for the per-(view, plane) coefficients
+    double D_focal, D_forward, tth_x, tth_y, tthp_x, tthp_y, tphi_x, tphi_y;
+};
+
+void launch_comp_coeffs(const CompParams& p, const double* d, const int32_t* count, const CompWs& ws,
+                        cudaStream_t s);
+void launch_composite(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
+                      float* out, cudaStream_t s);
+
+}  // namespace lf

@@ -1,0 +1,229 @@
+// lf_raster.cu -- 3D-tiled rasterisation of every chunk into its sweeping
+// plane (Algorithm 1 lines 4-5, "Parallel for all k: Rasterize(H, P'_k)").
+//
+// One CTA per (16x16 tile, chunk). The CTA's (tile, chunk) list is already in
+// (depth, index) order; it is staged through shared memory in batches of 256
+// primitives and every thread blends its pixel front to back:
+//   Gaussians (Sec. 4.4, 3DGS model): alpha = min(0.99, o exp(-q/2)),
+//     q = d^T Sigma_2^{-1} d inside the primitive's footprint rectangle;
+//   voxels (Sec. 4.5, SVR model): alpha = 1 - exp(-integral of the trilinear
+//     density along the pixel's reference ray inside the cube), by Simpson's
+//     rule, exact for the cubic the trilinear density becomes along a line;
+//   C += T alpha rgb, T *= 1 - alpha. No early stop, no small-alpha skip.
+// The texel (C, 1 - T) is stored as FP32, FP16 or BF16 (FP32 accumulation).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lf_internal.cuh"
+
+namespace lf {
+
+namespace {
+
+template <int DT>
+__device__ __forceinline__ void store_texel(void* planes, size_t idx, float r, float g, float b, float a)
+{
+    if (DT == LF_F32) {
+        reinterpret_cast<float4*>(planes)[idx] = make_float4(r, g, b, a);
+    } else if (DT == LF_F16) {
+        const __half2 lo = __floats2half2_rn(r, g), hi = __floats2half2_rn(b, a);
+        uint2 u;
+        u.x = *reinterpret_cast<const uint32_t*>(&lo);
+        u.y = *reinterpret_cast<const uint32_t*>(&hi);
+        reinterpret_cast<uint2*>(planes)[idx] = u;
+    } else {
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(r, g), hi = __floats2bfloat162_rn(b, a);
+        uint2 u;
+        u.x = *reinterpret_cast<const uint32_t*>(&lo);
+        u.y = *reinterpret_cast<const uint32_t*>(&hi);
+        reinterpret_cast<uint2*>(planes)[idx] = u;
+    }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kTilePix) k_raster_gauss(BuildWs w, RasterParams p, const uint32_t* __restrict__ tvals,
+                                                           const float* __restrict__ rgb, const int4* __restrict__ rect,
+                                                           void* planes)
+{
+    __shared__ float2 s_mean[kTilePix];
+    __shared__ float4 s_con[kTilePix];
+    __shared__ float4 s_rgb[kTilePix];
+    __shared__ int4 s_rect[kTilePix];
+    const int t = blockIdx.x, k = blockIdx.y;
+    const int tx = t % p.tiles_x, ty = t / p.tiles_x;
+    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
+    const int py = ty * kTile + (threadIdx.x / kTile);
+    const int2 sg = w.seg[(size_t)t * p.N + k];
+    const float fpx = (float)px, fpy = (float)py;
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+    for (int base = sg.x; base < sg.y; base += kTilePix) {
+        const int i = base + threadIdx.x;
+        if (i < sg.y) {
+            const uint32_t g = tvals[i];
+            s_mean[threadIdx.x] = w.mean2d[g];
+            s_con[threadIdx.x] = w.conic_o[g];
+            s_rgb[threadIdx.x] = make_float4(rgb[3 * (size_t)g], rgb[3 * (size_t)g + 1], rgb[3 * (size_t)g + 2], 0.f);
+            s_rect[threadIdx.x] = rect[g];
+        }
+        __syncthreads();
+        const int cnt = min(kTilePix, sg.y - base);
+        for (int j = 0; j < cnt; ++j) {
+            const int4 rc = s_rect[j];
+            if (px >= rc.x && px <= rc.z && py >= rc.y && py <= rc.w) {
+                const float2 m = s_mean[j];
+                const float4 c = s_con[j];
+                const float dx = fpx - m.x, dy = fpy - m.y;
+                const float q = fmaf(c.x * dx, dx, fmaf(2.0f * c.y * dx, dy, c.z * dy * dy));
+                const float al = fminf(0.99f, c.w * __expf(-0.5f * q));
+                const float4 col = s_rgb[j];
+                const float ta = T * al;
+                C0 = fmaf(ta, col.x, C0);
+                C1 = fmaf(ta, col.y, C1);
+                C2 = fmaf(ta, col.z, C2);
+                T = T * (1.0f - al);
+            }
+        }
+        __syncthreads();
+    }
+    if (px < p.W && py < p.H) store_texel<DT>(planes, ((size_t)k * p.H + py) * p.W + px, C0, C1, C2, 1.0f - T);
+}
+
+__device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+__device__ __forceinline__ float trilinear(const float* rho, float fx, float fy, float fz)
+{
+    const float c00 = lerpf(rho[0], rho[1], fx), c10 = lerpf(rho[2], rho[3], fx);
+    const float c01 = lerpf(rho[4], rho[5], fx), c11 = lerpf(rho[6], rho[7], fx);
+    return lerpf(lerpf(c00, c10, fy), lerpf(c01, c11, fy), fz);
+}
+
+__device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.0f), 1.0f); }
+
+template <int DT>
+__global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterParams p, const uint32_t* __restrict__ tvals,
+                                                           const float* __restrict__ dens8, const float* __restrict__ rgb,
+                                                           const int4* __restrict__ rect, void* planes)
+{
+    __shared__ float4 s_box[kTilePix];
+    __shared__ float s_den[kTilePix * 8];
+    __shared__ float4 s_rgb[kTilePix];
+    __shared__ int4 s_rect[kTilePix];
+    const int t = blockIdx.x, k = blockIdx.y;
+    const int tx = t % p.tiles_x, ty = t / p.tiles_x;
+    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
+    const int py = ty * kTile + (threadIdx.x / kTile);
+    const int2 sg = w.seg[(size_t)t * p.N + k];
+
+    // world-frame direction of the reference ray through this pixel centre
+    const float dcx = ((float)px - p.cx) / p.fx, dcy = ((float)py - p.cy) / p.fy;
+    float d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = fmaf(p.Rt[3 * a], dcx, fmaf(p.Rt[3 * a + 1], dcy, p.Rt[3 * a + 2]));
+    const float nrm = rsqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+    float inv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        d[a] *= nrm;
+        inv[a] = 1.0f / d[a];
+    }
+
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+    for (int base = sg.x; base < sg.y; base += kTilePix) {
+        const int i = base + threadIdx.x;
+        if (i < sg.y) {
+            const uint32_t g = tvals[i];
+            s_box[threadIdx.x] = w.conic_o[g];
+            const float4* d4 = reinterpret_cast<const float4*>(dens8 + 8 * (size_t)g);
+            const float4 da = d4[0], db = d4[1];
+            float* sd = s_den + 8 * threadIdx.x;
+            sd[0] = da.x; sd[1] = da.y; sd[2] = da.z; sd[3] = da.w;
+            sd[4] = db.x; sd[5] = db.y; sd[6] = db.z; sd[7] = db.w;
+            s_rgb[threadIdx.x] = make_float4(rgb[3 * (size_t)g], rgb[3 * (size_t)g + 1], rgb[3 * (size_t)g + 2], 0.f);
+            s_rect[threadIdx.x] = rect[g];
+        }
+        __syncthreads();
+        const int cnt = min(kTilePix, sg.y - base);
+        for (int j = 0; j < cnt; ++j) {
+            const int4 rc = s_rect[j];
+            if (!(px >= rc.x && px <= rc.z && py >= rc.y && py <= rc.w)) continue;
+            const float4 b = s_box[j];  // cube low corner relative to the ray origin, side
+            const float lo[3] = {b.x, b.y, b.z};
+            float t0 = -__int_as_float(0x7f800000), t1 = __int_as_float(0x7f800000);
+            bool miss = false;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float hi = lo[a] + b.w;
+                if (d[a] != 0.0f) {
+                    float ta = lo[a] * inv[a], tb = hi * inv[a];
+                    if (ta > tb) {
+                        const float tmp = ta;
+                        ta = tb;
+                        tb = tmp;
+                    }
+                    t0 = fmaxf(t0, ta);
+                    t1 = fminf(t1, tb);
+                } else if (0.0f < lo[a] || 0.0f > hi) {
+                    miss = true;
+                }
+            }
+            t0 = fmaxf(t0, 0.0f);
+            if (miss || !(t1 > t0)) continue;
+            const float tm = 0.5f * (t0 + t1);
+            const float is = 1.0f / b.w;
+            const float* rho = s_den + 8 * j;
+            const float s0 = trilinear(rho, clamp01((t0 * d[0] - lo[0]) * is), clamp01((t0 * d[1] - lo[1]) * is),
+                                       clamp01((t0 * d[2] - lo[2]) * is));
+            const float sm = trilinear(rho, clamp01((tm * d[0] - lo[0]) * is), clamp01((tm * d[1] - lo[1]) * is),
+                                       clamp01((tm * d[2] - lo[2]) * is));
+            const float s1 = trilinear(rho, clamp01((t1 * d[0] - lo[0]) * is), clamp01((t1 * d[1] - lo[1]) * is),
+                                       clamp01((t1 * d[2] - lo[2]) * is));
+            const float integral = (t1 - t0) * (1.0f / 6.0f) * (s0 + 4.0f * sm + s1);
+            const float al = 1.0f - __expf(-integral);
+            const float4 col = s_rgb[j];
+            const float ta = T * al;
+            C0 = fmaf(ta, col.x, C0);
+            C1 = fmaf(ta, col.y, C1);
+            C2 = fmaf(ta, col.z, C2);
+            T = T * (1.0f - al);
+        }
+        __syncthreads();
+    }
+    if (px < p.W && py < p.H) store_texel<DT>(planes, ((size_t)k * p.H + py) * p.W + px, C0, C1, C2, 1.0f - T);
+}
+
+}  // namespace
+
+void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uint32_t* tvals, const float* rgb,
+                             const int32_t* rect, void* planes, cudaStream_t s)
+{
+    const dim3 grid((unsigned)(p.tiles_x * p.tiles_y), (unsigned)p.N);
+    const int4* r4 = reinterpret_cast<const int4*>(rect);
+    switch (p.dtype) {
+    case LF_F32: k_raster_gauss<LF_F32><<<grid, kTilePix, 0, s>>>(ws, p, tvals, rgb, r4, planes); note_launches(1); break;
+    case LF_F16: k_raster_gauss<LF_F16><<<grid, kTilePix, 0, s>>>(ws, p, tvals, rgb, r4, planes); note_launches(1); break;
+    default: k_raster_gauss<LF_BF16><<<grid, kTilePix, 0, s>>>(ws, p, tvals, rgb, r4, planes); note_launches(1); break;
+    }
+}
+
+void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32_t* tvals, const lf_voxels& v,
+                          const int32_t* rect, void* planes, cudaStream_t s)
+{
+    const dim3 grid((unsigned)(p.tiles_x * p.tiles_y), (unsigned)p.N);
+    const int4* r4 = reinterpret_cast<const int4*>(rect);
+    switch (p.dtype) {
+    case LF_F32:
+        k_raster_voxel<LF_F32><<<grid, kTilePix, 0, s>>>(ws, p, tvals, v.density8, v.rgb, r4, planes);
+        note_launches(1);
+        break;
+    case LF_F16:
+        k_raster_voxel<LF_F16><<<grid, kTilePix, 0, s>>>(ws, p, tvals, v.density8, v.rgb, r4, planes);
+        note_launches(1);
+        break;
+    default:
+        k_raster_voxel<LF_BF16><<<grid, kTilePix, 0, s>>>(ws, p, tvals, v.density8, v.rgb, r4, planes);
+        note_launches(1);
+        break;
+    }
+}
+
+}  // namespace lf

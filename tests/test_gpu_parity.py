@@ -1,0 +1,151 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Integer work is compared bit for bit (culling, footprint rectangles, depth
+order, chunk membership, plane distances, chunk counts, tile lists); colour
+within the tolerances stated below:
+  FP32 planes: max-abs <= 1e-4 per channel (planes and views);
+  FP16 planes: max-abs <= 4e-3 and PSNR >= 60 dB against the FP64 oracle;
+  BF16 planes: max-abs <= 3e-2 and PSNR >= 45 dB.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2508_18540_gb300 import synth as S
+from tests import gpu_util as G
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": (1e-4, 80.0), "f16": (4e-3, 60.0), "bf16": (3e-2, 45.0)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2508_18540_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def _compare(gpu, o, W, H, N, dtype, check_lists=True):
+    assert gpu["status"] == 0
+    valid = o["valid"].astype(bool)
+    n = valid.shape[0]
+    # culling and footprints: bit-exact
+    assert np.array_equal(gpu["rect"], o["rect"])
+    # depth order and chunk membership: bit-exact
+    assert gpu["M"] == o["M"]
+    assert np.array_equal(gpu["order"], o["order"])
+    assert np.array_equal(gpu["chunk"], o["chunk"])
+    assert np.array_equal(gpu["count"], o["count"])
+    assert np.array_equal(gpu["d"], o["d"])          # FP64 bits
+    if check_lists:
+        G.check_tile_lists(gpu, o, W, H, N)
+    tol, min_psnr = TOL[dtype]
+    err_p = np.abs(gpu["planes"] - o["planes"]).max()
+    err_v = np.abs(gpu["views"] - o["views"]).max()
+    assert err_p <= tol, err_p
+    assert err_v <= tol, err_v
+    for v in range(gpu["views"].shape[0]):
+        assert G.psnr(gpu["views"][v], o["views"][v]) >= min_psnr
+    return err_p, err_v
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_tiny_workload(orc, dtype):
+    w = S.workload_tiny()
+    o = orc.render(w)
+    gpu = G.run_gpu(w.scene, w.camera, w.display, w.views, w.N, w.binning, dtype)
+    _compare(gpu, o, o["ref"].W, o["ref"].H, w.N, dtype, check_lists=(dtype == "f32"))
+
+
+@pytest.mark.parametrize("bilinear", [False, True])
+@pytest.mark.parametrize("binning", ["quantile", "disparity"])
+def test_ragged_rotated_scaled(orc, bilinear, binning):
+    # 100x70 views, P_s = 2 (200x140 planes: ragged 16x16 tiles), rotated and
+    # translated camera, D_shift, 1037 anisotropic Gaussians, N = 5, 7 views
+    cam = G.small_rotated_camera()
+    disp = S.display_for(3.0, 0.12, P_s=2, D_shift=0.03)
+    sc = S.blob_gaussians(1037, 21, n_blobs=12, z=(1.5, 6.0))
+    views = S.ViewSet(7, 1, bilinear, (0.1, 0.2, 0.3))
+    o = orc.render(scene=sc, camera=cam, display=disp, views=views, N=5, binning=binning)
+    gpu = G.run_gpu(sc, cam, disp, views, 5, binning, "f32")
+    _compare(gpu, o, o["ref"].W, o["ref"].H, 5, "f32")
+
+
+def test_two_view_rows(orc):
+    # vertical parallax too (Vy = 3), non-square views
+    cam = S.Camera(np.eye(3), np.zeros(3), np.radians(50.0), np.radians(40.0), 64, 48)
+    disp = S.Display(D_focal=3.0, phi_x=0.1, phi_y=0.06)
+    sc = S.uniform_gaussians(3000, 5)
+    views = S.ViewSet(5, 3, False)
+    o = orc.render(scene=sc, camera=cam, display=disp, views=views, N=8, binning="quantile")
+    gpu = G.run_gpu(sc, cam, disp, views, 8, "quantile")
+    _compare(gpu, o, o["ref"].W, o["ref"].H, 8, "f32")
+
+
+@pytest.mark.parametrize("N", [1, 3, 64])
+def test_chunk_counts_and_few_primitives(orc, N):
+    # N = 1 (plain alpha blending), and M < N (empty chunks, zero planes)
+    sc = S.uniform_gaussians(40, 9)
+    w = S.workload_tiny()
+    o = orc.render(scene=sc, camera=w.camera, display=w.display, views=w.views, N=N, binning="quantile")
+    gpu = G.run_gpu(sc, w.camera, w.display, w.views, N, "quantile")
+    _compare(gpu, o, o["ref"].W, o["ref"].H, N, "f32")
+
+
+def test_everything_culled(orc):
+    w = S.workload_tiny()
+    sc = S.uniform_gaussians(500, 3)
+    sc.means[:, 2] = -3.0
+    views = S.ViewSet(3, 1, False, (0.5, 0.25, 0.125))
+    o = orc.render(scene=sc, camera=w.camera, display=w.display, views=views, N=4, binning="quantile")
+    gpu = G.run_gpu(sc, w.camera, w.display, views, 4, "quantile")
+    assert gpu["M"] == 0
+    _compare(gpu, o, o["ref"].W, o["ref"].H, 4, "f32")
+    assert np.all(gpu["planes"] == 0.0)
+
+
+def test_empty_scene(orc):
+    w = S.workload_tiny()
+    sc = S.uniform_gaussians(0, 3)
+    gpu = G.run_gpu(sc, w.camera, w.display, w.views, 4, "quantile")
+    assert gpu["status"] == 0 and gpu["M"] == 0
+    assert np.all(gpu["planes"] == 0.0) and np.all(gpu["views"][..., 3] == 0.0)
+
+
+def test_tile_list_overflow_is_reported(orc):
+    from paper_2508_18540_gb300 import _lib
+    w = S.workload_tiny()
+    gpu = G.run_gpu(w.scene, w.camera, w.display, w.views, w.N, w.binning, dup_capacity=1000)
+    assert gpu["status"] == _lib.LF_ERR_OVERFLOW
+    assert gpu["needed"] > 1000
+
+
+def test_deterministic(orc):
+    w = S.workload_tiny(seed=4)
+    a = G.run_gpu(w.scene, w.camera, w.display, w.views, w.N, w.binning)
+    b = G.run_gpu(w.scene, w.camera, w.display, w.views, w.N, w.binning)
+    assert np.array_equal(a["planes"], b["planes"]) and np.array_equal(a["views"], b["views"])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_voxels(orc, dtype):
+    # small V2LF scene: 3-level sparse grid at 64^3 base, 96x96 views
+    sc = S.sparse_voxels(20_000, 3, base_res=64)
+    cam = S.identity_camera(96, t=(0.0, 0.0, 6.0))
+    disp = S.display_for(S.harmonic_focal(4.0, 8.0), 0.15)
+    views = S.ViewSet(9)
+    o = orc.render(scene=sc, camera=cam, display=disp, views=views, N=16, binning="quantile")
+    gpu = G.run_gpu(sc, cam, disp, views, 16, "quantile", dtype)
+    _compare(gpu, o, o["ref"].W, o["ref"].H, 16, dtype, check_lists=(dtype == "f32"))
+
+
+def test_voxels_rotated(orc):
+    sc = S.sparse_voxels(5_000, 4, base_res=32)
+    cam = G.small_rotated_camera(64, 48)
+    cam.t = np.array([0.1, -0.05, 6.0])
+    disp = S.display_for(S.harmonic_focal(4.0, 8.0), 0.15, P_s=2)
+    views = S.ViewSet(5, 1, True)
+    o = orc.render(scene=sc, camera=cam, display=disp, views=views, N=6, binning="disparity")
+    gpu = G.run_gpu(sc, cam, disp, views, 6, "disparity")
+    _compare(gpu, o, o["ref"].W, o["ref"].H, 6, "f32")
