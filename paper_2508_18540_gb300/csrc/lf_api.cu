@@ -103,6 +103,7 @@ size_t build_ws_layout(int64_t n, int32_t N, int32_t W, int32_t H, int64_t cap, 
     w.conic_o = carve<float4>(base, off, nn);
     w.hist = carve<uint32_t>(base, off, (size_t)kRadix * nb + 1);
     w.bsum = carve<uint32_t>(base, off, (size_t)nb + 1);
+    w.dtot = carve<uint32_t>(base, off, (size_t)kRadix);
     w.chunk_start = carve<int32_t>(base, off, (size_t)N + 1);
     w.dkeyA = carve<uint32_t>(base, off, cc);
     w.dkeyB = carve<uint32_t>(base, off, cc);
@@ -122,6 +123,7 @@ size_t comp_ws_layout(int32_t N, int32_t Vx, int32_t Vy, void* basev, CompWs* o)
     CompWs w;
     w.cx = carve<float>(base, off, (size_t)Vx * N * 3);
     w.cy = carve<float>(base, off, (size_t)Vy * N * 3);
+    w.err = carve<int>(base, off, 1);
     w.bytes = align_up(off, 256);
     if (o) *o = w;
     return w.bytes;
@@ -545,6 +547,7 @@ lf_status lf_composite(const lf_planes* planes, const lf_ref_camera* ref, const 
     p.tthp_y = ref->tthp_y;
     p.tphi_x = ref->tphi_x;
     p.tphi_y = ref->tphi_y;
+    if (cudaMemsetAsync(cw.err, 0, sizeof(int), stream) != cudaSuccess) return check_launch("composite reset");
     trace_begin("comp_coeffs", stream);
     launch_comp_coeffs(p, planes->d, planes->count, cw, stream);
     trace_end(stream);

@@ -163,10 +163,360 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
         make_float4(fmaf(T, p.bg[0], Q0), fmaf(T, p.bg[1], Q1), fmaf(T, p.bg[2], Q2), 1.0f - T);
 }
 
+// ---------------------------------------------------------------------------
+// Staged composite. All views of one view row i sample plane k on the same
+// plane rows (their vertical map depends on (i, k) only), and neighbouring
+// views read horizontally shifted copies of those rows. A CTA therefore owns
+// BY output rows x TX output columns for a group of VG views of one view row;
+// for every non-empty plane it copies the BY plane rows it needs (2 BY for
+// bilinear) into shared memory with bulk asynchronous copies
+// (cp.async.bulk + mbarrier transaction counts, 3-stage ring, one producer
+// thread), and every thread composites its pixel for the VG views from
+// shared memory. Every staged row has zero texels on both sides, so an
+// out-of-plane index reads a transparent zero without a branch.
+// ---------------------------------------------------------------------------
+
+constexpr int kStages = 3;
+constexpr int kStagedThreads = 512;
+constexpr long long kSpinLimit = 1ll << 26;   // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <int DT>
+struct Texel;
+template <>
+struct Texel<LF_F32> {
+    static constexpr int kBytes = 16;
+    static __device__ __forceinline__ float4 load(const char* row, uint32_t i)
+    {
+        return *reinterpret_cast<const float4*>(row + (size_t)i * 16);
+    }
+};
+template <>
+struct Texel<LF_F16> {
+    static constexpr int kBytes = 8;
+    static __device__ __forceinline__ float4 load(const char* row, uint32_t i)
+    {
+        const uint2 u = *reinterpret_cast<const uint2*>(row + (size_t)i * 8);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+};
+template <>
+struct Texel<LF_BF16> {
+    static constexpr int kBytes = 8;
+    static __device__ __forceinline__ float4 load(const char* row, uint32_t i)
+    {
+        const uint2 u = *reinterpret_cast<const uint2*>(row + (size_t)i * 8);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+};
+
+struct StagedGeom {
+    int TX, BY, VG, rows_per_y;    // rows_per_y: 1 nearest, 2 bilinear
+    int padl;                      // zero texels left of every staged row (16 bytes)
+    int row_texels;                // padl + W + right pad, rounded to 16 bytes
+    size_t row_bytes, stage_bytes, smem_bytes;
+    int groups_x;                  // view groups per view row
+};
+
+__host__ __device__ inline size_t round16(size_t v) { return (v + 15) / 16 * 16; }
+
+// FP32 decision of the plane row / column as in the unstaged kernel
+__device__ __forceinline__ float decide(float gm, int x, float h)
+{
+    return fminf(fmaxf(floorf(__fmaf_rn(gm, (float)x, h)), -2.0e6f), 2.0e6f);
+}
+
+template <int DT, bool BILINEAR, int VG>
+__global__ void __launch_bounds__(kStagedThreads, 2) k_composite_staged(CompParams p, StagedGeom G,
+                                                                        const char* __restrict__ planes,
+                                                                        const int32_t* __restrict__ count, CompWs w,
+                                                                        float* __restrict__ out, int* __restrict__ err)
+{
+    using TX_ = Texel<DT>;
+    constexpr int TB = TX_::kBytes;
+    extern __shared__ __align__(128) unsigned char smem[];
+    // layout: [stages][rows][row_bytes] | mbarriers | coef | plane list
+    unsigned char* stage_base = smem;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * G.stage_bytes);
+    float* coef = reinterpret_cast<float*>(bars + kStages);          // [N][VG + 3]
+    int* plist = reinterpret_cast<int*>(coef + (size_t)p.N * (VG + 3));
+    __shared__ int s_nplanes;
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const int vgroup = blockIdx.x;                 // fastest: neighbouring CTAs share plane rows in L2
+    const int vi = vgroup / G.groups_x;            // view row
+    const int j0 = (vgroup % G.groups_x) * VG;     // first view column of the group
+    const int Y0 = blockIdx.y * G.BY;
+    const int X0 = blockIdx.z * G.TX;
+    const int tx = tid % G.TX, ty = tid / G.TX;
+    const int x = X0 + tx, y = Y0 + ty;
+    const int CW = VG + 3;
+
+    // coefficients of this CTA's views: [gm_x, gm_y, h_y, h_x[VG]] per plane
+    for (int e = tid; e < p.N * VG; e += kStagedThreads) {
+        const int k = e / VG, jj = e % VG;
+        const int j = min(j0 + jj, p.Vx - 1);
+        const float* cx = w.cx + 3 * ((size_t)j * p.N + k);
+        coef[k * CW + 3 + jj] = BILINEAR ? cx[2] : cx[1];
+        if (jj == 0) {
+            const float* cy = w.cy + 3 * ((size_t)vi * p.N + k);
+            coef[k * CW + 0] = cx[0];
+            coef[k * CW + 1] = cy[0];
+            coef[k * CW + 2] = BILINEAR ? cy[2] : cy[1];
+        }
+    }
+    // list of non-empty planes (warp 0, ballot compaction keeps plane order)
+    if (tid < 32) {
+        int n = 0;
+        for (int b = 0; b < p.N; b += 32) {
+            const int k = b + tid;
+            const bool ne = k < p.N && count[k] != 0;
+            const unsigned m = __ballot_sync(0xffffffffu, ne);
+            if (ne) plist[n + __popc(m & ((1u << tid) - 1u))] = k;
+            n += __popc(m);
+        }
+        if (tid == 0) {
+            s_nplanes = n;
+            s_abort = 0;
+        }
+    }
+    // zero pads of every staged row (never written by the bulk copies)
+    const int nrows = G.BY * G.rows_per_y;
+    for (int e = tid; e < kStages * nrows; e += kStagedThreads) {
+        unsigned char* row = stage_base + (size_t)(e / nrows) * G.stage_bytes + (size_t)(e % nrows) * G.row_bytes;
+        for (int b = 0; b < G.padl * TB; b += 4) *reinterpret_cast<uint32_t*>(row + b) = 0u;
+        for (size_t b = (size_t)(G.padl + p.W) * TB; b < G.row_bytes; b += 4) *reinterpret_cast<uint32_t*>(row + b) = 0u;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        fence_proxy_async();
+    }
+    __syncthreads();
+    const int P = s_nplanes;
+    const size_t plane_bytes = (size_t)p.W * p.H * TB;
+    const uint32_t row_copy = (uint32_t)((size_t)p.W * TB / 16 * 16);   // bulk part (multiple of 16 bytes)
+    const uint32_t row_tail = (uint32_t)((size_t)p.W * TB - row_copy);  // 0 or 8 bytes
+
+    // producer: stage the plane rows of list entry q into stage q % kStages
+    auto produce = [&](int q) {
+        const int k = plist[q];
+        const float* c = coef + (size_t)k * CW;
+        unsigned char* sb = stage_base + (size_t)(q % kStages) * G.stage_bytes;
+        const uint32_t bar = smem_addr(&bars[q % kStages]);
+        uint32_t bytes = 0;
+        int rows[16];
+        int nr = 0;
+        for (int r = 0; r < G.BY; ++r) {
+            const int yy = Y0 + r;
+            const int base = yy < p.Ny ? p.P_s * yy + (int)decide(c[1], yy, c[2]) : -1;
+            for (int t = 0; t < G.rows_per_y; ++t) {
+                const int iy = base + t;
+                const bool ok = yy < p.Ny && iy >= 0 && iy < p.H;
+                rows[nr++] = ok ? iy : -1;
+                if (ok) bytes += row_copy;
+            }
+        }
+        fence_proxy_async();
+        mbar_arrive_expect_tx(bar, bytes);
+        for (int r = 0; r < nr; ++r) {
+            if (rows[r] < 0) continue;
+            const char* src = planes + (size_t)k * plane_bytes + (size_t)rows[r] * p.W * TB;
+            unsigned char* dst = sb + (size_t)r * G.row_bytes + (size_t)G.padl * TB;
+            if (row_copy) bulk_copy_g2s(smem_addr(dst), src, row_copy, bar);
+            if (row_tail) *reinterpret_cast<uint2*>(dst + row_copy) = *reinterpret_cast<const uint2*>(src + row_copy);
+        }
+    };
+
+    if (tid == 0)
+        for (int q = 0; q < min(P, kStages); ++q) produce(q);
+    __syncthreads();
+
+    float acc[VG][4];
+#pragma unroll
+    for (int jj = 0; jj < VG; ++jj) acc[jj][0] = acc[jj][1] = acc[jj][2] = 0.f, acc[jj][3] = 1.f;
+    const bool live = ty < G.BY && x < p.Nx && y < p.Ny;   // threads past BY rows idle
+    const uint32_t maxi = (uint32_t)(G.padl + p.W);     // first right-pad texel
+
+    for (int q = 0; q < P; ++q) {
+        const int s = q % kStages;
+        const uint32_t bar = smem_addr(&bars[s]);
+        const uint32_t parity = (uint32_t)((q / kStages) & 1);
+        bool done = false;
+        for (long long it = 0; it < kSpinLimit && !done; ++it) done = mbar_try_wait(bar, parity);
+        if (__syncthreads_or(!done)) {
+            if (tid == 0) {
+                s_abort = 1;
+                atomicExch(err, 1);
+            }
+            break;
+        }
+        const int k = plist[q];
+        const float* c = coef + (size_t)k * CW;
+        if (live) {
+            const unsigned char* sb = stage_base + (size_t)s * G.stage_bytes;
+            const float gmx = c[0];
+            const float fy = __fmaf_rn(c[1], (float)y, c[2]);
+            if (!BILINEAR) {
+                const int iy = p.P_s * y + (int)decide(c[1], y, c[2]);
+                if (iy >= 0 && iy < p.H) {
+                    const char* row = reinterpret_cast<const char*>(sb + (size_t)ty * G.row_bytes);
+#pragma unroll
+                    for (int jj = 0; jj < VG; ++jj) {
+                        const int ix = p.P_s * x + (int)decide(gmx, x, c[3 + jj]);
+                        const uint32_t i = min((uint32_t)(ix + G.padl), maxi);
+                        const float4 t = TX_::load(row, i);
+                        const float T = acc[jj][3];
+                        acc[jj][0] = fmaf(T, t.x, acc[jj][0]);
+                        acc[jj][1] = fmaf(T, t.y, acc[jj][1]);
+                        acc[jj][2] = fmaf(T, t.z, acc[jj][2]);
+                        acc[jj][3] = T * (1.0f - t.w);
+                    }
+                }
+            } else if (fy >= -1.0e6f && fy <= 1.0e6f) {
+                const float fly = floorf(fy);
+                const float wy = fy - fly;
+                const int y0 = p.P_s * y + (int)fly;
+                const char* r0 = reinterpret_cast<const char*>(sb + (size_t)(2 * ty) * G.row_bytes);
+                const char* r1 = r0 + G.row_bytes;
+                const bool v0 = y0 >= 0 && y0 < p.H, v1 = y0 + 1 >= 0 && y0 + 1 < p.H;
+                const float w0 = v0 ? 1.0f - wy : 0.0f, w1 = v1 ? wy : 0.0f;
+#pragma unroll
+                for (int jj = 0; jj < VG; ++jj) {
+                    const float fx = __fmaf_rn(gmx, (float)x, c[3 + jj]);
+                    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (fx >= -1.0e6f && fx <= 1.0e6f) {
+                        const float flx = floorf(fx);
+                        const float wx = fx - flx;
+                        const int x0 = p.P_s * x + (int)flx;
+                        const uint32_t i0 = min((uint32_t)(x0 + G.padl), maxi);
+                        const uint32_t i1 = min((uint32_t)(x0 + 1 + G.padl), maxi);
+                        const float wa = 1.0f - wx;
+                        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+                        if (v0) {
+                            const float4 ta = TX_::load(r0, i0), tb = TX_::load(r0, i1);
+                            a = make_float4(fmaf(wa, ta.x, wx * tb.x), fmaf(wa, ta.y, wx * tb.y),
+                                            fmaf(wa, ta.z, wx * tb.z), fmaf(wa, ta.w, wx * tb.w));
+                        }
+                        if (v1) {
+                            const float4 ta = TX_::load(r1, i0), tb = TX_::load(r1, i1);
+                            b = make_float4(fmaf(wa, ta.x, wx * tb.x), fmaf(wa, ta.y, wx * tb.y),
+                                            fmaf(wa, ta.z, wx * tb.z), fmaf(wa, ta.w, wx * tb.w));
+                        }
+                        t = make_float4(fmaf(w0, a.x, w1 * b.x), fmaf(w0, a.y, w1 * b.y), fmaf(w0, a.z, w1 * b.z),
+                                        fmaf(w0, a.w, w1 * b.w));
+                    }
+                    const float T = acc[jj][3];
+                    acc[jj][0] = fmaf(T, t.x, acc[jj][0]);
+                    acc[jj][1] = fmaf(T, t.y, acc[jj][1]);
+                    acc[jj][2] = fmaf(T, t.z, acc[jj][2]);
+                    acc[jj][3] = T * (1.0f - t.w);
+                }
+            }
+        }
+        __syncthreads();   // stage s is free again
+        if (tid == 0 && q + kStages < P) produce(q + kStages);
+    }
+    if (s_abort) return;
+    if (live) {
+#pragma unroll
+        for (int jj = 0; jj < VG; ++jj) {
+            const int j = j0 + jj;
+            if (j >= p.Vx) break;
+            const int v = vi * p.Vx + j;
+            const float T = acc[jj][3];
+            reinterpret_cast<float4*>(out)[((size_t)v * p.Ny + y) * p.Nx + x] =
+                make_float4(fmaf(T, p.bg[0], acc[jj][0]), fmaf(T, p.bg[1], acc[jj][1]),
+                            fmaf(T, p.bg[2], acc[jj][2]), 1.0f - T);
+        }
+    }
+}
+
+template <int DT, bool BILINEAR, int VG>
+bool launch_staged_vg(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
+                      cudaStream_t s)
+{
+    constexpr int TB = Texel<DT>::kBytes;
+    StagedGeom G;
+    G.TX = p.Nx >= 512 ? 512 : (p.Nx + 31) / 32 * 32;
+    G.BY = kStagedThreads / G.TX;
+    G.VG = VG;
+    G.rows_per_y = BILINEAR ? 2 : 1;
+    G.padl = 16 / TB;
+    G.row_texels = (int)(round16((size_t)(G.padl + p.W + 1) * TB) / TB);
+    G.row_bytes = (size_t)G.row_texels * TB;
+    G.stage_bytes = G.row_bytes * G.BY * G.rows_per_y;
+    G.groups_x = (p.Vx + VG - 1) / VG;
+    G.smem_bytes = kStages * G.stage_bytes + kStages * 8 + sizeof(float) * (size_t)p.N * (VG + 3) +
+                   sizeof(int) * (size_t)p.N;
+    if (G.smem_bytes > 200 * 1024 || G.BY * G.rows_per_y > 16) return false;
+    auto kern = k_composite_staged<DT, BILINEAR, VG>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem_bytes) != cudaSuccess)
+        return false;
+    const dim3 grid((unsigned)(G.groups_x * p.Vy), (unsigned)((p.Ny + G.BY - 1) / G.BY),
+                    (unsigned)((p.Nx + G.TX - 1) / G.TX));
+    kern<<<grid, kStagedThreads, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, out, ws.err);
+    note_launches(1);
+    return true;
+}
+
+template <int DT, bool BILINEAR>
+bool launch_staged(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
+                   cudaStream_t s)
+{
+    if (p.Vx >= 9) return launch_staged_vg<DT, BILINEAR, 9>(p, planes, count, ws, out, s);
+    if (p.Vx >= 5) return launch_staged_vg<DT, BILINEAR, 5>(p, planes, count, ws, out, s);
+    return launch_staged_vg<DT, BILINEAR, 3>(p, planes, count, ws, out, s);
+}
+
 template <int DT>
 void launch_composite_t(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
                         cudaStream_t s)
 {
+    if (p.N <= 4096) {
+        const bool ok = p.bilinear ? launch_staged<DT, true>(p, planes, count, ws, out, s)
+                                   : launch_staged<DT, false>(p, planes, count, ws, out, s);
+        if (ok) return;
+    }
+    // fallback: per-pixel kernel reading the planes through L1/L2
     const dim3 block(kCompBX, kCompBY);
     const dim3 grid((unsigned)((p.Nx + kCompBX - 1) / kCompBX), (unsigned)((p.Ny + kCompBY - 1) / kCompBY),
                     (unsigned)(p.Vx * p.Vy));

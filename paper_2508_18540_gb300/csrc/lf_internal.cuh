@@ -63,6 +63,7 @@ struct BuildWs {
     float4* conic_o;              // [n] (a, b, c, opacity) / voxel (lo_rel xyz, side)
     uint32_t* hist;               // [kRadix * nb_max] radix histograms
     uint32_t* bsum;               // [nb_max + 1] block sums / offsets
+    uint32_t* dtot;               // [kRadix] per-digit totals of a radix pass
     int32_t* chunk_start;         // [N + 1]
     uint32_t* dkeyA;              // [cap] tile ids
     uint32_t* dkeyB;
@@ -137,6 +138,7 @@ void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32
 struct CompWs {
     float* cx;      // [Vx][N][3] (gm, hn, hb) along x
     float* cy;      // [Vy][N][3] along y
+    int* err;       // [1] set to 1 if a bounded device wait gave up
     size_t bytes;
 };
 size_t comp_ws_layout(int32_t N, int32_t Vx, int32_t Vy, void* base, CompWs* out);

@@ -71,49 +71,46 @@ __global__ void __launch_bounds__(kSortThreads) k_upsweep(const K* __restrict__ 
     for (int i = threadIdx.x; i < kRadix; i += kSortThreads) hist[(size_t)i * a.nb + blockIdx.x] = h[i];
 }
 
-// Exclusive scan of len entries in one block of 1024 threads (contiguous
-// per-thread ranges, warp-shuffle scan of the range sums).
-__global__ void __launch_bounds__(1024) k_scan_hist(uint32_t* data, PassArgs a, int len)
+// Exclusive scan of every digit's row of per-block counts (row d holds
+// hist[d * nb + b] for blocks b), in place, one CTA per digit; the row total
+// goes to tot[d]. The downsweep adds the prefix of the digit totals.
+__global__ void __launch_bounds__(kSortThreads) k_rowscan(uint32_t* hist, uint32_t* tot, PassArgs a)
 {
     if (pass_uniform(a)) return;
-    __shared__ uint32_t warp_tot[32];
-    const int t = threadIdx.x;
-    const int per = (len + 1023) / 1024;
-    const int b = t * per;
-    const int e = min(len, b + per);
-    uint32_t sum = 0;
-    for (int i = b; i < e; ++i) sum += data[i];
-    // inclusive warp scan
-    uint32_t v = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
-        if ((t & 31) >= o) v += u;
-    }
-    if ((t & 31) == 31) warp_tot[t >> 5] = v;
-    __syncthreads();
-    if (t < 32) {
-        uint32_t w = warp_tot[t];
+    __shared__ uint32_t warp_tot[kWarps];
+    uint32_t* row = hist + (size_t)blockIdx.x * a.nb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (int base = 0; base < a.nb; base += kSortThreads) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < a.nb ? row[i] : 0u;
+        uint32_t x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t u = __shfl_up_sync(0xffffffffu, w, o);
-            if (t >= o) w += u;
+            const uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
         }
-        warp_tot[t] = w;
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t t = warp_tot[w];
+            before += w < warp ? t : 0u;
+            total += t;
+        }
+        if (i < a.nb) row[i] = carry + before + x - v;
+        carry += total;
+        __syncthreads();
     }
-    __syncthreads();
-    uint32_t run = v - sum + ((t >> 5) ? warp_tot[(t >> 5) - 1] : 0u);
-    for (int i = b; i < e; ++i) {
-        const uint32_t x = data[i];
-        data[i] = run;
-        run += x;
-    }
+    if (threadIdx.x == 0) tot[blockIdx.x] = carry;
 }
 
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads) k_downsweep(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                             K* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                            PassArgs a, const uint32_t* __restrict__ hist)
+                                                            PassArgs a, const uint32_t* __restrict__ hist,
+                                                            const uint32_t* __restrict__ tot)
 {
     __shared__ uint32_t base_off[kRadix];
     __shared__ uint32_t run[kRadix];
@@ -132,8 +129,24 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(const K* __restrict_
         return;
     }
     if (base >= n) return;
+    // digit bases: exclusive scan of the digit totals (kRadix == kSortThreads)
+    {
+        const int d = threadIdx.x, lane = d & 31, warp = d >> 5;
+        const uint32_t v = tot[d];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        if (lane == 31) wcnt[0][warp] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += wcnt[0][w];
+        base_off[d] = before + x - v + hist[(size_t)d * a.nb + blockIdx.x];
+        __syncthreads();
+    }
     for (int i = threadIdx.x; i < kRadix; i += kSortThreads) {
-        base_off[i] = hist[(size_t)i * a.nb + blockIdx.x];
         run[i] = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) wcnt[w][i] = 0;
@@ -177,15 +190,17 @@ __global__ void __launch_bounds__(kSortThreads) k_downsweep(const K* __restrict_
     }
 }
 
+static_assert(kRadix == kSortThreads, "digit-base scan assumes one digit per thread");
+
 template <typename K>
 void radix_pass(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, const PassArgs& a, uint32_t* hist,
-                cudaStream_t s)
+                uint32_t* tot, cudaStream_t s)
 {
     k_upsweep<K><<<a.nb, kSortThreads, 0, s>>>(kin, a, hist);
     note_launches(1);
-    k_scan_hist<<<1, 1024, 0, s>>>(hist, a, kRadix * a.nb);
+    k_rowscan<<<kRadix, kSortThreads, 0, s>>>(hist, tot, a);
     note_launches(1);
-    k_downsweep<K><<<a.nb, kSortThreads, 0, s>>>(kin, vin, kout, vout, a, hist);
+    k_downsweep<K><<<a.nb, kSortThreads, 0, s>>>(kin, vin, kout, vout, a, hist, tot);
     note_launches(1);
 }
 
@@ -207,7 +222,7 @@ void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s)
         a.shift = pass * kRadixBits;
         a.drop_invalid = pass == 0;
         a.nb = nb;
-        radix_pass<unsigned long long>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], a, ws.hist, s);
+        radix_pass<unsigned long long>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], a, ws.hist, ws.dtot, s);
         cur ^= 1;
     }
     // 64 / 8 = 8 passes: the result is back in (keyA, valA)
@@ -231,7 +246,7 @@ void sort_tile_keys(const BuildWs& ws, long long cap, int tile_bits, cudaStream_
             a.shift = pass * kRadixBits;
             a.drop_invalid = 0;
             a.nb = nb;
-            radix_pass<uint32_t>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], a, ws.hist, s);
+            radix_pass<uint32_t>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], a, ws.hist, ws.dtot, s);
             cur ^= 1;
         }
     }
