@@ -488,6 +488,8 @@ bool launch_staged_vg(const CompParams& p, const void* planes, const int32_t* co
     G.smem_bytes = kStages * G.stage_bytes + kStages * 8 + sizeof(float) * (size_t)p.N * (VG + 3) +
                    sizeof(int) * (size_t)p.N;
     if (G.smem_bytes > 200 * 1024 || G.BY * G.rows_per_y > 16) return false;
+    // bulk copies need 16-byte aligned rows: plane base and row pitch
+    if (((uintptr_t)planes) % 16 != 0 || ((size_t)p.W * TB) % 16 != 0) return false;
     auto kern = k_composite_staged<DT, BILINEAR, VG>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem_bytes) != cudaSuccess)
         return false;
