@@ -260,6 +260,25 @@ def run_ours(args):
     return line
 
 
+def run_profile(args):
+    """Short run for profilers: W warm-up frames then one frame per plane
+    dtype (f32, f16), no timing, no e2e, no CPU baseline."""
+    import torch
+
+    from paper_2508_18540_gb300 import api
+    from paper_2508_18540_gb300 import synth as S
+    wl = S.workload_display(seed=WORKLOAD["seed"], n=WORKLOAD["n"], res=WORKLOAD["res"], N=WORKLOAD["N"],
+                            V=WORKLOAD["V"])
+    g = api.DeviceGaussians.from_scene(wl.scene)
+    for dtype in args.profile_dtypes.split(","):
+        r = api.LightFieldRenderer(wl.camera, wl.display, wl.views, wl.N, wl.binning, dtype)
+        for _ in range(args.warmup + 1):
+            r.render(g)
+        torch.cuda.synchronize()
+        st, needed, M = r.status()
+        print("profile %s: status %d, M %d, pairs %d" % (dtype, st, M, needed), flush=True)
+
+
 def cpu_baseline(n_frames=1):
     """The FP64 oracle, as it stands, on the host cores: one full LF frame of
     the same workload (all 1M Gaussians splatted into 64 planes, 45 views
@@ -312,7 +331,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="short untimed run for ncu")
+    ap.add_argument("--profile-dtypes", default="f32,f16")
     args = ap.parse_args()
+    if args.profile:
+        import __graft_entry__
+        __graft_entry__.build()
+        run_profile(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     import __graft_entry__
