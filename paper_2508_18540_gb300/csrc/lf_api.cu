@@ -123,7 +123,8 @@ size_t comp_ws_layout(int32_t N, int32_t Vx, int32_t Vy, void* basev, CompWs* o)
     CompWs w;
     w.cx = carve<float>(base, off, (size_t)Vx * N * 3);
     w.cy = carve<float>(base, off, (size_t)Vy * N * 3);
-    w.err = carve<int>(base, off, 1);
+    w.err = carve<int>(base, off, 1 + (size_t)N);
+    w.wide = w.err + 1;
     w.bytes = align_up(off, 256);
     if (o) *o = w;
     return w.bytes;
@@ -547,7 +548,8 @@ lf_status lf_composite(const lf_planes* planes, const lf_ref_camera* ref, const 
     p.tthp_y = ref->tthp_y;
     p.tphi_x = ref->tphi_x;
     p.tphi_y = ref->tphi_y;
-    if (cudaMemsetAsync(cw.err, 0, sizeof(int), stream) != cudaSuccess) return check_launch("composite reset");
+    if (cudaMemsetAsync(cw.err, 0, sizeof(int) * (1 + (size_t)planes->N), stream) != cudaSuccess)
+        return check_launch("composite reset");
     trace_begin("comp_coeffs", stream);
     launch_comp_coeffs(p, planes->d, planes->count, cw, stream);
     trace_end(stream);

@@ -18,7 +18,7 @@ namespace lf {
 namespace {
 
 constexpr int kDupThreads = 256;
-constexpr int kDupPer = 16;
+constexpr int kDupPer = 4;
 constexpr int kDupBlock = kDupThreads * kDupPer;
 
 __device__ __forceinline__ double key_depth(unsigned long long k) { return __longlong_as_double((long long)k); }
@@ -198,13 +198,23 @@ __global__ void __launch_bounds__(kDupThreads) k_dup_emit(BuildWs w, const int4*
     }
 }
 
+__device__ __forceinline__ void range_one(const BuildWs& w, const uint32_t* __restrict__ keys,
+                                          const uint32_t* __restrict__ vals, const int32_t* __restrict__ chunk,
+                                          int N, long long n, long long i);
+
 __global__ void __launch_bounds__(256) k_ranges(BuildWs w, const uint32_t* __restrict__ keys,
                                                 const uint32_t* __restrict__ vals, const int32_t* __restrict__ chunk,
                                                 int N)
 {
     const long long n = (long long)w.hdr->tile_n;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        range_one(w, keys, vals, chunk, N, n, i);
+}
+
+__device__ __forceinline__ void range_one(const BuildWs& w, const uint32_t* __restrict__ keys,
+                                          const uint32_t* __restrict__ vals, const int32_t* __restrict__ chunk,
+                                          int N, long long n, long long i)
+{
     const uint32_t t = keys[i];
     const int c = chunk[vals[i]];
     const long long sidx = (long long)t * N + c;
@@ -243,7 +253,9 @@ void launch_ranges(const BuildWs& ws, long long cap, const uint32_t* tkeys, cons
                    int N, cudaStream_t s)
 {
     if (cap <= 0) return;
-    const unsigned blocks = (unsigned)((cap + 255) / 256);
+    // grid-stride over the device-side pair count
+    const long long want = (cap + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
     k_ranges<<<blocks, 256, 0, s>>>(ws, tkeys, tvals, chunk, N);
     note_launches(1);
 }

@@ -8,7 +8,7 @@
 // den = (d_k - D_forward) tan(theta'/2), a = d_k tan(theta/2),
 // g = W a / (Nx den), h = (W/2)((Delta (D_focal - d_k)/D_focal + a (1-Nx)/Nx)/den + 1) - 1/2,
 // gm = g - P_s), rounded once to FP32.
-// k_composite walks the planes front to back for every view pixel:
+// The composite kernels walk the planes front to back for every view pixel:
 // nearest texel index P_s x + floor(fma(gm, x, hn)) (FP32 decision), or
 // bilinear taps around X with zero padding; Q += T c_k, T *= 1 - A_k
 // (Eq. (alpha_blend)); empty planes skipped; output (Q + T bg, 1 - T).
@@ -20,6 +20,11 @@
 namespace lf {
 
 namespace {
+
+// |fma(gm, x, h)| below this bound for every x of a row lets the staged
+// kernel skip its clamps (and keeps the exact floor below valid).
+constexpr float kNarrow = 1048576.0f;    // 2^20
+constexpr float kClamp = 2097152.0f;     // 2^21
 
 __device__ __forceinline__ double view_offset(int j, int V, double Df, double tphi)
 {
@@ -55,12 +60,21 @@ __global__ void k_comp_coeffs(CompParams p, const double* __restrict__ d, const 
         out[0] = out[1] = out[2] = 0.0f;
         return;
     }
-    if (along_x)
+    int n;
+    if (along_x) {
         axis_coeffs(view_offset(v, p.Vx, p.D_focal, p.tphi_x), d[k], p.D_focal, p.D_forward, p.tth_x, p.tthp_x, p.Nx,
                     p.W, p.P_s, out);
-    else
+        n = p.Nx;
+    } else {
         axis_coeffs(view_offset(v, p.Vy, p.D_focal, p.tphi_y), d[k], p.D_focal, p.D_forward, p.tth_y, p.tthp_y, p.Ny,
                     p.H, p.P_s, out);
+        n = p.Ny;
+    }
+    // the row's range of gm x + h (affine in x): flag planes that may leave it
+    const double lo = fmin((double)out[2], (double)out[1]);
+    const double hi = fmax((double)out[2], (double)out[1]);
+    const double span = fabs((double)out[0]) * (double)(n - 1);
+    if (!(fmax(fabs(lo), fabs(hi)) + span + 2.0 < (double)kNarrow)) atomicOr(&w.wide[k], 1);
 }
 
 template <int DT>
@@ -92,6 +106,8 @@ __device__ __forceinline__ int nearest_index(int P_s, int x, float gm, float hn)
 
 constexpr int kCompBX = 32, kCompBY = 8;
 
+// Unstaged fallback (planes read through L1/L2), used when the staged kernel's
+// shared-memory layout does not fit or rows are not 16-byte aligned.
 template <int DT, bool BILINEAR>
 __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, const void* __restrict__ planes,
                                                                const int32_t* __restrict__ count, CompWs w,
@@ -168,22 +184,26 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
 // plane rows (their vertical map depends on (i, k) only), and neighbouring
 // views read horizontally shifted copies of those rows. A CTA therefore owns
 // BY output rows x TX output columns for a group of VG views of one view row;
-// for every non-empty plane it copies the BY plane rows it needs (2 BY for
-// bilinear) into shared memory with bulk asynchronous copies
-// (cp.async.bulk + mbarrier transaction counts, 3-stage ring, one producer
-// thread), and every thread composites its pixel for the VG views from
-// shared memory. Every staged row has zero texels on both sides, so an
-// out-of-plane index reads a transparent zero without a branch.
+// for every non-empty plane one producer thread copies the BY plane rows the
+// CTA needs (2 BY for bilinear) into shared memory with bulk asynchronous
+// copies (cp.async.bulk, completion counted on a "full" mbarrier), and every
+// thread composites its pixel for the VG views from shared memory. Warps
+// release a stage through an "empty" mbarrier, so no CTA-wide barrier sits in
+// the plane loop. Every staged row carries zero texels on both sides: an
+// out-of-plane index is clamped onto one and reads a transparent zero.
+// The floor of the FP32 index uses the exact round-toward-minus-infinity add
+// of 1.5 * 2^23 (valid for |value| < 2^22) instead of a conversion unit op.
+// All waits are bounded; a wait that gives up sets the error word.
 // ---------------------------------------------------------------------------
 
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 constexpr int kStagedThreads = 512;
-constexpr long long kSpinLimit = 1ll << 26;   // bounded mbarrier waits
+constexpr int kStagedWarps = kStagedThreads / 32;
+constexpr long long kSpinLimit = 1ll << 26;
+constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
@@ -195,6 +215,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
@@ -204,6 +229,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
         : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    for (long long it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
 }
 
 __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
@@ -251,37 +283,113 @@ struct Texel<LF_BF16> {
 struct StagedGeom {
     int TX, BY, VG, rows_per_y;    // rows_per_y: 1 nearest, 2 bilinear
     int padl;                      // zero texels left of every staged row (16 bytes)
-    int row_texels;                // padl + W + right pad, rounded to 16 bytes
+    int row_texels;                // padl + W + right pad, a multiple of 16 bytes
     size_t row_bytes, stage_bytes, smem_bytes;
     int groups_x;                  // view groups per view row
 };
 
-__host__ __device__ inline size_t round16(size_t v) { return (v + 15) / 16 * 16; }
+inline size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 
-// FP32 decision of the plane row / column as in the unstaged kernel
-__device__ __forceinline__ float decide(float gm, int x, float h)
+// floor(fma(g, x, h)) as the bit pattern of (value + 1.5 * 2^23) rounded
+// toward minus infinity; callers add base - kMagicBits to get an index.
+template <bool CLAMP>
+__device__ __forceinline__ float floor_magic(float g, float x, float h)
 {
-    return fminf(fmaxf(floorf(__fmaf_rn(gm, (float)x, h)), -2.0e6f), 2.0e6f);
+    float f = __fmaf_rn(g, x, h);
+    if (CLAMP) f = fminf(fmaxf(f, -kClamp), kClamp);
+    return __fadd_rd(f, kMagic);
+}
+
+// plane row sampled by output row y (nearest) or its upper bilinear row
+__device__ __forceinline__ int plane_row(int P_s, int y, float gm, float h)
+{
+    return P_s * y + (__float_as_int(floor_magic<true>(gm, (float)y, h)) - kMagicBits);
+}
+
+template <int DT, bool BILINEAR, int VG, bool CLAMP>
+__device__ __forceinline__ void blend_plane(float (&acc)[VG][4], const float* c, const unsigned char* sb,
+                                            const StagedGeom& G, const CompParams& p, int x, int y, int ty,
+                                            uint32_t maxi)
+{
+    using TX_ = Texel<DT>;
+    const float gmx = c[0];
+    const float xf = (float)x;
+    const int base_x = p.P_s * x + G.padl - kMagicBits;
+    if (!BILINEAR) {
+        const int iy = plane_row(p.P_s, y, c[1], c[2]);
+        if (iy < 0 || iy >= p.H) return;
+        const char* row = reinterpret_cast<const char*>(sb + (size_t)ty * G.row_bytes);
+#pragma unroll
+        for (int jj = 0; jj < VG; ++jj) {
+            const int ix = __float_as_int(floor_magic<CLAMP>(gmx, xf, c[3 + jj])) + base_x;
+            const float4 t = TX_::load(row, min((uint32_t)ix, maxi));
+            const float T = acc[jj][3];
+            acc[jj][0] = fmaf(T, t.x, acc[jj][0]);
+            acc[jj][1] = fmaf(T, t.y, acc[jj][1]);
+            acc[jj][2] = fmaf(T, t.z, acc[jj][2]);
+            acc[jj][3] = fmaf(-T, t.w, T);
+        }
+    } else {
+        float fy = __fmaf_rn(c[1], (float)y, c[2]);
+        fy = fminf(fmaxf(fy, -kClamp), kClamp);
+        const float ty_m = __fadd_rd(fy, kMagic);
+        const float wy = fy - (ty_m - kMagic);
+        const int y0 = p.P_s * y + (__float_as_int(ty_m) - kMagicBits);
+        const bool v0 = y0 >= 0 && y0 < p.H, v1 = y0 + 1 >= 0 && y0 + 1 < p.H;
+        if (!v0 && !v1) return;
+        const float w0 = v0 ? 1.0f - wy : 0.0f, w1 = v1 ? wy : 0.0f;
+        const char* r0 = reinterpret_cast<const char*>(sb + (size_t)(2 * ty) * G.row_bytes);
+        const char* r1 = r0 + G.row_bytes;
+#pragma unroll
+        for (int jj = 0; jj < VG; ++jj) {
+            float fx = __fmaf_rn(gmx, xf, c[3 + jj]);
+            if (CLAMP) fx = fminf(fmaxf(fx, -kClamp), kClamp);
+            const float tm = __fadd_rd(fx, kMagic);
+            const float wx = fx - (tm - kMagic), wa = 1.0f - wx;
+            const int i0 = __float_as_int(tm) + base_x;
+            const uint32_t a0 = min((uint32_t)i0, maxi), a1 = min((uint32_t)(i0 + 1), maxi);
+            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (v0) {
+                const float4 ta = TX_::load(r0, a0), tb = TX_::load(r0, a1);
+                t.x = w0 * fmaf(wa, ta.x, wx * tb.x);
+                t.y = w0 * fmaf(wa, ta.y, wx * tb.y);
+                t.z = w0 * fmaf(wa, ta.z, wx * tb.z);
+                t.w = w0 * fmaf(wa, ta.w, wx * tb.w);
+            }
+            if (v1) {
+                const float4 ta = TX_::load(r1, a0), tb = TX_::load(r1, a1);
+                t.x = fmaf(w1, fmaf(wa, ta.x, wx * tb.x), t.x);
+                t.y = fmaf(w1, fmaf(wa, ta.y, wx * tb.y), t.y);
+                t.z = fmaf(w1, fmaf(wa, ta.z, wx * tb.z), t.z);
+                t.w = fmaf(w1, fmaf(wa, ta.w, wx * tb.w), t.w);
+            }
+            const float T = acc[jj][3];
+            acc[jj][0] = fmaf(T, t.x, acc[jj][0]);
+            acc[jj][1] = fmaf(T, t.y, acc[jj][1]);
+            acc[jj][2] = fmaf(T, t.z, acc[jj][2]);
+            acc[jj][3] = fmaf(-T, t.w, T);
+        }
+    }
 }
 
 template <int DT, bool BILINEAR, int VG>
 __global__ void __launch_bounds__(kStagedThreads, 2) k_composite_staged(CompParams p, StagedGeom G,
                                                                         const char* __restrict__ planes,
                                                                         const int32_t* __restrict__ count, CompWs w,
-                                                                        float* __restrict__ out, int* __restrict__ err)
+                                                                        float* __restrict__ out)
 {
-    using TX_ = Texel<DT>;
-    constexpr int TB = TX_::kBytes;
+    constexpr int TB = Texel<DT>::kBytes;
     extern __shared__ __align__(128) unsigned char smem[];
-    // layout: [stages][rows][row_bytes] | mbarriers | coef | plane list
+    // [stages][rows][row_bytes] | full[stages] | empty[stages] | coef [N][VG+3] | plist [N] | wide [N]
     unsigned char* stage_base = smem;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * G.stage_bytes);
-    float* coef = reinterpret_cast<float*>(bars + kStages);          // [N][VG + 3]
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * G.stage_bytes);
+    uint64_t* empty = full + kStages;
+    float* coef = reinterpret_cast<float*>(empty + kStages);
     int* plist = reinterpret_cast<int*>(coef + (size_t)p.N * (VG + 3));
+    int* pwide = plist + p.N;
     __shared__ int s_nplanes;
-    __shared__ int s_abort;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int vgroup = blockIdx.x;                 // fastest: neighbouring CTAs share plane rows in L2
     const int vi = vgroup / G.groups_x;            // view row
     const int j0 = (vgroup % G.groups_x) * VG;     // first view column of the group
@@ -304,169 +412,119 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k_composite_staged(CompPara
             coef[k * CW + 2] = BILINEAR ? cy[2] : cy[1];
         }
     }
-    // list of non-empty planes (warp 0, ballot compaction keeps plane order)
+    // list of non-empty planes in order (warp 0, ballot compaction)
     if (tid < 32) {
         int n = 0;
         for (int b = 0; b < p.N; b += 32) {
             const int k = b + tid;
             const bool ne = k < p.N && count[k] != 0;
             const unsigned m = __ballot_sync(0xffffffffu, ne);
-            if (ne) plist[n + __popc(m & ((1u << tid) - 1u))] = k;
+            if (ne) {
+                const int pos = n + __popc(m & ((1u << tid) - 1u));
+                plist[pos] = k;
+                pwide[pos] = w.wide[k];
+            }
             n += __popc(m);
         }
-        if (tid == 0) {
-            s_nplanes = n;
-            s_abort = 0;
-        }
+        if (tid == 0) s_nplanes = n;
     }
-    // zero pads of every staged row (never written by the bulk copies)
+    // zero pads of every staged row (the bulk copies never write them)
     const int nrows = G.BY * G.rows_per_y;
     for (int e = tid; e < kStages * nrows; e += kStagedThreads) {
         unsigned char* row = stage_base + (size_t)(e / nrows) * G.stage_bytes + (size_t)(e % nrows) * G.row_bytes;
         for (int b = 0; b < G.padl * TB; b += 4) *reinterpret_cast<uint32_t*>(row + b) = 0u;
-        for (size_t b = (size_t)(G.padl + p.W) * TB; b < G.row_bytes; b += 4) *reinterpret_cast<uint32_t*>(row + b) = 0u;
+        for (size_t b = (size_t)(G.padl + p.W) * TB; b < G.row_bytes; b += 4)
+            *reinterpret_cast<uint32_t*>(row + b) = 0u;
     }
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(smem_addr(&bars[s]), 1);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_addr(&full[s]), 1);
+            mbar_init(smem_addr(&empty[s]), kStagedWarps);
+        }
         fence_proxy_async();
     }
     __syncthreads();
     const int P = s_nplanes;
     const size_t plane_bytes = (size_t)p.W * p.H * TB;
-    const uint32_t row_copy = (uint32_t)((size_t)p.W * TB / 16 * 16);   // bulk part (multiple of 16 bytes)
-    const uint32_t row_tail = (uint32_t)((size_t)p.W * TB - row_copy);  // 0 or 8 bytes
+    const uint32_t row_copy = (uint32_t)((size_t)p.W * TB);   // a multiple of 16 (checked at launch)
 
     // producer: stage the plane rows of list entry q into stage q % kStages
     auto produce = [&](int q) {
         const int k = plist[q];
         const float* c = coef + (size_t)k * CW;
         unsigned char* sb = stage_base + (size_t)(q % kStages) * G.stage_bytes;
-        const uint32_t bar = smem_addr(&bars[q % kStages]);
+        const uint32_t bar = smem_addr(&full[q % kStages]);
         uint32_t bytes = 0;
-        int rows[16];
-        int nr = 0;
         for (int r = 0; r < G.BY; ++r) {
             const int yy = Y0 + r;
-            const int base = yy < p.Ny ? p.P_s * yy + (int)decide(c[1], yy, c[2]) : -1;
-            for (int t = 0; t < G.rows_per_y; ++t) {
-                const int iy = base + t;
-                const bool ok = yy < p.Ny && iy >= 0 && iy < p.H;
-                rows[nr++] = ok ? iy : -1;
-                if (ok) bytes += row_copy;
-            }
+            if (yy >= p.Ny) continue;
+            const int base = plane_row(p.P_s, yy, c[1], c[2]);
+            for (int t = 0; t < G.rows_per_y; ++t)
+                if (base + t >= 0 && base + t < p.H) bytes += row_copy;
         }
         fence_proxy_async();
         mbar_arrive_expect_tx(bar, bytes);
-        for (int r = 0; r < nr; ++r) {
-            if (rows[r] < 0) continue;
-            const char* src = planes + (size_t)k * plane_bytes + (size_t)rows[r] * p.W * TB;
-            unsigned char* dst = sb + (size_t)r * G.row_bytes + (size_t)G.padl * TB;
-            if (row_copy) bulk_copy_g2s(smem_addr(dst), src, row_copy, bar);
-            if (row_tail) *reinterpret_cast<uint2*>(dst + row_copy) = *reinterpret_cast<const uint2*>(src + row_copy);
+        for (int r = 0; r < G.BY; ++r) {
+            const int yy = Y0 + r;
+            if (yy >= p.Ny) continue;
+            const int base = plane_row(p.P_s, yy, c[1], c[2]);
+            for (int t = 0; t < G.rows_per_y; ++t) {
+                const int iy = base + t;
+                if (iy < 0 || iy >= p.H) continue;
+                const char* src = planes + (size_t)k * plane_bytes + (size_t)iy * row_copy;
+                unsigned char* dst = sb + (size_t)(r * G.rows_per_y + t) * G.row_bytes + (size_t)G.padl * TB;
+                bulk_copy_g2s(smem_addr(dst), src, row_copy, bar);
+            }
         }
     };
 
     if (tid == 0)
         for (int q = 0; q < min(P, kStages); ++q) produce(q);
-    __syncthreads();
 
     float acc[VG][4];
 #pragma unroll
     for (int jj = 0; jj < VG; ++jj) acc[jj][0] = acc[jj][1] = acc[jj][2] = 0.f, acc[jj][3] = 1.f;
     const bool live = ty < G.BY && x < p.Nx && y < p.Ny;   // threads past BY rows idle
-    const uint32_t maxi = (uint32_t)(G.padl + p.W);     // first right-pad texel
+    const uint32_t maxi = (uint32_t)(G.padl + p.W);       // first right-pad texel
+    bool ok = true;
 
-    for (int q = 0; q < P; ++q) {
+    for (int q = 0; q < P && ok; ++q) {
         const int s = q % kStages;
-        const uint32_t bar = smem_addr(&bars[s]);
         const uint32_t parity = (uint32_t)((q / kStages) & 1);
-        bool done = false;
-        for (long long it = 0; it < kSpinLimit && !done; ++it) done = mbar_try_wait(bar, parity);
-        if (__syncthreads_or(!done)) {
-            if (tid == 0) {
-                s_abort = 1;
-                atomicExch(err, 1);
-            }
+        if (!mbar_wait_bounded(smem_addr(&full[s]), parity)) {
+            atomicExch(w.err, 1);
+            ok = false;
             break;
         }
-        const int k = plist[q];
-        const float* c = coef + (size_t)k * CW;
         if (live) {
+            const float* c = coef + (size_t)plist[q] * CW;
             const unsigned char* sb = stage_base + (size_t)s * G.stage_bytes;
-            const float gmx = c[0];
-            const float fy = __fmaf_rn(c[1], (float)y, c[2]);
-            if (!BILINEAR) {
-                const int iy = p.P_s * y + (int)decide(c[1], y, c[2]);
-                if (iy >= 0 && iy < p.H) {
-                    const char* row = reinterpret_cast<const char*>(sb + (size_t)ty * G.row_bytes);
-#pragma unroll
-                    for (int jj = 0; jj < VG; ++jj) {
-                        const int ix = p.P_s * x + (int)decide(gmx, x, c[3 + jj]);
-                        const uint32_t i = min((uint32_t)(ix + G.padl), maxi);
-                        const float4 t = TX_::load(row, i);
-                        const float T = acc[jj][3];
-                        acc[jj][0] = fmaf(T, t.x, acc[jj][0]);
-                        acc[jj][1] = fmaf(T, t.y, acc[jj][1]);
-                        acc[jj][2] = fmaf(T, t.z, acc[jj][2]);
-                        acc[jj][3] = T * (1.0f - t.w);
-                    }
-                }
-            } else if (fy >= -1.0e6f && fy <= 1.0e6f) {
-                const float fly = floorf(fy);
-                const float wy = fy - fly;
-                const int y0 = p.P_s * y + (int)fly;
-                const char* r0 = reinterpret_cast<const char*>(sb + (size_t)(2 * ty) * G.row_bytes);
-                const char* r1 = r0 + G.row_bytes;
-                const bool v0 = y0 >= 0 && y0 < p.H, v1 = y0 + 1 >= 0 && y0 + 1 < p.H;
-                const float w0 = v0 ? 1.0f - wy : 0.0f, w1 = v1 ? wy : 0.0f;
-#pragma unroll
-                for (int jj = 0; jj < VG; ++jj) {
-                    const float fx = __fmaf_rn(gmx, (float)x, c[3 + jj]);
-                    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (fx >= -1.0e6f && fx <= 1.0e6f) {
-                        const float flx = floorf(fx);
-                        const float wx = fx - flx;
-                        const int x0 = p.P_s * x + (int)flx;
-                        const uint32_t i0 = min((uint32_t)(x0 + G.padl), maxi);
-                        const uint32_t i1 = min((uint32_t)(x0 + 1 + G.padl), maxi);
-                        const float wa = 1.0f - wx;
-                        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-                        if (v0) {
-                            const float4 ta = TX_::load(r0, i0), tb = TX_::load(r0, i1);
-                            a = make_float4(fmaf(wa, ta.x, wx * tb.x), fmaf(wa, ta.y, wx * tb.y),
-                                            fmaf(wa, ta.z, wx * tb.z), fmaf(wa, ta.w, wx * tb.w));
-                        }
-                        if (v1) {
-                            const float4 ta = TX_::load(r1, i0), tb = TX_::load(r1, i1);
-                            b = make_float4(fmaf(wa, ta.x, wx * tb.x), fmaf(wa, ta.y, wx * tb.y),
-                                            fmaf(wa, ta.z, wx * tb.z), fmaf(wa, ta.w, wx * tb.w));
-                        }
-                        t = make_float4(fmaf(w0, a.x, w1 * b.x), fmaf(w0, a.y, w1 * b.y), fmaf(w0, a.z, w1 * b.z),
-                                        fmaf(w0, a.w, w1 * b.w));
-                    }
-                    const float T = acc[jj][3];
-                    acc[jj][0] = fmaf(T, t.x, acc[jj][0]);
-                    acc[jj][1] = fmaf(T, t.y, acc[jj][1]);
-                    acc[jj][2] = fmaf(T, t.z, acc[jj][2]);
-                    acc[jj][3] = T * (1.0f - t.w);
-                }
+            if (pwide[q])
+                blend_plane<DT, BILINEAR, VG, true>(acc, c, sb, G, p, x, y, ty, maxi);
+            else
+                blend_plane<DT, BILINEAR, VG, false>(acc, c, sb, G, p, x, y, ty, maxi);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
+        if (tid == 0 && q + kStages < P) {
+            // every warp has released stage s: refill it
+            if (!mbar_wait_bounded(smem_addr(&empty[s]), parity)) {
+                atomicExch(w.err, 1);
+                ok = false;
+                break;
             }
+            produce(q + kStages);
         }
-        __syncthreads();   // stage s is free again
-        if (tid == 0 && q + kStages < P) produce(q + kStages);
     }
-    if (s_abort) return;
-    if (live) {
+    if (!ok || !live) return;
 #pragma unroll
-        for (int jj = 0; jj < VG; ++jj) {
-            const int j = j0 + jj;
-            if (j >= p.Vx) break;
-            const int v = vi * p.Vx + j;
-            const float T = acc[jj][3];
-            reinterpret_cast<float4*>(out)[((size_t)v * p.Ny + y) * p.Nx + x] =
-                make_float4(fmaf(T, p.bg[0], acc[jj][0]), fmaf(T, p.bg[1], acc[jj][1]),
-                            fmaf(T, p.bg[2], acc[jj][2]), 1.0f - T);
-        }
+    for (int jj = 0; jj < VG; ++jj) {
+        const int j = j0 + jj;
+        if (j >= p.Vx) break;
+        const int v = vi * p.Vx + j;
+        const float T = acc[jj][3];
+        reinterpret_cast<float4*>(out)[((size_t)v * p.Ny + y) * p.Nx + x] = make_float4(
+            fmaf(T, p.bg[0], acc[jj][0]), fmaf(T, p.bg[1], acc[jj][1]), fmaf(T, p.bg[2], acc[jj][2]), 1.0f - T);
     }
 }
 
@@ -485,9 +543,9 @@ bool launch_staged_vg(const CompParams& p, const void* planes, const int32_t* co
     G.row_bytes = (size_t)G.row_texels * TB;
     G.stage_bytes = G.row_bytes * G.BY * G.rows_per_y;
     G.groups_x = (p.Vx + VG - 1) / VG;
-    G.smem_bytes = kStages * G.stage_bytes + kStages * 8 + sizeof(float) * (size_t)p.N * (VG + 3) +
-                   sizeof(int) * (size_t)p.N;
-    if (G.smem_bytes > 200 * 1024 || G.BY * G.rows_per_y > 16) return false;
+    G.smem_bytes = kStages * G.stage_bytes + 2 * kStages * 8 + sizeof(float) * (size_t)p.N * (VG + 3) +
+                   2 * sizeof(int) * (size_t)p.N;
+    if (G.smem_bytes > 200 * 1024) return false;
     // bulk copies need 16-byte aligned rows: plane base and row pitch
     if (((uintptr_t)planes) % 16 != 0 || ((size_t)p.W * TB) % 16 != 0) return false;
     auto kern = k_composite_staged<DT, BILINEAR, VG>;
@@ -495,7 +553,7 @@ bool launch_staged_vg(const CompParams& p, const void* planes, const int32_t* co
         return false;
     const dim3 grid((unsigned)(G.groups_x * p.Vy), (unsigned)((p.Ny + G.BY - 1) / G.BY),
                     (unsigned)((p.Nx + G.TX - 1) / G.TX));
-    kern<<<grid, kStagedThreads, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, out, ws.err);
+    kern<<<grid, kStagedThreads, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, out);
     note_launches(1);
     return true;
 }
@@ -518,7 +576,6 @@ void launch_composite_t(const CompParams& p, const void* planes, const int32_t* 
                                    : launch_staged<DT, false>(p, planes, count, ws, out, s);
         if (ok) return;
     }
-    // fallback: per-pixel kernel reading the planes through L1/L2
     const dim3 block(kCompBX, kCompBY);
     const dim3 grid((unsigned)((p.Nx + kCompBX - 1) / kCompBX), (unsigned)((p.Ny + kCompBY - 1) / kCompBY),
                     (unsigned)(p.Vx * p.Vy));

@@ -18,7 +18,7 @@ namespace lf {
 constexpr int kTile = 16;                 // splat tile edge (pixels)
 constexpr int kTilePix = kTile * kTile;   // threads per rasterisation CTA
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;            // keys per thread per radix block
+constexpr int kSortItems = 4;             // keys per thread per radix block
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
@@ -139,6 +139,7 @@ struct CompWs {
     float* cx;      // [Vx][N][3] (gm, hn, hb) along x
     float* cy;      // [Vy][N][3] along y
     int* err;       // [1] set to 1 if a bounded device wait gave up
+    int* wide;      // [N] 1 if some view's index range of plane k needs clamping
     size_t bytes;
 };
 size_t comp_ws_layout(int32_t N, int32_t Vx, int32_t Vy, void* base, CompWs* out);

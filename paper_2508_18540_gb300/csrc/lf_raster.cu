@@ -40,19 +40,36 @@ __device__ __forceinline__ void store_texel(void* planes, size_t idx, float r, f
     }
 }
 
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// One CTA per (16x16 tile, chunk); warp w owns pixel rows 2w, 2w+1 of the
+// tile. Each batch of up to 256 list entries is staged in shared memory
+// with the conic pre-scaled so that alpha = min(0.99, o 2^(A dx^2 + B dx dy + C dy^2)),
+// A = -log2(e)/2 a, B = -log2(e) b, C = -log2(e)/2 c. Every warp first
+// ballots which entries touch its 2 x 16 strip and then visits only those,
+// in list order, so per-pixel blending order is unchanged.
 template <int DT>
 __global__ void __launch_bounds__(kTilePix) k_raster_gauss(BuildWs w, RasterParams p, const uint32_t* __restrict__ tvals,
                                                            const float* __restrict__ rgb, const int4* __restrict__ rect,
                                                            void* planes)
 {
+    constexpr float kL2E = 1.4426950408889634f;
     __shared__ float2 s_mean[kTilePix];
     __shared__ float4 s_con[kTilePix];
     __shared__ float4 s_rgb[kTilePix];
-    __shared__ int4 s_rect[kTilePix];
+    __shared__ int4 s_rect[kTilePix];   // x0, y0, x1 - x0, y1 - y0
     const int t = blockIdx.x, k = blockIdx.y;
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
     const int py = ty * kTile + (threadIdx.x / kTile);
+    const int sx0 = tx * kTile, sx1 = sx0 + kTile - 1;            // warp strip bounds
+    const int sy0 = ty * kTile + 2 * warp, sy1 = sy0 + 1;
     const int2 sg = w.seg[(size_t)t * p.N + k];
     const float fpx = (float)px, fpy = (float)py;
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
@@ -61,26 +78,39 @@ __global__ void __launch_bounds__(kTilePix) k_raster_gauss(BuildWs w, RasterPara
         if (i < sg.y) {
             const uint32_t g = tvals[i];
             s_mean[threadIdx.x] = w.mean2d[g];
-            s_con[threadIdx.x] = w.conic_o[g];
+            const float4 c = w.conic_o[g];
+            s_con[threadIdx.x] = make_float4(-0.5f * kL2E * c.x, -kL2E * c.y, -0.5f * kL2E * c.z, c.w);
             s_rgb[threadIdx.x] = make_float4(rgb[3 * (size_t)g], rgb[3 * (size_t)g + 1], rgb[3 * (size_t)g + 2], 0.f);
-            s_rect[threadIdx.x] = rect[g];
+            const int4 r = rect[g];
+            s_rect[threadIdx.x] = make_int4(r.x, r.y, r.z - r.x, r.w - r.y);
         }
         __syncthreads();
         const int cnt = min(kTilePix, sg.y - base);
-        for (int j = 0; j < cnt; ++j) {
-            const int4 rc = s_rect[j];
-            if (px >= rc.x && px <= rc.z && py >= rc.y && py <= rc.w) {
-                const float2 m = s_mean[j];
-                const float4 c = s_con[j];
-                const float dx = fpx - m.x, dy = fpy - m.y;
-                const float q = fmaf(c.x * dx, dx, fmaf(2.0f * c.y * dx, dy, c.z * dy * dy));
-                const float al = fminf(0.99f, c.w * __expf(-0.5f * q));
-                const float4 col = s_rgb[j];
-                const float ta = T * al;
-                C0 = fmaf(ta, col.x, C0);
-                C1 = fmaf(ta, col.y, C1);
-                C2 = fmaf(ta, col.z, C2);
-                T = T * (1.0f - al);
+        for (int m0 = 0; m0 < cnt; m0 += 32) {
+            const int jl = m0 + lane;
+            bool hit = false;
+            if (jl < cnt) {
+                const int4 r = s_rect[jl];
+                hit = r.x <= sx1 && r.x + r.z >= sx0 && r.y <= sy1 && r.y + r.w >= sy0;
+            }
+            uint32_t mask = __ballot_sync(0xffffffffu, hit);
+            while (mask) {
+                const int j = m0 + __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int4 rc = s_rect[j];
+                if ((uint32_t)(px - rc.x) <= (uint32_t)rc.z && (uint32_t)(py - rc.y) <= (uint32_t)rc.w) {
+                    const float2 m = s_mean[j];
+                    const float4 c = s_con[j];
+                    const float dx = fpx - m.x, dy = fpy - m.y;
+                    const float pw = fmaf(dx, fmaf(c.x, dx, c.y * dy), c.z * dy * dy);
+                    const float al = fminf(0.99f, c.w * ex2_approx(pw));
+                    const float4 col = s_rgb[j];
+                    const float ta = T * al;
+                    C0 = fmaf(ta, col.x, C0);
+                    C1 = fmaf(ta, col.y, C1);
+                    C2 = fmaf(ta, col.z, C2);
+                    T = fmaf(-T, al, T);
+                }
             }
         }
         __syncthreads();

@@ -59,13 +59,19 @@ __global__ void __launch_bounds__(kSortThreads) k_upsweep(const K* __restrict__ 
     for (int i = threadIdx.x; i < kRadix; i += kSortThreads) h[i] = 0;
     __syncthreads();
     const long long base = (long long)blockIdx.x * kSortTile;
-#pragma unroll 4
+    // warp-aggregated counting: one shared atomic per distinct digit per warp
+    // (depth keys of nearby primitives share their high digits)
+    const int lane = threadIdx.x & 31;
+#pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
         const long long idx = base + (long long)it * kSortThreads + threadIdx.x;
+        uint32_t d = (uint32_t)kRadix;
         if (idx < n) {
             const K k = keys[idx];
-            if (!(a.drop_invalid && (unsigned long long)k == kInvalidKey)) atomicAdd(&h[digit_of(k, a.shift)], 1u);
+            if (!(a.drop_invalid && (unsigned long long)k == kInvalidKey)) d = digit_of(k, a.shift);
         }
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (d < (uint32_t)kRadix && (__ffs(peers) - 1) == lane) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kRadix; i += kSortThreads) hist[(size_t)i * a.nb + blockIdx.x] = h[i];
