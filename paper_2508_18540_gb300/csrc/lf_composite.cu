@@ -196,9 +196,10 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
 // All waits are bounded; a wait that gives up sets the error word.
 // ---------------------------------------------------------------------------
 
-constexpr int kStages = 4;
-constexpr int kStagedThreads = 512;
-constexpr int kStagedWarps = kStagedThreads / 32;
+constexpr int kStages = 6;
+constexpr int kStagedThreads = 512;                  // consumer threads
+constexpr int kStagedWarps = kStagedThreads / 32;     // consumer warps
+constexpr int kStagedBlock = kStagedThreads + 32;     // + one producer warp
 constexpr long long kSpinLimit = 1ll << 26;
 constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
@@ -247,22 +248,48 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uin
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// explicit shared-space loads (32-bit shared addresses, LDS)
+__device__ __forceinline__ float4 lds_f4(uint32_t a)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ uint2 lds_u2(uint32_t a)
+{
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ float lds_f(uint32_t a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ int lds_i(uint32_t a)
+{
+    int v;
+    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
 template <int DT>
 struct Texel;
 template <>
 struct Texel<LF_F32> {
     static constexpr int kBytes = 16;
-    static __device__ __forceinline__ float4 load(const char* row, uint32_t i)
-    {
-        return *reinterpret_cast<const float4*>(row + (size_t)i * 16);
-    }
+    static __device__ __forceinline__ float4 load(uint32_t row, uint32_t i) { return lds_f4(row + i * 16u); }
 };
 template <>
 struct Texel<LF_F16> {
     static constexpr int kBytes = 8;
-    static __device__ __forceinline__ float4 load(const char* row, uint32_t i)
+    static __device__ __forceinline__ float4 load(uint32_t row, uint32_t i)
     {
-        const uint2 u = *reinterpret_cast<const uint2*>(row + (size_t)i * 8);
+        const uint2 u = lds_u2(row + i * 8u);
         const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
         const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
         return make_float4(a.x, a.y, b.x, b.y);
@@ -271,9 +298,9 @@ struct Texel<LF_F16> {
 template <>
 struct Texel<LF_BF16> {
     static constexpr int kBytes = 8;
-    static __device__ __forceinline__ float4 load(const char* row, uint32_t i)
+    static __device__ __forceinline__ float4 load(uint32_t row, uint32_t i)
     {
-        const uint2 u = *reinterpret_cast<const uint2*>(row + (size_t)i * 8);
+        const uint2 u = lds_u2(row + i * 8u);
         const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
         const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
         return make_float4(a.x, a.y, b.x, b.y);
@@ -306,19 +333,23 @@ __device__ __forceinline__ int plane_row(int P_s, int y, float gm, float h)
     return P_s * y + (__float_as_int(floor_magic<true>(gm, (float)y, h)) - kMagicBits);
 }
 
+// c: shared address of the plane's coefficients [gm_x, gm_y, h_y, h_x[VG]];
+// sb: shared address of the stage holding the plane's rows
 template <int DT, bool BILINEAR, int VG, bool CLAMP>
-__device__ __forceinline__ void blend_plane(float (&acc)[VG][4], const float* c, const unsigned char* sb,
-                                            const StagedGeom& G, const CompParams& p, int x, int y, int ty,
-                                            uint32_t maxi)
+__device__ __forceinline__ void blend_plane(float (&acc)[VG][4], uint32_t ca, uint32_t sb, const StagedGeom& G,
+                                            const CompParams& p, int x, int y, int ty, uint32_t maxi)
 {
     using TX_ = Texel<DT>;
+    float c[3 + VG];
+#pragma unroll
+    for (int e = 0; e < 3 + VG; ++e) c[e] = lds_f(ca + 4u * e);
     const float gmx = c[0];
     const float xf = (float)x;
     const int base_x = p.P_s * x + G.padl - kMagicBits;
     if (!BILINEAR) {
         const int iy = plane_row(p.P_s, y, c[1], c[2]);
         if (iy < 0 || iy >= p.H) return;
-        const char* row = reinterpret_cast<const char*>(sb + (size_t)ty * G.row_bytes);
+        const uint32_t row = sb + (uint32_t)(ty * G.row_bytes);
 #pragma unroll
         for (int jj = 0; jj < VG; ++jj) {
             const int ix = __float_as_int(floor_magic<CLAMP>(gmx, xf, c[3 + jj])) + base_x;
@@ -338,8 +369,8 @@ __device__ __forceinline__ void blend_plane(float (&acc)[VG][4], const float* c,
         const bool v0 = y0 >= 0 && y0 < p.H, v1 = y0 + 1 >= 0 && y0 + 1 < p.H;
         if (!v0 && !v1) return;
         const float w0 = v0 ? 1.0f - wy : 0.0f, w1 = v1 ? wy : 0.0f;
-        const char* r0 = reinterpret_cast<const char*>(sb + (size_t)(2 * ty) * G.row_bytes);
-        const char* r1 = r0 + G.row_bytes;
+        const uint32_t r0 = sb + (uint32_t)(2 * ty * G.row_bytes);
+        const uint32_t r1 = r0 + (uint32_t)G.row_bytes;
 #pragma unroll
         for (int jj = 0; jj < VG; ++jj) {
             float fx = __fmaf_rn(gmx, xf, c[3 + jj]);
@@ -373,7 +404,7 @@ __device__ __forceinline__ void blend_plane(float (&acc)[VG][4], const float* c,
 }
 
 template <int DT, bool BILINEAR, int VG>
-__global__ void __launch_bounds__(kStagedThreads, 2) k_composite_staged(CompParams p, StagedGeom G,
+__global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams p, StagedGeom G,
                                                                         const char* __restrict__ planes,
                                                                         const int32_t* __restrict__ count, CompWs w,
                                                                         float* __restrict__ out)
@@ -400,7 +431,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k_composite_staged(CompPara
     const int CW = VG + 3;
 
     // coefficients of this CTA's views: [gm_x, gm_y, h_y, h_x[VG]] per plane
-    for (int e = tid; e < p.N * VG; e += kStagedThreads) {
+    for (int e = tid; e < p.N * VG; e += kStagedBlock) {
         const int k = e / VG, jj = e % VG;
         const int j = min(j0 + jj, p.Vx - 1);
         const float* cx = w.cx + 3 * ((size_t)j * p.N + k);
@@ -430,7 +461,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k_composite_staged(CompPara
     }
     // zero pads of every staged row (the bulk copies never write them)
     const int nrows = G.BY * G.rows_per_y;
-    for (int e = tid; e < kStages * nrows; e += kStagedThreads) {
+    for (int e = tid; e < kStages * nrows; e += kStagedBlock) {
         unsigned char* row = stage_base + (size_t)(e / nrows) * G.stage_bytes + (size_t)(e % nrows) * G.row_bytes;
         for (int b = 0; b < G.padl * TB; b += 4) *reinterpret_cast<uint32_t*>(row + b) = 0u;
         for (size_t b = (size_t)(G.padl + p.W) * TB; b < G.row_bytes; b += 4)
@@ -478,17 +509,33 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k_composite_staged(CompPara
         }
     };
 
-    if (tid == 0)
-        for (int q = 0; q < min(P, kStages); ++q) produce(q);
+    if (tid >= kStagedThreads) {
+        // producer warp: one lane streams the planes through the stage ring,
+        // refilling a stage as soon as every consumer warp has released it
+        if (tid == kStagedThreads) {
+            for (int q = 0; q < P; ++q) {
+                const int s = q % kStages;
+                if (q >= kStages &&
+                    !mbar_wait_bounded(smem_addr(&empty[s]), (uint32_t)(((q / kStages) - 1) & 1))) {
+                    atomicExch(w.err, 1);
+                    break;
+                }
+                produce(q);
+            }
+        }
+        return;
+    }
 
     float acc[VG][4];
 #pragma unroll
     for (int jj = 0; jj < VG; ++jj) acc[jj][0] = acc[jj][1] = acc[jj][2] = 0.f, acc[jj][3] = 1.f;
+    const uint32_t stage_a = smem_addr(stage_base), coef_a = smem_addr(coef);
+    const uint32_t plist_a = smem_addr(plist), pwide_a = smem_addr(pwide);
     const bool live = ty < G.BY && x < p.Nx && y < p.Ny;   // threads past BY rows idle
     const uint32_t maxi = (uint32_t)(G.padl + p.W);       // first right-pad texel
     bool ok = true;
 
-    for (int q = 0; q < P && ok; ++q) {
+    for (int q = 0; q < P; ++q) {
         const int s = q % kStages;
         const uint32_t parity = (uint32_t)((q / kStages) & 1);
         if (!mbar_wait_bounded(smem_addr(&full[s]), parity)) {
@@ -497,24 +544,15 @@ __global__ void __launch_bounds__(kStagedThreads, 2) k_composite_staged(CompPara
             break;
         }
         if (live) {
-            const float* c = coef + (size_t)plist[q] * CW;
-            const unsigned char* sb = stage_base + (size_t)s * G.stage_bytes;
-            if (pwide[q])
-                blend_plane<DT, BILINEAR, VG, true>(acc, c, sb, G, p, x, y, ty, maxi);
+            const uint32_t ca = coef_a + 4u * (uint32_t)(lds_i(plist_a + 4u * q) * CW);
+            const uint32_t sb = stage_a + (uint32_t)(s * G.stage_bytes);
+            if (lds_i(pwide_a + 4u * q))
+                blend_plane<DT, BILINEAR, VG, true>(acc, ca, sb, G, p, x, y, ty, maxi);
             else
-                blend_plane<DT, BILINEAR, VG, false>(acc, c, sb, G, p, x, y, ty, maxi);
+                blend_plane<DT, BILINEAR, VG, false>(acc, ca, sb, G, p, x, y, ty, maxi);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
-        if (tid == 0 && q + kStages < P) {
-            // every warp has released stage s: refill it
-            if (!mbar_wait_bounded(smem_addr(&empty[s]), parity)) {
-                atomicExch(w.err, 1);
-                ok = false;
-                break;
-            }
-            produce(q + kStages);
-        }
     }
     if (!ok || !live) return;
 #pragma unroll
@@ -553,7 +591,7 @@ bool launch_staged_vg(const CompParams& p, const void* planes, const int32_t* co
         return false;
     const dim3 grid((unsigned)(G.groups_x * p.Vy), (unsigned)((p.Ny + G.BY - 1) / G.BY),
                     (unsigned)((p.Nx + G.TX - 1) / G.TX));
-    kern<<<grid, kStagedThreads, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, out);
+    kern<<<grid, kStagedBlock, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, out);
     note_launches(1);
     return true;
 }
@@ -562,7 +600,8 @@ template <int DT, bool BILINEAR>
 bool launch_staged(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
                    cudaStream_t s)
 {
-    if (p.Vx >= 9) return launch_staged_vg<DT, BILINEAR, 9>(p, planes, count, ws, out, s);
+    // bilinear keeps 5 views per thread (9 would spill at this register budget)
+    if (p.Vx >= 9 && !BILINEAR) return launch_staged_vg<DT, BILINEAR, 9>(p, planes, count, ws, out, s);
     if (p.Vx >= 5) return launch_staged_vg<DT, BILINEAR, 5>(p, planes, count, ws, out, s);
     return launch_staged_vg<DT, BILINEAR, 3>(p, planes, count, ws, out, s);
 }

@@ -47,75 +47,98 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// One CTA per (16x16 tile, chunk); warp w owns pixel rows 2w, 2w+1 of the
-// tile. Each batch of up to 256 list entries is staged in shared memory
-// with the conic pre-scaled so that alpha = min(0.99, o 2^(A dx^2 + B dx dy + C dy^2)),
-// A = -log2(e)/2 a, B = -log2(e) b, C = -log2(e)/2 c. Every warp first
-// ballots which entries touch its 2 x 16 strip and then visits only those,
-// in list order, so per-pixel blending order is unchanged.
-template <int DT>
-__global__ void __launch_bounds__(kTilePix) k_raster_gauss(BuildWs w, RasterParams p, const uint32_t* __restrict__ tvals,
-                                                           const float* __restrict__ rgb, const int4* __restrict__ rect,
-                                                           void* planes)
+// One CTA per (16x16 tile, chunk) with 256 / PPT threads: thread t shades
+// the PPT pixels of column t % 16 in rows PPT (t / 16) ... PPT (t / 16) + PPT - 1,
+// so warp w owns the 2 PPT x 16 strip of rows 2 PPT w .. 2 PPT w + 2 PPT - 1.
+// Each batch of list entries is staged in shared memory as three 16-byte
+// words {mean x, mean y, A, B}, {C, o, x0 | y0 << 16, (x1 - x0) | (y1 - y0) << 16},
+// {r, g, b, -}, with the conic pre-scaled so that
+//   alpha = min(0.99, o 2^(A dx^2 + B dx dy + C dy^2)),
+//   A = -log2(e)/2 a, B = -log2(e) b, C = -log2(e)/2 c.
+// Every warp ballots which entries touch its strip and visits only those, in
+// list order, so the blending order of every pixel is unchanged.
+template <int DT, int PPT>
+__global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, RasterParams p,
+                                                                 const uint32_t* __restrict__ tvals,
+                                                                 const float* __restrict__ rgb,
+                                                                 const int4* __restrict__ rect, void* planes)
 {
+    constexpr int NT = kTilePix / PPT;
     constexpr float kL2E = 1.4426950408889634f;
-    __shared__ float2 s_mean[kTilePix];
-    __shared__ float4 s_con[kTilePix];
-    __shared__ float4 s_rgb[kTilePix];
-    __shared__ int4 s_rect[kTilePix];   // x0, y0, x1 - x0, y1 - y0
+    __shared__ float4 s_e0[NT];
+    __shared__ float4 s_e1[NT];
+    __shared__ float4 s_rgb[NT];
     const int t = blockIdx.x, k = blockIdx.y;
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py = ty * kTile + (threadIdx.x / kTile);
-    const int sx0 = tx * kTile, sx1 = sx0 + kTile - 1;            // warp strip bounds
-    const int sy0 = ty * kTile + 2 * warp, sy1 = sy0 + 1;
+    const int py0 = ty * kTile + (threadIdx.x / kTile) * PPT;
+    const int sx0 = tx * kTile, sx1 = sx0 + kTile - 1;                // warp strip bounds
+    const int sy0 = ty * kTile + 2 * PPT * warp, sy1 = sy0 + 2 * PPT - 1;
     const int2 sg = w.seg[(size_t)t * p.N + k];
-    const float fpx = (float)px, fpy = (float)py;
-    float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
-    for (int base = sg.x; base < sg.y; base += kTilePix) {
+    const float fpx = (float)px;
+    float C[PPT][3], T[PPT];
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) C[r][0] = C[r][1] = C[r][2] = 0.f, T[r] = 1.f;
+    for (int base = sg.x; base < sg.y; base += NT) {
         const int i = base + threadIdx.x;
         if (i < sg.y) {
             const uint32_t g = tvals[i];
-            s_mean[threadIdx.x] = w.mean2d[g];
+            const float2 m = w.mean2d[g];
             const float4 c = w.conic_o[g];
-            s_con[threadIdx.x] = make_float4(-0.5f * kL2E * c.x, -kL2E * c.y, -0.5f * kL2E * c.z, c.w);
-            s_rgb[threadIdx.x] = make_float4(rgb[3 * (size_t)g], rgb[3 * (size_t)g + 1], rgb[3 * (size_t)g + 2], 0.f);
             const int4 r = rect[g];
-            s_rect[threadIdx.x] = make_int4(r.x, r.y, r.z - r.x, r.w - r.y);
+            s_e0[threadIdx.x] = make_float4(m.x, m.y, -0.5f * kL2E * c.x, -kL2E * c.y);
+            s_e1[threadIdx.x] = make_float4(-0.5f * kL2E * c.z, c.w, __int_as_float((r.x & 0xffff) | (r.y << 16)),
+                                            __int_as_float(((r.z - r.x) & 0xffff) | ((r.w - r.y) << 16)));
+            s_rgb[threadIdx.x] = make_float4(rgb[3 * (size_t)g], rgb[3 * (size_t)g + 1], rgb[3 * (size_t)g + 2], 0.f);
         }
         __syncthreads();
-        const int cnt = min(kTilePix, sg.y - base);
+        const int cnt = min(NT, sg.y - base);
         for (int m0 = 0; m0 < cnt; m0 += 32) {
             const int jl = m0 + lane;
             bool hit = false;
             if (jl < cnt) {
-                const int4 r = s_rect[jl];
-                hit = r.x <= sx1 && r.x + r.z >= sx0 && r.y <= sy1 && r.y + r.w >= sy0;
+                const float4 e1 = s_e1[jl];
+                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
+                const int rx0 = xy & 0xffff, ry0 = xy >> 16;
+                hit = rx0 <= sx1 && rx0 + (wh & 0xffff) >= sx0 && ry0 <= sy1 && ry0 + (wh >> 16) >= sy0;
             }
             uint32_t mask = __ballot_sync(0xffffffffu, hit);
             while (mask) {
                 const int j = m0 + __ffs(mask) - 1;
                 mask &= mask - 1;
-                const int4 rc = s_rect[j];
-                if ((uint32_t)(px - rc.x) <= (uint32_t)rc.z && (uint32_t)(py - rc.y) <= (uint32_t)rc.w) {
-                    const float2 m = s_mean[j];
-                    const float4 c = s_con[j];
-                    const float dx = fpx - m.x, dy = fpy - m.y;
-                    const float pw = fmaf(dx, fmaf(c.x, dx, c.y * dy), c.z * dy * dy);
-                    const float al = fminf(0.99f, c.w * ex2_approx(pw));
-                    const float4 col = s_rgb[j];
-                    const float ta = T * al;
-                    C0 = fmaf(ta, col.x, C0);
-                    C1 = fmaf(ta, col.y, C1);
-                    C2 = fmaf(ta, col.z, C2);
-                    T = fmaf(-T, al, T);
+                const float4 e1 = s_e1[j];
+                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
+                if ((uint32_t)(px - (xy & 0xffff)) > (uint32_t)(wh & 0xffff)) continue;
+                const float4 e0 = s_e0[j];
+                const float4 col = s_rgb[j];
+                const float dx = fpx - e0.x;
+                const float adx = e0.z * dx;
+                const int ry0 = xy >> 16, rh = wh >> 16;
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) {
+                    if ((uint32_t)(py0 + r - ry0) <= (uint32_t)rh) {
+                        const float dy = (float)(py0 + r) - e0.y;
+                        const float pw = fmaf(dx, fmaf(e0.w, dy, adx), e1.x * dy * dy);
+                        const float al = fminf(0.99f, e1.y * ex2_approx(pw));
+                        const float ta = T[r] * al;
+                        C[r][0] = fmaf(ta, col.x, C[r][0]);
+                        C[r][1] = fmaf(ta, col.y, C[r][1]);
+                        C[r][2] = fmaf(ta, col.z, C[r][2]);
+                        T[r] = fmaf(-T[r], al, T[r]);
+                    }
                 }
             }
         }
         __syncthreads();
     }
-    if (px < p.W && py < p.H) store_texel<DT>(planes, ((size_t)k * p.H + py) * p.W + px, C0, C1, C2, 1.0f - T);
+    if (px < p.W) {
+#pragma unroll
+        for (int r = 0; r < PPT; ++r)
+            if (py0 + r < p.H)
+                store_texel<DT>(planes, ((size_t)k * p.H + py0 + r) * p.W + px, C[r][0], C[r][1], C[r][2],
+                                1.0f - T[r]);
+    }
 }
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
@@ -228,11 +251,14 @@ void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uin
 {
     const dim3 grid((unsigned)(p.tiles_x * p.tiles_y), (unsigned)p.N);
     const int4* r4 = reinterpret_cast<const int4*>(rect);
+    constexpr int kPPT = 2;   // pixels per thread
+    constexpr int kThreads = kTilePix / kPPT;
     switch (p.dtype) {
-    case LF_F32: k_raster_gauss<LF_F32><<<grid, kTilePix, 0, s>>>(ws, p, tvals, rgb, r4, planes); note_launches(1); break;
-    case LF_F16: k_raster_gauss<LF_F16><<<grid, kTilePix, 0, s>>>(ws, p, tvals, rgb, r4, planes); note_launches(1); break;
-    default: k_raster_gauss<LF_BF16><<<grid, kTilePix, 0, s>>>(ws, p, tvals, rgb, r4, planes); note_launches(1); break;
+    case LF_F32: k_raster_gauss<LF_F32, kPPT><<<grid, kThreads, 0, s>>>(ws, p, tvals, rgb, r4, planes); break;
+    case LF_F16: k_raster_gauss<LF_F16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, tvals, rgb, r4, planes); break;
+    default: k_raster_gauss<LF_BF16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, tvals, rgb, r4, planes); break;
     }
+    note_launches(1);
 }
 
 void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32_t* tvals, const lf_voxels& v,
