@@ -88,8 +88,9 @@ size_t build_ws_layout(int64_t n, int32_t N, int32_t W, int32_t H, int64_t cap, 
 {
     char* base = static_cast<char*>(basev);
     const long long tiles = (long long)((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
-    const long long nmax = n > cap ? n : cap;
-    const long long nb = (nmax + kSortTile - 1) / kSortTile + 1;
+    const long long S = tiles * N;                                  // (tile, chunk) lists
+    const long long nb = (n + kSortBlockKeys - 1) / kSortBlockKeys + 1;
+    const long long nbs = (S + kScanBlock - 1) / kScanBlock + 1;
     const size_t nn = (size_t)(n > 0 ? n : 1);
     const size_t cc = (size_t)(cap > 0 ? cap : 1);
     size_t off = 0;
@@ -101,17 +102,24 @@ size_t build_ws_layout(int64_t n, int32_t N, int32_t W, int32_t H, int64_t cap, 
     w.valB = carve<uint32_t>(base, off, nn);
     w.mean2d = carve<float2>(base, off, nn);
     w.conic_o = carve<float4>(base, off, nn);
-    w.hist = carve<uint32_t>(base, off, (size_t)kRadix * nb + 1);
-    w.bsum = carve<uint32_t>(base, off, (size_t)nb + 1);
-    w.dtot = carve<uint32_t>(base, off, (size_t)kRadix);
+    w.r_geo = carve<float4>(base, off, nn);
+    w.r_con = carve<float4>(base, off, nn);
+    w.r_rect = carve<int4>(base, off, nn);
+    w.r_rgb = carve<float4>(base, off, nn);
+    w.r_den = carve<float4>(base, off, 2 * nn);
+    w.r_chunk = carve<int32_t>(base, off, nn);
+    w.hist = carve<uint32_t>(base, off, (size_t)kSortDigits * nb);
+    w.dtot = carve<uint32_t>(base, off, (size_t)kSortDigits);
+    w.bsum = carve<uint32_t>(base, off, (size_t)nbs);
     w.chunk_start = carve<int32_t>(base, off, (size_t)N + 1);
-    w.dkeyA = carve<uint32_t>(base, off, cc);
-    w.dkeyB = carve<uint32_t>(base, off, cc);
-    w.dvalA = carve<uint32_t>(base, off, cc);
-    w.dvalB = carve<uint32_t>(base, off, cc);
-    w.seg = carve<int2>(base, off, (size_t)tiles * N);
+    w.segcnt = carve<uint32_t>(base, off, (size_t)S);
+    w.seg = carve<int2>(base, off, (size_t)S);
+    w.biglist = carve<uint32_t>(base, off, (size_t)S);
+    w.entA = carve<uint32_t>(base, off, cc);
+    w.entB = carve<uint32_t>(base, off, cc);
     w.bytes = align_up(off, 256);
-    w.nb_max = nb;
+    w.nb_sort = nb;
+    w.nb_scan = nbs;
     if (o) *o = w;
     return w.bytes;
 }
@@ -135,17 +143,6 @@ static std::mutex g_ws_mu;
 static std::map<const void*, cudaStream_t> g_ws_stream;
 
 static int64_t default_cap(int64_t n) { return 8 * n + (1ll << 20); }
-
-static int tile_bits_for(long long tiles)
-{
-    int b = 1;
-    while ((1ll << b) < tiles) ++b;
-    return b;
-}
-
-// number of radix passes of the tile sort (its result is in the A buffers
-// after an even count, in the B buffers after an odd one)
-static int tile_sort_passes(long long tiles) { return (tile_bits_for(tiles) + kRadixBits - 1) / kRadixBits; }
 
 static lf_status check_ref(const lf_ref_camera* r)
 {
@@ -271,8 +268,6 @@ static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, in
     launch_init_header(h, w.hdr, stream);
     if ((st = check_launch("header init")) != LF_OK) return st;
     const long long n_tiles = (long long)h.tiles_x * h.tiles_y;
-    if (cudaMemsetAsync(w.seg, 0, sizeof(int2) * (size_t)n_tiles * N, stream) != cudaSuccess)
-        return check_launch("segment reset");
 
     ProjParams pp;
     fill_proj_params(ref, n, &pp);
@@ -290,36 +285,26 @@ static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, in
     bp.N = N;
     bp.binning = binning;
     bp.D_forward = ref->D_forward;
+    const float* rgb = kind == 0 ? static_cast<const lf_gaussians*>(raster_arg)->rgb
+                                 : static_cast<const lf_voxels*>(raster_arg)->rgb;
+    const float* dens8 = kind == 0 ? nullptr : static_cast<const lf_voxels*>(raster_arg)->density8;
     trace_begin("bin", stream);
-    launch_bin(w, bp, n, out->chunk, out->d, out->count, stream);
+    launch_bin(w, bp, n, out->chunk, out->d, out->count, out->rect, rgb, dens8, kind, stream);
     trace_end(stream);
     if ((st = check_launch("bin")) != LF_OK) return st;
 
-    trace_begin("duplicate", stream);
-    launch_duplicate(w, n, out->rect, h.tiles_x, stream);
+    trace_begin("tile_lists", stream);
+    launch_tile_lists(w, n, cap, N, h.tiles_x, (int)n_tiles, stream);
     trace_end(stream);
-    if ((st = check_launch("duplicate")) != LF_OK) return st;
-
-    uint32_t* tkeys = nullptr;
-    uint32_t* tvals = nullptr;
-    trace_begin("tile_sort", stream);
-    sort_tile_keys(w, cap, tile_bits_for(n_tiles), stream, &tkeys, &tvals);
-    trace_end(stream);
-    if ((st = check_launch("tile sort")) != LF_OK) return st;
-
-    trace_begin("ranges", stream);
-    launch_ranges(w, cap, tkeys, tvals, out->chunk, N, stream);
-    trace_end(stream);
-    if ((st = check_launch("ranges")) != LF_OK) return st;
+    if ((st = check_launch("tile lists")) != LF_OK) return st;
 
     RasterParams rp;
     fill_raster_params(ref, N, out->dtype, &rp);
     trace_begin(kind == 0 ? "raster_gaussians" : "raster_voxels", stream);
     if (kind == 0)
-        launch_raster_gaussians(w, rp, tvals, static_cast<const lf_gaussians*>(raster_arg)->rgb, out->rect,
-                                out->rgba, stream);
+        launch_raster_gaussians(w, rp, out->rgba, stream);
     else
-        launch_raster_voxels(w, rp, tvals, *static_cast<const lf_voxels*>(raster_arg), out->rect, out->rgba, stream);
+        launch_raster_voxels(w, rp, out->rgba, stream);
     trace_end(stream);
     return check_launch("rasterise");
 }
@@ -490,11 +475,22 @@ lf_status lf_mpi_tile_lists(const void* ws, int32_t* order, int64_t n, int32_t* 
             return check_launch("order read");
     }
     if (tile_prims) {
+        // the lists hold ranks (sorted once the planes are rasterised); map
+        // them to primitive indices through the depth order
         if (cap < needed) return fail(LF_ERR_INVALID_ARG, "tile list buffer too small");
-        if (needed > 0 &&
-            cudaMemcpy(tile_prims, tile_sort_passes((long long)h.tiles_x * h.tiles_y) % 2 ? w.dvalB : w.dvalA,
-                       sizeof(uint32_t) * (size_t)needed, cudaMemcpyDeviceToHost) != cudaSuccess)
-            return check_launch("tile list read");
+        if (needed > 0) {
+            std::vector<uint32_t> rank_prim((size_t)(M > 0 ? M : 1));
+            if (cudaMemcpy(tile_prims, w.entA, sizeof(uint32_t) * (size_t)needed, cudaMemcpyDeviceToHost) !=
+                    cudaSuccess ||
+                cudaMemcpy(rank_prim.data(), w.valA, sizeof(uint32_t) * (size_t)M, cudaMemcpyDeviceToHost) !=
+                    cudaSuccess)
+                return check_launch("tile list read");
+            for (int64_t i = 0; i < needed; ++i) {
+                const uint32_t rk = (uint32_t)tile_prims[i];
+                if (rk >= (uint64_t)M) return fail(LF_ERR_CUDA, "corrupt tile list entry");
+                tile_prims[i] = (int32_t)rank_prim[rk];
+            }
+        }
     }
     if (seg) {
         const size_t ns = (size_t)h.tiles_x * h.tiles_y * h.N;

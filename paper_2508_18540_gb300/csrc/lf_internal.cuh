@@ -17,11 +17,10 @@ namespace lf {
 
 constexpr int kTile = 16;                 // splat tile edge (pixels)
 constexpr int kTilePix = kTile * kTile;   // threads per rasterisation CTA
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 4;             // keys per thread per radix block
-constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortBlockKeys = 2048;      // keys per depth-sort block
+constexpr int kSortDigits = 2048;         // 11-bit radix digits
+constexpr int kSegSortCap = 2048;         // longest (tile, chunk) list sorted inside a raster CTA
+constexpr int kScanBlock = 1024;          // elements per block of the segment scan
 constexpr uint64_t kInvalidKey = ~0ull;
 
 // ---- launch counting and stage tracing ------------------------------------
@@ -43,7 +42,7 @@ struct WsHeader {
     unsigned long long kmax;
     unsigned long long M;         // culled-in primitives
     unsigned long long total_dups;
-    unsigned long long tile_n;    // pairs to sort (0 after an overflow)
+    unsigned long long n_big;     // (tile, chunk) lists longer than kSegSortCap
     int overflow;                 // 1 if total_dups > dup_capacity
     int kind;                     // 0 gaussians, 1 voxels
     long long n;
@@ -55,23 +54,30 @@ struct WsHeader {
 // Carved build workspace (all device pointers).
 struct BuildWs {
     WsHeader* hdr;
-    unsigned long long* keyA;     // [n] depth keys
+    unsigned long long* keyA;     // [n] depth keys (relative to the smallest after sorting)
     unsigned long long* keyB;
-    uint32_t* valA;               // [n] primitive ids
+    uint32_t* valA;               // [n] primitive ids (rank order after sorting)
     uint32_t* valB;
-    float2* mean2d;               // [n]
-    float4* conic_o;              // [n] (a, b, c, opacity) / voxel (lo_rel xyz, side)
-    uint32_t* hist;               // [kRadix * nb_max] radix histograms
-    uint32_t* bsum;               // [nb_max + 1] block sums / offsets
-    uint32_t* dtot;               // [kRadix] per-digit totals of a radix pass
+    float2* mean2d;               // [n] per primitive (Gaussians)
+    float4* conic_o;              // [n] per primitive: (a, b, c, opacity) / voxel (lo_rel xyz, side)
+    // copies in rank order, made while binning
+    float4* r_geo;                // [n] (mean x, mean y, -) or voxel (lo_rel xyz, side)
+    float4* r_con;                // [n] Gaussian (a, b, c, opacity)
+    int4* r_rect;                 // [n] footprint
+    float4* r_rgb;                // [n] colour
+    float4* r_den;                // [2 n] voxel corner densities
+    int32_t* r_chunk;             // [n]
+    uint32_t* hist;               // [kSortDigits * nb] radix histograms
+    uint32_t* dtot;               // [kSortDigits] per-digit totals of a radix pass
+    uint32_t* bsum;               // [nbs] block sums of the segment scan
     int32_t* chunk_start;         // [N + 1]
-    uint32_t* dkeyA;              // [cap] tile ids
-    uint32_t* dkeyB;
-    uint32_t* dvalA;              // [cap] primitive ids
-    uint32_t* dvalB;
-    int2* seg;                    // [tiles * N] (start, end)
+    uint32_t* segcnt;             // [tiles * N] list lengths (then countdown cursors)
+    int2* seg;                    // [tiles * N] (start, end) of every (tile, chunk) list
+    uint32_t* biglist;            // [tiles * N] lists longer than kSegSortCap
+    uint32_t* entA;               // [cap] ranks of the list entries
+    uint32_t* entB;               // [cap] scratch of the long-list sort
     size_t bytes;
-    long long nb_max;
+    long long nb_sort, nb_scan;
 };
 
 size_t build_ws_layout(int64_t n, int32_t N, int32_t W, int32_t H, int64_t cap, void* base, BuildWs* out);
@@ -114,25 +120,18 @@ void launch_project_gaussians(const lf_gaussians& g, const ProjParams& p, const 
 void launch_project_voxels(const lf_voxels& v, const ProjParams& p, const BuildWs& ws, int32_t* rect,
                            int32_t* chunk, cudaStream_t s);
 
-// LSD radix sort of (key, value) pairs, stable. 64-bit depth keys: the first
-// pass drops kInvalidKey entries (culled primitives); the count after it is
-// hdr->M. Result ends in (keyA, valA).
+// Stable LSD radix sort of the culled-in primitives by (depth, index); the
+// culled-in count ends in hdr->M and the result in (keyA, valA).
 void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s);
-// Stable sort of (tile id, primitive id) pairs by tile id (tile_bits bits);
-// count in hdr->total_dups. Result ends in (dkeyA, dvalA).
-void sort_tile_keys(const BuildWs& ws, long long cap, int tile_bits, cudaStream_t s, uint32_t** keys_out,
-                    uint32_t** vals_out);
 
 void launch_bin(const BuildWs& ws, const BinParams& p, long long n, int32_t* chunk, double* d, int32_t* count,
-                cudaStream_t s);
-void launch_duplicate(const BuildWs& ws, long long n, const int32_t* rect, int tiles_x, cudaStream_t s);
-void launch_ranges(const BuildWs& ws, long long cap, const uint32_t* tkeys, const uint32_t* tvals,
-                   const int32_t* chunk, int N, cudaStream_t s);
+                const int32_t* rect, const float* rgb, const float* dens8, int kind, cudaStream_t s);
+// (tile, chunk) lists: count, scan, emit (unordered), sort long lists.
+void launch_tile_lists(const BuildWs& ws, long long n, long long cap, int N, int tiles_x, int n_tiles,
+                       cudaStream_t s);
 
-void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uint32_t* tvals, const float* rgb,
-                             const int32_t* rect, void* planes, cudaStream_t s);
-void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32_t* tvals, const lf_voxels& v,
-                          const int32_t* rect, void* planes, cudaStream_t s);
+void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, void* planes, cudaStream_t s);
+void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, void* planes, cudaStream_t s);
 
 // ---- composite ----------------------------------------------------------
 struct CompWs {

@@ -1,9 +1,11 @@
 // lf_raster.cu -- 3D-tiled rasterisation of every chunk into its sweeping
 // plane (Algorithm 1 lines 4-5, "Parallel for all k: Rasterize(H, P'_k)").
 //
-// One CTA per (16x16 tile, chunk). The CTA's (tile, chunk) list is already in
-// (depth, index) order; it is staged through shared memory in batches of 256
-// primitives and every thread blends its pixel front to back:
+// One CTA per (16x16 tile, chunk). The CTA first puts its (tile, chunk) list
+// in rank order -- depth order -- (lists up to kSegSortCap are sorted here in
+// shared memory and written back; longer ones were sorted beforehand), then
+// stages the listed primitives through shared memory in batches and every
+// thread blends its pixels front to back:
 //   Gaussians (Sec. 4.4, 3DGS model): alpha = min(0.99, o exp(-q/2)),
 //     q = d^T Sigma_2^{-1} d inside the primitive's footprint rectangle;
 //   voxels (Sec. 4.5, SVR model): alpha = 1 - exp(-integral of the trilinear
@@ -19,6 +21,8 @@
 namespace lf {
 
 namespace {
+
+constexpr int kCountSortMax = 256;   // lists up to this length: rank-counting sort
 
 template <int DT>
 __device__ __forceinline__ void store_texel(void* planes, size_t idx, float r, float g, float b, float a)
@@ -40,6 +44,57 @@ __device__ __forceinline__ void store_texel(void* planes, size_t idx, float r, f
     }
 }
 
+// Puts the CTA's list [sg.x, sg.y) of entA in rank order in s_rank and back in
+// entA. Returns false for a list longer than kSegSortCap (already sorted in
+// global memory by the long-list pass); the caller then reads entA directly.
+// Every thread of the CTA must call it (it synchronises).
+template <int NT>
+__device__ __forceinline__ bool sorted_list(const BuildWs& w, int2 sg, uint32_t* s_rank, uint32_t* s_tmp)
+{
+    const int L = sg.y - sg.x;
+    if (L > kSegSortCap) return false;
+    for (int i = threadIdx.x; i < L; i += NT) s_rank[i] = w.entA[sg.x + i];
+    __syncthreads();
+    if (L <= 1) return true;
+    if (L <= kCountSortMax) {
+        // position of every rank = number of smaller ranks (ranks are distinct)
+        for (int i = threadIdx.x; i < L; i += NT) {
+            const uint32_t v = s_rank[i];
+            int c = 0;
+            for (int j = 0; j < L; ++j) c += s_rank[j] < v;
+            s_tmp[c] = v;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < L; i += NT) {
+            s_rank[i] = s_tmp[i];
+            w.entA[sg.x + i] = s_tmp[i];
+        }
+        __syncthreads();
+        return true;
+    }
+    int P = 1;
+    while (P < L) P <<= 1;
+    for (int i = L + threadIdx.x; i < P; i += NT) s_rank[i] = 0xffffffffu;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += NT) {
+                const int ij = i ^ j;
+                if (ij > i) {
+                    const uint32_t a = s_rank[i], b = s_rank[ij];
+                    if ((a > b) == ((i & k) == 0)) {
+                        s_rank[i] = b;
+                        s_rank[ij] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < L; i += NT) w.entA[sg.x + i] = s_rank[i];
+    return true;
+}
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
@@ -47,27 +102,25 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// One CTA per (16x16 tile, chunk) with 256 / PPT threads: thread t shades
-// the PPT pixels of column t % 16 in rows PPT (t / 16) ... PPT (t / 16) + PPT - 1,
-// so warp w owns the 2 PPT x 16 strip of rows 2 PPT w .. 2 PPT w + 2 PPT - 1.
-// Each batch of list entries is staged in shared memory as three 16-byte
-// words {mean x, mean y, A, B}, {C, o, x0 | y0 << 16, (x1 - x0) | (y1 - y0) << 16},
-// {r, g, b, -}, with the conic pre-scaled so that
-//   alpha = min(0.99, o 2^(A dx^2 + B dx dy + C dy^2)),
-//   A = -log2(e)/2 a, B = -log2(e) b, C = -log2(e)/2 c.
-// Every warp ballots which entries touch its strip and visits only those, in
-// list order, so the blending order of every pixel is unchanged.
+// Gaussians: 256 / PPT threads; thread t shades the PPT pixels of column
+// t % 16 in rows PPT (t / 16) ... PPT (t / 16) + PPT - 1, so warp w owns the
+// 2 PPT x 16 strip of rows 2 PPT w ... Each batch of list entries is staged
+// as three 16-byte words {mean x, mean y, A, B}, {C, o, x0 | y0 << 16,
+// (x1 - x0) | (y1 - y0) << 16}, {r, g, b, -}, with the conic pre-scaled so
+// that alpha = min(0.99, o 2^(A dx^2 + B dx dy + C dy^2)),
+// A = -log2(e)/2 a, B = -log2(e) b, C = -log2(e)/2 c. Every warp ballots which
+// entries touch its strip and visits only those, in list order, so the
+// blending order of every pixel is unchanged.
 template <int DT, int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, RasterParams p,
-                                                                 const uint32_t* __restrict__ tvals,
-                                                                 const float* __restrict__ rgb,
-                                                                 const int4* __restrict__ rect, void* planes)
+__global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, RasterParams p, void* planes)
 {
     constexpr int NT = kTilePix / PPT;
     constexpr float kL2E = 1.4426950408889634f;
     __shared__ float4 s_e0[NT];
     __shared__ float4 s_e1[NT];
     __shared__ float4 s_rgb[NT];
+    __shared__ uint32_t s_rank[kSegSortCap];
+    __shared__ uint32_t s_tmp[kCountSortMax];
     const int t = blockIdx.x, k = blockIdx.y;
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -76,24 +129,26 @@ __global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, Rast
     const int sx0 = tx * kTile, sx1 = sx0 + kTile - 1;                // warp strip bounds
     const int sy0 = ty * kTile + 2 * PPT * warp, sy1 = sy0 + 2 * PPT - 1;
     const int2 sg = w.seg[(size_t)t * p.N + k];
+    const int L = sg.y - sg.x;
+    const bool local = sorted_list<NT>(w, sg, s_rank, s_tmp);
     const float fpx = (float)px;
     float C[PPT][3], T[PPT];
 #pragma unroll
     for (int r = 0; r < PPT; ++r) C[r][0] = C[r][1] = C[r][2] = 0.f, T[r] = 1.f;
-    for (int base = sg.x; base < sg.y; base += NT) {
+    for (int base = 0; base < L; base += NT) {
         const int i = base + threadIdx.x;
-        if (i < sg.y) {
-            const uint32_t g = tvals[i];
-            const float2 m = w.mean2d[g];
-            const float4 c = w.conic_o[g];
-            const int4 r = rect[g];
-            s_e0[threadIdx.x] = make_float4(m.x, m.y, -0.5f * kL2E * c.x, -kL2E * c.y);
+        if (i < L) {
+            const uint32_t rk = local ? s_rank[i] : w.entA[sg.x + i];
+            const float4 geo = w.r_geo[rk];
+            const float4 c = w.r_con[rk];
+            const int4 r = w.r_rect[rk];
+            s_e0[threadIdx.x] = make_float4(geo.x, geo.y, -0.5f * kL2E * c.x, -kL2E * c.y);
             s_e1[threadIdx.x] = make_float4(-0.5f * kL2E * c.z, c.w, __int_as_float((r.x & 0xffff) | (r.y << 16)),
                                             __int_as_float(((r.z - r.x) & 0xffff) | ((r.w - r.y) << 16)));
-            s_rgb[threadIdx.x] = make_float4(rgb[3 * (size_t)g], rgb[3 * (size_t)g + 1], rgb[3 * (size_t)g + 2], 0.f);
+            s_rgb[threadIdx.x] = w.r_rgb[rk];
         }
         __syncthreads();
-        const int cnt = min(NT, sg.y - base);
+        const int cnt = min(NT, L - base);
         for (int m0 = 0; m0 < cnt; m0 += 32) {
             const int jl = m0 + lane;
             bool hit = false;
@@ -152,20 +207,26 @@ __device__ __forceinline__ float trilinear(const float* rho, float fx, float fy,
 
 __device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.0f), 1.0f); }
 
+// Voxels: one thread per pixel (256 threads); cube corner relative to the
+// reference centre and side from the projection pass, densities and colour
+// in rank order.
 template <int DT>
-__global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterParams p, const uint32_t* __restrict__ tvals,
-                                                           const float* __restrict__ dens8, const float* __restrict__ rgb,
-                                                           const int4* __restrict__ rect, void* planes)
+__global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterParams p, void* planes)
 {
-    __shared__ float4 s_box[kTilePix];
-    __shared__ float s_den[kTilePix * 8];
-    __shared__ float4 s_rgb[kTilePix];
-    __shared__ int4 s_rect[kTilePix];
+    constexpr int NT = kTilePix;
+    __shared__ float4 s_box[NT];
+    __shared__ float s_den[NT * 8];
+    __shared__ float4 s_rgb[NT];
+    __shared__ int4 s_rect[NT];
+    __shared__ uint32_t s_rank[kSegSortCap];
+    __shared__ uint32_t s_tmp[kCountSortMax];
     const int t = blockIdx.x, k = blockIdx.y;
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
     const int py = ty * kTile + (threadIdx.x / kTile);
     const int2 sg = w.seg[(size_t)t * p.N + k];
+    const int L = sg.y - sg.x;
+    const bool local = sorted_list<NT>(w, sg, s_rank, s_tmp);
 
     // world-frame direction of the reference ray through this pixel centre
     const float dcx = ((float)px - p.cx) / p.fx, dcy = ((float)py - p.cy) / p.fy;
@@ -181,21 +242,20 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
     }
 
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
-    for (int base = sg.x; base < sg.y; base += kTilePix) {
+    for (int base = 0; base < L; base += NT) {
         const int i = base + threadIdx.x;
-        if (i < sg.y) {
-            const uint32_t g = tvals[i];
-            s_box[threadIdx.x] = w.conic_o[g];
-            const float4* d4 = reinterpret_cast<const float4*>(dens8 + 8 * (size_t)g);
-            const float4 da = d4[0], db = d4[1];
+        if (i < L) {
+            const uint32_t rk = local ? s_rank[i] : w.entA[sg.x + i];
+            s_box[threadIdx.x] = w.r_geo[rk];
+            const float4 da = w.r_den[2 * (size_t)rk], db = w.r_den[2 * (size_t)rk + 1];
             float* sd = s_den + 8 * threadIdx.x;
             sd[0] = da.x; sd[1] = da.y; sd[2] = da.z; sd[3] = da.w;
             sd[4] = db.x; sd[5] = db.y; sd[6] = db.z; sd[7] = db.w;
-            s_rgb[threadIdx.x] = make_float4(rgb[3 * (size_t)g], rgb[3 * (size_t)g + 1], rgb[3 * (size_t)g + 2], 0.f);
-            s_rect[threadIdx.x] = rect[g];
+            s_rgb[threadIdx.x] = w.r_rgb[rk];
+            s_rect[threadIdx.x] = w.r_rect[rk];
         }
         __syncthreads();
-        const int cnt = min(kTilePix, sg.y - base);
+        const int cnt = min(NT, L - base);
         for (int j = 0; j < cnt; ++j) {
             const int4 rc = s_rect[j];
             if (!(px >= rc.x && px <= rc.z && py >= rc.y && py <= rc.w)) continue;
@@ -246,40 +306,28 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
 
 }  // namespace
 
-void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uint32_t* tvals, const float* rgb,
-                             const int32_t* rect, void* planes, cudaStream_t s)
+void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, void* planes, cudaStream_t s)
 {
     const dim3 grid((unsigned)(p.tiles_x * p.tiles_y), (unsigned)p.N);
-    const int4* r4 = reinterpret_cast<const int4*>(rect);
     constexpr int kPPT = 2;   // pixels per thread
     constexpr int kThreads = kTilePix / kPPT;
     switch (p.dtype) {
-    case LF_F32: k_raster_gauss<LF_F32, kPPT><<<grid, kThreads, 0, s>>>(ws, p, tvals, rgb, r4, planes); break;
-    case LF_F16: k_raster_gauss<LF_F16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, tvals, rgb, r4, planes); break;
-    default: k_raster_gauss<LF_BF16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, tvals, rgb, r4, planes); break;
+    case LF_F32: k_raster_gauss<LF_F32, kPPT><<<grid, kThreads, 0, s>>>(ws, p, planes); break;
+    case LF_F16: k_raster_gauss<LF_F16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, planes); break;
+    default: k_raster_gauss<LF_BF16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, planes); break;
     }
     note_launches(1);
 }
 
-void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32_t* tvals, const lf_voxels& v,
-                          const int32_t* rect, void* planes, cudaStream_t s)
+void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, void* planes, cudaStream_t s)
 {
     const dim3 grid((unsigned)(p.tiles_x * p.tiles_y), (unsigned)p.N);
-    const int4* r4 = reinterpret_cast<const int4*>(rect);
     switch (p.dtype) {
-    case LF_F32:
-        k_raster_voxel<LF_F32><<<grid, kTilePix, 0, s>>>(ws, p, tvals, v.density8, v.rgb, r4, planes);
-        note_launches(1);
-        break;
-    case LF_F16:
-        k_raster_voxel<LF_F16><<<grid, kTilePix, 0, s>>>(ws, p, tvals, v.density8, v.rgb, r4, planes);
-        note_launches(1);
-        break;
-    default:
-        k_raster_voxel<LF_BF16><<<grid, kTilePix, 0, s>>>(ws, p, tvals, v.density8, v.rgb, r4, planes);
-        note_launches(1);
-        break;
+    case LF_F32: k_raster_voxel<LF_F32><<<grid, kTilePix, 0, s>>>(ws, p, planes); break;
+    case LF_F16: k_raster_voxel<LF_F16><<<grid, kTilePix, 0, s>>>(ws, p, planes); break;
+    default: k_raster_voxel<LF_BF16><<<grid, kTilePix, 0, s>>>(ws, p, planes); break;
     }
+    note_launches(1);
 }
 
 }  // namespace lf
