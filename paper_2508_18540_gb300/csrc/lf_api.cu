@@ -89,8 +89,9 @@ size_t build_ws_layout(int64_t n, int32_t N, int32_t W, int32_t H, int64_t cap, 
     char* base = static_cast<char*>(basev);
     const long long tiles = (long long)((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
     const long long S = tiles * N;                                  // (tile, chunk) lists
-    const long long nb = (n + kSortBlockKeys - 1) / kSortBlockKeys + 1;
-    const long long nbs = (S + kScanBlock - 1) / kScanBlock + 1;
+    const long long nmax = n > cap ? n : cap;
+    const long long nb = (nmax + kRadixBlockKeys - 1) / kRadixBlockKeys + 1;
+    const long long nbd = (n + kDupBlock - 1) / kDupBlock + 1;
     const size_t nn = (size_t)(n > 0 ? n : 1);
     const size_t cc = (size_t)(cap > 0 ? cap : 1);
     size_t off = 0;
@@ -110,16 +111,16 @@ size_t build_ws_layout(int64_t n, int32_t N, int32_t W, int32_t H, int64_t cap, 
     w.r_chunk = carve<int32_t>(base, off, nn);
     w.hist = carve<uint32_t>(base, off, (size_t)kSortDigits * nb);
     w.dtot = carve<uint32_t>(base, off, (size_t)kSortDigits);
-    w.bsum = carve<uint32_t>(base, off, (size_t)nbs);
+    w.bsum = carve<uint32_t>(base, off, (size_t)nbd);
     w.chunk_start = carve<int32_t>(base, off, (size_t)N + 1);
-    w.segcnt = carve<uint32_t>(base, off, (size_t)S);
-    w.seg = carve<int2>(base, off, (size_t)S);
-    w.biglist = carve<uint32_t>(base, off, (size_t)S);
+    w.tkeyA = carve<uint32_t>(base, off, cc);
+    w.tkeyB = carve<uint32_t>(base, off, cc);
     w.entA = carve<uint32_t>(base, off, cc);
     w.entB = carve<uint32_t>(base, off, cc);
+    w.seg = carve<int2>(base, off, (size_t)S);
     w.bytes = align_up(off, 256);
     w.nb_sort = nb;
-    w.nb_scan = nbs;
+    w.nb_dup = nbd;
     if (o) *o = w;
     return w.bytes;
 }
@@ -294,7 +295,7 @@ static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, in
     if ((st = check_launch("bin")) != LF_OK) return st;
 
     trace_begin("tile_lists", stream);
-    launch_tile_lists(w, n, cap, N, h.tiles_x, (int)n_tiles, stream);
+    const uint32_t* ranks = launch_tile_lists(w, n, cap, N, h.tiles_x, (int)n_tiles, stream);
     trace_end(stream);
     if ((st = check_launch("tile lists")) != LF_OK) return st;
 
@@ -302,9 +303,9 @@ static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, in
     fill_raster_params(ref, N, out->dtype, &rp);
     trace_begin(kind == 0 ? "raster_gaussians" : "raster_voxels", stream);
     if (kind == 0)
-        launch_raster_gaussians(w, rp, out->rgba, stream);
+        launch_raster_gaussians(w, rp, ranks, out->rgba, stream);
     else
-        launch_raster_voxels(w, rp, out->rgba, stream);
+        launch_raster_voxels(w, rp, ranks, out->rgba, stream);
     trace_end(stream);
     return check_launch("rasterise");
 }
@@ -475,12 +476,14 @@ lf_status lf_mpi_tile_lists(const void* ws, int32_t* order, int64_t n, int32_t* 
             return check_launch("order read");
     }
     if (tile_prims) {
-        // the lists hold ranks (sorted once the planes are rasterised); map
-        // them to primitive indices through the depth order
+        // the lists hold ranks; map them to primitive indices through the
+        // depth order
         if (cap < needed) return fail(LF_ERR_INVALID_ARG, "tile list buffer too small");
         if (needed > 0) {
             std::vector<uint32_t> rank_prim((size_t)(M > 0 ? M : 1));
-            if (cudaMemcpy(tile_prims, w.entA, sizeof(uint32_t) * (size_t)needed, cudaMemcpyDeviceToHost) !=
+            const uint32_t* ranks = tile_sort_passes(tile_bits_for((long long)h.tiles_x * h.tiles_y)) % 2 ? w.entB
+                                                                                                          : w.entA;
+            if (cudaMemcpy(tile_prims, ranks, sizeof(uint32_t) * (size_t)needed, cudaMemcpyDeviceToHost) !=
                     cudaSuccess ||
                 cudaMemcpy(rank_prim.data(), w.valA, sizeof(uint32_t) * (size_t)M, cudaMemcpyDeviceToHost) !=
                     cudaSuccess)

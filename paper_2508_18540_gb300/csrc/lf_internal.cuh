@@ -17,10 +17,9 @@ namespace lf {
 
 constexpr int kTile = 16;                 // splat tile edge (pixels)
 constexpr int kTilePix = kTile * kTile;   // threads per rasterisation CTA
-constexpr int kSortBlockKeys = 2048;      // keys per depth-sort block
-constexpr int kSortDigits = 2048;         // 11-bit radix digits
-constexpr int kSegSortCap = 2048;         // longest (tile, chunk) list sorted inside a raster CTA
-constexpr int kScanBlock = 1024;          // elements per block of the segment scan
+constexpr int kRadixBlockKeys = 4096;     // keys per radix-sort block
+constexpr int kSortDigits = 256;          // 8-bit radix digits
+constexpr int kDupBlock = 1024;           // ranks per block of the tile-pair emission
 constexpr uint64_t kInvalidKey = ~0ull;
 
 // ---- launch counting and stage tracing ------------------------------------
@@ -42,7 +41,7 @@ struct WsHeader {
     unsigned long long kmax;
     unsigned long long M;         // culled-in primitives
     unsigned long long total_dups;
-    unsigned long long n_big;     // (tile, chunk) lists longer than kSegSortCap
+    unsigned long long tile_n;    // pairs to sort (0 after an overflow)
     int overflow;                 // 1 if total_dups > dup_capacity
     int kind;                     // 0 gaussians, 1 voxels
     long long n;
@@ -69,15 +68,15 @@ struct BuildWs {
     int32_t* r_chunk;             // [n]
     uint32_t* hist;               // [kSortDigits * nb] radix histograms
     uint32_t* dtot;               // [kSortDigits] per-digit totals of a radix pass
-    uint32_t* bsum;               // [nbs] block sums of the segment scan
+    uint32_t* bsum;               // [nbd] block sums of the pair emission
     int32_t* chunk_start;         // [N + 1]
-    uint32_t* segcnt;             // [tiles * N] list lengths (then countdown cursors)
+    uint32_t* tkeyA;              // [cap] tile id of every (tile, rank) pair
+    uint32_t* tkeyB;
+    uint32_t* entA;               // [cap] rank of every pair
+    uint32_t* entB;
     int2* seg;                    // [tiles * N] (start, end) of every (tile, chunk) list
-    uint32_t* biglist;            // [tiles * N] lists longer than kSegSortCap
-    uint32_t* entA;               // [cap] ranks of the list entries
-    uint32_t* entB;               // [cap] scratch of the long-list sort
     size_t bytes;
-    long long nb_sort, nb_scan;
+    long long nb_sort, nb_dup;
 };
 
 size_t build_ws_layout(int64_t n, int32_t N, int32_t W, int32_t H, int64_t cap, void* base, BuildWs* out);
@@ -126,12 +125,19 @@ void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s);
 
 void launch_bin(const BuildWs& ws, const BinParams& p, long long n, int32_t* chunk, double* d, int32_t* count,
                 const int32_t* rect, const float* rgb, const float* dens8, int kind, cudaStream_t s);
-// (tile, chunk) lists: count, scan, emit (unordered), sort long lists.
-void launch_tile_lists(const BuildWs& ws, long long n, long long cap, int N, int tiles_x, int n_tiles,
-                       cudaStream_t s);
+// (tile, chunk) lists: (tile, rank) pairs emitted in rank order, stable sort
+// by tile, [start, end) of every (tile, chunk) list. Returns the sorted ranks.
+const uint32_t* launch_tile_lists(const BuildWs& ws, long long n, long long cap, int N, int tiles_x, int n_tiles,
+                                  cudaStream_t s);
+void sort_tile_keys(const BuildWs& ws, long long cap, int tile_bits, cudaStream_t s, uint32_t** keys_out,
+                    uint32_t** vals_out);
+int tile_sort_passes(int tile_bits);
+int tile_bits_for(long long tiles);
 
-void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, void* planes, cudaStream_t s);
-void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, void* planes, cudaStream_t s);
+void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
+                             cudaStream_t s);
+void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
+                          cudaStream_t s);
 
 // ---- composite ----------------------------------------------------------
 struct CompWs {

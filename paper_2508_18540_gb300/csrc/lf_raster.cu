@@ -1,11 +1,9 @@
 // lf_raster.cu -- 3D-tiled rasterisation of every chunk into its sweeping
 // plane (Algorithm 1 lines 4-5, "Parallel for all k: Rasterize(H, P'_k)").
 //
-// One CTA per (16x16 tile, chunk). The CTA first puts its (tile, chunk) list
-// in rank order -- depth order -- (lists up to kSegSortCap are sorted here in
-// shared memory and written back; longer ones were sorted beforehand), then
-// stages the listed primitives through shared memory in batches and every
-// thread blends its pixels front to back:
+// One CTA per (16x16 tile, chunk). Its (tile, chunk) list holds ranks in
+// depth order; the listed primitives (rank-ordered copies) are staged through
+// shared memory in batches and every thread blends its pixels front to back:
 //   Gaussians (Sec. 4.4, 3DGS model): alpha = min(0.99, o exp(-q/2)),
 //     q = d^T Sigma_2^{-1} d inside the primitive's footprint rectangle;
 //   voxels (Sec. 4.5, SVR model): alpha = 1 - exp(-integral of the trilinear
@@ -21,8 +19,6 @@
 namespace lf {
 
 namespace {
-
-constexpr int kCountSortMax = 256;   // lists up to this length: rank-counting sort
 
 template <int DT>
 __device__ __forceinline__ void store_texel(void* planes, size_t idx, float r, float g, float b, float a)
@@ -44,57 +40,6 @@ __device__ __forceinline__ void store_texel(void* planes, size_t idx, float r, f
     }
 }
 
-// Puts the CTA's list [sg.x, sg.y) of entA in rank order in s_rank and back in
-// entA. Returns false for a list longer than kSegSortCap (already sorted in
-// global memory by the long-list pass); the caller then reads entA directly.
-// Every thread of the CTA must call it (it synchronises).
-template <int NT>
-__device__ __forceinline__ bool sorted_list(const BuildWs& w, int2 sg, uint32_t* s_rank, uint32_t* s_tmp)
-{
-    const int L = sg.y - sg.x;
-    if (L > kSegSortCap) return false;
-    for (int i = threadIdx.x; i < L; i += NT) s_rank[i] = w.entA[sg.x + i];
-    __syncthreads();
-    if (L <= 1) return true;
-    if (L <= kCountSortMax) {
-        // position of every rank = number of smaller ranks (ranks are distinct)
-        for (int i = threadIdx.x; i < L; i += NT) {
-            const uint32_t v = s_rank[i];
-            int c = 0;
-            for (int j = 0; j < L; ++j) c += s_rank[j] < v;
-            s_tmp[c] = v;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < L; i += NT) {
-            s_rank[i] = s_tmp[i];
-            w.entA[sg.x + i] = s_tmp[i];
-        }
-        __syncthreads();
-        return true;
-    }
-    int P = 1;
-    while (P < L) P <<= 1;
-    for (int i = L + threadIdx.x; i < P; i += NT) s_rank[i] = 0xffffffffu;
-    __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < P; i += NT) {
-                const int ij = i ^ j;
-                if (ij > i) {
-                    const uint32_t a = s_rank[i], b = s_rank[ij];
-                    if ((a > b) == ((i & k) == 0)) {
-                        s_rank[i] = b;
-                        s_rank[ij] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    for (int i = threadIdx.x; i < L; i += NT) w.entA[sg.x + i] = s_rank[i];
-    return true;
-}
-
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
@@ -112,15 +57,14 @@ __device__ __forceinline__ float ex2_approx(float x)
 // entries touch its strip and visits only those, in list order, so the
 // blending order of every pixel is unchanged.
 template <int DT, int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, RasterParams p, void* planes)
+__global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, RasterParams p,
+                                                                 const uint32_t* __restrict__ ranks, void* planes)
 {
     constexpr int NT = kTilePix / PPT;
     constexpr float kL2E = 1.4426950408889634f;
     __shared__ float4 s_e0[NT];
     __shared__ float4 s_e1[NT];
     __shared__ float4 s_rgb[NT];
-    __shared__ uint32_t s_rank[kSegSortCap];
-    __shared__ uint32_t s_tmp[kCountSortMax];
     const int t = blockIdx.x, k = blockIdx.y;
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -130,7 +74,6 @@ __global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, Rast
     const int sy0 = ty * kTile + 2 * PPT * warp, sy1 = sy0 + 2 * PPT - 1;
     const int2 sg = w.seg[(size_t)t * p.N + k];
     const int L = sg.y - sg.x;
-    const bool local = sorted_list<NT>(w, sg, s_rank, s_tmp);
     const float fpx = (float)px;
     float C[PPT][3], T[PPT];
 #pragma unroll
@@ -138,7 +81,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, Rast
     for (int base = 0; base < L; base += NT) {
         const int i = base + threadIdx.x;
         if (i < L) {
-            const uint32_t rk = local ? s_rank[i] : w.entA[sg.x + i];
+            const uint32_t rk = ranks[sg.x + i];
             const float4 geo = w.r_geo[rk];
             const float4 c = w.r_con[rk];
             const int4 r = w.r_rect[rk];
@@ -211,22 +154,20 @@ __device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.0f),
 // reference centre and side from the projection pass, densities and colour
 // in rank order.
 template <int DT>
-__global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterParams p, void* planes)
+__global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterParams p,
+                                                           const uint32_t* __restrict__ ranks, void* planes)
 {
     constexpr int NT = kTilePix;
     __shared__ float4 s_box[NT];
     __shared__ float s_den[NT * 8];
     __shared__ float4 s_rgb[NT];
     __shared__ int4 s_rect[NT];
-    __shared__ uint32_t s_rank[kSegSortCap];
-    __shared__ uint32_t s_tmp[kCountSortMax];
     const int t = blockIdx.x, k = blockIdx.y;
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
     const int py = ty * kTile + (threadIdx.x / kTile);
     const int2 sg = w.seg[(size_t)t * p.N + k];
     const int L = sg.y - sg.x;
-    const bool local = sorted_list<NT>(w, sg, s_rank, s_tmp);
 
     // world-frame direction of the reference ray through this pixel centre
     const float dcx = ((float)px - p.cx) / p.fx, dcy = ((float)py - p.cy) / p.fy;
@@ -245,7 +186,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
     for (int base = 0; base < L; base += NT) {
         const int i = base + threadIdx.x;
         if (i < L) {
-            const uint32_t rk = local ? s_rank[i] : w.entA[sg.x + i];
+            const uint32_t rk = ranks[sg.x + i];
             s_box[threadIdx.x] = w.r_geo[rk];
             const float4 da = w.r_den[2 * (size_t)rk], db = w.r_den[2 * (size_t)rk + 1];
             float* sd = s_den + 8 * threadIdx.x;
@@ -306,26 +247,28 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
 
 }  // namespace
 
-void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, void* planes, cudaStream_t s)
+void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
+                             cudaStream_t s)
 {
     const dim3 grid((unsigned)(p.tiles_x * p.tiles_y), (unsigned)p.N);
     constexpr int kPPT = 2;   // pixels per thread
     constexpr int kThreads = kTilePix / kPPT;
     switch (p.dtype) {
-    case LF_F32: k_raster_gauss<LF_F32, kPPT><<<grid, kThreads, 0, s>>>(ws, p, planes); break;
-    case LF_F16: k_raster_gauss<LF_F16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, planes); break;
-    default: k_raster_gauss<LF_BF16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, planes); break;
+    case LF_F32: k_raster_gauss<LF_F32, kPPT><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
+    case LF_F16: k_raster_gauss<LF_F16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
+    default: k_raster_gauss<LF_BF16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
     }
     note_launches(1);
 }
 
-void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, void* planes, cudaStream_t s)
+void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
+                          cudaStream_t s)
 {
     const dim3 grid((unsigned)(p.tiles_x * p.tiles_y), (unsigned)p.N);
     switch (p.dtype) {
-    case LF_F32: k_raster_voxel<LF_F32><<<grid, kTilePix, 0, s>>>(ws, p, planes); break;
-    case LF_F16: k_raster_voxel<LF_F16><<<grid, kTilePix, 0, s>>>(ws, p, planes); break;
-    default: k_raster_voxel<LF_BF16><<<grid, kTilePix, 0, s>>>(ws, p, planes); break;
+    case LF_F32: k_raster_voxel<LF_F32><<<grid, kTilePix, 0, s>>>(ws, p, ranks, planes); break;
+    case LF_F16: k_raster_voxel<LF_F16><<<grid, kTilePix, 0, s>>>(ws, p, ranks, planes); break;
+    default: k_raster_voxel<LF_BF16><<<grid, kTilePix, 0, s>>>(ws, p, ranks, planes); break;
     }
     note_launches(1);
 }

@@ -1,23 +1,26 @@
-// lf_sort.cu -- stable LSD radix sort of the culled-in primitives by
-// (FP64 reference depth, index): Algorithm 1 line 3, "Sort_and_Chunk".
+// lf_sort.cu -- stable LSD radix sort (8-bit digits) of (key, value) pairs.
 //
-// Keys are the IEEE bits of the positive FP64 reference depth, which order
-// like the depths. The first pass drops culled primitives (key kInvalidKey)
-// and rewrites every key relative to the smallest valid key, so only the
-// bits that vary across the scene are sorted; a later pass whose digit is
-// the same for every key (known from the key range) is a plain copy. Values
-// start in index order and every pass is stable, so equal depths stay in
-// index order.
+// Used twice per build:
+//  - the depth sort of Algorithm 1 line 3 ("Sort_and_Chunk"): 64-bit keys =
+//    IEEE bits of the positive FP64 reference depth (they order like the
+//    depths), values = primitive index. The first pass drops culled
+//    primitives (key kInvalidKey) and makes every key relative to the
+//    smallest valid key, so passes above the varying bits are plain copies.
+//    Values start in index order and every pass is stable, so equal depths
+//    stay in index order.
+//  - the 3D tiling (Sec. 4.4): 32-bit keys = tile id of every (tile, rank)
+//    pair emitted in rank order; the stable sort groups the pairs by tile and
+//    keeps each tile's pairs in depth order.
 //
-// Each pass is reduce-then-scan over blocks of 2048 keys with 11-bit digits:
+// Each pass is reduce-then-scan over blocks of 4096 keys:
 //   k_upsweep   per-block digit histogram (warp-aggregated shared atomics);
 //   k_rowscan   one CTA per digit scans that digit's per-block counts;
-//   k_downsweep ranks the block's keys stably (warp match + per-warp
-//               counters; warps own contiguous key ranges), exchanges them
-//               through shared memory into digit order and writes every digit
-//               run contiguously.
-// Item counts may live on the device (the culled-in count), so grids are
-// sized for the capacity and blocks past the count write zero histograms.
+//   k_downsweep ranks the block's keys stably (ballot-based digit matching,
+//               per-warp counters, warps own contiguous key ranges), exchanges
+//               them through shared memory into digit order and writes every
+//               digit run contiguously.
+// Item counts may live on the device (culled-in count, pair count), so grids
+// are sized for the capacity and blocks past the count write zero histograms.
 #include "lf_internal.cuh"
 
 namespace lf {
@@ -26,19 +29,18 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kKPT = kSortBlockKeys / kThreads;  // 8 keys per thread
-constexpr int kDigits = kSortDigits;             // 2048
-constexpr int kBits = 11;
-static_assert((1 << kBits) == kDigits, "digit width");
-static_assert(kKPT * 32 <= 65535, "per-warp counters are 16-bit");
+constexpr int kBits = 8;
+constexpr int kDigits = 1 << kBits;             // 256 = one digit per thread
+constexpr int kKPT = kRadixBlockKeys / kThreads; // 16 keys per thread
+static_assert(kDigits == kThreads, "one digit per thread in the digit scans");
 
 struct PassArgs {
     long long n_static;                    // upper bound / fixed count
     const unsigned long long* n_dev;       // device count (or null)
-    const unsigned long long* kmin;        // absolute range of the valid keys
+    const unsigned long long* kmin;        // valid key range (depth keys) or null
     const unsigned long long* kmax;
     int shift;
-    int first;                             // drop invalid keys, make keys relative
+    int first;                             // depth keys: drop invalid, make relative
     int nb;                                // number of blocks (histogram stride)
 };
 
@@ -47,54 +49,69 @@ __device__ __forceinline__ long long pass_count(const PassArgs& a)
     return a.n_dev ? (long long)*a.n_dev : a.n_static;
 }
 
-// every relative key has the same digit at this shift: identity pass
+// every (relative) key has the same digit at this shift: identity pass
 __device__ __forceinline__ bool pass_uniform(const PassArgs& a)
 {
-    if (a.first) return false;
+    if (a.first || !a.kmin) return false;
     const unsigned long long lo = *a.kmin, hi = *a.kmax;
     if (lo > hi) return true;   // no valid keys
     return ((hi - lo) >> a.shift) == 0ull;
 }
 
-__device__ __forceinline__ uint32_t digit_of(unsigned long long k, int shift)
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K k, int shift)
 {
     return (uint32_t)(k >> shift) & (uint32_t)(kDigits - 1);
 }
 
-// the key as sorted (relative to the smallest valid key); false if absent
-__device__ __forceinline__ bool load_key(const unsigned long long* keys, long long idx, long long n,
-                                         const PassArgs& a, unsigned long long kmin, unsigned long long& k)
+// the key as sorted; false if absent (past the count, or culled)
+template <typename K>
+__device__ __forceinline__ bool load_key(const K* keys, long long idx, long long n, const PassArgs& a,
+                                         unsigned long long kmin, K& k)
 {
     if (idx >= n) return false;
     k = keys[idx];
     if (a.first) {
-        if (k == kInvalidKey) return false;
-        k -= kmin;
+        if ((unsigned long long)k == kInvalidKey) return false;
+        k = (K)((unsigned long long)k - kmin);
     }
     return true;
 }
 
-__global__ void __launch_bounds__(kThreads) k_upsweep(const unsigned long long* __restrict__ keys, PassArgs a,
-                                                      uint32_t* hist)
+// lanes holding the same digit (ballot per digit bit); valid lanes only
+__device__ __forceinline__ uint32_t match_digit(uint32_t d, bool ok)
+{
+    uint32_t peers = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int b = 0; b < kBits; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+    }
+    return peers;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_upsweep(const K* __restrict__ keys, PassArgs a, uint32_t* hist)
 {
     __shared__ uint32_t h[kDigits];
     if (pass_uniform(a)) return;
     const long long n = pass_count(a);
-    const unsigned long long kmin = *a.kmin;
-    for (int i = threadIdx.x; i < kDigits; i += kThreads) h[i] = 0;
+    const unsigned long long kmin = a.kmin ? *a.kmin : 0ull;
+    h[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long base = (long long)blockIdx.x * kSortBlockKeys + warp * (32 * kKPT);
-#pragma unroll
+    const long long base = (long long)blockIdx.x * kRadixBlockKeys + warp * (32 * kKPT);
+#pragma unroll 4
     for (int r = 0; r < kKPT; ++r) {
-        unsigned long long k = 0;
+        K k = 0;
         const bool ok = load_key(keys, base + r * 32 + lane, n, a, kmin, k);
-        const uint32_t d = ok ? digit_of(k, a.shift) : (uint32_t)kDigits;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t d = ok ? digit_of(k, a.shift) : 0u;
+        const uint32_t peers = match_digit(d, ok);
         if (ok && (__ffs(peers) - 1) == lane) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kDigits; i += kThreads) hist[(size_t)i * a.nb + blockIdx.x] = h[i];
+    hist[(size_t)threadIdx.x * a.nb + blockIdx.x] = h[threadIdx.x];
 }
 
 // Exclusive scan of digit row d (hist[d * nb + b] over blocks b), in place;
@@ -131,66 +148,54 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(uint32_t* hist, uint32_t* 
     if (threadIdx.x == 0) tot[blockIdx.x] = carry;
 }
 
-// In-place exclusive scan of kDigits values (thread t owns kDigits/kThreads
-// consecutive digits); returns the total. Ends with a CTA barrier.
-__device__ __forceinline__ uint32_t scan_digits(uint32_t* vals, uint32_t* warp_tmp)
+// exclusive scan of one value per thread over the block; returns the total
+__device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t* warp_tmp, uint32_t* total)
 {
-    constexpr int P = kDigits / kThreads;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    uint32_t s = 0;
-#pragma unroll
-    for (int i = 0; i < P; ++i) s += vals[threadIdx.x * P + i];
-    uint32_t x = s;
+    uint32_t x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += u;
     }
+    __syncthreads();
     if (lane == 31) warp_tmp[warp] = x;
     __syncthreads();
-    uint32_t before = 0, total = 0;
+    uint32_t before = 0, tot = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
         const uint32_t t = warp_tmp[w];
         before += w < warp ? t : 0u;
-        total += t;
+        tot += t;
     }
-    uint32_t run = before + x - s;
-#pragma unroll
-    for (int i = 0; i < P; ++i) {
-        const uint32_t v = vals[threadIdx.x * P + i];
-        vals[threadIdx.x * P + i] = run;
-        run += v;
-    }
-    __syncthreads();
-    return total;
+    *total = tot;
+    return before + x - v;
 }
 
+template <typename K>
 struct DownSmem {
-    uint16_t wcnt[kWarps][kDigits];           // per-warp digit counts, then per-warp offsets
-    uint32_t blk_start[kDigits];              // block-local start of every digit run
-    uint32_t glob_base[kDigits];              // global destination of every digit run
-    unsigned long long xkey[kSortBlockKeys];  // exchange buffer in block-local digit order
-    uint32_t xval[kSortBlockKeys];
+    uint32_t wcnt[kWarps][kDigits];       // per-warp digit counts, then per-warp offsets
+    uint32_t blk_start[kDigits];          // block-local start of every digit run
+    uint32_t glob_base[kDigits];          // global destination of every digit run
+    K xkey[kRadixBlockKeys];              // exchange buffer in block-local digit order
+    uint32_t xval[kRadixBlockKeys];
     uint32_t warp_tmp[kWarps];
 };
 
-__global__ void __launch_bounds__(kThreads) k_downsweep(const unsigned long long* __restrict__ kin,
-                                                        const uint32_t* __restrict__ vin,
-                                                        unsigned long long* __restrict__ kout,
-                                                        uint32_t* __restrict__ vout, PassArgs a,
-                                                        const uint32_t* __restrict__ hist,
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_downsweep(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                        K* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                        PassArgs a, const uint32_t* __restrict__ hist,
                                                         const uint32_t* __restrict__ tot)
 {
     extern __shared__ __align__(16) unsigned char dsm_raw[];
-    DownSmem& S = *reinterpret_cast<DownSmem*>(dsm_raw);
+    DownSmem<K>& S = *reinterpret_cast<DownSmem<K>*>(dsm_raw);
     const long long n = pass_count(a);
-    const long long blk = (long long)blockIdx.x * kSortBlockKeys;
+    const long long blk = (long long)blockIdx.x * kRadixBlockKeys;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (pass_uniform(a)) {
         // every key has the same digit: the stable permutation is the identity
-        for (int i = threadIdx.x; i < kSortBlockKeys; i += kThreads) {
+        for (int i = threadIdx.x; i < kRadixBlockKeys; i += kThreads) {
             const long long idx = blk + i;
             if (idx < n) {
                 kout[idx] = kin[idx];
@@ -200,48 +205,51 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const unsigned long long
         return;
     }
     if (blk >= n) return;
-    const unsigned long long kmin = *a.kmin;
+    const unsigned long long kmin = a.kmin ? *a.kmin : 0ull;
+    const int d0 = threadIdx.x;   // the digit this thread scans
 
-    for (int i = threadIdx.x; i < kWarps * kDigits; i += kThreads) (&S.wcnt[0][0])[i] = 0;
-    // global digit bases (exclusive scan of the digit totals) plus this
-    // block's exclusive offset within each digit row
-    for (int d = threadIdx.x; d < kDigits; d += kThreads) S.glob_base[d] = tot[d];
-    scan_digits(S.glob_base, S.warp_tmp);
-    for (int d = threadIdx.x; d < kDigits; d += kThreads) S.glob_base[d] += hist[(size_t)d * a.nb + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) S.wcnt[w][d0] = 0;
+    {
+        uint32_t total;
+        S.glob_base[d0] = block_exscan(tot[d0], S.warp_tmp, &total) + hist[(size_t)d0 * a.nb + blockIdx.x];
+    }
+    __syncthreads();
 
-    // rank: warp w owns keys [256 w, 256 w + 256) of the block, visited in
+    // rank: warp w owns keys [512 w, 512 w + 512) of the block, visited in
     // order round by round, so equal digits keep their order
-    unsigned long long key[kKPT];
+    K key[kKPT];
     uint32_t val[kKPT], dig[kKPT], pos[kKPT];
     const long long wbase = blk + warp * (32 * kKPT);
+    const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < kKPT; ++r) {
         const long long idx = wbase + r * 32 + lane;
-        unsigned long long k = 0;
+        K k = 0;
         const bool ok = load_key(kin, idx, n, a, kmin, k);
         key[r] = k;
         val[r] = ok ? vin[idx] : 0u;
-        dig[r] = ok ? digit_of(k, a.shift) : (uint32_t)kDigits;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
-        const uint32_t before = ok ? (uint32_t)S.wcnt[warp][dig[r]] : 0u;
+        const uint32_t d = ok ? digit_of(k, a.shift) : 0u;
+        dig[r] = ok ? d : (uint32_t)kDigits;
+        const uint32_t peers = match_digit(d, ok);
+        const uint32_t before = ok ? S.wcnt[warp][d] : 0u;
         __syncwarp();
-        pos[r] = before + __popc(peers & ((1u << lane) - 1u));
-        if (ok && (__ffs(peers) - 1) == lane) S.wcnt[warp][dig[r]] = (uint16_t)(before + __popc(peers));
+        pos[r] = before + __popc(peers & lt);
+        if (ok && (__ffs(peers) - 1) == lane) S.wcnt[warp][d] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
     // per digit: exclusive offsets over warps and the block-local digit total
-    for (int d = threadIdx.x; d < kDigits; d += kThreads) {
-        uint32_t run = 0;
+    uint32_t run = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t c = S.wcnt[w][d];
-            S.wcnt[w][d] = (uint16_t)run;
-            run += c;
-        }
-        S.blk_start[d] = run;
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = S.wcnt[w][d0];
+        S.wcnt[w][d0] = run;
+        run += c;
     }
-    const uint32_t placed = scan_digits(S.blk_start, S.warp_tmp);
+    uint32_t placed;
+    S.blk_start[d0] = block_exscan(run, S.warp_tmp, &placed);
+    __syncthreads();
     // exchange into block-local digit order
 #pragma unroll
     for (int r = 0; r < kKPT; ++r) {
@@ -253,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const unsigned long long
     __syncthreads();
     // coalesced write-out: item l of digit d goes to glob_base[d] + (l - blk_start[d])
     for (uint32_t l = threadIdx.x; l < placed; l += kThreads) {
-        const unsigned long long k = S.xkey[l];
+        const K k = S.xkey[l];
         const uint32_t d = digit_of(k, a.shift);
         const uint32_t dst = S.glob_base[d] + (l - S.blk_start[d]);
         kout[dst] = k;
@@ -261,23 +269,27 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const unsigned long long
     }
 }
 
+template <typename K>
+void radix_pass(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, const PassArgs& a, uint32_t* hist,
+                uint32_t* tot, cudaStream_t s)
+{
+    cudaFuncSetAttribute(k_downsweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DownSmem<K>));
+    k_upsweep<K><<<a.nb, kThreads, 0, s>>>(kin, a, hist);
+    k_rowscan<<<kDigits, kThreads, 0, s>>>(hist, tot, a);
+    k_downsweep<K><<<a.nb, kThreads, sizeof(DownSmem<K>), s>>>(kin, vin, kout, vout, a, hist, tot);
+    note_launches(3);
+}
+
 }  // namespace
 
 void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s)
 {
     if (n <= 0) return;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DownSmem));
-        attr_set = true;
-    }
-    const int nb = (int)((n + kSortBlockKeys - 1) / kSortBlockKeys);
+    const int nb = (int)((n + kRadixBlockKeys - 1) / kRadixBlockKeys);
     unsigned long long* kb[2] = {ws.keyA, ws.keyB};
     uint32_t* vb[2] = {ws.valA, ws.valB};
     int cur = 0;
-    constexpr int kPasses = (64 + kBits - 1) / kBits;   // 6: the result returns to (keyA, valA)
-    static_assert(kPasses % 2 == 0, "even pass count keeps the result in the A buffers");
-    for (int pass = 0; pass < kPasses; ++pass) {
+    for (int pass = 0; pass < 64 / kBits; ++pass) {
         PassArgs a;
         a.n_static = n;
         a.n_dev = pass == 0 ? nullptr : &ws.hdr->M;
@@ -286,15 +298,37 @@ void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s)
         a.shift = pass * kBits;
         a.first = pass == 0;
         a.nb = nb;
-        k_upsweep<<<nb, kThreads, 0, s>>>(kb[cur], a, ws.hist);
-        note_launches(1);
-        k_rowscan<<<kDigits, kThreads, 0, s>>>(ws.hist, ws.dtot, a);
-        note_launches(1);
-        k_downsweep<<<nb, kThreads, sizeof(DownSmem), s>>>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], a, ws.hist,
-                                                           ws.dtot);
-        note_launches(1);
+        radix_pass<unsigned long long>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], a, ws.hist, ws.dtot, s);
         cur ^= 1;
     }
+    // 8 passes: the result is back in (keyA, valA)
+}
+
+int tile_sort_passes(int tile_bits) { return (tile_bits + kBits - 1) / kBits; }
+
+void sort_tile_keys(const BuildWs& ws, long long cap, int tile_bits, cudaStream_t s, uint32_t** keys_out,
+                    uint32_t** vals_out)
+{
+    uint32_t* kb[2] = {ws.tkeyA, ws.tkeyB};
+    uint32_t* vb[2] = {ws.entA, ws.entB};
+    int cur = 0;
+    if (cap > 0) {
+        const int nb = (int)((cap + kRadixBlockKeys - 1) / kRadixBlockKeys);
+        for (int pass = 0; pass < tile_sort_passes(tile_bits); ++pass) {
+            PassArgs a;
+            a.n_static = cap;
+            a.n_dev = &ws.hdr->tile_n;
+            a.kmin = nullptr;
+            a.kmax = nullptr;
+            a.shift = pass * kBits;
+            a.first = 0;
+            a.nb = nb;
+            radix_pass<uint32_t>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], a, ws.hist, ws.dtot, s);
+            cur ^= 1;
+        }
+    }
+    *keys_out = kb[cur];
+    *vals_out = vb[cur];
 }
 
 }  // namespace lf

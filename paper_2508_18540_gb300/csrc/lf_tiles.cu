@@ -1,19 +1,16 @@
-// lf_tiles.cu -- 3D tiling (Sec. 4.4): the list of every (16x16 tile, chunk)
-// pair, holding the ranks of the chunk's primitives whose footprint meets
-// the tile.
+// lf_tiles.cu -- 3D tiling (Sec. 4.4): for every (16x16 tile, chunk) pair,
+// the list of the chunk's primitives whose footprint rectangle meets the
+// tile, in depth order.
 //
-//  k_seg_count  one counter per (tile, chunk), bumped for every tile a
-//               primitive's footprint rectangle touches;
-//  k_seg_scan_* exclusive scan of the counters -> [start, end) of every list,
-//               total pair count (overflow check against the capacity) and the
-//               lists longer than kSegSortCap;
-//  k_seg_emit   writes every rank into its list through a countdown cursor
-//               (list order arbitrary at this point);
-//  k_sort_big   sorts the long lists by rank (ranks in a list are distinct
-//               and lie inside their chunk's rank range: a shared-memory
-//               bitmap over that range, compacted in order). Lists up to
-//               kSegSortCap are sorted by the raster CTA that consumes them.
-// Rank order is depth order, so every list ends in front-to-back order.
+//  k_dup_count / k_dup_scan / k_dup_emit
+//      one (tile id, rank) pair per tile a primitive's footprint touches,
+//      written in rank (depth) order: per-block totals, one scan, then every
+//      block writes its pairs at its offset;
+//  sort_tile_keys (lf_sort.cu)
+//      stable radix sort of the pairs by tile id: every tile's pairs stay in
+//      depth order, and chunks (monotone in rank) form contiguous runs;
+//  k_ranges
+//      [start, end) of every (tile, chunk) run.
 #include "lf_internal.cuh"
 
 namespace lf {
@@ -21,48 +18,18 @@ namespace lf {
 namespace {
 
 constexpr int kT = 256;
-constexpr int kBigWords = 8192;   // 32 KB bitmap: 262144 ranks per window
+constexpr int kPer = kDupBlock / kT;   // consecutive ranks per thread
 
-__device__ __forceinline__ void tile_span(int4 rc, int& tx0, int& tx1, int& ty0, int& ty1)
+__device__ __forceinline__ uint32_t tile_count(int4 rc)
 {
-    tx0 = rc.x / kTile;
-    tx1 = rc.z / kTile;
-    ty0 = rc.y / kTile;
-    ty1 = rc.w / kTile;
+    if (rc.z < rc.x || rc.w < rc.y) return 0u;
+    return (uint32_t)((rc.z / kTile - rc.x / kTile + 1) * (rc.w / kTile - rc.y / kTile + 1));
 }
 
-__global__ void __launch_bounds__(kT) k_seg_count(BuildWs w, int N, int tiles_x)
+// exclusive scan of one value per thread over a 256-thread block
+__device__ __forceinline__ uint32_t block_exscan256(uint32_t v, uint32_t* total)
 {
-    const long long M = (long long)w.hdr->M;
-    const long long r = (long long)blockIdx.x * kT + threadIdx.x;
-    if (r >= M) return;
-    const int4 rc = w.r_rect[r];
-    const int c = w.r_chunk[r];
-    int tx0, tx1, ty0, ty1;
-    tile_span(rc, tx0, tx1, ty0, ty1);
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&w.segcnt[((size_t)ty * tiles_x + tx) * N + c], 1u);
-}
-
-__device__ __forceinline__ uint32_t block_sum_1024(uint32_t v, uint32_t* wtmp)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) wtmp[warp] = v;
-    __syncthreads();
-    uint32_t t = 0;
-    if (warp == 0) {
-        t = wtmp[lane];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    }
-    return t;  // valid in warp 0
-}
-
-// exclusive scan of one value per thread over a 1024-thread block
-__device__ __forceinline__ uint32_t block_exscan_1024(uint32_t v, uint32_t* wtmp)
-{
+    __shared__ uint32_t wsum[kT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
 #pragma unroll
@@ -70,36 +37,38 @@ __device__ __forceinline__ uint32_t block_exscan_1024(uint32_t v, uint32_t* wtmp
         const uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += u;
     }
-    if (lane == 31) wtmp[warp] = x;
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
-    if (warp == 0) {
-        uint32_t s = wtmp[lane];
+    uint32_t before = 0, tot = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t u = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += u;
-        }
-        wtmp[lane] = s;
+    for (int w = 0; w < kT / 32; ++w) {
+        const uint32_t t = wsum[w];
+        before += w < warp ? t : 0u;
+        tot += t;
     }
-    __syncthreads();
-    return (warp ? wtmp[warp - 1] : 0u) + x - v;
+    if (total) *total = tot;
+    return before + x - v;
 }
 
-__global__ void __launch_bounds__(kScanBlock) k_seg_scan_a(BuildWs w, long long S)
+__global__ void __launch_bounds__(kT) k_dup_count(BuildWs w)
 {
-    __shared__ uint32_t wtmp[32];
-    const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
-    const uint32_t v = i < S ? w.segcnt[i] : 0u;
-    const uint32_t t = block_sum_1024(v, wtmp);
-    if (threadIdx.x == 0) w.bsum[blockIdx.x] = t;
+    const long long M = (long long)w.hdr->M;
+    const long long r0 = (long long)blockIdx.x * kDupBlock + (long long)threadIdx.x * kPer;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j)
+        if (r0 + j < M) sum += tile_count(w.r_rect[r0 + j]);
+    uint32_t total;
+    block_exscan256(sum, &total);
+    if (threadIdx.x == 0) w.bsum[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(1024) k_seg_scan_b(BuildWs w, int nbs)
+__global__ void __launch_bounds__(1024) k_dup_scan(BuildWs w, int nb)
 {
     __shared__ unsigned long long wt[32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int per = (nbs + 1023) / 1024;
-    const int b = t * per, e = min(nbs, b + per);
+    const int per = (nb + 1023) / 1024;
+    const int b = t * per, e = min(nb, b + per);
     unsigned long long sum = 0;
     for (int i = b; i < e; ++i) sum += w.bsum[i];
     unsigned long long x = sum;
@@ -129,116 +98,87 @@ __global__ void __launch_bounds__(1024) k_seg_scan_b(BuildWs w, int nbs)
     if (t == 1023) {
         const unsigned long long total = wt[31];
         w.hdr->total_dups = total;
-        w.hdr->overflow = total > (unsigned long long)w.hdr->dup_capacity;
+        const int over = total > (unsigned long long)w.hdr->dup_capacity;
+        w.hdr->overflow = over;
+        w.hdr->tile_n = over ? 0ull : total;
     }
 }
 
-__global__ void __launch_bounds__(kScanBlock) k_seg_scan_c(BuildWs w, long long S)
-{
-    __shared__ uint32_t wtmp[32];
-    const long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
-    const uint32_t v = i < S ? w.segcnt[i] : 0u;
-    const uint32_t start = w.bsum[blockIdx.x] + block_exscan_1024(v, wtmp);
-    if (i >= S) return;
-    if (w.hdr->overflow) {
-        w.seg[i] = make_int2(0, 0);
-        return;
-    }
-    w.seg[i] = make_int2((int)start, (int)(start + v));
-    if (v > (uint32_t)kSegSortCap) w.biglist[atomicAdd(&w.hdr->n_big, 1ull)] = (uint32_t)i;
-}
-
-__global__ void __launch_bounds__(kT) k_seg_emit(BuildWs w, int N, int tiles_x)
+__global__ void __launch_bounds__(kT) k_dup_emit(BuildWs w, int tiles_x)
 {
     if (w.hdr->overflow) return;
     const long long M = (long long)w.hdr->M;
-    const long long r = (long long)blockIdx.x * kT + threadIdx.x;
-    if (r >= M) return;
-    const int4 rc = w.r_rect[r];
-    const int c = w.r_chunk[r];
-    int tx0, tx1, ty0, ty1;
-    tile_span(rc, tx0, tx1, ty0, ty1);
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            const size_t s = ((size_t)ty * tiles_x + tx) * N + c;
-            const uint32_t left = atomicSub(&w.segcnt[s], 1u);
-            w.entA[(size_t)w.seg[s].x + left - 1u] = (uint32_t)r;
-        }
+    const long long r0 = (long long)blockIdx.x * kDupBlock + (long long)threadIdx.x * kPer;
+    int4 rc[kPer];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        rc[j] = r0 + j < M ? w.r_rect[r0 + j] : make_int4(0, 0, -1, -1);
+        sum += tile_count(rc[j]);
+    }
+    uint32_t off = w.bsum[blockIdx.x] + block_exscan256(sum, nullptr);
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        if (rc[j].z < rc[j].x || rc[j].w < rc[j].y) continue;
+        const int tx0 = rc[j].x / kTile, tx1 = rc[j].z / kTile, ty0 = rc[j].y / kTile, ty1 = rc[j].w / kTile;
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) {
+                w.tkeyA[off] = (uint32_t)(ty * tiles_x + tx);
+                w.entA[off] = (uint32_t)(r0 + j);
+                ++off;
+            }
+    }
 }
 
-__global__ void __launch_bounds__(kT) k_sort_big(BuildWs w, int N)
+__device__ __forceinline__ void range_one(const BuildWs& w, const uint32_t* __restrict__ keys,
+                                          const uint32_t* __restrict__ ranks, int N, long long n, long long i)
 {
-    __shared__ uint32_t bm[kBigWords];
-    __shared__ uint32_t wtmp[kT / 32];
-    const unsigned long long nbig = w.hdr->n_big;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int P = kBigWords / kT;
-    for (unsigned long long bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
-        const uint32_t s = w.biglist[bi];
-        const int c = (int)(s % (uint32_t)N);
-        const int2 sg = w.seg[s];
-        const uint32_t lo = (uint32_t)w.chunk_start[c], hi = (uint32_t)w.chunk_start[c + 1];
-        uint32_t out = (uint32_t)sg.x;
-        for (uint32_t w0 = lo; w0 < hi; w0 += 32u * kBigWords) {
-            for (int i = threadIdx.x; i < kBigWords; i += kT) bm[i] = 0u;
-            __syncthreads();
-            for (int i = sg.x + threadIdx.x; i < sg.y; i += kT) {
-                const uint32_t rk = w.entA[i];
-                if (rk >= w0 && rk - w0 < 32u * kBigWords) atomicOr(&bm[(rk - w0) >> 5], 1u << ((rk - w0) & 31u));
-            }
-            __syncthreads();
-            uint32_t cnt = 0;
-#pragma unroll 4
-            for (int q = 0; q < P; ++q) cnt += __popc(bm[threadIdx.x * P + q]);
-            // block exclusive scan of cnt
-            uint32_t x = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t u = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += u;
-            }
-            if (lane == 31) wtmp[warp] = x;
-            __syncthreads();
-            uint32_t before = 0, total = 0;
-#pragma unroll
-            for (int q = 0; q < kT / 32; ++q) {
-                before += q < warp ? wtmp[q] : 0u;
-                total += wtmp[q];
-            }
-            uint32_t o = out + before + x - cnt;
-            for (int q = 0; q < P; ++q) {
-                const int word = threadIdx.x * P + q;
-                uint32_t bits = bm[word];
-                while (bits) {
-                    const int b = __ffs(bits) - 1;
-                    bits &= bits - 1u;
-                    w.entB[o++] = w0 + 32u * (uint32_t)word + (uint32_t)b;
-                }
-            }
-            out += total;
-            __syncthreads();
-        }
-        for (int i = sg.x + threadIdx.x; i < sg.y; i += kT) w.entA[i] = w.entB[i];
-        __syncthreads();
-    }
+    const uint32_t t = keys[i];
+    const int c = w.r_chunk[ranks[i]];
+    const long long sidx = (long long)t * N + c;
+    bool first = i == 0, last = i == n - 1;
+    if (!first) first = keys[i - 1] != t || w.r_chunk[ranks[i - 1]] != c;
+    if (!last) last = keys[i + 1] != t || w.r_chunk[ranks[i + 1]] != c;
+    if (first) w.seg[sidx].x = (int)i;
+    if (last) w.seg[sidx].y = (int)(i + 1);
+}
+
+__global__ void __launch_bounds__(256) k_ranges(BuildWs w, const uint32_t* __restrict__ keys,
+                                                const uint32_t* __restrict__ ranks, int N)
+{
+    const long long n = (long long)w.hdr->tile_n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        range_one(w, keys, ranks, N, n, i);
 }
 
 }  // namespace
 
-void launch_tile_lists(const BuildWs& ws, long long n, long long cap, int N, int tiles_x, int n_tiles, cudaStream_t s)
+int tile_bits_for(long long tiles)
 {
-    (void)cap;
-    const long long S = (long long)n_tiles * N;
-    cudaMemsetAsync(ws.segcnt, 0, sizeof(uint32_t) * (size_t)S, s);
-    const unsigned rb = (unsigned)(((n > 0 ? n : 1) + kT - 1) / kT);
-    k_seg_count<<<rb, kT, 0, s>>>(ws, N, tiles_x);
-    const int nbs = (int)((S + kScanBlock - 1) / kScanBlock);
-    k_seg_scan_a<<<nbs, kScanBlock, 0, s>>>(ws, S);
-    k_seg_scan_b<<<1, 1024, 0, s>>>(ws, nbs);
-    k_seg_scan_c<<<nbs, kScanBlock, 0, s>>>(ws, S);
-    k_seg_emit<<<rb, kT, 0, s>>>(ws, N, tiles_x);
-    k_sort_big<<<2 * 152, kT, 0, s>>>(ws, N);
-    note_launches(6);
+    int b = 1;
+    while ((1ll << b) < tiles) ++b;
+    return b;
+}
+
+const uint32_t* launch_tile_lists(const BuildWs& ws, long long n, long long cap, int N, int tiles_x, int n_tiles,
+                                  cudaStream_t s)
+{
+    cudaMemsetAsync(ws.seg, 0, sizeof(int2) * (size_t)n_tiles * N, s);
+    const int nb = (int)(((n > 0 ? n : 1) + kDupBlock - 1) / kDupBlock);
+    k_dup_count<<<nb, kT, 0, s>>>(ws);
+    k_dup_scan<<<1, 1024, 0, s>>>(ws, nb);
+    k_dup_emit<<<nb, kT, 0, s>>>(ws, tiles_x);
+    note_launches(3);
+    uint32_t* keys = nullptr;
+    uint32_t* ranks = nullptr;
+    sort_tile_keys(ws, cap, tile_bits_for(n_tiles), s, &keys, &ranks);
+    if (cap > 0) {
+        const long long want = (cap + 255) / 256;
+        const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+        k_ranges<<<blocks, 256, 0, s>>>(ws, keys, ranks, N);
+        note_launches(1);
+    }
+    return ranks;
 }
 
 }  // namespace lf
