@@ -102,11 +102,18 @@ __global__ void __launch_bounds__(kThreads) k_upsweep(const K* __restrict__ keys
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long base = (long long)blockIdx.x * kRadixBlockKeys + warp * (32 * kKPT);
-#pragma unroll 4
+    K kk[kKPT];
+    uint32_t okm = 0;
+#pragma unroll
     for (int r = 0; r < kKPT; ++r) {
         K k = 0;
-        const bool ok = load_key(keys, base + r * 32 + lane, n, a, kmin, k);
-        const uint32_t d = ok ? digit_of(k, a.shift) : 0u;
+        okm |= load_key(keys, base + r * 32 + lane, n, a, kmin, k) ? (1u << r) : 0u;
+        kk[r] = k;
+    }
+#pragma unroll
+    for (int r = 0; r < kKPT; ++r) {
+        const bool ok = (okm >> r) & 1u;
+        const uint32_t d = ok ? digit_of(kk[r], a.shift) : 0u;
         const uint32_t peers = match_digit(d, ok);
         if (ok && (__ffs(peers) - 1) == lane) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
@@ -222,6 +229,8 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const K* __restrict__ ki
     uint32_t val[kKPT], dig[kKPT], pos[kKPT];
     const long long wbase = blk + warp * (32 * kKPT);
     const uint32_t lt = (1u << lane) - 1u;
+    // all loads first (the ranking rounds below synchronise the warp)
+    uint32_t okm = 0;
 #pragma unroll
     for (int r = 0; r < kKPT; ++r) {
         const long long idx = wbase + r * 32 + lane;
@@ -229,6 +238,12 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const K* __restrict__ ki
         const bool ok = load_key(kin, idx, n, a, kmin, k);
         key[r] = k;
         val[r] = ok ? vin[idx] : 0u;
+        okm |= ok ? (1u << r) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kKPT; ++r) {
+        const bool ok = (okm >> r) & 1u;
+        const K k = key[r];
         const uint32_t d = ok ? digit_of(k, a.shift) : 0u;
         dig[r] = ok ? d : (uint32_t)kDigits;
         const uint32_t peers = match_digit(d, ok);
