@@ -333,16 +333,33 @@ __device__ __forceinline__ int plane_row(int P_s, int y, float gm, float h)
     return P_s * y + (__float_as_int(floor_magic<true>(gm, (float)y, h)) - kMagicBits);
 }
 
-// c: shared address of the plane's coefficients [gm_x, gm_y, h_y, h_x[VG]];
-// sb: shared address of the stage holding the plane's rows
+// Coefficient block of one plane (16-byte aligned, read with broadcast
+// 16-byte loads): [gm_x, gm_y, h_y, wide] then h_x of the VG views.
+template <int VG>
+struct CoefBlock {
+    static constexpr int kFloats = 4 + 4 * ((VG + 3) / 4);
+};
+
+// hdr: (gm_x, gm_y, h_y, -); ca: shared address of the plane's coefficient
+// block; sb: shared address of the stage holding the plane's rows
 template <int DT, bool BILINEAR, int VG, bool CLAMP>
-__device__ __forceinline__ void blend_plane(float (&acc)[VG][4], uint32_t ca, uint32_t sb, const StagedGeom& G,
-                                            const CompParams& p, int x, int y, int ty, uint32_t maxi)
+__device__ __forceinline__ void blend_plane(float (&acc)[VG][4], float4 hdr, uint32_t ca, uint32_t sb,
+                                            const StagedGeom& G, const CompParams& p, int x, int y, int ty,
+                                            uint32_t maxi)
 {
     using TX_ = Texel<DT>;
-    float c[3 + VG];
+    float c[3 + 4 * ((VG + 3) / 4)];
+    c[0] = hdr.x;
+    c[1] = hdr.y;
+    c[2] = hdr.z;
 #pragma unroll
-    for (int e = 0; e < 3 + VG; ++e) c[e] = lds_f(ca + 4u * e);
+    for (int e = 0; e < (VG + 3) / 4; ++e) {
+        const float4 v = lds_f4(ca + 16u * (1 + e));
+        c[3 + 4 * e + 0] = v.x;
+        c[3 + 4 * e + 1] = v.y;
+        c[3 + 4 * e + 2] = v.z;
+        c[3 + 4 * e + 3] = v.w;
+    }
     const float gmx = c[0];
     const float xf = (float)x;
     const int base_x = p.P_s * x + G.padl - kMagicBits;
@@ -411,13 +428,13 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
 {
     constexpr int TB = Texel<DT>::kBytes;
     extern __shared__ __align__(128) unsigned char smem[];
-    // [stages][rows][row_bytes] | full[stages] | empty[stages] | coef [N][VG+3] | plist [N] | wide [N]
+    // [stages][rows][row_bytes] | full[stages] | empty[stages] | coef [N][CW] | plist [N]
+    constexpr int CW = CoefBlock<VG>::kFloats;
     unsigned char* stage_base = smem;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * G.stage_bytes);
     uint64_t* empty = full + kStages;
-    float* coef = reinterpret_cast<float*>(empty + kStages);
-    int* plist = reinterpret_cast<int*>(coef + (size_t)p.N * (VG + 3));
-    int* pwide = plist + p.N;
+    float* coef = reinterpret_cast<float*>(empty + kStages);   // 16-byte aligned (stage_bytes, 2 kStages * 8)
+    int* plist = reinterpret_cast<int*>(coef + (size_t)p.N * CW);
     __shared__ int s_nplanes;
 
     const int tid = threadIdx.x, lane = tid & 31;
@@ -428,21 +445,7 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
     const int X0 = blockIdx.z * G.TX;
     const int tx = tid % G.TX, ty = tid / G.TX;
     const int x = X0 + tx, y = Y0 + ty;
-    const int CW = VG + 3;
 
-    // coefficients of this CTA's views: [gm_x, gm_y, h_y, h_x[VG]] per plane
-    for (int e = tid; e < p.N * VG; e += kStagedBlock) {
-        const int k = e / VG, jj = e % VG;
-        const int j = min(j0 + jj, p.Vx - 1);
-        const float* cx = w.cx + 3 * ((size_t)j * p.N + k);
-        coef[k * CW + 3 + jj] = BILINEAR ? cx[2] : cx[1];
-        if (jj == 0) {
-            const float* cy = w.cy + 3 * ((size_t)vi * p.N + k);
-            coef[k * CW + 0] = cx[0];
-            coef[k * CW + 1] = cy[0];
-            coef[k * CW + 2] = BILINEAR ? cy[2] : cy[1];
-        }
-    }
     // list of non-empty planes in order (warp 0, ballot compaction)
     if (tid < 32) {
         int n = 0;
@@ -450,14 +453,26 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
             const int k = b + tid;
             const bool ne = k < p.N && count[k] != 0;
             const unsigned m = __ballot_sync(0xffffffffu, ne);
-            if (ne) {
-                const int pos = n + __popc(m & ((1u << tid) - 1u));
-                plist[pos] = k;
-                pwide[pos] = w.wide[k];
-            }
+            if (ne) plist[n + __popc(m & ((1u << tid) - 1u))] = k;
             n += __popc(m);
         }
         if (tid == 0) s_nplanes = n;
+    }
+    __syncthreads();
+    // coefficient blocks of this CTA's views, in list order
+    for (int e = tid; e < s_nplanes * VG; e += kStagedBlock) {
+        const int q = e / VG, jj = e % VG;
+        const int k = plist[q];
+        const int j = min(j0 + jj, p.Vx - 1);
+        const float* cx = w.cx + 3 * ((size_t)j * p.N + k);
+        coef[q * CW + 4 + jj] = BILINEAR ? cx[2] : cx[1];
+        if (jj == 0) {
+            const float* cy = w.cy + 3 * ((size_t)vi * p.N + k);
+            coef[q * CW + 0] = cx[0];
+            coef[q * CW + 1] = cy[0];
+            coef[q * CW + 2] = BILINEAR ? cy[2] : cy[1];
+            coef[q * CW + 3] = __int_as_float(w.wide[k]);
+        }
     }
     // zero pads of every staged row (the bulk copies never write them)
     const int nrows = G.BY * G.rows_per_y;
@@ -482,7 +497,7 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
     // producer: stage the plane rows of list entry q into stage q % kStages
     auto produce = [&](int q) {
         const int k = plist[q];
-        const float* c = coef + (size_t)k * CW;
+        const float* c = coef + (size_t)q * CW;
         unsigned char* sb = stage_base + (size_t)(q % kStages) * G.stage_bytes;
         const uint32_t bar = smem_addr(&full[q % kStages]);
         uint32_t bytes = 0;
@@ -530,7 +545,6 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
 #pragma unroll
     for (int jj = 0; jj < VG; ++jj) acc[jj][0] = acc[jj][1] = acc[jj][2] = 0.f, acc[jj][3] = 1.f;
     const uint32_t stage_a = smem_addr(stage_base), coef_a = smem_addr(coef);
-    const uint32_t plist_a = smem_addr(plist), pwide_a = smem_addr(pwide);
     const bool live = ty < G.BY && x < p.Nx && y < p.Ny;   // threads past BY rows idle
     const uint32_t maxi = (uint32_t)(G.padl + p.W);       // first right-pad texel
     bool ok = true;
@@ -544,12 +558,13 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
             break;
         }
         if (live) {
-            const uint32_t ca = coef_a + 4u * (uint32_t)(lds_i(plist_a + 4u * q) * CW);
+            const uint32_t ca = coef_a + 4u * (uint32_t)(q * CW);
             const uint32_t sb = stage_a + (uint32_t)(s * G.stage_bytes);
-            if (lds_i(pwide_a + 4u * q))
-                blend_plane<DT, BILINEAR, VG, true>(acc, ca, sb, G, p, x, y, ty, maxi);
+            const float4 hdr = lds_f4(ca);
+            if (__float_as_int(hdr.w))
+                blend_plane<DT, BILINEAR, VG, true>(acc, hdr, ca, sb, G, p, x, y, ty, maxi);
             else
-                blend_plane<DT, BILINEAR, VG, false>(acc, ca, sb, G, p, x, y, ty, maxi);
+                blend_plane<DT, BILINEAR, VG, false>(acc, hdr, ca, sb, G, p, x, y, ty, maxi);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
@@ -581,8 +596,8 @@ bool launch_staged_vg(const CompParams& p, const void* planes, const int32_t* co
     G.row_bytes = (size_t)G.row_texels * TB;
     G.stage_bytes = G.row_bytes * G.BY * G.rows_per_y;
     G.groups_x = (p.Vx + VG - 1) / VG;
-    G.smem_bytes = kStages * G.stage_bytes + 2 * kStages * 8 + sizeof(float) * (size_t)p.N * (VG + 3) +
-                   2 * sizeof(int) * (size_t)p.N;
+    G.smem_bytes = kStages * G.stage_bytes + 2 * kStages * 8 + sizeof(float) * (size_t)p.N * CoefBlock<VG>::kFloats +
+                   sizeof(int) * (size_t)p.N;
     if (G.smem_bytes > 200 * 1024) return false;
     // bulk copies need 16-byte aligned rows: plane base and row pitch
     if (((uintptr_t)planes) % 16 != 0 || ((size_t)p.W * TB) % 16 != 0) return false;
