@@ -155,8 +155,8 @@ lf_status lf_make_ref_camera(const lf_camera* cam, const lf_display* disp, lf_re
 /* ---- splat: radiance field -> sweeping planes (Algorithm 1 lines 1-5) --- */
 
 /* Workspace bytes for lf_build_mpi_* on n primitives into N planes of the
- * reference camera ref, with room for dup_capacity (primitive, 16x16 tile)
- * pairs (0 = 8 n + 2^20). */
+ * reference camera ref, with room for dup_capacity (primitive, 64x64
+ * super-tile) pairs (0 = 8 n + 2^20). */
 size_t lf_build_mpi_workspace_size(const lf_ref_camera* ref, int64_t n, int32_t N, int64_t dup_capacity);
 
 /* Sec. 4.4 (G2LF). Culls Gaussians to the reference frustum (reference depth
@@ -188,15 +188,17 @@ lf_status lf_build_mpi_voxels(const lf_voxels* v, const lf_ref_camera* ref, int3
  * and *culled_in (host, may be NULL) the number M of primitives kept. */
 lf_status lf_mpi_status(const void* ws, int64_t* needed, int64_t* culled_in);
 
-/* Copies the build's sorted order and tile lists out of ws (synchronous).
- * order [n] int32 (host): primitive index of ranks 0..M-1; tile_prims
- * [cap] int32 (host): primitive of every (tile, chunk) entry in list order;
- * seg [tiles * N][2] int32 (host): [start, end) of every (tile, chunk) list,
- * tiles = ceil(W/16) * ceil(H/16), segment index tile * N + chunk. Any output
- * may be NULL. Fails with LF_ERR_INVALID_ARG if cap is smaller than the pair
- * count. For tests and inspection. */
+/* Copies the build's depth order and its 16x16 tile lists out of ws
+ * (synchronous; for tests and inspection). order [n] int32 (host): primitive
+ * index of ranks 0..M-1. tile_prims [cap] int32 (host): for every tile
+ * (row-major over ceil(W/16) x ceil(H/16)) and chunk, the primitives of that
+ * chunk whose footprint meets the tile, in depth order; seg [tiles * N][2]
+ * int32 (host): [start, end) of list (tile, chunk) at index tile * N + chunk;
+ * *n_pairs (host): total entries. Any output may be NULL. Fails with
+ * LF_ERR_INVALID_ARG if cap is smaller than the entry count, LF_ERR_OVERFLOW
+ * after an overflowed build. */
 lf_status lf_mpi_tile_lists(const void* ws, int32_t* order, int64_t n, int32_t* tile_prims, int64_t cap,
-                            int32_t* seg);
+                            int32_t* seg, int64_t* n_pairs);
 
 /* ---- composite: planes -> quilt views (Algorithm 1 lines 6-11) --------- */
 

@@ -208,16 +208,18 @@ def lf_mpi_status(ws: torch.Tensor):
 
 
 def lf_mpi_tile_lists(ws: torch.Tensor, n: int, n_tiles: int, N: int):
-    """Sorted order, tile-list entries and (tile, chunk) segments (numpy)."""
+    """Depth order, 16x16 tile-list entries and (tile, chunk) segments (numpy)."""
     st, needed, M = lf_mpi_status(ws)
     check(st)
+    total = ctypes.c_int64(0)
+    check(load().lf_mpi_tile_lists(_ptr(ws), None, 0, None, 0, None, ctypes.byref(total)))
     order = np.zeros(max(n, 1), np.int32)
-    prims = np.zeros(max(needed, 1), np.int32)
+    prims = np.zeros(max(total.value, 1), np.int32)
     seg = np.zeros((n_tiles * N, 2), np.int32)
     check(load().lf_mpi_tile_lists(_ptr(ws), order.ctypes.data_as(ctypes.c_void_p), int(n),
                                    prims.ctypes.data_as(ctypes.c_void_p), int(prims.shape[0]),
-                                   seg.ctypes.data_as(ctypes.c_void_p)))
-    return order[:M], prims[:needed], seg
+                                   seg.ctypes.data_as(ctypes.c_void_p), ctypes.byref(total)))
+    return order[:M], prims[:total.value], seg
 
 
 # ---------------------------------------------------------------------------

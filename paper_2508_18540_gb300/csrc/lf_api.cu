@@ -87,8 +87,8 @@ static T* carve(char* base, size_t& off, size_t count)
 size_t build_ws_layout(int64_t n, int32_t N, int32_t W, int32_t H, int64_t cap, void* basev, BuildWs* o)
 {
     char* base = static_cast<char*>(basev);
-    const long long tiles = (long long)((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
-    const long long S = tiles * N;                                  // (tile, chunk) lists
+    const long long supers = (long long)((W + kSuper - 1) / kSuper) * ((H + kSuper - 1) / kSuper);
+    const long long S = supers * N;                                 // (super-tile, chunk) lists
     const long long nmax = n > cap ? n : cap;
     const long long nb = (nmax + kRadixBlockKeys - 1) / kRadixBlockKeys + 1;
     const long long nbd = (n + kDupBlock - 1) / kDupBlock + 1;
@@ -204,6 +204,7 @@ static void fill_raster_params(const lf_ref_camera* r, int32_t N, int32_t dtype,
     p->N = N;
     p->tiles_x = (r->W + kTile - 1) / kTile;
     p->tiles_y = (r->H + kTile - 1) / kTile;
+    p->supers_x = (r->W + kSuper - 1) / kSuper;
     p->dtype = dtype;
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) p->Rt[3 * i + j] = (float)r->base.R[3 * j + i];
@@ -264,11 +265,13 @@ static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, in
     h.H = ref->H;
     h.tiles_x = (ref->W + kTile - 1) / kTile;
     h.tiles_y = (ref->H + kTile - 1) / kTile;
+    h.supers_x = (ref->W + kSuper - 1) / kSuper;
+    h.supers_y = (ref->H + kSuper - 1) / kSuper;
     h.binning = binning;
     // the header is written by a kernel so the whole build stays on the stream
     launch_init_header(h, w.hdr, stream);
     if ((st = check_launch("header init")) != LF_OK) return st;
-    const long long n_tiles = (long long)h.tiles_x * h.tiles_y;
+    const long long n_supers = (long long)h.supers_x * h.supers_y;
 
     ProjParams pp;
     fill_proj_params(ref, n, &pp);
@@ -295,7 +298,7 @@ static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, in
     if ((st = check_launch("bin")) != LF_OK) return st;
 
     trace_begin("tile_lists", stream);
-    const uint32_t* ranks = launch_tile_lists(w, n, cap, N, h.tiles_x, (int)n_tiles, stream);
+    const uint32_t* ranks = launch_tile_lists(w, n, cap, N, h.supers_x, (int)n_supers, stream);
     trace_end(stream);
     if ((st = check_launch("tile lists")) != LF_OK) return st;
 
@@ -461,7 +464,7 @@ lf_status lf_mpi_status(const void* ws, int64_t* needed, int64_t* culled_in)
 }
 
 lf_status lf_mpi_tile_lists(const void* ws, int32_t* order, int64_t n, int32_t* tile_prims, int64_t cap,
-                            int32_t* seg)
+                            int32_t* seg, int64_t* n_pairs)
 {
     int64_t needed = 0, M = 0;
     lf_status st = lf_mpi_status(ws, &needed, &M);
@@ -470,36 +473,54 @@ lf_status lf_mpi_tile_lists(const void* ws, int32_t* order, int64_t n, int32_t* 
     if (cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return check_launch("header read");
     BuildWs w;
     build_ws_layout(h.n, h.N, h.W, h.H, h.dup_capacity, const_cast<void*>(ws), &w);
+    std::vector<uint32_t> rank_prim((size_t)(M > 0 ? M : 1));
+    if (M > 0 && cudaMemcpy(rank_prim.data(), w.valA, sizeof(uint32_t) * (size_t)M, cudaMemcpyDeviceToHost) !=
+                     cudaSuccess)
+        return check_launch("order read");
     if (order) {
         if (n < M) return fail(LF_ERR_INVALID_ARG, "order buffer too small");
-        if (M > 0 && cudaMemcpy(order, w.valA, sizeof(uint32_t) * (size_t)M, cudaMemcpyDeviceToHost) != cudaSuccess)
-            return check_launch("order read");
+        std::memcpy(order, rank_prim.data(), sizeof(uint32_t) * (size_t)M);
     }
-    if (tile_prims) {
-        // the lists hold ranks; map them to primitive indices through the
-        // depth order
-        if (cap < needed) return fail(LF_ERR_INVALID_ARG, "tile list buffer too small");
-        if (needed > 0) {
-            std::vector<uint32_t> rank_prim((size_t)(M > 0 ? M : 1));
-            const uint32_t* ranks = tile_sort_passes(tile_bits_for((long long)h.tiles_x * h.tiles_y)) % 2 ? w.entB
-                                                                                                          : w.entA;
-            if (cudaMemcpy(tile_prims, ranks, sizeof(uint32_t) * (size_t)needed, cudaMemcpyDeviceToHost) !=
-                    cudaSuccess ||
-                cudaMemcpy(rank_prim.data(), w.valA, sizeof(uint32_t) * (size_t)M, cudaMemcpyDeviceToHost) !=
-                    cudaSuccess)
-                return check_launch("tile list read");
-            for (int64_t i = 0; i < needed; ++i) {
-                const uint32_t rk = (uint32_t)tile_prims[i];
-                if (rk >= (uint64_t)M) return fail(LF_ERR_CUDA, "corrupt tile list entry");
-                tile_prims[i] = (int32_t)rank_prim[rk];
+    if (!tile_prims && !seg && !n_pairs) return LF_OK;
+    // device lists are per (super-tile, chunk); filter them per 16x16 tile on
+    // the host with the footprint rectangles, keeping their (depth) order
+    const int n_supers = h.supers_x * h.supers_y;
+    std::vector<int2> sseg((size_t)n_supers * h.N);
+    std::vector<uint32_t> sranks((size_t)(needed > 0 ? needed : 1));
+    std::vector<int4> rrect((size_t)(M > 0 ? M : 1));
+    const uint32_t* dranks = tile_sort_passes(tile_bits_for(n_supers)) % 2 ? w.entB : w.entA;
+    if (cudaMemcpy(sseg.data(), w.seg, sizeof(int2) * sseg.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (needed > 0 &&
+         cudaMemcpy(sranks.data(), dranks, sizeof(uint32_t) * (size_t)needed, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (M > 0 && cudaMemcpy(rrect.data(), w.r_rect, sizeof(int4) * (size_t)M, cudaMemcpyDeviceToHost) != cudaSuccess))
+        return check_launch("tile list read");
+    int64_t total = 0;
+    for (int ty = 0; ty < h.tiles_y; ++ty)
+        for (int tx = 0; tx < h.tiles_x; ++tx) {
+            const int s = (ty / kTilesPerSuper) * h.supers_x + tx / kTilesPerSuper;
+            const int x0 = tx * kTile, x1 = x0 + kTile - 1, y0 = ty * kTile, y1 = y0 + kTile - 1;
+            for (int c = 0; c < h.N; ++c) {
+                const int2 r = sseg[(size_t)s * h.N + c];
+                const int64_t start = total;
+                for (int i = r.x; i < r.y; ++i) {
+                    const uint32_t rk = sranks[(size_t)i];
+                    if (rk >= (uint64_t)M) return fail(LF_ERR_CUDA, "corrupt tile list entry");
+                    const int4 q = rrect[rk];
+                    if (q.x > x1 || q.z < x0 || q.y > y1 || q.w < y0) continue;
+                    if (tile_prims) {
+                        if (total >= cap) return fail(LF_ERR_INVALID_ARG, "tile list buffer too small");
+                        tile_prims[total] = (int32_t)rank_prim[rk];
+                    }
+                    ++total;
+                }
+                if (seg) {
+                    const size_t t = ((size_t)ty * h.tiles_x + tx) * h.N + c;
+                    seg[2 * t] = (int32_t)start;
+                    seg[2 * t + 1] = (int32_t)total;
+                }
             }
         }
-    }
-    if (seg) {
-        const size_t ns = (size_t)h.tiles_x * h.tiles_y * h.N;
-        if (cudaMemcpy(seg, w.seg, sizeof(int2) * ns, cudaMemcpyDeviceToHost) != cudaSuccess)
-            return check_launch("segment read");
-    }
+    if (n_pairs) *n_pairs = total;
     return LF_OK;
 }
 

@@ -15,8 +15,10 @@
 
 namespace lf {
 
-constexpr int kTile = 16;                 // splat tile edge (pixels)
-constexpr int kTilePix = kTile * kTile;   // threads per rasterisation CTA
+constexpr int kTile = 16;                 // raster tile edge (pixels): one CTA per (tile, chunk)
+constexpr int kTilePix = kTile * kTile;
+constexpr int kSuper = 64;                // list super-tile edge (pixels): lists per (super-tile, chunk)
+constexpr int kTilesPerSuper = kSuper / kTile;
 constexpr int kRadixBlockKeys = 4096;     // keys per radix-sort block
 constexpr int kSortDigits = 256;          // 8-bit radix digits
 constexpr int kDupBlock = 1024;           // ranks per block of the tile-pair emission
@@ -46,7 +48,7 @@ struct WsHeader {
     int kind;                     // 0 gaussians, 1 voxels
     long long n;
     long long dup_capacity;
-    int N, W, H, tiles_x, tiles_y;
+    int N, W, H, tiles_x, tiles_y, supers_x, supers_y;
     int binning;
 };
 
@@ -74,7 +76,7 @@ struct BuildWs {
     uint32_t* tkeyB;
     uint32_t* entA;               // [cap] rank of every pair
     uint32_t* entB;
-    int2* seg;                    // [tiles * N] (start, end) of every (tile, chunk) list
+    int2* seg;                    // [supers * N] (start, end) of every (super-tile, chunk) list
     size_t bytes;
     long long nb_sort, nb_dup;
 };
@@ -100,7 +102,7 @@ struct ProjParams {
 };
 
 struct RasterParams {
-    int W, H, N, tiles_x, tiles_y, dtype;
+    int W, H, N, tiles_x, tiles_y, supers_x, dtype;
     // voxels: world-frame reference rays
     float Rt[9];                    // R^T row-major (camera -> world)
     float fx, fy, cx, cy;
@@ -125,9 +127,10 @@ void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s);
 
 void launch_bin(const BuildWs& ws, const BinParams& p, long long n, int32_t* chunk, double* d, int32_t* count,
                 const int32_t* rect, const float* rgb, const float* dens8, int kind, cudaStream_t s);
-// (tile, chunk) lists: (tile, rank) pairs emitted in rank order, stable sort
-// by tile, [start, end) of every (tile, chunk) list. Returns the sorted ranks.
-const uint32_t* launch_tile_lists(const BuildWs& ws, long long n, long long cap, int N, int tiles_x, int n_tiles,
+// (super-tile, chunk) lists: (super-tile, rank) pairs emitted in rank order,
+// stable sort by super-tile, [start, end) of every (super-tile, chunk) list.
+// Returns the sorted ranks.
+const uint32_t* launch_tile_lists(const BuildWs& ws, long long n, long long cap, int N, int supers_x, int n_supers,
                                   cudaStream_t s);
 void sort_tile_keys(const BuildWs& ws, long long cap, int tile_bits, cudaStream_t s, uint32_t** keys_out,
                     uint32_t** vals_out);

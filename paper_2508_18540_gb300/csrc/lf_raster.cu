@@ -1,9 +1,11 @@
 // lf_raster.cu -- 3D-tiled rasterisation of every chunk into its sweeping
 // plane (Algorithm 1 lines 4-5, "Parallel for all k: Rasterize(H, P'_k)").
 //
-// One CTA per (16x16 tile, chunk). Its (tile, chunk) list holds ranks in
-// depth order; the listed primitives (rank-ordered copies) are staged through
-// shared memory in batches and every thread blends its pixels front to back:
+// One CTA per (16x16 tile, chunk). It walks the (64x64 super-tile, chunk)
+// list holding its tile (ranks in depth order) in batches, keeps the entries
+// whose footprint meets its tile (order-preserving compaction), stages those
+// primitives (rank-ordered copies) in shared memory, and every thread blends
+// its pixels front to back:
 //   Gaussians (Sec. 4.4, 3DGS model): alpha = min(0.99, o exp(-q/2)),
 //     q = d^T Sigma_2^{-1} d inside the primitive's footprint rectangle;
 //   voxels (Sec. 4.5, SVR model): alpha = 1 - exp(-integral of the trilinear
@@ -40,6 +42,31 @@ __device__ __forceinline__ void store_texel(void* planes, size_t idx, float r, f
     }
 }
 
+// Order-preserving compaction of a batch: returns this thread's slot among
+// the batch's hits (valid if hit) and the hit count. s_wc: [NT / 32] ints.
+template <int NT>
+__device__ __forceinline__ int compact_slot(bool hit, int* s_wc, int* count)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) s_wc[warp] = __popc(bal);
+    __syncthreads();
+    int off = 0, cnt = 0;
+#pragma unroll
+    for (int q = 0; q < NT / 32; ++q) {
+        const int v = s_wc[q];
+        off += q < warp ? v : 0;
+        cnt += v;
+    }
+    *count = cnt;
+    return off + __popc(bal & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ bool meets_tile(int4 r, int x0, int y0)
+{
+    return r.x <= x0 + kTile - 1 && r.z >= x0 && r.y <= y0 + kTile - 1 && r.w >= y0;
+}
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
@@ -65,6 +92,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, Rast
     __shared__ float4 s_e0[NT];
     __shared__ float4 s_e1[NT];
     __shared__ float4 s_rgb[NT];
+    __shared__ int s_wc[NT / 32];
     const int t = blockIdx.x, k = blockIdx.y;
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -72,7 +100,8 @@ __global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, Rast
     const int py0 = ty * kTile + (threadIdx.x / kTile) * PPT;
     const int sx0 = tx * kTile, sx1 = sx0 + kTile - 1;                // warp strip bounds
     const int sy0 = ty * kTile + 2 * PPT * warp, sy1 = sy0 + 2 * PPT - 1;
-    const int2 sg = w.seg[(size_t)t * p.N + k];
+    const int st = (ty / kTilesPerSuper) * p.supers_x + tx / kTilesPerSuper;
+    const int2 sg = w.seg[(size_t)st * p.N + k];
     const int L = sg.y - sg.x;
     const float fpx = (float)px;
     float C[PPT][3], T[PPT];
@@ -80,18 +109,24 @@ __global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, Rast
     for (int r = 0; r < PPT; ++r) C[r][0] = C[r][1] = C[r][2] = 0.f, T[r] = 1.f;
     for (int base = 0; base < L; base += NT) {
         const int i = base + threadIdx.x;
+        uint32_t rk = 0;
+        int4 r = make_int4(0, 0, -1, -1);
         if (i < L) {
-            const uint32_t rk = ranks[sg.x + i];
+            rk = ranks[sg.x + i];
+            r = w.r_rect[rk];
+        }
+        const bool hit = i < L && meets_tile(r, sx0, ty * kTile);
+        int cnt;
+        const int slot = compact_slot<NT>(hit, s_wc, &cnt);
+        if (hit) {
             const float4 geo = w.r_geo[rk];
             const float4 c = w.r_con[rk];
-            const int4 r = w.r_rect[rk];
-            s_e0[threadIdx.x] = make_float4(geo.x, geo.y, -0.5f * kL2E * c.x, -kL2E * c.y);
-            s_e1[threadIdx.x] = make_float4(-0.5f * kL2E * c.z, c.w, __int_as_float((r.x & 0xffff) | (r.y << 16)),
-                                            __int_as_float(((r.z - r.x) & 0xffff) | ((r.w - r.y) << 16)));
-            s_rgb[threadIdx.x] = w.r_rgb[rk];
+            s_e0[slot] = make_float4(geo.x, geo.y, -0.5f * kL2E * c.x, -kL2E * c.y);
+            s_e1[slot] = make_float4(-0.5f * kL2E * c.z, c.w, __int_as_float((r.x & 0xffff) | (r.y << 16)),
+                                     __int_as_float(((r.z - r.x) & 0xffff) | ((r.w - r.y) << 16)));
+            s_rgb[slot] = w.r_rgb[rk];
         }
         __syncthreads();
-        const int cnt = min(NT, L - base);
         for (int m0 = 0; m0 < cnt; m0 += 32) {
             const int jl = m0 + lane;
             bool hit = false;
@@ -162,11 +197,13 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
     __shared__ float s_den[NT * 8];
     __shared__ float4 s_rgb[NT];
     __shared__ int4 s_rect[NT];
+    __shared__ int s_wc[NT / 32];
     const int t = blockIdx.x, k = blockIdx.y;
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
     const int py = ty * kTile + (threadIdx.x / kTile);
-    const int2 sg = w.seg[(size_t)t * p.N + k];
+    const int st = (ty / kTilesPerSuper) * p.supers_x + tx / kTilesPerSuper;
+    const int2 sg = w.seg[(size_t)st * p.N + k];
     const int L = sg.y - sg.x;
 
     // world-frame direction of the reference ray through this pixel centre
@@ -185,18 +222,25 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
     for (int base = 0; base < L; base += NT) {
         const int i = base + threadIdx.x;
+        uint32_t rk = 0;
+        int4 r = make_int4(0, 0, -1, -1);
         if (i < L) {
-            const uint32_t rk = ranks[sg.x + i];
-            s_box[threadIdx.x] = w.r_geo[rk];
+            rk = ranks[sg.x + i];
+            r = w.r_rect[rk];
+        }
+        const bool hit = i < L && meets_tile(r, tx * kTile, ty * kTile);
+        int cnt;
+        const int slot = compact_slot<NT>(hit, s_wc, &cnt);
+        if (hit) {
+            s_box[slot] = w.r_geo[rk];
             const float4 da = w.r_den[2 * (size_t)rk], db = w.r_den[2 * (size_t)rk + 1];
-            float* sd = s_den + 8 * threadIdx.x;
+            float* sd = s_den + 8 * slot;
             sd[0] = da.x; sd[1] = da.y; sd[2] = da.z; sd[3] = da.w;
             sd[4] = db.x; sd[5] = db.y; sd[6] = db.z; sd[7] = db.w;
-            s_rgb[threadIdx.x] = w.r_rgb[rk];
-            s_rect[threadIdx.x] = w.r_rect[rk];
+            s_rgb[slot] = w.r_rgb[rk];
+            s_rect[slot] = r;
         }
         __syncthreads();
-        const int cnt = min(NT, L - base);
         for (int j = 0; j < cnt; ++j) {
             const int4 rc = s_rect[j];
             if (!(px >= rc.x && px <= rc.z && py >= rc.y && py <= rc.w)) continue;

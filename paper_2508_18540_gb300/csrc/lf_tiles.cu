@@ -1,16 +1,17 @@
-// lf_tiles.cu -- 3D tiling (Sec. 4.4): for every (16x16 tile, chunk) pair,
-// the list of the chunk's primitives whose footprint rectangle meets the
-// tile, in depth order.
+// lf_tiles.cu -- 3D tiling (Sec. 4.4), two levels: lists are built per
+// (64x64 super-tile, chunk) and every raster CTA (16x16 tile, chunk) filters
+// its super-tile's list down to the primitives whose footprint meets its
+// tile, keeping the order.
 //
 //  k_dup_count / k_dup_scan / k_dup_emit
-//      one (tile id, rank) pair per tile a primitive's footprint touches,
-//      written in rank (depth) order: per-block totals, one scan, then every
-//      block writes its pairs at its offset;
+//      one (super-tile id, rank) pair per super-tile a primitive's footprint
+//      touches, written in rank (depth) order: per-block totals, one scan,
+//      then every block writes its pairs at its offset;
 //  sort_tile_keys (lf_sort.cu)
-//      stable radix sort of the pairs by tile id: every tile's pairs stay in
+//      stable radix sort of the pairs by super-tile id: every list stays in
 //      depth order, and chunks (monotone in rank) form contiguous runs;
 //  k_ranges
-//      [start, end) of every (tile, chunk) run.
+//      [start, end) of every (super-tile, chunk) run.
 #include "lf_internal.cuh"
 
 namespace lf {
@@ -23,7 +24,7 @@ constexpr int kPer = kDupBlock / kT;   // consecutive ranks per thread
 __device__ __forceinline__ uint32_t tile_count(int4 rc)
 {
     if (rc.z < rc.x || rc.w < rc.y) return 0u;
-    return (uint32_t)((rc.z / kTile - rc.x / kTile + 1) * (rc.w / kTile - rc.y / kTile + 1));
+    return (uint32_t)((rc.z / kSuper - rc.x / kSuper + 1) * (rc.w / kSuper - rc.y / kSuper + 1));
 }
 
 // exclusive scan of one value per thread over a 256-thread block
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(1024) k_dup_scan(BuildWs w, int nb)
     }
 }
 
-__global__ void __launch_bounds__(kT) k_dup_emit(BuildWs w, int tiles_x)
+__global__ void __launch_bounds__(kT) k_dup_emit(BuildWs w, int supers_x)
 {
     if (w.hdr->overflow) return;
     const long long M = (long long)w.hdr->M;
@@ -120,10 +121,10 @@ __global__ void __launch_bounds__(kT) k_dup_emit(BuildWs w, int tiles_x)
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         if (rc[j].z < rc[j].x || rc[j].w < rc[j].y) continue;
-        const int tx0 = rc[j].x / kTile, tx1 = rc[j].z / kTile, ty0 = rc[j].y / kTile, ty1 = rc[j].w / kTile;
-        for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) {
-                w.tkeyA[off] = (uint32_t)(ty * tiles_x + tx);
+        const int sx0 = rc[j].x / kSuper, sx1 = rc[j].z / kSuper, sy0 = rc[j].y / kSuper, sy1 = rc[j].w / kSuper;
+        for (int sy = sy0; sy <= sy1; ++sy)
+            for (int sx = sx0; sx <= sx1; ++sx) {
+                w.tkeyA[off] = (uint32_t)(sy * supers_x + sx);
                 w.entA[off] = (uint32_t)(r0 + j);
                 ++off;
             }
@@ -160,18 +161,18 @@ int tile_bits_for(long long tiles)
     return b;
 }
 
-const uint32_t* launch_tile_lists(const BuildWs& ws, long long n, long long cap, int N, int tiles_x, int n_tiles,
+const uint32_t* launch_tile_lists(const BuildWs& ws, long long n, long long cap, int N, int supers_x, int n_supers,
                                   cudaStream_t s)
 {
-    cudaMemsetAsync(ws.seg, 0, sizeof(int2) * (size_t)n_tiles * N, s);
+    cudaMemsetAsync(ws.seg, 0, sizeof(int2) * (size_t)n_supers * N, s);
     const int nb = (int)(((n > 0 ? n : 1) + kDupBlock - 1) / kDupBlock);
     k_dup_count<<<nb, kT, 0, s>>>(ws);
     k_dup_scan<<<1, 1024, 0, s>>>(ws, nb);
-    k_dup_emit<<<nb, kT, 0, s>>>(ws, tiles_x);
+    k_dup_emit<<<nb, kT, 0, s>>>(ws, supers_x);
     note_launches(3);
     uint32_t* keys = nullptr;
     uint32_t* ranks = nullptr;
-    sort_tile_keys(ws, cap, tile_bits_for(n_tiles), s, &keys, &ranks);
+    sort_tile_keys(ws, cap, tile_bits_for(n_supers), s, &keys, &ranks);
     if (cap > 0) {
         const long long want = (cap + 255) / 256;
         const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);

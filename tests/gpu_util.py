@@ -26,7 +26,7 @@ def run_gpu(scene, camera, display, views, N, binning, dtype="f32", dup_capacity
     tiles_x = (r.ref.W + TILE - 1) // TILE
     tiles_y = (r.ref.H + TILE - 1) // TILE
     order, prims_l, seg = api.lf_mpi_tile_lists(r.ws, n, tiles_x * tiles_y, N)
-    out.update(order=order, tile_prims=prims_l, seg=seg, tiles_x=tiles_x, tiles_y=tiles_y)
+    out.update(order=order, tile_prims=prims_l, seg=seg, tiles_x=tiles_x, tiles_y=tiles_y, n_pairs=len(prims_l))
     return out
 
 
@@ -57,7 +57,7 @@ def check_tile_lists(gpu, orc_out, W, H, N):
             got = gpu["tile_prims"][s:e].tolist() if e > s else []
             assert got == want, (t, c)
             total += len(want)
-    assert total == gpu["needed"]
+    assert total == gpu["n_pairs"]
 
 
 def psnr(a, b):
