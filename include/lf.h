@@ -155,7 +155,7 @@ lf_status lf_make_ref_camera(const lf_camera* cam, const lf_display* disp, lf_re
 /* ---- splat: radiance field -> sweeping planes (Algorithm 1 lines 1-5) --- */
 
 /* Workspace bytes for lf_build_mpi_* on n primitives into N planes of the
- * reference camera ref, with room for dup_capacity (primitive, 64x64
+ * reference camera ref, with room for dup_capacity (primitive, 32x32
  * super-tile) pairs (0 = 8 n + 2^20). */
 size_t lf_build_mpi_workspace_size(const lf_ref_camera* ref, int64_t n, int32_t N, int64_t dup_capacity);
 

@@ -17,7 +17,7 @@ namespace lf {
 
 constexpr int kTile = 16;                 // raster tile edge (pixels): one CTA per (tile, chunk)
 constexpr int kTilePix = kTile * kTile;
-constexpr int kSuper = 64;                // list super-tile edge (pixels): lists per (super-tile, chunk)
+constexpr int kSuper = 32;                // list super-tile edge (pixels): lists per (super-tile, chunk)
 constexpr int kTilesPerSuper = kSuper / kTile;
 constexpr int kRadixBlockKeys = 4096;     // keys per radix-sort block
 constexpr int kSortDigits = 256;          // 8-bit radix digits

@@ -1,7 +1,7 @@
 // lf_raster.cu -- 3D-tiled rasterisation of every chunk into its sweeping
 // plane (Algorithm 1 lines 4-5, "Parallel for all k: Rasterize(H, P'_k)").
 //
-// One CTA per (16x16 tile, chunk). It walks the (64x64 super-tile, chunk)
+// One CTA per (16x16 tile, chunk). It walks the (32x32 super-tile, chunk)
 // list holding its tile (ranks in depth order) in batches, keeps the entries
 // whose footprint meets its tile (order-preserving compaction), stages those
 // primitives (rank-ordered copies) in shared memory, and every thread blends

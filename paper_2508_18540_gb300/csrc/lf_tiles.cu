@@ -1,5 +1,5 @@
 // lf_tiles.cu -- 3D tiling (Sec. 4.4), two levels: lists are built per
-// (64x64 super-tile, chunk) and every raster CTA (16x16 tile, chunk) filters
+// (32x32 super-tile, chunk) and every raster CTA (16x16 tile, chunk) filters
 // its super-tile's list down to the primitives whose footprint meets its
 // tile, keeping the order.
 //
