@@ -159,7 +159,7 @@ def gauss_decide(ref: OrcRef, scene):
 
 def gauss_values(ref: OrcRef, scene):
     n = scene.n
-    means, scales, quats = (_c(a, np.float32) for a in (scene.means, scene.scales, scene.quats))
+    means, scales, quats = (_c(a, np.float64) for a in (scene.means, scene.scales, scene.quats))
     mean2d = np.zeros((n, 2), np.float64)
     conic = np.zeros((n, 3), np.float64)
     cov2d = np.zeros((n, 3), np.float64)
@@ -198,7 +198,7 @@ def splat_gaussians(ref: OrcRef, order, chunk, rect, mean2d, conic, opacity, rgb
     order = _c(order, np.int64)
     planes = np.zeros((N, ref.H, ref.W, 4), np.float64)
     args = [_c(chunk, np.int32), _c(rect, np.int32), _c(mean2d, np.float64), _c(conic, np.float64),
-            _c(opacity, np.float32), _c(rgb, np.float32)]
+            _c(opacity, np.float64), _c(rgb, np.float64)]
     lib().orc_splat_gaussians(ctypes.byref(ref), order.shape[0], _ptr(order), *[_ptr(a) for a in args], N,
                               _ptr(planes))
     return planes
@@ -209,8 +209,8 @@ def splat_voxels(ref: OrcRef, order, chunk, rect, scene, N: int) -> np.ndarray:
     planes = np.zeros((N, ref.H, ref.W, 4), np.float64)
     arrs = [_c(chunk, np.int32), _c(rect, np.int32), _c(scene.ijk, np.int32), _c(scene.level, np.uint8),
             _c(scene.origin, np.float64)]
-    dens = _c(scene.density8, np.float32)
-    rgb = _c(scene.rgb, np.float32)
+    dens = _c(scene.density8, np.float64)
+    rgb = _c(scene.rgb, np.float64)
     lib().orc_splat_voxels(ctypes.byref(ref), order.shape[0], _ptr(order), *[_ptr(a) for a in arrs],
                            float(scene.base_size), _ptr(dens), _ptr(rgb), N, _ptr(planes))
     return planes
@@ -218,7 +218,7 @@ def splat_voxels(ref: OrcRef, order, chunk, rect, scene, N: int) -> np.ndarray:
 
 def voxel_alpha(lo, side: float, density8, origin, direction):
     lo = _c(lo, np.float64)
-    dens = _c(density8, np.float32)
+    dens = _c(density8, np.float64)
     o = _c(origin, np.float64)
     d = _c(direction, np.float64)
     seg = ctypes.c_double(0.0)

@@ -91,9 +91,10 @@ void orc_gauss_decide(const orc_ref* r, int64_t n, const float* means, const flo
                       const float* quats, double* z, uint8_t* valid, int32_t* rect);
 
 /* Per-Gaussian FP64 values: mean2d[n][2] (plane pixels), conic[n][3] =
- * inverse 2D covariance {a, b, c}. Uses the EWA splatting projection. */
-void orc_gauss_values(const orc_ref* r, int64_t n, const float* means, const float* scales,
-                      const float* quats, double* mean2d, double* conic, double* cov2d);
+ * inverse 2D covariance {a, b, c}. Uses the EWA splatting projection.
+ * Parameters are FP64 (finite differences perturb them below FP32 spacing). */
+void orc_gauss_values(const orc_ref* r, int64_t n, const double* means, const double* scales,
+                      const double* quats, double* mean2d, double* conic, double* cov2d);
 
 /* Per-voxel decision data. Voxel v is the axis-aligned cube with low corner
  * origin + ijk * s and side s = base_size * 2^-level. */
@@ -113,17 +114,17 @@ int64_t orc_bin(const orc_ref* r, int64_t n, const double* z, const uint8_t* val
 /* Sec. 4.4: rasterise every chunk into its plane. planes[N][H][W][4] FP64. */
 void orc_splat_gaussians(const orc_ref* r, int64_t M, const int64_t* order, const int32_t* chunk,
                          const int32_t* rect, const double* mean2d, const double* conic,
-                         const float* opacity, const float* rgb, int32_t N, double* planes);
+                         const double* opacity, const double* rgb, int32_t N, double* planes);
 
 /* Sec. 4.5: rasterise voxels (ray-segment integral of trilinear density). */
 void orc_splat_voxels(const orc_ref* r, int64_t M, const int64_t* order, const int32_t* chunk,
                       const int32_t* rect, const int32_t* ijk, const uint8_t* level,
-                      const double* origin, double base_size, const float* density8,
-                      const float* rgb, int32_t N, double* planes);
+                      const double* origin, double base_size, const double* density8,
+                      const double* rgb, int32_t N, double* planes);
 
 /* Opacity of one voxel along one reference ray (exposed for pins):
  * ray origin o[3] and unit direction dir[3] in world coordinates. */
-double orc_voxel_alpha(const double* lo, double side, const float* density8,
+double orc_voxel_alpha(const double* lo, double side, const double* density8,
                        const double* o, const double* dir, double* seg_len);
 
 /* Sec. 4.3 swizzle blending, Algorithm 1 second loop.

@@ -128,12 +128,12 @@ void orc_gauss_decide(const orc_ref* r, int64_t n, const float* means, const flo
 /* EWA projection in FP64 (values): Sigma_3 = Q S^2 Q^T in the world frame,
  * Sigma_cam = R Sigma_3 R^T, Sigma_2 = J Sigma_cam J^T + f' I, 2D mean
  * (fx x/z + cx, fy y/z + cy); conic = Sigma_2^{-1}. */
-void orc_gauss_values(const orc_ref* r, int64_t n, const float* means, const float* scales,
-                      const float* quats, double* mean2d, double* conic, double* cov2d)
+void orc_gauss_values(const orc_ref* r, int64_t n, const double* means, const double* scales,
+                      const double* quats, double* mean2d, double* conic, double* cov2d)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t g = 0; g < n; ++g) {
-        const float* m = means + 3 * g;
+        const double* m = means + 3 * g;
         const double* R = r->cam.R;
         const double* t = r->cam.t;
         double pc[3];
@@ -141,17 +141,15 @@ void orc_gauss_values(const orc_ref* r, int64_t n, const float* means, const flo
             pc[i] = R[3 * i] * m[0] + R[3 * i + 1] * m[1] + R[3 * i + 2] * m[2] + t[i];
         pc[2] -= r->D_forward;
 
-        const float* qf = quats + 4 * g;
-        double qn = sqrt((double)qf[0] * qf[0] + (double)qf[1] * qf[1] + (double)qf[2] * qf[2] +
-                         (double)qf[3] * qf[3]);
+        const double* qf = quats + 4 * g;
+        double qn = sqrt(qf[0] * qf[0] + qf[1] * qf[1] + qf[2] * qf[2] + qf[3] * qf[3]);
         const double w = qf[0] / qn, x = qf[1] / qn, y = qf[2] / qn, z = qf[3] / qn;
         const double Q[3][3] = {
             {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
             {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
             {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
-        const double s2[3] = {(double)scales[3 * g] * scales[3 * g],
-                              (double)scales[3 * g + 1] * scales[3 * g + 1],
-                              (double)scales[3 * g + 2] * scales[3 * g + 2]};
+        const double s2[3] = {scales[3 * g] * scales[3 * g], scales[3 * g + 1] * scales[3 * g + 1],
+                              scales[3 * g + 2] * scales[3 * g + 2]};
         double S3[3][3], Sc[3][3], tmp[3][3];
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) {
@@ -207,7 +205,7 @@ void orc_gauss_values(const orc_ref* r, int64_t n, const float* means, const flo
  * each pixel exactly its ordered sequence of contributions. */
 void orc_splat_gaussians(const orc_ref* r, int64_t M, const int64_t* order, const int32_t* chunk,
                          const int32_t* rect, const double* mean2d, const double* conic,
-                         const float* opacity, const float* rgb, int32_t N, double* planes)
+                         const double* opacity, const double* rgb, int32_t N, double* planes)
 {
     const int64_t W = r->W, H = r->H;
     const int64_t plane_sz = W * H * 4;

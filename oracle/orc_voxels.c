@@ -83,14 +83,14 @@ void orc_voxel_decide(const orc_ref* r, int64_t n, const int32_t* ijk, const uin
 
 /* Trilinear density inside the cube at local coordinates f in [0,1]^3.
  * Corner c = i + 2 j + 4 k holds the density at offset (i, j, k). */
-static double trilinear(const float* rho8, const double* f)
+static double trilinear(const double* rho8, const double* f)
 {
     double acc = 0.0;
     for (int c = 0; c < 8; ++c) {
         const double wx = (c & 1) ? f[0] : 1.0 - f[0];
         const double wy = ((c >> 1) & 1) ? f[1] : 1.0 - f[1];
         const double wz = ((c >> 2) & 1) ? f[2] : 1.0 - f[2];
-        acc += wx * wy * wz * (double)rho8[c];
+        acc += wx * wy * wz * rho8[c];
     }
     return acc;
 }
@@ -107,7 +107,7 @@ static void local_coords(const double* lo, double side, const double* o, const d
 /* alpha = 1 - exp(-integral of sigma over the ray segment inside the cube).
  * Along a line the trilinear density is a cubic polynomial in t, so
  * Simpson's rule over the segment is exact. */
-double orc_voxel_alpha(const double* lo, double side, const float* density8,
+double orc_voxel_alpha(const double* lo, double side, const double* density8,
                        const double* o, const double* dir, double* seg_len)
 {
     double t0 = -INFINITY, t1 = INFINITY;
@@ -142,8 +142,8 @@ double orc_voxel_alpha(const double* lo, double side, const float* density8,
 
 void orc_splat_voxels(const orc_ref* r, int64_t M, const int64_t* order, const int32_t* chunk,
                       const int32_t* rect, const int32_t* ijk, const uint8_t* level,
-                      const double* origin, double base_size, const float* density8,
-                      const float* rgb, int32_t N, double* planes)
+                      const double* origin, double base_size, const double* density8,
+                      const double* rgb, int32_t N, double* planes)
 {
     const int64_t W = r->W, H = r->H;
     const int64_t plane_sz = W * H * 4;
