@@ -118,6 +118,25 @@ typedef struct {
     const float* rgb;
 } lf_voxels;
 
+/* Gradients with respect to the Gaussian parameters (device FP32, caller
+ * allocated, layouts of lf_gaussians): dmeans [n][3], dscales [n][3],
+ * dquats [n][4] (raw quaternion, through the normalisation), dopacity [n],
+ * drgb [n][3]. */
+typedef struct {
+    float* dmeans;
+    float* dscales;
+    float* dquats;
+    float* dopacity;
+    float* drgb;
+} lf_gaussians_grad;
+
+/* Gradients with respect to the voxel parameters (device FP32, caller
+ * allocated): ddensity8 [n][8], drgb [n][3]. */
+typedef struct {
+    float* ddensity8;
+    float* drgb;
+} lf_voxels_grad;
+
 /* Sweeping planes (Sec. 4.2 C and T), caller-allocated device memory:
  *  rgba  [N][H][W][4] of dtype (premultiplied RGB, A = 1 - T);
  *  d     [N] FP64 plane distances in the base camera frame (0 if empty);
@@ -216,6 +235,45 @@ size_t lf_composite_workspace_size(int32_t N, const lf_view_set* views);
  * Errors: LF_ERR_INVALID_ARG, LF_ERR_WORKSPACE, LF_ERR_CUDA. */
 lf_status lf_composite(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views, float* out,
                        void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---- differentiation ------------------------------------------------------ */
+/*
+ * Reverse-mode adjoints of the two stages, for fitting a scene against
+ * target light-field views. The integer structure of the forward pass
+ * (culling, chunk membership, plane depths d_k, footprint rectangles, tile
+ * lists, nearest indices) is held fixed: it is piecewise constant in the
+ * parameters and receives no gradient. Transmittance is recomputed inside
+ * the adjoint kernels, never stored by the forward pass. The clamp
+ * alpha = min(0.99, .) passes no gradient where it is active. Gradients are
+ * accumulated in FP32 with atomics, so their last bits depend on scheduling.
+ */
+
+/* Adjoint of lf_composite: given dviews = dL/d(views) [Vy*Vx][Ny][Nx][4]
+ * FP32 device, writes dplanes = dL/d(planes.rgba) [N][H][W][4] FP32 device
+ * (overwritten, whatever the plane dtype). planes, ref, views are those of
+ * the forward call; planes->rgba must still hold the forward's planes.
+ * ws: a composite workspace (lf_composite_workspace_size). Errors as
+ * lf_composite. */
+lf_status lf_composite_backward(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
+                                const float* dviews, float* dplanes, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Adjoint of lf_build_mpi_gaussians: given dplanes = dL/d(planes.rgba)
+ * [N][H][W][4] FP32 device, writes the parameter gradients into grad (every
+ * array overwritten; culled Gaussians get 0). g, ref and planes must be those
+ * of the forward call and ws (ws_bytes) the workspace that call used,
+ * unchanged since: the adjoint reads the forward's depth order, rank-ordered
+ * records and tile lists from it. After an overflowed build the gradients are
+ * all 0 (lf_mpi_status reports the overflow). Errors: LF_ERR_INVALID_ARG,
+ * LF_ERR_WORKSPACE, LF_ERR_CUDA. */
+lf_status lf_build_mpi_backward_gaussians(const lf_gaussians* g, const lf_ref_camera* ref, const lf_planes* planes,
+                                          const float* dplanes, lf_gaussians_grad* grad, void* ws, size_t ws_bytes,
+                                          cudaStream_t stream);
+
+/* Adjoint of lf_build_mpi_voxels (Sec. 4.5): gradients of the corner
+ * densities and colours; same contract as lf_build_mpi_backward_gaussians. */
+lf_status lf_build_mpi_backward_voxels(const lf_voxels* v, const lf_ref_camera* ref, const lf_planes* planes,
+                                       const float* dplanes, lf_voxels_grad* grad, void* ws, size_t ws_bytes,
+                                       cudaStream_t stream);
 
 /* ---- tracing -------------------------------------------------------------- */
 

@@ -57,6 +57,14 @@ class LfVoxels(ctypes.Structure):
                 ("density8", _P), ("rgb", _P)]
 
 
+class LfGaussiansGrad(ctypes.Structure):
+    _fields_ = [("dmeans", _P), ("dscales", _P), ("dquats", _P), ("dopacity", _P), ("drgb", _P)]
+
+
+class LfVoxelsGrad(ctypes.Structure):
+    _fields_ = [("ddensity8", _P), ("drgb", _P)]
+
+
 class LfPlanes(ctypes.Structure):
     _fields_ = [("N", _I32), ("H", _I32), ("W", _I32), ("dtype", _I32), ("rgba", _P), ("d", _P), ("count", _P),
                 ("chunk", _P), ("rect", _P)]
@@ -80,6 +88,14 @@ SIGNATURES = [
     ("lf_composite_workspace_size", ctypes.c_size_t, [_I32, ctypes.POINTER(LfViewSet)]),
     ("lf_composite", ctypes.c_int, [ctypes.POINTER(LfPlanes), ctypes.POINTER(LfRefCamera),
                                     ctypes.POINTER(LfViewSet), _P, _P, ctypes.c_size_t, _P]),
+    ("lf_composite_backward", ctypes.c_int, [ctypes.POINTER(LfPlanes), ctypes.POINTER(LfRefCamera),
+                                             ctypes.POINTER(LfViewSet), _P, _P, _P, ctypes.c_size_t, _P]),
+    ("lf_build_mpi_backward_gaussians", ctypes.c_int, [ctypes.POINTER(LfGaussians), ctypes.POINTER(LfRefCamera),
+                                                       ctypes.POINTER(LfPlanes), _P, ctypes.POINTER(LfGaussiansGrad),
+                                                       _P, ctypes.c_size_t, _P]),
+    ("lf_build_mpi_backward_voxels", ctypes.c_int, [ctypes.POINTER(LfVoxels), ctypes.POINTER(LfRefCamera),
+                                                    ctypes.POINTER(LfPlanes), _P, ctypes.POINTER(LfVoxelsGrad),
+                                                    _P, ctypes.c_size_t, _P]),
     ("lf_launch_count", _I64, []),
     ("lf_trace_enable", ctypes.c_int, [_I32]),
     ("lf_trace_collect", _I32, [_P, _P, _P, _I32]),

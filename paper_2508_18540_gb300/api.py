@@ -241,6 +241,80 @@ def lf_composite(planes: Planes, ref: L.LfRefCamera, views, out: torch.Tensor, w
 
 
 # ---------------------------------------------------------------------------
+# differentiation
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class GaussianGrads:
+    dmeans: torch.Tensor
+    dscales: torch.Tensor
+    dquats: torch.Tensor
+    dopacity: torch.Tensor
+    drgb: torch.Tensor
+
+    @classmethod
+    def empty(cls, n: int, device="cuda"):
+        f = dict(dtype=torch.float32, device=device)
+        return cls(torch.empty((n, 3), **f), torch.empty((n, 3), **f), torch.empty((n, 4), **f),
+                   torch.empty((n,), **f), torch.empty((n, 3), **f))
+
+    def c_struct(self, n: int) -> L.LfGaussiansGrad:
+        for name, t, w in (("dmeans", self.dmeans, 3), ("dscales", self.dscales, 3), ("dquats", self.dquats, 4),
+                           ("drgb", self.drgb, 3)):
+            _need(t, (n, w), torch.float32, name)
+        _need(self.dopacity, (n,), torch.float32, "dopacity")
+        return L.LfGaussiansGrad(self.dmeans.data_ptr(), self.dscales.data_ptr(), self.dquats.data_ptr(),
+                                 self.dopacity.data_ptr(), self.drgb.data_ptr())
+
+
+@dataclasses.dataclass
+class VoxelGrads:
+    ddensity8: torch.Tensor
+    drgb: torch.Tensor
+
+    @classmethod
+    def empty(cls, n: int, device="cuda"):
+        return cls(torch.empty((n, 8), dtype=torch.float32, device=device),
+                   torch.empty((n, 3), dtype=torch.float32, device=device))
+
+    def c_struct(self, n: int) -> L.LfVoxelsGrad:
+        _need(self.ddensity8, (n, 8), torch.float32, "ddensity8")
+        _need(self.drgb, (n, 3), torch.float32, "drgb")
+        return L.LfVoxelsGrad(self.ddensity8.data_ptr(), self.drgb.data_ptr())
+
+
+def lf_composite_backward(planes: Planes, ref: L.LfRefCamera, views, dviews: torch.Tensor, dplanes: torch.Tensor,
+                          ws: torch.Tensor, stream=None):
+    """Adjoint of lf_composite: dplanes [N][H][W][4] float32 from dviews (asynchronous)."""
+    vs = view_set(views)
+    _need(dviews, (vs.Vx * vs.Vy, ref.base.Ny, ref.base.Nx, 4), torch.float32, "dviews")
+    _need(dplanes, (planes.N, ref.H, ref.W, 4), torch.float32, "dplanes")
+    ps = planes.c_struct()
+    check(load().lf_composite_backward(ctypes.byref(ps), ctypes.byref(ref), ctypes.byref(vs), _ptr(dviews),
+                                       _ptr(dplanes), _ptr(ws), ws.numel(), _stream_ptr(stream)))
+
+
+def lf_build_mpi_backward_gaussians(g: DeviceGaussians, ref: L.LfRefCamera, planes: Planes, dplanes: torch.Tensor,
+                                    grads: GaussianGrads, ws: torch.Tensor, stream=None):
+    """Adjoint of lf_build_mpi_gaussians (ws: the forward's workspace, unchanged)."""
+    _need(dplanes, (planes.N, ref.H, ref.W, 4), torch.float32, "dplanes")
+    gs, ps, gr = g.c_struct(), planes.c_struct(), grads.c_struct(g.n)
+    check(load().lf_build_mpi_backward_gaussians(ctypes.byref(gs), ctypes.byref(ref), ctypes.byref(ps),
+                                                 _ptr(dplanes), ctypes.byref(gr), _ptr(ws), ws.numel(),
+                                                 _stream_ptr(stream)))
+
+
+def lf_build_mpi_backward_voxels(v: DeviceVoxels, ref: L.LfRefCamera, planes: Planes, dplanes: torch.Tensor,
+                                 grads: VoxelGrads, ws: torch.Tensor, stream=None):
+    """Adjoint of lf_build_mpi_voxels (ws: the forward's workspace, unchanged)."""
+    _need(dplanes, (planes.N, ref.H, ref.W, 4), torch.float32, "dplanes")
+    vs, ps, gr = v.c_struct(), planes.c_struct(), grads.c_struct(v.n)
+    check(load().lf_build_mpi_backward_voxels(ctypes.byref(vs), ctypes.byref(ref), ctypes.byref(ps),
+                                              _ptr(dplanes), ctypes.byref(gr), _ptr(ws), ws.numel(),
+                                              _stream_ptr(stream)))
+
+
+# ---------------------------------------------------------------------------
 # convenience: one object holding every buffer of a workload
 # ---------------------------------------------------------------------------
 
@@ -271,6 +345,7 @@ class LightFieldRenderer:
 
     def build(self, prims, stream=None):
         self._ensure(prims.n)
+        self.generation = getattr(self, "generation", 0) + 1
         pl = self.planes
         view = Planes(pl.rgba, pl.d, pl.count, pl.chunk[: max(prims.n, 1)], pl.rect[: max(prims.n, 1)], pl.dtype_code)
         if isinstance(prims, DeviceGaussians):
@@ -290,6 +365,24 @@ class LightFieldRenderer:
 
     def status(self):
         return lf_mpi_status(self.ws)
+
+    def planes_view(self, n: int) -> Planes:
+        pl = self.planes
+        return Planes(pl.rgba, pl.d, pl.count, pl.chunk[: max(n, 1)], pl.rect[: max(n, 1)], pl.dtype_code)
+
+    def backward(self, prims, dviews: torch.Tensor, stream=None):
+        """Gradients of the last render of prims given dL/d(views): composite
+        adjoint, then the splat adjoint on the same workspace."""
+        dplanes = torch.empty((self.N, self.ref.H, self.ref.W, 4), dtype=torch.float32, device=self.device)
+        lf_composite_backward(self.planes, self.ref, self.views, dviews, dplanes, self.cws, stream)
+        view = self.planes_view(prims.n)
+        if isinstance(prims, DeviceGaussians):
+            grads = GaussianGrads.empty(prims.n, self.device)
+            lf_build_mpi_backward_gaussians(prims, self.ref, view, dplanes, grads, self.ws, stream)
+        else:
+            grads = VoxelGrads.empty(prims.n, self.device)
+            lf_build_mpi_backward_voxels(prims, self.ref, view, dplanes, grads, self.ws, stream)
+        return grads, dplanes
 
 
 # ---------------------------------------------------------------------------

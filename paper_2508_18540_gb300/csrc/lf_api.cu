@@ -118,6 +118,7 @@ size_t build_ws_layout(int64_t n, int32_t N, int32_t W, int32_t H, int64_t cap, 
     w.entA = carve<uint32_t>(base, off, cc);
     w.entB = carve<uint32_t>(base, off, cc);
     w.seg = carve<int2>(base, off, (size_t)S);
+    w.g2d = carve<float>(base, off, 12 * nn);
     w.bytes = align_up(off, 256);
     w.nb_sort = nb;
     w.nb_dup = nbd;
@@ -144,6 +145,21 @@ static std::mutex g_ws_mu;
 static std::map<const void*, cudaStream_t> g_ws_stream;
 
 static int64_t default_cap(int64_t n) { return 8 * n + (1ll << 20); }
+
+// pair capacity of a build workspace: the largest one ws_bytes holds (the
+// layout size grows monotonically with it); 0 if none
+static int64_t ws_capacity(int64_t n, int32_t N, int32_t W, int32_t H, size_t ws_bytes)
+{
+    int64_t lo = 0, hi = (1ll << 31) - 1;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (build_ws_layout(n, N, W, H, mid, nullptr, nullptr) <= ws_bytes)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
 
 static lf_status check_ref(const lf_ref_camera* r)
 {
@@ -214,6 +230,53 @@ static void fill_raster_params(const lf_ref_camera* r, int32_t N, int32_t dtype,
     p->cy = (float)r->cy;
 }
 
+static void fill_comp_params(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
+                             CompParams* pp)
+{
+    CompParams& p = *pp;
+    std::memset(&p, 0, sizeof(p));
+    p.N = planes->N;
+    p.W = ref->W;
+    p.H = ref->H;
+    p.Nx = ref->base.Nx;
+    p.Ny = ref->base.Ny;
+    p.Vx = views->Vx;
+    p.Vy = views->Vy;
+    p.P_s = ref->disp.P_s;
+    p.bilinear = views->bilinear ? 1 : 0;
+    p.dtype = planes->dtype;
+    for (int c = 0; c < 3; ++c) p.bg[c] = views->bg[c];
+    p.D_focal = ref->disp.D_focal;
+    p.D_forward = ref->D_forward;
+    p.tth_x = ref->tth_x;
+    p.tth_y = ref->tth_y;
+    p.tthp_x = ref->tthp_x;
+    p.tthp_y = ref->tthp_y;
+    p.tphi_x = ref->tphi_x;
+    p.tphi_y = ref->tphi_y;
+}
+
+// argument checks shared by lf_composite and its adjoint; views_buf is the
+// output views (forward) or their gradient (backward)
+static lf_status check_composite_args(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
+                                      const float* views_buf, void* ws, size_t ws_bytes, CompWs* cw)
+{
+    lf_status st = check_ref(ref);
+    if (st != LF_OK) return st;
+    if (!planes || !views || !views_buf) return fail(LF_ERR_INVALID_ARG, "NULL argument");
+    if (planes->N < 1 || planes->W != ref->W || planes->H != ref->H)
+        return fail(LF_ERR_INVALID_ARG, "plane array shape does not match the reference camera");
+    if (planes->dtype < LF_F32 || planes->dtype > LF_BF16) return fail(LF_ERR_INVALID_ARG, "unknown plane dtype");
+    if (!planes->rgba || !planes->d || !planes->count) return fail(LF_ERR_INVALID_ARG, "plane pointer is NULL");
+    if (views->Vx < 1 || views->Vy < 1 || views->Vx > 65535 || views->Vy > 65535)
+        return fail(LF_ERR_INVALID_ARG, "view counts must be in 1..65535");
+    if (!ws) return fail(LF_ERR_WORKSPACE, "workspace is NULL");
+    if (((uintptr_t)ws) % 256) return fail(LF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+    if (comp_ws_layout(planes->N, views->Vx, views->Vy, ws, cw) > ws_bytes)
+        return fail(LF_ERR_WORKSPACE, "composite workspace too small");
+    return LF_OK;
+}
+
 template <typename Launch>
 static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, int32_t binning, void* ws,
                               size_t ws_bytes, lf_planes* out, cudaStream_t stream, int kind, Launch project,
@@ -229,22 +292,12 @@ static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, in
     if (!ws) return fail(LF_ERR_WORKSPACE, "workspace is NULL");
     if (((uintptr_t)ws) % 256) return fail(LF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
 
-    // pair capacity: the largest one the given workspace holds (the layout
-    // size grows monotonically with it)
-    int64_t lo = 0, hi = (1ll << 31) - 1;
-    while (lo < hi) {
-        const int64_t mid = lo + (hi - lo + 1) / 2;
-        if (build_ws_layout(n, N, ref->W, ref->H, mid, nullptr, nullptr) <= ws_bytes)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    if (lo < 1) {
+    const int64_t cap = ws_capacity(n, N, ref->W, ref->H, ws_bytes);
+    if (cap < 1) {
         const size_t need = build_ws_layout(n, N, ref->W, ref->H, default_cap(n), nullptr, nullptr);
         return fail(LF_ERR_WORKSPACE, "workspace too small (default capacity needs " + std::to_string(need) +
                                           " bytes)");
     }
-    const int64_t cap = lo;
     BuildWs w;
     build_ws_layout(n, N, ref->W, ref->H, cap, ws, &w);
 
@@ -533,41 +586,11 @@ size_t lf_composite_workspace_size(int32_t N, const lf_view_set* views)
 lf_status lf_composite(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views, float* out,
                        void* ws, size_t ws_bytes, cudaStream_t stream)
 {
-    lf_status st = check_ref(ref);
-    if (st != LF_OK) return st;
-    if (!planes || !views || !out) return fail(LF_ERR_INVALID_ARG, "NULL argument");
-    if (planes->N < 1 || planes->W != ref->W || planes->H != ref->H)
-        return fail(LF_ERR_INVALID_ARG, "plane array shape does not match the reference camera");
-    if (planes->dtype < LF_F32 || planes->dtype > LF_BF16) return fail(LF_ERR_INVALID_ARG, "unknown plane dtype");
-    if (!planes->rgba || !planes->d || !planes->count) return fail(LF_ERR_INVALID_ARG, "plane pointer is NULL");
-    if (views->Vx < 1 || views->Vy < 1 || views->Vx > 65535 || views->Vy > 65535)
-        return fail(LF_ERR_INVALID_ARG, "view counts must be in 1..65535");
-    if (!ws) return fail(LF_ERR_WORKSPACE, "workspace is NULL");
-    if (((uintptr_t)ws) % 256) return fail(LF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
     CompWs cw;
-    if (comp_ws_layout(planes->N, views->Vx, views->Vy, ws, &cw) > ws_bytes)
-        return fail(LF_ERR_WORKSPACE, "composite workspace too small");
+    lf_status st = check_composite_args(planes, ref, views, out, ws, ws_bytes, &cw);
+    if (st != LF_OK) return st;
     CompParams p;
-    std::memset(&p, 0, sizeof(p));
-    p.N = planes->N;
-    p.W = ref->W;
-    p.H = ref->H;
-    p.Nx = ref->base.Nx;
-    p.Ny = ref->base.Ny;
-    p.Vx = views->Vx;
-    p.Vy = views->Vy;
-    p.P_s = ref->disp.P_s;
-    p.bilinear = views->bilinear ? 1 : 0;
-    p.dtype = planes->dtype;
-    for (int c = 0; c < 3; ++c) p.bg[c] = views->bg[c];
-    p.D_focal = ref->disp.D_focal;
-    p.D_forward = ref->D_forward;
-    p.tth_x = ref->tth_x;
-    p.tth_y = ref->tth_y;
-    p.tthp_x = ref->tthp_x;
-    p.tthp_y = ref->tthp_y;
-    p.tphi_x = ref->tphi_x;
-    p.tphi_y = ref->tphi_y;
+    fill_comp_params(planes, ref, views, &p);
     if (cudaMemsetAsync(cw.err, 0, sizeof(int) * (1 + (size_t)planes->N), stream) != cudaSuccess)
         return check_launch("composite reset");
     trace_begin("comp_coeffs", stream);
@@ -578,6 +601,112 @@ lf_status lf_composite(const lf_planes* planes, const lf_ref_camera* ref, const 
     launch_composite(p, planes->rgba, planes->count, cw, out, stream);
     trace_end(stream);
     return check_launch("composite");
+}
+
+lf_status lf_composite_backward(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
+                                const float* dviews, float* dplanes, void* ws, size_t ws_bytes, cudaStream_t stream)
+{
+    CompWs cw;
+    lf_status st = check_composite_args(planes, ref, views, dviews, ws, ws_bytes, &cw);
+    if (st != LF_OK) return st;
+    if (!dplanes) return fail(LF_ERR_INVALID_ARG, "dplanes is NULL");
+    if (((uintptr_t)dviews) % 16 || ((uintptr_t)dplanes) % 16)
+        return fail(LF_ERR_INVALID_ARG, "dviews and dplanes must be 16-byte aligned");
+    CompParams p;
+    fill_comp_params(planes, ref, views, &p);
+    const size_t dbytes = sizeof(float) * 4 * (size_t)planes->N * planes->W * planes->H;
+    if (cudaMemsetAsync(dplanes, 0, dbytes, stream) != cudaSuccess ||
+        cudaMemsetAsync(cw.err, 0, sizeof(int) * (1 + (size_t)planes->N), stream) != cudaSuccess)
+        return check_launch("composite backward reset");
+    trace_begin("comp_coeffs", stream);
+    launch_comp_coeffs(p, planes->d, planes->count, cw, stream);
+    trace_end(stream);
+    if ((st = check_launch("composite coefficients")) != LF_OK) return st;
+    trace_begin("composite_bwd", stream);
+    launch_composite_bwd(p, planes->rgba, planes->count, cw, dviews, dplanes, stream);
+    trace_end(stream);
+    return check_launch("composite backward");
+}
+
+// Common part of the two splat adjoints: argument checks, the forward's
+// workspace layout, zeroing of the gradient accumulators and the raster
+// adjoint. Returns the layout in *w.
+static lf_status splat_backward_common(int64_t n, const lf_ref_camera* ref, const lf_planes* planes,
+                                       const float* dplanes, void* ws, size_t ws_bytes, int kind, BuildWs* w,
+                                       cudaStream_t stream)
+{
+    lf_status st = check_ref(ref);
+    if (st != LF_OK) return st;
+    if (!planes || !dplanes) return fail(LF_ERR_INVALID_ARG, "NULL argument");
+    if (planes->N < 1 || planes->N > 65535 || planes->W != ref->W || planes->H != ref->H)
+        return fail(LF_ERR_INVALID_ARG, "plane array shape does not match the reference camera");
+    if (((uintptr_t)dplanes) % 16) return fail(LF_ERR_INVALID_ARG, "dplanes must be 16-byte aligned");
+    if (n < 0 || n > (int64_t)0x7fffffff) return fail(LF_ERR_INVALID_ARG, "primitive count out of range");
+    if (!ws) return fail(LF_ERR_WORKSPACE, "workspace is NULL");
+    if (((uintptr_t)ws) % 256) return fail(LF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+    const int64_t cap = ws_capacity(n, planes->N, ref->W, ref->H, ws_bytes);
+    if (cap < 1) return fail(LF_ERR_WORKSPACE, "workspace too small for this build");
+    build_ws_layout(n, planes->N, ref->W, ref->H, cap, ws, w);
+    if (n > 0 && cudaMemsetAsync(w->g2d, 0, sizeof(float) * 12 * (size_t)n, stream) != cudaSuccess)
+        return check_launch("gradient accumulator reset");
+    RasterParams rp;
+    fill_raster_params(ref, planes->N, LF_F32, &rp);
+    const int n_supers = ((ref->W + kSuper - 1) / kSuper) * ((ref->H + kSuper - 1) / kSuper);
+    const uint32_t* ranks = tile_sort_passes(tile_bits_for(n_supers)) % 2 ? w->entB : w->entA;
+    trace_begin(kind == 0 ? "raster_gaussians_bwd" : "raster_voxels_bwd", stream);
+    if (kind == 0)
+        launch_raster_gaussians_bwd(*w, rp, ranks, dplanes, stream);
+    else
+        launch_raster_voxels_bwd(*w, rp, ranks, dplanes, stream);
+    trace_end(stream);
+    return check_launch("raster backward");
+}
+
+lf_status lf_build_mpi_backward_gaussians(const lf_gaussians* g, const lf_ref_camera* ref, const lf_planes* planes,
+                                          const float* dplanes, lf_gaussians_grad* grad, void* ws, size_t ws_bytes,
+                                          cudaStream_t stream)
+{
+    if (!g || !grad) return fail(LF_ERR_INVALID_ARG, "NULL argument");
+    if (g->n > 0 && (!g->means || !g->scales || !g->quats || !g->opacity || !g->rgb))
+        return fail(LF_ERR_INVALID_ARG, "a Gaussian attribute pointer is NULL");
+    if (g->n > 0 && (!grad->dmeans || !grad->dscales || !grad->dquats || !grad->dopacity || !grad->drgb))
+        return fail(LF_ERR_INVALID_ARG, "a gradient pointer is NULL");
+    BuildWs w;
+    lf_status st = splat_backward_common(g->n, ref, planes, dplanes, ws, ws_bytes, 0, &w, stream);
+    if (st != LF_OK) return st;
+    const size_t n = (size_t)g->n;
+    if (n > 0) {
+        const float* bufs[5] = {grad->dmeans, grad->dscales, grad->dquats, grad->dopacity, grad->drgb};
+        const size_t widths[5] = {3, 3, 4, 1, 3};
+        for (int b = 0; b < 5; ++b)
+            if (cudaMemsetAsync(const_cast<float*>(bufs[b]), 0, sizeof(float) * widths[b] * n, stream) != cudaSuccess)
+                return check_launch("gradient reset");
+    }
+    ProjParams pp;
+    fill_proj_params(ref, g->n, &pp);
+    trace_begin("project_bwd", stream);
+    launch_gauss_chain(*g, pp, w, *grad, stream);
+    trace_end(stream);
+    return check_launch("projection backward");
+}
+
+lf_status lf_build_mpi_backward_voxels(const lf_voxels* v, const lf_ref_camera* ref, const lf_planes* planes,
+                                       const float* dplanes, lf_voxels_grad* grad, void* ws, size_t ws_bytes,
+                                       cudaStream_t stream)
+{
+    if (!v || !grad) return fail(LF_ERR_INVALID_ARG, "NULL argument");
+    if (v->n > 0 && (!grad->ddensity8 || !grad->drgb)) return fail(LF_ERR_INVALID_ARG, "a gradient pointer is NULL");
+    BuildWs w;
+    lf_status st = splat_backward_common(v->n, ref, planes, dplanes, ws, ws_bytes, 1, &w, stream);
+    if (st != LF_OK) return st;
+    const size_t n = (size_t)v->n;
+    if (n > 0 && (cudaMemsetAsync(grad->ddensity8, 0, sizeof(float) * 8 * n, stream) != cudaSuccess ||
+                  cudaMemsetAsync(grad->drgb, 0, sizeof(float) * 3 * n, stream) != cudaSuccess))
+        return check_launch("gradient reset");
+    trace_begin("scatter_bwd", stream);
+    launch_voxel_scatter(w, v->n, *grad, stream);
+    trace_end(stream);
+    return check_launch("voxel gradient scatter");
 }
 
 }  // extern "C"

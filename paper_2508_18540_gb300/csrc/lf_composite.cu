@@ -647,7 +647,183 @@ void launch_composite_t(const CompParams& p, const void* planes, const int32_t* 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the swizzle blending. For one view pixel the forward computes
+// Q = sum_k T_k C_k, T_{k+1} = T_k (1 - A_k), output (Q + T_N bg, 1 - T_N).
+// With upstream gradient g = (g_rgb, g_a):
+//   dL/dC_k = T_k g_rgb,   dL/dA_k = -T_k B_k,
+//   B_k = sum_{j>k} (prod_{k<l<j} (1 - A_l)) C_j . g_rgb + (prod_{l>k} (1 - A_l)) (g_rgb . bg - g_a),
+//   B_{k-1} = C_k . g_rgb + (1 - A_k) B_k.
+// B needs no transmittance; T_k is recovered back to front as
+// T_{k+1} / (1 - A_k), carried as m 2^-e against underflow. A stored A_k
+// can be exactly 1 (T_{k+1} = 0); the forward walk keeps T before the first
+// such plane, and every plane behind it gets T = 0. The texel gradients are
+// scattered with FP32 vector atomics into dplanes (nearest: the sampled
+// texel; bilinear: the in-plane taps with their weights). Per-chunk
+// transmittance is recomputed, never stored.
+// ---------------------------------------------------------------------------
+
+constexpr float kUpB = 18446744073709551616.0f;       // 2^64
+constexpr float kDownB = 5.42101086242752217e-20f;    // 2^-64
+constexpr float kBigB = 4294967296.0f;                // 2^32
+
+template <int DT, bool BILINEAR>
+__global__ void __launch_bounds__(kCompBX* kCompBY) k_composite_bwd(CompParams p, const void* __restrict__ planes,
+                                                                   const int32_t* __restrict__ count, CompWs w,
+                                                                   const float4* __restrict__ dviews,
+                                                                   float4* __restrict__ dplanes)
+{
+    extern __shared__ float s_coef[];  // as k_composite
+    int* s_cnt = reinterpret_cast<int*>(s_coef + 6 * p.N);
+    const int v = blockIdx.z;
+    const int i = v / p.Vx, j = v % p.Vx;
+    const int tid = threadIdx.y * kCompBX + threadIdx.x;
+    for (int k = tid; k < p.N; k += kCompBX * kCompBY) {
+        const float* cx = w.cx + 3 * ((size_t)j * p.N + k);
+        const float* cy = w.cy + 3 * ((size_t)i * p.N + k);
+        s_coef[6 * k + 0] = cx[0];
+        s_coef[6 * k + 1] = cx[1];
+        s_coef[6 * k + 2] = cx[2];
+        s_coef[6 * k + 3] = cy[0];
+        s_coef[6 * k + 4] = cy[1];
+        s_coef[6 * k + 5] = cy[2];
+        s_cnt[k] = count[k];
+    }
+    __syncthreads();
+    const int x = blockIdx.x * kCompBX + threadIdx.x;
+    const int y = blockIdx.y * kCompBY + threadIdx.y;
+    if (x >= p.Nx || y >= p.Ny) return;
+    const size_t plane_sz = (size_t)p.W * p.H;
+
+    // taps of plane k for this pixel: up to 4 (plane offset, weight)
+    int tap[4];
+    float wt[4];
+    auto taps = [&](int k) -> int {
+        const float* c = s_coef + 6 * k;
+        int n = 0;
+        if (!BILINEAR) {
+            const int ix = nearest_index(p.P_s, x, c[0], c[1]);
+            const int iy = nearest_index(p.P_s, y, c[3], c[4]);
+            if (ix >= 0 && ix < p.W && iy >= 0 && iy < p.H) {
+                tap[0] = iy * p.W + ix;
+                wt[0] = 1.0f;
+                n = 1;
+            }
+        } else {
+            const float Dx = __fmaf_rn(c[0], (float)x, c[2]);
+            const float Dy = __fmaf_rn(c[3], (float)y, c[5]);
+            if (Dx >= -1.0e6f && Dx <= 1.0e6f && Dy >= -1.0e6f && Dy <= 1.0e6f) {
+                const float flx = floorf(Dx), fly = floorf(Dy);
+                const float wx = Dx - flx, wy = Dy - fly;
+                const int x0 = p.P_s * x + (int)flx, y0 = p.P_s * y + (int)fly;
+#pragma unroll
+                for (int dy = 0; dy < 2; ++dy) {
+                    const int yy = y0 + dy;
+                    if (yy < 0 || yy >= p.H) continue;
+                    const float wyy = dy ? wy : 1.0f - wy;
+#pragma unroll
+                    for (int dx = 0; dx < 2; ++dx) {
+                        const int xx = x0 + dx;
+                        if (xx < 0 || xx >= p.W) continue;
+                        tap[n] = yy * p.W + xx;
+                        wt[n] = wyy * (dx ? wx : 1.0f - wx);
+                        ++n;
+                    }
+                }
+            }
+        }
+        return n;
+    };
+    auto sample = [&](int k, int n) -> float4 {
+        float4 tx = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < n; ++q) {
+            const float4 t = load_texel<DT>(planes, (size_t)k * plane_sz + tap[q]);
+            tx.x = fmaf(wt[q], t.x, tx.x);
+            tx.y = fmaf(wt[q], t.y, tx.y);
+            tx.z = fmaf(wt[q], t.z, tx.z);
+            tx.w = fmaf(wt[q], t.w, tx.w);
+        }
+        return tx;
+    };
+
+    float Tm = 1.f, oTm = 0.f;
+    int Te = 0, oTe = 0, ok = -1;
+    for (int k = 0; k < p.N; ++k) {
+        if (s_cnt[k] == 0) continue;
+        const float4 tx = sample(k, taps(k));
+        const float oma = 1.0f - tx.w;
+        if (!(oma > 0.0f) && Tm > 0.0f && ok < 0) {
+            oTm = Tm;
+            oTe = Te;
+            ok = k;
+        }
+        Tm = Tm * oma;
+        if (Tm < kDownB && Tm > 0.0f) {
+            Tm *= kUpB;
+            Te += 64;
+        }
+    }
+    const float4 g = dviews[((size_t)v * p.Ny + y) * p.Nx + x];
+    float B = fmaf(g.x, p.bg[0], fmaf(g.y, p.bg[1], fmaf(g.z, p.bg[2], -g.w)));
+    for (int k = p.N - 1; k >= 0; --k) {
+        if (s_cnt[k] == 0) continue;
+        const int n = taps(k);
+        const float4 tx = sample(k, n);
+        const float oma = 1.0f - tx.w;
+        if (k == ok) {
+            Tm = oTm;
+            Te = oTe;
+        } else if (oma > 0.0f) {
+            Tm = __fdiv_rn(Tm, oma);
+            if (Te > 0 && Tm > kBigB) {
+                Tm *= kDownB;
+                Te -= 64;
+            }
+        }
+        const float Tk = Te == 0 ? Tm : ldexpf(Tm, -Te);
+        if (Tk > 0.0f) {
+            const float4 gt = make_float4(Tk * g.x, Tk * g.y, Tk * g.z, -Tk * B);
+            for (int q = 0; q < n; ++q)
+                atomicAdd(dplanes + (size_t)k * plane_sz + tap[q],
+                          make_float4(wt[q] * gt.x, wt[q] * gt.y, wt[q] * gt.z, wt[q] * gt.w));
+        }
+        B = fmaf(tx.x, g.x, fmaf(tx.y, g.y, fmaf(tx.z, g.z, oma * B)));
+    }
+}
+
+template <int DT>
+void launch_composite_bwd_t(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
+                            const float* dviews, float* dplanes, cudaStream_t s)
+{
+    const dim3 block(kCompBX, kCompBY);
+    const dim3 grid((unsigned)((p.Nx + kCompBX - 1) / kCompBX), (unsigned)((p.Ny + kCompBY - 1) / kCompBY),
+                    (unsigned)(p.Vx * p.Vy));
+    const size_t smem = sizeof(float) * 6 * p.N + sizeof(int) * p.N;
+    const float4* dv = reinterpret_cast<const float4*>(dviews);
+    float4* dp = reinterpret_cast<float4*>(dplanes);
+    if (p.bilinear) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_composite_bwd<DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_composite_bwd<DT, true><<<grid, block, smem, s>>>(p, planes, count, ws, dv, dp);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_composite_bwd<DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_composite_bwd<DT, false><<<grid, block, smem, s>>>(p, planes, count, ws, dv, dp);
+    }
+    note_launches(1);
+}
+
 }  // namespace
+
+void launch_composite_bwd(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
+                          const float* dviews, float* dplanes, cudaStream_t s)
+{
+    switch (p.dtype) {
+    case LF_F32: launch_composite_bwd_t<LF_F32>(p, planes, count, ws, dviews, dplanes, s); break;
+    case LF_F16: launch_composite_bwd_t<LF_F16>(p, planes, count, ws, dviews, dplanes, s); break;
+    default: launch_composite_bwd_t<LF_BF16>(p, planes, count, ws, dviews, dplanes, s); break;
+    }
+}
 
 void launch_comp_coeffs(const CompParams& p, const double* d, const int32_t* count, const CompWs& ws, cudaStream_t s)
 {

@@ -77,6 +77,7 @@ struct BuildWs {
     uint32_t* entA;               // [cap] rank of every pair
     uint32_t* entB;
     int2* seg;                    // [supers * N] (start, end) of every (super-tile, chunk) list
+    float* g2d;                   // [n][12] per-rank gradient accumulators of the backward pass
     size_t bytes;
     long long nb_sort, nb_dup;
 };
@@ -142,6 +143,16 @@ void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uin
 void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
                           cudaStream_t s);
 
+// backward: raster adjoints accumulate into ws.g2d (zeroed by the caller),
+// then the per-rank chain rule / scatter writes the parameter gradients
+void launch_raster_gaussians_bwd(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks,
+                                 const float* dplanes, cudaStream_t s);
+void launch_raster_voxels_bwd(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, const float* dplanes,
+                              cudaStream_t s);
+void launch_gauss_chain(const lf_gaussians& g, const ProjParams& p, const BuildWs& ws, const lf_gaussians_grad& out,
+                        cudaStream_t s);
+void launch_voxel_scatter(const BuildWs& ws, long long n, const lf_voxels_grad& out, cudaStream_t s);
+
 // ---- composite ----------------------------------------------------------
 struct CompWs {
     float* cx;      // [Vx][N][3] (gm, hn, hb) along x
@@ -163,5 +174,7 @@ void launch_comp_coeffs(const CompParams& p, const double* d, const int32_t* cou
                         cudaStream_t s);
 void launch_composite(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
                       float* out, cudaStream_t s);
+void launch_composite_bwd(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
+                          const float* dviews, float* dplanes, cudaStream_t s);
 
 }  // namespace lf

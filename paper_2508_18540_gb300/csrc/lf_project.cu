@@ -223,6 +223,172 @@ __global__ void __launch_bounds__(256) k_project_voxels(lf_voxels v, ProjParams 
     publish_key(w.hdr, key);
 }
 
+// ---------------------------------------------------------------------------
+// Backward of the per-Gaussian projection (chain rule of the EWA splatting
+// model, 3DGS, with the dilation f' of Eq. (gs_prefilter_fix)). Input per
+// rank: gradients of the 2D mean (px, py), of the conic scalars (a, b, c)
+// with q = a dx^2 + 2 b dx dy + c dy^2, of the opacity and of the colour,
+// accumulated by the raster backward. Output per Gaussian index: gradients
+// of means, scales, raw quaternions (through the normalisation), opacity and
+// colour. Forward (FP32, as in the projection above):
+//   (x, y, z) = R m + t - D_forward e_z, q^ = q / |q|, Q = rot(q^),
+//   V = R Q diag(s), U0 = (fx/z) (V_0 - (x/z) V_2), U1 = (fy/z) (V_1 - (y/z) V_2),
+//   S00 = U0.U0 + f', S01 = U0.U1, S11 = U1.U1 + f', det = S00 S11 - S01^2,
+//   (a, b, c) = (S11, -S01, S00) / det,  px = fx x/z + cx, py = fy y/z + cy.
+// The conic adjoint is G_S = -K G_K K with K the conic matrix and G_K =
+// [[ga, gb/2], [gb/2, gc]] (b sits twice in the symmetric matrix).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gauss_chain(lf_gaussians g, ProjParams p, BuildWs w, lf_gaussians_grad out)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w.hdr->overflow || r >= (long long)w.hdr->M) return;
+    const uint32_t i = w.valA[r];
+    const float4 a0 = reinterpret_cast<const float4*>(w.g2d)[3 * r];
+    const float4 a1 = reinterpret_cast<const float4*>(w.g2d)[3 * r + 1];
+    const float4 a2 = reinterpret_cast<const float4*>(w.g2d)[3 * r + 2];
+    const float gpx = a0.x, gpy = a0.y, ga = a0.z, gb = a0.w, gc = a1.x;
+    out.dopacity[i] = a1.y;
+    out.drgb[3 * (size_t)i + 0] = a1.z;
+    out.drgb[3 * (size_t)i + 1] = a1.w;
+    out.drgb[3 * (size_t)i + 2] = a2.x;
+
+    const float* R = p.Rf;
+    const float m0 = g.means[3 * (size_t)i], m1 = g.means[3 * (size_t)i + 1], m2 = g.means[3 * (size_t)i + 2];
+    const float xc = fmaf(R[0], m0, fmaf(R[1], m1, fmaf(R[2], m2, p.t0f)));
+    const float yc = fmaf(R[3], m0, fmaf(R[4], m1, fmaf(R[5], m2, p.t1f)));
+    const float zc = __double2float_rn(ref_depth(p, (double)m0, (double)m1, (double)m2));
+    const float q[4] = {g.quats[4 * (size_t)i], g.quats[4 * (size_t)i + 1], g.quats[4 * (size_t)i + 2],
+                        g.quats[4 * (size_t)i + 3]};
+    const float qn = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const float iqn = 1.0f / qn;
+    const float qw = q[0] * iqn, qx = q[1] * iqn, qy = q[2] * iqn, qz = q[3] * iqn;
+    float Q[9];
+    Q[0] = 1.f - 2.f * (qy * qy + qz * qz);
+    Q[1] = 2.f * (qx * qy - qw * qz);
+    Q[2] = 2.f * (qx * qz + qw * qy);
+    Q[3] = 2.f * (qx * qy + qw * qz);
+    Q[4] = 1.f - 2.f * (qx * qx + qz * qz);
+    Q[5] = 2.f * (qy * qz - qw * qx);
+    Q[6] = 2.f * (qx * qz - qw * qy);
+    Q[7] = 2.f * (qy * qz + qw * qx);
+    Q[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    const float sc[3] = {g.scales[3 * (size_t)i], g.scales[3 * (size_t)i + 1], g.scales[3 * (size_t)i + 2]};
+    float M[9], V[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) M[3 * a + l] = Q[3 * a + l] * sc[l];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) V[3 * a + l] = R[3 * a] * M[l] + R[3 * a + 1] * M[3 + l] + R[3 * a + 2] * M[6 + l];
+    const float iz = 1.0f / zc;
+    const float xn = xc * iz, yn = yc * iz, ax = p.fxf * iz, ay = p.fyf * iz;
+    float U0[3], U1[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        U0[l] = ax * (V[l] - xn * V[6 + l]);
+        U1[l] = ay * (V[3 + l] - yn * V[6 + l]);
+    }
+    const float S00 = U0[0] * U0[0] + U0[1] * U0[1] + U0[2] * U0[2] + p.fpf;
+    const float S01 = U0[0] * U1[0] + U0[1] * U1[1] + U0[2] * U1[2];
+    const float S11 = U1[0] * U1[0] + U1[1] * U1[1] + U1[2] * U1[2] + p.fpf;
+    const float idet = 1.0f / (S00 * S11 - S01 * S01);
+    const float Ka = S11 * idet, Kb = -S01 * idet, Kc = S00 * idet;
+    // G_S = -K G_K K
+    const float P00 = ga * Ka + 0.5f * gb * Kb, P01 = ga * Kb + 0.5f * gb * Kc;
+    const float P10 = 0.5f * gb * Ka + gc * Kb, P11 = 0.5f * gb * Kb + gc * Kc;
+    const float gS00 = -(Ka * P00 + Kb * P10);
+    const float gS11 = -(Kb * P01 + Kc * P11);
+    const float gS01 = -2.0f * (Ka * P01 + Kb * P11);
+    // S = U U^T + f' I
+    float gU0[3], gU1[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        gU0[l] = 2.0f * gS00 * U0[l] + gS01 * U1[l];
+        gU1[l] = 2.0f * gS11 * U1[l] + gS01 * U0[l];
+    }
+    // U0 = ax (V_0 - xn V_2), U1 = ay (V_1 - yn V_2)
+    float gV[9];
+    float g_ax = 0.f, g_ay = 0.f, g_xn = p.fxf * gpx, g_yn = p.fyf * gpy;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        gV[l] = ax * gU0[l];
+        gV[3 + l] = ay * gU1[l];
+        gV[6 + l] = -ax * xn * gU0[l] - ay * yn * gU1[l];
+        g_ax += gU0[l] * (V[l] - xn * V[6 + l]);
+        g_ay += gU1[l] * (V[3 + l] - yn * V[6 + l]);
+        g_xn -= ax * V[6 + l] * gU0[l];
+        g_yn -= ay * V[6 + l] * gU1[l];
+    }
+    const float g_xc = g_xn * iz, g_yc = g_yn * iz;
+    const float g_iz = g_xn * xc + g_yn * yc + g_ax * p.fxf + g_ay * p.fyf;
+    const float g_zc = -g_iz * iz * iz;
+    // m: camera point = R m + t
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        out.dmeans[3 * (size_t)i + a] = R[a] * g_xc + R[3 + a] * g_yc + R[6 + a] * g_zc;
+    // V = R M -> gM = R^T gV; M = Q diag(s)
+    float gQ[9];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        float gs = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float gM = R[a] * gV[l] + R[3 + a] * gV[3 + l] + R[6 + a] * gV[6 + l];
+            gs += gM * Q[3 * a + l];
+            gQ[3 * a + l] = gM * sc[l];
+        }
+        out.dscales[3 * (size_t)i + l] = gs;
+    }
+    // rotation matrix of the unit quaternion (w, x, y, z)
+    const float gw = 2.f * (-qz * gQ[1] + qy * gQ[2] + qz * gQ[3] - qx * gQ[5] - qy * gQ[6] + qx * gQ[7]);
+    const float gx = 2.f * (qy * gQ[1] + qz * gQ[2] + qy * gQ[3] - 2.f * qx * gQ[4] - qw * gQ[5] + qz * gQ[6] +
+                            qw * gQ[7] - 2.f * qx * gQ[8]);
+    const float gy = 2.f * (-2.f * qy * gQ[0] + qx * gQ[1] + qw * gQ[2] + qx * gQ[3] + qz * gQ[5] - qw * gQ[6] +
+                            qz * gQ[7] - 2.f * qy * gQ[8]);
+    const float gz = 2.f * (-2.f * qz * gQ[0] - qw * gQ[1] + qx * gQ[2] + qw * gQ[3] - 2.f * qz * gQ[4] +
+                            qy * gQ[5] + qx * gQ[6] + qy * gQ[7]);
+    // through q^ = q / |q|
+    const float dot = gw * qw + gx * qx + gy * qy + gz * qz;
+    out.dquats[4 * (size_t)i + 0] = (gw - qw * dot) * iqn;
+    out.dquats[4 * (size_t)i + 1] = (gx - qx * dot) * iqn;
+    out.dquats[4 * (size_t)i + 2] = (gy - qy * dot) * iqn;
+    out.dquats[4 * (size_t)i + 3] = (gz - qz * dot) * iqn;
+}
+
+// Voxels: the accumulators are already the parameter gradients; scatter
+// them from rank order to primitive order.
+__global__ void __launch_bounds__(256) k_voxel_scatter(BuildWs w, lf_voxels_grad out)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w.hdr->overflow || r >= (long long)w.hdr->M) return;
+    const uint32_t i = w.valA[r];
+    const float4* a = reinterpret_cast<const float4*>(w.g2d) + 3 * r;
+    const float4 a0 = a[0], a1 = a[1], a2 = a[2];
+    float* dd = out.ddensity8 + 8 * (size_t)i;
+    dd[0] = a0.x; dd[1] = a0.y; dd[2] = a0.z; dd[3] = a0.w;
+    dd[4] = a1.x; dd[5] = a1.y; dd[6] = a1.z; dd[7] = a1.w;
+    out.drgb[3 * (size_t)i + 0] = a2.x;
+    out.drgb[3 * (size_t)i + 1] = a2.y;
+    out.drgb[3 * (size_t)i + 2] = a2.z;
+}
+
+void launch_gauss_chain(const lf_gaussians& g, const ProjParams& p, const BuildWs& ws, const lf_gaussians_grad& out,
+                        cudaStream_t s)
+{
+    if (p.n <= 0) return;
+    k_gauss_chain<<<(unsigned)((p.n + 255) / 256), 256, 0, s>>>(g, p, ws, out);
+    note_launches(1);
+}
+
+void launch_voxel_scatter(const BuildWs& ws, long long n, const lf_voxels_grad& out, cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_voxel_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws, out);
+    note_launches(1);
+}
+
 void launch_project_gaussians(const lf_gaussians& g, const ProjParams& p, const BuildWs& ws, int32_t* rect,
                               int32_t* chunk, cudaStream_t s)
 {

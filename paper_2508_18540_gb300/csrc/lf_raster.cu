@@ -289,7 +289,458 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
     if (px < p.W && py < p.H) store_texel<DT>(planes, ((size_t)k * p.H + py) * p.W + px, C0, C1, C2, 1.0f - T);
 }
 
+// ---------------------------------------------------------------------------
+// Adjoints of the per-chunk blending (the splat half of the backward pass).
+//
+// Per plane pixel the forward computes C = sum_i T_i a_i c_i and A = 1 - T_end
+// with T_{i+1} = T_i (1 - a_i). With upstream gradients dC (3) and dA, and
+// w_i = c_i . dC + dA (because 1 - T_end = sum_i T_i a_i):
+//   dL/dc_i = T_i a_i dC,   dL/da_i = T_i (w_i - S_i),
+//   S_i = sum_{j>i} (T_j / T_{i+1}) a_j w_j,  S_{i-1} = a_i w_i + (1 - a_i) S_i.
+// The kernels first recompute T_end per pixel (front to back, the forward's
+// operation order), then walk the list back to front recovering
+// T_i = T_{i+1} / (1 - a_i); a_i <= 0.99 (Gaussians) keeps every divisor
+// >= 0.01. Transmittance is carried as m 2^-e (e a multiple of 64) so that a
+// long list cannot underflow it before the reverse walk. Nothing per entry is
+// stored: the per-chunk transmittance is recomputed, not kept.
+// Per entry each warp sums its pixels' contributions with shuffles and adds
+// them to the primitive's accumulator (rank order) with one vector atomic.
+// ---------------------------------------------------------------------------
+
+constexpr float kUp = 18446744073709551616.0f;        // 2^64
+constexpr float kDown = 5.42101086242752217e-20f;     // 2^-64
+constexpr float kSmall = 5.42101086242752217e-20f;    // rescale below 2^-64
+constexpr float kBig = 4294967296.0f;                 // 2^32
+
+__device__ __forceinline__ void t_forward(float& m, int& e, float al)
+{
+    m = fmaf(-m, al, m);
+    if (m < kSmall && m > 0.0f) {
+        m *= kUp;
+        e += 64;
+    }
+}
+
+__device__ __forceinline__ void t_reverse(float& m, int& e, float one_minus_al)
+{
+    m = __fdiv_rn(m, one_minus_al);
+    if (e > 0 && m > kBig) {
+        m *= kDown;
+        e -= 64;
+    }
+}
+
+__device__ __forceinline__ float t_value(float m, int e) { return e == 0 ? m : ldexpf(m, -e); }
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float4 load_grad(const float4* __restrict__ dplanes, int k, int x, int y, int W, int H)
+{
+    if (x < W && y < H) return __ldg(dplanes + ((size_t)k * H + y) * W + x);
+    return make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Gaussians. Same CTA shape and list walk as k_raster_gauss. Accumulator of
+// rank r: g2d[3 r .. 3 r + 2] = {d mean x, d mean y, d a, d b}, {d c, d o,
+// d r, d g}, {d b(lue), 0, 0, 0} with (a, b, c) the conic, q = a dx^2 +
+// 2 b dx dy + c dy^2, alpha = min(0.99, o exp(-q/2)); a clamped alpha passes
+// no gradient to o or q.
+template <int PPT>
+__global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss_bwd(BuildWs w, RasterParams p,
+                                                                     const uint32_t* __restrict__ ranks,
+                                                                     const float4* __restrict__ dplanes,
+                                                                     float4* __restrict__ g2d)
+{
+    constexpr int NT = kTilePix / PPT;
+    constexpr float kL2E = 1.4426950408889634f;
+    __shared__ float4 s_e0[NT];
+    __shared__ float4 s_e1[NT];
+    __shared__ float4 s_rgb[NT];
+    __shared__ float4 s_abc[NT];
+    __shared__ int s_wc[NT / 32];
+    if (w.hdr->overflow) return;
+    const int t = blockIdx.x, k = blockIdx.y;
+    const int tx = t % p.tiles_x, ty = t / p.tiles_x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
+    const int py0 = ty * kTile + (threadIdx.x / kTile) * PPT;
+    const int sx0 = tx * kTile, sx1 = sx0 + kTile - 1;
+    const int sy0 = ty * kTile + 2 * PPT * warp, sy1 = sy0 + 2 * PPT - 1;
+    const int st = (ty / kTilesPerSuper) * p.supers_x + tx / kTilesPerSuper;
+    const int2 sg = w.seg[(size_t)st * p.N + k];
+    const int L = sg.y - sg.x;
+    const float fpx = (float)px;
+    float Tm[PPT], S[PPT], dC[PPT][3], dA[PPT];
+    int Te[PPT];
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        const float4 g = load_grad(dplanes, k, px, py0 + r, p.W, p.H);
+        dC[r][0] = g.x, dC[r][1] = g.y, dC[r][2] = g.z, dA[r] = g.w;
+        Tm[r] = 1.f, Te[r] = 0, S[r] = 0.f;
+    }
+    if (L == 0) return;
+    const int nbatch = (L + NT - 1) / NT;
+
+    // stages batch b: compacted entries of the tile in list order; returns the count
+    auto stage = [&](int b) -> int {
+        const int i = b * NT + threadIdx.x;
+        uint32_t rk = 0;
+        int4 r = make_int4(0, 0, -1, -1);
+        if (i < L) {
+            rk = ranks[sg.x + i];
+            r = w.r_rect[rk];
+        }
+        const bool hit = i < L && meets_tile(r, sx0, ty * kTile);
+        int cnt;
+        const int slot = compact_slot<NT>(hit, s_wc, &cnt);
+        if (hit) {
+            const float4 geo = w.r_geo[rk];
+            const float4 c = w.r_con[rk];
+            s_e0[slot] = make_float4(geo.x, geo.y, -0.5f * kL2E * c.x, -kL2E * c.y);
+            s_e1[slot] = make_float4(-0.5f * kL2E * c.z, c.w, __int_as_float((r.x & 0xffff) | (r.y << 16)),
+                                     __int_as_float(((r.z - r.x) & 0xffff) | ((r.w - r.y) << 16)));
+            s_rgb[slot] = w.r_rgb[rk];
+            s_abc[slot] = make_float4(c.x, c.y, c.z, __uint_as_float(rk));
+        }
+        __syncthreads();
+        return cnt;
+    };
+    auto strip_hit = [&](int jl, int cnt) -> bool {
+        if (jl >= cnt) return false;
+        const float4 e1 = s_e1[jl];
+        const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
+        const int rx0 = xy & 0xffff, ry0 = xy >> 16;
+        return rx0 <= sx1 && rx0 + (wh & 0xffff) >= sx0 && ry0 <= sy1 && ry0 + (wh >> 16) >= sy0;
+    };
+
+    // 1) forward: T_end per pixel
+    for (int b = 0; b < nbatch; ++b) {
+        const int cnt = stage(b);
+        for (int m0 = 0; m0 < cnt; m0 += 32) {
+            uint32_t mask = __ballot_sync(0xffffffffu, strip_hit(m0 + lane, cnt));
+            while (mask) {
+                const int j = m0 + __ffs(mask) - 1;
+                mask &= mask - 1;
+                const float4 e1 = s_e1[j];
+                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
+                if ((uint32_t)(px - (xy & 0xffff)) > (uint32_t)(wh & 0xffff)) continue;
+                const float4 e0 = s_e0[j];
+                const float dx = fpx - e0.x;
+                const float adx = e0.z * dx;
+                const int ry0 = xy >> 16, rh = wh >> 16;
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) {
+                    if ((uint32_t)(py0 + r - ry0) <= (uint32_t)rh) {
+                        const float dy = (float)(py0 + r) - e0.y;
+                        const float pw = fmaf(dx, fmaf(e0.w, dy, adx), e1.x * dy * dy);
+                        const float al = fminf(0.99f, e1.y * ex2_approx(pw));
+                        t_forward(Tm[r], Te[r], al);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // 2) reverse: back to front through the batches and the entries
+    for (int b = nbatch - 1; b >= 0; --b) {
+        const int cnt = stage(b);
+        for (int m0 = ((cnt - 1) / 32) * 32; m0 >= 0; m0 -= 32) {
+            uint32_t mask = __ballot_sync(0xffffffffu, strip_hit(m0 + lane, cnt));
+            while (mask) {
+                const int bit = 31 - __clz(mask);
+                mask &= ~(1u << bit);
+                const int j = m0 + bit;
+                const float4 e1 = s_e1[j];
+                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
+                const bool colin = (uint32_t)(px - (xy & 0xffff)) <= (uint32_t)(wh & 0xffff);
+                const float4 e0 = s_e0[j];
+                const float4 abc = s_abc[j];
+                const float4 col = s_rgb[j];
+                const float dx = fpx - e0.x;
+                const float adx = e0.z * dx;
+                const int ry0 = xy >> 16, rh = wh >> 16;
+                float g_mx = 0.f, g_my = 0.f, g_a = 0.f, g_b = 0.f, g_c = 0.f, g_o = 0.f;
+                float g_r = 0.f, g_g = 0.f, g_bl = 0.f;
+#pragma unroll
+                for (int r = 0; r < PPT; ++r) {
+                    if (colin && (uint32_t)(py0 + r - ry0) <= (uint32_t)rh) {
+                        const float dy = (float)(py0 + r) - e0.y;
+                        const float pw = fmaf(dx, fmaf(e0.w, dy, adx), e1.x * dy * dy);
+                        const float G = ex2_approx(pw);
+                        const float araw = e1.y * G;
+                        const float al = fminf(0.99f, araw);
+                        const float oma = 1.0f - al;
+                        t_reverse(Tm[r], Te[r], oma);
+                        const float Ti = t_value(Tm[r], Te[r]);
+                        const float wv = fmaf(col.x, dC[r][0], fmaf(col.y, dC[r][1], fmaf(col.z, dC[r][2], dA[r])));
+                        const float dal = Ti * (wv - S[r]);
+                        S[r] = fmaf(al, wv, oma * S[r]);
+                        const float ta = Ti * al;
+                        g_r = fmaf(ta, dC[r][0], g_r);
+                        g_g = fmaf(ta, dC[r][1], g_g);
+                        g_bl = fmaf(ta, dC[r][2], g_bl);
+                        if (araw < 0.99f) {
+                            g_o = fmaf(dal, G, g_o);
+                            const float dq = -0.5f * dal * al;
+                            g_a = fmaf(dq, dx * dx, g_a);
+                            g_b = fmaf(dq, 2.0f * dx * dy, g_b);
+                            g_c = fmaf(dq, dy * dy, g_c);
+                            g_mx = fmaf(dq, -2.0f * fmaf(abc.x, dx, abc.y * dy), g_mx);
+                            g_my = fmaf(dq, -2.0f * fmaf(abc.y, dx, abc.z * dy), g_my);
+                        }
+                    }
+                }
+                g_mx = warp_sum(g_mx);
+                g_my = warp_sum(g_my);
+                g_a = warp_sum(g_a);
+                g_b = warp_sum(g_b);
+                g_c = warp_sum(g_c);
+                g_o = warp_sum(g_o);
+                g_r = warp_sum(g_r);
+                g_g = warp_sum(g_g);
+                g_bl = warp_sum(g_bl);
+                if (lane == 0) {
+                    float4* acc = g2d + 3 * (size_t)__float_as_uint(abc.w);
+                    atomicAdd(acc, make_float4(g_mx, g_my, g_a, g_b));
+                    atomicAdd(acc + 1, make_float4(g_c, g_o, g_r, g_g));
+                    atomicAdd(&acc[2].x, g_bl);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Voxels. alpha = 1 - exp(-I), I = (t1 - t0)/6 (s(t0) + 4 s(tm) + s(t1)),
+// s(t) = sum_c W_c(f(t)) rho_c (trilinear weights), so
+// dalpha/drho_c = (1 - alpha) (t1 - t0)/6 (W_c(f0) + 4 W_c(fm) + W_c(f1)).
+// Accumulator of rank r: g2d[3 r .. 3 r + 2] = {d rho_0..3}, {d rho_4..7},
+// {d r, d g, d b, 0}.
+__device__ __forceinline__ void tri_weights(float fx, float fy, float fz, float s, float* Wc)
+{
+    const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+    Wc[0] = fmaf(s, gx * gy * gz, Wc[0]);
+    Wc[1] = fmaf(s, fx * gy * gz, Wc[1]);
+    Wc[2] = fmaf(s, gx * fy * gz, Wc[2]);
+    Wc[3] = fmaf(s, fx * fy * gz, Wc[3]);
+    Wc[4] = fmaf(s, gx * gy * fz, Wc[4]);
+    Wc[5] = fmaf(s, fx * gy * fz, Wc[5]);
+    Wc[6] = fmaf(s, gx * fy * fz, Wc[6]);
+    Wc[7] = fmaf(s, fx * fy * fz, Wc[7]);
+}
+
+// Ray-segment integral of one voxel for one pixel (the forward's arithmetic);
+// returns false on a miss. Fills the Simpson-weighted trilinear weights when Wc is given.
+__device__ __forceinline__ bool voxel_integral(const float4 b, const float* rho, const float* d, const float* inv,
+                                               float* integral, float* Wc)
+{
+    const float lo[3] = {b.x, b.y, b.z};
+    float t0 = -__int_as_float(0x7f800000), t1 = __int_as_float(0x7f800000);
+    bool miss = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float hi = lo[a] + b.w;
+        if (d[a] != 0.0f) {
+            float ta = lo[a] * inv[a], tb = hi * inv[a];
+            if (ta > tb) {
+                const float tmp = ta;
+                ta = tb;
+                tb = tmp;
+            }
+            t0 = fmaxf(t0, ta);
+            t1 = fminf(t1, tb);
+        } else if (0.0f < lo[a] || 0.0f > hi) {
+            miss = true;
+        }
+    }
+    t0 = fmaxf(t0, 0.0f);
+    if (miss || !(t1 > t0)) return false;
+    const float tm = 0.5f * (t0 + t1);
+    const float is = 1.0f / b.w;
+    const float f0x = clamp01((t0 * d[0] - lo[0]) * is), f0y = clamp01((t0 * d[1] - lo[1]) * is),
+                f0z = clamp01((t0 * d[2] - lo[2]) * is);
+    const float fmx = clamp01((tm * d[0] - lo[0]) * is), fmy = clamp01((tm * d[1] - lo[1]) * is),
+                fmz = clamp01((tm * d[2] - lo[2]) * is);
+    const float f1x = clamp01((t1 * d[0] - lo[0]) * is), f1y = clamp01((t1 * d[1] - lo[1]) * is),
+                f1z = clamp01((t1 * d[2] - lo[2]) * is);
+    const float s0 = trilinear(rho, f0x, f0y, f0z);
+    const float sm = trilinear(rho, fmx, fmy, fmz);
+    const float s1 = trilinear(rho, f1x, f1y, f1z);
+    const float len6 = (t1 - t0) * (1.0f / 6.0f);
+    *integral = len6 * (s0 + 4.0f * sm + s1);
+    if (Wc) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) Wc[c] = 0.f;
+        tri_weights(f0x, f0y, f0z, len6, Wc);
+        tri_weights(fmx, fmy, fmz, 4.0f * len6, Wc);
+        tri_weights(f1x, f1y, f1z, len6, Wc);
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kTilePix) k_raster_voxel_bwd(BuildWs w, RasterParams p,
+                                                               const uint32_t* __restrict__ ranks,
+                                                               const float4* __restrict__ dplanes,
+                                                               float4* __restrict__ g2d)
+{
+    constexpr int NT = kTilePix;
+    __shared__ float4 s_box[NT];
+    __shared__ float s_den[NT * 8];
+    __shared__ float4 s_rgb[NT];
+    __shared__ int4 s_rect[NT];
+    __shared__ uint32_t s_rank[NT];
+    __shared__ int s_wc[NT / 32];
+    if (w.hdr->overflow) return;
+    const int t = blockIdx.x, k = blockIdx.y;
+    const int tx = t % p.tiles_x, ty = t / p.tiles_x;
+    const int lane = threadIdx.x & 31;
+    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
+    const int py = ty * kTile + (threadIdx.x / kTile);
+    const int st = (ty / kTilesPerSuper) * p.supers_x + tx / kTilesPerSuper;
+    const int2 sg = w.seg[(size_t)st * p.N + k];
+    const int L = sg.y - sg.x;
+    if (L == 0) return;
+
+    const float dcx = ((float)px - p.cx) / p.fx, dcy = ((float)py - p.cy) / p.fy;
+    float d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d[a] = fmaf(p.Rt[3 * a], dcx, fmaf(p.Rt[3 * a + 1], dcy, p.Rt[3 * a + 2]));
+    const float nrm = rsqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+    float inv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        d[a] *= nrm;
+        inv[a] = 1.0f / d[a];
+    }
+    const float4 gpl = load_grad(dplanes, k, px, py, p.W, p.H);
+    float Tm = 1.f, S = 0.f;
+    int Te = 0;
+    // alpha rounds to 1 for a large integral: T is then 0 behind that entry,
+    // which the reverse walk cannot divide back, so the forward keeps T just
+    // before the first such entry (batch ob, slot oj)
+    float oTm = 0.f;
+    int oTe = 0, ob = -1, oj = -1;
+    const int nbatch = (L + NT - 1) / NT;
+    auto stage = [&](int b) -> int {
+        const int i = b * NT + threadIdx.x;
+        uint32_t rk = 0;
+        int4 r = make_int4(0, 0, -1, -1);
+        if (i < L) {
+            rk = ranks[sg.x + i];
+            r = w.r_rect[rk];
+        }
+        const bool hit = i < L && meets_tile(r, tx * kTile, ty * kTile);
+        int cnt;
+        const int slot = compact_slot<NT>(hit, s_wc, &cnt);
+        if (hit) {
+            s_box[slot] = w.r_geo[rk];
+            const float4 da = w.r_den[2 * (size_t)rk], db = w.r_den[2 * (size_t)rk + 1];
+            float* sd = s_den + 8 * slot;
+            sd[0] = da.x; sd[1] = da.y; sd[2] = da.z; sd[3] = da.w;
+            sd[4] = db.x; sd[5] = db.y; sd[6] = db.z; sd[7] = db.w;
+            s_rgb[slot] = w.r_rgb[rk];
+            s_rect[slot] = r;
+            s_rank[slot] = rk;
+        }
+        __syncthreads();
+        return cnt;
+    };
+
+    for (int b = 0; b < nbatch; ++b) {
+        const int cnt = stage(b);
+        for (int j = 0; j < cnt; ++j) {
+            const int4 rc = s_rect[j];
+            if (!(px >= rc.x && px <= rc.z && py >= rc.y && py <= rc.w)) continue;
+            float integral;
+            if (!voxel_integral(s_box[j], s_den + 8 * j, d, inv, &integral, nullptr)) continue;
+            const float al = 1.0f - __expf(-integral);
+            if (al >= 1.0f && Tm > 0.0f && ob < 0) {
+                oTm = Tm;
+                oTe = Te;
+                ob = b;
+                oj = j;
+            }
+            t_forward(Tm, Te, al);
+        }
+        __syncthreads();
+    }
+    for (int b = nbatch - 1; b >= 0; --b) {
+        const int cnt = stage(b);
+        for (int j = cnt - 1; j >= 0; --j) {
+            const int4 rc = s_rect[j];
+            const bool in = px >= rc.x && px <= rc.z && py >= rc.y && py <= rc.w;
+            float Wc[8], integral = 0.f;
+            bool hit = false;
+            if (in) hit = voxel_integral(s_box[j], s_den + 8 * j, d, inv, &integral, Wc);
+            float gr = 0.f, gg = 0.f, gb = 0.f, gd[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) gd[c] = 0.f;
+            if (hit) {
+                const float al = 1.0f - __expf(-integral);
+                const float oma = 1.0f - al;
+                const float4 col = s_rgb[j];
+                if (b == ob && j == oj) {
+                    Tm = oTm;
+                    Te = oTe;
+                } else if (oma > 0.0f) {
+                    t_reverse(Tm, Te, oma);
+                }
+                const float Ti = t_value(Tm, Te);
+                const float wv = fmaf(col.x, gpl.x, fmaf(col.y, gpl.y, fmaf(col.z, gpl.z, gpl.w)));
+                const float dal = Ti * (wv - S);
+                S = fmaf(al, wv, oma * S);
+                const float ta = Ti * al;
+                gr = ta * gpl.x;
+                gg = ta * gpl.y;
+                gb = ta * gpl.z;
+                const float dI = dal * oma;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) gd[c] = dI * Wc[c];
+            }
+            const bool any = __syncthreads_or(hit);
+            if (!any) continue;
+            gr = warp_sum(gr);
+            gg = warp_sum(gg);
+            gb = warp_sum(gb);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) gd[c] = warp_sum(gd[c]);
+            if (lane == 0) {
+                float4* acc = g2d + 3 * (size_t)s_rank[j];
+                atomicAdd(acc, make_float4(gd[0], gd[1], gd[2], gd[3]));
+                atomicAdd(acc + 1, make_float4(gd[4], gd[5], gd[6], gd[7]));
+                atomicAdd(acc + 2, make_float4(gr, gg, gb, 0.f));
+            }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+void launch_raster_gaussians_bwd(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks,
+                                 const float* dplanes, cudaStream_t s)
+{
+    const dim3 grid((unsigned)(p.tiles_x * p.tiles_y), (unsigned)p.N);
+    constexpr int kPPT = 2;
+    k_raster_gauss_bwd<kPPT><<<grid, kTilePix / kPPT, 0, s>>>(ws, p, ranks, reinterpret_cast<const float4*>(dplanes),
+                                                             reinterpret_cast<float4*>(ws.g2d));
+    note_launches(1);
+}
+
+void launch_raster_voxels_bwd(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, const float* dplanes,
+                              cudaStream_t s)
+{
+    const dim3 grid((unsigned)(p.tiles_x * p.tiles_y), (unsigned)p.N);
+    k_raster_voxel_bwd<<<grid, kTilePix, 0, s>>>(ws, p, ranks, reinterpret_cast<const float4*>(dplanes),
+                                                 reinterpret_cast<float4*>(ws.g2d));
+    note_launches(1);
+}
 
 void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
                              cudaStream_t s)

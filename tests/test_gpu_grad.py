@@ -1,0 +1,278 @@
+"""GPU adjoints (lf_composite_backward, lf_build_mpi_backward_*) against
+central finite differences of the FP64 oracle.
+
+The integer structure (culling, chunks, plane depths d_k, footprints, depth
+order) is frozen at the unperturbed point: the oracle's own decisions, which
+the parity tests show to be bit-identical to the GPU's. The loss is the
+linear functional L = sum(W * views) with seeded Gaussian weights W, so
+dL/dviews = W. Step h = 1e-6 max(1, |x|) per element (FP64). Opacities are
+kept below 0.95 so the alpha = 0.99 clamp never binds (a kink the finite
+difference would straddle). Bar: relative L2 error <= 1e-3 per parameter
+group over the sampled elements, and the same for random directional
+derivatives over whole groups.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2508_18540_gb300 import api
+from paper_2508_18540_gb300 import autograd as AG
+from paper_2508_18540_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2508_18540_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _fd_scene(seed=5, n=2000, res=64, N=8, V=5):
+    # the differentiable workload's distributions at the finite-difference size
+    # plus 20 culled copies: 10 behind the camera, 10 far outside the frustum
+    w = S.workload_display(seed=seed, n=n, res=res, N=N, V=V)
+    sc = w.scene
+    out = sc.subset(np.arange(20))
+    out.means = out.means.copy()
+    out.means[:10, 2] = -2.0
+    out.means[10:, 0] = 50.0
+    sc = S.GaussianScene(*(np.concatenate([a, b]) for a, b in
+                           zip((sc.means, sc.scales, sc.quats, sc.opacity, sc.rgb),
+                               (out.means, out.scales, out.quats, out.opacity, out.rgb))))
+    sc.opacity = np.minimum(sc.opacity, 0.95).astype(np.float32)
+    return S.Workload(w.name + "_fd", sc, w.camera, w.display, w.views, w.N, w.binning)
+
+
+class _OracleLoss:
+    """L(params) = sum(W * views) through the FP64 oracle with frozen structure."""
+
+    def __init__(self, orc, w, W):
+        self.orc, self.w, self.W = orc, w, W
+        self.ref = orc.make_ref(w.camera, w.display)
+        z, valid, self.rect = orc.gauss_decide(self.ref, w.scene)
+        self.order, self.chunk, self.d, self.count, self.M = orc.bin_primitives(self.ref, z, valid, w.N, w.binning)
+        sc = w.scene
+        self.p = {k: np.array(getattr(sc, k), np.float64) for k in ("means", "scales", "quats", "opacity", "rgb")}
+
+    def __call__(self, p):
+        o = self.orc
+        sc = S.GaussianScene(p["means"], p["scales"], p["quats"], p["opacity"], p["rgb"])
+        mean2d, conic, _ = o.gauss_values(self.ref, sc)
+        planes = o.splat_gaussians(self.ref, self.order, self.chunk, self.rect, mean2d, conic, p["opacity"],
+                                   p["rgb"], self.w.N)
+        v = self.w.views
+        views = o.composite(self.ref, planes, self.d, self.count, v.Vx, v.Vy, v.bilinear, v.bg)
+        return float(np.sum(self.W * views))
+
+    def fd_element(self, key, idx):
+        p = {k: a.copy() for k, a in self.p.items()}
+        x = p[key][idx]
+        h = 1e-6 * max(1.0, abs(x))
+        p[key][idx] = x + h
+        lp = self(p)
+        p[key][idx] = x - h
+        lm = self(p)
+        return (lp - lm) / (2 * h)
+
+    def fd_direction(self, key, u, scale):
+        p = {k: a.copy() for k, a in self.p.items()}
+        h = 1e-6 * max(1.0, scale)
+        base = p[key].copy()
+        p[key] = base + h * u
+        lp = self(p)
+        p[key] = base - h * u
+        lm = self(p)
+        return (lp - lm) / (2 * h)
+
+
+def _gpu_grads(w, W, dtype="f32"):
+    r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, dtype)
+    g = api.DeviceGaussians.from_scene(w.scene)
+    r.render(g)
+    grads, dplanes = r.backward(g, torch.from_numpy(W.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    st, _, _ = r.status()
+    assert st == 0
+    return {"means": grads.dmeans.cpu().numpy().astype(np.float64),
+            "scales": grads.dscales.cpu().numpy().astype(np.float64),
+            "quats": grads.dquats.cpu().numpy().astype(np.float64),
+            "opacity": grads.dopacity.cpu().numpy().astype(np.float64),
+            "rgb": grads.drgb.cpu().numpy().astype(np.float64)}, dplanes, r
+
+
+@pytest.fixture(scope="module")
+def fd_case(orc):
+    w = _fd_scene()
+    rng = np.random.default_rng(11)
+    W = rng.normal(size=(w.views.Vx * w.views.Vy, w.camera.Ny, w.camera.Nx, 4))
+    loss = _OracleLoss(orc, w, W)
+    g, _, _ = _gpu_grads(w, W)
+    return w, W, loss, g
+
+
+def test_gaussian_gradients_elementwise(fd_case):
+    w, W, loss, g = fd_case
+    rng = np.random.default_rng(12)
+    culled_in = np.flatnonzero(loss.chunk >= 0)
+    assert culled_in.size > 1000
+    pick = rng.choice(culled_in, 30, replace=False)
+    for key, width in (("means", 3), ("scales", 3), ("quats", 4), ("opacity", 1), ("rgb", 3)):
+        fd, gp = [], []
+        for i in pick:
+            for c in range(width):
+                idx = (i,) if width == 1 else (i, c)
+                fd.append(loss.fd_element(key, idx))
+                gp.append(g[key][idx])
+        fd, gp = np.array(fd), np.array(gp)
+        assert np.linalg.norm(fd) > 0, key
+        assert _rel(gp, fd) <= REL_TOL, (key, _rel(gp, fd))
+
+
+def test_gaussian_gradients_directional(fd_case):
+    w, W, loss, g = fd_case
+    rng = np.random.default_rng(13)
+    for key in ("means", "scales", "quats", "opacity", "rgb"):
+        for _ in range(3):
+            u = rng.normal(size=loss.p[key].shape)
+            u /= np.linalg.norm(u)
+            fd = loss.fd_direction(key, u, float(np.abs(loss.p[key]).max()))
+            an = float(np.sum(g[key] * u))
+            assert abs(an - fd) <= REL_TOL * max(abs(fd), 1e-12) + 1e-9, (key, an, fd)
+
+
+def test_culled_gaussians_get_zero_gradient(fd_case):
+    w, W, loss, g = fd_case
+    out = loss.chunk < 0
+    assert out.any()
+    for key in g:
+        assert np.all(g[key][out] == 0.0), key
+
+
+def test_composite_adjoint_against_fd(orc):
+    # dplanes of the composite alone, on random texels, nearest and bilinear
+    for bilinear in (False, True):
+        w = _fd_scene(seed=6, n=1500)
+        w = S.Workload(w.name, w.scene, w.camera, w.display, S.ViewSet(5, 1, bilinear, (0.2, 0.1, 0.3)), w.N,
+                       w.binning)
+        rng = np.random.default_rng(14)
+        W = rng.normal(size=(5, w.camera.Ny, w.camera.Nx, 4))
+        _, dplanes, r = _gpu_grads(w, W)
+        dp = dplanes.cpu().numpy().astype(np.float64)
+        o = orc.render(w)
+        planes = o["planes"].copy()
+        ref, d, count = o["ref"], o["d"], o["count"]
+
+        def L(pl):
+            return float(np.sum(W * orc.composite(ref, pl, d, count, 5, 1, bilinear, (0.2, 0.1, 0.3))))
+
+        nz = np.argwhere(np.abs(dp).sum(axis=-1) > 0)
+        assert nz.shape[0] > 100
+        sel = nz[rng.choice(nz.shape[0], 40, replace=False)]
+        fd, an = [], []
+        for (k, y, x) in sel:
+            for c in range(4):
+                p = planes.copy()
+                x0 = p[k, y, x, c]
+                h = 1e-6 * max(1.0, abs(x0))
+                p[k, y, x, c] = x0 + h
+                lp = L(p)
+                p[k, y, x, c] = x0 - h
+                lm = L(p)
+                fd.append((lp - lm) / (2 * h))
+                an.append(dp[k, y, x, c])
+        assert _rel(np.array(an), np.array(fd)) <= REL_TOL
+
+
+def test_fp16_plane_gradients_track_fp32(fd_case):
+    w, W, loss, g32 = fd_case
+    g16, _, _ = _gpu_grads(w, W, "f16")
+    for key in g32:
+        assert _rel(g16[key], g32[key]) <= 2e-2, key
+
+
+def test_voxel_gradients_against_fd(orc):
+    cam = S.identity_camera(48, t=(0.0, 0.0, 6.0))
+    vs = S.sparse_voxels(1500, 7, base_res=32)
+    sc = S.VoxelScene(vs.ijk, vs.level, vs.origin, vs.base_size,
+                      (0.5 * vs.density8).astype(np.float32), vs.rgb)
+    disp = S.display_for(S.harmonic_focal(4.0, 8.0), 0.15)
+    views = S.ViewSet(5, 1, False)
+    N = 6
+    rng = np.random.default_rng(15)
+    W = rng.normal(size=(5, 48, 48, 4))
+    r = api.LightFieldRenderer(cam, disp, views, N, "quantile", "f32")
+    v = api.DeviceVoxels.from_scene(sc)
+    r.render(v)
+    grads, _ = r.backward(v, torch.from_numpy(W.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    assert r.status()[0] == 0
+    gd = grads.ddensity8.cpu().numpy().astype(np.float64)
+    gc = grads.drgb.cpu().numpy().astype(np.float64)
+
+    ref = orc.make_ref(cam, disp)
+    z, valid, rect = orc.voxel_decide(ref, sc)
+    order, chunk, d, count, M = orc.bin_primitives(ref, z, valid, N, "quantile")
+    base = {"density8": np.array(sc.density8, np.float64), "rgb": np.array(sc.rgb, np.float64)}
+
+    def L(p):
+        s2 = S.VoxelScene(sc.ijk, sc.level, sc.origin, sc.base_size, p["density8"], p["rgb"])
+        planes = orc.splat_voxels(ref, order, chunk, rect, s2, N)
+        return float(np.sum(W * orc.composite(ref, planes, d, count, 5, 1, False)))
+
+    vis = np.flatnonzero(np.abs(gc).sum(axis=1) > 0)
+    assert vis.size > 50
+    pick = rng.choice(vis, 20, replace=False)
+    for key, g, width in (("density8", gd, 8), ("rgb", gc, 3)):
+        fd, an = [], []
+        for i in pick:
+            for c in range(width):
+                p = {k: a.copy() for k, a in base.items()}
+                x0 = p[key][i, c]
+                h = 1e-6 * max(1.0, abs(x0))
+                p[key][i, c] = x0 + h
+                lp = L(p)
+                p[key][i, c] = x0 - h
+                lm = L(p)
+                fd.append((lp - lm) / (2 * h))
+                an.append(g[i, c])
+        assert _rel(np.array(an), np.array(fd)) <= REL_TOL, key
+
+
+def test_autograd_function_and_fit_step():
+    # torch.autograd path: gradients equal the direct adjoint call, and a few
+    # gradient steps on opacities reduce the L2 loss against target views
+    w = _fd_scene(seed=8, n=3000)
+    tgt_scene = S.perturbed(w.scene, 9, mean_std=0.0)
+    r_t = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f32")
+    target = r_t.render(api.DeviceGaussians.from_scene(tgt_scene)).clone()
+    r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f32")
+    g = api.DeviceGaussians.from_scene(w.scene)
+    params = [t.clone().requires_grad_(True) for t in (g.means, g.scales, g.quats, g.opacity, g.rgb)]
+    views = AG.render_gaussians(r, *params)
+    loss = ((views - target) ** 2).sum()
+    loss.backward()
+    grads, _ = r.backward(g, (2.0 * (views.detach() - target)).contiguous())
+    for p, ref_g in zip(params, (grads.dmeans, grads.dscales, grads.dquats, grads.dopacity, grads.drgb)):
+        assert torch.allclose(p.grad, ref_g, rtol=1e-4, atol=1e-6)
+    opa = params[3].detach().clone().requires_grad_(True)
+    opt = torch.optim.Adam([opa], lr=0.01)
+    losses = []
+    for _ in range(15):
+        opt.zero_grad()
+        v = AG.render_gaussians(r, params[0].detach(), params[1].detach(), params[2].detach(), opa,
+                                params[4].detach())
+        l2 = ((v - target) ** 2).sum()
+        l2.backward()
+        opt.step()
+        with torch.no_grad():
+            opa.clamp_(0.01, 0.99)
+        losses.append(float(l2.detach()))
+    assert losses[-1] < 0.8 * losses[0], losses
