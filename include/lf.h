@@ -236,6 +236,23 @@ size_t lf_composite_workspace_size(int32_t N, const lf_view_set* views);
 lf_status lf_composite(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views, float* out,
                        void* ws, size_t ws_bytes, cudaStream_t stream);
 
+/* Allocation-free form of lf_composite (the paper has no counterpart): the
+ * same computation and result, with its scratch in a static device array of
+ * lf_composite_noalloc_max_bytes() bytes (1 MiB) inside the library instead
+ * of a caller workspace, for callers that cannot provide device memory (for
+ * example a display runtime's per-frame present callback that must not call
+ * a device allocator). The scratch address is looked up once per device with
+ * that device current (the first call on a device does it). Requests whose
+ * scratch (lf_composite_workspace_size) exceeds the limit fail with
+ * LF_ERR_WORKSPACE and a message. Calls that overlap in time share the one
+ * scratch array and race: the caller must serialise them. Other arguments
+ * and errors as lf_composite. */
+lf_status lf_composite_noalloc(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
+                               float* out, cudaStream_t stream);
+
+/* Size in bytes of lf_composite_noalloc's static scratch. */
+size_t lf_composite_noalloc_max_bytes(void);
+
 /* ---- differentiation ------------------------------------------------------ */
 /*
  * Reverse-mode adjoints of the two stages, for fitting a scene against

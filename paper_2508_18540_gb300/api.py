@@ -240,6 +240,20 @@ def lf_composite(planes: Planes, ref: L.LfRefCamera, views, out: torch.Tensor, w
                               ws.numel(), _stream_ptr(stream)))
 
 
+def lf_composite_noalloc(planes: Planes, ref: L.LfRefCamera, views, out: torch.Tensor, stream=None):
+    """lf_composite with the library's static scratch instead of a workspace
+    (calls must not overlap in time)."""
+    vs = view_set(views)
+    _need(out, (vs.Vx * vs.Vy, ref.base.Ny, ref.base.Nx, 4), torch.float32, "views")
+    ps = planes.c_struct()
+    check(load().lf_composite_noalloc(ctypes.byref(ps), ctypes.byref(ref), ctypes.byref(vs), _ptr(out),
+                                      _stream_ptr(stream)))
+
+
+def lf_composite_noalloc_max_bytes() -> int:
+    return int(load().lf_composite_noalloc_max_bytes())
+
+
 # ---------------------------------------------------------------------------
 # differentiation
 # ---------------------------------------------------------------------------

@@ -709,4 +709,83 @@ lf_status lf_build_mpi_backward_voxels(const lf_voxels* v, const lf_ref_camera* 
     return check_launch("voxel gradient scatter");
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free composite. The paper has no counterpart; this is a
+// deployment form of lf_composite for callers that cannot hand the library a
+// device buffer: e.g. a display runtime's per-frame present callback, which
+// must not call into a device allocator (allocation can synchronise the
+// device and stall the frame) and owns no workspace of its own. Its scratch
+// (the per-(view, plane) coefficient tables, the error word and the
+// wide-shift flags) lives in the file-scope device array below instead of a
+// caller workspace. The error word and the flags must be zero before the
+// composite kernel reads them; every call zeroes them on its stream first.
+// Calls that overlap in time (two streams, or two host threads) share this
+// one array and race; the caller serialises them.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace lf {
+constexpr size_t kStaticCompBytes = 1u << 20;   // 1 MiB: e.g. N = 512 planes x 128 views
+static __device__ __align__(256) unsigned char g_comp_scratch[kStaticCompBytes];
+
+// device address of g_comp_scratch per device, looked up once per device
+// with that device current
+static std::mutex g_scratch_mu;
+static std::map<int, void*> g_scratch_addr;
+
+static lf_status static_scratch(void** out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return check_launch("cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    auto it = g_scratch_addr.find(dev);
+    if (it != g_scratch_addr.end()) {
+        *out = it->second;
+        return LF_OK;
+    }
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_comp_scratch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LF_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") +
+                                     cudaGetErrorString(e));
+    }
+    g_scratch_addr[dev] = p;
+    *out = p;
+    return LF_OK;
+}
+}  // namespace lf
+
+extern "C" {
+
+size_t lf_composite_noalloc_max_bytes(void) { return lf::kStaticCompBytes; }
+
+lf_status lf_composite_noalloc(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
+                               float* out, cudaStream_t stream)
+{
+    if (!planes || !views) return fail(LF_ERR_INVALID_ARG, "NULL argument");
+    if (planes->N < 1 || views->Vx < 1 || views->Vy < 1 || views->Vx > 65535 || views->Vy > 65535)
+        return fail(LF_ERR_INVALID_ARG, "N and view counts must be positive");
+    const size_t need = comp_ws_layout(planes->N, views->Vx, views->Vy, nullptr, nullptr);
+    if (need > lf::kStaticCompBytes)
+        return fail(LF_ERR_WORKSPACE, "lf_composite_noalloc: N = " + std::to_string(planes->N) + " planes and " +
+                                          std::to_string(views->Vx) + " x " + std::to_string(views->Vy) +
+                                          " views need " + std::to_string(need) + " scratch bytes, above its " +
+                                          std::to_string(lf::kStaticCompBytes) + "-byte static limit; use lf_composite");
+    void* scratch = nullptr;
+    lf_status st = lf::static_scratch(&scratch);
+    if (st != LF_OK) return st;
+    CompWs cw;
+    st = check_composite_args(planes, ref, views, out, scratch, lf::kStaticCompBytes, &cw);
+    if (st != LF_OK) return st;
+    CompParams p;
+    fill_comp_params(planes, ref, views, &p);
+    if (cudaMemsetAsync(cw.err, 0, sizeof(int) * (1 + (size_t)planes->N), stream) != cudaSuccess)
+        return check_launch("composite reset");
+    launch_comp_coeffs(p, planes->d, planes->count, cw, stream);
+    if ((st = check_launch("composite coefficients")) != LF_OK) return st;
+    launch_composite(p, planes->rgba, planes->count, cw, out, stream);
+    return check_launch("composite");
+}
+
 }  // extern "C"
