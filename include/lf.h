@@ -292,6 +292,93 @@ lf_status lf_build_mpi_backward_voxels(const lf_voxels* v, const lf_ref_camera* 
                                        const float* dplanes, lf_voxels_grad* grad, void* ws, size_t ws_bytes,
                                        cudaStream_t stream);
 
+/* ---- batching ------------------------------------------------------------ */
+/*
+ * Several G2LF scenes of uneven sizes, view counts, resolutions and N
+ * rendered together: each scene's build runs up to its tile lists, then ONE
+ * persistent raster launch covers the (tile, chunk) items of every scene and
+ * ONE persistent staged-composite launch covers the (view group, row band,
+ * column tile) items of every scene, CTAs pulling items from a global
+ * counter. The whole batch can be captured once into a CUDA graph and
+ * relaunched per frame. An autotuner times candidate plans (views per
+ * thread, composite tile shape, raster pixels per thread, scene schedule)
+ * on the batch itself. Results are identical for every plan.
+ */
+
+/* One scene of a batch. Every pointer is device memory the caller owns and
+ * keeps alive (and unmoved) for the life of the batch; the fields mean what
+ * they mean for lf_build_mpi_gaussians (ws: its build workspace) and
+ * lf_composite (cws: its composite workspace, out: its views). All scenes of
+ * a batch share planes.dtype and views.bilinear. */
+typedef struct {
+    lf_gaussians g;
+    lf_ref_camera ref;
+    int32_t N, binning;
+    lf_planes planes;
+    lf_view_set views;
+    float* out;
+    void* ws;
+    size_t ws_bytes;
+    void* cws;
+    size_t cws_bytes;
+} lf_batch_scene;
+
+/* Launch plan of a batch:
+ *  views_per_thread  composite views per thread: 3, 5 or 9;
+ *  tile_x            composite CTA tile width (columns): 128, 256 or 512
+ *                    (the tile is tile_x x 512/tile_x pixels);
+ *  raster_ppt        raster pixels per thread: 2 or 4;
+ *  schedule          0: items in scene order; 1: largest scenes first. */
+typedef struct {
+    int32_t views_per_thread;
+    int32_t tile_x;
+    int32_t raster_ppt;
+    int32_t schedule;
+} lf_batch_plan;
+
+typedef struct lf_batch lf_batch;   /* opaque host-side batch object */
+
+/* Validates the scenes and copies their descriptions (host) into a new batch
+ * object. Errors: LF_ERR_INVALID_ARG (bad scene, mixed dtype or sampling),
+ * LF_ERR_UNSUPPORTED (a plane row that is not a multiple of 16 bytes). */
+lf_status lf_batch_create(const lf_batch_scene* scenes, int32_t n_scenes, lf_batch** out);
+
+/* Device bytes of the batch workspace (scene tables and work counters). */
+size_t lf_batch_workspace_size(const lf_batch* b);
+
+/* Sets the plan (NULL = default {9, 512, 2, 1}) and uploads the scene tables
+ * into ws (device, ws_bytes, 256-byte aligned) on stream. Must be called
+ * before lf_batch_render and again after a plan change; not during capture. */
+lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Enqueues one frame of the whole batch on stream (builds, persistent
+ * raster, coefficient tables, persistent composite). No host
+ * synchronisation; may be captured. */
+lf_status lf_batch_render(lf_batch* b, cudaStream_t stream);
+
+/* Captures lf_batch_render on stream (which must not be the legacy default
+ * stream) into a CUDA graph kept by b, replacing any earlier one. */
+lf_status lf_batch_capture(lf_batch* b, cudaStream_t stream);
+
+/* Launches the captured graph on stream (LF_ERR_INVALID_ARG if none). */
+lf_status lf_batch_launch(lf_batch* b, cudaStream_t stream);
+
+/* Times every candidate plan (coordinate search: composite views per thread
+ * x tile width, then raster pixels per thread x schedule), reps frames each
+ * after one warm-up frame, with CUDA events on stream; leaves b prepared with
+ * the fastest plan and returns it in *best (host) and its mean frame time in
+ * *best_ms (host, may be NULL). Synchronises the stream. */
+lf_status lf_batch_autotune(lf_batch* b, void* ws, size_t ws_bytes, int32_t reps, cudaStream_t stream,
+                            lf_batch_plan* best, float* best_ms);
+
+/* Synchronises stream and returns LF_ERR_OVERFLOW if a scene's tile list
+ * overflowed its capacity, LF_ERR_TIMEOUT if a bounded wait of the
+ * composite gave up, else LF_OK. */
+lf_status lf_batch_status(lf_batch* b, cudaStream_t stream);
+
+/* Frees the batch object and its graph (device memory stays the caller's). */
+lf_status lf_batch_destroy(lf_batch* b);
+
 /* ---- tracing -------------------------------------------------------------- */
 
 /* Number of kernels the library has launched in this process so far. */

@@ -74,6 +74,16 @@ class LfViewSet(ctypes.Structure):
     _fields_ = [("Vx", _I32), ("Vy", _I32), ("bilinear", _I32), ("bg", ctypes.c_float * 3)]
 
 
+class LfBatchScene(ctypes.Structure):
+    _fields_ = [("g", LfGaussians), ("ref", LfRefCamera), ("N", _I32), ("binning", _I32), ("planes", LfPlanes),
+                ("views", LfViewSet), ("out", _P), ("ws", _P), ("ws_bytes", ctypes.c_size_t), ("cws", _P),
+                ("cws_bytes", ctypes.c_size_t)]
+
+
+class LfBatchPlan(ctypes.Structure):
+    _fields_ = [("views_per_thread", _I32), ("tile_x", _I32), ("raster_ppt", _I32), ("schedule", _I32)]
+
+
 # (name, restype, argtypes) of every exported symbol declared in include/lf.h
 SIGNATURES = [
     ("lf_make_ref_camera", ctypes.c_int, [ctypes.POINTER(LfCamera), ctypes.POINTER(LfDisplay),
@@ -99,6 +109,16 @@ SIGNATURES = [
     ("lf_build_mpi_backward_voxels", ctypes.c_int, [ctypes.POINTER(LfVoxels), ctypes.POINTER(LfRefCamera),
                                                     ctypes.POINTER(LfPlanes), _P, ctypes.POINTER(LfVoxelsGrad),
                                                     _P, ctypes.c_size_t, _P]),
+    ("lf_batch_create", ctypes.c_int, [ctypes.POINTER(LfBatchScene), _I32, ctypes.POINTER(_P)]),
+    ("lf_batch_workspace_size", ctypes.c_size_t, [_P]),
+    ("lf_batch_prepare", ctypes.c_int, [_P, ctypes.POINTER(LfBatchPlan), _P, ctypes.c_size_t, _P]),
+    ("lf_batch_render", ctypes.c_int, [_P, _P]),
+    ("lf_batch_capture", ctypes.c_int, [_P, _P]),
+    ("lf_batch_launch", ctypes.c_int, [_P, _P]),
+    ("lf_batch_autotune", ctypes.c_int, [_P, _P, ctypes.c_size_t, _I32, _P, ctypes.POINTER(LfBatchPlan),
+                                         ctypes.POINTER(ctypes.c_float)]),
+    ("lf_batch_status", ctypes.c_int, [_P, _P]),
+    ("lf_batch_destroy", ctypes.c_int, [_P]),
     ("lf_launch_count", _I64, []),
     ("lf_trace_enable", ctypes.c_int, [_I32]),
     ("lf_trace_collect", _I32, [_P, _P, _P, _I32]),

@@ -400,6 +400,102 @@ class LightFieldRenderer:
 
 
 # ---------------------------------------------------------------------------
+# batching: several scenes, persistent launches, CUDA graph, autotuner
+# ---------------------------------------------------------------------------
+
+class BatchRenderer:
+    """Several Gaussian scenes rendered as one batch (lf_batch_*): per-scene
+    builds, one persistent raster and one persistent composite launch over
+    every scene's work items; optionally captured once into a CUDA graph.
+    workloads: objects with scene, camera, display, views, N, binning.
+    Scene data is copied to the device once (update it in place through
+    .prims[i] tensors; the captured graph reads the same buffers)."""
+
+    def __init__(self, workloads, dtype: str = "f16", device="cuda", stream: Optional[torch.cuda.Stream] = None):
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
+        self.parts = []
+        scenes = (L.LfBatchScene * len(workloads))()
+        for i, w in enumerate(workloads):
+            r = LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, dtype, device=device)
+            g = DeviceGaussians.from_scene(w.scene, device=device)
+            r._ensure(g.n)
+            pv = r.planes_view(g.n)
+            sc = scenes[i]
+            sc.g = g.c_struct()
+            sc.ref = r.ref
+            sc.N, sc.binning = r.N, BINNING[w.binning]
+            sc.planes = pv.c_struct()
+            sc.views = view_set(w.views)
+            sc.out = r.out.data_ptr()
+            sc.ws, sc.ws_bytes = r.ws.data_ptr(), r.ws.numel()
+            sc.cws, sc.cws_bytes = r.cws.data_ptr(), r.cws.numel()
+            self.parts.append((r, g, pv))
+        self._scenes = scenes
+        h = ctypes.c_void_p()
+        check(load().lf_batch_create(scenes, len(workloads), ctypes.byref(h)))
+        self.handle = h
+        self.ws = alloc_workspace(int(load().lf_batch_workspace_size(h)), device)
+        self.plan = None
+        self.prepare()
+
+    @property
+    def outputs(self):
+        return [r.out for r, _, _ in self.parts]
+
+    @property
+    def prims(self):
+        return [g for _, g, _ in self.parts]
+
+    @property
+    def planes(self):
+        return [pv for _, _, pv in self.parts]
+
+    def prepare(self, plan: Optional[dict] = None):
+        p = None
+        if plan is not None:
+            p = L.LfBatchPlan(plan["views_per_thread"], plan["tile_x"], plan["raster_ppt"], plan["schedule"])
+        check(load().lf_batch_prepare(self.handle, ctypes.byref(p) if p is not None else None, _ptr(self.ws),
+                                      self.ws.numel(), ctypes.c_void_p(self.stream.cuda_stream)))
+        self.plan = plan
+
+    def render(self):
+        check(load().lf_batch_render(self.handle, ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def capture(self):
+        check(load().lf_batch_capture(self.handle, ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def launch(self):
+        check(load().lf_batch_launch(self.handle, ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def autotune(self, reps: int = 2):
+        best = L.LfBatchPlan()
+        ms = ctypes.c_float(0.0)
+        check(load().lf_batch_autotune(self.handle, _ptr(self.ws), self.ws.numel(), int(reps),
+                                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(best), ctypes.byref(ms)))
+        self.plan = {"views_per_thread": best.views_per_thread, "tile_x": best.tile_x,
+                     "raster_ppt": best.raster_ppt, "schedule": best.schedule}
+        return self.plan, float(ms.value)
+
+    def status(self):
+        return load().lf_batch_status(self.handle, ctypes.c_void_p(self.stream.cuda_stream))
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            load().lf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
 # tracing
 # ---------------------------------------------------------------------------
 

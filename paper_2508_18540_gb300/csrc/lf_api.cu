@@ -58,6 +58,13 @@ void trace_end(cudaStream_t s)
     g_trace_open = -1;
 }
 
+bool trace_swap(bool on)
+{
+    const bool old = g_trace_on;
+    g_trace_on = on;
+    return old;
+}
+
 void set_error(const std::string& msg) { g_last_error = msg; }
 
 lf_status fail(lf_status st, const std::string& msg)
@@ -148,7 +155,7 @@ static int64_t default_cap(int64_t n) { return 8 * n + (1ll << 20); }
 
 // pair capacity of a build workspace: the largest one ws_bytes holds (the
 // layout size grows monotonically with it); 0 if none
-static int64_t ws_capacity(int64_t n, int32_t N, int32_t W, int32_t H, size_t ws_bytes)
+int64_t ws_capacity(int64_t n, int32_t N, int32_t W, int32_t H, size_t ws_bytes)
 {
     int64_t lo = 0, hi = (1ll << 31) - 1;
     while (lo < hi) {
@@ -277,10 +284,14 @@ static lf_status check_composite_args(const lf_planes* planes, const lf_ref_came
     return LF_OK;
 }
 
+// The build pipeline. With prefix_only the raster is left to the caller
+// (the batched persistent raster), which gets the carved workspace and the
+// sorted tile-list ranks back.
 template <typename Launch>
 static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, int32_t binning, void* ws,
                               size_t ws_bytes, lf_planes* out, cudaStream_t stream, int kind, Launch project,
-                              const void* raster_arg)
+                              const void* raster_arg, bool prefix_only = false, BuildWs* w_out = nullptr,
+                              const uint32_t** ranks_out = nullptr)
 {
     lf_status st = check_ref(ref);
     if (st != LF_OK) return st;
@@ -355,6 +366,11 @@ static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, in
     trace_end(stream);
     if ((st = check_launch("tile lists")) != LF_OK) return st;
 
+    if (prefix_only) {
+        if (w_out) *w_out = w;
+        if (ranks_out) *ranks_out = ranks;
+        return LF_OK;
+    }
     RasterParams rp;
     fill_raster_params(ref, N, out->dtype, &rp);
     trace_begin(kind == 0 ? "raster_gaussians" : "raster_voxels", stream);
@@ -364,6 +380,34 @@ static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, in
         launch_raster_voxels(w, rp, ranks, out->rgba, stream);
     trace_end(stream);
     return check_launch("rasterise");
+}
+
+lf_status build_gaussians_prefix(const lf_gaussians* g, const lf_ref_camera* ref, int32_t N, int32_t binning,
+                                 void* ws, size_t ws_bytes, lf_planes* out, cudaStream_t stream, BuildWs* w,
+                                 const uint32_t** ranks)
+{
+    if (!g) return fail(LF_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n > 0 && (!g->means || !g->scales || !g->quats || !g->opacity || !g->rgb))
+        return fail(LF_ERR_INVALID_ARG, "a Gaussian attribute pointer is NULL");
+    const lf_gaussians gc = *g;
+    auto project = [&](const ProjParams& pp, const BuildWs& ww, cudaStream_t s) {
+        launch_project_gaussians(gc, pp, ww, out->rect, out->chunk, s);
+    };
+    return build_common(g->n, ref, N, binning, ws, ws_bytes, out, stream, 0, project, &gc, true, w, ranks);
+}
+
+lf_status composite_args(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
+                         const float* out, void* ws, size_t ws_bytes, CompWs* cw, CompParams* p)
+{
+    const lf_status st = check_composite_args(planes, ref, views, out, ws, ws_bytes, cw);
+    if (st != LF_OK) return st;
+    fill_comp_params(planes, ref, views, p);
+    return LF_OK;
+}
+
+void raster_params(const lf_ref_camera* ref, int32_t N, int32_t dtype, RasterParams* p)
+{
+    fill_raster_params(ref, N, dtype, p);
 }
 
 }  // namespace lf

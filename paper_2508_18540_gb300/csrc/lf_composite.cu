@@ -196,8 +196,6 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
 // All waits are bounded; a wait that gives up sets the error word.
 // ---------------------------------------------------------------------------
 
-constexpr int kStages = 6;
-constexpr int kStagedThreads = 512;                  // consumer threads
 constexpr int kStagedWarps = kStagedThreads / 32;     // consumer warps
 constexpr int kStagedBlock = kStagedThreads + 32;     // + one producer warp
 constexpr long long kSpinLimit = 1ll << 26;
@@ -307,15 +305,6 @@ struct Texel<LF_BF16> {
     }
 };
 
-struct StagedGeom {
-    int TX, BY, VG, rows_per_y;    // rows_per_y: 1 nearest, 2 bilinear
-    int padl;                      // zero texels left of every staged row (16 bytes)
-    int row_texels;                // padl + W + right pad, a multiple of 16 bytes
-    size_t row_bytes, stage_bytes, smem_bytes;
-    int groups_x;                  // view groups per view row
-};
-
-inline size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 
 // floor(fma(g, x, h)) as the bit pattern of (value + 1.5 * 2^23) rounded
 // toward minus infinity; callers add base - kMagicBits to get an index.
@@ -340,14 +329,65 @@ struct CoefBlock {
     static constexpr int kFloats = 4 + 4 * ((VG + 3) / 4);
 };
 
+inline size_t round16(size_t v) { return (v + 15) / 16 * 16; }
+
+}  // namespace
+
+// Staged layout of one composite: TX columns x BY rows per CTA (TX a
+// multiple of 32 not above tx_max, BY = 512 / TX), VG views per thread.
+StagedGeom staged_geom(const CompParams& p, int texel_bytes, bool bilinear, int VG, int tx_max)
+{
+    StagedGeom G;
+    const int nx32 = (p.Nx + 31) / 32 * 32;
+    G.TX = nx32 < tx_max ? nx32 : tx_max;
+    G.BY = kStagedThreads / G.TX;
+    G.VG = VG;
+    G.rows_per_y = bilinear ? 2 : 1;
+    G.padl = 16 / texel_bytes;
+    G.row_texels = (int)(round16((size_t)(G.padl + p.W + 1) * texel_bytes) / texel_bytes);
+    G.row_bytes = (size_t)G.row_texels * texel_bytes;
+    G.stage_bytes = G.row_bytes * G.BY * G.rows_per_y;
+    G.groups_x = (p.Vx + VG - 1) / VG;
+    G.smem_bytes = kStages * G.stage_bytes + 2 * kStages * 8 + sizeof(float) * (size_t)p.N * (4 + 4 * ((VG + 3) / 4)) +
+                   sizeof(int) * (size_t)p.N;
+    return G;
+}
+
+namespace {
+
+// Per-thread constants of one staged item, computed once per item.
+struct ThreadGeom {
+    float xf, yf;          // output pixel
+    int psy;               // P_s y
+    int base_x;            // P_s x + left pad - magic bits
+    int H;                 // plane rows
+    uint32_t row0;         // offset of the thread's (first) staged row in a stage
+    uint32_t row_bytes;    // staged row pitch
+    uint32_t maxi;         // first right-pad texel
+};
+
+__device__ __forceinline__ ThreadGeom thread_geom(const CompParams& p, const StagedGeom& G, int x, int y, int ty)
+{
+    ThreadGeom t;
+    t.xf = (float)x;
+    t.yf = (float)y;
+    t.psy = p.P_s * y;
+    t.base_x = p.P_s * x + G.padl - kMagicBits;
+    t.H = p.H;
+    t.row0 = (uint32_t)(ty * G.rows_per_y) * (uint32_t)G.row_bytes;
+    t.row_bytes = (uint32_t)G.row_bytes;
+    t.maxi = (uint32_t)(G.padl + p.W);
+    return t;
+}
+
 // hdr: (gm_x, gm_y, h_y, -); ca: shared address of the plane's coefficient
 // block; sb: shared address of the stage holding the plane's rows
 template <int DT, bool BILINEAR, int VG, bool CLAMP>
 __device__ __forceinline__ void blend_plane(float (&acc)[VG][4], float4 hdr, uint32_t ca, uint32_t sb,
-                                            const StagedGeom& G, const CompParams& p, int x, int y, int ty,
-                                            uint32_t maxi)
+                                            const ThreadGeom& tg)
 {
     using TX_ = Texel<DT>;
+    const uint32_t maxi = tg.maxi;
     float c[3 + 4 * ((VG + 3) / 4)];
     c[0] = hdr.x;
     c[1] = hdr.y;
@@ -361,12 +401,12 @@ __device__ __forceinline__ void blend_plane(float (&acc)[VG][4], float4 hdr, uin
         c[3 + 4 * e + 3] = v.w;
     }
     const float gmx = c[0];
-    const float xf = (float)x;
-    const int base_x = p.P_s * x + G.padl - kMagicBits;
+    const float xf = tg.xf;
+    const int base_x = tg.base_x;
     if (!BILINEAR) {
-        const int iy = plane_row(p.P_s, y, c[1], c[2]);
-        if (iy < 0 || iy >= p.H) return;
-        const uint32_t row = sb + (uint32_t)(ty * G.row_bytes);
+        const int iy = tg.psy + (__float_as_int(floor_magic<true>(c[1], tg.yf, c[2])) - kMagicBits);
+        if (iy < 0 || iy >= tg.H) return;
+        const uint32_t row = sb + tg.row0;
 #pragma unroll
         for (int jj = 0; jj < VG; ++jj) {
             const int ix = __float_as_int(floor_magic<CLAMP>(gmx, xf, c[3 + jj])) + base_x;
@@ -378,16 +418,16 @@ __device__ __forceinline__ void blend_plane(float (&acc)[VG][4], float4 hdr, uin
             acc[jj][3] = fmaf(-T, t.w, T);
         }
     } else {
-        float fy = __fmaf_rn(c[1], (float)y, c[2]);
+        float fy = __fmaf_rn(c[1], tg.yf, c[2]);
         fy = fminf(fmaxf(fy, -kClamp), kClamp);
         const float ty_m = __fadd_rd(fy, kMagic);
         const float wy = fy - (ty_m - kMagic);
-        const int y0 = p.P_s * y + (__float_as_int(ty_m) - kMagicBits);
-        const bool v0 = y0 >= 0 && y0 < p.H, v1 = y0 + 1 >= 0 && y0 + 1 < p.H;
+        const int y0 = tg.psy + (__float_as_int(ty_m) - kMagicBits);
+        const bool v0 = y0 >= 0 && y0 < tg.H, v1 = y0 + 1 >= 0 && y0 + 1 < tg.H;
         if (!v0 && !v1) return;
         const float w0 = v0 ? 1.0f - wy : 0.0f, w1 = v1 ? wy : 0.0f;
-        const uint32_t r0 = sb + (uint32_t)(2 * ty * G.row_bytes);
-        const uint32_t r1 = r0 + (uint32_t)G.row_bytes;
+        const uint32_t r0 = sb + tg.row0;
+        const uint32_t r1 = r0 + tg.row_bytes;
 #pragma unroll
         for (int jj = 0; jj < VG; ++jj) {
             float fx = __fmaf_rn(gmx, xf, c[3 + jj]);
@@ -420,13 +460,98 @@ __device__ __forceinline__ void blend_plane(float (&acc)[VG][4], float4 hdr, uin
     }
 }
 
+// Stages the plane rows that list entry q (plane k = plist[q], coefficient
+// block c) needs for output rows Y0 .. Y0 + BY - 1 into stage sb, with their
+// byte count announced on mbarrier bar (one producer thread).
+template <int DT>
+__device__ __forceinline__ void produce_rows(const CompParams& p, const StagedGeom& G, const char* __restrict__ planes,
+                                             int k, const float* c, int Y0, unsigned char* sb, uint32_t bar)
+{
+    constexpr int TB = Texel<DT>::kBytes;
+    const size_t plane_bytes = (size_t)p.W * p.H * TB;
+    const uint32_t row_copy = (uint32_t)((size_t)p.W * TB);   // a multiple of 16 (checked at launch)
+    uint32_t bytes = 0;
+    for (int r = 0; r < G.BY; ++r) {
+        const int yy = Y0 + r;
+        if (yy >= p.Ny) continue;
+        const int base = plane_row(p.P_s, yy, c[1], c[2]);
+        for (int t = 0; t < G.rows_per_y; ++t)
+            if (base + t >= 0 && base + t < p.H) bytes += row_copy;
+    }
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, bytes);
+    for (int r = 0; r < G.BY; ++r) {
+        const int yy = Y0 + r;
+        if (yy >= p.Ny) continue;
+        const int base = plane_row(p.P_s, yy, c[1], c[2]);
+        for (int t = 0; t < G.rows_per_y; ++t) {
+            const int iy = base + t;
+            if (iy < 0 || iy >= p.H) continue;
+            const char* src = planes + (size_t)k * plane_bytes + (size_t)iy * row_copy;
+            unsigned char* dst = sb + (size_t)(r * G.rows_per_y + t) * G.row_bytes + (size_t)G.padl * TB;
+            bulk_copy_g2s(smem_addr(dst), src, row_copy, bar);
+        }
+    }
+}
+
+// Non-empty planes in order into plist (warp 0 only); returns their count.
+__device__ __forceinline__ int plane_list(const CompParams& p, const int32_t* __restrict__ count, int* plist)
+{
+    const int lane = threadIdx.x & 31;
+    int n = 0;
+    for (int b = 0; b < p.N; b += 32) {
+        const int k = b + lane;
+        const bool ne = k < p.N && count[k] != 0;
+        const unsigned m = __ballot_sync(0xffffffffu, ne);
+        if (ne) plist[n + __popc(m & ((1u << lane) - 1u))] = k;
+        n += __popc(m);
+    }
+    return n;
+}
+
+// Coefficient blocks of views j0 .. j0 + VG - 1 (view row vi), list order.
+template <bool BILINEAR, int VG>
+__device__ __forceinline__ void load_coefs(const CompParams& p, const CompWs& w, const int* plist, int P, int vi,
+                                           int j0, float* coef)
+{
+    constexpr int CW = CoefBlock<VG>::kFloats;
+    for (int e = threadIdx.x; e < P * VG; e += blockDim.x) {
+        const int q = e / VG, jj = e % VG;
+        const int k = plist[q];
+        const int j = min(j0 + jj, p.Vx - 1);
+        const float* cx = w.cx + 3 * ((size_t)j * p.N + k);
+        coef[q * CW + 4 + jj] = BILINEAR ? cx[2] : cx[1];
+        if (jj == 0) {
+            const float* cy = w.cy + 3 * ((size_t)vi * p.N + k);
+            coef[q * CW + 0] = cx[0];
+            coef[q * CW + 1] = cy[0];
+            coef[q * CW + 2] = BILINEAR ? cy[2] : cy[1];
+            coef[q * CW + 3] = __int_as_float(w.wide[k]);
+        }
+    }
+}
+
+// Zero left and right pads of every staged row (the bulk copies never write them).
+template <int DT>
+__device__ __forceinline__ void zero_pads(const CompParams& p, const StagedGeom& G, unsigned char* stage_base,
+                                          size_t stage_stride)
+{
+    constexpr int TB = Texel<DT>::kBytes;
+    const int nrows = G.BY * G.rows_per_y;
+    for (int e = threadIdx.x; e < kStages * nrows; e += blockDim.x) {
+        unsigned char* row = stage_base + (size_t)(e / nrows) * stage_stride + (size_t)(e % nrows) * G.row_bytes;
+        for (int b = 0; b < G.padl * TB; b += 4) *reinterpret_cast<uint32_t*>(row + b) = 0u;
+        for (size_t b = (size_t)(G.padl + p.W) * TB; b < G.row_bytes; b += 4)
+            *reinterpret_cast<uint32_t*>(row + b) = 0u;
+    }
+}
+
 template <int DT, bool BILINEAR, int VG>
 __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams p, StagedGeom G,
                                                                         const char* __restrict__ planes,
                                                                         const int32_t* __restrict__ count, CompWs w,
                                                                         float* __restrict__ out)
 {
-    constexpr int TB = Texel<DT>::kBytes;
     extern __shared__ __align__(128) unsigned char smem[];
     // [stages][rows][row_bytes] | full[stages] | empty[stages] | coef [N][CW] | plist [N]
     constexpr int CW = CoefBlock<VG>::kFloats;
@@ -448,40 +573,12 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
 
     // list of non-empty planes in order (warp 0, ballot compaction)
     if (tid < 32) {
-        int n = 0;
-        for (int b = 0; b < p.N; b += 32) {
-            const int k = b + tid;
-            const bool ne = k < p.N && count[k] != 0;
-            const unsigned m = __ballot_sync(0xffffffffu, ne);
-            if (ne) plist[n + __popc(m & ((1u << tid) - 1u))] = k;
-            n += __popc(m);
-        }
+        const int n = plane_list(p, count, plist);
         if (tid == 0) s_nplanes = n;
     }
     __syncthreads();
-    // coefficient blocks of this CTA's views, in list order
-    for (int e = tid; e < s_nplanes * VG; e += kStagedBlock) {
-        const int q = e / VG, jj = e % VG;
-        const int k = plist[q];
-        const int j = min(j0 + jj, p.Vx - 1);
-        const float* cx = w.cx + 3 * ((size_t)j * p.N + k);
-        coef[q * CW + 4 + jj] = BILINEAR ? cx[2] : cx[1];
-        if (jj == 0) {
-            const float* cy = w.cy + 3 * ((size_t)vi * p.N + k);
-            coef[q * CW + 0] = cx[0];
-            coef[q * CW + 1] = cy[0];
-            coef[q * CW + 2] = BILINEAR ? cy[2] : cy[1];
-            coef[q * CW + 3] = __int_as_float(w.wide[k]);
-        }
-    }
-    // zero pads of every staged row (the bulk copies never write them)
-    const int nrows = G.BY * G.rows_per_y;
-    for (int e = tid; e < kStages * nrows; e += kStagedBlock) {
-        unsigned char* row = stage_base + (size_t)(e / nrows) * G.stage_bytes + (size_t)(e % nrows) * G.row_bytes;
-        for (int b = 0; b < G.padl * TB; b += 4) *reinterpret_cast<uint32_t*>(row + b) = 0u;
-        for (size_t b = (size_t)(G.padl + p.W) * TB; b < G.row_bytes; b += 4)
-            *reinterpret_cast<uint32_t*>(row + b) = 0u;
-    }
+    load_coefs<BILINEAR, VG>(p, w, plist, s_nplanes, vi, j0, coef);
+    zero_pads<DT>(p, G, stage_base, G.stage_bytes);
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(smem_addr(&full[s]), 1);
@@ -491,37 +588,11 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
     }
     __syncthreads();
     const int P = s_nplanes;
-    const size_t plane_bytes = (size_t)p.W * p.H * TB;
-    const uint32_t row_copy = (uint32_t)((size_t)p.W * TB);   // a multiple of 16 (checked at launch)
 
     // producer: stage the plane rows of list entry q into stage q % kStages
     auto produce = [&](int q) {
-        const int k = plist[q];
-        const float* c = coef + (size_t)q * CW;
-        unsigned char* sb = stage_base + (size_t)(q % kStages) * G.stage_bytes;
-        const uint32_t bar = smem_addr(&full[q % kStages]);
-        uint32_t bytes = 0;
-        for (int r = 0; r < G.BY; ++r) {
-            const int yy = Y0 + r;
-            if (yy >= p.Ny) continue;
-            const int base = plane_row(p.P_s, yy, c[1], c[2]);
-            for (int t = 0; t < G.rows_per_y; ++t)
-                if (base + t >= 0 && base + t < p.H) bytes += row_copy;
-        }
-        fence_proxy_async();
-        mbar_arrive_expect_tx(bar, bytes);
-        for (int r = 0; r < G.BY; ++r) {
-            const int yy = Y0 + r;
-            if (yy >= p.Ny) continue;
-            const int base = plane_row(p.P_s, yy, c[1], c[2]);
-            for (int t = 0; t < G.rows_per_y; ++t) {
-                const int iy = base + t;
-                if (iy < 0 || iy >= p.H) continue;
-                const char* src = planes + (size_t)k * plane_bytes + (size_t)iy * row_copy;
-                unsigned char* dst = sb + (size_t)(r * G.rows_per_y + t) * G.row_bytes + (size_t)G.padl * TB;
-                bulk_copy_g2s(smem_addr(dst), src, row_copy, bar);
-            }
-        }
+        produce_rows<DT>(p, G, planes, plist[q], coef + (size_t)q * CW, Y0,
+                         stage_base + (size_t)(q % kStages) * G.stage_bytes, smem_addr(&full[q % kStages]));
     };
 
     if (tid >= kStagedThreads) {
@@ -546,7 +617,7 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
     for (int jj = 0; jj < VG; ++jj) acc[jj][0] = acc[jj][1] = acc[jj][2] = 0.f, acc[jj][3] = 1.f;
     const uint32_t stage_a = smem_addr(stage_base), coef_a = smem_addr(coef);
     const bool live = ty < G.BY && x < p.Nx && y < p.Ny;   // threads past BY rows idle
-    const uint32_t maxi = (uint32_t)(G.padl + p.W);       // first right-pad texel
+    const ThreadGeom tg = thread_geom(p, G, x, y, ty);
     bool ok = true;
 
     for (int q = 0; q < P; ++q) {
@@ -562,9 +633,9 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
             const uint32_t sb = stage_a + (uint32_t)(s * G.stage_bytes);
             const float4 hdr = lds_f4(ca);
             if (__float_as_int(hdr.w))
-                blend_plane<DT, BILINEAR, VG, true>(acc, hdr, ca, sb, G, p, x, y, ty, maxi);
+                blend_plane<DT, BILINEAR, VG, true>(acc, hdr, ca, sb, tg);
             else
-                blend_plane<DT, BILINEAR, VG, false>(acc, hdr, ca, sb, G, p, x, y, ty, maxi);
+                blend_plane<DT, BILINEAR, VG, false>(acc, hdr, ca, sb, tg);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
@@ -581,23 +652,158 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
     }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent staged composite over the items of several scenes (same plane
+// type, sampling and views per thread). Each CTA takes (scene, view group,
+// row band, column tile) items from a global counter until none are left;
+// shared memory is laid out once for the largest stage and N of the batch.
+// The plane-row ring and its mbarriers run on across items: the producer and
+// the consumers count every plane they pass through the ring (Q), so stage
+// Q % kStages and phase (Q / kStages) & 1 stay consistent from one item to
+// the next. Between items the CTA synchronises, rebuilds the plane list and
+// coefficient blocks, and re-zeroes row pads when the scene (row layout)
+// changes. A wait that gives up sets the scene's error word and the CTA
+// stops taking items.
+// ---------------------------------------------------------------------------
+template <int DT, bool BILINEAR, int VG>
+__global__ void __launch_bounds__(kStagedBlock, 2) k_composite_batched(const CompScene* __restrict__ scs, int n_sc,
+                                                                         long long total,
+                                                                         unsigned long long* __restrict__ counter,
+                                                                         size_t max_stage_bytes, int maxN)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int CW = CoefBlock<VG>::kFloats;
+    unsigned char* stage_base = smem;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * max_stage_bytes);
+    uint64_t* empty = full + kStages;
+    float* coef = reinterpret_cast<float*>(empty + kStages);
+    int* plist = reinterpret_cast<int*>(coef + (size_t)maxN * CW);
+    __shared__ int s_nplanes, s_abort;
+    __shared__ long long s_item;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) {
+            mbar_init(smem_addr(&full[st]), 1);
+            mbar_init(smem_addr(&empty[st]), kStagedWarps);
+        }
+        fence_proxy_async();
+        s_abort = 0;
+    }
+    const uint32_t stage_a = smem_addr(stage_base), coef_a = smem_addr(coef);
+    // ring position of the next plane: stage st0, phase ph0 (flips every
+    // kStages planes), and whether the ring has been round once (from then
+    // on the producer waits for the consumers to release a stage)
+    int st0 = 0;
+    uint32_t ph0 = 0;
+    bool wrapped = false;
+    int prev = -1;
+    for (;;) {
+        if (tid == 0) s_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long it = s_item;
+        if (it >= total || s_abort) break;
+        int si = 0;
+        while (si + 1 < n_sc && it >= scs[si + 1].base) ++si;
+        const CompParams p = scs[si].p;
+        const StagedGeom G = scs[si].G;
+        const CompWs w = scs[si].w;
+        const char* planes = scs[si].planes;
+        const int nby = scs[si].nby;
+        const long long li = it - scs[si].base;
+        const int ng = G.groups_x * p.Vy;
+        const int vgroup = (int)(li % ng);
+        const long long rest = li / ng;
+        const int vi = vgroup / G.groups_x, j0 = (vgroup % G.groups_x) * VG;
+        const int Y0 = (int)(rest % nby) * G.BY, X0 = (int)(rest / nby) * G.TX;
+
+        if (tid < 32) {
+            const int n = plane_list(p, scs[si].count, plist);
+            if (tid == 0) s_nplanes = n;
+        }
+        if (si != prev) zero_pads<DT>(p, G, stage_base, max_stage_bytes);
+        __syncthreads();
+        load_coefs<BILINEAR, VG>(p, w, plist, s_nplanes, vi, j0, coef);
+        __syncthreads();
+        const int P = s_nplanes;
+
+        if (tid >= kStagedThreads) {
+            if (tid == kStagedThreads) {
+                int st = st0;
+                uint32_t ph = ph0;
+                bool wr = wrapped;
+                for (int q = 0; q < P; ++q) {
+                    if (wr && !mbar_wait_bounded(smem_addr(&empty[st]), ph ^ 1u)) {
+                        atomicExch(w.err, 1);
+                        s_abort = 1;
+                        break;
+                    }
+                    produce_rows<DT>(p, G, planes, plist[q], coef + (size_t)q * CW, Y0,
+                                     stage_base + (size_t)st * max_stage_bytes, smem_addr(&full[st]));
+                    if (++st == kStages) st = 0, ph ^= 1u, wr = true;
+                }
+            }
+        } else {
+            const int tx = tid % G.TX, ty = tid / G.TX;
+            const int x = X0 + tx, y = Y0 + ty;
+            const bool live = ty < G.BY && x < p.Nx && y < p.Ny;
+            const ThreadGeom tg = thread_geom(p, G, x, y, ty);
+            float acc[VG][4];
+#pragma unroll
+            for (int jj = 0; jj < VG; ++jj) acc[jj][0] = acc[jj][1] = acc[jj][2] = 0.f, acc[jj][3] = 1.f;
+            bool ok = true;
+            int st = st0;
+            uint32_t ph = ph0;
+            const uint32_t stage_stride = (uint32_t)max_stage_bytes;
+            for (int q = 0; q < P; ++q) {
+                if (!mbar_wait_bounded(smem_addr(&full[st]), ph)) {
+                    atomicExch(w.err, 1);
+                    s_abort = 1;
+                    ok = false;
+                    break;
+                }
+                if (live) {
+                    const uint32_t ca = coef_a + 4u * (uint32_t)(q * CW);
+                    const uint32_t sb = stage_a + (uint32_t)st * stage_stride;
+                    const float4 hdr = lds_f4(ca);
+                    if (__float_as_int(hdr.w))
+                        blend_plane<DT, BILINEAR, VG, true>(acc, hdr, ca, sb, tg);
+                    else
+                        blend_plane<DT, BILINEAR, VG, false>(acc, hdr, ca, sb, tg);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&empty[st]));
+                if (++st == kStages) st = 0, ph ^= 1u;
+            }
+            if (ok && live) {
+                float* out = scs[si].out;
+#pragma unroll
+                for (int jj = 0; jj < VG; ++jj) {
+                    const int j = j0 + jj;
+                    if (j >= p.Vx) break;
+                    const int v = vi * p.Vx + j;
+                    const float T = acc[jj][3];
+                    reinterpret_cast<float4*>(out)[((size_t)v * p.Ny + y) * p.Nx + x] =
+                        make_float4(fmaf(T, p.bg[0], acc[jj][0]), fmaf(T, p.bg[1], acc[jj][1]),
+                                    fmaf(T, p.bg[2], acc[jj][2]), 1.0f - T);
+                }
+            }
+        }
+        // every thread advances the ring position by the P planes of the item
+        const int adv = st0 + P % kStages;
+        ph0 ^= (uint32_t)((P / kStages + (adv >= kStages ? 1 : 0)) & 1);
+        wrapped = wrapped || (st0 + P >= kStages);
+        st0 = adv >= kStages ? adv - kStages : adv;
+        prev = si;
+        __syncthreads();
+    }
+}
+
 template <int DT, bool BILINEAR, int VG>
 bool launch_staged_vg(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
                       cudaStream_t s)
 {
     constexpr int TB = Texel<DT>::kBytes;
-    StagedGeom G;
-    G.TX = p.Nx >= 512 ? 512 : (p.Nx + 31) / 32 * 32;
-    G.BY = kStagedThreads / G.TX;
-    G.VG = VG;
-    G.rows_per_y = BILINEAR ? 2 : 1;
-    G.padl = 16 / TB;
-    G.row_texels = (int)(round16((size_t)(G.padl + p.W + 1) * TB) / TB);
-    G.row_bytes = (size_t)G.row_texels * TB;
-    G.stage_bytes = G.row_bytes * G.BY * G.rows_per_y;
-    G.groups_x = (p.Vx + VG - 1) / VG;
-    G.smem_bytes = kStages * G.stage_bytes + 2 * kStages * 8 + sizeof(float) * (size_t)p.N * CoefBlock<VG>::kFloats +
-                   sizeof(int) * (size_t)p.N;
+    const StagedGeom G = staged_geom(p, TB, BILINEAR, VG, 512);
     if (G.smem_bytes > 200 * 1024) return false;
     // bulk copies need 16-byte aligned rows: plane base and row pitch
     if (((uintptr_t)planes) % 16 != 0 || ((size_t)p.W * TB) % 16 != 0) return false;
@@ -813,9 +1019,65 @@ void launch_composite_bwd_t(const CompParams& p, const void* planes, const int32
     note_launches(1);
 }
 
+template <int DT, bool BILINEAR, int VG>
+void launch_batched_t(const CompScene* scs, int n_sc, long long total, size_t max_stage_bytes, int maxN,
+                      unsigned long long* counter, int n_ctas, size_t smem, cudaStream_t s)
+{
+    auto kern = k_composite_batched<DT, BILINEAR, VG>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<n_ctas, kStagedBlock, smem, s>>>(scs, n_sc, total, counter, max_stage_bytes, maxN);
+}
+
+template <int DT, bool BILINEAR>
+void launch_batched_vg(int VG, const CompScene* scs, int n_sc, long long total, size_t mx, int maxN,
+                       unsigned long long* counter, int n_ctas, size_t smem, cudaStream_t s)
+{
+    if (VG == 9)
+        launch_batched_t<DT, BILINEAR, 9>(scs, n_sc, total, mx, maxN, counter, n_ctas, smem, s);
+    else if (VG == 5)
+        launch_batched_t<DT, BILINEAR, 5>(scs, n_sc, total, mx, maxN, counter, n_ctas, smem, s);
+    else
+        launch_batched_t<DT, BILINEAR, 3>(scs, n_sc, total, mx, maxN, counter, n_ctas, smem, s);
+}
+
+template <int DT>
+void launch_batched_dt(bool bilinear, int VG, const CompScene* scs, int n_sc, long long total, size_t mx, int maxN,
+                       unsigned long long* counter, int n_ctas, size_t smem, cudaStream_t s)
+{
+    if (bilinear)
+        launch_batched_vg<DT, true>(VG, scs, n_sc, total, mx, maxN, counter, n_ctas, smem, s);
+    else
+        launch_batched_vg<DT, false>(VG, scs, n_sc, total, mx, maxN, counter, n_ctas, smem, s);
+}
+
 }  // namespace
 
-void launch_composite_bwd(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
+size_t composite_batched_smem(size_t max_stage_bytes, int maxN, int VG)
+{
+    return kStages * max_stage_bytes + 2 * kStages * 8 + sizeof(float) * (size_t)maxN * (4 + 4 * ((VG + 3) / 4)) +
+           sizeof(int) * (size_t)maxN;
+}
+
+bool launch_composite_batched(const CompScene* scenes_dev, int n_sc, long long total, int dtype, bool bilinear,
+                              int VG, size_t max_stage_bytes, int maxN, unsigned long long* counter, int n_ctas,
+                              cudaStream_t s)
+{
+    if (total <= 0) return true;
+    const size_t smem = composite_batched_smem(max_stage_bytes, maxN, VG);
+    if (smem > 200 * 1024) return false;
+    if (dtype == LF_F32)
+        launch_batched_dt<LF_F32>(bilinear, VG, scenes_dev, n_sc, total, max_stage_bytes, maxN, counter, n_ctas, smem, s);
+    else if (dtype == LF_F16)
+        launch_batched_dt<LF_F16>(bilinear, VG, scenes_dev, n_sc, total, max_stage_bytes, maxN, counter, n_ctas, smem, s);
+    else
+        launch_batched_dt<LF_BF16>(bilinear, VG, scenes_dev, n_sc, total, max_stage_bytes, maxN, counter, n_ctas, smem,
+                                   s);
+    note_launches(1);
+    return true;
+}
+
+void launch_composite_bwd(
+const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
                           const float* dviews, float* dplanes, cudaStream_t s)
 {
     switch (p.dtype) {

@@ -31,6 +31,7 @@ constexpr uint64_t kInvalidKey = ~0ull;
 void note_launches(int k);
 void trace_begin(const char* stage, cudaStream_t s);
 void trace_end(cudaStream_t s);
+bool trace_swap(bool on);   // sets this thread's tracing flag, returns the old one
 
 // ---- error plumbing ------------------------------------------------------
 void set_error(const std::string& msg);
@@ -83,6 +84,8 @@ struct BuildWs {
 };
 
 size_t build_ws_layout(int64_t n, int32_t N, int32_t W, int32_t H, int64_t cap, void* base, BuildWs* out);
+// tile-pair capacity that a workspace of ws_bytes holds (0 if too small)
+int64_t ws_capacity(int64_t n, int32_t N, int32_t W, int32_t H, size_t ws_bytes);
 
 // ---- per-launch parameters computed on the host -------------------------
 struct ProjParams {
@@ -143,6 +146,18 @@ void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uin
 void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
                           cudaStream_t s);
 
+// batched (several scenes, one persistent launch): per-scene item table
+struct RasterScene {
+    BuildWs w;
+    RasterParams p;
+    const uint32_t* ranks;
+    void* planes;
+    long long base;     // first global item of this scene (tiles * N items)
+};
+void launch_raster_gauss_batched(const RasterScene* scenes_dev, int n_sc, long long total, int dtype, int ppt,
+                                 unsigned long long* counter, int n_ctas, cudaStream_t s);
+int raster_batched_ctas_per_sm(int ppt);
+
 // backward: raster adjoints accumulate into ws.g2d (zeroed by the caller),
 // then the per-rank chain rule / scatter writes the parameter gradients
 void launch_raster_gaussians_bwd(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks,
@@ -152,6 +167,13 @@ void launch_raster_voxels_bwd(const BuildWs& ws, const RasterParams& p, const ui
 void launch_gauss_chain(const lf_gaussians& g, const ProjParams& p, const BuildWs& ws, const lf_gaussians_grad& out,
                         cudaStream_t s);
 void launch_voxel_scatter(const BuildWs& ws, long long n, const lf_voxels_grad& out, cudaStream_t s);
+
+// ---- helpers exported by lf_api.cu to the batch module -------------------
+// the build of one Gaussian scene up to its tile lists (no raster)
+lf_status build_gaussians_prefix(const lf_gaussians* g, const lf_ref_camera* ref, int32_t N, int32_t binning,
+                                 void* ws, size_t ws_bytes, lf_planes* out, cudaStream_t stream, BuildWs* w,
+                                 const uint32_t** ranks);
+void raster_params(const lf_ref_camera* ref, int32_t N, int32_t dtype, RasterParams* p);
 
 // ---- composite ----------------------------------------------------------
 struct CompWs {
@@ -170,8 +192,41 @@ struct CompParams {
     double D_focal, D_forward, tth_x, tth_y, tthp_x, tthp_y, tphi_x, tphi_y;
 };
 
+// staged composite layout (see lf_composite.cu)
+constexpr int kStagedThreads = 512;   // consumer threads of a staged-composite CTA
+constexpr int kStages = 6;            // depth of its plane-row ring
+struct StagedGeom {
+    int TX, BY, VG, rows_per_y;    // rows_per_y: 1 nearest, 2 bilinear
+    int padl;                      // zero texels left of every staged row (16 bytes)
+    int row_texels;                // padl + W + right pad, a multiple of 16 bytes
+    size_t row_bytes, stage_bytes, smem_bytes;
+    int groups_x;                  // view groups per view row
+};
+StagedGeom staged_geom(const CompParams& p, int texel_bytes, bool bilinear, int VG, int tx_max);
+
+// batched (several scenes, one persistent launch): per-scene item table;
+// item li of a scene: view group li % (groups_x Vy), then row band, then
+// column tile
+struct CompScene {
+    CompParams p;
+    StagedGeom G;
+    const char* planes;
+    const int32_t* count;
+    CompWs w;
+    float* out;
+    long long base;     // first global item of this scene
+    int nby, nbz;       // row bands, column tiles
+};
 void launch_comp_coeffs(const CompParams& p, const double* d, const int32_t* count, const CompWs& ws,
                         cudaStream_t s);
+// smem_bytes: the largest staged layout of the batch (its stage size, N)
+bool launch_composite_batched(const CompScene* scenes_dev, int n_sc, long long total, int dtype, bool bilinear,
+                              int VG, size_t max_stage_bytes, int maxN, unsigned long long* counter, int n_ctas,
+                              cudaStream_t s);
+size_t composite_batched_smem(size_t max_stage_bytes, int maxN, int VG);
+// argument checks and parameters of one composite (lf_api.cu)
+lf_status composite_args(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
+                         const float* out, void* ws, size_t ws_bytes, CompWs* cw, CompParams* p);
 void launch_composite(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
                       float* out, cudaStream_t s);
 void launch_composite_bwd(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,

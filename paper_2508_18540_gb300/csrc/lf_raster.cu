@@ -83,17 +83,27 @@ __device__ __forceinline__ float ex2_approx(float x)
 // A = -log2(e)/2 a, B = -log2(e) b, C = -log2(e)/2 c. Every warp ballots which
 // entries touch its strip and visits only those, in list order, so the
 // blending order of every pixel is unchanged.
+template <int PPT>
+struct GaussSmem {
+    static constexpr int NT = kTilePix / PPT;
+    float4 e0[NT];
+    float4 e1[NT];
+    float4 rgb[NT];
+    int wc[NT / 32];
+};
+
+// One (tile t, chunk k) work item; every thread of the CTA calls it.
 template <int DT, int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, RasterParams p,
-                                                                 const uint32_t* __restrict__ ranks, void* planes)
+__device__ __forceinline__ void raster_gauss_tile(const BuildWs& w, const RasterParams& p,
+                                                  const uint32_t* __restrict__ ranks, void* planes, int t, int k,
+                                                  GaussSmem<PPT>& sm)
 {
     constexpr int NT = kTilePix / PPT;
     constexpr float kL2E = 1.4426950408889634f;
-    __shared__ float4 s_e0[NT];
-    __shared__ float4 s_e1[NT];
-    __shared__ float4 s_rgb[NT];
-    __shared__ int s_wc[NT / 32];
-    const int t = blockIdx.x, k = blockIdx.y;
+    float4* s_e0 = sm.e0;
+    float4* s_e1 = sm.e1;
+    float4* s_rgb = sm.rgb;
+    int* s_wc = sm.wc;
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
@@ -171,6 +181,40 @@ __global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, Rast
             if (py0 + r < p.H)
                 store_texel<DT>(planes, ((size_t)k * p.H + py0 + r) * p.W + px, C[r][0], C[r][1], C[r][2],
                                 1.0f - T[r]);
+    }
+}
+
+template <int DT, int PPT>
+__global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, RasterParams p,
+                                                                 const uint32_t* __restrict__ ranks, void* planes)
+{
+    __shared__ GaussSmem<PPT> sm;
+    raster_gauss_tile<DT, PPT>(w, p, ranks, planes, blockIdx.x, blockIdx.y, sm);
+}
+
+// Persistent form over the (tile, chunk) items of several scenes: CTAs take
+// items from a global counter in the order of the item table (scenes
+// concatenated in the order the schedule chose, tiles fastest within a
+// chunk) until it is exhausted.
+template <int DT, int PPT>
+__global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss_batched(const RasterScene* __restrict__ sc, int n_sc,
+                                                                         long long total,
+                                                                         unsigned long long* __restrict__ counter)
+{
+    __shared__ GaussSmem<PPT> sm;
+    __shared__ long long s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long it = s_item;
+        __syncthreads();
+        if (it >= total) return;
+        int s = 0;
+        while (s + 1 < n_sc && it >= sc[s + 1].base) ++s;
+        const RasterScene& S = sc[s];
+        const long long li = it - S.base;
+        const int tiles = S.p.tiles_x * S.p.tiles_y;
+        raster_gauss_tile<DT, PPT>(S.w, S.p, S.ranks, S.planes, (int)(li % tiles), (int)(li / tiles), sm);
     }
 }
 
@@ -754,6 +798,31 @@ void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uin
     default: k_raster_gauss<LF_BF16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
     }
     note_launches(1);
+}
+
+void launch_raster_gauss_batched(const RasterScene* scenes_dev, int n_sc, long long total, int dtype, int ppt,
+                                 unsigned long long* counter, int n_ctas, cudaStream_t s)
+{
+    if (total <= 0) return;
+#define LF_RB(DT_, PPT_)                                                                                  \
+    k_raster_gauss_batched<DT_, PPT_><<<n_ctas, kTilePix / PPT_, 0, s>>>(scenes_dev, n_sc, total, counter)
+    if (ppt == 4) {
+        if (dtype == LF_F32) LF_RB(LF_F32, 4); else if (dtype == LF_F16) LF_RB(LF_F16, 4); else LF_RB(LF_BF16, 4);
+    } else {
+        if (dtype == LF_F32) LF_RB(LF_F32, 2); else if (dtype == LF_F16) LF_RB(LF_F16, 2); else LF_RB(LF_BF16, 2);
+    }
+#undef LF_RB
+    note_launches(1);
+}
+
+int raster_batched_ctas_per_sm(int ppt)
+{
+    int n = 0;
+    if (ppt == 4)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_gauss_batched<LF_F16, 4>, kTilePix / 4, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_gauss_batched<LF_F16, 2>, kTilePix / 2, 0);
+    return n > 0 ? n : 1;
 }
 
 void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
