@@ -49,8 +49,8 @@ def _config(extra=None):
 # (profiles/k_*_g2lf_display_1M_512px_N64_45v.md), valid only while the
 # kernel's sources hash to the value recorded with them.
 NCU_TRAFFIC = {
-    "raster_gaussians": (71_788_032 + 210_645_248, ("lf_raster.cu", "lf_internal.cuh"), "556e5ca813f4d5ae"),
-    "composite": (253_064_192 + 154_835_456, ("lf_composite.cu", "lf_internal.cuh"), "a12a6c79a1668b7b"),
+    "raster_gaussians": (71_790_080 + 210_722_304, ("lf_raster.cu", "lf_internal.cuh"), "6bd28c7a4f40c853"),
+    "composite": (253_049_600 + 154_599_168, ("lf_composite.cu", "lf_internal.cuh"), "8072b1463550b3db"),
 }
 
 
@@ -188,6 +188,8 @@ def run_ours(args):
         if dtype == "f32":
             clk = clocks.stop()
         res[dtype] = dict(ms=ms, launches=launches, stages=stages, renderer=r)
+        if rank == 0 and world == 1:
+            res[dtype]["views_host"] = r.out.cpu().numpy()
 
     # end to end through the public API with host buffers (pinned), f32 planes
     r32 = res["f32"]["renderer"]
@@ -277,10 +279,142 @@ def run_ours(args):
             "roofline_by_kernel": roofs["f32"],
             "clocks": clk,
         }
+    if rank == 0 and world == 1 and not args.no_extras:
+        views_host = {d: res[d].pop("views_host", None) for d in res}
+        for d in res:
+            res[d]["renderer"] = None
+        del r32, host_in, host_out, g, flush
+        torch.cuda.empty_cache()
+        line["v2lf"] = run_v2lf(args, dev)
+        torch.cuda.empty_cache()
+        line["differentiable"] = run_differentiable(args, dev)
+        torch.cuda.empty_cache()
+        line["batched"] = run_batched(args, dev)
+        torch.cuda.empty_cache()
+        line["_views_host"] = views_host
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+def _event_ms(fn, steps, warmup, stream, flush=None):
+    """Mean CUDA-event time of fn over steps calls after warmup calls (L2
+    flushed before each timed call when a flush buffer is given)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / steps
+
+
+def run_v2lf(args, dev):
+    """V2LF at display scale: 2M sparse voxels (3-level grid), 512^2, N 64,
+    45 views, FP32 planes; same timing rules as the primary number."""
+    import torch
+    from paper_2508_18540_gb300 import api
+    from paper_2508_18540_gb300 import synth as S
+    wl = S.workload_voxels()
+    v = api.DeviceVoxels.from_scene(wl.scene, device=dev)
+    r = api.LightFieldRenderer(wl.camera, wl.display, wl.views, wl.N, wl.binning, "f32", device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+    ms = _event_ms(lambda: r.render(v), args.steps, args.warmup, st, flush)
+    status, needed, M = r.status()
+    api.lf_trace_collect()
+    api.lf_trace_enable(True)
+    for _ in range(3):
+        r.render(v)
+    torch.cuda.synchronize()
+    api.lf_trace_enable(False)
+    stages = {k: round(t / c, 4) for k, (t, c) in api.lf_trace_collect().items()}
+    return {"workload": wl.name, "voxels": wl.scene.n, "culled_in": M, "status": status, "planes": "f32",
+            "value": round(1000.0 / ms, 2), "unit": UNIT, "ms_per_step": round(ms, 4),
+            "views_per_s": round(1000.0 / ms * wl.views.Vx, 1), "stages_ms": stages}
+
+
+def run_differentiable(args, dev):
+    """Differentiable G2LF: 300k Gaussians, 512^2, N 64, 45 views: forward
+    (build + composite) and backward (composite adjoint, splat adjoint,
+    projection chain rule) per step, FP32."""
+    import torch
+    from paper_2508_18540_gb300 import api
+    from paper_2508_18540_gb300 import synth as S
+    wl = S.workload_fit()
+    g = api.DeviceGaussians.from_scene(wl.scene, device=dev)
+    r = api.LightFieldRenderer(wl.camera, wl.display, wl.views, wl.N, wl.binning, "f32", device=dev)
+    dv = torch.randn((wl.views.Vx, wl.camera.Ny, wl.camera.Nx, 4), device=dev)
+    st = torch.cuda.current_stream()
+    fwd = _event_ms(lambda: r.render(g), args.steps, args.warmup, st)
+    bwd = _event_ms(lambda: r.backward(g, dv), args.steps, args.warmup, st)
+    api.lf_trace_collect()
+    api.lf_trace_enable(True)
+    for _ in range(3):
+        r.render(g)
+        r.backward(g, dv)
+    torch.cuda.synchronize()
+    api.lf_trace_enable(False)
+    stages = {k: round(t / c, 4) for k, (t, c) in api.lf_trace_collect().items()}
+    return {"workload": wl.name, "gaussians": wl.scene.n, "forward_ms": round(fwd, 4), "backward_ms": round(bwd, 4),
+            "steps_per_s": round(1000.0 / (fwd + bwd), 2), "stages_ms": stages,
+            "gradient_check": "tests/test_gpu_grad.py (finite differences of the FP64 oracle)"}
+
+
+def run_batched(args, dev):
+    """Six uneven G2LF scenes (50k..3M Gaussians, 9..128 views, 256^2..1024^2,
+    N 64..512, FP16 planes): autotuned plan, one CUDA-graph launch per frame,
+    against the same scenes rendered one by one."""
+    import torch
+    from paper_2508_18540_gb300 import api
+    from paper_2508_18540_gb300 import synth as S
+    wls = S.workloads_batched()
+    b = api.BatchRenderer(wls, "f16", device=dev)
+    plan, tune_ms = b.autotune(reps=1)
+    b.capture()
+    s = b.stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    k0 = api.lf_launch_count()
+    g_ms = _event_ms(b.launch, args.steps, args.warmup, s, flush)
+    launches = (api.lf_launch_count() - k0) // max(1, args.steps + args.warmup)
+    status = b.status()
+    rs = []
+    for w in wls:
+        r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f16", device=dev)
+        rs.append((r, api.DeviceGaussians.from_scene(w.scene, device=dev)))
+
+    def seq():
+        for r, g in rs:
+            r.render(g, s)
+    with torch.cuda.stream(s):
+        s_ms = _event_ms(seq, args.steps, args.warmup, s, flush)
+    views = sum(w.views.Vx * w.views.Vy for w in wls)
+    b.close()
+    return {"scenes": [{"gaussians": w.scene.n, "views": w.views.Vx, "res": w.camera.Nx, "N": w.N} for w in wls],
+            "planes": "f16", "status": status, "plan": plan, "autotune_ms": round(tune_ms, 3),
+            "graph_ms_per_frame": round(g_ms, 3), "batch_frames_per_s": round(1000.0 / g_ms, 2),
+            "views_per_s": round(views * 1000.0 / g_ms, 1), "kernels_per_frame": int(launches),
+            "one_by_one_ms_per_frame": round(s_ms, 3)}
+
+
+def view_errors(gpu_views, oracle_views):
+    """Per-view max-abs error and PSNR of GPU views against the FP64 oracle."""
+    out = []
+    for v in range(gpu_views.shape[0]):
+        d = gpu_views[v].astype(np.float64) - oracle_views[v]
+        mse = float(np.mean(d * d))
+        out.append((float(np.abs(d).max()), float("inf") if mse == 0 else 10.0 * math.log10(1.0 / mse)))
+    return {"max_abs": round(max(e[0] for e in out), 6), "min_psnr_db": round(min(e[1] for e in out), 2),
+            "per_view_max_abs": [round(e[0], 6) for e in out], "per_view_psnr_db": [round(e[1], 2) for e in out]}
 
 
 def run_profile(args):
@@ -313,8 +447,9 @@ def cpu_baseline(min_seconds=10.0, max_frames=40):
     oracle.lib()
     t0 = time.perf_counter()
     n_frames = 0
+    last = None
     while n_frames < max_frames:
-        oracle.render(wl)
+        last = oracle.render(wl)
         n_frames += 1
         if time.perf_counter() - t0 >= min_seconds:
             break
@@ -322,7 +457,7 @@ def cpu_baseline(min_seconds=10.0, max_frames=40):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": round(n_frames / dt, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d full LF frame(s) of the 1M-Gaussian 512px N64 45-view workload, FP64, OpenMP" % n_frames,
-            "seconds": round(dt, 2)}
+            "seconds": round(dt, 2)}, last["views"]
 
 
 def run_reference(args):
@@ -358,6 +493,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the V2LF, differentiable and batched sections")
     ap.add_argument("--profile", action="store_true", help="short untimed run for ncu")
     ap.add_argument("--profile-dtypes", default="f32,f16")
     args = ap.parse_args()
@@ -375,8 +511,12 @@ def main():
     else:
         line = run_ours(args)
         rank, world, _ = _env_rank()
+        views_host = line.pop("_views_host", None) if line is not None else None
         if line is not None and world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"], oviews = cpu_baseline()
+            if views_host:
+                line["accuracy_vs_fp64_oracle"] = {d: view_errors(v, oviews) for d, v in views_host.items()
+                                                   if v is not None}
     if line is not None:
         print(json.dumps(line), flush=True)
 
