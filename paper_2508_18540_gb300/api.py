@@ -400,6 +400,55 @@ class LightFieldRenderer:
 
 
 # ---------------------------------------------------------------------------
+# host-memory frames: copies overlapped with the compute of neighbouring frames
+# ---------------------------------------------------------------------------
+
+class HostPipeline:
+    """Renders frames whose Gaussians live in (pinned) host memory and whose
+    views go back to (pinned) host memory. Two device input slots and two
+    device view slots let frame i's host-to-device copy (copy stream) and
+    frame i-1's device-to-host copy (second copy stream) run while frame i-1
+    or i is computed, ordered by CUDA events. submit() returns the event that
+    marks frame i's views in host memory."""
+
+    def __init__(self, renderer: "LightFieldRenderer", n: int, device="cuda"):
+        self.r = renderer
+        f = dict(dtype=torch.float32, device=device)
+        self.slots = [DeviceGaussians(torch.empty((n, 3), **f), torch.empty((n, 3), **f), torch.empty((n, 4), **f),
+                                      torch.empty((n,), **f), torch.empty((n, 3), **f)) for _ in range(2)]
+        self.outs = [torch.empty_like(renderer.out) for _ in range(2)]
+        self.s_in, self.s_comp, self.s_out = (torch.cuda.Stream(device=device) for _ in range(3))
+        E = torch.cuda.Event
+        self.in_ready, self.in_free = [E(), E()], [E(), E()]
+        self.out_ready, self.out_free = [E(), E()], [E(), E()]
+        self.i = 0
+
+    def submit(self, host: DeviceGaussians, host_out: torch.Tensor) -> torch.cuda.Event:
+        k = self.i % 2
+        dev = self.slots[k]
+        self.s_in.wait_event(self.in_free[k])          # frame i-2 no longer reads this slot
+        with torch.cuda.stream(self.s_in):
+            for dst, src in ((dev.means, host.means), (dev.scales, host.scales), (dev.quats, host.quats),
+                             (dev.opacity, host.opacity), (dev.rgb, host.rgb)):
+                dst.copy_(src, non_blocking=True)
+        self.in_ready[k].record(self.s_in)
+        self.s_comp.wait_event(self.in_ready[k])
+        self.s_comp.wait_event(self.out_free[k])       # frame i-2's views have left this slot
+        self.r.build(dev, self.s_comp)
+        self.r.composite(self.s_comp, out=self.outs[k])
+        self.in_free[k].record(self.s_comp)
+        self.out_ready[k].record(self.s_comp)
+        self.s_out.wait_event(self.out_ready[k])
+        with torch.cuda.stream(self.s_out):
+            host_out.copy_(self.outs[k], non_blocking=True)
+        self.out_free[k].record(self.s_out)
+        self.i += 1
+        done = torch.cuda.Event()
+        done.record(self.s_out)
+        return done
+
+
+# ---------------------------------------------------------------------------
 # batching: several scenes, persistent launches, CUDA graph, autotuner
 # ---------------------------------------------------------------------------
 

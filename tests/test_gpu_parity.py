@@ -149,3 +149,26 @@ def test_voxels_rotated(orc):
     o = orc.render(scene=sc, camera=cam, display=disp, views=views, N=6, binning="disparity")
     gpu = G.run_gpu(sc, cam, disp, views, 6, "disparity")
     _compare(gpu, o, o["ref"].W, o["ref"].H, 6, "f32")
+
+
+def test_host_pipeline_frames_match_synchronous_renders():
+    # api.HostPipeline overlaps copies with compute across frames; every
+    # frame's host views must equal a plain synchronous render of its input
+    from paper_2508_18540_gb300 import api
+    w = S.workload_tiny()
+    scenes = [w.scene, S.perturbed(w.scene, 3), S.perturbed(w.scene, 4), S.perturbed(w.scene, 5)]
+    r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f32")
+    pipe = api.HostPipeline(r, w.scene.n)
+    outs, evs = [], []
+    hosts = [api.DeviceGaussians.from_scene(sc, pin=True) for sc in scenes]
+    for h in hosts:
+        o = torch.empty(r.out.shape, dtype=torch.float32, pin_memory=True)
+        evs.append(pipe.submit(h, o))
+        outs.append(o)
+    for ev in evs:
+        ev.synchronize()
+    torch.cuda.synchronize()
+    ref = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f32")
+    for sc, o in zip(scenes, outs):
+        want = ref.render(api.DeviceGaussians.from_scene(sc)).cpu()
+        assert torch.equal(o, want)
