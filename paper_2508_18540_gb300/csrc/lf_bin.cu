@@ -9,28 +9,27 @@
 //  k_medians  d_k = median member depth + D_forward (quantile; mean of the two
 //             middle depths for an even count) or the bin's disparity midpoint.
 // All FP64 operations use explicit round-to-nearest intrinsics in the order
-// of the definitions above. Sorted keys are stored relative to the smallest
-// valid key (hdr->kmin), so a depth is rebuilt from the bits key + kmin.
+// of the definitions above. The depth of rank r is the FP64 whose IEEE bits
+// are the depth key of primitive valA[r] (keyA, by primitive).
 #include "lf_internal.cuh"
 
 namespace lf {
 
 namespace {
 
-__device__ __forceinline__ double key_depth(unsigned long long rel, unsigned long long kmin)
+__device__ __forceinline__ double rank_depth(const BuildWs& w, long long r)
 {
-    return __longlong_as_double((long long)(rel + kmin));
+    return __longlong_as_double((long long)w.keyA[w.valA[r]]);
 }
 
-__device__ __forceinline__ int chunk_of_rank(const BuildWs& w, const BinParams& p, long long r, long long M,
-                                             unsigned long long kmin)
+__device__ __forceinline__ int chunk_of_rank(const BuildWs& w, const BinParams& p, long long r, long long M)
 {
     if (p.binning == LF_BIN_QUANTILE) return (int)((r * (long long)p.N) / M);
-    const double zmin = key_depth(w.keyA[0], kmin), zmax = key_depth(w.keyA[M - 1], kmin);
+    const double zmin = rank_depth(w, 0), zmax = rank_depth(w, M - 1);
     const double izmin = __ddiv_rn(1.0, zmin), izmax = __ddiv_rn(1.0, zmax);
     const double span = __dsub_rn(izmin, izmax);
     if (!(span > 0.0)) return 0;
-    const double z = key_depth(w.keyA[r], kmin);
+    const double z = rank_depth(w, r);
     const double f = floor(__ddiv_rn(__dmul_rn((double)p.N, __dsub_rn(izmin, __ddiv_rn(1.0, z))), span));
     return f >= (double)(p.N - 1) ? p.N - 1 : (int)f;
 }
@@ -39,7 +38,6 @@ __global__ void __launch_bounds__(256) k_bin(BuildWs w, BinParams p, int32_t* ch
                                              const float* __restrict__ rgb, const float* __restrict__ dens8, int kind)
 {
     const long long M = (long long)w.hdr->M;
-    const unsigned long long kmin = w.hdr->kmin;
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (M == 0) {
         if (r == 0)
@@ -47,10 +45,10 @@ __global__ void __launch_bounds__(256) k_bin(BuildWs w, BinParams p, int32_t* ch
         return;
     }
     if (r >= M) return;
-    const int c = chunk_of_rank(w, p, r, M, kmin);
+    const int c = chunk_of_rank(w, p, r, M);
     const uint32_t g = w.valA[r];
     chunk_out[g] = c;
-    const int cp = r == 0 ? -1 : chunk_of_rank(w, p, r - 1, M, kmin);
+    const int cp = r == 0 ? -1 : chunk_of_rank(w, p, r - 1, M);
     for (int k = cp + 1; k <= c; ++k) w.chunk_start[k] = (int32_t)r;
     if (r == M - 1)
         for (int k = c + 1; k <= p.N; ++k) w.chunk_start[k] = (int32_t)M;
@@ -75,7 +73,6 @@ __global__ void k_medians(BuildWs w, BinParams p, double* d_out, int32_t* count_
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.N) return;
     const long long M = (long long)w.hdr->M;
-    const unsigned long long kmin = w.hdr->kmin;
     const int lo = w.chunk_start[k], hi = w.chunk_start[k + 1];
     const int c = hi - lo;
     count_out[k] = c;
@@ -84,15 +81,15 @@ __global__ void k_medians(BuildWs w, BinParams p, double* d_out, int32_t* count_
         if (c > 0) {
             double med;
             if (c & 1)
-                med = key_depth(w.keyA[lo + c / 2], kmin);
+                med = rank_depth(w, lo + c / 2);
             else
-                med = __dmul_rn(__dadd_rn(key_depth(w.keyA[lo + c / 2 - 1], kmin), key_depth(w.keyA[lo + c / 2], kmin)),
+                med = __dmul_rn(__dadd_rn(rank_depth(w, lo + c / 2 - 1), rank_depth(w, lo + c / 2)),
                                 0.5);
             d = __dadd_rn(med, p.D_forward);
         }
     } else if (M > 0) {
-        const double izmin = __ddiv_rn(1.0, key_depth(w.keyA[0], kmin));
-        const double izmax = __ddiv_rn(1.0, key_depth(w.keyA[M - 1], kmin));
+        const double izmin = __ddiv_rn(1.0, rank_depth(w, 0));
+        const double izmax = __ddiv_rn(1.0, rank_depth(w, M - 1));
         const double span = __dsub_rn(izmin, izmax);
         const double disp = __dsub_rn(izmin, __dmul_rn(__ddiv_rn(__dadd_rn((double)k, 0.5), (double)p.N), span));
         d = __dadd_rn(__ddiv_rn(1.0, disp), p.D_forward);

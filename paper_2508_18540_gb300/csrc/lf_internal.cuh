@@ -45,6 +45,7 @@ struct WsHeader {
     unsigned long long M;         // culled-in primitives
     unsigned long long total_dups;
     unsigned long long tile_n;    // pairs to sort (0 after an overflow)
+    unsigned long long long_runs; // depth-sort runs longer than 32 keys, sorted by k_depth_long_runs
     int overflow;                 // 1 if total_dups > dup_capacity
     int kind;                     // 0 gaussians, 1 voxels
     long long n;
@@ -56,8 +57,8 @@ struct WsHeader {
 // Carved build workspace (all device pointers).
 struct BuildWs {
     WsHeader* hdr;
-    unsigned long long* keyA;     // [n] depth keys (relative to the smallest after sorting)
-    unsigned long long* keyB;
+    unsigned long long* keyA;     // [n] depth keys by primitive (IEEE bits of the FP64 depth, or invalid)
+    unsigned long long* keyB;     // [n] scratch of the depth sort
     uint32_t* valA;               // [n] primitive ids (rank order after sorting)
     uint32_t* valB;
     float2* mean2d;               // [n] per primitive (Gaussians)
@@ -125,8 +126,9 @@ void launch_project_gaussians(const lf_gaussians& g, const ProjParams& p, const 
 void launch_project_voxels(const lf_voxels& v, const ProjParams& p, const BuildWs& ws, int32_t* rect,
                            int32_t* chunk, cudaStream_t s);
 
-// Stable LSD radix sort of the culled-in primitives by (depth, index); the
-// culled-in count ends in hdr->M and the result in (keyA, valA).
+// Order of the culled-in primitives by (FP64 depth, index): valA[r] = the
+// primitive of rank r (r < hdr->M). keyA keeps the primitives' depth keys
+// (IEEE bits, by primitive index). Uses tkeyA/tkeyB, valB, keyB as scratch.
 void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s);
 
 void launch_bin(const BuildWs& ws, const BinParams& p, long long n, int32_t* chunk, double* d, int32_t* count,

@@ -1,13 +1,19 @@
-// lf_sort.cu -- stable LSD radix sort (8-bit digits) of (key, value) pairs.
+// lf_sort.cu -- stable LSD radix sort (8-bit digits) of (key, value) pairs,
+// and the depth order built on it.
 //
 // Used twice per build:
-//  - the depth sort of Algorithm 1 line 3 ("Sort_and_Chunk"): 64-bit keys =
-//    IEEE bits of the positive FP64 reference depth (they order like the
-//    depths), values = primitive index. The first pass drops culled
-//    primitives (key kInvalidKey) and makes every key relative to the
-//    smallest valid key, so passes above the varying bits are plain copies.
-//    Values start in index order and every pass is stable, so equal depths
-//    stay in index order.
+//  - the depth sort of Algorithm 1 line 3 ("Sort_and_Chunk"): the order of
+//    the culled-in primitives by (FP64 depth, index). The IEEE bits of a
+//    positive FP64 depth order like the depth; relative to the smallest valid
+//    key they span up to ~55 bits. The sort takes their top 31 varying bits
+//    (an order-preserving truncation) as a 32-bit key, drops culled
+//    primitives in the first pass and sorts stably in four passes (values
+//    start in index order, so equal keys stay in index order). Keys that
+//    share the truncated value form runs that are then put in (full key,
+//    index) order: runs of up to 32 by one thread (insertion), longer runs by
+//    one CTA each (Batcher's odd-even merge network, in shared memory up to
+//    2048 keys, in global memory beyond). Realistic scenes have almost no
+//    runs; the run pass keeps the order exact for any input.
 //  - the 3D tiling (Sec. 4.4): 32-bit keys = tile id of every (tile, rank)
 //    pair emitted in rank order; the stable sort groups the pairs by tile and
 //    keeps each tile's pairs in depth order.
@@ -20,7 +26,7 @@
 //               them through shared memory into digit order and writes every
 //               digit run contiguously.
 // Item counts may live on the device (culled-in count, pair count), so grids
-// are sized for the capacity and blocks past the count write zero histograms.
+// are sized for the capacity and blocks past the count exit early.
 #include "lf_internal.cuh"
 
 namespace lf {
@@ -37,10 +43,10 @@ static_assert(kDigits == kThreads, "one digit per thread in the digit scans");
 struct PassArgs {
     long long n_static;                    // upper bound / fixed count
     const unsigned long long* n_dev;       // device count (or null)
-    const unsigned long long* kmin;        // valid key range (depth keys) or null
+    const unsigned long long* kmin;        // valid depth-key range (depth sort) or null
     const unsigned long long* kmax;
     int shift;
-    int first;                             // depth keys: drop invalid, make relative
+    int first;                             // depth sort: drop the invalid key (all ones)
     int nb;                                // number of blocks (histogram stride)
 };
 
@@ -49,13 +55,22 @@ __device__ __forceinline__ long long pass_count(const PassArgs& a)
     return a.n_dev ? (long long)*a.n_dev : a.n_static;
 }
 
-// every (relative) key has the same digit at this shift: identity pass
+// Right shift that keeps the top 31 varying bits of a depth key relative to
+// the smallest valid key (0 if the range already fits).
+__device__ __forceinline__ int depth_shift(unsigned long long lo, unsigned long long hi)
+{
+    if (lo > hi) return 0;
+    const int bits = 64 - __clzll((long long)(hi - lo));
+    return bits > 31 ? bits - 31 : 0;
+}
+
+// every valid truncated depth key has the same digit at this shift: identity pass
 __device__ __forceinline__ bool pass_uniform(const PassArgs& a)
 {
     if (a.first || !a.kmin) return false;
     const unsigned long long lo = *a.kmin, hi = *a.kmax;
     if (lo > hi) return true;   // no valid keys
-    return ((hi - lo) >> a.shift) == 0ull;
+    return (((hi - lo) >> depth_shift(lo, hi)) >> a.shift) == 0ull;
 }
 
 template <typename K>
@@ -66,16 +81,11 @@ __device__ __forceinline__ uint32_t digit_of(K k, int shift)
 
 // the key as sorted; false if absent (past the count, or culled)
 template <typename K>
-__device__ __forceinline__ bool load_key(const K* keys, long long idx, long long n, const PassArgs& a,
-                                         unsigned long long kmin, K& k)
+__device__ __forceinline__ bool load_key(const K* keys, long long idx, long long n, const PassArgs& a, K& k)
 {
     if (idx >= n) return false;
     k = keys[idx];
-    if (a.first) {
-        if ((unsigned long long)k == kInvalidKey) return false;
-        k = (K)((unsigned long long)k - kmin);
-    }
-    return true;
+    return !(a.first && k == (K)~(K)0);
 }
 
 // lanes holding the same digit (ballot per digit bit); valid lanes only
@@ -97,7 +107,10 @@ __global__ void __launch_bounds__(kThreads) k_upsweep(const K* __restrict__ keys
     __shared__ uint32_t h[kDigits];
     if (pass_uniform(a)) return;
     const long long n = pass_count(a);
-    const unsigned long long kmin = a.kmin ? *a.kmin : 0ull;
+    if ((long long)blockIdx.x * kRadixBlockKeys >= n) {   // past the device count: empty histogram
+        hist[(size_t)threadIdx.x * a.nb + blockIdx.x] = 0u;
+        return;
+    }
     h[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -107,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) k_upsweep(const K* __restrict__ keys
 #pragma unroll
     for (int r = 0; r < kKPT; ++r) {
         K k = 0;
-        okm |= load_key(keys, base + r * 32 + lane, n, a, kmin, k) ? (1u << r) : 0u;
+        okm |= load_key(keys, base + r * 32 + lane, n, a, k) ? (1u << r) : 0u;
         kk[r] = k;
     }
 #pragma unroll
@@ -129,10 +142,13 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(uint32_t* hist, uint32_t* 
     __shared__ uint32_t warp_tot[kWarps];
     uint32_t* row = hist + (size_t)blockIdx.x * a.nb;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // blocks past the device count hold no keys (their downsweep exits)
+    const long long n = pass_count(a);
+    const int nb = (int)min((long long)a.nb, (n + kRadixBlockKeys - 1) / kRadixBlockKeys);
     uint32_t carry = 0;
-    for (int base = 0; base < a.nb; base += kThreads) {
+    for (int base = 0; base < nb; base += kThreads) {
         const int i = base + threadIdx.x;
-        const uint32_t v = i < a.nb ? row[i] : 0u;
+        const uint32_t v = i < nb ? row[i] : 0u;
         uint32_t x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -148,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) k_rowscan(uint32_t* hist, uint32_t* 
             before += w < warp ? t : 0u;
             total += t;
         }
-        if (i < a.nb) row[i] = carry + before + x - v;
+        if (i < nb) row[i] = carry + before + x - v;
         carry += total;
         __syncthreads();
     }
@@ -212,7 +228,6 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const K* __restrict__ ki
         return;
     }
     if (blk >= n) return;
-    const unsigned long long kmin = a.kmin ? *a.kmin : 0ull;
     const int d0 = threadIdx.x;   // the digit this thread scans
 
 #pragma unroll
@@ -235,7 +250,7 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const K* __restrict__ ki
     for (int r = 0; r < kKPT; ++r) {
         const long long idx = wbase + r * 32 + lane;
         K k = 0;
-        const bool ok = load_key(kin, idx, n, a, kmin, k);
+        const bool ok = load_key(kin, idx, n, a, k);
         key[r] = k;
         val[r] = ok ? vin[idx] : 0u;
         okm |= ok ? (1u << r) : 0u;
@@ -284,6 +299,136 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const K* __restrict__ ki
     }
 }
 
+// ---- depth order ---------------------------------------------------------
+
+// truncated 32-bit depth key of every primitive (all ones if culled)
+__global__ void __launch_bounds__(256) k_depth_key32(const unsigned long long* __restrict__ key64,
+                                                     uint32_t* __restrict__ k32, long long n,
+                                                     const WsHeader* __restrict__ hdr)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned long long lo = hdr->kmin, hi = hdr->kmax;
+    const unsigned long long k = key64[i];
+    k32[i] = k == kInvalidKey ? 0xffffffffu : (uint32_t)((k - lo) >> depth_shift(lo, hi));
+}
+
+// (full key, index) order of two ranks' primitives
+__device__ __forceinline__ bool depth_less(unsigned long long ka, uint32_t va, unsigned long long kb, uint32_t vb)
+{
+    return ka < kb || (ka == kb && va < vb);
+}
+
+constexpr int kShortRun = 32;
+constexpr int kLongRunCtas = 304;
+constexpr int kLongRunThreads = 1024;
+constexpr int kSmemRun = 2048;
+
+// Runs of equal truncated keys: up to kShortRun sorted here by the thread
+// at the run start; longer ones listed (start, length) in tkeyB.
+__global__ void __launch_bounds__(256) k_depth_runs(BuildWs w)
+{
+    const long long M = (long long)w.hdr->M;
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    const uint32_t* k = w.tkeyA;
+    const uint32_t kr = k[r];
+    if (r > 0 && k[r - 1] == kr) return;          // not the start of a run
+    if (r + 1 >= M || k[r + 1] != kr) return;     // a run of one
+    long long e = r + 2;
+    while (e < M && k[e] == kr) ++e;
+    const int L = (int)min(e - r, (long long)0x7fffffff);
+    if (L > kShortRun) {
+        const unsigned long long q = atomicAdd(&w.hdr->long_runs, 1ull);
+        w.tkeyB[2 * q] = (uint32_t)r;
+        w.tkeyB[2 * q + 1] = (uint32_t)L;
+        return;
+    }
+    unsigned long long kk[kShortRun];
+    uint32_t vv[kShortRun];
+    for (int i = 0; i < L; ++i) {
+        const uint32_t v = w.valA[r + i];
+        const unsigned long long key = w.keyA[v];
+        int j = i;
+        while (j > 0 && depth_less(key, v, kk[j - 1], vv[j - 1])) {
+            kk[j] = kk[j - 1];
+            vv[j] = vv[j - 1];
+            --j;
+        }
+        kk[j] = key;
+        vv[j] = v;
+    }
+    for (int i = 0; i < L; ++i) w.valA[r + i] = vv[i];
+}
+
+// Batcher's odd-even merge network over P = 2^m slots: every comparator puts
+// the smaller element at the lower slot, so slots past the run length L act
+// as +infinity and are never touched. Stage (p, k) compares slot a with
+// a + k when a >= k mod p, (a - k mod p) mod 2k < k and a, a + k lie in the
+// same block of 2p slots.
+__device__ __forceinline__ bool oem_pair(long long a, long long p, long long k)
+{
+    const long long j0 = k % p;
+    return a >= j0 && ((a - j0) % (2 * k)) < k && (a / (2 * p)) == ((a + k) / (2 * p));
+}
+
+// Runs longer than kShortRun: one CTA per run (grid-stride over the list).
+__global__ void __launch_bounds__(kLongRunThreads) k_depth_long_runs(BuildWs w)
+{
+    __shared__ unsigned long long sk[kSmemRun];
+    __shared__ uint32_t sv[kSmemRun];
+    const unsigned long long nr = w.hdr->long_runs;
+    for (unsigned long long q = blockIdx.x; q < nr; q += gridDim.x) {
+        const long long r = w.tkeyB[2 * q];
+        const long long L = w.tkeyB[2 * q + 1];
+        long long P = 1;
+        while (P < L) P <<= 1;
+        if (P <= kSmemRun) {
+            for (long long i = threadIdx.x; i < L; i += blockDim.x) {
+                const uint32_t v = w.valA[r + i];
+                sv[i] = v;
+                sk[i] = w.keyA[v];
+            }
+            __syncthreads();
+            for (long long p = 1; p < P; p <<= 1)
+                for (long long k = p; k >= 1; k >>= 1) {
+                    for (long long a = threadIdx.x; a + k < L; a += blockDim.x) {
+                        if (!oem_pair(a, p, k)) continue;
+                        const long long b = a + k;
+                        if (depth_less(sk[b], sv[b], sk[a], sv[a])) {
+                            const unsigned long long tk = sk[a];
+                            const uint32_t tv = sv[a];
+                            sk[a] = sk[b], sv[a] = sv[b];
+                            sk[b] = tk, sv[b] = tv;
+                        }
+                    }
+                    __syncthreads();
+                }
+            for (long long i = threadIdx.x; i < L; i += blockDim.x) w.valA[r + i] = sv[i];
+            __syncthreads();
+        } else {
+            unsigned long long* gk = w.keyB + r;
+            uint32_t* gv = w.valA + r;
+            for (long long i = threadIdx.x; i < L; i += blockDim.x) gk[i] = w.keyA[gv[i]];
+            __syncthreads();
+            for (long long p = 1; p < P; p <<= 1)
+                for (long long k = p; k >= 1; k >>= 1) {
+                    for (long long a = threadIdx.x; a + k < L; a += blockDim.x) {
+                        if (!oem_pair(a, p, k)) continue;
+                        const long long b = a + k;
+                        if (depth_less(gk[b], gv[b], gk[a], gv[a])) {
+                            const unsigned long long tk = gk[a];
+                            const uint32_t tv = gv[a];
+                            gk[a] = gk[b], gv[a] = gv[b];
+                            gk[b] = tk, gv[b] = tv;
+                        }
+                    }
+                    __syncthreads();
+                }
+        }
+    }
+}
+
 template <typename K>
 void radix_pass(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, const PassArgs& a, uint32_t* hist,
                 uint32_t* tot, cudaStream_t s)
@@ -301,10 +446,11 @@ void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s)
 {
     if (n <= 0) return;
     const int nb = (int)((n + kRadixBlockKeys - 1) / kRadixBlockKeys);
-    unsigned long long* kb[2] = {ws.keyA, ws.keyB};
+    k_depth_key32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws.keyA, ws.tkeyA, n, ws.hdr);
+    uint32_t* kb[2] = {ws.tkeyA, ws.tkeyB};
     uint32_t* vb[2] = {ws.valA, ws.valB};
     int cur = 0;
-    for (int pass = 0; pass < 64 / kBits; ++pass) {
+    for (int pass = 0; pass < 32 / kBits; ++pass) {
         PassArgs a;
         a.n_static = n;
         a.n_dev = pass == 0 ? nullptr : &ws.hdr->M;
@@ -313,10 +459,13 @@ void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s)
         a.shift = pass * kBits;
         a.first = pass == 0;
         a.nb = nb;
-        radix_pass<unsigned long long>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], a, ws.hist, ws.dtot, s);
+        radix_pass<uint32_t>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], a, ws.hist, ws.dtot, s);
         cur ^= 1;
     }
-    // 8 passes: the result is back in (keyA, valA)
+    // four passes: truncated keys in tkeyA, ranks in valA; now the runs
+    k_depth_runs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws);
+    k_depth_long_runs<<<kLongRunCtas, kLongRunThreads, 0, s>>>(ws);
+    note_launches(3);
 }
 
 int tile_sort_passes(int tile_bits) { return (tile_bits + kBits - 1) / kBits; }

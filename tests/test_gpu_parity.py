@@ -172,3 +172,34 @@ def test_host_pipeline_frames_match_synchronous_renders():
     for sc, o in zip(scenes, outs):
         want = ref.render(api.DeviceGaussians.from_scene(sc)).cpu()
         assert torch.equal(o, want)
+
+
+def test_depth_order_with_near_equal_depths(orc):
+    # A camera turned by 1e-9 rad about y gives depth = z - 1e-9 x (FP64), so
+    # Gaussians sharing z but not x differ in depth by ~1e-13: far below the
+    # 31 bits the depth sort keeps of the key range. Clusters of 5000, 40 and
+    # 10 such Gaussians (shuffled) exercise all three run fix-ups (global
+    # memory network, shared memory network, insertion); the order must
+    # still equal the oracle's (FP64 depth, index) order exactly.
+    rng = np.random.default_rng(77)
+    th = 1e-9
+    R = np.array([[np.cos(th), 0.0, np.sin(th)], [0.0, 1.0, 0.0], [-np.sin(th), 0.0, np.cos(th)]])
+    cam = S.Camera(R, np.zeros(3), np.radians(50.0), np.radians(50.0), 96, 96)
+    bg = S.uniform_gaussians(3000, 78)
+    parts = [bg]
+    for cnt, z in ((5000, 4.0), (40, 3.0), (10, 5.0)):
+        m = np.zeros((cnt, 3), np.float32)
+        m[:, 0] = rng.permutation(np.linspace(-0.5, 0.5, cnt)).astype(np.float32)
+        m[:, 1] = rng.uniform(-0.3, 0.3, cnt).astype(np.float32)
+        m[:, 2] = z
+        q = rng.normal(size=(cnt, 4)).astype(np.float32)
+        parts.append(S.GaussianScene(m, np.full((cnt, 3), 0.01, np.float32), q,
+                                     rng.uniform(0.1, 0.9, cnt).astype(np.float32),
+                                     rng.uniform(0, 1, (cnt, 3)).astype(np.float32)))
+    sc = S.GaussianScene(*(np.ascontiguousarray(np.concatenate([getattr(p, f) for p in parts]))
+                           for f in ("means", "scales", "quats", "opacity", "rgb")))
+    disp = S.display_for(3.0, 0.1)
+    views = S.ViewSet(5)
+    o = orc.render(scene=sc, camera=cam, display=disp, views=views, N=8, binning="quantile")
+    gpu = G.run_gpu(sc, cam, disp, views, 8, "quantile", "f32")
+    _compare(gpu, o, o["ref"].W, o["ref"].H, 8, "f32")
