@@ -180,7 +180,7 @@ def run_ours(args):
 
     res = {}
     clocks = ClockSampler(local)
-    for dtype in ("f32", "f16", "bf16"):
+    for dtype in ("f32", "f16", "bf16", "u8"):
         r = api.LightFieldRenderer(wl.camera, wl.display, wl.views, wl.N, wl.binning, dtype, device=dev)
         if dtype == "f32":
             clocks.start()
@@ -233,7 +233,7 @@ def run_ours(args):
 
     def roof(dtype):
         st = res[dtype]["stages"]
-        bp = {"f32": 4, "f16": 2, "bf16": 2}[dtype]
+        bp = {"f32": 4, "f16": 2, "bf16": 2, "u8": 1}[dtype]
         out = {}
         if "composite" in st:
             ms_c = st["composite"][0] / st["composite"][1]
@@ -270,7 +270,7 @@ def run_ours(args):
             "views_per_s": round(fps * WORKLOAD["V"], 1),
             "variants": {d: {"planes": d, "value": round(1000.0 / res[d]["ms"] * world, 2),
                              "ms_per_step": round(res[d]["ms"], 4), "roofline": roofs[d]}
-                         for d in ("f16", "bf16")},
+                         for d in ("f16", "bf16", "u8")},
             "stages_ms": {d: {k: round(v[0] / v[1], 4) for k, v in res[d]["stages"].items()} for d in res},
             "e2e": {"value": round(1000.0 / e_ms * world, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e_ms, 4),
@@ -283,8 +283,9 @@ def run_ours(args):
             "roofline_by_kernel": roofs["f32"],
             "clocks": clk,
         }
+    if rank == 0 and world == 1:
+        line["_views_host"] = {d: res[d].pop("views_host", None) for d in res}
     if rank == 0 and world == 1 and not args.no_extras:
-        views_host = {d: res[d].pop("views_host", None) for d in res}
         for d in res:
             res[d]["renderer"] = None
         del r32, host_in, host_out, g, flush, pipe
@@ -295,7 +296,6 @@ def run_ours(args):
         torch.cuda.empty_cache()
         line["batched"] = run_batched(args, dev)
         torch.cuda.empty_cache()
-        line["_views_host"] = views_host
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

@@ -49,7 +49,10 @@ typedef enum {
     LF_ERR_TIMEOUT = 6        /* a bounded device-side wait gave up */
 } lf_status;
 
-typedef enum { LF_F32 = 0, LF_F16 = 1, LF_BF16 = 2 } lf_dtype;
+/* Plane storage types. LF_U8 is RGBA8 unorm: every channel (premultiplied
+ * colour, A) clamped to [0, 1] and stored as round(255 v), read back as
+ * byte / 255 (the paper's default plane format). Accumulation is FP32. */
+typedef enum { LF_F32 = 0, LF_F16 = 1, LF_BF16 = 2, LF_U8 = 3 } lf_dtype;
 
 typedef enum {
     LF_BIN_QUANTILE = 0,      /* Sec. 4.4: equal-count chunks, d_k = median depth */

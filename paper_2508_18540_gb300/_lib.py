@@ -22,7 +22,7 @@ LF_ERR_TIMEOUT = 6
 STATUS_NAMES = {0: "LF_OK", 1: "LF_ERR_INVALID_ARG", 2: "LF_ERR_WORKSPACE", 3: "LF_ERR_CUDA",
                 4: "LF_ERR_OVERFLOW", 5: "LF_ERR_UNSUPPORTED", 6: "LF_ERR_TIMEOUT"}
 
-LF_F32, LF_F16, LF_BF16 = 0, 1, 2
+LF_F32, LF_F16, LF_BF16, LF_U8 = 0, 1, 2, 3
 LF_BIN_QUANTILE, LF_BIN_DISPARITY = 0, 1
 
 _D = ctypes.c_double

@@ -16,8 +16,8 @@ import torch
 from . import _lib as L
 from ._lib import check, load
 
-DTYPES = {"f32": L.LF_F32, "f16": L.LF_F16, "bf16": L.LF_BF16}
-TORCH_DTYPES = {L.LF_F32: torch.float32, L.LF_F16: torch.float16, L.LF_BF16: torch.bfloat16}
+DTYPES = {"f32": L.LF_F32, "f16": L.LF_F16, "bf16": L.LF_BF16, "u8": L.LF_U8}
+TORCH_DTYPES = {L.LF_F32: torch.float32, L.LF_F16: torch.float16, L.LF_BF16: torch.bfloat16, L.LF_U8: torch.uint8}
 BINNING = {"quantile": L.LF_BIN_QUANTILE, "disparity": L.LF_BIN_DISPARITY}
 
 

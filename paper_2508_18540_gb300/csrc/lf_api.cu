@@ -183,7 +183,7 @@ static lf_status check_planes(const lf_planes* p, const lf_ref_camera* r, int32_
     if (N < 1 || N > 65535) return fail(LF_ERR_INVALID_ARG, "N_chunk must be in 1..65535");
     if (p->N != N || p->W != r->W || p->H != r->H)
         return fail(LF_ERR_INVALID_ARG, "plane array shape does not match N / reference camera");
-    if (p->dtype < LF_F32 || p->dtype > LF_BF16) return fail(LF_ERR_INVALID_ARG, "unknown plane dtype");
+    if (p->dtype < LF_F32 || p->dtype > LF_U8) return fail(LF_ERR_INVALID_ARG, "unknown plane dtype");
     if (!p->rgba || !p->d || !p->count || !p->chunk || !p->rect)
         return fail(LF_ERR_INVALID_ARG, "a plane output pointer is NULL");
     return LF_OK;
@@ -273,7 +273,7 @@ static lf_status check_composite_args(const lf_planes* planes, const lf_ref_came
     if (!planes || !views || !views_buf) return fail(LF_ERR_INVALID_ARG, "NULL argument");
     if (planes->N < 1 || planes->W != ref->W || planes->H != ref->H)
         return fail(LF_ERR_INVALID_ARG, "plane array shape does not match the reference camera");
-    if (planes->dtype < LF_F32 || planes->dtype > LF_BF16) return fail(LF_ERR_INVALID_ARG, "unknown plane dtype");
+    if (planes->dtype < LF_F32 || planes->dtype > LF_U8) return fail(LF_ERR_INVALID_ARG, "unknown plane dtype");
     if (!planes->rgba || !planes->d || !planes->count) return fail(LF_ERR_INVALID_ARG, "plane pointer is NULL");
     if (views->Vx < 1 || views->Vy < 1 || views->Vx > 65535 || views->Vy > 65535)
         return fail(LF_ERR_INVALID_ARG, "view counts must be in 1..65535");

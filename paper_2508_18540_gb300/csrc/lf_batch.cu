@@ -55,7 +55,7 @@ lf_status check_scene(const lf_batch_scene& s, int i)
         return fail(LF_ERR_INVALID_ARG, at + "NULL plane or view pointer");
     if (!s.ws || !s.cws || ((uintptr_t)s.ws) % 256 || ((uintptr_t)s.cws) % 256)
         return fail(LF_ERR_WORKSPACE, at + "workspaces must be non-NULL and 256-byte aligned");
-    const int tb = s.planes.dtype == LF_F32 ? 16 : 8;
+    const int tb = texel_bytes(s.planes.dtype);
     if (((size_t)s.ref.W * tb) % 16 || ((uintptr_t)s.planes.rgba) % 16)
         return fail(LF_ERR_UNSUPPORTED, at + "plane rows must be 16-byte multiples on a 16-byte aligned base");
     return LF_OK;
@@ -102,7 +102,7 @@ lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, siz
     b->rtab = reinterpret_cast<RasterScene*>(base + align256(16));
     b->ctab = reinterpret_cast<CompScene*>(base + align256(16) + align256(sizeof(RasterScene) * n));
 
-    const int tb = b->dtype == LF_F32 ? 16 : 8;
+    const int tb = texel_bytes(b->dtype);
     std::vector<RasterScene> r(n);
     std::vector<CompScene> c(n);
     std::vector<double> rwork(n), cwork(n);

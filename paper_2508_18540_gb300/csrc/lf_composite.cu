@@ -77,11 +77,21 @@ __global__ void k_comp_coeffs(CompParams p, const double* __restrict__ d, const 
     if (!(fmax(fabs(lo), fabs(hi)) + span + 2.0 < (double)kNarrow)) atomicOr(&w.wide[k], 1);
 }
 
+// RGBA8 unorm texel: byte / 255 per channel
+__device__ __forceinline__ float4 unpack_u8x4(uint32_t u)
+{
+    constexpr float s = 1.0f / 255.0f;
+    return make_float4((float)(u & 0xffu) * s, (float)((u >> 8) & 0xffu) * s, (float)((u >> 16) & 0xffu) * s,
+                       (float)(u >> 24) * s);
+}
+
 template <int DT>
 __device__ __forceinline__ float4 load_texel(const void* planes, size_t idx)
 {
     if (DT == LF_F32) {
         return __ldg(reinterpret_cast<const float4*>(planes) + idx);
+    } else if (DT == LF_U8) {
+        return unpack_u8x4(__ldg(reinterpret_cast<const uint32_t*>(planes) + idx));
     } else {
         const uint2 u = __ldg(reinterpret_cast<const uint2*>(planes) + idx);
         if (DT == LF_F16) {
@@ -261,6 +271,13 @@ __device__ __forceinline__ uint2 lds_u2(uint32_t a)
     return v;
 }
 
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
 __device__ __forceinline__ float lds_f(uint32_t a)
 {
     float v;
@@ -292,6 +309,11 @@ struct Texel<LF_F16> {
         const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
         return make_float4(a.x, a.y, b.x, b.y);
     }
+};
+template <>
+struct Texel<LF_U8> {
+    static constexpr int kBytes = 4;
+    static __device__ __forceinline__ float4 load(uint32_t row, uint32_t i) { return unpack_u8x4(lds_u32(row + i * 4u)); }
 };
 template <>
 struct Texel<LF_BF16> {
@@ -1065,7 +1087,9 @@ bool launch_composite_batched(const CompScene* scenes_dev, int n_sc, long long t
     if (total <= 0) return true;
     const size_t smem = composite_batched_smem(max_stage_bytes, maxN, VG);
     if (smem > 200 * 1024) return false;
-    if (dtype == LF_F32)
+    if (dtype == LF_U8)
+        launch_batched_dt<LF_U8>(bilinear, VG, scenes_dev, n_sc, total, max_stage_bytes, maxN, counter, n_ctas, smem, s);
+    else if (dtype == LF_F32)
         launch_batched_dt<LF_F32>(bilinear, VG, scenes_dev, n_sc, total, max_stage_bytes, maxN, counter, n_ctas, smem, s);
     else if (dtype == LF_F16)
         launch_batched_dt<LF_F16>(bilinear, VG, scenes_dev, n_sc, total, max_stage_bytes, maxN, counter, n_ctas, smem, s);
@@ -1083,6 +1107,7 @@ const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
     switch (p.dtype) {
     case LF_F32: launch_composite_bwd_t<LF_F32>(p, planes, count, ws, dviews, dplanes, s); break;
     case LF_F16: launch_composite_bwd_t<LF_F16>(p, planes, count, ws, dviews, dplanes, s); break;
+    case LF_U8: launch_composite_bwd_t<LF_U8>(p, planes, count, ws, dviews, dplanes, s); break;
     default: launch_composite_bwd_t<LF_BF16>(p, planes, count, ws, dviews, dplanes, s); break;
     }
 }
@@ -1100,6 +1125,7 @@ void launch_composite(const CompParams& p, const void* planes, const int32_t* co
     switch (p.dtype) {
     case LF_F32: launch_composite_t<LF_F32>(p, planes, count, ws, out, s); break;
     case LF_F16: launch_composite_t<LF_F16>(p, planes, count, ws, out, s); break;
+    case LF_U8: launch_composite_t<LF_U8>(p, planes, count, ws, out, s); break;
     default: launch_composite_t<LF_BF16>(p, planes, count, ws, out, s); break;
     }
 }

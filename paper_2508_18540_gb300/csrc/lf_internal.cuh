@@ -24,6 +24,9 @@ constexpr int kSortDigits = 256;          // 8-bit radix digits
 constexpr int kDupBlock = 1024;           // ranks per block of the tile-pair emission
 constexpr uint64_t kInvalidKey = ~0ull;
 
+// bytes of one RGBA texel of a plane type
+inline int texel_bytes(int dtype) { return dtype == LF_F32 ? 16 : dtype == LF_U8 ? 4 : 8; }
+
 // ---- launch counting and stage tracing ------------------------------------
 // Every kernel launch of the library bumps a process-wide counter; when
 // tracing is on, each pipeline stage is bracketed by a CUDA event pair on the

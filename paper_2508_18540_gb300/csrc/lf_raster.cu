@@ -27,6 +27,11 @@ __device__ __forceinline__ void store_texel(void* planes, size_t idx, float r, f
 {
     if (DT == LF_F32) {
         reinterpret_cast<float4*>(planes)[idx] = make_float4(r, g, b, a);
+    } else if (DT == LF_U8) {
+        // RGBA8 unorm: round(255 clamp(v, 0, 1)) per channel
+        const uint32_t q0 = __float2uint_rn(__saturatef(r) * 255.0f), q1 = __float2uint_rn(__saturatef(g) * 255.0f);
+        const uint32_t q2 = __float2uint_rn(__saturatef(b) * 255.0f), q3 = __float2uint_rn(__saturatef(a) * 255.0f);
+        reinterpret_cast<uint32_t*>(planes)[idx] = q0 | (q1 << 8) | (q2 << 16) | (q3 << 24);
     } else if (DT == LF_F16) {
         const __half2 lo = __floats2half2_rn(r, g), hi = __floats2half2_rn(b, a);
         uint2 u;
@@ -795,6 +800,7 @@ void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uin
     switch (p.dtype) {
     case LF_F32: k_raster_gauss<LF_F32, kPPT><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
     case LF_F16: k_raster_gauss<LF_F16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
+    case LF_U8: k_raster_gauss<LF_U8, kPPT><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
     default: k_raster_gauss<LF_BF16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
     }
     note_launches(1);
@@ -807,9 +813,11 @@ void launch_raster_gauss_batched(const RasterScene* scenes_dev, int n_sc, long l
 #define LF_RB(DT_, PPT_)                                                                                  \
     k_raster_gauss_batched<DT_, PPT_><<<n_ctas, kTilePix / PPT_, 0, s>>>(scenes_dev, n_sc, total, counter)
     if (ppt == 4) {
-        if (dtype == LF_F32) LF_RB(LF_F32, 4); else if (dtype == LF_F16) LF_RB(LF_F16, 4); else LF_RB(LF_BF16, 4);
+        if (dtype == LF_F32) LF_RB(LF_F32, 4); else if (dtype == LF_F16) LF_RB(LF_F16, 4);
+        else if (dtype == LF_U8) LF_RB(LF_U8, 4); else LF_RB(LF_BF16, 4);
     } else {
-        if (dtype == LF_F32) LF_RB(LF_F32, 2); else if (dtype == LF_F16) LF_RB(LF_F16, 2); else LF_RB(LF_BF16, 2);
+        if (dtype == LF_F32) LF_RB(LF_F32, 2); else if (dtype == LF_F16) LF_RB(LF_F16, 2);
+        else if (dtype == LF_U8) LF_RB(LF_U8, 2); else LF_RB(LF_BF16, 2);
     }
 #undef LF_RB
     note_launches(1);
@@ -832,6 +840,7 @@ void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32
     switch (p.dtype) {
     case LF_F32: k_raster_voxel<LF_F32><<<grid, kTilePix, 0, s>>>(ws, p, ranks, planes); break;
     case LF_F16: k_raster_voxel<LF_F16><<<grid, kTilePix, 0, s>>>(ws, p, ranks, planes); break;
+    case LF_U8: k_raster_voxel<LF_U8><<<grid, kTilePix, 0, s>>>(ws, p, ranks, planes); break;
     default: k_raster_voxel<LF_BF16><<<grid, kTilePix, 0, s>>>(ws, p, ranks, planes); break;
     }
     note_launches(1);

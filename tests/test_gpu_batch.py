@@ -47,7 +47,7 @@ def _check_equal(batch, wls, dtype):
         assert torch.equal(batch.outputs[i], want), i
 
 
-@pytest.mark.parametrize("dtype", ["f16", "f32"])
+@pytest.mark.parametrize("dtype", ["f16", "f32", "u8"])
 def test_batch_equals_one_by_one(dtype):
     wls = _scenes()
     b = api.BatchRenderer(wls, dtype)

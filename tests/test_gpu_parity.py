@@ -203,3 +203,24 @@ def test_depth_order_with_near_equal_depths(orc):
     o = orc.render(scene=sc, camera=cam, display=disp, views=views, N=8, binning="quantile")
     gpu = G.run_gpu(sc, cam, disp, views, 8, "quantile", "f32")
     _compare(gpu, o, o["ref"].W, o["ref"].H, 8, "f32")
+
+
+@pytest.mark.parametrize("bilinear", [False, True])
+def test_u8_planes(orc, bilinear):
+    # RGBA8 planes (the paper's default format): every texel within half a
+    # code (plus FP32 rounding) of the FP64 plane; the views equal the FP64
+    # composite of the GPU's own dequantised planes within the FP32 bar; and
+    # the quantisation error of the views against the FP64 oracle stays
+    # above 40 dB PSNR per view.
+    w = S.workload_tiny()
+    views = S.ViewSet(w.views.Vx, 1, bilinear)
+    o = orc.render(scene=w.scene, camera=w.camera, display=w.display, views=views, N=w.N, binning=w.binning)
+    gpu = G.run_gpu(w.scene, w.camera, w.display, views, w.N, w.binning, "u8")
+    assert gpu["status"] == 0
+    pl = gpu["renderer"].planes.rgba.cpu().numpy().astype(np.float64) / 255.0
+    assert np.abs(pl - o["planes"]).max() <= 0.5 / 255.0 + 2e-4
+    ref = o["ref"]
+    v_own = orc.composite(ref, pl, o["d"], o["count"], views.Vx, views.Vy, bilinear, views.bg)
+    assert np.abs(gpu["views"] - v_own).max() <= 1e-4
+    for k in range(gpu["views"].shape[0]):
+        assert G.psnr(gpu["views"][k], o["views"][k]) >= 40.0
