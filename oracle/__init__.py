@@ -81,6 +81,9 @@ def lib():
                                        ctypes.c_double, _P, _P, ctypes.c_int32, _P]
         L.orc_voxel_alpha.argtypes = [_P, ctypes.c_double, _P, _P, _P, _P]
         L.orc_voxel_alpha.restype = ctypes.c_double
+        L.orc_filter_weights.argtypes = [ctypes.c_double, ctypes.c_int32, _P]
+        L.orc_filter_planes.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                        ctypes.c_int32]
         L.orc_composite.argtypes = [ctypes.POINTER(OrcRef), ctypes.c_int32, _P, _P, _P, ctypes.c_int32,
                                     ctypes.c_int32, ctypes.c_int32, _P, _P]
         _lib = L
@@ -237,6 +240,20 @@ def composite(ref: OrcRef, planes: np.ndarray, d, count, Vx: int, Vy: int, bilin
     lib().orc_composite(ctypes.byref(ref), N, _ptr(planes), _ptr(d), _ptr(count), Vx, Vy, int(bool(bilinear)),
                         _ptr(bgv), _ptr(views))
     return views
+
+
+def filter_weights(sigma: float, radius: int) -> np.ndarray:
+    w = np.zeros(2 * radius + 1, np.float64)
+    lib().orc_filter_weights(float(sigma), int(radius), _ptr(w))
+    return w
+
+
+def filter_planes(planes: np.ndarray, sigma: float, radius: int) -> np.ndarray:
+    """Sec. 4.5 low-pass plane filter (separable Gaussian, zero padding); returns a filtered copy."""
+    out = _c(planes, np.float64).copy()
+    N, H, W, _ = out.shape
+    lib().orc_filter_planes(_ptr(out), N, H, W, float(sigma), int(radius))
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -10,7 +10,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["orc_geometry.c", "orc_gaussians.c", "orc_voxels.c", "orc_composite.c"]
+SOURCES = ["orc_geometry.c", "orc_gaussians.c", "orc_voxels.c", "orc_composite.c", "orc_filter.c"]
 LIB = os.path.join(HERE, "liborc.so")
 
 

@@ -127,6 +127,14 @@ void orc_splat_voxels(const orc_ref* r, int64_t M, const int64_t* order, const i
 double orc_voxel_alpha(const double* lo, double side, const double* density8,
                        const double* o, const double* dir, double* seg_len);
 
+/* Sec. 4.5 low-pass plane filter (V2LF): normalised discrete Gaussian
+ * weights w[2 radius + 1] for offsets -radius..radius. */
+void orc_filter_weights(double sigma, int32_t radius, double* w);
+
+/* Separable filter of every RGBA channel of planes[N][H][W][4] (rows, then
+ * columns), zero padding outside the plane; in place. */
+void orc_filter_planes(double* planes, int32_t N, int32_t H, int32_t W, double sigma, int32_t radius);
+
 /* Sec. 4.3 swizzle blending, Algorithm 1 second loop.
  * views[Vy*Vx][Ny][Nx][4] = (Q + T bg, 1 - T); view index i*Vx + j. */
 void orc_composite(const orc_ref* r, int32_t N, const double* planes, const double* d,
