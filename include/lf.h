@@ -222,6 +222,15 @@ lf_status lf_mpi_status(const void* ws, int64_t* needed, int64_t* culled_in);
 lf_status lf_mpi_tile_lists(const void* ws, int32_t* order, int64_t n, int32_t* tile_prims, int64_t cap,
                             int32_t* seg, int64_t* n_pairs);
 
+/* Sec. 4.5 low-pass plane filter of V2LF (it replaces SVR's supersampling):
+ * every RGBA channel of every plane is filtered in place with a separable,
+ * normalised discrete Gaussian of standard deviation sigma (plane pixels)
+ * over offsets -radius..radius (radius <= 0: ceil(3 sigma)), rows then
+ * columns, transparent zero padding outside the plane, FP32 arithmetic.
+ * Allocates nothing. Weights are computed on the host in FP64 and rounded
+ * to FP32. Errors: LF_ERR_INVALID_ARG (sigma <= 0, radius > 16, bad planes). */
+lf_status lf_filter_planes(const lf_planes* planes, double sigma, int32_t radius, cudaStream_t stream);
+
 /* ---- composite: planes -> quilt views (Algorithm 1 lines 6-11) --------- */
 
 /* Workspace bytes for lf_composite / lf_composite_backward. */

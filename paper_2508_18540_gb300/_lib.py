@@ -95,6 +95,7 @@ SIGNATURES = [
                                            _P, ctypes.c_size_t, ctypes.POINTER(LfPlanes), _P]),
     ("lf_mpi_status", ctypes.c_int, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     ("lf_mpi_tile_lists", ctypes.c_int, [_P, _P, _I64, _P, _I64, _P, ctypes.POINTER(_I64)]),
+    ("lf_filter_planes", ctypes.c_int, [ctypes.POINTER(LfPlanes), _D, _I32, _P]),
     ("lf_composite_workspace_size", ctypes.c_size_t, [_I32, ctypes.POINTER(LfViewSet)]),
     ("lf_composite", ctypes.c_int, [ctypes.POINTER(LfPlanes), ctypes.POINTER(LfRefCamera),
                                     ctypes.POINTER(LfViewSet), _P, _P, ctypes.c_size_t, _P]),

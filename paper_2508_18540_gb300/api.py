@@ -222,6 +222,12 @@ def lf_mpi_tile_lists(ws: torch.Tensor, n: int, n_tiles: int, N: int):
     return order[:M], prims[:total.value], seg
 
 
+def lf_filter_planes(planes: Planes, sigma: float, radius: int = 0, stream=None):
+    """Sec. 4.5 low-pass plane filter (separable Gaussian, zero padding), in place."""
+    ps = planes.c_struct()
+    check(load().lf_filter_planes(ctypes.byref(ps), float(sigma), int(radius), _stream_ptr(stream)))
+
+
 # ---------------------------------------------------------------------------
 # composite
 # ---------------------------------------------------------------------------
@@ -337,13 +343,14 @@ class LightFieldRenderer:
     runs splat + composite through the C ABI."""
 
     def __init__(self, camera, display, views, N: int, binning: str = "quantile", dtype: str = "f32",
-                 n_capacity: int = 0, dup_capacity: int = 0, device="cuda"):
+                 n_capacity: int = 0, dup_capacity: int = 0, device="cuda", plane_filter: float = 0.0):
         self.camera, self.display, self.views = camera, display, views
         self.N, self.binning, self.dtype = int(N), binning, dtype
         self.ref = lf_make_ref_camera(camera, display)
         self.device = device
         self.n_capacity = int(n_capacity)
         self.dup_capacity = int(dup_capacity)
+        self.plane_filter = float(plane_filter)   # V2LF low-pass sigma (plane pixels); 0 = off
         self.planes = None
         self.ws = None
         self.cws = alloc_workspace(lf_composite_workspace_size(self.N, views), device)
@@ -366,6 +373,8 @@ class LightFieldRenderer:
             lf_build_mpi_gaussians(prims, self.ref, self.N, self.binning, self.ws, view, stream)
         else:
             lf_build_mpi_voxels(prims, self.ref, self.N, self.binning, self.ws, view, stream)
+            if self.plane_filter > 0.0:
+                lf_filter_planes(view, self.plane_filter, 0, stream)
         return view
 
     def composite(self, stream=None, out: Optional[torch.Tensor] = None):

@@ -621,6 +621,30 @@ lf_status lf_mpi_tile_lists(const void* ws, int32_t* order, int64_t n, int32_t* 
     return LF_OK;
 }
 
+lf_status lf_filter_planes(const lf_planes* planes, double sigma, int32_t radius, cudaStream_t stream)
+{
+    if (!planes || !planes->rgba) return fail(LF_ERR_INVALID_ARG, "planes is NULL");
+    if (planes->N < 1 || planes->W < 1 || planes->H < 1) return fail(LF_ERR_INVALID_ARG, "empty plane array");
+    if (planes->dtype < LF_F32 || planes->dtype > LF_U8) return fail(LF_ERR_INVALID_ARG, "unknown plane dtype");
+    if (!(sigma > 0.0)) return fail(LF_ERR_INVALID_ARG, "filter sigma must be positive");
+    if (radius <= 0) radius = (int32_t)std::ceil(3.0 * sigma);
+    if (radius > kFilterMaxRadius) return fail(LF_ERR_INVALID_ARG, "filter radius above 16");
+    FilterParams f;
+    std::memset(&f, 0, sizeof(f));
+    f.radius = radius;
+    // normalised FP64 Gaussian weights, rounded once to FP32
+    double w[2 * kFilterMaxRadius + 1], sum = 0.0;
+    for (int i = -radius; i <= radius; ++i) {
+        w[i + radius] = std::exp(-0.5 * (double)i * (double)i / (sigma * sigma));
+        sum += w[i + radius];
+    }
+    for (int i = 0; i <= 2 * radius; ++i) f.w[i] = (float)(w[i] / sum);
+    trace_begin("plane_filter", stream);
+    launch_filter_planes(planes->rgba, planes->dtype, planes->N, planes->W, planes->H, f, stream);
+    trace_end(stream);
+    return check_launch("plane filter");
+}
+
 size_t lf_composite_workspace_size(int32_t N, const lf_view_set* views)
 {
     if (!views || N < 1 || views->Vx < 1 || views->Vy < 1) return 0;

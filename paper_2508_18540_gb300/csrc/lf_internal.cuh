@@ -180,6 +180,14 @@ lf_status build_gaussians_prefix(const lf_gaussians* g, const lf_ref_camera* ref
                                  const uint32_t** ranks);
 void raster_params(const lf_ref_camera* ref, int32_t N, int32_t dtype, RasterParams* p);
 
+// ---- V2LF low-pass plane filter ------------------------------------------
+constexpr int kFilterMaxRadius = 16;
+struct FilterParams {
+    int radius;
+    float w[2 * kFilterMaxRadius + 1];   // normalised weights of offsets -radius..radius
+};
+void launch_filter_planes(void* planes, int dtype, int N, int W, int H, const FilterParams& f, cudaStream_t s);
+
 // ---- composite ----------------------------------------------------------
 struct CompWs {
     float* cx;      // [Vx][N][3] (gm, hn, hb) along x

@@ -224,3 +224,41 @@ def test_u8_planes(orc, bilinear):
     assert np.abs(gpu["views"] - v_own).max() <= 1e-4
     for k in range(gpu["views"].shape[0]):
         assert G.psnr(gpu["views"][k], o["views"][k]) >= 40.0
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", 2e-6), ("f16", 2e-3)])
+def test_plane_filter_against_oracle(orc, dtype, tol):
+    # the V2LF low-pass filter in place on the GPU planes against the FP64
+    # filter of the same unfiltered planes; ragged width (not a multiple of
+    # the row segment or the column block), several radii
+    from paper_2508_18540_gb300 import api
+    cam = S.identity_camera(72, t=(0.0, 0.0, 6.0))
+    cam.Nx = 1100     # a row longer than one 1024-texel segment
+    vs = S.sparse_voxels(3000, 9, base_res=32)
+    disp = S.display_for(S.harmonic_focal(4.0, 8.0), 0.15)
+    r = api.LightFieldRenderer(cam, disp, S.ViewSet(3), 5, "quantile", dtype)
+    v = api.DeviceVoxels.from_scene(vs)
+    for sigma, radius in ((0.8, 0), (1.7, 5), (3.0, 16)):
+        pl = r.build(v)
+        torch.cuda.synchronize()
+        before = pl.rgba.float().cpu().numpy().astype(np.float64)
+        api.lf_filter_planes(pl, sigma, radius)
+        torch.cuda.synchronize()
+        after = pl.rgba.float().cpu().numpy().astype(np.float64)
+        rad = radius if radius > 0 else int(np.ceil(3 * sigma))
+        want = orc.filter_planes(before, sigma, rad)
+        assert np.abs(after - want).max() <= tol, (sigma, radius)
+
+
+def test_v2lf_with_plane_filter_end_to_end(orc):
+    from paper_2508_18540_gb300 import api
+    cam = S.identity_camera(64, t=(0.0, 0.0, 6.0))
+    vs = S.sparse_voxels(2500, 10, base_res=32)
+    disp = S.display_for(S.harmonic_focal(4.0, 8.0), 0.15)
+    views = S.ViewSet(5)
+    r = api.LightFieldRenderer(cam, disp, views, 6, "quantile", "f32", plane_filter=0.7)
+    out = r.render(api.DeviceVoxels.from_scene(vs)).cpu().numpy().astype(np.float64)
+    o = orc.render(scene=vs, camera=cam, display=disp, views=views, N=6, binning="quantile")
+    planes = orc.filter_planes(o["planes"], 0.7, 3)
+    want = orc.composite(o["ref"], planes, o["d"], o["count"], 5, 1, False)
+    assert np.abs(out - want).max() <= 1e-4
