@@ -482,6 +482,18 @@ __device__ __forceinline__ void blend_plane(float (&acc)[VG][4], float4 hdr, uin
     }
 }
 
+// Every view of this thread has T == 0 exactly (or the thread is idle).
+// T never leaves 0 (T <- T - T A), and behind it a plane adds T c = 0 to Q
+// and leaves T = 0, so skipping such planes changes no bit of the output.
+template <int VG>
+__device__ __forceinline__ bool saturated(const float (&acc)[VG][4], bool live)
+{
+    bool s = true;
+#pragma unroll
+    for (int jj = 0; jj < VG; ++jj) s = s && acc[jj][3] == 0.0f;
+    return s || !live;
+}
+
 // Stages the plane rows that list entry q (plane k = plist[q], coefficient
 // block c) needs for output rows Y0 .. Y0 + BY - 1 into stage sb, with their
 // byte count announced on mbarrier bar (one producer thread).
@@ -641,6 +653,7 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
     const bool live = ty < G.BY && x < p.Nx && y < p.Ny;   // threads past BY rows idle
     const ThreadGeom tg = thread_geom(p, G, x, y, ty);
     bool ok = true;
+    bool warp_sat = false;   // every view of every lane of this warp has T == 0
 
     for (int q = 0; q < P; ++q) {
         const int s = q % kStages;
@@ -650,7 +663,8 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
             ok = false;
             break;
         }
-        if (live) {
+        if ((q & 3) == 0 && q > 0 && !warp_sat) warp_sat = __all_sync(0xffffffffu, saturated<VG>(acc, live));
+        if (live && !warp_sat) {
             const uint32_t ca = coef_a + 4u * (uint32_t)(q * CW);
             const uint32_t sb = stage_a + (uint32_t)(s * G.stage_bytes);
             const float4 hdr = lds_f4(ca);
@@ -773,6 +787,7 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_batched(const Com
 #pragma unroll
             for (int jj = 0; jj < VG; ++jj) acc[jj][0] = acc[jj][1] = acc[jj][2] = 0.f, acc[jj][3] = 1.f;
             bool ok = true;
+            bool warp_sat = false;
             int st = st0;
             uint32_t ph = ph0;
             const uint32_t stage_stride = (uint32_t)max_stage_bytes;
@@ -783,7 +798,9 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_batched(const Com
                     ok = false;
                     break;
                 }
-                if (live) {
+                if ((q & 3) == 0 && q > 0 && !warp_sat)
+                    warp_sat = __all_sync(0xffffffffu, saturated<VG>(acc, live));
+                if (live && !warp_sat) {
                     const uint32_t ca = coef_a + 4u * (uint32_t)(q * CW);
                     const uint32_t sb = stage_a + (uint32_t)st * stage_stride;
                     const float4 hdr = lds_f4(ca);
