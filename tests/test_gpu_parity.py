@@ -262,3 +262,15 @@ def test_v2lf_with_plane_filter_end_to_end(orc):
     planes = orc.filter_planes(o["planes"], 0.7, 3)
     want = orc.composite(o["ref"], planes, o["d"], o["count"], 5, 1, False)
     assert np.abs(out - want).max() <= 1e-4
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_display_scale_workload(orc, dtype):
+    # the benchmark's own workload and launch configuration (1M Gaussians,
+    # 512^2, N = 64, 45 views): culling, rectangles, depth order, chunks and
+    # plane depths bit-exact; planes and all views within the tolerance
+    # (the 16x16 tile lists are checked at the smaller sizes above)
+    w = S.workload_display()
+    o = orc.render(w)
+    gpu = G.run_gpu(w.scene, w.camera, w.display, w.views, w.N, w.binning, dtype)
+    _compare(gpu, o, o["ref"].W, o["ref"].H, w.N, dtype, check_lists=False)
