@@ -19,7 +19,7 @@ constexpr int kTile = 16;                 // raster tile edge (pixels): one CTA 
 constexpr int kTilePix = kTile * kTile;
 constexpr int kSuper = 32;                // list super-tile edge (pixels): lists per (super-tile, chunk)
 constexpr int kTilesPerSuper = kSuper / kTile;
-constexpr int kRadixBlockKeys = 4096;     // keys per radix-sort block
+constexpr int kRadixBlockKeys = 2048;     // keys per radix-sort block
 constexpr int kSortDigits = 256;          // 8-bit radix digits
 constexpr int kDupBlock = 1024;           // ranks per block of the tile-pair emission
 constexpr uint64_t kInvalidKey = ~0ull;

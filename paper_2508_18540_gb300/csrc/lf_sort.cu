@@ -18,7 +18,7 @@
 //    pair emitted in rank order; the stable sort groups the pairs by tile and
 //    keeps each tile's pairs in depth order.
 //
-// Each pass is reduce-then-scan over blocks of 4096 keys:
+// Each pass is reduce-then-scan over blocks of 2048 keys:
 //   k_upsweep   per-block digit histogram (warp-aggregated shared atomics);
 //   k_rowscan   one CTA per digit scans that digit's per-block counts;
 //   k_downsweep ranks the block's keys stably (ballot-based digit matching,
