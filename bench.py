@@ -182,17 +182,39 @@ def run_ours(args):
     clocks = ClockSampler(local)
     for dtype in ("f32", "f16", "bf16", "u8"):
         r = api.LightFieldRenderer(wl.camera, wl.display, wl.views, wl.N, wl.binning, dtype, device=dev)
-        if dtype == "f32":
-            clocks.start()
         ms, launches, stages = timed(r, args.steps, args.warmup, trace=True)
-        if dtype == "f32":
-            clk = clocks.stop()
         res[dtype] = dict(ms=ms, launches=launches, stages=stages, renderer=r)
         if rank == 0 and world == 1:
             res[dtype]["views_host"] = r.out.cpu().numpy()
 
-    # end to end through the public API with host buffers (pinned), f32 planes
+    # the same frames captured once into a CUDA graph and replayed (no launch
+    # gaps between the frame's kernels); same timing rules
+    def timed_graph(rr, steps, warmup):
+        for _ in range(warmup):
+            rr.replay()
+        barrier()
+        evg = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evg:
+            flush.zero_()
+            a.record(stream)
+            rr.replay()
+            b.record(stream)
+        barrier()
+        t = torch.tensor([sum(a.elapsed_time(b) for a, b in evg) / steps], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     r32 = res["f32"]["renderer"]
+    graph_kernels = r32.capture(g)
+    clocks.start()
+    g_ms = timed_graph(r32, args.steps, args.warmup)
+    clk = clocks.stop()
+    for d in ("f16", "bf16", "u8"):
+        res[d]["renderer"].capture(g)
+        res[d]["graph_ms"] = timed_graph(res[d]["renderer"], args.steps, args.warmup)
+
+    # end to end through the public API with host buffers (pinned), f32 planes
     host_in = api.DeviceGaussians.from_scene(wl.scene, pin=True)
     host_out = torch.empty(r32.out.shape, dtype=torch.float32, pin_memory=True)
     h2d = sum(t.numel() * t.element_size() for t in (host_in.means, host_in.scales, host_in.quats,
@@ -261,24 +283,29 @@ def run_ours(args):
 
     line = None
     if rank == 0:
-        fps = 1000.0 / res["f32"]["ms"] * world
+        # the frame as a render loop runs it: one CUDA-graph replay per frame
+        fps = 1000.0 / g_ms * world
         line = {
             "metric": METRIC, "value": round(fps, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(res["f32"]["ms"], 4), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": round(g_ms, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config({"planes": "f32", "parallelism": "replicas" if world > 1 else "single"}),
+            "config": _config({"planes": "f32", "parallelism": "replicas" if world > 1 else "single",
+                               "launch": "one CUDA-graph replay per frame (%d kernels)" % graph_kernels}),
             "views_per_s": round(fps * WORKLOAD["V"], 1),
-            "variants": {d: {"planes": d, "value": round(1000.0 / res[d]["ms"] * world, 2),
-                             "ms_per_step": round(res[d]["ms"], 4), "roofline": roofs[d]}
+            "plain_launches": {"value": round(1000.0 / res["f32"]["ms"] * world, 2),
+                               "ms_per_step": round(res["f32"]["ms"], 4)},
+            "variants": {d: {"planes": d, "value": round(1000.0 / res[d]["graph_ms"] * world, 2),
+                             "ms_per_step": round(res[d]["graph_ms"], 4),
+                             "plain_launches_value": round(1000.0 / res[d]["ms"] * world, 2), "roofline": roofs[d]}
                          for d in ("f16", "bf16", "u8")},
             "stages_ms": {d: {k: round(v[0] / v[1], 4) for k, v in res[d]["stages"].items()} for d in res},
             "e2e": {"value": round(1000.0 / e_ms * world, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e_ms, 4),
                     "api": "HostPipeline.submit (pinned host Gaussians in, pinned host views out, "
-                           "copies overlapped with neighbouring frames)",
+                           "copies overlapped with neighbouring frames, one CUDA-graph replay per frame)",
                     "l2": "not flushed between steps: each step streams > 0.7 GB (planes, views, workspace) "
                           "through the 129 MB L2"},
-            "gpu_launches": res["f32"]["launches"] * args.steps,
+            "gpu_launches": graph_kernels * args.steps,
             "roofline": dict(primary, kernel=dom if dom in roofs["f32"] else "composite") if primary else None,
             "roofline_by_kernel": roofs["f32"],
             "clocks": clk,

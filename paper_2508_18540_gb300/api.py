@@ -389,6 +389,27 @@ class LightFieldRenderer:
     def status(self):
         return lf_mpi_status(self.ws)
 
+    def capture(self, prims):
+        """Captures one render of prims (build + composite, every kernel of the
+        frame) into a CUDA graph; replay() then re-runs it on the current
+        contents of the prims' and renderer's buffers. Stage tracing is turned
+        off for this thread. Returns the number of kernels in the graph."""
+        self._ensure(prims.n)
+        self.render(prims)                      # warm: workspace and kernel attributes set up
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        lf_trace_enable(False)
+        k0 = lf_launch_count()
+        with torch.cuda.graph(g):
+            self.render(prims, torch.cuda.current_stream())
+        self.graph_kernels = lf_launch_count() - k0
+        self.graph = g
+        return self.graph_kernels
+
+    def replay(self):
+        self.graph.replay()
+        return self.out
+
     def planes_view(self, n: int) -> Planes:
         pl = self.planes
         return Planes(pl.rgba, pl.d, pl.count, pl.chunk[: max(n, 1)], pl.rect[: max(n, 1)], pl.dtype_code)
@@ -420,17 +441,34 @@ class HostPipeline:
     or i is computed, ordered by CUDA events. submit() returns the event that
     marks frame i's views in host memory."""
 
-    def __init__(self, renderer: "LightFieldRenderer", n: int, device="cuda"):
+    def __init__(self, renderer: "LightFieldRenderer", n: int, device="cuda", graphs: bool = True):
         self.r = renderer
         f = dict(dtype=torch.float32, device=device)
-        self.slots = [DeviceGaussians(torch.empty((n, 3), **f), torch.empty((n, 3), **f), torch.empty((n, 4), **f),
-                                      torch.empty((n,), **f), torch.empty((n, 3), **f)) for _ in range(2)]
+        # zero Gaussians sit at the world origin, in front of no reference camera
+        # that sees them from z_near on, so warm-up and capture renders cull them
+        self.slots = [DeviceGaussians(torch.zeros((n, 3), **f), torch.zeros((n, 3), **f), torch.zeros((n, 4), **f),
+                                      torch.zeros((n,), **f), torch.zeros((n, 3), **f)) for _ in range(2)]
         self.outs = [torch.empty_like(renderer.out) for _ in range(2)]
         self.s_in, self.s_comp, self.s_out = (torch.cuda.Stream(device=device) for _ in range(3))
         E = torch.cuda.Event
         self.in_ready, self.in_free = [E(), E()], [E(), E()]
         self.out_ready, self.out_free = [E(), E()], [E(), E()]
         self.i = 0
+        # one CUDA graph per slot: build from slot k, composite into view slot k
+        self.graphs = None
+        if graphs:
+            self.graphs = []
+            for k in range(2):
+                renderer.build(self.slots[k])
+                renderer.composite(out=self.outs[k])
+                torch.cuda.synchronize()
+                gk = torch.cuda.CUDAGraph()
+                lf_trace_enable(False)
+                with torch.cuda.graph(gk):
+                    st = torch.cuda.current_stream()
+                    renderer.build(self.slots[k], st)
+                    renderer.composite(st, out=self.outs[k])
+                self.graphs.append(gk)
 
     def submit(self, host: DeviceGaussians, host_out: torch.Tensor) -> torch.cuda.Event:
         k = self.i % 2
@@ -443,8 +481,12 @@ class HostPipeline:
         self.in_ready[k].record(self.s_in)
         self.s_comp.wait_event(self.in_ready[k])
         self.s_comp.wait_event(self.out_free[k])       # frame i-2's views have left this slot
-        self.r.build(dev, self.s_comp)
-        self.r.composite(self.s_comp, out=self.outs[k])
+        if self.graphs is not None:
+            with torch.cuda.stream(self.s_comp):
+                self.graphs[k].replay()
+        else:
+            self.r.build(dev, self.s_comp)
+            self.r.composite(self.s_comp, out=self.outs[k])
         self.in_free[k].record(self.s_comp)
         self.out_ready[k].record(self.s_comp)
         self.s_out.wait_event(self.out_ready[k])

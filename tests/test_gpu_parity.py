@@ -151,14 +151,15 @@ def test_voxels_rotated(orc):
     _compare(gpu, o, o["ref"].W, o["ref"].H, 6, "f32")
 
 
-def test_host_pipeline_frames_match_synchronous_renders():
+@pytest.mark.parametrize("graphs", [True, False])
+def test_host_pipeline_frames_match_synchronous_renders(graphs):
     # api.HostPipeline overlaps copies with compute across frames; every
     # frame's host views must equal a plain synchronous render of its input
     from paper_2508_18540_gb300 import api
     w = S.workload_tiny()
     scenes = [w.scene, S.perturbed(w.scene, 3), S.perturbed(w.scene, 4), S.perturbed(w.scene, 5)]
     r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f32")
-    pipe = api.HostPipeline(r, w.scene.n)
+    pipe = api.HostPipeline(r, w.scene.n, graphs=graphs)
     outs, evs = [], []
     hosts = [api.DeviceGaussians.from_scene(sc, pin=True) for sc in scenes]
     for h in hosts:
@@ -274,3 +275,26 @@ def test_display_scale_workload(orc, dtype):
     o = orc.render(w)
     gpu = G.run_gpu(w.scene, w.camera, w.display, w.views, w.N, w.binning, dtype)
     _compare(gpu, o, o["ref"].W, o["ref"].H, w.N, dtype, check_lists=False)
+
+
+def test_renderer_graph_replay():
+    # one CUDA graph per frame: replays equal a plain render, and read the
+    # scene buffers in place (new colours show up in the next replay)
+    from paper_2508_18540_gb300 import api
+    w = S.workload_tiny()
+    r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f32")
+    g = api.DeviceGaussians.from_scene(w.scene)
+    want = r.render(g).clone()
+    kernels = r.capture(g)
+    assert kernels > 10
+    r.out.fill_(float("nan"))
+    got = r.replay().clone()
+    torch.cuda.synchronize()
+    assert torch.equal(got, want)
+    with torch.no_grad():
+        g.rgb.mul_(0.5)
+    got2 = r.replay().clone()
+    ref = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f32")
+    want2 = ref.render(g).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(got2, want2)
