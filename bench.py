@@ -49,8 +49,8 @@ def _config(extra=None):
 # (profiles/k_*_g2lf_display_1M_512px_N64_45v.md), valid only while the
 # kernel's sources hash to the value recorded with them.
 NCU_TRAFFIC = {
-    "raster_gaussians": (71_790_080 + 210_722_304, ("lf_raster.cu", "lf_internal.cuh"), "6bd28c7a4f40c853"),
-    "composite": (253_049_600 + 154_599_168, ("lf_composite.cu", "lf_internal.cuh"), "8072b1463550b3db"),
+    "raster_gaussians": (71_813_120 + 210_758_144, ("lf_raster.cu", "lf_internal.cuh"), "934a46caca68d149"),
+    "composite": (253_724_160 + 157_447_424, ("lf_composite.cu", "lf_internal.cuh"), "578019e2eb58df9d"),
 }
 
 

@@ -324,18 +324,41 @@ constexpr int kLongRunCtas = 304;
 constexpr int kLongRunThreads = 1024;
 constexpr int kSmemRun = 2048;
 
-// Runs of equal truncated keys: up to kShortRun sorted here by the thread
-// at the run start; longer ones listed (start, length) in tkeyB.
-__global__ void __launch_bounds__(256) k_depth_runs(BuildWs w)
+// Within a run of equal truncated keys the ranks are in index order (the
+// sort is stable), so the run is already in (full key, index) order unless
+// some neighbour pair has a larger full key first. One flag per rank marks
+// such pairs (bytes over keyB, free at this point).
+__global__ void __launch_bounds__(256) k_depth_bad(BuildWs w)
 {
     const long long M = (long long)w.hdr->M;
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= M) return;
+    uint8_t b = 0;
+    if (r > 0 && w.tkeyA[r] == w.tkeyA[r - 1]) b = w.keyA[w.valA[r - 1]] > w.keyA[w.valA[r]] ? 1 : 0;
+    reinterpret_cast<uint8_t*>(w.keyB)[r] = b;
+}
+
+// Runs of equal truncated keys that hold an out-of-order pair. Work starts
+// at flagged ranks only: a flagged rank walks back to its run's start and
+// leaves if it meets an earlier flag (that one owns the run), so every run
+// is owned once and walked once. The owner finds the run's end, sorts a run
+// of up to kShortRun keys itself and lists longer ones (start, length) in
+// tkeyB. Runs with no flag (equal keys, e.g. primitives on one grid layer)
+// cost nothing.
+__global__ void __launch_bounds__(256) k_depth_runs(BuildWs w)
+{
+    const long long M = (long long)w.hdr->M;
+    const long long r0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint8_t* bad = reinterpret_cast<const uint8_t*>(w.keyB);
+    if (r0 >= M || !bad[r0]) return;
     const uint32_t* k = w.tkeyA;
-    const uint32_t kr = k[r];
-    if (r > 0 && k[r - 1] == kr) return;          // not the start of a run
-    if (r + 1 >= M || k[r + 1] != kr) return;     // a run of one
-    long long e = r + 2;
+    const uint32_t kr = k[r0];
+    long long r = r0 - 1;                         // candidate run start
+    while (r > 0 && k[r - 1] == kr) {
+        if (bad[r]) return;                       // an earlier flag owns this run
+        --r;
+    }
+    long long e = r0 + 1;
     while (e < M && k[e] == kr) ++e;
     const int L = (int)min(e - r, (long long)0x7fffffff);
     if (L > kShortRun) {
@@ -463,9 +486,10 @@ void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s)
         cur ^= 1;
     }
     // four passes: truncated keys in tkeyA, ranks in valA; now the runs
+    k_depth_bad<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws);
     k_depth_runs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws);
     k_depth_long_runs<<<kLongRunCtas, kLongRunThreads, 0, s>>>(ws);
-    note_launches(3);
+    note_launches(4);
 }
 
 int tile_sort_passes(int tile_bits) { return (tile_bits + kBits - 1) / kBits; }
