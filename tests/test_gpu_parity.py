@@ -298,3 +298,18 @@ def test_renderer_graph_replay():
     want2 = ref.render(g).clone()
     torch.cuda.synchronize()
     assert torch.equal(got2, want2)
+
+
+@pytest.mark.parametrize("dtype,Nx,Ny,bilinear", [("f16", 99, 37, False), ("f16", 99, 37, True),
+                                                  ("f32", 2560, 24, False), ("bf16", 2561, 20, True)])
+def test_unstaged_composite_fallback(orc, dtype, Nx, Ny, bilinear):
+    # plane rows the staged kernel cannot take (an FP16 row that is not a
+    # multiple of 16 bytes; rows too wide for the shared-memory ring) go
+    # through the L1-cached kernel; same bar as the other parity tests
+    cam = S.Camera(np.eye(3), np.zeros(3), np.radians(50.0), np.radians(20.0), Nx, Ny)
+    sc = S.uniform_gaussians(4000, 31, xy=(-1.5, 1.5), z=(2.0, 6.0))
+    views = S.ViewSet(7, 1, bilinear, (0.1, 0.2, 0.3))
+    disp = S.display_for(3.0, 0.1)
+    o = orc.render(scene=sc, camera=cam, display=disp, views=views, N=6, binning="quantile")
+    gpu = G.run_gpu(sc, cam, disp, views, 6, "quantile", dtype)
+    _compare(gpu, o, o["ref"].W, o["ref"].H, 6, dtype, check_lists=False)
