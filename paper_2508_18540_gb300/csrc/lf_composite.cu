@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
 {
     extern __shared__ float s_coef[];  // [N][6]: x (gm, hn, hb), y (gm, hn, hb); count in [N] ints after
     int* s_cnt = reinterpret_cast<int*>(s_coef + 6 * p.N);
-    const int v = blockIdx.z;
+    const int v = blockIdx.x;   // fastest: the views of one pixel tile share plane rows in L2
     const int i = v / p.Vx, j = v % p.Vx;
     const int tid = threadIdx.y * kCompBX + threadIdx.x;
     for (int k = tid; k < p.N; k += kCompBX * kCompBY) {
@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
         s_cnt[k] = count[k];
     }
     __syncthreads();
-    const int x = blockIdx.x * kCompBX + threadIdx.x;
-    const int y = blockIdx.y * kCompBY + threadIdx.y;
+    const int x = blockIdx.y * kCompBX + threadIdx.x;
+    const int y = blockIdx.z * kCompBY + threadIdx.y;
     if (x >= p.Nx || y >= p.Ny) return;
     const size_t plane_sz = (size_t)p.W * p.H;
     float Q0 = 0.f, Q1 = 0.f, Q2 = 0.f, T = 1.f;
@@ -876,8 +876,8 @@ void launch_composite_t(const CompParams& p, const void* planes, const int32_t* 
         if (ok) return;
     }
     const dim3 block(kCompBX, kCompBY);
-    const dim3 grid((unsigned)((p.Nx + kCompBX - 1) / kCompBX), (unsigned)((p.Ny + kCompBY - 1) / kCompBY),
-                    (unsigned)(p.Vx * p.Vy));
+    const dim3 grid((unsigned)(p.Vx * p.Vy), (unsigned)((p.Nx + kCompBX - 1) / kCompBX),
+                    (unsigned)((p.Ny + kCompBY - 1) / kCompBY));
     const size_t smem = sizeof(float) * 6 * p.N + sizeof(int) * p.N;
     if (p.bilinear) {
         if (smem > 48 * 1024)
@@ -920,7 +920,7 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite_bwd(CompParams p
 {
     extern __shared__ float s_coef[];  // as k_composite
     int* s_cnt = reinterpret_cast<int*>(s_coef + 6 * p.N);
-    const int v = blockIdx.z;
+    const int v = blockIdx.x;   // fastest: the views of one pixel tile share plane rows in L2
     const int i = v / p.Vx, j = v % p.Vx;
     const int tid = threadIdx.y * kCompBX + threadIdx.x;
     for (int k = tid; k < p.N; k += kCompBX * kCompBY) {
@@ -935,8 +935,8 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite_bwd(CompParams p
         s_cnt[k] = count[k];
     }
     __syncthreads();
-    const int x = blockIdx.x * kCompBX + threadIdx.x;
-    const int y = blockIdx.y * kCompBY + threadIdx.y;
+    const int x = blockIdx.y * kCompBX + threadIdx.x;
+    const int y = blockIdx.z * kCompBY + threadIdx.y;
     if (x >= p.Nx || y >= p.Ny) return;
     const size_t plane_sz = (size_t)p.W * p.H;
 
@@ -1041,8 +1041,8 @@ void launch_composite_bwd_t(const CompParams& p, const void* planes, const int32
                             const float* dviews, float* dplanes, cudaStream_t s)
 {
     const dim3 block(kCompBX, kCompBY);
-    const dim3 grid((unsigned)((p.Nx + kCompBX - 1) / kCompBX), (unsigned)((p.Ny + kCompBY - 1) / kCompBY),
-                    (unsigned)(p.Vx * p.Vy));
+    const dim3 grid((unsigned)(p.Vx * p.Vy), (unsigned)((p.Nx + kCompBX - 1) / kCompBX),
+                    (unsigned)((p.Ny + kCompBY - 1) / kCompBY));
     const size_t smem = sizeof(float) * 6 * p.N + sizeof(int) * p.N;
     const float4* dv = reinterpret_cast<const float4*>(dviews);
     float4* dp = reinterpret_cast<float4*>(dplanes);
