@@ -105,8 +105,15 @@ __global__ void __launch_bounds__(1024) k_dup_scan(BuildWs w, int nb)
     }
 }
 
+// The block's pairs are written to shared memory at their block-local
+// offsets and copied out contiguously (coalesced); a block with more pairs
+// than the staging area writes them directly.
+constexpr int kEmitStage = 4096;
+
 __global__ void __launch_bounds__(kT) k_dup_emit(BuildWs w, int supers_x)
 {
+    __shared__ uint32_t s_key[kEmitStage];
+    __shared__ uint32_t s_rank[kEmitStage];
     if (w.hdr->overflow) return;
     const long long M = (long long)w.hdr->M;
     const long long r0 = (long long)blockIdx.x * kDupBlock + (long long)threadIdx.x * kPer;
@@ -117,39 +124,76 @@ __global__ void __launch_bounds__(kT) k_dup_emit(BuildWs w, int supers_x)
         rc[j] = r0 + j < M ? w.r_rect[r0 + j] : make_int4(0, 0, -1, -1);
         sum += tile_count(rc[j]);
     }
-    uint32_t off = w.bsum[blockIdx.x] + block_exscan256(sum, nullptr);
+    uint32_t total;
+    const uint32_t local = block_exscan256(sum, &total);
+    const uint32_t base = w.bsum[blockIdx.x];
+    const bool staged = total <= (uint32_t)kEmitStage;
+    uint32_t off = local;
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         if (rc[j].z < rc[j].x || rc[j].w < rc[j].y) continue;
         const int sx0 = rc[j].x / kSuper, sx1 = rc[j].z / kSuper, sy0 = rc[j].y / kSuper, sy1 = rc[j].w / kSuper;
         for (int sy = sy0; sy <= sy1; ++sy)
             for (int sx = sx0; sx <= sx1; ++sx) {
-                w.tkeyA[off] = (uint32_t)(sy * supers_x + sx);
-                w.entA[off] = (uint32_t)(r0 + j);
+                const uint32_t key = (uint32_t)(sy * supers_x + sx), rank = (uint32_t)(r0 + j);
+                if (staged) {
+                    s_key[off] = key;
+                    s_rank[off] = rank;
+                } else {
+                    w.tkeyA[base + off] = key;
+                    w.entA[base + off] = rank;
+                }
                 ++off;
             }
     }
+    if (!staged) return;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < total; i += kT) {
+        w.tkeyA[base + i] = s_key[i];
+        w.entA[base + i] = s_rank[i];
+    }
 }
 
-__device__ __forceinline__ void range_one(const BuildWs& w, const uint32_t* __restrict__ keys,
-                                          const uint32_t* __restrict__ ranks, int N, long long n, long long i)
+// chunk of a rank: the last chunk whose first rank is not above it (binary
+// search over the N chunk starts, which stay in L1)
+__device__ __forceinline__ int chunk_of(const int* __restrict__ start, int N, uint32_t rank)
 {
-    const uint32_t t = keys[i];
-    const int c = w.r_chunk[ranks[i]];
-    const long long sidx = (long long)t * N + c;
-    bool first = i == 0, last = i == n - 1;
-    if (!first) first = keys[i - 1] != t || w.r_chunk[ranks[i - 1]] != c;
-    if (!last) last = keys[i + 1] != t || w.r_chunk[ranks[i + 1]] != c;
-    if (first) w.seg[sidx].x = (int)i;
-    if (last) w.seg[sidx].y = (int)(i + 1);
+    int lo = 0, hi = N - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((uint32_t)__ldg(start + mid) <= rank)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
 }
 
+// Entry i starts a (super-tile, chunk) list when its super-tile or chunk
+// differs from entry i - 1's; it then also ends the list of entry i - 1.
 __global__ void __launch_bounds__(256) k_ranges(BuildWs w, const uint32_t* __restrict__ keys,
                                                 const uint32_t* __restrict__ ranks, int N)
 {
+    const int* s_start = w.chunk_start;
     const long long n = (long long)w.hdr->tile_n;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        range_one(w, keys, ranks, N, n, i);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t t = keys[i];
+        const int c = chunk_of(s_start, N, ranks[i]);
+        bool first = i == 0;
+        long long pidx = -1;
+        if (!first) {
+            const uint32_t tp = keys[i - 1];
+            const int cp = chunk_of(s_start, N, ranks[i - 1]);
+            first = tp != t || cp != c;
+            pidx = (long long)tp * N + cp;
+        }
+        if (first) {
+            w.seg[(long long)t * N + c].x = (int)i;
+            if (pidx >= 0) w.seg[pidx].y = (int)i;
+        }
+        if (i == n - 1) w.seg[(long long)t * N + c].y = (int)n;
+    }
 }
 
 }  // namespace
