@@ -323,6 +323,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         line["batched"] = run_batched(args, dev)
         torch.cuda.empty_cache()
+        line["sweeps"] = run_sweeps(args, dev)
+        torch.cuda.empty_cache()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -448,6 +450,45 @@ def run_batched(args, dev):
             "graph_ms_per_frame": round(g_ms, 3), "batch_frames_per_s": round(1000.0 / g_ms, 2),
             "views_per_s": round(views * 1000.0 / g_ms, 1), "kernels_per_frame": int(launches),
             "one_by_one_ms_per_frame": round(s_ms, 3)}
+
+
+def run_sweeps(args, dev):
+    """Speed sweeps on the 1M-Gaussian display scene (the paper's scenes and
+    trained models are not available): LF frames/s and views/s against the
+    number of views (the paper's real-time-beyond-90-views claim), and over
+    N_chunk x P_s x sampling (its Table 1 axes), FP32 and FP16 planes, one
+    CUDA-graph replay per frame, L2 flushed between frames."""
+    import torch
+    from paper_2508_18540_gb300 import api
+    from paper_2508_18540_gb300 import synth as S
+    wl = S.workload_display(seed=WORKLOAD["seed"])
+    g = api.DeviceGaussians.from_scene(wl.scene, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+    steps, warm = max(5, args.steps // 2), 3
+
+    def fps(display, views, N, dtype):
+        r = api.LightFieldRenderer(wl.camera, display, views, N, wl.binning, dtype, device=dev)
+        r.capture(g)
+        ms = _event_ms(r.replay, steps, warm, st, flush)
+        out = {"value": round(1000.0 / ms, 2), "views_per_s": round(1000.0 / ms * views.Vx * views.Vy, 1),
+               "ms_per_step": round(ms, 4)}
+        del r
+        return out
+
+    res = {"unit": UNIT, "views": {}, "table1": {}}
+    for V in (9, 45, 90, 180):
+        for dtype in ("f32", "f16"):
+            res["views"]["V%d_%s" % (V, dtype)] = fps(wl.display, S.ViewSet(V), 64, dtype)
+    for N in (16, 64, 256):
+        for Ps in (1, 2):
+            disp = S.display_for(wl.display.D_focal, 0.15, P_s=Ps)
+            for bil in (False, True):
+                for dtype in ("f32", "f16"):
+                    key = "N%d_Ps%d_%s_%s" % (N, Ps, "bilinear" if bil else "nearest", dtype)
+                    res["table1"][key] = fps(disp, S.ViewSet(45, 1, bil), N, dtype)
+    torch.cuda.empty_cache()
+    return res
 
 
 def view_errors(gpu_views, oracle_views):

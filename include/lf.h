@@ -159,11 +159,16 @@ typedef struct {
 
 /* Quilt views (Sec. 4.3): Vx x Vy views, view index i * Vx + j; nearest
  * (bilinear = 0, the paper's default) or bilinear sampling; background
- * colour bg under the remaining transmittance (0 in the paper). */
+ * colour bg under the remaining transmittance (0 in the paper).
+ * Output layout: atlas_cols = 0 gives separate views [V][Ny][Nx][4];
+ * atlas_cols = c > 0 gives one quilt atlas image [ceil(V/c) Ny][c Nx][4]
+ * with view v in tile (row v / c, column v % c), rows from the top (tiles
+ * past V are left untouched). The adjoint takes separate views only. */
 typedef struct {
     int32_t Vx, Vy;
     int32_t bilinear;
     float bg[3];
+    int32_t atlas_cols;
 } lf_view_set;
 
 /* ---- set-up ------------------------------------------------------------ */

@@ -71,7 +71,7 @@ class LfPlanes(ctypes.Structure):
 
 
 class LfViewSet(ctypes.Structure):
-    _fields_ = [("Vx", _I32), ("Vy", _I32), ("bilinear", _I32), ("bg", ctypes.c_float * 3)]
+    _fields_ = [("Vx", _I32), ("Vy", _I32), ("bilinear", _I32), ("bg", ctypes.c_float * 3), ("atlas_cols", _I32)]
 
 
 class LfBatchScene(ctypes.Structure):

@@ -163,7 +163,17 @@ def view_set(views) -> L.LfViewSet:
     vs = L.LfViewSet()
     vs.Vx, vs.Vy, vs.bilinear = int(views.Vx), int(views.Vy), int(bool(views.bilinear))
     vs.bg[:] = [float(c) for c in views.bg]
+    vs.atlas_cols = int(getattr(views, "atlas_cols", 0) or 0)
     return vs
+
+
+def views_shape(views, Nx: int, Ny: int):
+    """Output shape: separate views [V][Ny][Nx][4], or the quilt atlas."""
+    V = int(views.Vx) * int(views.Vy)
+    c = int(getattr(views, "atlas_cols", 0) or 0)
+    if c <= 0:
+        return (V, Ny, Nx, 4)
+    return ((V + c - 1) // c * Ny, c * Nx, 4)
 
 
 def alloc_workspace(nbytes: int, device="cuda") -> torch.Tensor:
@@ -240,7 +250,7 @@ def lf_composite_workspace_size(N: int, views) -> int:
 def lf_composite(planes: Planes, ref: L.LfRefCamera, views, out: torch.Tensor, ws: torch.Tensor, stream=None):
     """Sec. 4.3 swizzle blending into out [Vy*Vx][Ny][Nx][4] float32 (asynchronous)."""
     vs = view_set(views)
-    _need(out, (vs.Vx * vs.Vy, ref.base.Ny, ref.base.Nx, 4), torch.float32, "views")
+    _need(out, views_shape(views, ref.base.Nx, ref.base.Ny), torch.float32, "views")
     ps = planes.c_struct()
     check(load().lf_composite(ctypes.byref(ps), ctypes.byref(ref), ctypes.byref(vs), _ptr(out), _ptr(ws),
                               ws.numel(), _stream_ptr(stream)))
@@ -250,7 +260,7 @@ def lf_composite_noalloc(planes: Planes, ref: L.LfRefCamera, views, out: torch.T
     """lf_composite with the library's static scratch instead of a workspace
     (calls must not overlap in time)."""
     vs = view_set(views)
-    _need(out, (vs.Vx * vs.Vy, ref.base.Ny, ref.base.Nx, 4), torch.float32, "views")
+    _need(out, views_shape(views, ref.base.Nx, ref.base.Ny), torch.float32, "views")
     ps = planes.c_struct()
     check(load().lf_composite_noalloc(ctypes.byref(ps), ctypes.byref(ref), ctypes.byref(vs), _ptr(out),
                                       _stream_ptr(stream)))
@@ -354,7 +364,7 @@ class LightFieldRenderer:
         self.planes = None
         self.ws = None
         self.cws = alloc_workspace(lf_composite_workspace_size(self.N, views), device)
-        self.out = torch.empty((views.Vx * views.Vy, camera.Ny, camera.Nx, 4), dtype=torch.float32, device=device)
+        self.out = torch.empty(views_shape(views, camera.Nx, camera.Ny), dtype=torch.float32, device=device)
 
     def _ensure(self, n: int):
         if self.planes is None or n > self.n_capacity:

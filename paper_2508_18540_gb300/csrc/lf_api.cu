@@ -251,6 +251,7 @@ static void fill_comp_params(const lf_planes* planes, const lf_ref_camera* ref, 
     p.Vy = views->Vy;
     p.P_s = ref->disp.P_s;
     p.bilinear = views->bilinear ? 1 : 0;
+    p.atlas_cols = views->atlas_cols > 0 ? views->atlas_cols : 0;
     p.dtype = planes->dtype;
     for (int c = 0; c < 3; ++c) p.bg[c] = views->bg[c];
     p.D_focal = ref->disp.D_focal;
@@ -277,6 +278,7 @@ static lf_status check_composite_args(const lf_planes* planes, const lf_ref_came
     if (!planes->rgba || !planes->d || !planes->count) return fail(LF_ERR_INVALID_ARG, "plane pointer is NULL");
     if (views->Vx < 1 || views->Vy < 1 || views->Vx > 65535 || views->Vy > 65535)
         return fail(LF_ERR_INVALID_ARG, "view counts must be in 1..65535");
+    if (views->atlas_cols < 0) return fail(LF_ERR_INVALID_ARG, "atlas_cols must be >= 0");
     if (!ws) return fail(LF_ERR_WORKSPACE, "workspace is NULL");
     if (((uintptr_t)ws) % 256) return fail(LF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
     if (comp_ws_layout(planes->N, views->Vx, views->Vy, ws, cw) > ws_bytes)
@@ -678,6 +680,7 @@ lf_status lf_composite_backward(const lf_planes* planes, const lf_ref_camera* re
     lf_status st = check_composite_args(planes, ref, views, dviews, ws, ws_bytes, &cw);
     if (st != LF_OK) return st;
     if (!dplanes) return fail(LF_ERR_INVALID_ARG, "dplanes is NULL");
+    if (views->atlas_cols > 0) return fail(LF_ERR_UNSUPPORTED, "the composite adjoint takes separate views only");
     if (((uintptr_t)dviews) % 16 || ((uintptr_t)dplanes) % 16)
         return fail(LF_ERR_INVALID_ARG, "dviews and dplanes must be 16-byte aligned");
     CompParams p;

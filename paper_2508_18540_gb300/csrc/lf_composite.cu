@@ -106,6 +106,15 @@ __device__ __forceinline__ float4 load_texel(const void* planes, size_t idx)
     }
 }
 
+// index of view v's pixel (x, y) in the output: separate views, or the
+// quilt atlas (tile row v / c, tile column v % c)
+__device__ __forceinline__ size_t view_pixel(const CompParams& p, int v, int x, int y)
+{
+    if (p.atlas_cols <= 0) return ((size_t)v * p.Ny + y) * p.Nx + x;
+    const int c = p.atlas_cols;
+    return ((size_t)(v / c) * p.Ny + y) * ((size_t)c * p.Nx) + (size_t)(v % c) * p.Nx + x;
+}
+
 // plane index of the nearest texel, or -1 when the FP32 result is far outside
 __device__ __forceinline__ int nearest_index(int P_s, int x, float gm, float hn)
 {
@@ -185,7 +194,7 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
         Q2 = fmaf(T, tx.z, Q2);
         T = T * (1.0f - tx.w);
     }
-    reinterpret_cast<float4*>(out)[((size_t)v * p.Ny + y) * p.Nx + x] =
+    reinterpret_cast<float4*>(out)[view_pixel(p, v, x, y)] =
         make_float4(fmaf(T, p.bg[0], Q0), fmaf(T, p.bg[1], Q1), fmaf(T, p.bg[2], Q2), 1.0f - T);
 }
 
@@ -683,7 +692,7 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
         if (j >= p.Vx) break;
         const int v = vi * p.Vx + j;
         const float T = acc[jj][3];
-        reinterpret_cast<float4*>(out)[((size_t)v * p.Ny + y) * p.Nx + x] = make_float4(
+        reinterpret_cast<float4*>(out)[view_pixel(p, v, x, y)] = make_float4(
             fmaf(T, p.bg[0], acc[jj][0]), fmaf(T, p.bg[1], acc[jj][1]), fmaf(T, p.bg[2], acc[jj][2]), 1.0f - T);
     }
 }
@@ -821,7 +830,7 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_batched(const Com
                     if (j >= p.Vx) break;
                     const int v = vi * p.Vx + j;
                     const float T = acc[jj][3];
-                    reinterpret_cast<float4*>(out)[((size_t)v * p.Ny + y) * p.Nx + x] =
+                    reinterpret_cast<float4*>(out)[view_pixel(p, v, x, y)] =
                         make_float4(fmaf(T, p.bg[0], acc[jj][0]), fmaf(T, p.bg[1], acc[jj][1]),
                                     fmaf(T, p.bg[2], acc[jj][2]), 1.0f - T);
                 }

@@ -200,6 +200,7 @@ size_t comp_ws_layout(int32_t N, int32_t Vx, int32_t Vy, void* base, CompWs* out
 
 struct CompParams {
     int N, W, H, Nx, Ny, Vx, Vy, P_s, bilinear, dtype;
+    int atlas_cols;     // 0: separate views; c: quilt atlas of c view tiles per row
     float bg[3];
     // FP64 set-up for the per-(view, plane) coefficients
     double D_focal, D_forward, tth_x, tth_y, tthp_x, tthp_y, tphi_x, tphi_y;

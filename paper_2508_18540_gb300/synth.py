@@ -48,6 +48,7 @@ class ViewSet:
     Vy: int = 1
     bilinear: bool = False
     bg: tuple = (0.0, 0.0, 0.0)
+    atlas_cols: int = 0      # 0: separate views; c: quilt atlas with c view tiles per row
 
 
 @dataclasses.dataclass

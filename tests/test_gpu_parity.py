@@ -313,3 +313,27 @@ def test_unstaged_composite_fallback(orc, dtype, Nx, Ny, bilinear):
     o = orc.render(scene=sc, camera=cam, display=disp, views=views, N=6, binning="quantile")
     gpu = G.run_gpu(sc, cam, disp, views, 6, "quantile", dtype)
     _compare(gpu, o, o["ref"].W, o["ref"].H, 6, dtype, check_lists=False)
+
+
+@pytest.mark.parametrize("bilinear", [False, True])
+def test_quilt_atlas_layout(bilinear):
+    # the atlas output is the separate views laid out in tiles (row-major
+    # from the top); tiles past the last view stay untouched; the adjoint
+    # refuses the atlas layout
+    from paper_2508_18540_gb300 import api
+    w = S.workload_tiny()
+    g = api.DeviceGaussians.from_scene(w.scene)
+    r1 = api.LightFieldRenderer(w.camera, w.display, S.ViewSet(9, 1, bilinear), w.N, w.binning, "f32")
+    r2 = api.LightFieldRenderer(w.camera, w.display, S.ViewSet(9, 1, bilinear, atlas_cols=4), w.N, w.binning, "f32")
+    sep = r1.render(g).clone()
+    r2.out.fill_(float("nan"))
+    atlas = r2.render(g).clone()
+    torch.cuda.synchronize()
+    Ny, Nx = w.camera.Ny, w.camera.Nx
+    assert tuple(atlas.shape) == (3 * Ny, 4 * Nx, 4)
+    for v in range(9):
+        tile = atlas[(v // 4) * Ny:(v // 4 + 1) * Ny, (v % 4) * Nx:(v % 4 + 1) * Nx]
+        assert torch.equal(tile, sep[v]), v
+    assert torch.isnan(atlas[2 * Ny:, Nx:]).all()
+    with pytest.raises(api.L.LFError):
+        r2.backward(g, torch.zeros_like(sep))
