@@ -208,8 +208,14 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
 // copies (cp.async.bulk, completion counted on a "full" mbarrier), and every
 // thread composites its pixel for the VG views from shared memory. Warps
 // release a stage through an "empty" mbarrier, so no CTA-wide barrier sits in
-// the plane loop. Every staged row carries zero texels on both sides: an
-// out-of-plane index is clamped onto one and reads a transparent zero.
+// the nearest plane loop. Bilinear (single-scene kernel): the vertical tap
+// pair depends on (i, k, y) only, so the threads of an output row first blend
+// the two staged rows into an FP32 row in shared memory (double buffered by
+// plane parity, one CTA barrier per plane, the stage released right after),
+// and each view then takes its two horizontal taps from that row: 2 instead
+// of 4 texel reads per view and plane. Every staged row carries zero texels
+// on both sides: an out-of-plane index is clamped onto one and reads a
+// transparent zero.
 // The floor of the FP32 index uses the exact round-toward-minus-infinity add
 // of 1.5 * 2^23 (valid for |value| < 2^22) instead of a conversion unit op.
 // All waits are bounded; a wait that gives up sets the error word.
@@ -284,20 +290,6 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t a)
 {
     uint32_t v;
     asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
-    return v;
-}
-
-__device__ __forceinline__ float lds_f(uint32_t a)
-{
-    float v;
-    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
-    return v;
-}
-
-__device__ __forceinline__ int lds_i(uint32_t a)
-{
-    int v;
-    asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
 }
 
@@ -379,8 +371,14 @@ StagedGeom staged_geom(const CompParams& p, int texel_bytes, bool bilinear, int 
     G.row_bytes = (size_t)G.row_texels * texel_bytes;
     G.stage_bytes = G.row_bytes * G.BY * G.rows_per_y;
     G.groups_x = (p.Vx + VG - 1) / VG;
-    G.smem_bytes = kStages * G.stage_bytes + 2 * kStages * 8 + sizeof(float) * (size_t)p.N * (4 + 4 * ((VG + 3) / 4)) +
-                   sizeof(int) * (size_t)p.N;
+    G.blend_bytes = bilinear ? (size_t)2 * G.BY * G.row_texels * 16 : 0;
+    const size_t fixed = G.blend_bytes + 2 * kStages * 8 + sizeof(float) * (size_t)p.N * (4 + 4 * ((VG + 3) / 4)) +
+                         sizeof(int) * (size_t)p.N;
+    // a bilinear stage is released once its rows are blended, so a shallower
+    // ring suffices; keep two CTAs per SM where the blend rows would not fit
+    G.stages = kStages;
+    while (bilinear && G.stages > 3 && G.stages * G.stage_bytes + fixed > kTwoCtaSmem) --G.stages;
+    G.smem_bytes = G.stages * G.stage_bytes + fixed;
     return G;
 }
 
@@ -491,6 +489,38 @@ __device__ __forceinline__ void blend_plane(float (&acc)[VG][4], float4 hdr, uin
     }
 }
 
+// Bilinear horizontal taps from a vertically pre-blended FP32 row (shared
+// address ba, same texel layout as a staged row).
+template <int VG, bool CLAMP>
+__device__ __forceinline__ void blend_blended_row(float (&acc)[VG][4], float4 hdr, uint32_t ca, uint32_t ba,
+                                                  const ThreadGeom& tg)
+{
+    float c[4 * ((VG + 3) / 4)];
+#pragma unroll
+    for (int e = 0; e < (VG + 3) / 4; ++e) {
+        const float4 v = lds_f4(ca + 16u * (1 + e));
+        c[4 * e + 0] = v.x;
+        c[4 * e + 1] = v.y;
+        c[4 * e + 2] = v.z;
+        c[4 * e + 3] = v.w;
+    }
+#pragma unroll
+    for (int jj = 0; jj < VG; ++jj) {
+        float fx = __fmaf_rn(hdr.x, tg.xf, c[jj]);
+        if (CLAMP) fx = fminf(fmaxf(fx, -kClamp), kClamp);
+        const float tm = __fadd_rd(fx, kMagic);
+        const float wx = fx - (tm - kMagic), wa = 1.0f - wx;
+        const int i0 = __float_as_int(tm) + tg.base_x;
+        const uint32_t a0 = min((uint32_t)i0, tg.maxi), a1 = min((uint32_t)(i0 + 1), tg.maxi);
+        const float4 ta = lds_f4(ba + a0 * 16u), tb = lds_f4(ba + a1 * 16u);
+        const float T = acc[jj][3];
+        acc[jj][0] = fmaf(T, fmaf(wa, ta.x, wx * tb.x), acc[jj][0]);
+        acc[jj][1] = fmaf(T, fmaf(wa, ta.y, wx * tb.y), acc[jj][1]);
+        acc[jj][2] = fmaf(T, fmaf(wa, ta.z, wx * tb.z), acc[jj][2]);
+        acc[jj][3] = fmaf(-T, fmaf(wa, ta.w, wx * tb.w), T);
+    }
+}
+
 // Every view of this thread has T == 0 exactly (or the thread is idle).
 // T never leaves 0 (T <- T - T A), and behind it a plane adds T c = 0 to Q
 // and leaves T = 0, so skipping such planes changes no bit of the output.
@@ -577,15 +607,18 @@ __device__ __forceinline__ void load_coefs(const CompParams& p, const CompWs& w,
 // Zero left and right pads of every staged row (the bulk copies never write them).
 template <int DT>
 __device__ __forceinline__ void zero_pads(const CompParams& p, const StagedGeom& G, unsigned char* stage_base,
-                                          size_t stage_stride)
+                                          size_t stage_stride, int nstages)
 {
     constexpr int TB = Texel<DT>::kBytes;
     const int nrows = G.BY * G.rows_per_y;
-    for (int e = threadIdx.x; e < kStages * nrows; e += blockDim.x) {
-        unsigned char* row = stage_base + (size_t)(e / nrows) * stage_stride + (size_t)(e % nrows) * G.row_bytes;
-        for (int b = 0; b < G.padl * TB; b += 4) *reinterpret_cast<uint32_t*>(row + b) = 0u;
-        for (size_t b = (size_t)(G.padl + p.W) * TB; b < G.row_bytes; b += 4)
-            *reinterpret_cast<uint32_t*>(row + b) = 0u;
+    // 16-byte chunks: left pad [0, padl TB), right pad [(padl + W) TB, row_bytes)
+    const int lc = G.padl * TB / 16, rc = (int)((G.row_bytes - (size_t)(G.padl + p.W) * TB) / 16);
+    const int per_row = lc + rc;
+    for (int e = threadIdx.x; e < nstages * nrows * per_row; e += blockDim.x) {
+        const int r = e / per_row, c = e % per_row;
+        unsigned char* row = stage_base + (size_t)(r / nrows) * stage_stride + (size_t)(r % nrows) * G.row_bytes;
+        const size_t off = c < lc ? (size_t)c * 16 : (size_t)(G.padl + p.W) * TB + (size_t)(c - lc) * 16;
+        *reinterpret_cast<uint4*>(row + off) = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -596,10 +629,17 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
                                                                         float* __restrict__ out)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    // [stages][rows][row_bytes] | full[stages] | empty[stages] | coef [N][CW] | plist [N]
+    // [stages][rows][row_bytes] | bilinear: [2][BY][row_texels] float4 |
+    // full[kStages] | empty[kStages] | coef [N][CW] | plist [N]
     constexpr int CW = CoefBlock<VG>::kFloats;
     unsigned char* stage_base = smem;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * G.stage_bytes);
+    // bilinear: the two staged rows of an output row are blended vertically
+    // once per plane into an FP32 row (double buffered by plane parity)
+    const int NS = BILINEAR ? G.stages : kStages;   // nearest keeps a compile-time ring depth
+    unsigned char* blend_base = smem + NS * G.stage_bytes;
+    // nearest has no blend rows; spelling its barrier base out as the ring's
+    // end gives measurably faster per-plane barrier addressing
+    uint64_t* full = reinterpret_cast<uint64_t*>(BILINEAR ? blend_base + G.blend_bytes : smem + kStages * G.stage_bytes);
     uint64_t* empty = full + kStages;
     float* coef = reinterpret_cast<float*>(empty + kStages);   // 16-byte aligned (stage_bytes, 2 kStages * 8)
     int* plist = reinterpret_cast<int*>(coef + (size_t)p.N * CW);
@@ -621,9 +661,18 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
     }
     __syncthreads();
     load_coefs<BILINEAR, VG>(p, w, plist, s_nplanes, vi, j0, coef);
-    zero_pads<DT>(p, G, stage_base, G.stage_bytes);
+    zero_pads<DT>(p, G, stage_base, G.stage_bytes, NS);
+    if constexpr (BILINEAR) {
+        // pads of the blended rows: zero once (the blend writes interiors only)
+        float4* bb = reinterpret_cast<float4*>(blend_base);
+        const int pads = G.row_texels - p.W;
+        for (int e = tid; e < 2 * G.BY * pads; e += blockDim.x) {
+            const int r = e / pads, t = e % pads;
+            bb[(size_t)r * G.row_texels + (t < G.padl ? t : t + p.W)] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(smem_addr(&full[s]), 1);
             mbar_init(smem_addr(&empty[s]), kStagedWarps);
         }
@@ -632,10 +681,10 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
     __syncthreads();
     const int P = s_nplanes;
 
-    // producer: stage the plane rows of list entry q into stage q % kStages
+    // producer: stage the plane rows of list entry q into stage q % NS
     auto produce = [&](int q) {
         produce_rows<DT>(p, G, planes, plist[q], coef + (size_t)q * CW, Y0,
-                         stage_base + (size_t)(q % kStages) * G.stage_bytes, smem_addr(&full[q % kStages]));
+                         stage_base + (size_t)(q % NS) * G.stage_bytes, smem_addr(&full[q % NS]));
     };
 
     if (tid >= kStagedThreads) {
@@ -643,9 +692,8 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
         // refilling a stage as soon as every consumer warp has released it
         if (tid == kStagedThreads) {
             for (int q = 0; q < P; ++q) {
-                const int s = q % kStages;
-                if (q >= kStages &&
-                    !mbar_wait_bounded(smem_addr(&empty[s]), (uint32_t)(((q / kStages) - 1) & 1))) {
+                const int s = q % NS;
+                if (q >= NS && !mbar_wait_bounded(smem_addr(&empty[s]), (uint32_t)(((q / NS) - 1) & 1))) {
                     atomicExch(w.err, 1);
                     break;
                 }
@@ -665,25 +713,68 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams
     bool warp_sat = false;   // every view of every lane of this warp has T == 0
 
     for (int q = 0; q < P; ++q) {
-        const int s = q % kStages;
-        const uint32_t parity = (uint32_t)((q / kStages) & 1);
-        if (!mbar_wait_bounded(smem_addr(&full[s]), parity)) {
+        const int s = q % NS;
+        const uint32_t parity = (uint32_t)((q / NS) & 1);
+        if ((!BILINEAR || ok) && !mbar_wait_bounded(smem_addr(&full[s]), parity)) {
             atomicExch(w.err, 1);
             ok = false;
-            break;
+            // bilinear: keep meeting the per-plane CTA barrier (results discarded)
+            if (!BILINEAR) break;
         }
         if ((q & 3) == 0 && q > 0 && !warp_sat) warp_sat = __all_sync(0xffffffffu, saturated<VG>(acc, live));
-        if (live && !warp_sat) {
+        if constexpr (BILINEAR) {
+            // the threads of an output row blend interior texels tx, tx + TX,
+            // ... of its two staged rows into the FP32 row buffer
             const uint32_t ca = coef_a + 4u * (uint32_t)(q * CW);
-            const uint32_t sb = stage_a + (uint32_t)(s * G.stage_bytes);
             const float4 hdr = lds_f4(ca);
-            if (__float_as_int(hdr.w))
-                blend_plane<DT, BILINEAR, VG, true>(acc, hdr, ca, sb, tg);
-            else
-                blend_plane<DT, BILINEAR, VG, false>(acc, hdr, ca, sb, tg);
+            float4* brow = reinterpret_cast<float4*>(blend_base) + ((size_t)(q & 1) * G.BY + ty) * G.row_texels;
+            if (ty < G.BY) {
+                float fy = __fmaf_rn(hdr.y, tg.yf, hdr.z);
+                fy = fminf(fmaxf(fy, -kClamp), kClamp);
+                const float ty_m = __fadd_rd(fy, kMagic);
+                const float wy = fy - (ty_m - kMagic);
+                const int y0 = tg.psy + (__float_as_int(ty_m) - kMagicBits);
+                const bool v0 = y0 >= 0 && y0 < tg.H, v1 = y0 + 1 >= 0 && y0 + 1 < tg.H;
+                const float w0 = v0 ? 1.0f - wy : 0.0f, w1 = v1 ? wy : 0.0f;
+                const uint32_t r0 = stage_a + (uint32_t)(s * G.stage_bytes) + tg.row0;
+                const uint32_t r1 = r0 + tg.row_bytes;
+                for (int i = G.padl + tx; i < G.padl + p.W; i += G.TX) {
+                    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (v0) {
+                        const float4 a = Texel<DT>::load(r0, (uint32_t)i);
+                        t = make_float4(w0 * a.x, w0 * a.y, w0 * a.z, w0 * a.w);
+                    }
+                    if (v1) {
+                        const float4 b = Texel<DT>::load(r1, (uint32_t)i);
+                        t = make_float4(fmaf(w1, b.x, t.x), fmaf(w1, b.y, t.y), fmaf(w1, b.z, t.z), fmaf(w1, b.w, t.w));
+                    }
+                    brow[i] = t;
+                }
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(kStagedThreads) : "memory");
+            // the staged rows are no longer needed: release the stage now
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
+            if (live && !warp_sat) {
+                const uint32_t ba = smem_addr(brow);
+                if (__float_as_int(hdr.w))
+                    blend_blended_row<VG, true>(acc, hdr, ca, ba, tg);
+                else
+                    blend_blended_row<VG, false>(acc, hdr, ca, ba, tg);
+            }
+        } else {
+            if (live && !warp_sat) {
+                const uint32_t ca = coef_a + 4u * (uint32_t)(q * CW);
+                const uint32_t sb = stage_a + (uint32_t)(s * G.stage_bytes);
+                const float4 hdr = lds_f4(ca);
+                if (__float_as_int(hdr.w))
+                    blend_plane<DT, BILINEAR, VG, true>(acc, hdr, ca, sb, tg);
+                else
+                    blend_plane<DT, BILINEAR, VG, false>(acc, hdr, ca, sb, tg);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
     }
     if (!ok || !live) return;
 #pragma unroll
@@ -765,7 +856,7 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_batched(const Com
             const int n = plane_list(p, scs[si].count, plist);
             if (tid == 0) s_nplanes = n;
         }
-        if (si != prev) zero_pads<DT>(p, G, stage_base, max_stage_bytes);
+        if (si != prev) zero_pads<DT>(p, G, stage_base, max_stage_bytes, kStages);
         __syncthreads();
         load_coefs<BILINEAR, VG>(p, w, plist, s_nplanes, vi, j0, coef);
         __syncthreads();
@@ -869,8 +960,10 @@ template <int DT, bool BILINEAR>
 bool launch_staged(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
                    cudaStream_t s)
 {
-    // bilinear keeps 5 views per thread (9 would spill at this register budget)
-    if (p.Vx >= 9 && !BILINEAR) return launch_staged_vg<DT, BILINEAR, 9>(p, planes, count, ws, out, s);
+    // bilinear FP32 keeps 5 views per thread (measured faster: 9 spill more
+    // with four-channel FP32 taps); the narrower plane types take 9
+    if (p.Vx >= 9 && !(BILINEAR && DT == LF_F32))
+        return launch_staged_vg<DT, BILINEAR, 9>(p, planes, count, ws, out, s);
     if (p.Vx >= 5) return launch_staged_vg<DT, BILINEAR, 5>(p, planes, count, ws, out, s);
     return launch_staged_vg<DT, BILINEAR, 3>(p, planes, count, ws, out, s);
 }

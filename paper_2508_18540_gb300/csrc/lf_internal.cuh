@@ -209,12 +209,15 @@ struct CompParams {
 // staged composite layout (see lf_composite.cu)
 constexpr int kStagedThreads = 512;   // consumer threads of a staged-composite CTA
 constexpr int kStages = 6;            // depth of its plane-row ring
+constexpr size_t kTwoCtaSmem = 112 * 1024;   // dynamic shared memory that still lets two CTAs share an SM
 struct StagedGeom {
     int TX, BY, VG, rows_per_y;    // rows_per_y: 1 nearest, 2 bilinear
     int padl;                      // zero texels left of every staged row (16 bytes)
     int row_texels;                // padl + W + right pad, a multiple of 16 bytes
     size_t row_bytes, stage_bytes, smem_bytes;
     int groups_x;                  // view groups per view row
+    int stages;                    // ring depth of the single-scene kernel (<= kStages)
+    size_t blend_bytes;            // bilinear: two FP32 row buffers per output row (single-scene kernel)
 };
 StagedGeom staged_geom(const CompParams& p, int texel_bytes, bool bilinear, int VG, int tx_max);
 

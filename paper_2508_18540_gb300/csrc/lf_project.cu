@@ -41,17 +41,44 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
-// Publishes the depth key range and culled-in count of one warp.
-__device__ __forceinline__ void publish_key(WsHeader* hdr, unsigned long long key)
+constexpr int kProjThreads = 256;
+constexpr int kProjItems = 4;   // primitives per thread (block-strided)
+
+// Culled-in count and depth key range of the primitives one thread projected.
+struct KeyStats {
+    unsigned long long n = 0, mn = ~0ull, mx = 0ull;
+    __device__ __forceinline__ void add(unsigned long long key)
+    {
+        if (key == kInvalidKey) return;
+        ++n;
+        mn = key < mn ? key : mn;
+        mx = key > mx ? key : mx;
+    }
+};
+
+// Publishes the statistics of one CTA with one atomic of each kind (the
+// header words are shared by the whole grid, so per-warp atomics serialise).
+__device__ __forceinline__ void publish_keys(WsHeader* hdr, KeyStats s)
 {
-    const bool valid = key != kInvalidKey;
-    const unsigned ballot = __ballot_sync(0xffffffffu, valid);
-    const unsigned long long mn = warp_min_u64(valid ? key : ~0ull);
-    const unsigned long long mx = warp_max_u64(valid ? key : 0ull);
-    if ((threadIdx.x & 31) == 0 && ballot) {
-        atomicAdd(&hdr->M, (unsigned long long)__popc(ballot));
-        atomicMin(&hdr->kmin, mn);
-        atomicMax(&hdr->kmax, mx);
+    __shared__ unsigned long long sh[3][kProjThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s.n += __shfl_xor_sync(0xffffffffu, s.n, o);
+    s.mn = warp_min_u64(s.mn);
+    s.mx = warp_max_u64(s.mx);
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) sh[0][wid] = s.n, sh[1][wid] = s.mn, sh[2][wid] = s.mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < kProjThreads / 32; ++k) {
+            s.n += sh[0][k];
+            s.mn = sh[1][k] < s.mn ? sh[1][k] : s.mn;
+            s.mx = sh[2][k] > s.mx ? sh[2][k] : s.mx;
+        }
+        if (s.n) {
+            atomicAdd(&hdr->M, s.n);
+            atomicMin(&hdr->kmin, s.mn);
+            atomicMax(&hdr->kmax, s.mx);
+        }
     }
 }
 
@@ -132,95 +159,103 @@ __device__ __forceinline__ bool gauss_footprint(const ProjParams& p, float m0, f
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_project_gaussians(lf_gaussians g, ProjParams p, BuildWs w, int4* rect_out,
-                                                           int32_t* chunk_out)
+__global__ void __launch_bounds__(kProjThreads) k_project_gaussians(lf_gaussians g, ProjParams p, BuildWs w,
+                                                                    int4* rect_out, int32_t* chunk_out)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long key = kInvalidKey;
-    if (i < p.n) {
-        const float m0 = g.means[3 * i + 0], m1 = g.means[3 * i + 1], m2 = g.means[3 * i + 2];
-        const double z = ref_depth(p, (double)m0, (double)m1, (double)m2);
-        int4 rect = make_int4(0, 0, -1, -1);
-        chunk_out[i] = -1;
-        if (z > p.z_near) {
-            const float4 q = *reinterpret_cast<const float4*>(g.quats + 4 * i);
-            float2 mean;
-            float4 conic;
-            if (gauss_footprint(p, m0, m1, m2, g.scales[3 * i + 0], g.scales[3 * i + 1], g.scales[3 * i + 2], q, z,
-                                rect, mean, conic)) {
-                key = (unsigned long long)__double_as_longlong(z);
-                conic.w = g.opacity[i];
-                w.mean2d[i] = mean;
-                w.conic_o[i] = conic;
-            } else {
-                rect = make_int4(0, 0, -1, -1);
+    KeyStats st;
+    for (int it = 0; it < kProjItems; ++it) {
+        const long long i = ((long long)blockIdx.x * kProjItems + it) * kProjThreads + threadIdx.x;
+        unsigned long long key = kInvalidKey;
+        if (i < p.n) {
+            const float m0 = g.means[3 * i + 0], m1 = g.means[3 * i + 1], m2 = g.means[3 * i + 2];
+            const double z = ref_depth(p, (double)m0, (double)m1, (double)m2);
+            int4 rect = make_int4(0, 0, -1, -1);
+            chunk_out[i] = -1;
+            if (z > p.z_near) {
+                const float4 q = *reinterpret_cast<const float4*>(g.quats + 4 * i);
+                float2 mean;
+                float4 conic;
+                if (gauss_footprint(p, m0, m1, m2, g.scales[3 * i + 0], g.scales[3 * i + 1], g.scales[3 * i + 2], q, z,
+                                    rect, mean, conic)) {
+                    key = (unsigned long long)__double_as_longlong(z);
+                    conic.w = g.opacity[i];
+                    w.mean2d[i] = mean;
+                    w.conic_o[i] = conic;
+                } else {
+                    rect = make_int4(0, 0, -1, -1);
+                }
             }
+            rect_out[i] = rect;
+            w.keyA[i] = key;
+            w.valA[i] = (uint32_t)i;
         }
-        rect_out[i] = rect;
-        w.keyA[i] = key;
-        w.valA[i] = (uint32_t)i;
+        st.add(key);
     }
-    publish_key(w.hdr, key);
+    publish_keys(w.hdr, st);
 }
 
 // Voxel v: cube of side s = base_size 2^-level with low corner origin + ijk s.
 // Depth = centre depth; culled unless the nearest corner lies past z_near;
 // footprint = bounding box of the 8 projected corners (pixel centres inside).
-__global__ void __launch_bounds__(256) k_project_voxels(lf_voxels v, ProjParams p, BuildWs w, int4* rect_out,
-                                                        int32_t* chunk_out)
+__global__ void __launch_bounds__(kProjThreads) k_project_voxels(lf_voxels v, ProjParams p, BuildWs w,
+                                                                 int4* rect_out, int32_t* chunk_out)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long key = kInvalidKey;
-    if (i < p.n) {
-        double s = p.base_size;
-        for (int l = 0; l < (int)v.level[i]; ++l) s = __dmul_rn(s, 0.5);
-        double lo[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) lo[a] = __dadd_rn(p.origin[a], __dmul_rn((double)v.ijk[3 * i + a], s));
-        const double hs = __dmul_rn(0.5, s);
-        const double z = ref_depth(p, __dadd_rn(lo[0], hs), __dadd_rn(lo[1], hs), __dadd_rn(lo[2], hs));
-        const double zmin = __dsub_rn(z, __dmul_rn(hs, p.rho));
-        int4 rect = make_int4(0, 0, -1, -1);
-        chunk_out[i] = -1;
-        if (zmin > p.z_near) {
-            const float* R = p.Rf;
-            float mnx = __int_as_float(0x7f800000), mny = mnx;
-            float mxx = -mnx, mxy = -mnx;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float X = __double2float_rn(__dadd_rn(lo[0], __dmul_rn((double)(c & 1), s)));
-                const float Y = __double2float_rn(__dadd_rn(lo[1], __dmul_rn((double)((c >> 1) & 1), s)));
-                const float Z = __double2float_rn(__dadd_rn(lo[2], __dmul_rn((double)((c >> 2) & 1), s)));
-                const float xc = __fmaf_rn(R[0], X, __fmaf_rn(R[1], Y, __fmaf_rn(R[2], Z, p.t0f)));
-                const float yc = __fmaf_rn(R[3], X, __fmaf_rn(R[4], Y, __fmaf_rn(R[5], Z, p.t1f)));
-                const float zc = __fmaf_rn(R[6], X, __fmaf_rn(R[7], Y, __fmaf_rn(R[8], Z, p.t2rf)));
-                const float iz = __fdiv_rn(1.0f, zc);
-                const float px = __fmaf_rn(p.fxf, __fmul_rn(xc, iz), p.cxf);
-                const float py = __fmaf_rn(p.fyf, __fmul_rn(yc, iz), p.cyf);
-                mnx = fminf(mnx, px);
-                mxx = fmaxf(mxx, px);
-                mny = fminf(mny, py);
-                mxy = fmaxf(mxy, py);
+    KeyStats st;
+    for (int it = 0; it < kProjItems; ++it) {
+        const long long i = ((long long)blockIdx.x * kProjItems + it) * kProjThreads + threadIdx.x;
+        unsigned long long key = kInvalidKey;
+        if (i < p.n) {
+            double s = p.base_size;
+            for (int l = 0; l < (int)v.level[i]; ++l) s = __dmul_rn(s, 0.5);
+            double lo[3];
+    #pragma unroll
+            for (int a = 0; a < 3; ++a) lo[a] = __dadd_rn(p.origin[a], __dmul_rn((double)v.ijk[3 * i + a], s));
+            const double hs = __dmul_rn(0.5, s);
+            const double z = ref_depth(p, __dadd_rn(lo[0], hs), __dadd_rn(lo[1], hs), __dadd_rn(lo[2], hs));
+            const double zmin = __dsub_rn(z, __dmul_rn(hs, p.rho));
+            int4 rect = make_int4(0, 0, -1, -1);
+            chunk_out[i] = -1;
+            if (zmin > p.z_near) {
+                const float* R = p.Rf;
+                float mnx = __int_as_float(0x7f800000), mny = mnx;
+                float mxx = -mnx, mxy = -mnx;
+    #pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float X = __double2float_rn(__dadd_rn(lo[0], __dmul_rn((double)(c & 1), s)));
+                    const float Y = __double2float_rn(__dadd_rn(lo[1], __dmul_rn((double)((c >> 1) & 1), s)));
+                    const float Z = __double2float_rn(__dadd_rn(lo[2], __dmul_rn((double)((c >> 2) & 1), s)));
+                    const float xc = __fmaf_rn(R[0], X, __fmaf_rn(R[1], Y, __fmaf_rn(R[2], Z, p.t0f)));
+                    const float yc = __fmaf_rn(R[3], X, __fmaf_rn(R[4], Y, __fmaf_rn(R[5], Z, p.t1f)));
+                    const float zc = __fmaf_rn(R[6], X, __fmaf_rn(R[7], Y, __fmaf_rn(R[8], Z, p.t2rf)));
+                    const float iz = __fdiv_rn(1.0f, zc);
+                    const float px = __fmaf_rn(p.fxf, __fmul_rn(xc, iz), p.cxf);
+                    const float py = __fmaf_rn(p.fyf, __fmul_rn(yc, iz), p.cyf);
+                    mnx = fminf(mnx, px);
+                    mxx = fmaxf(mxx, px);
+                    mny = fminf(mny, py);
+                    mxy = fmaxf(mxy, py);
+                }
+                const float fx0 = ceilf(mnx), fx1 = floorf(mxx);
+                const float fy0 = ceilf(mny), fy1 = floorf(mxy);
+                if ((fx0 <= fx1 && fy0 <= fy1) && (fx0 <= p.wmax && fx1 >= 0.0f && fy0 <= p.hmax && fy1 >= 0.0f)) {
+                    rect.x = (int)fmaxf(fx0, 0.0f);
+                    rect.y = (int)fmaxf(fy0, 0.0f);
+                    rect.z = (int)fminf(fx1, p.wmax);
+                    rect.w = (int)fminf(fy1, p.hmax);
+                    key = (unsigned long long)__double_as_longlong(z);
+                    // cube relative to the reference centre, for the ray integrals
+                    w.conic_o[i] = make_float4(__double2float_rn(__dsub_rn(lo[0], p.cam_o[0])),
+                                               __double2float_rn(__dsub_rn(lo[1], p.cam_o[1])),
+                                               __double2float_rn(__dsub_rn(lo[2], p.cam_o[2])), __double2float_rn(s));
+                }
             }
-            const float fx0 = ceilf(mnx), fx1 = floorf(mxx);
-            const float fy0 = ceilf(mny), fy1 = floorf(mxy);
-            if ((fx0 <= fx1 && fy0 <= fy1) && (fx0 <= p.wmax && fx1 >= 0.0f && fy0 <= p.hmax && fy1 >= 0.0f)) {
-                rect.x = (int)fmaxf(fx0, 0.0f);
-                rect.y = (int)fmaxf(fy0, 0.0f);
-                rect.z = (int)fminf(fx1, p.wmax);
-                rect.w = (int)fminf(fy1, p.hmax);
-                key = (unsigned long long)__double_as_longlong(z);
-                // cube relative to the reference centre, for the ray integrals
-                w.conic_o[i] = make_float4(__double2float_rn(__dsub_rn(lo[0], p.cam_o[0])),
-                                           __double2float_rn(__dsub_rn(lo[1], p.cam_o[1])),
-                                           __double2float_rn(__dsub_rn(lo[2], p.cam_o[2])), __double2float_rn(s));
-            }
+            rect_out[i] = rect;
+            w.keyA[i] = key;
+            w.valA[i] = (uint32_t)i;
         }
-        rect_out[i] = rect;
-        w.keyA[i] = key;
-        w.valA[i] = (uint32_t)i;
+        st.add(key);
     }
-    publish_key(w.hdr, key);
+    publish_keys(w.hdr, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -393,8 +428,9 @@ void launch_project_gaussians(const lf_gaussians& g, const ProjParams& p, const 
                               int32_t* chunk, cudaStream_t s)
 {
     if (p.n <= 0) return;
-    const unsigned blocks = (unsigned)((p.n + 255) / 256);
-    k_project_gaussians<<<blocks, 256, 0, s>>>(g, p, ws, reinterpret_cast<int4*>(rect), chunk);
+    const long long per = (long long)kProjThreads * kProjItems;
+    const unsigned blocks = (unsigned)((p.n + per - 1) / per);
+    k_project_gaussians<<<blocks, kProjThreads, 0, s>>>(g, p, ws, reinterpret_cast<int4*>(rect), chunk);
     note_launches(1);
 }
 
@@ -402,8 +438,9 @@ void launch_project_voxels(const lf_voxels& v, const ProjParams& p, const BuildW
                            cudaStream_t s)
 {
     if (p.n <= 0) return;
-    const unsigned blocks = (unsigned)((p.n + 255) / 256);
-    k_project_voxels<<<blocks, 256, 0, s>>>(v, p, ws, reinterpret_cast<int4*>(rect), chunk);
+    const long long per = (long long)kProjThreads * kProjItems;
+    const unsigned blocks = (unsigned)((p.n + per - 1) / per);
+    k_project_voxels<<<blocks, kProjThreads, 0, s>>>(v, p, ws, reinterpret_cast<int4*>(rect), chunk);
     note_launches(1);
 }
 

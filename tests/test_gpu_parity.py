@@ -72,6 +72,19 @@ def test_ragged_rotated_scaled(orc, bilinear, binning):
     _compare(gpu, o, o["ref"].W, o["ref"].H, 5, "f32")
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_bilinear_nine_views_per_thread(orc, dtype):
+    # bilinear with 9 views per thread: 11 x 2 views (a ragged view group and
+    # two view rows), so every CTA pre-blends the rows of its own view row
+    cam = S.Camera(np.eye(3), np.zeros(3), np.radians(50.0), np.radians(40.0), 96, 40)
+    disp = S.Display(D_focal=3.0, phi_x=0.12, phi_y=0.05)
+    sc = S.uniform_gaussians(4000, 17)
+    views = S.ViewSet(11, 2, True, (0.3, 0.1, 0.2))
+    o = orc.render(scene=sc, camera=cam, display=disp, views=views, N=12, binning="quantile")
+    gpu = G.run_gpu(sc, cam, disp, views, 12, "quantile", dtype)
+    _compare(gpu, o, o["ref"].W, o["ref"].H, 12, dtype)
+
+
 def test_two_view_rows(orc):
     # vertical parallax too (Vy = 3), non-square views
     cam = S.Camera(np.eye(3), np.zeros(3), np.radians(50.0), np.radians(40.0), 64, 48)
