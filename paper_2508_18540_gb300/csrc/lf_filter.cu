@@ -10,10 +10,13 @@
 //                 memory, the left halo is the previous segment's tail of
 //                 original texels carried in shared memory, so writing the
 //                 segment back never destroys an input still needed.
-//  k_filter_cols  one thread per (plane, column): walks down the column
-//                 keeping the last 2r+1 original texels in a per-thread ring
-//                 in shared memory; output row y - r is written once row y
-//                 has been read, after every read that needs its original.
+//  k_filter_cols  one CTA per (plane, strip of 32 columns), 8 threads per
+//                 column: walks down the strip in bands of 32 rows; each
+//                 band and the r rows below it are read into shared memory
+//                 (the r rows above are the previous band's tail of original
+//                 texels, carried with the look-ahead), so writing the band
+//                 back never destroys an input still needed. Every texel is
+//                 read once and written once.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -25,7 +28,10 @@ namespace {
 
 constexpr int kRowThreads = 256;
 constexpr int kSeg = 1024;          // texels per row segment
-constexpr int kColThreads = 64;
+constexpr int kColStrip = 32;   // columns per CTA of the column pass
+constexpr int kColLanes = 8;    // threads per column
+constexpr int kColBand = 32;    // output rows per step (>= 2 * kFilterMaxRadius: the carry never overlaps)
+static_assert(kColBand >= 2 * kFilterMaxRadius, "column carry would overlap");
 
 template <int DT>
 __device__ __forceinline__ float4 ld(const void* p, size_t i)
@@ -118,25 +124,49 @@ __global__ void __launch_bounds__(kRowThreads) k_filter_rows(void* planes, int W
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kColThreads) k_filter_cols(void* planes, int W, int H, FilterParams f)
+__global__ void __launch_bounds__(kColStrip* kColLanes) k_filter_cols(void* planes, int W, int H, FilterParams f)
 {
-    extern __shared__ float4 ring[];   // [2r + 1][kColThreads]
-    const int r = f.radius, L = 2 * r + 1;
-    const int x = blockIdx.x * kColThreads + threadIdx.x;
+    extern __shared__ float4 cbuf[];   // rows [r + kColBand + r][kColStrip]: top halo, band, look-ahead
+    const int r = f.radius;
+    const int tx = threadIdx.x % kColStrip, ty = threadIdx.x / kColStrip;
+    const int x = blockIdx.x * kColStrip + tx;
+    const bool col = x < W;
     const size_t plane = (size_t)blockIdx.y * (size_t)W * H;
-    if (x >= W) return;
-    float4* my = ring + threadIdx.x;
-    for (int y = 0; y < H + r; ++y) {
-        my[(y % L) * kColThreads] = y < H ? ld<DT>(planes, plane + (size_t)y * W + x) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const int o = y - r;
-        if (o < 0) continue;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int t = -r; t <= r; ++t) {
-            const int yy = o + t;
-            if (yy < 0) continue;   // zero padding above; rows >= H were stored as zero
-            fma4(a, f.w[t + r], my[(yy % L) * kColThreads]);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    // rows -r .. r - 1 of the first band: zero padding above, then originals
+    for (int i = ty; i < 2 * r; i += kColLanes) {
+        const int y = i - r;
+        cbuf[i * kColStrip + tx] = (col && y >= 0 && y < H) ? ld<DT>(planes, plane + (size_t)y * W + x) : zero;
+    }
+    for (int y0 = 0; y0 < H; y0 += kColBand) {
+        const int n = min(kColBand, H - y0);
+        // rows y0 + r .. y0 + n + r - 1 (originals; zero below the plane);
+        // rows y0 - r .. y0 + r - 1 are already in place
+        for (int i = 2 * r + ty; i < n + 2 * r; i += kColLanes) {
+            const int y = y0 + i - r;
+            cbuf[i * kColStrip + tx] = (col && y < H) ? ld<DT>(planes, plane + (size_t)y * W + x) : zero;
         }
-        st<DT>(planes, plane + (size_t)o * W + x, a);
+        __syncthreads();
+        float4 out[kColBand / kColLanes];
+#pragma unroll
+        for (int q = 0; q < kColBand / kColLanes; ++q) {
+            const int i = ty + q * kColLanes;
+            float4 a = zero;
+            if (i < n)
+                for (int t = -r; t <= r; ++t) fma4(a, f.w[t + r], cbuf[(r + i + t) * kColStrip + tx]);
+            out[q] = a;
+        }
+        __syncthreads();
+        // the band's last r rows and the look-ahead become the next band's
+        // top halo and first rows (originals: nothing below y0 + n is written yet)
+        if (n == kColBand)
+            for (int i = threadIdx.x; i < 2 * r * kColStrip; i += blockDim.x) cbuf[i] = cbuf[kColBand * kColStrip + i];
+#pragma unroll
+        for (int q = 0; q < kColBand / kColLanes; ++q) {
+            const int i = ty + q * kColLanes;
+            if (col && i < n) st<DT>(planes, plane + (size_t)(y0 + i) * W + x, out[q]);
+        }
+        __syncthreads();
     }
 }
 
@@ -145,8 +175,9 @@ void launch_filter_t(void* planes, int N, int W, int H, const FilterParams& f, c
 {
     k_filter_rows<DT><<<(unsigned)((size_t)N * H), kRowThreads, sizeof(float4) * (kSeg + 2 * f.radius), s>>>(
         planes, W, H, f);
-    const dim3 grid((unsigned)((W + kColThreads - 1) / kColThreads), (unsigned)N);
-    k_filter_cols<DT><<<grid, kColThreads, sizeof(float4) * (2 * f.radius + 1) * kColThreads, s>>>(planes, W, H, f);
+    const dim3 grid((unsigned)((W + kColStrip - 1) / kColStrip), (unsigned)N);
+    k_filter_cols<DT><<<grid, kColStrip * kColLanes, sizeof(float4) * (kColBand + 2 * f.radius) * kColStrip, s>>>(
+        planes, W, H, f);
     note_launches(2);
 }
 
