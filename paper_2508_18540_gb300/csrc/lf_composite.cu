@@ -77,21 +77,13 @@ __global__ void k_comp_coeffs(CompParams p, const double* __restrict__ d, const 
     if (!(fmax(fabs(lo), fabs(hi)) + span + 2.0 < (double)kNarrow)) atomicOr(&w.wide[k], 1);
 }
 
-// RGBA8 unorm texel: byte / 255 per channel
-__device__ __forceinline__ float4 unpack_u8x4(uint32_t u)
-{
-    constexpr float s = 1.0f / 255.0f;
-    return make_float4((float)(u & 0xffu) * s, (float)((u >> 8) & 0xffu) * s, (float)((u >> 16) & 0xffu) * s,
-                       (float)(u >> 24) * s);
-}
-
 template <int DT>
 __device__ __forceinline__ float4 load_texel(const void* planes, size_t idx)
 {
     if (DT == LF_F32) {
         return __ldg(reinterpret_cast<const float4*>(planes) + idx);
     } else if (DT == LF_U8) {
-        return unpack_u8x4(__ldg(reinterpret_cast<const uint32_t*>(planes) + idx));
+        return u8_unpack(__ldg(reinterpret_cast<const uint32_t*>(planes) + idx));
     } else {
         const uint2 u = __ldg(reinterpret_cast<const uint2*>(planes) + idx);
         if (DT == LF_F16) {
@@ -314,7 +306,7 @@ struct Texel<LF_F16> {
 template <>
 struct Texel<LF_U8> {
     static constexpr int kBytes = 4;
-    static __device__ __forceinline__ float4 load(uint32_t row, uint32_t i) { return unpack_u8x4(lds_u32(row + i * 4u)); }
+    static __device__ __forceinline__ float4 load(uint32_t row, uint32_t i) { return u8_unpack(lds_u32(row + i * 4u)); }
 };
 template <>
 struct Texel<LF_BF16> {
@@ -439,12 +431,24 @@ __device__ __forceinline__ void blend_plane(float (&acc)[VG][4], float4 hdr, uin
 #pragma unroll
         for (int jj = 0; jj < VG; ++jj) {
             const int ix = __float_as_int(floor_magic<CLAMP>(gmx, xf, c[3 + jj])) + base_x;
-            const float4 t = TX_::load(row, min((uint32_t)ix, maxi));
             const float T = acc[jj][3];
-            acc[jj][0] = fmaf(T, t.x, acc[jj][0]);
-            acc[jj][1] = fmaf(T, t.y, acc[jj][1]);
-            acc[jj][2] = fmaf(T, t.z, acc[jj][2]);
-            acc[jj][3] = fmaf(-T, t.w, T);
+            if constexpr (DT == LF_U8) {
+                // colour bytes scale by 1/255 through T (one multiply per
+                // texel instead of three); alpha keeps A = byte / 255
+                constexpr float s = 1.0f / 255.0f;
+                const uint32_t u = lds_u32(row + min((uint32_t)ix, maxi) * 4u);
+                const float Ts = T * s;
+                acc[jj][0] = fmaf(Ts, u8_byte<0>(u), acc[jj][0]);
+                acc[jj][1] = fmaf(Ts, u8_byte<1>(u), acc[jj][1]);
+                acc[jj][2] = fmaf(Ts, u8_byte<2>(u), acc[jj][2]);
+                acc[jj][3] = fmaf(-T, u8_byte<3>(u) * s, T);
+            } else {
+                const float4 t = TX_::load(row, min((uint32_t)ix, maxi));
+                acc[jj][0] = fmaf(T, t.x, acc[jj][0]);
+                acc[jj][1] = fmaf(T, t.y, acc[jj][1]);
+                acc[jj][2] = fmaf(T, t.z, acc[jj][2]);
+                acc[jj][3] = fmaf(-T, t.w, T);
+            }
         }
     } else {
         float fy = __fmaf_rn(c[1], tg.yf, c[2]);

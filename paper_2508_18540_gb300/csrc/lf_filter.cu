@@ -37,12 +37,7 @@ template <int DT>
 __device__ __forceinline__ float4 ld(const void* p, size_t i)
 {
     if (DT == LF_F32) return reinterpret_cast<const float4*>(p)[i];
-    if (DT == LF_U8) {
-        const uint32_t u = reinterpret_cast<const uint32_t*>(p)[i];
-        constexpr float s = 1.0f / 255.0f;
-        return make_float4((float)(u & 0xffu) * s, (float)((u >> 8) & 0xffu) * s, (float)((u >> 16) & 0xffu) * s,
-                           (float)(u >> 24) * s);
-    }
+    if (DT == LF_U8) return u8_unpack(reinterpret_cast<const uint32_t*>(p)[i]);
     const uint2 u = reinterpret_cast<const uint2*>(p)[i];
     if (DT == LF_F16) {
         const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
@@ -60,9 +55,7 @@ __device__ __forceinline__ void st(void* p, size_t i, float4 v)
     if (DT == LF_F32) {
         reinterpret_cast<float4*>(p)[i] = v;
     } else if (DT == LF_U8) {
-        const uint32_t q0 = __float2uint_rn(__saturatef(v.x) * 255.0f), q1 = __float2uint_rn(__saturatef(v.y) * 255.0f);
-        const uint32_t q2 = __float2uint_rn(__saturatef(v.z) * 255.0f), q3 = __float2uint_rn(__saturatef(v.w) * 255.0f);
-        reinterpret_cast<uint32_t*>(p)[i] = q0 | (q1 << 8) | (q2 << 16) | (q3 << 24);
+        reinterpret_cast<uint32_t*>(p)[i] = u8_pack(v.x, v.y, v.z, v.w);
     } else if (DT == LF_F16) {
         const __half2 lo = __floats2half2_rn(v.x, v.y), hi = __floats2half2_rn(v.z, v.w);
         uint2 u;

@@ -27,6 +27,37 @@ constexpr uint64_t kInvalidKey = ~0ull;
 // bytes of one RGBA texel of a plane type
 inline int texel_bytes(int dtype) { return dtype == LF_F32 ? 16 : dtype == LF_U8 ? 4 : 8; }
 
+// ---- RGBA8 unorm codec (exact, no conversion-unit instructions) -------------
+// decode: byte k of u placed under the exponent of 2^23 reads 2^23 + byte;
+//         subtracting 2^23 leaves the byte as an exact FP32 integer.
+// encode: round(255 clamp(v, 0, 1)) to nearest even is the low byte of the
+//         FP32 sum fl(255 clamp(v)) + 2^23, whose ulp there is 1.
+#ifdef __CUDACC__
+template <int K>
+__device__ __forceinline__ float u8_byte(uint32_t u)
+{
+    return __int_as_float((int)__byte_perm(u, 0x4B000000u, 0x7440u | (uint32_t)K)) - 8388608.0f;
+}
+
+__device__ __forceinline__ float4 u8_unpack(uint32_t u)
+{
+    constexpr float s = 1.0f / 255.0f;
+    return make_float4(u8_byte<0>(u) * s, u8_byte<1>(u) * s, u8_byte<2>(u) * s, u8_byte<3>(u) * s);
+}
+
+__device__ __forceinline__ uint32_t u8_code(float v)
+{
+    return __float_as_uint(__fadd_rn(__fmul_rn(__saturatef(v), 255.0f), 8388608.0f));   // code in the low byte
+}
+
+__device__ __forceinline__ uint32_t u8_pack(float r, float g, float b, float a)
+{
+    const uint32_t lo = __byte_perm(u8_code(r), u8_code(g), 0x0040u);   // [r, g, r, r]
+    const uint32_t hi = __byte_perm(u8_code(b), u8_code(a), 0x0040u);   // [b, a, b, b]
+    return __byte_perm(lo, hi, 0x5410u);                                // [r, g, b, a]
+}
+#endif
+
 // ---- launch counting and stage tracing ------------------------------------
 // Every kernel launch of the library bumps a process-wide counter; when
 // tracing is on, each pipeline stage is bracketed by a CUDA event pair on the

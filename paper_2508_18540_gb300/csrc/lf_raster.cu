@@ -29,9 +29,7 @@ __device__ __forceinline__ void store_texel(void* planes, size_t idx, float r, f
         reinterpret_cast<float4*>(planes)[idx] = make_float4(r, g, b, a);
     } else if (DT == LF_U8) {
         // RGBA8 unorm: round(255 clamp(v, 0, 1)) per channel
-        const uint32_t q0 = __float2uint_rn(__saturatef(r) * 255.0f), q1 = __float2uint_rn(__saturatef(g) * 255.0f);
-        const uint32_t q2 = __float2uint_rn(__saturatef(b) * 255.0f), q3 = __float2uint_rn(__saturatef(a) * 255.0f);
-        reinterpret_cast<uint32_t*>(planes)[idx] = q0 | (q1 << 8) | (q2 << 16) | (q3 << 24);
+        reinterpret_cast<uint32_t*>(planes)[idx] = u8_pack(r, g, b, a);
     } else if (DT == LF_F16) {
         const __half2 lo = __floats2half2_rn(r, g), hi = __floats2half2_rn(b, a);
         uint2 u;
