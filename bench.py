@@ -49,8 +49,8 @@ def _config(extra=None):
 # (profiles/k_*_g2lf_display_1M_512px_N64_45v.md), valid only while the
 # kernel's sources hash to the value recorded with them.
 NCU_TRAFFIC = {
-    "raster_gaussians": (71_813_120 + 210_758_144, ("lf_raster.cu", "lf_internal.cuh"), "934a46caca68d149"),
-    "composite": (253_724_160 + 157_447_424, ("lf_composite.cu", "lf_internal.cuh"), "578019e2eb58df9d"),
+    "raster_gaussians": (71_787_776 + 210_689_280, ("lf_raster.cu", "lf_internal.cuh"), "d098eb214691b03c"),
+    "composite": (253_843_200 + 159_061_760, ("lf_composite.cu", "lf_internal.cuh"), "abca58235e63d3e9"),
 }
 
 
