@@ -5,15 +5,18 @@
 //  - the depth sort of Algorithm 1 line 3 ("Sort_and_Chunk"): the order of
 //    the culled-in primitives by (FP64 depth, index). The IEEE bits of a
 //    positive FP64 depth order like the depth; relative to the smallest valid
-//    key they span up to ~55 bits. The sort takes their top 31 varying bits
+//    key they span up to ~55 bits. The sort takes their top 24 varying bits
 //    (an order-preserving truncation) as a 32-bit key, drops culled
-//    primitives in the first pass and sorts stably in four passes (values
-//    start in index order, so equal keys stay in index order). Keys that
-//    share the truncated value form runs that are then put in (full key,
-//    index) order: runs of up to 32 by one thread (insertion), longer runs by
-//    one CTA each (Batcher's odd-even merge network, in shared memory up to
-//    2048 keys, in global memory beyond). Realistic scenes have almost no
-//    runs; the run pass keeps the order exact for any input.
+//    primitives in the first pass and sorts stably in three passes (the
+//    first pass takes each key's index as its value, so equal keys stay in
+//    index order). Keys that share the truncated value form runs that are
+//    then put in (full key, index) order: runs of up to 32 by one thread
+//    (insertion), longer runs by one CTA each (Batcher's odd-even merge
+//    network, in shared memory up to 2048 keys, in global memory beyond).
+//    The run pass keeps the order exact for any input; 24 bits trade a
+//    fourth pass for short runs (1M Gaussians over depths 1.5..10: runs of at
+//    most 5 keys, 12k pairs to reorder; grid-aligned voxels: runs of equal
+//    full keys, already in order).
 //  - the 3D tiling (Sec. 4.4): 32-bit keys = tile id of every (tile, rank)
 //    pair emitted in rank order; the stable sort groups the pairs by tile and
 //    keeps each tile's pairs in depth order.
@@ -37,7 +40,9 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kBits = 8;
 constexpr int kDigits = 1 << kBits;             // 256 = one digit per thread
-constexpr int kKPT = kRadixBlockKeys / kThreads; // 16 keys per thread
+constexpr int kKPT = kRadixBlockKeys / kThreads; // 8 keys per thread
+constexpr int kDepthKeyBits = 24;                // truncated depth key width
+constexpr int kDepthPasses = (kDepthKeyBits + kBits - 1) / kBits;
 static_assert(kDigits == kThreads, "one digit per thread in the digit scans");
 
 struct PassArgs {
@@ -46,7 +51,7 @@ struct PassArgs {
     const unsigned long long* kmin;        // valid depth-key range (depth sort) or null
     const unsigned long long* kmax;
     int shift;
-    int first;                             // depth sort: drop the invalid key (all ones)
+    int first;                             // depth sort: drop the invalid key (all ones); value = index
     int nb;                                // number of blocks (histogram stride)
 };
 
@@ -55,13 +60,13 @@ __device__ __forceinline__ long long pass_count(const PassArgs& a)
     return a.n_dev ? (long long)*a.n_dev : a.n_static;
 }
 
-// Right shift that keeps the top 31 varying bits of a depth key relative to
-// the smallest valid key (0 if the range already fits).
+// Right shift that keeps the top kDepthKeyBits varying bits of a depth key
+// relative to the smallest valid key (0 if the range already fits).
 __device__ __forceinline__ int depth_shift(unsigned long long lo, unsigned long long hi)
 {
     if (lo > hi) return 0;
     const int bits = 64 - __clzll((long long)(hi - lo));
-    return bits > 31 ? bits - 31 : 0;
+    return bits > kDepthKeyBits ? bits - kDepthKeyBits : 0;
 }
 
 // every valid truncated depth key has the same digit at this shift: identity pass
@@ -252,7 +257,7 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const K* __restrict__ ki
         K k = 0;
         const bool ok = load_key(kin, idx, n, a, k);
         key[r] = k;
-        val[r] = ok ? vin[idx] : 0u;
+        val[r] = ok ? (a.first ? (uint32_t)idx : vin[idx]) : 0u;
         okm |= ok ? (1u << r) : 0u;
     }
 #pragma unroll
@@ -469,11 +474,12 @@ void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s)
 {
     if (n <= 0) return;
     const int nb = (int)((n + kRadixBlockKeys - 1) / kRadixBlockKeys);
-    k_depth_key32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws.keyA, ws.tkeyA, n, ws.hdr);
     uint32_t* kb[2] = {ws.tkeyA, ws.tkeyB};
     uint32_t* vb[2] = {ws.valA, ws.valB};
-    int cur = 0;
-    for (int pass = 0; pass < 32 / kBits; ++pass) {
+    // start in the buffer that makes the last pass end in tkeyA / valA
+    int cur = kDepthPasses & 1;
+    k_depth_key32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws.keyA, kb[cur], n, ws.hdr);
+    for (int pass = 0; pass < kDepthPasses; ++pass) {
         PassArgs a;
         a.n_static = n;
         a.n_dev = pass == 0 ? nullptr : &ws.hdr->M;
@@ -485,7 +491,7 @@ void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s)
         radix_pass<uint32_t>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], a, ws.hist, ws.dtot, s);
         cur ^= 1;
     }
-    // four passes: truncated keys in tkeyA, ranks in valA; now the runs
+    // truncated keys in tkeyA, ranks in valA; now the runs
     k_depth_bad<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws);
     k_depth_runs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws);
     k_depth_long_runs<<<kLongRunCtas, kLongRunThreads, 0, s>>>(ws);

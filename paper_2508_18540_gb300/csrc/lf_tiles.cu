@@ -154,43 +154,32 @@ __global__ void __launch_bounds__(kT) k_dup_emit(BuildWs w, int supers_x)
     }
 }
 
-// chunk of a rank: the last chunk whose first rank is not above it (binary
-// search over the N chunk starts, which stay in L1)
-__device__ __forceinline__ int chunk_of(const int* __restrict__ start, int N, uint32_t rank)
-{
-    int lo = 0, hi = N - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if ((uint32_t)__ldg(start + mid) <= rank)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
 // Entry i starts a (super-tile, chunk) list when its super-tile or chunk
-// differs from entry i - 1's; it then also ends the list of entry i - 1.
+// differs from entry i - 1's; it then also ends the list of entry i - 1. A
+// warp takes 32 consecutive entries: the chunk of an entry's rank comes from
+// the rank-ordered chunk array, the previous entry's from the lane below.
 __global__ void __launch_bounds__(256) k_ranges(BuildWs w, const uint32_t* __restrict__ keys,
                                                 const uint32_t* __restrict__ ranks, int N)
 {
-    const int* s_start = w.chunk_start;
     const long long n = (long long)w.hdr->tile_n;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const uint32_t t = keys[i];
-        const int c = chunk_of(s_start, N, ranks[i]);
-        bool first = i == 0;
-        long long pidx = -1;
-        if (!first) {
-            const uint32_t tp = keys[i - 1];
-            const int cp = chunk_of(s_start, N, ranks[i - 1]);
-            first = tp != t || cp != c;
-            pidx = (long long)tp * N + cp;
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x - lane); i0 < n; i0 += stride) {
+        const long long i = i0 + lane;
+        const bool in = i < n;
+        const uint32_t t = in ? keys[i] : 0u;
+        const int c = in ? w.r_chunk[ranks[i]] : 0;
+        uint32_t tp = __shfl_up_sync(0xffffffffu, t, 1);
+        int cp = __shfl_up_sync(0xffffffffu, c, 1);
+        if (lane == 0 && in && i > 0) {
+            tp = keys[i - 1];
+            cp = w.r_chunk[ranks[i - 1]];
         }
+        if (!in) continue;
+        const bool first = i == 0 || tp != t || cp != c;
         if (first) {
             w.seg[(long long)t * N + c].x = (int)i;
-            if (pidx >= 0) w.seg[pidx].y = (int)i;
+            if (i > 0) w.seg[(long long)tp * N + cp].y = (int)i;
         }
         if (i == n - 1) w.seg[(long long)t * N + c].y = (int)n;
     }
