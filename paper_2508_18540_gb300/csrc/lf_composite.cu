@@ -1014,6 +1014,7 @@ void launch_composite_t(const CompParams& p, const void* planes, const int32_t* 
 // transmittance is recomputed, never stored.
 // ---------------------------------------------------------------------------
 
+constexpr int kBwdViews = 3;                          // views per thread of the staged adjoint
 constexpr float kUpB = 18446744073709551616.0f;       // 2^64
 constexpr float kDownB = 5.42101086242752217e-20f;    // 2^-64
 constexpr float kBigB = 4294967296.0f;                // 2^32
@@ -1142,6 +1143,335 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite_bwd(CompParams p
     }
 }
 
+// ---------------------------------------------------------------------------
+// Staged adjoint: the forward staged layout (a CTA owns BY output rows x TX
+// columns for VG views of one view row; one producer lane streams the plane
+// rows those pixels sample into the shared-memory ring) run twice: the list
+// of non-empty planes front to back to carry every view's transmittance to
+// the far end (alpha only; T before its first opaque plane is noted), then
+// back to front for the B recurrence, the T recovery by division and the
+// texel gradients (FP32 vector atomics into dplanes, as the unstaged
+// kernel). The row geometry of a plane is computed once per thread, the
+// views' horizontal taps per view. The ring counts 2P planes; every wait is
+// bounded, and a wait that gives up sets the error word and ends the walk.
+// ---------------------------------------------------------------------------
+template <int DT>
+__device__ __forceinline__ float texel_alpha(uint32_t row, uint32_t i);
+template <>
+__device__ __forceinline__ float texel_alpha<LF_F32>(uint32_t row, uint32_t i)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(row + i * 16u + 12u));
+    return v;
+}
+template <>
+__device__ __forceinline__ float texel_alpha<LF_F16>(uint32_t row, uint32_t i)
+{
+    unsigned short h;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(h) : "r"(row + i * 8u + 6u));
+    return __half2float(__ushort_as_half(h));
+}
+template <>
+__device__ __forceinline__ float texel_alpha<LF_BF16>(uint32_t row, uint32_t i)
+{
+    unsigned short h;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(h) : "r"(row + i * 8u + 6u));
+    return __uint_as_float((uint32_t)h << 16);
+}
+template <>
+__device__ __forceinline__ float texel_alpha<LF_U8>(uint32_t row, uint32_t i)
+{
+    return u8_byte<3>(lds_u32(row + i * 4u)) * (1.0f / 255.0f);
+}
+
+// T = m 2^-e (e a multiple of 64): m, m 2^-64, or below 2^-96 (taken as 0)
+__device__ __forceinline__ float scaled_t(float m, int e) { return e == 0 ? m : (e == 64 ? m * kDownB : 0.0f); }
+
+template <int DT, bool BILINEAR, int VG>
+__global__ void __launch_bounds__(kStagedBlock, 2) k_composite_bwd_staged(CompParams p, StagedGeom G,
+                                                                            const char* __restrict__ planes,
+                                                                            const int32_t* __restrict__ count,
+                                                                            CompWs w,
+                                                                            const float4* __restrict__ dviews,
+                                                                            float4* __restrict__ dplanes)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    // [kStages][rows][row_bytes] | full[kStages] | empty[kStages] | coef [N][CW] | plist [N]
+    constexpr int CW = CoefBlock<VG>::kFloats;
+    constexpr int NC = 4 * ((VG + 3) / 4);
+    using TX_ = Texel<DT>;
+    unsigned char* stage_base = smem;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * G.stage_bytes);
+    uint64_t* empty = full + kStages;
+    float* coef = reinterpret_cast<float*>(empty + kStages);
+    int* plist = reinterpret_cast<int*>(coef + (size_t)p.N * CW);
+    __shared__ int s_nplanes;
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int vgroup = blockIdx.x;
+    const int vi = vgroup / G.groups_x;
+    const int j0 = (vgroup % G.groups_x) * VG;
+    const int Y0 = blockIdx.y * G.BY;
+    const int X0 = blockIdx.z * G.TX;
+    const int tx = tid % G.TX, ty = tid / G.TX;
+    const int x = X0 + tx, y = Y0 + ty;
+
+    if (tid < 32) {
+        const int n = plane_list(p, count, plist);
+        if (tid == 0) s_nplanes = n;
+    }
+    __syncthreads();
+    load_coefs<BILINEAR, VG>(p, w, plist, s_nplanes, vi, j0, coef);
+    zero_pads<DT>(p, G, stage_base, G.stage_bytes, kStages);
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) {
+            mbar_init(smem_addr(&full[st]), 1);
+            mbar_init(smem_addr(&empty[st]), kStagedWarps);
+        }
+        fence_proxy_async();
+    }
+    __syncthreads();
+    const int P = s_nplanes;
+    // ring slot q < P holds list entry q, slot q >= P list entry 2P - 1 - q
+    auto entry = [&](int q) { return q < P ? q : 2 * P - 1 - q; };
+
+    if (tid >= kStagedThreads) {
+        if (tid == kStagedThreads) {
+            for (int q = 0; q < 2 * P; ++q) {
+                const int st = q % kStages;
+                if (q >= kStages &&
+                    !mbar_wait_bounded(smem_addr(&empty[st]), (uint32_t)(((q / kStages) - 1) & 1))) {
+                    atomicExch(w.err, 1);
+                    break;
+                }
+                const int e = entry(q);
+                produce_rows<DT>(p, G, planes, plist[e], coef + (size_t)e * CW, Y0,
+                                 stage_base + (size_t)st * G.stage_bytes, smem_addr(&full[st]));
+            }
+        }
+        return;
+    }
+
+    const bool live = ty < G.BY && x < p.Nx && y < p.Ny;
+    const ThreadGeom tg = thread_geom(p, G, x, y, ty);
+    const uint32_t stage_a = smem_addr(stage_base), coef_a = smem_addr(coef);
+    const size_t plane_sz = (size_t)p.W * p.H;
+    const uint32_t Wu = (uint32_t)p.W, padl = (uint32_t)G.padl;
+
+    // per plane: the view offsets c[] and the vertical sample (nearest row
+    // iy, or rows y0, y0 + 1 with weights w0, w1; a weight is 0 off the plane)
+    auto load_c = [&](int e, float (&c)[NC]) {
+#pragma unroll
+        for (int m = 0; m < NC / 4; ++m) {
+            const float4 v = lds_f4(coef_a + 4u * (uint32_t)(e * CW + 4 + 4 * m));
+            c[4 * m + 0] = v.x;
+            c[4 * m + 1] = v.y;
+            c[4 * m + 2] = v.z;
+            c[4 * m + 3] = v.w;
+        }
+    };
+    // padded horizontal index (bits of the magic floor + base) and, for
+    // bilinear, the fractional weight
+    auto hindex = [&](float4 hdr, float cj, float& wx) -> int {
+        float fx = __fmaf_rn(hdr.x, tg.xf, cj);
+        if (__float_as_int(hdr.w)) fx = fminf(fmaxf(fx, -kClamp), kClamp);
+        const float tm = __fadd_rd(fx, kMagic);
+        wx = fx - (tm - kMagic);
+        return __float_as_int(tm) + tg.base_x;
+    };
+
+    float Tm[VG], oTm[VG];
+    int Te[VG], oTe[VG], okq[VG];
+#pragma unroll
+    for (int jj = 0; jj < VG; ++jj) Tm[jj] = 1.f, oTm[jj] = 0.f, Te[jj] = 0, oTe[jj] = 0, okq[jj] = -1;
+    int q = 0;
+    // front to back: transmittance at the far end, and T before the first
+    // opaque plane (alpha only)
+    for (; q < P; ++q) {
+        const int st = q % kStages;
+        if (!mbar_wait_bounded(smem_addr(&full[st]), (uint32_t)((q / kStages) & 1))) {
+            atomicExch(w.err, 1);
+            return;
+        }
+        if (live) {
+            const uint32_t sb = stage_a + (uint32_t)(st * G.stage_bytes) + tg.row0;
+            const float4 hdr = lds_f4(coef_a + 4u * (uint32_t)(q * CW));
+            float c[NC];
+            load_c(q, c);
+            float w0 = 0.f, w1 = 0.f;
+            bool rv = false;
+            if (!BILINEAR) {
+                const int iy = tg.psy + (__float_as_int(floor_magic<true>(hdr.y, tg.yf, hdr.z)) - kMagicBits);
+                rv = iy >= 0 && iy < tg.H;
+            } else {
+                float fy = fminf(fmaxf(__fmaf_rn(hdr.y, tg.yf, hdr.z), -kClamp), kClamp);
+                const float ty_m = __fadd_rd(fy, kMagic);
+                const float wy = fy - (ty_m - kMagic);
+                const int y0 = tg.psy + (__float_as_int(ty_m) - kMagicBits);
+                w0 = (y0 >= 0 && y0 < tg.H) ? 1.0f - wy : 0.0f;
+                w1 = (y0 + 1 >= 0 && y0 + 1 < tg.H) ? wy : 0.0f;
+            }
+#pragma unroll
+            for (int jj = 0; jj < VG; ++jj) {
+                float wx;
+                const int ip = hindex(hdr, c[jj], wx);
+                float a = 0.0f;
+                if (!BILINEAR) {
+                    if (rv && (uint32_t)ip - padl < Wu) a = texel_alpha<DT>(sb, (uint32_t)ip);
+                } else {
+                    const bool c0 = (uint32_t)ip - padl < Wu, c1 = (uint32_t)ip + 1u - padl < Wu;
+                    const float wa = 1.0f - wx;
+                    if (w0 != 0.0f) {
+                        const float a0 = c0 ? texel_alpha<DT>(sb, (uint32_t)ip) : 0.f;
+                        const float a1 = c1 ? texel_alpha<DT>(sb, (uint32_t)ip + 1u) : 0.f;
+                        a = w0 * fmaf(wa, a0, wx * a1);
+                    }
+                    if (w1 != 0.0f) {
+                        const uint32_t r1 = sb + tg.row_bytes;
+                        const float a0 = c0 ? texel_alpha<DT>(r1, (uint32_t)ip) : 0.f;
+                        const float a1 = c1 ? texel_alpha<DT>(r1, (uint32_t)ip + 1u) : 0.f;
+                        a = fmaf(w1, fmaf(wa, a0, wx * a1), a);
+                    }
+                }
+                const float oma = 1.0f - a;
+                if (!(oma > 0.0f) && Tm[jj] > 0.0f && okq[jj] < 0) {
+                    oTm[jj] = Tm[jj];
+                    oTe[jj] = Te[jj];
+                    okq[jj] = q;
+                }
+                Tm[jj] = Tm[jj] * oma;
+                if (Tm[jj] < kDownB && Tm[jj] > 0.0f) {
+                    Tm[jj] *= kUpB;
+                    Te[jj] += 64;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&empty[st]));
+    }
+    float4 g[VG];
+    float B[VG];
+#pragma unroll
+    for (int jj = 0; jj < VG; ++jj) {
+        const bool vv = live && j0 + jj < p.Vx;   // padding views of a ragged group get no gradient
+        g[jj] = vv ? dviews[view_pixel(p, vi * p.Vx + j0 + jj, x, y)] : make_float4(0.f, 0.f, 0.f, 0.f);
+        B[jj] = fmaf(g[jj].x, p.bg[0], fmaf(g[jj].y, p.bg[1], fmaf(g[jj].z, p.bg[2], -g[jj].w)));
+    }
+    // back to front: T recovered by division, texel gradients, B recurrence
+    for (; q < 2 * P; ++q) {
+        const int st = q % kStages;
+        if (!mbar_wait_bounded(smem_addr(&full[st]), (uint32_t)((q / kStages) & 1))) {
+            atomicExch(w.err, 1);
+            return;
+        }
+        if (live) {
+            const int e = entry(q);
+            const uint32_t sb = stage_a + (uint32_t)(st * G.stage_bytes) + tg.row0;
+            const float4 hdr = lds_f4(coef_a + 4u * (uint32_t)(e * CW));
+            float c[NC];
+            load_c(e, c);
+            float4* dk = dplanes + (size_t)plist[e] * plane_sz;
+            float w0 = 0.f, w1 = 0.f, wy = 0.f;
+            bool rv = false;
+            int yrow = 0;
+            if (!BILINEAR) {
+                yrow = tg.psy + (__float_as_int(floor_magic<true>(hdr.y, tg.yf, hdr.z)) - kMagicBits);
+                rv = yrow >= 0 && yrow < tg.H;
+            } else {
+                float fy = fminf(fmaxf(__fmaf_rn(hdr.y, tg.yf, hdr.z), -kClamp), kClamp);
+                const float ty_m = __fadd_rd(fy, kMagic);
+                wy = fy - (ty_m - kMagic);
+                yrow = tg.psy + (__float_as_int(ty_m) - kMagicBits);
+                w0 = (yrow >= 0 && yrow < tg.H) ? 1.0f - wy : 0.0f;
+                w1 = (yrow + 1 >= 0 && yrow + 1 < tg.H) ? wy : 0.0f;
+            }
+            float4* drow = dk + ((long long)yrow * p.W - (long long)padl);   // indexed by padded column
+#pragma unroll
+            for (int jj = 0; jj < VG; ++jj) {
+                float wx;
+                const int ip = hindex(hdr, c[jj], wx);
+                float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool c0 = (uint32_t)ip - padl < Wu;
+                const bool c1 = BILINEAR && (uint32_t)ip + 1u - padl < Wu;
+                const float wa = 1.0f - wx;
+                if (!BILINEAR) {
+                    if (rv && c0) t = TX_::load(sb, (uint32_t)ip);
+                } else {
+                    if (w0 != 0.0f) {
+                        const float4 t0 = c0 ? TX_::load(sb, (uint32_t)ip) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 t1 = c1 ? TX_::load(sb, (uint32_t)ip + 1u) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        t.x = w0 * fmaf(wa, t0.x, wx * t1.x);
+                        t.y = w0 * fmaf(wa, t0.y, wx * t1.y);
+                        t.z = w0 * fmaf(wa, t0.z, wx * t1.z);
+                        t.w = w0 * fmaf(wa, t0.w, wx * t1.w);
+                    }
+                    if (w1 != 0.0f) {
+                        const uint32_t r1 = sb + tg.row_bytes;
+                        const float4 t0 = c0 ? TX_::load(r1, (uint32_t)ip) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 t1 = c1 ? TX_::load(r1, (uint32_t)ip + 1u) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        t.x = fmaf(w1, fmaf(wa, t0.x, wx * t1.x), t.x);
+                        t.y = fmaf(w1, fmaf(wa, t0.y, wx * t1.y), t.y);
+                        t.z = fmaf(w1, fmaf(wa, t0.z, wx * t1.z), t.z);
+                        t.w = fmaf(w1, fmaf(wa, t0.w, wx * t1.w), t.w);
+                    }
+                }
+                const float oma = 1.0f - t.w;
+                if (e == okq[jj]) {
+                    Tm[jj] = oTm[jj];
+                    Te[jj] = oTe[jj];
+                } else if (oma > 0.0f) {
+                    Tm[jj] = __fdividef(Tm[jj], oma);
+                    if (Te[jj] > 0 && Tm[jj] > kBigB) {
+                        Tm[jj] *= kDownB;
+                        Te[jj] -= 64;
+                    }
+                }
+                const float Tk = scaled_t(Tm[jj], Te[jj]);
+                if (Tk > 0.0f) {
+                    const float4 gt = make_float4(Tk * g[jj].x, Tk * g[jj].y, Tk * g[jj].z, -Tk * B[jj]);
+                    if (!BILINEAR) {
+                        if (rv && c0) atomicAdd(drow + ip, gt);
+                    } else {
+                        const float ww[4] = {w0 * wa, w0 * wx, w1 * wa, w1 * wx};
+                        const bool ok4[4] = {w0 != 0.0f && c0, w0 != 0.0f && c1, w1 != 0.0f && c0, w1 != 0.0f && c1};
+#pragma unroll
+                        for (int m = 0; m < 4; ++m)
+                            if (ok4[m])
+                                atomicAdd(drow + (m >> 1) * p.W + ip + (m & 1),
+                                          make_float4(ww[m] * gt.x, ww[m] * gt.y, ww[m] * gt.z, ww[m] * gt.w));
+                    }
+                }
+                B[jj] = fmaf(t.x, g[jj].x, fmaf(t.y, g[jj].y, fmaf(t.z, g[jj].z, oma * B[jj])));
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&empty[st]));
+    }
+}
+
+template <int DT, bool BILINEAR, int VG>
+bool launch_bwd_staged_vg(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
+                          const float4* dviews, float4* dplanes, cudaStream_t s)
+{
+    constexpr int TB = Texel<DT>::kBytes;
+    StagedGeom G = staged_geom(p, TB, BILINEAR, VG, 512);
+    // no blended rows here: the full ring
+    G.blend_bytes = 0;
+    G.stages = kStages;
+    G.smem_bytes = kStages * G.stage_bytes + 2 * kStages * 8 + sizeof(float) * (size_t)p.N * CoefBlock<VG>::kFloats +
+                   sizeof(int) * (size_t)p.N;
+    if (G.smem_bytes > 200 * 1024) return false;
+    if (((uintptr_t)planes) % 16 != 0 || ((size_t)p.W * TB) % 16 != 0) return false;
+    auto kern = k_composite_bwd_staged<DT, BILINEAR, VG>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem_bytes) != cudaSuccess)
+        return false;
+    const dim3 grid((unsigned)(G.groups_x * p.Vy), (unsigned)((p.Ny + G.BY - 1) / G.BY),
+                    (unsigned)((p.Nx + G.TX - 1) / G.TX));
+    kern<<<grid, kStagedBlock, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, dviews, dplanes);
+    note_launches(1);
+    return true;
+}
+
 template <int DT>
 void launch_composite_bwd_t(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
                             const float* dviews, float* dplanes, cudaStream_t s)
@@ -1152,6 +1482,11 @@ void launch_composite_bwd_t(const CompParams& p, const void* planes, const int32
     const size_t smem = sizeof(float) * 6 * p.N + sizeof(int) * p.N;
     const float4* dv = reinterpret_cast<const float4*>(dviews);
     float4* dp = reinterpret_cast<float4*>(dplanes);
+    if (p.N <= 4096) {
+        const bool ok = p.bilinear ? launch_bwd_staged_vg<DT, true, kBwdViews>(p, planes, count, ws, dv, dp, s)
+                                   : launch_bwd_staged_vg<DT, false, kBwdViews>(p, planes, count, ws, dv, dp, s);
+        if (ok) return;
+    }
     if (p.bilinear) {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k_composite_bwd<DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
