@@ -276,3 +276,34 @@ def test_autograd_function_and_fit_step():
             opa.clamp_(0.01, 0.99)
         losses.append(float(l2.detach()))
     assert losses[-1] < 0.8 * losses[0], losses
+
+
+@pytest.mark.parametrize("dtype", ["f16", "u8"])
+@pytest.mark.parametrize("bilinear", [False, True])
+def test_staged_and_unstaged_composite_adjoints_agree(dtype, bilinear):
+    # The staged adjoint (plane rows streamed through shared memory) runs when
+    # plane rows start on 16-byte boundaries; a copy of the same planes one
+    # texel off that boundary takes the unstaged adjoint. Both must give the
+    # same dplanes up to FP32 rounding (T recovery, atomic summation order).
+    w = _fd_scene(seed=7, n=3000, res=64, N=8)
+    views = S.ViewSet(7, 1, bilinear, (0.2, 0.1, 0.3))
+    r = api.LightFieldRenderer(w.camera, w.display, views, w.N, w.binning, dtype)
+    r.render(api.DeviceGaussians.from_scene(w.scene))
+    pl = r.planes
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    dv = torch.randn((7, w.camera.Ny, w.camera.Nx, 4), device="cuda", generator=gen)
+    shape = tuple(pl.rgba.shape)
+    dp_staged = torch.empty(shape, dtype=torch.float32, device="cuda")
+    api.lf_composite_backward(pl, r.ref, views, dv, dp_staged, r.cws)
+    n_tex = shape[0] * shape[1] * shape[2]
+    flat = torch.empty((n_tex + 1, 4), dtype=pl.rgba.dtype, device="cuda")
+    moved = flat[1:].view(shape)
+    moved.copy_(pl.rgba)
+    assert moved.data_ptr() % 16 != 0
+    pl2 = api.Planes(moved, pl.d, pl.count, pl.chunk, pl.rect, pl.dtype_code)
+    dp_unstaged = torch.empty(shape, dtype=torch.float32, device="cuda")
+    api.lf_composite_backward(pl2, r.ref, views, dv, dp_unstaged, r.cws)
+    torch.cuda.synchronize()
+    scale = float(dp_staged.abs().max())
+    assert scale > 0.0
+    assert float((dp_staged - dp_unstaged).abs().max()) <= 2e-5 * scale
