@@ -191,7 +191,7 @@ def test_host_pipeline_frames_match_synchronous_renders(graphs):
 def test_depth_order_with_near_equal_depths(orc):
     # A camera turned by 1e-9 rad about y gives depth = z - 1e-9 x (FP64), so
     # Gaussians sharing z but not x differ in depth by ~1e-13: far below the
-    # 31 bits the depth sort keeps of the key range. Clusters of 5000, 40 and
+    # 24 bits the depth sort keeps of the key range. Clusters of 5000, 40 and
     # 10 such Gaussians (shuffled) exercise all three run fix-ups (global
     # memory network, shared memory network, insertion); the order must
     # still equal the oracle's (FP64 depth, index) order exactly.
