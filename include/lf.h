@@ -316,10 +316,11 @@ lf_status lf_build_mpi_backward_voxels(const lf_voxels* v, const lf_ref_camera* 
  * persistent raster launch covers the (tile, chunk) items of every scene and
  * ONE persistent staged-composite launch covers the (view group, row band,
  * column tile) items of every scene, CTAs pulling items from a global
- * counter. The whole batch can be captured once into a CUDA graph and
- * relaunched per frame. An autotuner times candidate plans (views per
- * thread, composite tile shape, raster pixels per thread, scene schedule)
- * on the batch itself. Results are identical for every plan.
+ * counter; or (schedule 2) every scene's single-scene pipeline runs on a
+ * stream of its own, all in parallel. The whole batch can be captured once
+ * into a CUDA graph and relaunched per frame. An autotuner times candidate
+ * plans (views per thread, composite tile shape, raster pixels per thread,
+ * scene schedule) on the batch itself. Results are identical for every plan.
  */
 
 /* One scene of a batch. Every pointer is device memory the caller owns and
@@ -345,7 +346,11 @@ typedef struct {
  *  tile_x            composite CTA tile width (columns): 128, 256 or 512
  *                    (the tile is tile_x x 512/tile_x pixels);
  *  raster_ppt        raster pixels per thread: 2 or 4;
- *  schedule          0: items in scene order; 1: largest scenes first. */
+ *  schedule          0: items in scene order; 1: largest scenes first;
+ *                    2: no persistent launches -- every scene's own
+ *                    lf_build_mpi_gaussians + lf_composite on a stream of its
+ *                    own, forked from and joined back into the caller's
+ *                    stream (the other fields are then unused). */
 typedef struct {
     int32_t views_per_thread;
     int32_t tile_x;
@@ -381,7 +386,8 @@ lf_status lf_batch_capture(lf_batch* b, cudaStream_t stream);
 lf_status lf_batch_launch(lf_batch* b, cudaStream_t stream);
 
 /* Times every candidate plan (coordinate search: composite views per thread
- * x tile width, then raster pixels per thread x schedule), reps frames each
+ * x tile width, then raster pixels per thread x schedules 0 and 1, then
+ * schedule 2), reps frames each
  * after one warm-up frame, with CUDA events on stream; leaves b prepared with
  * the fastest plan and returns it in *best (host) and its mean frame time in
  * *best_ms (host, may be NULL). Synchronises the stream. */

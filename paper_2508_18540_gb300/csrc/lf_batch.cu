@@ -1,6 +1,8 @@
 // lf_batch.cu -- several G2LF scenes in one frame: per-scene builds up to the
 // tile lists, then one persistent raster launch and one persistent staged
-// composite launch over the work items of every scene, CUDA-graph capture of
+// composite launch over the work items of every scene (schedules 0 and 1),
+// or every scene's own pipeline on a stream of its own, forked from and
+// joined back into the caller's stream (schedule 2); CUDA-graph capture of
 // the whole frame, and an autotuner over the launch plan.
 //
 // The method itself (Algorithm 1 per scene) is unchanged: a plan only
@@ -35,6 +37,10 @@ struct lf_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long graph_kernels = 0;              // kernels in one launch of the graph
+    // schedule 2: one stream per scene, a fork event and a join event per scene
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -92,8 +98,18 @@ lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, siz
     const lf_batch_plan pl = plan ? *plan : lf_batch_plan{9, 512, 2, 1};
     if ((pl.views_per_thread != 3 && pl.views_per_thread != 5 && pl.views_per_thread != 9) ||
         (pl.tile_x != 128 && pl.tile_x != 256 && pl.tile_x != 512) || (pl.raster_ppt != 2 && pl.raster_ppt != 4) ||
-        (pl.schedule != 0 && pl.schedule != 1))
+        (pl.schedule < 0 || pl.schedule > 2))
         return fail(LF_ERR_INVALID_ARG, "lf_batch_prepare: plan out of range");
+    if (pl.schedule == 2 && b->side.empty()) {
+        b->side.resize(b->sc.size(), nullptr);
+        b->done.resize(b->sc.size(), nullptr);
+        if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+            return check_launch("batch fork event");
+        for (size_t i = 0; i < b->sc.size(); ++i)
+            if (cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming) != cudaSuccess)
+                return check_launch("batch scene streams");
+    }
     const int n = (int)b->sc.size();
     if (!ws || ((uintptr_t)ws) % 256) return fail(LF_ERR_WORKSPACE, "batch workspace NULL or not 256-byte aligned");
     if (ws_bytes < batch_ws_bytes(n)) return fail(LF_ERR_WORKSPACE, "batch workspace too small");
@@ -135,7 +151,7 @@ lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, siz
         max_stage = std::max(max_stage, c[i].G.stage_bytes);
         maxN = std::max(maxN, s.N);
     }
-    if (composite_batched_smem(max_stage, maxN, pl.views_per_thread) > 200 * 1024)
+    if (pl.schedule != 2 && composite_batched_smem(max_stage, maxN, pl.views_per_thread) > 200 * 1024)
         return fail(LF_ERR_UNSUPPORTED, "lf_batch_prepare: the batch's largest plane row and N need more than "
                                         "200 KB of shared memory for the staged composite");
     // schedule: order of the scenes in the item tables
@@ -185,6 +201,24 @@ lf_status lf_batch_render(lf_batch* b, cudaStream_t stream)
 {
     if (!b || !b->prepared) return fail(LF_ERR_INVALID_ARG, "batch not prepared");
     lf_status st;
+    if (b->plan.schedule == 2) {
+        // every scene's single-scene pipeline on its own stream, all forked
+        // from and joined back into stream (captured as parallel branches)
+        if (cudaEventRecord(b->fork, stream) != cudaSuccess) return check_launch("batch fork");
+        for (size_t i = 0; i < b->sc.size(); ++i) {
+            lf_batch_scene& s = b->sc[i];
+            if (cudaStreamWaitEvent(b->side[i], b->fork, 0) != cudaSuccess) return check_launch("batch fork");
+            if ((st = lf_build_mpi_gaussians(&s.g, &s.ref, s.N, s.binning, s.ws, s.ws_bytes, &s.planes,
+                                             b->side[i])) != LF_OK)
+                return st;
+            if ((st = lf_composite(&s.planes, &s.ref, &s.views, s.out, s.cws, s.cws_bytes, b->side[i])) != LF_OK)
+                return st;
+            if (cudaEventRecord(b->done[i], b->side[i]) != cudaSuccess ||
+                cudaStreamWaitEvent(stream, b->done[i], 0) != cudaSuccess)
+                return check_launch("batch join");
+        }
+        return LF_OK;
+    }
     if (cudaMemsetAsync(b->counters, 0, 2 * sizeof(unsigned long long), stream) != cudaSuccess)
         return check_launch("batch counter reset");
     for (size_t i = 0; i < b->sc.size(); ++i) {
@@ -310,6 +344,12 @@ lf_status lf_batch_autotune(lf_batch* b, void* ws, size_t ws_bytes, int32_t reps
             st = time_plan(pl, &ms);
             if (st == LF_OK && ms < cur_ms) cur_ms = ms, cur = pl;
         }
+    if (st == LF_OK) {   // concurrent single-scene pipelines
+        lf_batch_plan pl{cur.views_per_thread, cur.tile_x, cur.raster_ppt, 2};
+        float ms = 0.f;
+        st = time_plan(pl, &ms);
+        if (st == LF_OK && ms < cur_ms) cur_ms = ms, cur = pl;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != LF_OK) return st;
@@ -347,6 +387,11 @@ lf_status lf_batch_destroy(lf_batch* b)
     if (!b) return LF_OK;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaStream_t s : b->side)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->done)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
     return LF_OK;
 }
