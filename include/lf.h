@@ -421,6 +421,20 @@ lf_status lf_trace_enable(int32_t on);
  * be NULL. Clears the record. */
 int32_t lf_trace_collect(char* names, double* total_ms, int64_t* launches, int32_t max_stages);
 
+/* ---- failure detection ----------------------------------------------------- */
+
+/* Every device-side wait of the library (the staged composite's mbarrier
+ * waits) is bounded: after 2 s of wall time it gives up, the kernel sets the
+ * call's error word and returns, and the status calls report LF_ERR_TIMEOUT;
+ * the CUDA context stays usable. This self-test exercises that path without
+ * a fault: one thread waits, with a limit of limit_ms (1..10000)
+ * milliseconds, on a shared-memory mbarrier that nothing arrives on.
+ * Synchronises the stream; returns LF_ERR_TIMEOUT when the wait gave up as
+ * designed, LF_ERR_CUDA if the launch failed, LF_ERR_INVALID_ARG for a limit
+ * out of range. Allocates nothing (the result word is a static device
+ * variable). */
+lf_status lf_selftest_bounded_wait(int32_t limit_ms, cudaStream_t stream);
+
 /* ---- misc --------------------------------------------------------------- */
 
 /* Thread-local description of the last error on this thread ("" if none). */

@@ -120,6 +120,7 @@ SIGNATURES = [
                                          ctypes.POINTER(ctypes.c_float)]),
     ("lf_batch_status", ctypes.c_int, [_P, _P]),
     ("lf_batch_destroy", ctypes.c_int, [_P]),
+    ("lf_selftest_bounded_wait", ctypes.c_int, [_I32, _P]),
     ("lf_launch_count", _I64, []),
     ("lf_trace_enable", ctypes.c_int, [_I32]),
     ("lf_trace_collect", _I32, [_P, _P, _P, _I32]),

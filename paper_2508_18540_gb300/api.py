@@ -613,6 +613,12 @@ def lf_launch_count() -> int:
     return int(load().lf_launch_count())
 
 
+def lf_selftest_bounded_wait(limit_ms: int = 50, stream=None) -> int:
+    """Failure-detection self-test (bounded device wait that must give up):
+    returns the status code, LF_ERR_TIMEOUT when the wait gave up as designed."""
+    return int(load().lf_selftest_bounded_wait(int(limit_ms), _stream_ptr(stream)))
+
+
 def lf_trace_enable(on: bool):
     check(load().lf_trace_enable(int(bool(on))))
 

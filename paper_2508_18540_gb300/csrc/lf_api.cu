@@ -422,6 +422,30 @@ const char* lf_last_error(void) { return lf::g_last_error.c_str(); }
 
 const char* lf_version(void) { return "liblf 0.1 (sm_103a)"; }
 
+}  // extern "C"
+
+// result word of lf_selftest_bounded_wait (a static device variable: the
+// self-test allocates nothing)
+static __device__ int g_selftest_result;
+
+extern "C" {
+
+lf_status lf_selftest_bounded_wait(int32_t limit_ms, cudaStream_t stream)
+{
+    if (limit_ms < 1 || limit_ms > 10000) return fail(LF_ERR_INVALID_ARG, "self-test limit must be 1..10000 ms");
+    int* d = nullptr;
+    if (cudaGetSymbolAddress(reinterpret_cast<void**>(&d), g_selftest_result) != cudaSuccess)
+        return check_launch("self-test result word");
+    if (cudaMemsetAsync(d, 0, sizeof(int), stream) != cudaSuccess) return check_launch("self-test reset");
+    launch_wait_selftest((unsigned long long)limit_ms * 1000000ull, d, stream);
+    int r = 0;
+    if (cudaMemcpyAsync(&r, d, sizeof(int), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return check_launch("self-test");
+    if (r == 1) return fail(LF_ERR_TIMEOUT, "self-test: the bounded wait gave up as designed");
+    return fail(LF_ERR_CUDA, "self-test: unexpected result " + std::to_string(r));
+}
+
 int64_t lf_launch_count(void) { return (int64_t)g_launches.load(); }
 
 lf_status lf_trace_enable(int32_t on)

@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
 constexpr int kStagedWarps = kStagedThreads / 32;     // consumer warps
 constexpr int kStagedBlock = kStagedThreads + 32;     // + one producer warp
 constexpr long long kSpinLimit = 1ll << 26;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s: a staged wait that long has failed
 constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
 
@@ -247,11 +248,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase with the given parity; gives up (false) after limit_ns
+// of wall time (read every 256 tries) or kSpinLimit tries, whichever first.
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, unsigned long long limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < kSpinLimit; it += 256) {
+        for (int i = 0; i < 256; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+}
+
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 {
-    for (long long it = 0; it < kSpinLimit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    return mbar_wait_for(bar, parity, kWaitLimitNs);
 }
 
 __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
@@ -1472,6 +1492,19 @@ bool launch_bwd_staged_vg(const CompParams& p, const void* planes, const int32_t
     return true;
 }
 
+// Failure-detection self-test: one thread waits on an mbarrier of expected
+// count 1 that nothing arrives on, with the wait limit given; the bounded
+// wait gives up and the kernel records how (1: gave up, 2: the phase
+// completed, which cannot happen) and exits normally.
+__global__ void k_wait_selftest(unsigned long long limit_ns, int* result)
+{
+    __shared__ uint64_t bar;
+    const uint32_t b = smem_addr(&bar);
+    mbar_init(b, 1);
+    fence_proxy_async();
+    *result = mbar_wait_for(b, 0u, limit_ns) ? 2 : 1;
+}
+
 template <int DT>
 void launch_composite_bwd_t(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
                             const float* dviews, float* dplanes, cudaStream_t s)
@@ -1556,6 +1589,12 @@ bool launch_composite_batched(const CompScene* scenes_dev, int n_sc, long long t
                                    s);
     note_launches(1);
     return true;
+}
+
+void launch_wait_selftest(unsigned long long limit_ns, int* result, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 1, 0, s>>>(limit_ns, result);
+    note_launches(1);
 }
 
 void launch_composite_bwd(

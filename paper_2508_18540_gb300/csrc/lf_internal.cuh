@@ -277,6 +277,7 @@ lf_status composite_args(const lf_planes* planes, const lf_ref_camera* ref, cons
                          const float* out, void* ws, size_t ws_bytes, CompWs* cw, CompParams* p);
 void launch_composite(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
                       float* out, cudaStream_t s);
+void launch_wait_selftest(unsigned long long limit_ns, int* result, cudaStream_t s);
 void launch_composite_bwd(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
                           const float* dviews, float* dplanes, cudaStream_t s);
 
