@@ -253,6 +253,12 @@ size_t lf_composite_workspace_size(int32_t N, const lf_view_set* views);
 lf_status lf_composite(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views, float* out,
                        void* ws, size_t ws_bytes, cudaStream_t stream);
 
+/* Synchronises stream and reads the error word that lf_composite /
+ * lf_composite_backward keep in the composite workspace cws (laid out for N
+ * and views): LF_ERR_TIMEOUT if a bounded wait of the last such call on cws
+ * gave up (its views or dplanes are then not valid), else LF_OK. */
+lf_status lf_composite_status(int32_t N, const lf_view_set* views, const void* cws, cudaStream_t stream);
+
 /* Allocation-free form of lf_composite (the paper has no counterpart): the
  * same computation and result, with its scratch in a static device array of
  * lf_composite_noalloc_max_bytes() bytes (1 MiB) inside the library instead
@@ -425,7 +431,8 @@ int32_t lf_trace_collect(char* names, double* total_ms, int64_t* launches, int32
 
 /* Every device-side wait of the library (the staged composite's mbarrier
  * waits) is bounded: after 2 s of wall time it gives up, the kernel sets the
- * call's error word and returns, and the status calls report LF_ERR_TIMEOUT;
+ * call's error word and returns, and lf_composite_status / lf_batch_status
+ * report LF_ERR_TIMEOUT;
  * the CUDA context stays usable. This self-test exercises that path without
  * a fault: one thread waits, with a limit of limit_ms (1..10000)
  * milliseconds, on a shared-memory mbarrier that nothing arrives on.

@@ -121,6 +121,7 @@ SIGNATURES = [
     ("lf_batch_status", ctypes.c_int, [_P, _P]),
     ("lf_batch_destroy", ctypes.c_int, [_P]),
     ("lf_selftest_bounded_wait", ctypes.c_int, [_I32, _P]),
+    ("lf_composite_status", ctypes.c_int, [_I32, ctypes.POINTER(LfViewSet), _P, _P]),
     ("lf_launch_count", _I64, []),
     ("lf_trace_enable", ctypes.c_int, [_I32]),
     ("lf_trace_collect", _I32, [_P, _P, _P, _I32]),

@@ -399,6 +399,12 @@ class LightFieldRenderer:
     def status(self):
         return lf_mpi_status(self.ws)
 
+    def composite_status(self, stream=None) -> int:
+        """Status code of the last composite (or its adjoint) on this renderer:
+        LF_ERR_TIMEOUT if a bounded device wait gave up, else LF_OK."""
+        vs = view_set(self.views)
+        return int(load().lf_composite_status(int(self.N), ctypes.byref(vs), _ptr(self.cws), _stream_ptr(stream)))
+
     def capture(self, prims):
         """Captures one render of prims (build + composite, every kernel of the
         frame) into a CUDA graph; replay() then re-runs it on the current

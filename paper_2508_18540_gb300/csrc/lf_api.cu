@@ -430,6 +430,19 @@ static __device__ int g_selftest_result;
 
 extern "C" {
 
+lf_status lf_composite_status(int32_t N, const lf_view_set* views, const void* cws, cudaStream_t stream)
+{
+    if (!views || !cws || N < 1 || views->Vx < 1 || views->Vy < 1) return fail(LF_ERR_INVALID_ARG, "bad argument");
+    CompWs cw;
+    comp_ws_layout(N, views->Vx, views->Vy, const_cast<void*>(cws), &cw);
+    int err = 0;
+    if (cudaStreamSynchronize(stream) != cudaSuccess ||
+        cudaMemcpy(&err, cw.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return check_launch("composite status");
+    if (err) return fail(LF_ERR_TIMEOUT, "a bounded wait of the composite gave up");
+    return LF_OK;
+}
+
 lf_status lf_selftest_bounded_wait(int32_t limit_ms, cudaStream_t stream)
 {
     if (limit_ms < 1 || limit_ms > 10000) return fail(LF_ERR_INVALID_ARG, "self-test limit must be 1..10000 ms");

@@ -38,5 +38,6 @@ def test_bounded_wait_gives_up_and_context_survives(orc):
     w = S.workload_tiny()
     r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f32")
     v = r.render(api.DeviceGaussians.from_scene(w.scene)).cpu().numpy().astype(np.float64)
+    assert r.composite_status() == L.LF_OK
     o = orc.render(w)
     assert np.abs(v - o["views"]).max() <= 1e-4
