@@ -168,6 +168,8 @@ def run_ours(args):
             b.record(stream)
         launches = api.lf_launch_count() - l0
         barrier()
+        if renderer.composite_status() != 0:
+            raise RuntimeError("a bounded composite wait gave up during the timed frames")
         stages = {}
         if trace:
             api.lf_trace_enable(False)
