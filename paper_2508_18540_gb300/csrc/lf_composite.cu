@@ -255,16 +255,22 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Waits for the phase with the given parity; gives up (false) after limit_ns
-// of wall time (read every 256 tries) or kSpinLimit tries, whichever first.
+// Waits for the phase with the given parity; gives up (false) after about
+// limit_ns of wall time (the clock is read every 4096 failed tries, from the
+// first such read on) or kSpinLimit tries, whichever comes first. One plain
+// loop: the common case (first try succeeds) costs what an unbounded wait does.
 __device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, unsigned long long limit_ns)
 {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (long long it = 0; it < kSpinLimit; it += 256) {
-        for (int i = 0; i < 256; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > limit_ns) return false;
+    unsigned long long t0 = 0;
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 4095) == 4095) {
+            const unsigned long long t = global_ns();
+            if (t0 == 0)
+                t0 = t;
+            else if (t - t0 > limit_ns)
+                return false;
+        }
     }
     return false;
 }
