@@ -49,8 +49,8 @@ def _config(extra=None):
 # (profiles/k_*_g2lf_display_1M_512px_N64_45v.md), valid only while the
 # kernel's sources hash to the value recorded with them.
 NCU_TRAFFIC = {
-    "raster_gaussians": (71_787_776 + 210_689_280, ("lf_raster.cu", "lf_internal.cuh"), "d098eb214691b03c"),
-    "composite": (253_843_200 + 159_061_760, ("lf_composite.cu", "lf_internal.cuh"), "abca58235e63d3e9"),
+    "raster_gaussians": (71_790_592 + 211_246_080, ("lf_raster.cu", "lf_internal.cuh"), "b6e324aff5da18c1"),
+    "composite": (253_757_952 + 158_459_648, ("lf_composite.cu", "lf_internal.cuh"), "253063b37a99d37e"),
 }
 
 
