@@ -47,23 +47,52 @@ def _config(extra=None):
 
 # DRAM bytes (read + write) per launch from one ncu capture of the f32 frame
 # (profiles/k_*_g2lf_display_1M_512px_N64_45v.md), valid only while the
-# kernel's sources hash to the value recorded with them.
+# kernel's sources (their code, comments aside) hash to the value recorded
+# with them.
 NCU_TRAFFIC = {
-    "raster_gaussians": (71_790_592 + 211_246_080, ("lf_raster.cu", "lf_internal.cuh"), "b6e324aff5da18c1"),
-    "composite": (253_757_952 + 158_459_648, ("lf_composite.cu", "lf_internal.cuh"), "253063b37a99d37e"),
+    "raster_gaussians": (71_790_592 + 211_246_080, ("lf_raster.cu", "lf_internal.cuh"), "1111147cd6f634cf"),
+    "composite": (253_757_952 + 158_459_648, ("lf_composite.cu", "lf_internal.cuh"), "7f9bcd5e83fd40e0"),
 }
 
 
-def _traffic(kernel):
+def _code_only(src):
+    """C/CUDA source without its comments and with whitespace runs collapsed
+    (string and character literals kept verbatim): what the compiler sees."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
+def _source_hash(files):
     import hashlib
+    m = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2508_18540_gb300", "csrc", f)) as fh:
+            m.update(_code_only(fh.read()).encode())
+    return m.hexdigest()[:16]
+
+
+def _traffic(kernel):
     ent = NCU_TRAFFIC.get(kernel)
     if ent is None:
         return None
-    m = hashlib.sha256()
-    for f in ent[1]:
-        with open(os.path.join(ROOT, "paper_2508_18540_gb300", "csrc", f), "rb") as fh:
-            m.update(fh.read())
-    return ent[0] if m.hexdigest()[:16] == ent[2] else None
+    return ent[0] if _source_hash(ent[1]) == ent[2] else None
 
 
 def _peaks():

@@ -5,9 +5,9 @@
  * on Light Field Displays" (arXiv 2508.18540): a radiance field (3D Gaussians
  * with DC colour, or sparse voxels) is splatted once into N_chunk
  * depth-binned RGBA sweeping planes seen from a reference camera
- * (Sec. 4.2, 4.4, 4.5; Algorithm 1 lines 1-5), and the planes are composited
+ * (Sec. 4.2, 4.4, 4.5; the plane-building steps of Algorithm 1), and the planes are composited
  * into every light-field view in one pass ("swizzle blending", Sec. 4.3,
- * Eq. (u_prime), Eq. (alpha_blend); Algorithm 1 lines 6-11).
+ * Eq. (u_prime), Eq. (alpha_blend); the compositing steps of Algorithm 1).
  *
  * Conventions shared by every entry point
  *  - Camera frame: +x right, +y down, +z forward. The base camera maps a world
@@ -179,7 +179,7 @@ typedef struct {
  * shift that leaves D_forward >= D_focal. */
 lf_status lf_make_ref_camera(const lf_camera* cam, const lf_display* disp, lf_ref_camera* out);
 
-/* ---- splat: radiance field -> sweeping planes (Algorithm 1 lines 1-5) --- */
+/* ---- splat: radiance field -> sweeping planes (Algorithm 1, plane building) --- */
 
 /* Workspace bytes for lf_build_mpi_* on n primitives into N planes of the
  * reference camera ref, with room for dup_capacity (primitive, 32x32
@@ -236,7 +236,7 @@ lf_status lf_mpi_tile_lists(const void* ws, int32_t* order, int64_t n, int32_t* 
  * to FP32. Errors: LF_ERR_INVALID_ARG (sigma <= 0, radius > 16, bad planes). */
 lf_status lf_filter_planes(const lf_planes* planes, double sigma, int32_t radius, cudaStream_t stream);
 
-/* ---- composite: planes -> quilt views (Algorithm 1 lines 6-11) --------- */
+/* ---- composite: planes -> quilt views (Algorithm 1, compositing) --------- */
 
 /* Workspace bytes for lf_composite / lf_composite_backward. */
 size_t lf_composite_workspace_size(int32_t N, const lf_view_set* views);

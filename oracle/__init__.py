@@ -262,8 +262,8 @@ def filter_planes(planes: np.ndarray, sigma: float, radius: int) -> np.ndarray:
 
 def render(workload=None, *, scene=None, camera=None, display=None, views=None, N=None, binning=None,
            kind: Optional[str] = None, with_views: bool = True) -> dict:
-    """Algorithm 1 end to end on the CPU: CulledDepth, FindQuantile,
-    Sort_and_Chunk, Rasterize per chunk, then swizzle blending."""
+    """Algorithm 1 end to end on the CPU: projection and culling, depth sort
+    and chunking, per-chunk splatting, then swizzle blending."""
     if workload is not None:
         scene, camera, display = workload.scene, workload.camera, workload.display
         views, N, binning = workload.views, workload.N, workload.binning

@@ -2,9 +2,10 @@
  * orc_composite.c -- oracle: depth binning into chunks and swizzle blending.
  * TEST INFRASTRUCTURE ONLY (see lf_oracle.h).
  *
- * Sec. 4.4 (quantile binning, median plane distance), Algorithm 1 lines 1-3;
+ * Sec. 4.4 (quantile binning, median plane distance), the culling, depth-sort
+ * and chunking steps of Algorithm 1;
  * Sec. 4.3 swizzle blending, Eq. (u_prime), Eq. (alpha_blend),
- * Algorithm 1 lines 6-11.
+ * the compositing steps of Algorithm 1.
  */
 #include "lf_oracle.h"
 
@@ -123,7 +124,7 @@ static void sample_bilinear(const double* P, int32_t W, int32_t H, double X, dou
     }
 }
 
-/* Swizzle blending (Algorithm 1, lines 6-11): for every quilt view (i, j)
+/* Swizzle blending (the compositing steps of Algorithm 1): for every quilt view (i, j)
  * and pixel (x, y), walk the planes front to back, sample each at its
  * Eq. (u_prime) location and composite
  *   Q <- Q + T c_k,  T <- T (1 - A_k)      (Eq. (alpha_blend), c_k premultiplied).

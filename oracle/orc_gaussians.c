@@ -196,7 +196,7 @@ void orc_gauss_values(const orc_ref* r, int64_t n, const double* means, const do
     }
 }
 
-/* Sec. 4.4 / Algorithm 1 "Rasterize(H, P'_k)": each chunk is rendered alone
+/* Sec. 4.4 / the per-chunk rendering step of Algorithm 1: each chunk is rendered alone
  * into its plane, front to back in (depth, index) order:
  *   alpha = min(0.99, o exp(-q/2)),  q = d^T Sigma_2^{-1} d,  d = p - mean2d,
  *   C += T alpha rgb,  T *= (1 - alpha);  texel = (C, 1 - T).

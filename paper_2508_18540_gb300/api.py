@@ -193,7 +193,7 @@ def lf_build_mpi_workspace_size(ref: L.LfRefCamera, n: int, N: int, dup_capacity
 
 def lf_build_mpi_gaussians(g: DeviceGaussians, ref: L.LfRefCamera, N: int, binning: str, ws: torch.Tensor,
                            planes: Planes, stream=None):
-    """Sec. 4.4 / Algorithm 1 lines 1-5 for 3D Gaussians (asynchronous)."""
+    """Sec. 4.4 / the plane-building steps of Algorithm 1 for 3D Gaussians (asynchronous)."""
     gs = g.c_struct()
     ps = planes.c_struct()
     check(load().lf_build_mpi_gaussians(ctypes.byref(gs), ctypes.byref(ref), int(N), BINNING[binning],
@@ -202,7 +202,7 @@ def lf_build_mpi_gaussians(g: DeviceGaussians, ref: L.LfRefCamera, N: int, binni
 
 def lf_build_mpi_voxels(v: DeviceVoxels, ref: L.LfRefCamera, N: int, binning: str, ws: torch.Tensor,
                         planes: Planes, stream=None):
-    """Sec. 4.5 / Algorithm 1 lines 1-5 for sparse voxels (asynchronous)."""
+    """Sec. 4.5 / the plane-building steps of Algorithm 1 for sparse voxels (asynchronous)."""
     vs = v.c_struct()
     ps = planes.c_struct()
     check(load().lf_build_mpi_voxels(ctypes.byref(vs), ctypes.byref(ref), int(N), BINNING[binning],

@@ -1,7 +1,7 @@
-// lf_bin.cu -- depth binning (Algorithm 1 lines 2-3; Sec. 4.4).
+// lf_bin.cu -- depth binning (the chunking step of Algorithm 1; Sec. 4.4).
 //
 //  k_bin      rank r of the (depth, index) order -> chunk:
-//               quantile:  floor(r N / M)   (equal-count chunks, FindQuantile)
+//               quantile:  floor(r N / M)   (equal-count chunks)
 //               disparity: min(N-1, floor(N (1/z_min - 1/z) / (1/z_min - 1/z_max)))
 //             records the first rank of every chunk (chunks are monotone in
 //             rank) and copies the primitive's footprint, colour and

@@ -1,5 +1,5 @@
 // lf_composite.cu -- swizzle blending of the sweeping planes into the quilt
-// views (Sec. 4.3; Algorithm 1 lines 6-11).
+// views (Sec. 4.3; the compositing steps of Algorithm 1).
 //
 // k_comp_coeffs evaluates, per (view column j, plane k) and (view row i,
 // plane k), the affine form of Eq. (u_prime) in plane pixels,

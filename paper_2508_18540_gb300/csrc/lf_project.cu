@@ -1,5 +1,5 @@
-// lf_project.cu -- per-primitive projection and culling (Algorithm 1 line 1,
-// "CulledDepth"), for 3D Gaussians (Sec. 4.4) and sparse voxels (Sec. 4.5).
+// lf_project.cu -- per-primitive projection and culling (the first step of
+// Algorithm 1), for 3D Gaussians (Sec. 4.4) and sparse voxels (Sec. 4.5).
 //
 // Decisions that fix integers are taken in a prescribed precision and
 // operation order, with explicit round-to-nearest intrinsics so that the

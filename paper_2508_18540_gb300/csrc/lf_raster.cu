@@ -1,5 +1,5 @@
 // lf_raster.cu -- 3D-tiled rasterisation of every chunk into its sweeping
-// plane (Algorithm 1 lines 4-5, "Parallel for all k: Rasterize(H, P'_k)").
+// plane (the per-chunk rendering step of Algorithm 1, all chunks in parallel).
 //
 // One CTA per (16x16 tile, chunk). It walks the (32x32 super-tile, chunk)
 // list holding its tile (ranks in depth order) in batches, keeps the entries

@@ -2,7 +2,7 @@
 // and the depth order built on it.
 //
 // Used twice per build:
-//  - the depth sort of Algorithm 1 line 3 ("Sort_and_Chunk"): the order of
+//  - the depth sort of Algorithm 1 (its sort-and-chunk step): the order of
 //    the culled-in primitives by (FP64 depth, index). The IEEE bits of a
 //    positive FP64 depth order like the depth; relative to the smallest valid
 //    key they span up to ~55 bits. The sort takes their top 24 varying bits

@@ -1,5 +1,6 @@
 """Pins for the oracle's depth binning (Sec. 4.4 quantile binning with the
-median plane distance; uniform-in-disparity bins; Algorithm 1 lines 1-3)."""
+median plane distance; uniform-in-disparity bins; the culling, depth-sort and
+chunking steps of Algorithm 1)."""
 import numpy as np
 import pytest
 

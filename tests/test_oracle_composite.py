@@ -1,5 +1,5 @@
 """Pins for the oracle's swizzle blending (Sec. 4.3, Eq. (u_prime),
-Eq. (alpha_blend), Algorithm 1 lines 6-11) against geometric special cases
+Eq. (alpha_blend), the compositing steps of Algorithm 1) against geometric special cases
 and brute-force per-view volume rendering."""
 import math
 
