@@ -4,8 +4,10 @@ N_chunk = 64 quantile planes, 45 views over +-0.15), one step = one LF frame:
 lf_build_mpi_gaussians (project, depth sort, bin, tile lists, rasterise)
 + lf_composite (45 views), all inputs resident in HBM.
 
-Prints one JSON line (rank 0). FP32 planes are the primary number; FP16 and
-BF16 planes are reported beside it. See the design doc for the roofline figures.
+Prints one JSON line (rank 0). FP32 planes are the primary number; FP16,
+BF16 and RGBA8 planes are reported beside it, each with the roofline of its
+two dominant kernels (composite against the measured HBM copy bandwidth,
+raster against the FP32 issue rate at the sampled SM clock).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """

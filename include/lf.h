@@ -45,7 +45,7 @@ typedef enum {
     LF_ERR_WORKSPACE = 2,     /* workspace missing or too small */
     LF_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has it) */
     LF_ERR_OVERFLOW = 4,      /* tile list larger than the workspace capacity */
-    LF_ERR_UNSUPPORTED = 5,   /* valid request this build does not implement */
+    LF_ERR_UNSUPPORTED = 5,   /* valid request the library does not implement */
     LF_ERR_TIMEOUT = 6        /* a bounded device-side wait gave up */
 } lf_status;
 

@@ -753,7 +753,7 @@ static lf_status splat_backward_common(int64_t n, const lf_ref_camera* ref, cons
     if (!ws) return fail(LF_ERR_WORKSPACE, "workspace is NULL");
     if (((uintptr_t)ws) % 256) return fail(LF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
     const int64_t cap = ws_capacity(n, planes->N, ref->W, ref->H, ws_bytes);
-    if (cap < 1) return fail(LF_ERR_WORKSPACE, "workspace too small for this build");
+    if (cap < 1) return fail(LF_ERR_WORKSPACE, "workspace too small for these primitives and planes");
     build_ws_layout(n, planes->N, ref->W, ref->H, cap, ws, w);
     if (n > 0 && cudaMemsetAsync(w->g2d, 0, sizeof(float) * 12 * (size_t)n, stream) != cudaSuccess)
         return check_launch("gradient accumulator reset");
