@@ -37,6 +37,8 @@ __device__ __forceinline__ int chunk_of_rank(const BuildWs& w, const BinParams& 
 __global__ void __launch_bounds__(256) k_bin(BuildWs w, BinParams p, int32_t* chunk_out, const int4* __restrict__ rect,
                                              const float* __restrict__ rgb, const float* __restrict__ dens8, int kind)
 {
+    pdl_wait();
+    pdl_trigger();
     const long long M = (long long)w.hdr->M;
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (M == 0) {
@@ -70,6 +72,8 @@ __global__ void __launch_bounds__(256) k_bin(BuildWs w, BinParams p, int32_t* ch
 
 __global__ void k_medians(BuildWs w, BinParams p, double* d_out, int32_t* count_out)
 {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.N) return;
     const long long M = (long long)w.hdr->M;
@@ -103,9 +107,9 @@ void launch_bin(const BuildWs& ws, const BinParams& p, long long n, int32_t* chu
                 const int32_t* rect, const float* rgb, const float* dens8, int kind, cudaStream_t s)
 {
     const unsigned blocks = (unsigned)(((n > 0 ? n : 1) + 255) / 256);
-    k_bin<<<blocks, 256, 0, s>>>(ws, p, chunk, reinterpret_cast<const int4*>(rect), rgb, dens8, kind);
+    launch_pdl(k_bin, dim3(blocks), dim3(256), 0, s, ws, p, chunk, reinterpret_cast<const int4*>(rect), rgb, dens8, kind);
     note_launches(1);
-    k_medians<<<(p.N + 127) / 128, 128, 0, s>>>(ws, p, d, count);
+    launch_pdl(k_medians, dim3((p.N + 127) / 128), dim3(128), 0, s, ws, p, d, count);
     note_launches(1);
 }
 

@@ -27,6 +27,34 @@ constexpr uint64_t kInvalidKey = ~0ull;
 // bytes of one RGBA texel of a plane type
 inline int texel_bytes(int dtype) { return dtype == LF_F32 ? 16 : dtype == LF_U8 ? 4 : 8; }
 
+// ---- programmatic dependent launch (the build's chain of short kernels) ----
+// A kernel launched with launch_pdl may be scheduled while its predecessor in
+// the stream is still draining; it must call pdl_wait() before touching any
+// memory the predecessor writes or reads (griddepcontrol.wait returns once
+// the predecessor grid has completed and its writes are visible; it is a
+// no-op for an ordinary launch). pdl_trigger() lets the successor launch as
+// soon as every CTA of this grid has started.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+}
+#endif
+
 // ---- RGBA8 unorm codec (exact, no conversion-unit instructions) -------------
 // decode: byte k of u placed under the exponent of 2^23 reads 2^23 + byte;
 //         subtracting 2^23 leaves the byte as an exact FP32 integer.

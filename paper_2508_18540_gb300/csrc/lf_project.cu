@@ -13,11 +13,16 @@
 
 namespace lf {
 
-__global__ void k_init_header(WsHeader h, WsHeader* d) { *d = h; }
+__global__ void k_init_header(WsHeader h, WsHeader* d)
+{
+    pdl_wait();
+    pdl_trigger();
+    *d = h;
+}
 
 void launch_init_header(const WsHeader& h, WsHeader* d, cudaStream_t s)
 {
-    k_init_header<<<1, 1, 0, s>>>(h, d);
+    launch_pdl(k_init_header, dim3(1), dim3(1), 0, s, h, d);
     note_launches(1);
 }
 
@@ -162,6 +167,8 @@ __device__ __forceinline__ bool gauss_footprint(const ProjParams& p, float m0, f
 __global__ void __launch_bounds__(kProjThreads) k_project_gaussians(lf_gaussians g, ProjParams p, BuildWs w,
                                                                     int4* rect_out, int32_t* chunk_out)
 {
+    pdl_wait();
+    pdl_trigger();
     KeyStats st;
     for (int it = 0; it < kProjItems; ++it) {
         const long long i = ((long long)blockIdx.x * kProjItems + it) * kProjThreads + threadIdx.x;
@@ -200,6 +207,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project_gaussians(lf_gaussians
 __global__ void __launch_bounds__(kProjThreads) k_project_voxels(lf_voxels v, ProjParams p, BuildWs w,
                                                                  int4* rect_out, int32_t* chunk_out)
 {
+    pdl_wait();
+    pdl_trigger();
     KeyStats st;
     for (int it = 0; it < kProjItems; ++it) {
         const long long i = ((long long)blockIdx.x * kProjItems + it) * kProjThreads + threadIdx.x;
@@ -430,7 +439,7 @@ void launch_project_gaussians(const lf_gaussians& g, const ProjParams& p, const 
     if (p.n <= 0) return;
     const long long per = (long long)kProjThreads * kProjItems;
     const unsigned blocks = (unsigned)((p.n + per - 1) / per);
-    k_project_gaussians<<<blocks, kProjThreads, 0, s>>>(g, p, ws, reinterpret_cast<int4*>(rect), chunk);
+    launch_pdl(k_project_gaussians, dim3(blocks), dim3(kProjThreads), 0, s, g, p, ws, reinterpret_cast<int4*>(rect), chunk);
     note_launches(1);
 }
 
@@ -440,7 +449,7 @@ void launch_project_voxels(const lf_voxels& v, const ProjParams& p, const BuildW
     if (p.n <= 0) return;
     const long long per = (long long)kProjThreads * kProjItems;
     const unsigned blocks = (unsigned)((p.n + per - 1) / per);
-    k_project_voxels<<<blocks, kProjThreads, 0, s>>>(v, p, ws, reinterpret_cast<int4*>(rect), chunk);
+    launch_pdl(k_project_voxels, dim3(blocks), dim3(kProjThreads), 0, s, v, p, ws, reinterpret_cast<int4*>(rect), chunk);
     note_launches(1);
 }
 

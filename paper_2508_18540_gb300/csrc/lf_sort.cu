@@ -109,6 +109,8 @@ __device__ __forceinline__ uint32_t match_digit(uint32_t d, bool ok)
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_upsweep(const K* __restrict__ keys, PassArgs a, uint32_t* hist)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t h[kDigits];
     if (pass_uniform(a)) return;
     const long long n = pass_count(a);
@@ -143,6 +145,8 @@ __global__ void __launch_bounds__(kThreads) k_upsweep(const K* __restrict__ keys
 // the row total goes to tot[d].
 __global__ void __launch_bounds__(kThreads) k_rowscan(uint32_t* hist, uint32_t* tot, PassArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     if (pass_uniform(a)) return;
     __shared__ uint32_t warp_tot[kWarps];
     uint32_t* row = hist + (size_t)blockIdx.x * a.nb;
@@ -216,6 +220,8 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(const K* __restrict__ ki
                                                         PassArgs a, const uint32_t* __restrict__ hist,
                                                         const uint32_t* __restrict__ tot)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char dsm_raw[];
     DownSmem<K>& S = *reinterpret_cast<DownSmem<K>*>(dsm_raw);
     const long long n = pass_count(a);
@@ -311,6 +317,8 @@ __global__ void __launch_bounds__(256) k_depth_key32(const unsigned long long* _
                                                      uint32_t* __restrict__ k32, long long n,
                                                      const WsHeader* __restrict__ hdr)
 {
+    pdl_wait();
+    pdl_trigger();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const unsigned long long lo = hdr->kmin, hi = hdr->kmax;
@@ -335,6 +343,8 @@ constexpr int kSmemRun = 2048;
 // such pairs (bytes over keyB, free at this point).
 __global__ void __launch_bounds__(256) k_depth_bad(BuildWs w)
 {
+    pdl_wait();
+    pdl_trigger();
     const long long M = (long long)w.hdr->M;
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= M) return;
@@ -352,6 +362,8 @@ __global__ void __launch_bounds__(256) k_depth_bad(BuildWs w)
 // cost nothing.
 __global__ void __launch_bounds__(256) k_depth_runs(BuildWs w)
 {
+    pdl_wait();
+    pdl_trigger();
     const long long M = (long long)w.hdr->M;
     const long long r0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const uint8_t* bad = reinterpret_cast<const uint8_t*>(w.keyB);
@@ -403,6 +415,8 @@ __device__ __forceinline__ bool oem_pair(long long a, long long p, long long k)
 // Runs longer than kShortRun: one CTA per run (grid-stride over the list).
 __global__ void __launch_bounds__(kLongRunThreads) k_depth_long_runs(BuildWs w)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ unsigned long long sk[kSmemRun];
     __shared__ uint32_t sv[kSmemRun];
     const unsigned long long nr = w.hdr->long_runs;
@@ -462,9 +476,9 @@ void radix_pass(const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, cons
                 uint32_t* tot, cudaStream_t s)
 {
     cudaFuncSetAttribute(k_downsweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DownSmem<K>));
-    k_upsweep<K><<<a.nb, kThreads, 0, s>>>(kin, a, hist);
-    k_rowscan<<<kDigits, kThreads, 0, s>>>(hist, tot, a);
-    k_downsweep<K><<<a.nb, kThreads, sizeof(DownSmem<K>), s>>>(kin, vin, kout, vout, a, hist, tot);
+    launch_pdl(k_upsweep<K>, dim3(a.nb), dim3(kThreads), 0, s, kin, a, hist);
+    launch_pdl(k_rowscan, dim3(kDigits), dim3(kThreads), 0, s, hist, tot, a);
+    launch_pdl(k_downsweep<K>, dim3(a.nb), dim3(kThreads), sizeof(DownSmem<K>), s, kin, vin, kout, vout, a, hist, tot);
     note_launches(3);
 }
 
@@ -478,7 +492,7 @@ void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s)
     uint32_t* vb[2] = {ws.valA, ws.valB};
     // start in the buffer that makes the last pass end in tkeyA / valA
     int cur = kDepthPasses & 1;
-    k_depth_key32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws.keyA, kb[cur], n, ws.hdr);
+    launch_pdl(k_depth_key32, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, ws.keyA, kb[cur], n, ws.hdr);
     for (int pass = 0; pass < kDepthPasses; ++pass) {
         PassArgs a;
         a.n_static = n;
@@ -492,9 +506,9 @@ void sort_depth_keys(const BuildWs& ws, long long n, cudaStream_t s)
         cur ^= 1;
     }
     // truncated keys in tkeyA, ranks in valA; now the runs
-    k_depth_bad<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws);
-    k_depth_runs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ws);
-    k_depth_long_runs<<<kLongRunCtas, kLongRunThreads, 0, s>>>(ws);
+    launch_pdl(k_depth_bad, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, ws);
+    launch_pdl(k_depth_runs, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, ws);
+    launch_pdl(k_depth_long_runs, dim3(kLongRunCtas), dim3(kLongRunThreads), 0, s, ws);
     note_launches(4);
 }
 

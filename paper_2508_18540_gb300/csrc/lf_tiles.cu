@@ -53,6 +53,8 @@ __device__ __forceinline__ uint32_t block_exscan256(uint32_t v, uint32_t* total)
 
 __global__ void __launch_bounds__(kT) k_dup_count(BuildWs w)
 {
+    pdl_wait();
+    pdl_trigger();
     const long long M = (long long)w.hdr->M;
     const long long r0 = (long long)blockIdx.x * kDupBlock + (long long)threadIdx.x * kPer;
     uint32_t sum = 0;
@@ -66,6 +68,8 @@ __global__ void __launch_bounds__(kT) k_dup_count(BuildWs w)
 
 __global__ void __launch_bounds__(1024) k_dup_scan(BuildWs w, int nb)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ unsigned long long wt[32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int per = (nb + 1023) / 1024;
@@ -112,6 +116,8 @@ constexpr int kEmitStage = 4096;
 
 __global__ void __launch_bounds__(kT) k_dup_emit(BuildWs w, int supers_x)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t s_key[kEmitStage];
     __shared__ uint32_t s_rank[kEmitStage];
     if (w.hdr->overflow) return;
@@ -161,6 +167,8 @@ __global__ void __launch_bounds__(kT) k_dup_emit(BuildWs w, int supers_x)
 __global__ void __launch_bounds__(256) k_ranges(BuildWs w, const uint32_t* __restrict__ keys,
                                                 const uint32_t* __restrict__ ranks, int N)
 {
+    pdl_wait();
+    pdl_trigger();
     const long long n = (long long)w.hdr->tile_n;
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -199,9 +207,9 @@ const uint32_t* launch_tile_lists(const BuildWs& ws, long long n, long long cap,
 {
     cudaMemsetAsync(ws.seg, 0, sizeof(int2) * (size_t)n_supers * N, s);
     const int nb = (int)(((n > 0 ? n : 1) + kDupBlock - 1) / kDupBlock);
-    k_dup_count<<<nb, kT, 0, s>>>(ws);
-    k_dup_scan<<<1, 1024, 0, s>>>(ws, nb);
-    k_dup_emit<<<nb, kT, 0, s>>>(ws, supers_x);
+    launch_pdl(k_dup_count, dim3(nb), dim3(kT), 0, s, ws);
+    launch_pdl(k_dup_scan, dim3(1), dim3(1024), 0, s, ws, nb);
+    launch_pdl(k_dup_emit, dim3(nb), dim3(kT), 0, s, ws, supers_x);
     note_launches(3);
     uint32_t* keys = nullptr;
     uint32_t* ranks = nullptr;
@@ -209,7 +217,7 @@ const uint32_t* launch_tile_lists(const BuildWs& ws, long long n, long long cap,
     if (cap > 0) {
         const long long want = (cap + 255) / 256;
         const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
-        k_ranges<<<blocks, 256, 0, s>>>(ws, keys, ranks, N);
+        launch_pdl(k_ranges, dim3(blocks), dim3(256), 0, s, ws, keys, ranks, N);
         note_launches(1);
     }
     return ranks;
