@@ -230,7 +230,30 @@ __device__ __forceinline__ float trilinear(const float* rho, float fx, float fy,
     return lerpf(lerpf(c00, c10, fy), lerpf(c01, c11, fy), fz);
 }
 
-__device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.0f), 1.0f); }
+// clamp to [0, 1] (NaN -> 0) in one saturating operation
+__device__ __forceinline__ float clamp01(float v) { return __saturatef(v); }
+
+// The trilinear density of corner values r[x + 2y + 4z] in polynomial form:
+// rho(f) = c0 + c1 fx + c2 fy + c3 fz + c4 fx fy + c5 fx fz + c6 fy fz
+// + c7 fx fy fz; coefficients computed once per voxel, 7 FMAs per sample.
+__device__ __forceinline__ void trilinear_coeffs(const float* r, float* c)
+{
+    c[0] = r[0];
+    c[1] = r[1] - r[0];
+    c[2] = r[2] - r[0];
+    c[3] = r[4] - r[0];
+    c[4] = (r[3] - r[2]) - (r[1] - r[0]);
+    c[5] = (r[5] - r[4]) - (r[1] - r[0]);
+    c[6] = (r[6] - r[4]) - (r[2] - r[0]);
+    c[7] = ((r[7] - r[6]) - (r[5] - r[4])) - ((r[3] - r[2]) - (r[1] - r[0]));
+}
+
+__device__ __forceinline__ float trilinear_poly(const float* c, float fx, float fy, float fz)
+{
+    const float b = fmaf(fy, fmaf(fz, c[7], c[4]), fmaf(fz, c[5], c[1]));
+    const float e = fmaf(fz, c[6], c[2]);
+    return fmaf(fx, b, fmaf(fy, e, fmaf(fz, c[3], c[0])));
+}
 
 // Voxels: one thread per pixel (256 threads); cube corner relative to the
 // reference centre and side from the projection pass, densities and colour
@@ -241,7 +264,8 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
 {
     constexpr int NT = kTilePix;
     __shared__ float4 s_box[NT];
-    __shared__ float s_den[NT * 8];
+    __shared__ float s_inv_side[NT];   // 1 / side, once per staged voxel
+    __shared__ float s_den[NT * 8];    // trilinear polynomial coefficients per voxel
     __shared__ float4 s_rgb[NT];
     __shared__ int4 s_rect[NT];
     __shared__ int s_wc[NT / 32];
@@ -279,11 +303,12 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
         int cnt;
         const int slot = compact_slot<NT>(hit, s_wc, &cnt);
         if (hit) {
-            s_box[slot] = w.r_geo[rk];
+            const float4 box = w.r_geo[rk];
+            s_box[slot] = box;
+            s_inv_side[slot] = 1.0f / box.w;
             const float4 da = w.r_den[2 * (size_t)rk], db = w.r_den[2 * (size_t)rk + 1];
-            float* sd = s_den + 8 * slot;
-            sd[0] = da.x; sd[1] = da.y; sd[2] = da.z; sd[3] = da.w;
-            sd[4] = db.x; sd[5] = db.y; sd[6] = db.z; sd[7] = db.w;
+            const float rho8[8] = {da.x, da.y, da.z, da.w, db.x, db.y, db.z, db.w};
+            trilinear_coeffs(rho8, s_den + 8 * slot);   // polynomial coefficients, not corners
             s_rgb[slot] = w.r_rgb[rk];
             s_rect[slot] = r;
         }
@@ -314,14 +339,14 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
             t0 = fmaxf(t0, 0.0f);
             if (miss || !(t1 > t0)) continue;
             const float tm = 0.5f * (t0 + t1);
-            const float is = 1.0f / b.w;
-            const float* rho = s_den + 8 * j;
-            const float s0 = trilinear(rho, clamp01((t0 * d[0] - lo[0]) * is), clamp01((t0 * d[1] - lo[1]) * is),
-                                       clamp01((t0 * d[2] - lo[2]) * is));
-            const float sm = trilinear(rho, clamp01((tm * d[0] - lo[0]) * is), clamp01((tm * d[1] - lo[1]) * is),
-                                       clamp01((tm * d[2] - lo[2]) * is));
-            const float s1 = trilinear(rho, clamp01((t1 * d[0] - lo[0]) * is), clamp01((t1 * d[1] - lo[1]) * is),
-                                       clamp01((t1 * d[2] - lo[2]) * is));
+            const float is = s_inv_side[j];
+            const float* cf = s_den + 8 * j;
+            const float s0 = trilinear_poly(cf, clamp01((t0 * d[0] - lo[0]) * is), clamp01((t0 * d[1] - lo[1]) * is),
+                                            clamp01((t0 * d[2] - lo[2]) * is));
+            const float sm = trilinear_poly(cf, clamp01((tm * d[0] - lo[0]) * is), clamp01((tm * d[1] - lo[1]) * is),
+                                            clamp01((tm * d[2] - lo[2]) * is));
+            const float s1 = trilinear_poly(cf, clamp01((t1 * d[0] - lo[0]) * is), clamp01((t1 * d[1] - lo[1]) * is),
+                                            clamp01((t1 * d[2] - lo[2]) * is));
             const float integral = (t1 - t0) * (1.0f / 6.0f) * (s0 + 4.0f * sm + s1);
             const float al = 1.0f - __expf(-integral);
             const float4 col = s_rgb[j];
