@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kProjThreads) k_project_voxels(lf_voxels v, Pr
             double s = p.base_size;
             for (int l = 0; l < (int)v.level[i]; ++l) s = __dmul_rn(s, 0.5);
             double lo[3];
-    #pragma unroll
+#pragma unroll
             for (int a = 0; a < 3; ++a) lo[a] = __dadd_rn(p.origin[a], __dmul_rn((double)v.ijk[3 * i + a], s));
             const double hs = __dmul_rn(0.5, s);
             const double z = ref_depth(p, __dadd_rn(lo[0], hs), __dadd_rn(lo[1], hs), __dadd_rn(lo[2], hs));
@@ -228,11 +228,19 @@ __global__ void __launch_bounds__(kProjThreads) k_project_voxels(lf_voxels v, Pr
                 const float* R = p.Rf;
                 float mnx = __int_as_float(0x7f800000), mny = mnx;
                 float mxx = -mnx, mxy = -mnx;
-    #pragma unroll
+                // coordinate a of corner c is FP32(lo[a] + bit * s) with bit 0 or 1,
+                // i.e. FP32(lo[a]) or FP32(lo[a] + s): two values per axis
+                float cw[3][2];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    cw[a][0] = __double2float_rn(lo[a]);
+                    cw[a][1] = __double2float_rn(__dadd_rn(lo[a], s));
+                }
+#pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const float X = __double2float_rn(__dadd_rn(lo[0], __dmul_rn((double)(c & 1), s)));
-                    const float Y = __double2float_rn(__dadd_rn(lo[1], __dmul_rn((double)((c >> 1) & 1), s)));
-                    const float Z = __double2float_rn(__dadd_rn(lo[2], __dmul_rn((double)((c >> 2) & 1), s)));
+                    const float X = cw[0][c & 1];
+                    const float Y = cw[1][(c >> 1) & 1];
+                    const float Z = cw[2][(c >> 2) & 1];
                     const float xc = __fmaf_rn(R[0], X, __fmaf_rn(R[1], Y, __fmaf_rn(R[2], Z, p.t0f)));
                     const float yc = __fmaf_rn(R[3], X, __fmaf_rn(R[4], Y, __fmaf_rn(R[5], Z, p.t1f)));
                     const float zc = __fmaf_rn(R[6], X, __fmaf_rn(R[7], Y, __fmaf_rn(R[8], Z, p.t2rf)));
