@@ -28,8 +28,8 @@ constexpr uint64_t kInvalidKey = ~0ull;
 inline int texel_bytes(int dtype) { return dtype == LF_F32 ? 16 : dtype == LF_U8 ? 4 : 8; }
 
 // ---- programmatic dependent launch (the build's chain of short kernels) ----
-// A kernel launched with launch_pdl may be scheduled while its predecessor in
-// the stream is still draining; it must call pdl_wait() before touching any
+// A kernel launched with launch_pdl outside a graph capture may be scheduled
+// while its predecessor in the stream is still draining; it must call pdl_wait() before touching any
 // memory the predecessor writes or reads (griddepcontrol.wait returns once
 // the predecessor grid has completed and its writes are visible; it is a
 // no-op for an ordinary launch). pdl_trigger() lets the successor launch as
@@ -50,7 +50,11 @@ inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    // a CUDA graph already hides the launch gaps (measured: programmatic
+    // edges only add a few microseconds per frame there), so a launch that is
+    // being captured is an ordinary one
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cfg.numAttrs = (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) ? 1 : 0;
     cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
 }
 #endif
