@@ -554,6 +554,25 @@ def run_profile(args):
         print("profile %s: status %d, M %d, pairs %d" % (dtype, st, M, needed), flush=True)
 
 
+def run_profile_grad(args):
+    """Short run for profilers of the differentiable workload (300k Gaussians,
+    512^2, N 64, 45 views, FP32): W + 1 forward + backward steps, no timing."""
+    import torch
+
+    from paper_2508_18540_gb300 import api
+    from paper_2508_18540_gb300 import synth as S
+    wl = S.workload_fit()
+    g = api.DeviceGaussians.from_scene(wl.scene)
+    r = api.LightFieldRenderer(wl.camera, wl.display, wl.views, wl.N, wl.binning, "f32")
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    dv = torch.randn((wl.views.Vx, wl.camera.Ny, wl.camera.Nx, 4), device="cuda", generator=gen)
+    for _ in range(args.warmup + 1):
+        r.render(g)
+        r.backward(g, dv)
+    torch.cuda.synchronize()
+    print("profile grad: composite status %d" % r.composite_status(), flush=True)
+
+
 def cpu_baseline(min_seconds=10.0, max_frames=40):
     """The FP64 oracle, as it stands, on the host cores: full LF frames of
     the same workload (all 1M Gaussians splatted into 64 planes, 45 views
@@ -614,7 +633,13 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the V2LF, differentiable and batched sections")
     ap.add_argument("--profile", action="store_true", help="short untimed run for ncu")
     ap.add_argument("--profile-dtypes", default="f32,f16")
+    ap.add_argument("--profile-grad", action="store_true", help="short untimed forward + backward run for ncu")
     args = ap.parse_args()
+    if args.profile_grad:
+        import __graft_entry__
+        __graft_entry__.build()
+        run_profile_grad(args)
+        return
     if args.profile:
         import __graft_entry__
         __graft_entry__.build()
