@@ -92,6 +92,12 @@ def test_invalid_arguments_are_rejected(L):
     st = lib.lf_composite(ctypes.byref(planes), ctypes.byref(ref), ctypes.byref(vs), ctypes.c_void_p(16),
                           ctypes.c_void_p(256), 1 << 20, None)
     assert st == L.LF_ERR_INVALID_ARG
+    # status and self-test entry points reject bad arguments on the host
+    vs = L.LfViewSet(5, 1, 0)
+    assert lib.lf_composite_status(0, ctypes.byref(vs), ctypes.c_void_p(256), None) == L.LF_ERR_INVALID_ARG
+    assert lib.lf_composite_status(4, ctypes.byref(vs), None, None) == L.LF_ERR_INVALID_ARG
+    assert lib.lf_selftest_bounded_wait(0, None) == L.LF_ERR_INVALID_ARG
+    assert lib.lf_selftest_bounded_wait(20000, None) == L.LF_ERR_INVALID_ARG
 
 
 def test_workspace_sizes(L):
