@@ -394,8 +394,10 @@ StagedGeom staged_geom(const CompParams& p, int texel_bytes, bool bilinear, int 
                          sizeof(int) * (size_t)p.N;
     // a bilinear stage is released once its rows are blended, so a shallower
     // ring suffices; keep two CTAs per SM where the blend rows would not fit
+    // (view groups wider than kTwoCtaViews run one CTA per SM: no such limit)
     G.stages = kStages;
-    while (bilinear && G.stages > 3 && G.stages * G.stage_bytes + fixed > kTwoCtaSmem) --G.stages;
+    const size_t budget = VG > kTwoCtaViews ? (size_t)200 * 1024 : kTwoCtaSmem;
+    while (bilinear && G.stages > 3 && G.stages * G.stage_bytes + fixed > budget) --G.stages;
     G.smem_bytes = G.stages * G.stage_bytes + fixed;
     return G;
 }
@@ -653,7 +655,7 @@ __device__ __forceinline__ void zero_pads(const CompParams& p, const StagedGeom&
 }
 
 template <int DT, bool BILINEAR, int VG>
-__global__ void __launch_bounds__(kStagedBlock, 2) k_composite_staged(CompParams p, StagedGeom G,
+__global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_composite_staged(CompParams p, StagedGeom G,
                                                                         const char* __restrict__ planes,
                                                                         const int32_t* __restrict__ count, CompWs w,
                                                                         float* __restrict__ out)
@@ -986,16 +988,36 @@ bool launch_staged_vg(const CompParams& p, const void* planes, const int32_t* co
     return true;
 }
 
+// Views per thread of the staged composite, from {15, 9, 5, 3} (at most Vx,
+// or 3): the one with the least padded work, ceil(Vx / VG) (VG + 3) -- a view
+// group's fixed cost (plane list, coefficient block, staging every plane's
+// rows) measured worth about three views. Groups of 15 run one CTA per SM at
+// up to 96 registers; 9 at two CTAs per SM spills a little, and bilinear
+// FP32 (four-channel FP32 taps) spills more, so it skips 9. Measured on 45
+// views of 512^2, N 64: 15 beats 9 by 4 % (FP32) to 8 % (FP16) nearest and
+// 7-15 % bilinear.
+inline int staged_views_per_thread(int Vx, bool no9)
+{
+    int best = 3;
+    long long best_cost = -1;
+    for (int vg : {15, 9, 5, 3}) {
+        if ((vg > Vx && vg != 3) || (no9 && vg == 9)) continue;
+        const long long cost = (long long)((Vx + vg - 1) / vg) * (vg + 3);
+        if (best_cost < 0 || cost < best_cost) best_cost = cost, best = vg;
+    }
+    return best;
+}
+
 template <int DT, bool BILINEAR>
 bool launch_staged(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
                    cudaStream_t s)
 {
-    // bilinear FP32 keeps 5 views per thread (measured faster: 9 spill more
-    // with four-channel FP32 taps); the narrower plane types take 9
-    if (p.Vx >= 9 && !(BILINEAR && DT == LF_F32))
-        return launch_staged_vg<DT, BILINEAR, 9>(p, planes, count, ws, out, s);
-    if (p.Vx >= 5) return launch_staged_vg<DT, BILINEAR, 5>(p, planes, count, ws, out, s);
-    return launch_staged_vg<DT, BILINEAR, 3>(p, planes, count, ws, out, s);
+    switch (staged_views_per_thread(p.Vx, BILINEAR && DT == LF_F32)) {
+    case 15: return launch_staged_vg<DT, BILINEAR, 15>(p, planes, count, ws, out, s);
+    case 9: return launch_staged_vg<DT, BILINEAR, 9>(p, planes, count, ws, out, s);
+    case 5: return launch_staged_vg<DT, BILINEAR, 5>(p, planes, count, ws, out, s);
+    default: return launch_staged_vg<DT, BILINEAR, 3>(p, planes, count, ws, out, s);
+    }
 }
 
 template <int DT>

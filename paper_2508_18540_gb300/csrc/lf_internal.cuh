@@ -273,6 +273,7 @@ struct CompParams {
 constexpr int kStagedThreads = 512;   // consumer threads of a staged-composite CTA
 constexpr int kStages = 6;            // depth of its plane-row ring
 constexpr size_t kTwoCtaSmem = 112 * 1024;   // dynamic shared memory that still lets two CTAs share an SM
+constexpr int kTwoCtaViews = 9;               // widest view group run at two CTAs per SM
 struct StagedGeom {
     int TX, BY, VG, rows_per_y;    // rows_per_y: 1 nearest, 2 bilinear
     int padl;                      // zero texels left of every staged row (16 bytes)

@@ -85,6 +85,25 @@ def test_bilinear_nine_views_per_thread(orc, dtype):
     _compare(gpu, o, o["ref"].W, o["ref"].H, 12, dtype)
 
 
+@pytest.mark.parametrize("dtype,bilinear", [("f32", False), ("f16", False), ("f32", True), ("u8", True)])
+def test_fifteen_views_per_thread(orc, dtype, bilinear):
+    # 30 x 2 views: the staged composite runs view groups of 15 (one CTA per
+    # SM, its own launch bounds and shared-memory budget)
+    cam = S.Camera(np.eye(3), np.zeros(3), np.radians(50.0), np.radians(40.0), 80, 48)
+    disp = S.Display(D_focal=3.0, phi_x=0.12, phi_y=0.05)
+    sc = S.uniform_gaussians(3000, 23)
+    views = S.ViewSet(30, 2, bilinear, (0.2, 0.3, 0.1))
+    o = orc.render(scene=sc, camera=cam, display=disp, views=views, N=10, binning="quantile")
+    gpu = G.run_gpu(sc, cam, disp, views, 10, "quantile", dtype)
+    if dtype == "u8":
+        # RGBA8 planes: the composite of the GPU's own planes against FP64
+        pl = gpu["renderer"].planes.rgba.cpu().numpy().astype(np.float64) / 255.0
+        want = orc.composite(o["ref"], pl, o["d"], o["count"], 30, 2, bilinear, views.bg)
+        assert np.abs(gpu["views"] - want).max() <= 1e-4
+    else:
+        _compare(gpu, o, o["ref"].W, o["ref"].H, 10, dtype)
+
+
 def test_two_view_rows(orc):
     # vertical parallax too (Vy = 3), non-square views
     cam = S.Camera(np.eye(3), np.zeros(3), np.radians(50.0), np.radians(40.0), 64, 48)
