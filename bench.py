@@ -32,8 +32,8 @@ L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 
 
 def _env_rank():
-    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
-        int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2508_18540_gb300 import replicas
+    return replicas.env_rank()
 
 
 def _config(extra=None):
@@ -161,6 +161,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     from paper_2508_18540_gb300 import api
+    from paper_2508_18540_gb300 import replicas as R
     from paper_2508_18540_gb300 import synth as S
 
     rank, world, local = _env_rank()
@@ -169,16 +170,14 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     # replicas: every rank renders its own frame stream of the same-sized workload
-    wl = S.workload_display(seed=WORKLOAD["seed"] + rank, n=WORKLOAD["n"], res=WORKLOAD["res"], N=WORKLOAD["N"],
+    wl = S.workload_display(seed=R.replica_seed(WORKLOAD["seed"], rank), n=WORKLOAD["n"], res=WORKLOAD["res"], N=WORKLOAD["N"],
                             V=WORKLOAD["V"])
     g = api.DeviceGaussians.from_scene(wl.scene, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
     def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
+        R.barrier(world, dev)
 
     def timed(renderer, steps, warmup, trace=False):
         for _ in range(warmup):
@@ -205,11 +204,8 @@ def run_ours(args):
         if trace:
             api.lf_trace_enable(False)
             stages = api.lf_trace_collect()
-        ms = sum(a.elapsed_time(b) for a, b in ev)
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item()) / steps, launches // steps, stages
+        ms = R.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
+        return ms / steps, launches // steps, stages
 
     res = {}
     clocks = ClockSampler(local)
@@ -233,10 +229,7 @@ def run_ours(args):
             rr.replay()
             b.record(stream)
         barrier()
-        t = torch.tensor([sum(a.elapsed_time(b) for a, b in evg) / steps], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return R.max_over_ranks(sum(a.elapsed_time(b) for a, b in evg) / steps, world, dev)
 
     r32 = res["f32"]["renderer"]
     graph_kernels = r32.capture(g)
@@ -271,11 +264,7 @@ def run_ours(args):
     pipe.s_out.wait_event(last)
     e1.record(pipe.s_out)
     barrier()
-    e_ms = e0.elapsed_time(e1) / args.steps
-    t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e_ms = float(t.item())
+    e_ms = R.max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
 
     # per-kernel roofline of the dominant stage (live event times above)
     peaks = _peaks()
@@ -317,7 +306,7 @@ def run_ours(args):
     line = None
     if rank == 0:
         # the frame as a render loop runs it: one CUDA-graph replay per frame
-        fps = 1000.0 / g_ms * world
+        fps = R.job_rate(g_ms, world)
         line = {
             "metric": METRIC, "value": round(fps, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(g_ms, 4), "higher_is_better": True,
@@ -325,14 +314,14 @@ def run_ours(args):
             "config": _config({"planes": "f32", "parallelism": "replicas" if world > 1 else "single",
                                "launch": "one CUDA-graph replay per frame (%d kernels)" % graph_kernels}),
             "views_per_s": round(fps * WORKLOAD["V"], 1),
-            "plain_launches": {"value": round(1000.0 / res["f32"]["ms"] * world, 2),
+            "plain_launches": {"value": round(R.job_rate(res["f32"]["ms"], world), 2),
                                "ms_per_step": round(res["f32"]["ms"], 4)},
-            "variants": {d: {"planes": d, "value": round(1000.0 / res[d]["graph_ms"] * world, 2),
+            "variants": {d: {"planes": d, "value": round(R.job_rate(res[d]["graph_ms"], world), 2),
                              "ms_per_step": round(res[d]["graph_ms"], 4),
-                             "plain_launches_value": round(1000.0 / res[d]["ms"] * world, 2), "roofline": roofs[d]}
+                             "plain_launches_value": round(R.job_rate(res[d]["ms"], world), 2), "roofline": roofs[d]}
                          for d in ("f16", "bf16", "u8")},
             "stages_ms": {d: {k: round(v[0] / v[1], 4) for k, v in res[d]["stages"].items()} for d in res},
-            "e2e": {"value": round(1000.0 / e_ms * world, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": round(R.job_rate(e_ms, world), 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e_ms, 4),
                     "api": "HostPipeline.submit (pinned host Gaussians in, pinned host views out, "
                            "copies overlapped with neighbouring frames, one CUDA-graph replay per frame)",

@@ -7,6 +7,8 @@ paper_2508_18540_gb300/liblf.so. Host code is compiled with
 written order (chunk membership and nearest-texel indices depend on them).
 """
 import concurrent.futures as cf
+import contextlib
+import fcntl
 import os
 import shutil
 import subprocess
@@ -43,12 +45,35 @@ def _flags():
             "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    srcs = sources()
-    newest = max(os.path.getmtime(p) for p in srcs + _headers() + [os.path.abspath(__file__)])
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
-        return LIB
+@contextlib.contextmanager
+def _build_lock():
+    """Exclusive lock on the build folder: processes started together (one
+    per GPU) build once, the others wait and then find the library current."""
     os.makedirs(BUILD_DIR, exist_ok=True)
+    with open(os.path.join(BUILD_DIR, ".lock"), "w") as f:
+        fcntl.flock(f, fcntl.LOCK_EX)
+        try:
+            yield
+        finally:
+            fcntl.flock(f, fcntl.LOCK_UN)
+
+
+def _current() -> bool:
+    newest = max(os.path.getmtime(p) for p in sources() + _headers() + [os.path.abspath(__file__)])
+    return os.path.exists(LIB) and os.path.getmtime(LIB) >= newest
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and _current():
+        return LIB
+    with _build_lock():
+        if not force and _current():
+            return LIB
+        return _build(verbose)
+
+
+def _build(verbose: bool) -> str:
+    srcs = sources()
     nvcc = _nvcc()
     objs = []
 
