@@ -80,15 +80,12 @@ __device__ __forceinline__ float ex2_approx(float x)
 // Gaussians: 256 / PPT threads; thread t shades the PPT pixels of column
 // t % 16 in rows PPT (t / 16) ... PPT (t / 16) + PPT - 1, so warp w owns the
 // 2 PPT x 16 strip of rows 2 PPT w ... Each batch of list entries is staged
-// as three 16-byte words {mean x, mean y, A, B}, {C, o, cover, -},
-// {r, g, b, -}, with the conic pre-scaled so that
-// alpha = min(0.99, o 2^(A dx^2 + B dx dy + C dy^2)),
-// A = -log2(e)/2 a, B = -log2(e) b, C = -log2(e)/2 c, and cover the
-// footprint rectangle clipped to the tile as two 16-bit masks: bit c of the
-// low half set iff tile column c lies in [x0, x1], bit 16 + r iff tile row r
-// lies in [y0, y1]. A pixel is inside the rectangle iff both of its bits are
-// set. Every warp ballots which entries touch its strip and visits only
-// those, in list order, so the blending order of every pixel is unchanged.
+// as three 16-byte words {mean x, mean y, A, B}, {C, o, x0 | y0 << 16,
+// (x1 - x0) | (y1 - y0) << 16}, {r, g, b, -}, with the conic pre-scaled so
+// that alpha = min(0.99, o 2^(A dx^2 + B dx dy + C dy^2)),
+// A = -log2(e)/2 a, B = -log2(e) b, C = -log2(e)/2 c. Every warp ballots which
+// entries touch its strip and visits only those, in list order, so the
+// blending order of every pixel is unchanged.
 template <int PPT>
 struct GaussSmem {
     static constexpr int NT = kTilePix / PPT;
@@ -114,12 +111,8 @@ __device__ __forceinline__ void raster_gauss_tile(const BuildWs& w, const Raster
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
     const int py0 = ty * kTile + (threadIdx.x / kTile) * PPT;
-    const int sx0 = tx * kTile, sy0 = ty * kTile;
-    // this lane's column bit, its first row's bit position and the warp
-    // strip's row bits in a cover word
-    const uint32_t col_bit = 1u << (threadIdx.x & (kTile - 1));
-    const int row_shift = 16 + (threadIdx.x / kTile) * PPT;
-    const uint32_t strip_bits = ((1u << (2 * PPT)) - 1u) << (16 + 2 * PPT * warp);
+    const int sx0 = tx * kTile, sx1 = sx0 + kTile - 1;                // warp strip bounds
+    const int sy0 = ty * kTile + 2 * PPT * warp, sy1 = sy0 + 2 * PPT - 1;
     const int st = (ty / kTilesPerSuper) * p.supers_x + tx / kTilesPerSuper;
     const int2 sg = w.seg[(size_t)st * p.N + k];
     const int L = sg.y - sg.x;
@@ -135,39 +128,42 @@ __device__ __forceinline__ void raster_gauss_tile(const BuildWs& w, const Raster
             rk = ranks[sg.x + i];
             r = w.r_rect[rk];
         }
-        const bool hit = i < L && meets_tile(r, sx0, sy0);
+        const bool hit = i < L && meets_tile(r, sx0, ty * kTile);
         int cnt;
         const int slot = compact_slot<NT>(hit, s_wc, &cnt);
         if (hit) {
             const float4 geo = w.r_geo[rk];
             const float4 c = w.r_con[rk];
-            // the rectangle meets the tile, so both clipped ranges are non-empty
-            const int c0 = max(r.x - sx0, 0), c1 = min(r.z - sx0, kTile - 1);
-            const int r0 = max(r.y - sy0, 0), r1 = min(r.w - sy0, kTile - 1);
-            const uint32_t cover = ((2u << c1) - (1u << c0)) | (((2u << r1) - (1u << r0)) << 16);
             s_e0[slot] = make_float4(geo.x, geo.y, -0.5f * kL2E * c.x, -kL2E * c.y);
-            s_e1[slot] = make_float4(-0.5f * kL2E * c.z, c.w, __uint_as_float(cover), 0.f);
+            s_e1[slot] = make_float4(-0.5f * kL2E * c.z, c.w, __int_as_float((r.x & 0xffff) | (r.y << 16)),
+                                     __int_as_float(((r.z - r.x) & 0xffff) | ((r.w - r.y) << 16)));
             s_rgb[slot] = w.r_rgb[rk];
         }
         __syncthreads();
         for (int m0 = 0; m0 < cnt; m0 += 32) {
             const int jl = m0 + lane;
-            const bool hit = jl < cnt && (__float_as_uint(s_e1[jl].z) & strip_bits) != 0u;
+            bool hit = false;
+            if (jl < cnt) {
+                const float4 e1 = s_e1[jl];
+                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
+                const int rx0 = xy & 0xffff, ry0 = xy >> 16;
+                hit = rx0 <= sx1 && rx0 + (wh & 0xffff) >= sx0 && ry0 <= sy1 && ry0 + (wh >> 16) >= sy0;
+            }
             uint32_t mask = __ballot_sync(0xffffffffu, hit);
             while (mask) {
                 const int j = m0 + __ffs(mask) - 1;
                 mask &= mask - 1;
                 const float4 e1 = s_e1[j];
-                const uint32_t cover = __float_as_uint(e1.z);
-                if ((cover & col_bit) == 0u) continue;
+                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
+                if ((uint32_t)(px - (xy & 0xffff)) > (uint32_t)(wh & 0xffff)) continue;
                 const float4 e0 = s_e0[j];
                 const float4 col = s_rgb[j];
                 const float dx = fpx - e0.x;
                 const float adx = e0.z * dx;
-                const uint32_t rows = cover >> row_shift;
+                const int ry0 = xy >> 16, rh = wh >> 16;
 #pragma unroll
                 for (int r = 0; r < PPT; ++r) {
-                    if (rows & (1u << r)) {
+                    if ((uint32_t)(py0 + r - ry0) <= (uint32_t)rh) {
                         const float dy = (float)(py0 + r) - e0.y;
                         const float pw = fmaf(dx, fmaf(e0.w, dy, adx), e1.x * dy * dy);
                         const float al = fminf(0.99f, e1.y * ex2_approx(pw));
@@ -191,11 +187,8 @@ __device__ __forceinline__ void raster_gauss_tile(const BuildWs& w, const Raster
     }
 }
 
-// Held to 40 registers (12 CTAs, 48 warps per SM): the kernel is issue bound
-// and measured 3 % slower at the 10 CTAs per SM its unconstrained 45
-// registers allow.
 template <int DT, int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT, 12) k_raster_gauss(BuildWs w, RasterParams p,
+__global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, RasterParams p,
                                                                  const uint32_t* __restrict__ ranks, void* planes)
 {
     __shared__ GaussSmem<PPT> sm;
