@@ -77,6 +77,8 @@ def lib():
         L.orc_bin.restype = ctypes.c_int64
         L.orc_splat_gaussians.argtypes = [ctypes.POINTER(OrcRef), ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P,
                                           ctypes.c_int32, _P]
+        L.orc_splat_gaussians_3dgs.argtypes = [ctypes.POINTER(OrcRef), ctypes.c_int64, _P, _P, _P, _P, _P, _P,
+                                               _P, ctypes.c_int32, _P, _P]
         L.orc_splat_voxels.argtypes = [ctypes.POINTER(OrcRef), ctypes.c_int64, _P, _P, _P, _P, _P, _P,
                                        ctypes.c_double, _P, _P, ctypes.c_int32, _P]
         L.orc_voxel_alpha.argtypes = [_P, ctypes.c_double, _P, _P, _P, _P]
@@ -207,6 +209,20 @@ def splat_gaussians(ref: OrcRef, order, chunk, rect, mean2d, conic, opacity, rgb
     return planes
 
 
+def splat_gaussians_3dgs(ref: OrcRef, order, chunk, rect, mean2d, conic, opacity, rgb, N: int):
+    """The splat with the 3DGS cut-offs (alpha < 1/255 skipped, stop before
+    T < 1e-4); returns (planes, near), near[N][H][W] marking texels whose
+    trace comes within 1e-6 of either threshold."""
+    order = _c(order, np.int64)
+    planes = np.zeros((N, ref.H, ref.W, 4), np.float64)
+    near = np.zeros((N, ref.H, ref.W), np.uint8)
+    args = [_c(chunk, np.int32), _c(rect, np.int32), _c(mean2d, np.float64), _c(conic, np.float64),
+            _c(opacity, np.float64), _c(rgb, np.float64)]
+    lib().orc_splat_gaussians_3dgs(ctypes.byref(ref), order.shape[0], _ptr(order), *[_ptr(a) for a in args], N,
+                                   _ptr(planes), _ptr(near))
+    return planes, near
+
+
 def splat_voxels(ref: OrcRef, order, chunk, rect, scene, N: int) -> np.ndarray:
     order = _c(order, np.int64)
     planes = np.zeros((N, ref.H, ref.W, 4), np.float64)
@@ -261,9 +277,13 @@ def filter_planes(planes: np.ndarray, sigma: float, radius: int) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 def render(workload=None, *, scene=None, camera=None, display=None, views=None, N=None, binning=None,
-           kind: Optional[str] = None, with_views: bool = True) -> dict:
+           kind: Optional[str] = None, with_views: bool = True, blend: str = "exact") -> dict:
     """Algorithm 1 end to end on the CPU: projection and culling, depth sort
-    and chunking, per-chunk splatting, then swizzle blending."""
+    and chunking, per-chunk splatting, then swizzle blending. blend="3dgs"
+    splats Gaussians with the 3DGS cut-offs and adds the near-threshold
+    texel mask as out["near"]."""
+    if blend not in ("exact", "3dgs"):
+        raise ValueError("blend must be 'exact' or '3dgs'")
     if workload is not None:
         scene, camera, display = workload.scene, workload.camera, workload.display
         views, N, binning = workload.views, workload.N, workload.binning
@@ -278,9 +298,15 @@ def render(workload=None, *, scene=None, camera=None, display=None, views=None, 
     out = dict(ref=ref, z=z, valid=valid, rect=rect, order=order, chunk=chunk, d=d, count=count, M=M)
     if kind == "gaussians":
         mean2d, conic, cov2d = gauss_values(ref, scene)
-        planes = splat_gaussians(ref, order, chunk, rect, mean2d, conic, scene.opacity, scene.rgb, N)
+        if blend == "3dgs":
+            planes, out["near"] = splat_gaussians_3dgs(ref, order, chunk, rect, mean2d, conic, scene.opacity,
+                                                       scene.rgb, N)
+        else:
+            planes = splat_gaussians(ref, order, chunk, rect, mean2d, conic, scene.opacity, scene.rgb, N)
         out.update(mean2d=mean2d, conic=conic, cov2d=cov2d)
     else:
+        if blend != "exact":
+            raise ValueError("3DGS blending applies to Gaussians only")
         planes = splat_voxels(ref, order, chunk, rect, scene, N)
     out["planes"] = planes
     if with_views:

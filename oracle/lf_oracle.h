@@ -116,6 +116,18 @@ void orc_splat_gaussians(const orc_ref* r, int64_t M, const int64_t* order, cons
                          const int32_t* rect, const double* mean2d, const double* conic,
                          const double* opacity, const double* rgb, int32_t N, double* planes);
 
+/* Sec. 4.4 with the two cut-offs of the 3DGS rasteriser the chunks are
+ * rendered with: a member whose alpha is below 1/255 is skipped, and a pixel
+ * stops before the member whose blend would take T (1 - alpha) below 1e-4
+ * (that member and all later ones are left out). near[N][H][W] (may be NULL)
+ * is set to 1 where the pixel's trace, up to its stop, meets an alpha within
+ * 1e-6 of 1/255 or a T (1 - alpha) within 1e-6 of 1e-4: a decision another
+ * precision may take the other way. */
+void orc_splat_gaussians_3dgs(const orc_ref* r, int64_t M, const int64_t* order, const int32_t* chunk,
+                              const int32_t* rect, const double* mean2d, const double* conic,
+                              const double* opacity, const double* rgb, int32_t N, double* planes,
+                              uint8_t* near);
+
 /* Sec. 4.5: rasterise voxels (ray-segment integral of trilinear density). */
 void orc_splat_voxels(const orc_ref* r, int64_t M, const int64_t* order, const int32_t* chunk,
                       const int32_t* rect, const int32_t* ijk, const uint8_t* level,

@@ -13,6 +13,7 @@
 
 #include <math.h>
 #include <string.h>
+#include <stdlib.h>
 
 /* Reference depth in FP64 with a fixed fma order:
  *   z = fma(R20, x, fma(R21, y, fma(R22, z_w, t2))) - D_forward.
@@ -249,5 +250,71 @@ void orc_splat_gaussians(const orc_ref* r, int64_t M, const int64_t* order, cons
             }
         }
         for (int64_t p = 0; p < W * H; ++p) P[4 * p + 3] = 1.0 - P[4 * p + 3];
+    }
+}
+
+/* The 3DGS cut-offs on top of the splat above (same member order, same
+ * alpha): skip a member with alpha < 1/255; when T (1 - alpha) would fall
+ * below 1e-4, the pixel is finished and blends nothing more. */
+void orc_splat_gaussians_3dgs(const orc_ref* r, int64_t M, const int64_t* order, const int32_t* chunk,
+                              const int32_t* rect, const double* mean2d, const double* conic,
+                              const double* opacity, const double* rgb, int32_t N, double* planes,
+                              uint8_t* near)
+{
+    const double a_min = 1.0 / 255.0, t_min = 1e-4, window = 1e-6;
+    const int64_t W = r->W, H = r->H;
+    const int64_t plane_sz = W * H * 4;
+    memset(planes, 0, sizeof(double) * (size_t)(plane_sz * N));
+    if (near) memset(near, 0, (size_t)(W * H * N));
+
+    int64_t start[N + 1];
+    {
+        int64_t k = 0;
+        start[0] = 0;
+        for (int64_t i = 0; i < M; ++i) {
+            while (k < chunk[order[i]]) start[++k] = i;
+        }
+        while (k < N) start[++k] = M;
+    }
+
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t k = 0; k < N; ++k) {
+        double* P = planes + plane_sz * k;
+        uint8_t* done = (uint8_t*)calloc((size_t)(W * H), 1);
+        uint8_t* nr = near ? near + W * H * k : NULL;
+        for (int64_t p = 0; p < W * H; ++p) P[4 * p + 3] = 1.0;
+        for (int64_t i = start[k]; i < start[k + 1]; ++i) {
+            const int64_t g = order[i];
+            const int32_t* rc = rect + 4 * g;
+            const double mx = mean2d[2 * g], my = mean2d[2 * g + 1];
+            const double a = conic[3 * g], b = conic[3 * g + 1], c = conic[3 * g + 2];
+            const double o = opacity[g];
+            for (int32_t y = rc[1]; y <= rc[3]; ++y) {
+                for (int32_t x = rc[0]; x <= rc[2]; ++x) {
+                    const int64_t p = (int64_t)y * W + x;
+                    if (done[p]) continue;
+                    const double dx = (double)x - mx, dy = (double)y - my;
+                    const double q = a * dx * dx + 2.0 * b * dx * dy + c * dy * dy;
+                    double al = o * exp(-0.5 * q);
+                    if (al > 0.99) al = 0.99;
+                    if (nr && fabs(al - a_min) <= window) nr[p] = 1;
+                    if (al < a_min) continue;
+                    double* px = P + 4 * p;
+                    const double T = px[3];
+                    const double Tn = T * (1.0 - al);
+                    if (nr && fabs(Tn - t_min) <= window) nr[p] = 1;
+                    if (Tn < t_min) {
+                        done[p] = 1;
+                        continue;
+                    }
+                    px[0] += T * al * rgb[3 * g + 0];
+                    px[1] += T * al * rgb[3 * g + 1];
+                    px[2] += T * al * rgb[3 * g + 2];
+                    px[3] = Tn;
+                }
+            }
+        }
+        for (int64_t p = 0; p < W * H; ++p) P[4 * p + 3] = 1.0 - P[4 * p + 3];
+        free(done);
     }
 }

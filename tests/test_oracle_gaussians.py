@@ -222,3 +222,127 @@ def test_chunk_invariance_with_shifted_reference(orc):
     for N in (3, 16):
         many = orc.render(scene=sc, camera=cam, display=disp, views=S.ViewSet(1), N=N, binning="quantile")
         assert np.allclose(many["views"], base["views"], atol=1e-12)
+
+
+# ---- 3DGS-compatible blending (alpha < 1/255 skipped, stop before T < 1e-4)
+
+def test_3dgs_blend_single_gaussian_alpha_cutoff(orc):
+    # One flat Gaussian (f = 0, exact projection): the texel keeps the
+    # closed-form opacity where it is at least 1/255 and is empty where it is
+    # below; the near-threshold mask marks exactly the texels within 1e-6 of
+    # the cut.
+    cam = S.identity_camera(64, 50.0)
+    disp = S.display_for(3.0, 0.1, f_aa=0.0)
+    sc = H.flat_scene([((0.1, -0.05, 3.5), (0.08, 0.03), 0.7, 0.8, (1, 1, 1))])
+    out = orc.render(scene=sc, camera=cam, display=disp, views=S.ViewSet(1), N=1, binning="quantile",
+                     with_views=False, blend="3dgs")
+    r = out["ref"]
+    A = out["planes"][0, :, :, 3]
+    near = out["near"][0]
+    x0, y0, x1, y1 = out["rect"][0]
+    m = sc.means[0].astype(np.float64)
+    s = sc.scales[0, :2].astype(np.float64)
+    q = sc.quats[0].astype(np.float64)
+    ang = 2 * math.atan2(q[3], q[0])
+    kept = cut = 0
+    for y in range(r.H):
+        for x in range(r.W):
+            if not (x0 <= x <= x1 and y0 <= y <= y1):
+                assert A[y, x] == 0.0 and near[y, x] == 0
+                continue
+            o, d = H.ref_pixel_ray(r, x, y)
+            a = H.flat_gauss_alpha(H.hit_plane_z(o, d, m[2]), m, H.rot2(ang), s, float(sc.opacity[0]))
+            gap = abs(a - 1.0 / 255.0)
+            if abs(gap - 1e-6) > 1e-9:
+                assert near[y, x] == (1 if gap <= 1e-6 else 0)
+            if near[y, x]:
+                continue
+            if a >= 1.0 / 255.0:
+                assert A[y, x] == pytest.approx(a, abs=1e-12)
+                kept += 1
+            else:
+                assert A[y, x] == 0.0
+                cut += 1
+    assert kept > 20 and cut > 20
+
+
+def _layer_scene(n_layers, seed):
+    # wide flat fronto-parallel layers on the optical axis, front to back at
+    # z = 2, 2.25, ...; opacity 0.8 except a faint last layer (0.3), which a
+    # pixel that has stopped must not blend even though its own factor
+    # (1 - alpha) would keep T above 1e-4; distinct colours
+    rng = np.random.default_rng(seed)
+    return H.flat_scene([((0.0, 0.0, 2.0 + 0.25 * i), (2.0, 2.0), 0.0, 0.3 if i == n_layers - 1 else 0.8,
+                          tuple(rng.uniform(0.1, 1.0, 3))) for i in range(n_layers)])
+
+
+def test_3dgs_blend_stops_before_transmittance_cutoff(orc):
+    # Six layers of opacity about 0.8 and a faint seventh: a pixel's
+    # transmittance after m of them is the product of (1 - alpha_j), taken
+    # here from each layer's closed-form opacity. In 3DGS mode a pixel blends
+    # exactly the first m layers, m the count before the first layer that
+    # would take the product below 1e-4 (5 near the centre: 3.2e-4, then
+    # 6.4e-5), and nothing after it, i.e. it equals the exact render of a
+    # scene holding only those m layers.
+    cam = S.identity_camera(16, 50.0)
+    disp = S.display_for(3.0, 0.1, f_aa=0.0)
+    n_layers = 7
+    sc = _layer_scene(n_layers, 1)
+    args = dict(camera=cam, display=disp, views=S.ViewSet(1), N=1, binning="quantile", with_views=False)
+    g3 = orc.render(scene=sc, blend="3dgs", **args)
+    r = g3["ref"]
+    prefix = {m: orc.render(scene=sc.subset(np.arange(m)), **args)["planes"][0] for m in range(1, n_layers + 1)}
+    seen = set()
+    for y in range(r.H):
+        for x in range(r.W):
+            o, d = H.ref_pixel_ray(r, x, y)
+            T, m = 1.0, 0
+            for j in range(n_layers):
+                mj = sc.means[j].astype(np.float64)
+                a = H.flat_gauss_alpha(H.hit_plane_z(o, d, mj[2]), mj, H.rot2(0.0),
+                                       sc.scales[j, :2].astype(np.float64), float(sc.opacity[j]))
+                assert a > 0.05                     # no alpha cut in this scene
+                if T * (1 - a) < 1e-4:
+                    break
+                T *= 1 - a
+                m += 1
+            if g3["near"][0, y, x]:
+                continue
+            assert np.allclose(g3["planes"][0, y, x], prefix[m][y, x], atol=1e-12), (x, y, m)
+            seen.add(m)
+    assert {5, 6} <= seen                              # stops after five and after six layers
+
+
+def test_3dgs_blend_stop_is_per_plane(orc):
+    # The transmittance that decides the stop is the plane's own: split over
+    # two chunks (4 + 3 layers) neither plane gets near 1e-4, so 3DGS mode
+    # gives the exact planes bit for bit, and their composite differs from
+    # the single-plane 3DGS render (which stopped).
+    cam = S.identity_camera(16, 50.0)
+    disp = S.Display(D_focal=3.0, phi_x=0.0)
+    sc = _layer_scene(7, 2)
+    args = dict(camera=cam, display=disp, views=S.ViewSet(1), binning="quantile")
+    exact2 = orc.render(scene=sc, N=2, **args)
+    g3_2 = orc.render(scene=sc, N=2, blend="3dgs", **args)
+    assert np.array_equal(g3_2["planes"], exact2["planes"]) and not g3_2["near"].any()
+    g3_1 = orc.render(scene=sc, N=1, blend="3dgs", **args)
+    assert np.abs(g3_1["views"] - g3_2["views"]).max() > 1e-5
+
+
+def test_3dgs_blend_only_removes_occlusion(orc):
+    # Skipping a member or stopping early only drops factors (1 - alpha) from
+    # a texel's transmittance: A in 3DGS mode never exceeds the exact A, and
+    # the transmittance never goes below 1e-4.
+    cam = S.identity_camera(64, 50.0)
+    disp = S.display_for(3.0, 0.1)
+    sc = _rand_scene(3000, 11)
+    sc.opacity[:] = 0.5 + 0.49 * sc.opacity
+    args = dict(scene=sc, camera=cam, display=disp, views=S.ViewSet(1), N=2, binning="quantile",
+                with_views=False)
+    ex = orc.render(**args)["planes"]
+    g3 = orc.render(blend="3dgs", **args)["planes"]
+    assert (g3[..., 3] <= ex[..., 3] + 1e-12).all()
+    assert g3[..., 3].max() <= 1 - 1e-4 + 1e-15
+    assert (np.abs(g3 - ex).max(axis=-1) > 1e-6).mean() > 0.01      # the cut-offs change many texels
+    with pytest.raises(ValueError):
+        orc.render(blend="bogus", **args)
