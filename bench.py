@@ -489,8 +489,8 @@ def run_sweeps(args, dev):
     st = torch.cuda.current_stream()
     steps, warm = max(5, args.steps // 2), 3
 
-    def fps(display, views, N, dtype):
-        r = api.LightFieldRenderer(wl.camera, display, views, N, wl.binning, dtype, device=dev)
+    def fps(display, views, N, dtype, blend="exact"):
+        r = api.LightFieldRenderer(wl.camera, display, views, N, wl.binning, dtype, device=dev, blend=blend)
         r.capture(g)
         ms = _event_ms(r.replay, steps, warm, st, flush)
         out = {"value": round(1000.0 / ms, 2), "views_per_s": round(1000.0 / ms * views.Vx * views.Vy, 1),
@@ -498,7 +498,11 @@ def run_sweeps(args, dev):
         del r
         return out
 
-    res = {"unit": UNIT, "views": {}, "table1": {}}
+    res = {"unit": UNIT, "views": {}, "table1": {}, "blend_3dgs": {}}
+    # the 3DGS rasteriser's cut-offs (alpha < 1/255 skipped, stop before
+    # T < 1e-4) against exact blending, same frame
+    for dtype in ("f32", "f16"):
+        res["blend_3dgs"][dtype] = fps(wl.display, wl.views, 64, dtype, blend="3dgs")
     for V in (9, 45, 90, 180):
         for dtype in ("f32", "f16"):
             res["views"]["V%d_%s" % (V, dtype)] = fps(wl.display, S.ViewSet(V), 64, dtype)

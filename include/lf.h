@@ -59,6 +59,17 @@ typedef enum {
     LF_BIN_DISPARITY = 1      /* N equal bins in 1/z between nearest and farthest */
 } lf_binning;
 
+/* Blending flag, OR'd into the binning argument of lf_build_mpi_gaussians.
+ * Without it ("exact" mode, the default) every chunk member whose footprint
+ * rectangle holds the pixel is blended. LF_BLEND_3DGS adds the two cut-offs
+ * of the 3DGS rasteriser that Sec. 4.4 renders each chunk with: a member
+ * whose alpha is below 1/255 is skipped, and a pixel stops before the member
+ * that would take its transmittance T (1 - alpha) below 1e-4 (that member
+ * and every later one are left out). Gaussians only: the voxel build and the
+ * batch reject it (LF_ERR_UNSUPPORTED), and the adjoint differentiates exact
+ * mode. */
+enum { LF_BLEND_3DGS = 0x100 };
+
 /* Base camera (Sec. 4.2): world -> camera R (row-major), t; full fields of
  * view theta_x, theta_y in radians; per-view resolution Nx x Ny. */
 typedef struct {
@@ -191,11 +202,12 @@ size_t lf_build_mpi_workspace_size(const lf_ref_camera* ref, int64_t n, int32_t 
  * them (quantile: chunk = floor(rank N / M), d_k = median depth; disparity:
  * equal bins in 1/z), and rasterises each chunk into its plane with the EWA
  * projection of 3DGS plus the dilation f' (alpha = min(0.99, o e^{-q/2}),
- * front to back, no early stop). All planes are written (empty ones with 0).
+ * front to back, no early stop unless binning carries LF_BLEND_3DGS). All
+ * planes are written (empty ones with 0).
  * g: host struct of device pointers; ref, out: host structs; ws: device
  * workspace of ws_bytes; stream: the CUDA stream to enqueue on.
  * Errors: LF_ERR_INVALID_ARG (null pointer, N < 1 or > 65535, plane size not
- * the reference camera's, unknown dtype or binning), LF_ERR_WORKSPACE,
+ * the reference camera's, unknown dtype, binning or flag), LF_ERR_WORKSPACE,
  * LF_ERR_CUDA (launch failure). Tile-list overflow is reported by
  * lf_mpi_status after the stream has run. */
 lf_status lf_build_mpi_gaussians(const lf_gaussians* g, const lf_ref_camera* ref, int32_t N, int32_t binning,

@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "LF_OK", 1: "LF_ERR_INVALID_ARG", 2: "LF_ERR_WORKSPACE", 3: "
 
 LF_F32, LF_F16, LF_BF16, LF_U8 = 0, 1, 2, 3
 LF_BIN_QUANTILE, LF_BIN_DISPARITY = 0, 1
+LF_BLEND_3DGS = 0x100          # OR into the binning argument: 3DGS alpha / transmittance cut-offs
 
 _D = ctypes.c_double
 _I32 = ctypes.c_int32

@@ -19,6 +19,7 @@ from ._lib import check, load
 DTYPES = {"f32": L.LF_F32, "f16": L.LF_F16, "bf16": L.LF_BF16, "u8": L.LF_U8}
 TORCH_DTYPES = {L.LF_F32: torch.float32, L.LF_F16: torch.float16, L.LF_BF16: torch.bfloat16, L.LF_U8: torch.uint8}
 BINNING = {"quantile": L.LF_BIN_QUANTILE, "disparity": L.LF_BIN_DISPARITY}
+BLEND = {"exact": 0, "3dgs": L.LF_BLEND_3DGS}
 
 
 def _stream_ptr(stream: Optional[torch.cuda.Stream]):
@@ -192,12 +193,15 @@ def lf_build_mpi_workspace_size(ref: L.LfRefCamera, n: int, N: int, dup_capacity
 
 
 def lf_build_mpi_gaussians(g: DeviceGaussians, ref: L.LfRefCamera, N: int, binning: str, ws: torch.Tensor,
-                           planes: Planes, stream=None):
-    """Sec. 4.4 / the plane-building steps of Algorithm 1 for 3D Gaussians (asynchronous)."""
+                           planes: Planes, stream=None, blend: str = "exact"):
+    """Sec. 4.4 / the plane-building steps of Algorithm 1 for 3D Gaussians
+    (asynchronous). blend="3dgs" adds the 3DGS rasteriser's cut-offs
+    (alpha < 1/255 skipped, stop before T < 1e-4)."""
     gs = g.c_struct()
     ps = planes.c_struct()
-    check(load().lf_build_mpi_gaussians(ctypes.byref(gs), ctypes.byref(ref), int(N), BINNING[binning],
-                                        _ptr(ws), ws.numel(), ctypes.byref(ps), _stream_ptr(stream)))
+    check(load().lf_build_mpi_gaussians(ctypes.byref(gs), ctypes.byref(ref), int(N),
+                                        BINNING[binning] | BLEND[blend], _ptr(ws), ws.numel(), ctypes.byref(ps),
+                                        _stream_ptr(stream)))
 
 
 def lf_build_mpi_voxels(v: DeviceVoxels, ref: L.LfRefCamera, N: int, binning: str, ws: torch.Tensor,
@@ -353,9 +357,13 @@ class LightFieldRenderer:
     runs splat + composite through the C ABI."""
 
     def __init__(self, camera, display, views, N: int, binning: str = "quantile", dtype: str = "f32",
-                 n_capacity: int = 0, dup_capacity: int = 0, device="cuda", plane_filter: float = 0.0):
+                 n_capacity: int = 0, dup_capacity: int = 0, device="cuda", plane_filter: float = 0.0,
+                 blend: str = "exact"):
+        if blend not in BLEND:
+            raise ValueError("blend must be one of %s" % sorted(BLEND))
         self.camera, self.display, self.views = camera, display, views
         self.N, self.binning, self.dtype = int(N), binning, dtype
+        self.blend = blend                        # "3dgs": 3DGS cut-offs in the Gaussian splat
         self.ref = lf_make_ref_camera(camera, display)
         self.device = device
         self.n_capacity = int(n_capacity)
@@ -380,8 +388,10 @@ class LightFieldRenderer:
         pl = self.planes
         view = Planes(pl.rgba, pl.d, pl.count, pl.chunk[: max(prims.n, 1)], pl.rect[: max(prims.n, 1)], pl.dtype_code)
         if isinstance(prims, DeviceGaussians):
-            lf_build_mpi_gaussians(prims, self.ref, self.N, self.binning, self.ws, view, stream)
+            lf_build_mpi_gaussians(prims, self.ref, self.N, self.binning, self.ws, view, stream, self.blend)
         else:
+            if self.blend != "exact":
+                raise ValueError("3DGS blending applies to Gaussians only")
             lf_build_mpi_voxels(prims, self.ref, self.N, self.binning, self.ws, view, stream)
             if self.plane_filter > 0.0:
                 lf_filter_planes(view, self.plane_filter, 0, stream)
@@ -433,6 +443,8 @@ class LightFieldRenderer:
     def backward(self, prims, dviews: torch.Tensor, stream=None):
         """Gradients of the last render of prims given dL/d(views): composite
         adjoint, then the splat adjoint on the same workspace."""
+        if self.blend != "exact":
+            raise ValueError("the adjoint differentiates exact blending; this renderer uses %r" % self.blend)
         dplanes = torch.empty((self.N, self.ref.H, self.ref.W, 4), dtype=torch.float32, device=self.device)
         lf_composite_backward(self.planes, self.ref, self.views, dviews, dplanes, self.cws, stream)
         view = self.planes_view(prims.n)

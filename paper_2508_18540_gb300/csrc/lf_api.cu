@@ -299,8 +299,12 @@ static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, in
     if (st != LF_OK) return st;
     st = check_planes(out, ref, N);
     if (st != LF_OK) return st;
+    const bool blend3dgs = (binning & LF_BLEND_3DGS) != 0;
+    binning &= ~(int32_t)LF_BLEND_3DGS;
     if (binning != LF_BIN_QUANTILE && binning != LF_BIN_DISPARITY)
-        return fail(LF_ERR_INVALID_ARG, "unknown binning mode");
+        return fail(LF_ERR_INVALID_ARG, "unknown binning mode or flag");
+    if (blend3dgs && (kind != 0 || prefix_only))
+        return fail(LF_ERR_UNSUPPORTED, "3DGS blending is implemented for the single-scene Gaussian build only");
     if (n < 0 || n > (int64_t)0x7fffffff) return fail(LF_ERR_INVALID_ARG, "primitive count out of range");
     if (!ws) return fail(LF_ERR_WORKSPACE, "workspace is NULL");
     if (((uintptr_t)ws) % 256) return fail(LF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
@@ -377,7 +381,7 @@ static lf_status build_common(int64_t n, const lf_ref_camera* ref, int32_t N, in
     fill_raster_params(ref, N, out->dtype, &rp);
     trace_begin(kind == 0 ? "raster_gaussians" : "raster_voxels", stream);
     if (kind == 0)
-        launch_raster_gaussians(w, rp, ranks, out->rgba, stream);
+        launch_raster_gaussians(w, rp, ranks, out->rgba, blend3dgs, stream);
     else
         launch_raster_voxels(w, rp, ranks, out->rgba, stream);
     trace_end(stream);

@@ -78,6 +78,8 @@ lf_status lf_batch_create(const lf_batch_scene* scenes, int32_t n_scenes, lf_bat
     for (int i = 0; i < n_scenes; ++i) {
         const lf_status st = check_scene(scenes[i], i);
         if (st != LF_OK) return st;
+        if (scenes[i].binning & LF_BLEND_3DGS)
+            return fail(LF_ERR_UNSUPPORTED, "lf_batch_create: batches blend in exact mode only");
         if (scenes[i].planes.dtype != scenes[0].planes.dtype || (scenes[i].views.bilinear != 0) !=
                                                                     (scenes[0].views.bilinear != 0))
             return fail(LF_ERR_INVALID_ARG, "lf_batch_create: scenes must share plane dtype and sampling");

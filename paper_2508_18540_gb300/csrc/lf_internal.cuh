@@ -209,8 +209,9 @@ void sort_tile_keys(const BuildWs& ws, long long cap, int tile_bits, cudaStream_
 int tile_sort_passes(int tile_bits);
 int tile_bits_for(long long tiles);
 
+// blend3dgs: the alpha < 1/255 skip and T < 1e-4 stop of the 3DGS rasteriser
 void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
-                             cudaStream_t s);
+                             bool blend3dgs, cudaStream_t s);
 void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
                           cudaStream_t s);
 

@@ -95,8 +95,11 @@ struct GaussSmem {
     int wc[NT / 32];
 };
 
-// One (tile t, chunk k) work item; every thread of the CTA calls it.
-template <int DT, int PPT>
+// One (tile t, chunk k) work item; every thread of the CTA calls it. G3
+// adds the two cut-offs of the 3DGS rasteriser: a member with alpha < 1/255
+// is skipped, and a pixel whose next blend would take T (1 - alpha) below
+// 1e-4 stops blending (bit r of `stopped`).
+template <int DT, int PPT, bool G3 = false>
 __device__ __forceinline__ void raster_gauss_tile(const BuildWs& w, const RasterParams& p,
                                                   const uint32_t* __restrict__ ranks, void* planes, int t, int k,
                                                   GaussSmem<PPT>& sm)
@@ -118,6 +121,7 @@ __device__ __forceinline__ void raster_gauss_tile(const BuildWs& w, const Raster
     const int L = sg.y - sg.x;
     const float fpx = (float)px;
     float C[PPT][3], T[PPT];
+    uint32_t stopped = 0u;
 #pragma unroll
     for (int r = 0; r < PPT; ++r) C[r][0] = C[r][1] = C[r][2] = 0.f, T[r] = 1.f;
     for (int base = 0; base < L; base += NT) {
@@ -167,11 +171,20 @@ __device__ __forceinline__ void raster_gauss_tile(const BuildWs& w, const Raster
                         const float dy = (float)(py0 + r) - e0.y;
                         const float pw = fmaf(dx, fmaf(e0.w, dy, adx), e1.x * dy * dy);
                         const float al = fminf(0.99f, e1.y * ex2_approx(pw));
+                        const float tn = fmaf(-T[r], al, T[r]);
+                        if (G3) {
+                            if ((stopped >> r) & 1u) continue;
+                            if (al < 1.0f / 255.0f) continue;
+                            if (tn < 1e-4f) {
+                                stopped |= 1u << r;
+                                continue;
+                            }
+                        }
                         const float ta = T[r] * al;
                         C[r][0] = fmaf(ta, col.x, C[r][0]);
                         C[r][1] = fmaf(ta, col.y, C[r][1]);
                         C[r][2] = fmaf(ta, col.z, C[r][2]);
-                        T[r] = fmaf(-T[r], al, T[r]);
+                        T[r] = tn;
                     }
                 }
             }
@@ -187,12 +200,12 @@ __device__ __forceinline__ void raster_gauss_tile(const BuildWs& w, const Raster
     }
 }
 
-template <int DT, int PPT>
+template <int DT, int PPT, bool G3>
 __global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, RasterParams p,
                                                                  const uint32_t* __restrict__ ranks, void* planes)
 {
     __shared__ GaussSmem<PPT> sm;
-    raster_gauss_tile<DT, PPT>(w, p, ranks, planes, blockIdx.x, blockIdx.y, sm);
+    raster_gauss_tile<DT, PPT, G3>(w, p, ranks, planes, blockIdx.x, blockIdx.y, sm);
 }
 
 // Persistent form over the (tile, chunk) items of several scenes: CTAs take
@@ -814,18 +827,28 @@ void launch_raster_voxels_bwd(const BuildWs& ws, const RasterParams& p, const ui
     note_launches(1);
 }
 
-void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
-                             cudaStream_t s)
+template <bool G3>
+static void launch_raster_gaussians_mode(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks,
+                                         void* planes, cudaStream_t s)
 {
     const dim3 grid((unsigned)(p.tiles_x * p.tiles_y), (unsigned)p.N);
     constexpr int kPPT = 2;   // pixels per thread
     constexpr int kThreads = kTilePix / kPPT;
     switch (p.dtype) {
-    case LF_F32: k_raster_gauss<LF_F32, kPPT><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
-    case LF_F16: k_raster_gauss<LF_F16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
-    case LF_U8: k_raster_gauss<LF_U8, kPPT><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
-    default: k_raster_gauss<LF_BF16, kPPT><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
+    case LF_F32: k_raster_gauss<LF_F32, kPPT, G3><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
+    case LF_F16: k_raster_gauss<LF_F16, kPPT, G3><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
+    case LF_U8: k_raster_gauss<LF_U8, kPPT, G3><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
+    default: k_raster_gauss<LF_BF16, kPPT, G3><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
     }
+}
+
+void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
+                             bool blend3dgs, cudaStream_t s)
+{
+    if (blend3dgs)
+        launch_raster_gaussians_mode<true>(ws, p, ranks, planes, s);
+    else
+        launch_raster_gaussians_mode<false>(ws, p, ranks, planes, s);
     note_launches(1);
 }
 

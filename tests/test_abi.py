@@ -79,6 +79,13 @@ def test_invalid_arguments_are_rejected(L):
     st = lib.lf_build_mpi_gaussians(ctypes.byref(g), ctypes.byref(ref), 4, 7, ctypes.c_void_p(256), 1 << 20,
                                     ctypes.byref(planes), None)
     assert st == L.LF_ERR_INVALID_ARG                      # unknown binning
+    st = lib.lf_build_mpi_gaussians(ctypes.byref(g), ctypes.byref(ref), 4, 0x200, ctypes.c_void_p(256), 1 << 20,
+                                    ctypes.byref(planes), None)
+    assert st == L.LF_ERR_INVALID_ARG                      # unknown flag bit
+    vox = L.LfVoxels(10, 16, 16, (ctypes.c_double * 3)(0.0, 0.0, 0.0), 1.0, 16, 16)
+    st = lib.lf_build_mpi_voxels(ctypes.byref(vox), ctypes.byref(ref), 4, L.LF_BLEND_3DGS, ctypes.c_void_p(256),
+                                 1 << 20, ctypes.byref(planes), None)
+    assert st == L.LF_ERR_UNSUPPORTED                      # 3DGS blending is for Gaussians
     st = lib.lf_build_mpi_gaussians(ctypes.byref(g), ctypes.byref(ref), 4, 0, None, 0, ctypes.byref(planes), None)
     assert st == L.LF_ERR_WORKSPACE
     st = lib.lf_build_mpi_gaussians(ctypes.byref(g), ctypes.byref(ref), 4, 0, ctypes.c_void_p(256), 100,
