@@ -584,10 +584,33 @@ def cpu_baseline(min_seconds=10.0, max_frames=40):
         if time.perf_counter() - t0 >= min_seconds:
             break
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": round(n_frames / dt, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": round(n_frames / dt, 4), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": "%d full LF frame(s) of the 1M-Gaussian 512px N64 45-view workload, FP64, OpenMP" % n_frames,
-            "seconds": round(dt, 2)}, last["views"]
+            "seconds": round(dt, 2), "host": _host()}, last["views"]
+
+
+def _host():
+    """CPU of the machine the oracle ran on (architecture, model, logical CPUs)."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import subprocess
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            model = next((ln.split(":", 1)[1].strip() for ln in out.splitlines()
+                          if ln.lower().startswith("model name")), "")
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"arch": platform.machine(), "model": model or None, "logical_cpus": os.cpu_count()}
 
 
 def run_reference(args):
@@ -605,14 +628,14 @@ def run_reference(args):
     for _ in range(args.steps):
         oracle.render(wl)
     dt = (time.perf_counter() - t0) / args.steps
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.num_threads()
     v = round(1.0 / dt, 4)
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config({"planes": "f64", "parallelism": "host cores"}),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "one full LF frame per step (warm-up steps splat only)"},
+                             "sample": "one full LF frame per step (warm-up steps splat only)", "host": _host()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

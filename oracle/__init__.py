@@ -86,10 +86,17 @@ def lib():
         L.orc_filter_weights.argtypes = [ctypes.c_double, ctypes.c_int32, _P]
         L.orc_filter_planes.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                         ctypes.c_int32]
+        L.orc_num_threads.argtypes = []
+        L.orc_num_threads.restype = ctypes.c_int
         L.orc_composite.argtypes = [ctypes.POINTER(OrcRef), ctypes.c_int32, _P, _P, _P, ctypes.c_int32,
                                     ctypes.c_int32, ctypes.c_int32, _P, _P]
         _lib = L
     return _lib
+
+
+def num_threads() -> int:
+    """Threads the oracle's OpenMP loops use."""
+    return int(lib().orc_num_threads())
 
 
 def _ptr(a: np.ndarray):

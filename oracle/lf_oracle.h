@@ -153,6 +153,9 @@ void orc_composite(const orc_ref* r, int32_t N, const double* planes, const doub
                    const int64_t* count, int32_t Vx, int32_t Vy, int32_t bilinear,
                    const double* bg, double* views);
 
+/* Threads the oracle's OpenMP loops run on (omp_get_max_threads). */
+int orc_num_threads(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,7 @@
 #include "lf_oracle.h"
 
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -199,4 +200,9 @@ void orc_composite(const orc_ref* r, int32_t N, const double* planes, const doub
     free(hny);
     free(dx);
     free(dy);
+}
+
+int orc_num_threads(void)
+{
+    return omp_get_max_threads();
 }
