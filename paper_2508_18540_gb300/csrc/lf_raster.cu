@@ -189,7 +189,10 @@ __device__ __forceinline__ void raster_gauss_tile(const BuildWs& w, const Raster
                 }
             }
         }
-        __syncthreads();
+        // no barrier here: the next batch's compaction barrier already
+        // waits for every warp to finish walking this batch before any
+        // staged entry is overwritten, and the staging barrier above orders
+        // the reads of s_wc before its next write
     }
     if (px < p.W) {
 #pragma unroll
