@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
     const int py = ty * kTile + (threadIdx.x / kTile);
+    const int vy0 = ty * kTile + 2 * (threadIdx.x >> 5), vy1 = vy0 + 1;   // this warp's two rows
     const int st = (ty / kTilesPerSuper) * p.supers_x + tx / kTilesPerSuper;
     const int2 sg = w.seg[(size_t)st * p.N + k];
     const int L = sg.y - sg.x;
@@ -329,50 +330,65 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
             s_rect[slot] = r;
         }
         __syncthreads();
-        for (int j = 0; j < cnt; ++j) {
-            const int4 rc = s_rect[j];
-            if (!(px >= rc.x && px <= rc.z && py >= rc.y && py <= rc.w)) continue;
-            const float4 b = s_box[j];  // cube low corner relative to the ray origin, side
-            const float lo[3] = {b.x, b.y, b.z};
-            float t0 = -__int_as_float(0x7f800000), t1 = __int_as_float(0x7f800000);
-            bool miss = false;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float hi = lo[a] + b.w;
-                if (d[a] != 0.0f) {
-                    float ta = lo[a] * inv[a], tb = hi * inv[a];
-                    if (ta > tb) {
-                        const float tmp = ta;
-                        ta = tb;
-                        tb = tmp;
-                    }
-                    t0 = fmaxf(t0, ta);
-                    t1 = fminf(t1, tb);
-                } else if (0.0f < lo[a] || 0.0f > hi) {
-                    miss = true;
-                }
+        // every warp (two rows of the tile) ballots which staged voxels touch
+        // its rows and visits only those, in list order
+        for (int m0 = 0; m0 < cnt; m0 += 32) {
+            const int jl = m0 + (threadIdx.x & 31);
+            bool touches = false;
+            if (jl < cnt) {
+                const int4 rl = s_rect[jl];
+                touches = rl.y <= vy1 && rl.w >= vy0;
             }
-            t0 = fmaxf(t0, 0.0f);
-            if (miss || !(t1 > t0)) continue;
-            const float tm = 0.5f * (t0 + t1);
-            const float is = s_inv_side[j];
-            const float* cf = s_den + 8 * j;
-            const float s0 = trilinear_poly(cf, clamp01((t0 * d[0] - lo[0]) * is), clamp01((t0 * d[1] - lo[1]) * is),
-                                            clamp01((t0 * d[2] - lo[2]) * is));
-            const float sm = trilinear_poly(cf, clamp01((tm * d[0] - lo[0]) * is), clamp01((tm * d[1] - lo[1]) * is),
-                                            clamp01((tm * d[2] - lo[2]) * is));
-            const float s1 = trilinear_poly(cf, clamp01((t1 * d[0] - lo[0]) * is), clamp01((t1 * d[1] - lo[1]) * is),
-                                            clamp01((t1 * d[2] - lo[2]) * is));
-            const float integral = (t1 - t0) * (1.0f / 6.0f) * (s0 + 4.0f * sm + s1);
-            const float al = 1.0f - __expf(-integral);
-            const float4 col = s_rgb[j];
-            const float ta = T * al;
-            C0 = fmaf(ta, col.x, C0);
-            C1 = fmaf(ta, col.y, C1);
-            C2 = fmaf(ta, col.z, C2);
-            T = T * (1.0f - al);
+            uint32_t vmask = __ballot_sync(0xffffffffu, touches);
+            while (vmask) {
+                const int j = m0 + __ffs(vmask) - 1;
+                vmask &= vmask - 1;
+                const int4 rc = s_rect[j];
+                if (!(px >= rc.x && px <= rc.z && py >= rc.y && py <= rc.w)) continue;
+                const float4 b = s_box[j];  // cube low corner relative to the ray origin, side
+                const float lo[3] = {b.x, b.y, b.z};
+                float t0 = -__int_as_float(0x7f800000), t1 = __int_as_float(0x7f800000);
+                bool miss = false;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float hi = lo[a] + b.w;
+                    if (d[a] != 0.0f) {
+                        float ta = lo[a] * inv[a], tb = hi * inv[a];
+                        if (ta > tb) {
+                            const float tmp = ta;
+                            ta = tb;
+                            tb = tmp;
+                        }
+                        t0 = fmaxf(t0, ta);
+                        t1 = fminf(t1, tb);
+                    } else if (0.0f < lo[a] || 0.0f > hi) {
+                        miss = true;
+                    }
+                }
+                t0 = fmaxf(t0, 0.0f);
+                if (miss || !(t1 > t0)) continue;
+                const float tm = 0.5f * (t0 + t1);
+                const float is = s_inv_side[j];
+                const float* cf = s_den + 8 * j;
+                const float s0 = trilinear_poly(cf, clamp01((t0 * d[0] - lo[0]) * is),
+                                                clamp01((t0 * d[1] - lo[1]) * is), clamp01((t0 * d[2] - lo[2]) * is));
+                const float sm = trilinear_poly(cf, clamp01((tm * d[0] - lo[0]) * is),
+                                                clamp01((tm * d[1] - lo[1]) * is), clamp01((tm * d[2] - lo[2]) * is));
+                const float s1 = trilinear_poly(cf, clamp01((t1 * d[0] - lo[0]) * is),
+                                                clamp01((t1 * d[1] - lo[1]) * is), clamp01((t1 * d[2] - lo[2]) * is));
+                const float integral = (t1 - t0) * (1.0f / 6.0f) * (s0 + 4.0f * sm + s1);
+                const float al = 1.0f - __expf(-integral);
+                const float4 col = s_rgb[j];
+                const float ta = T * al;
+                C0 = fmaf(ta, col.x, C0);
+                C1 = fmaf(ta, col.y, C1);
+                C2 = fmaf(ta, col.z, C2);
+                T = T * (1.0f - al);
+            }
         }
-        __syncthreads();
+        // no barrier here: the next batch's compaction barrier already
+        // waits for every warp to finish this batch before any staged entry
+        // is overwritten
     }
     if (px < p.W && py < p.H) store_texel<DT>(planes, ((size_t)k * p.H + py) * p.W + px, C0, C1, C2, 1.0f - T);
 }
