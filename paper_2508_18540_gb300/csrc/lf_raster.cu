@@ -271,11 +271,83 @@ __device__ __forceinline__ float trilinear_poly(const float* c, float fx, float 
     return fmaf(fx, b, fmaf(fy, e, fmaf(fz, c[3], c[0])));
 }
 
-// Voxels: one thread per pixel (256 threads); cube corner relative to the
-// reference centre and side from the projection pass, densities and colour
-// in rank order.
+// Opacity of one voxel for one pixel's reference ray (unit direction d,
+// inv = 1 / d): the ray's parameter interval inside the cube (slab test),
+// then Simpson's rule on the trilinear density, exact for the cubic it
+// becomes along a line; 0 when the ray misses the cube.
+__device__ __forceinline__ float voxel_alpha(const float4 b, const float is, const float* cf, const float d[3],
+                                             const float inv[3])
+{
+    const float lo[3] = {b.x, b.y, b.z};   // cube low corner relative to the ray origin; b.w = side
+    float t0 = -__int_as_float(0x7f800000), t1 = __int_as_float(0x7f800000);
+    bool miss = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float hi = lo[a] + b.w;
+        if (d[a] != 0.0f) {
+            float ta = lo[a] * inv[a], tb = hi * inv[a];
+            if (ta > tb) {
+                const float tmp = ta;
+                ta = tb;
+                tb = tmp;
+            }
+            t0 = fmaxf(t0, ta);
+            t1 = fminf(t1, tb);
+        } else if (0.0f < lo[a] || 0.0f > hi) {
+            miss = true;
+        }
+    }
+    t0 = fmaxf(t0, 0.0f);
+    if (miss || !(t1 > t0)) return 0.0f;
+    const float tm = 0.5f * (t0 + t1);
+    const float s0 = trilinear_poly(cf, clamp01((t0 * d[0] - lo[0]) * is), clamp01((t0 * d[1] - lo[1]) * is),
+                                    clamp01((t0 * d[2] - lo[2]) * is));
+    const float sm = trilinear_poly(cf, clamp01((tm * d[0] - lo[0]) * is), clamp01((tm * d[1] - lo[1]) * is),
+                                    clamp01((tm * d[2] - lo[2]) * is));
+    const float s1 = trilinear_poly(cf, clamp01((t1 * d[0] - lo[0]) * is), clamp01((t1 * d[1] - lo[1]) * is),
+                                    clamp01((t1 * d[2] - lo[2]) * is));
+    const float integral = (t1 - t0) * (1.0f / 6.0f) * (s0 + 4.0f * sm + s1);
+    return 1.0f - __expf(-integral);
+}
+
+// Exclusive prefix sum of one value per thread over a 256-thread block (in
+// thread order); s_ws: [8] ints; *total receives the block sum.
+__device__ __forceinline__ int block_exscan_256(int v, int* s_ws, int* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_ws[warp] = x;
+    __syncthreads();
+    int before = 0, sum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int s = s_ws[q];
+        before += q < warp ? s : 0;
+        sum += s;
+    }
+    *total = sum;
+    return before + x - v;
+}
+
+constexpr int kVoxPairs = 2048;   // (voxel, pixel) opacities held in shared memory per pass
+
+// Voxels: one CTA of 256 threads per (16x16 tile, chunk), thread t owning
+// tile pixel (t % 16, t / 16). A voxel's footprint covers only a few pixels,
+// so each batch of staged voxels is processed pair-parallel: the footprints
+// clipped to the tile are numbered (voxel order, then rows, then columns),
+// every thread computes the opacities of pairs t, t + 256, ... into shared
+// memory, and then every pixel blends its pairs front to back in list order
+// (each warp visits only the voxels that touch its two rows). A pair whose
+// ray misses the cube has opacity 0, which leaves C and T unchanged exactly.
+// Cube corner relative to the reference centre and side come from the
+// projection pass; densities and colour in rank order.
 template <int DT>
-__global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterParams p,
+__global__ void __launch_bounds__(kTilePix, 5) k_raster_voxel(BuildWs w, RasterParams p,
                                                            const uint32_t* __restrict__ ranks, void* planes)
 {
     constexpr int NT = kTilePix;
@@ -283,28 +355,38 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
     __shared__ float s_inv_side[NT];   // 1 / side, once per staged voxel
     __shared__ float s_den[NT * 8];    // trilinear polynomial coefficients per voxel
     __shared__ float4 s_rgb[NT];
-    __shared__ int4 s_rect[NT];
+    __shared__ int4 s_rect[NT];        // footprint clipped to the tile, tile-local (x0, y0, x1, y1)
+    __shared__ int s_off[NT];          // number of the voxel's first pair
+    __shared__ float4 s_dir[NT];       // per pixel: unit reference-ray direction
+    __shared__ float4 s_inv[NT];       // per pixel: its reciprocal
+    __shared__ uint16_t s_pair[kVoxPairs];   // voxel slot | x << 8 | y << 12 (tile-local pixel)
+    __shared__ float s_alpha[kVoxPairs];
     __shared__ int s_wc[NT / 32];
+    __shared__ int s_ws[NT / 32];
     const int t = blockIdx.x, k = blockIdx.y;
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
-    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py = ty * kTile + (threadIdx.x / kTile);
-    const int vy0 = ty * kTile + 2 * (threadIdx.x >> 5), vy1 = vy0 + 1;   // this warp's two rows
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    const int px = tx * kTile + lx, py = ty * kTile + ly;
+    const int wy0 = 2 * (threadIdx.x >> 5), wy1 = wy0 + 1;   // this warp's two tile rows
     const int st = (ty / kTilesPerSuper) * p.supers_x + tx / kTilesPerSuper;
     const int2 sg = w.seg[(size_t)st * p.N + k];
     const int L = sg.y - sg.x;
 
-    // world-frame direction of the reference ray through this pixel centre
-    const float dcx = ((float)px - p.cx) / p.fx, dcy = ((float)py - p.cy) / p.fy;
-    float d[3];
+    {
+        // world-frame direction of the reference ray through this pixel centre
+        const float dcx = ((float)px - p.cx) / p.fx, dcy = ((float)py - p.cy) / p.fy;
+        float d[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = fmaf(p.Rt[3 * a], dcx, fmaf(p.Rt[3 * a + 1], dcy, p.Rt[3 * a + 2]));
-    const float nrm = rsqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
-    float inv[3];
+        for (int a = 0; a < 3; ++a) d[a] = fmaf(p.Rt[3 * a], dcx, fmaf(p.Rt[3 * a + 1], dcy, p.Rt[3 * a + 2]));
+        const float nrm = rsqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+        float inv[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        d[a] *= nrm;
-        inv[a] = 1.0f / d[a];
+        for (int a = 0; a < 3; ++a) {
+            d[a] *= nrm;
+            inv[a] = 1.0f / d[a];
+        }
+        s_dir[threadIdx.x] = make_float4(d[0], d[1], d[2], 0.f);
+        s_inv[threadIdx.x] = make_float4(inv[0], inv[1], inv[2], 0.f);
     }
 
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
@@ -319,7 +401,10 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
         const bool hit = i < L && meets_tile(r, tx * kTile, ty * kTile);
         int cnt;
         const int slot = compact_slot<NT>(hit, s_wc, &cnt);
+        int4 cr = make_int4(0, 0, -1, -1);
         if (hit) {
+            cr = make_int4(max(r.x - tx * kTile, 0), max(r.y - ty * kTile, 0), min(r.z - tx * kTile, kTile - 1),
+                           min(r.w - ty * kTile, kTile - 1));
             const float4 box = w.r_geo[rk];
             s_box[slot] = box;
             s_inv_side[slot] = 1.0f / box.w;
@@ -327,68 +412,61 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel(BuildWs w, RasterPara
             const float rho8[8] = {da.x, da.y, da.z, da.w, db.x, db.y, db.z, db.w};
             trilinear_coeffs(rho8, s_den + 8 * slot);   // polynomial coefficients, not corners
             s_rgb[slot] = w.r_rgb[rk];
-            s_rect[slot] = r;
+            s_rect[slot] = cr;
         }
+        // pairs are numbered in slot order, which is thread order among the hits
+        int P;
+        const int off = block_exscan_256(hit ? (cr.z - cr.x + 1) * (cr.w - cr.y + 1) : 0, s_ws, &P);
+        if (hit) s_off[slot] = off;
         __syncthreads();
-        // every warp (two rows of the tile) ballots which staged voxels touch
-        // its rows and visits only those, in list order
-        for (int m0 = 0; m0 < cnt; m0 += 32) {
-            const int jl = m0 + (threadIdx.x & 31);
-            bool touches = false;
-            if (jl < cnt) {
-                const int4 rl = s_rect[jl];
-                touches = rl.y <= vy1 && rl.w >= vy0;
+        for (int c0 = 0; c0 < P; c0 += kVoxPairs) {
+            const int c1 = min(P, c0 + kVoxPairs);
+            if (hit && off < c1) {
+                int q = off;
+                for (int yy = cr.y; yy <= cr.w && q < c1; ++yy)
+                    for (int xx = cr.x; xx <= cr.z && q < c1; ++xx, ++q)
+                        if (q >= c0) s_pair[q - c0] = (uint16_t)(slot | (xx << 8) | (yy << 12));
             }
-            uint32_t vmask = __ballot_sync(0xffffffffu, touches);
-            while (vmask) {
-                const int j = m0 + __ffs(vmask) - 1;
-                vmask &= vmask - 1;
-                const int4 rc = s_rect[j];
-                if (!(px >= rc.x && px <= rc.z && py >= rc.y && py <= rc.w)) continue;
-                const float4 b = s_box[j];  // cube low corner relative to the ray origin, side
-                const float lo[3] = {b.x, b.y, b.z};
-                float t0 = -__int_as_float(0x7f800000), t1 = __int_as_float(0x7f800000);
-                bool miss = false;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float hi = lo[a] + b.w;
-                    if (d[a] != 0.0f) {
-                        float ta = lo[a] * inv[a], tb = hi * inv[a];
-                        if (ta > tb) {
-                            const float tmp = ta;
-                            ta = tb;
-                            tb = tmp;
-                        }
-                        t0 = fmaxf(t0, ta);
-                        t1 = fminf(t1, tb);
-                    } else if (0.0f < lo[a] || 0.0f > hi) {
-                        miss = true;
-                    }
+            __syncthreads();
+            for (int q = threadIdx.x; q < c1 - c0; q += NT) {
+                const uint32_t e = s_pair[q];
+                const int j = e & 0xff, pix = (int)((e >> 12) << 4) + (int)((e >> 8) & 15);
+                const float4 dd = s_dir[pix], iv = s_inv[pix];
+                const float d[3] = {dd.x, dd.y, dd.z}, inv[3] = {iv.x, iv.y, iv.z};
+                s_alpha[q] = voxel_alpha(s_box[j], s_inv_side[j], s_den + 8 * j, d, inv);
+            }
+            __syncthreads();
+            // every warp ballots which staged voxels touch its rows and
+            // visits only those, in list order; each pixel takes its pair
+            // if it lies in this pass
+            for (int m0 = 0; m0 < cnt; m0 += 32) {
+                const int jl = m0 + (threadIdx.x & 31);
+                bool touches = false;
+                if (jl < cnt) {
+                    const int4 rl = s_rect[jl];
+                    touches = rl.y <= wy1 && rl.w >= wy0;
                 }
-                t0 = fmaxf(t0, 0.0f);
-                if (miss || !(t1 > t0)) continue;
-                const float tm = 0.5f * (t0 + t1);
-                const float is = s_inv_side[j];
-                const float* cf = s_den + 8 * j;
-                const float s0 = trilinear_poly(cf, clamp01((t0 * d[0] - lo[0]) * is),
-                                                clamp01((t0 * d[1] - lo[1]) * is), clamp01((t0 * d[2] - lo[2]) * is));
-                const float sm = trilinear_poly(cf, clamp01((tm * d[0] - lo[0]) * is),
-                                                clamp01((tm * d[1] - lo[1]) * is), clamp01((tm * d[2] - lo[2]) * is));
-                const float s1 = trilinear_poly(cf, clamp01((t1 * d[0] - lo[0]) * is),
-                                                clamp01((t1 * d[1] - lo[1]) * is), clamp01((t1 * d[2] - lo[2]) * is));
-                const float integral = (t1 - t0) * (1.0f / 6.0f) * (s0 + 4.0f * sm + s1);
-                const float al = 1.0f - __expf(-integral);
-                const float4 col = s_rgb[j];
-                const float ta = T * al;
-                C0 = fmaf(ta, col.x, C0);
-                C1 = fmaf(ta, col.y, C1);
-                C2 = fmaf(ta, col.z, C2);
-                T = T * (1.0f - al);
+                uint32_t vmask = __ballot_sync(0xffffffffu, touches);
+                while (vmask) {
+                    const int j = m0 + __ffs(vmask) - 1;
+                    vmask &= vmask - 1;
+                    const int4 rc = s_rect[j];
+                    if (lx < rc.x || lx > rc.z || ly < rc.y || ly > rc.w) continue;
+                    const int q = s_off[j] + (ly - rc.y) * (rc.z - rc.x + 1) + (lx - rc.x);
+                    if (q < c0 || q >= c1) continue;
+                    const float al = s_alpha[q - c0];
+                    const float4 col = s_rgb[j];
+                    const float ta = T * al;
+                    C0 = fmaf(ta, col.x, C0);
+                    C1 = fmaf(ta, col.y, C1);
+                    C2 = fmaf(ta, col.z, C2);
+                    T = T * (1.0f - al);
+                }
             }
+            // another pass of this batch overwrites s_pair and s_alpha; the
+            // next batch writes them only after its staging barrier
+            if (c1 < P) __syncthreads();
         }
-        // no barrier here: the next batch's compaction barrier already
-        // waits for every warp to finish this batch before any staged entry
-        // is overwritten
     }
     if (px < p.W && py < p.H) store_texel<DT>(planes, ((size_t)k * p.H + py) * p.W + px, C0, C1, C2, 1.0f - T);
 }
