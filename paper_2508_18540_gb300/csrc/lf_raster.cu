@@ -10,9 +10,13 @@
 //     q = d^T Sigma_2^{-1} d inside the primitive's footprint rectangle;
 //   voxels (Sec. 4.5, SVR model): alpha = 1 - exp(-integral of the trilinear
 //     density along the pixel's reference ray inside the cube), by Simpson's
-//     rule, exact for the cubic the trilinear density becomes along a line;
-//   C += T alpha rgb, T *= 1 - alpha. No early stop, no small-alpha skip.
-// The texel (C, 1 - T) is stored as FP32, FP16 or BF16 (FP32 accumulation).
+//     rule, exact for the cubic the trilinear density becomes along a line
+//     (computed pair-parallel into shared memory first: voxel footprints
+//     cover only a few pixels);
+//   C += T alpha rgb, T *= 1 - alpha. No early stop and no small-alpha skip,
+//   unless the Gaussian build asks for the 3DGS cut-offs.
+// The texel (C, 1 - T) is stored as FP32, FP16, BF16 or RGBA8 (FP32
+// accumulation).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
