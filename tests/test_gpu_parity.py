@@ -172,6 +172,27 @@ def test_voxels(orc, dtype):
     _compare(gpu, o, o["ref"].W, o["ref"].H, 16, dtype, check_lists=(dtype == "f32"))
 
 
+def test_voxels_large_footprints(orc):
+    # a dense block of coarse voxels (side 0.5 at depth 3 to 8, 64^2 views):
+    # footprints of about 10x10 pixels, so one batch of staged voxels holds
+    # more (voxel, pixel) pairs than a shared-memory pass (up to ~3200
+    # against 2048) and is processed in several passes
+    rng = np.random.default_rng(11)
+    n1 = 10
+    ii, jj, kk = np.meshgrid(np.arange(n1), np.arange(n1), np.arange(n1), indexing="ij")
+    ijk = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], 1).astype(np.int32)
+    n = ijk.shape[0]
+    base = 0.5
+    sc = S.VoxelScene(ijk, np.zeros(n, np.uint8), np.array([-n1 * base / 2, -n1 * base / 2, 3.0]), base,
+                      rng.uniform(0.05, 1.5, (n, 8)).astype(np.float32), rng.uniform(0, 1, (n, 3)).astype(np.float32))
+    cam = S.identity_camera(64)
+    disp = S.display_for(5.0, 0.15)
+    views = S.ViewSet(3)
+    o = orc.render(scene=sc, camera=cam, display=disp, views=views, N=1, binning="quantile")
+    gpu = G.run_gpu(sc, cam, disp, views, 1, "quantile", "f32")
+    _compare(gpu, o, o["ref"].W, o["ref"].H, 1, "f32")
+
+
 def test_voxels_rotated(orc):
     sc = S.sparse_voxels(5_000, 4, base_res=32)
     cam = G.small_rotated_camera(64, 48)
