@@ -345,7 +345,9 @@ lf_status lf_build_mpi_backward_voxels(const lf_voxels* v, const lf_ref_camera* 
  * keeps alive (and unmoved) for the life of the batch; the fields mean what
  * they mean for lf_build_mpi_gaussians (ws: its build workspace) and
  * lf_composite (cws: its composite workspace, out: its views). All scenes of
- * a batch share planes.dtype and views.bilinear. */
+ * a batch share planes.dtype and views.bilinear. Batches blend in exact
+ * mode: lf_batch_create rejects a binning carrying LF_BLEND_3DGS
+ * (LF_ERR_UNSUPPORTED). */
 typedef struct {
     lf_gaussians g;
     lf_ref_camera ref;
