@@ -91,6 +91,40 @@ def test_flat_gaussian_projection_is_exact(orc):
                 assert A[y, x] == 0.0
 
 
+def test_opacity_is_clamped_at_099(orc):
+    # alpha = min(0.99, o exp(-q/2)): a nearly opaque, wide flat Gaussian
+    # (o = 0.9995, sigma 2 x 1.5 at depth 3) gives exactly 0.99 wherever
+    # o exp(-q/2) exceeds it and the closed-form value elsewhere.
+    cam = S.identity_camera(32, 50.0)
+    disp = S.display_for(3.0, 0.1, f_aa=0.0)
+    sc = H.flat_scene([((0.0, 0.0, 3.0), (2.0, 1.5), 0.3, 0.9995, (1, 1, 1))])
+    out = orc.render(scene=sc, camera=cam, display=disp, views=S.ViewSet(1), N=1, binning="quantile",
+                     with_views=False)
+    r = out["ref"]
+    A = out["planes"][0, :, :, 3]
+    x0, y0, x1, y1 = out["rect"][0]
+    m = sc.means[0].astype(np.float64)
+    s = sc.scales[0, :2].astype(np.float64)
+    q = sc.quats[0].astype(np.float64)
+    ang = 2 * math.atan2(q[3], q[0])
+    o32 = float(sc.opacity[0])
+    clamped = free = 0
+    for y in range(y0, y1 + 1):
+        for x in range(x0, x1 + 1):
+            o, d = H.ref_pixel_ray(r, x, y)
+            P = H.hit_plane_z(o, d, m[2])
+            Sxy = H.rot2(ang) @ np.diag(s ** 2) @ H.rot2(ang).T
+            dd = P[:2] - m[:2]
+            raw = o32 * math.exp(-0.5 * dd @ np.linalg.solve(Sxy, dd))
+            if raw > 0.99 + 1e-9:
+                assert A[y, x] == 0.99
+                clamped += 1
+            elif raw < 0.99 - 1e-9:
+                assert A[y, x] == pytest.approx(raw, abs=1e-12)
+                free += 1
+    assert clamped > 3 and free > 20
+
+
 def test_footprint_contains_three_sigma_ellipse(orc):
     # Every plane pixel inside the 3-sigma ellipse of the projected Gaussian
     # (q <= 9) lies inside the FP32 footprint rectangle.

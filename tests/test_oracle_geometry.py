@@ -37,6 +37,26 @@ def test_reference_fov_identity(orc):
         assert r.tthp_x == pytest.approx(r.tphi_x + r.tth_x, rel=1e-13)
 
 
+def test_backward_shift_widens_the_covered_region(orc):
+    # Sec. 4.2: moving the reference camera back by D_shift widens the region
+    # it covers. The reading that achieves this keeps theta' (from the
+    # unshifted D_forward) and moves only the camera: then the frustum's
+    # half-width (z - D_forward) tan(theta'/2) grows by D_shift tan(theta'/2)
+    # at every depth, the focal plane included. Recomputing theta' from the
+    # shifted camera would leave the focal-plane width unchanged instead.
+    for D_f, b, shift in [(3.0, 0.1, 0.1), (2.6087, 0.15, 0.25), (5.0, 0.6, 1.0)]:
+        r0 = _ref(orc, D_f, b)
+        r1 = _ref(orc, D_f, b, D_shift=shift)
+        assert r1.D_forward == pytest.approx(r0.D_forward - shift, rel=1e-14)
+        assert r1.tthp_x == r0.tthp_x and r1.theta_px == r0.theta_px
+        for z in (0.5 * D_f, D_f, 2.0 * D_f):
+            w0 = (z - r0.D_forward) * r0.tthp_x
+            w1 = (z - r1.D_forward) * r1.tthp_x
+            assert w1 - w0 == pytest.approx(shift * r0.tthp_x, rel=1e-12)
+        # unshifted, the reference frustum meets the base frustum at the focal plane
+        assert (D_f - r0.D_forward) * r0.tthp_x == pytest.approx(D_f * r0.tth_x, rel=1e-12)
+
+
 def test_adaptive_dilation(orc):
     # Eq. (gs_prefilter_fix): f' = f P_s^2 when D_shift = 0, and
     # f' = f (P_s (D_f - D_fwd0) / (D_f - D_fwd))^2 after a backward shift.
