@@ -204,3 +204,25 @@ def test_background_and_empty(orc):
     v = out["views"]
     assert np.allclose(v[..., 0], 0.2) and np.allclose(v[..., 1], 0.3) and np.allclose(v[..., 2], 0.4)
     assert np.all(v[..., 3] == 0.0)
+    # one wide flat layer on the focal plane (no parallax, f = 0): every view
+    # pixel is its closed-form opacity a over the background, a c + (1 - a) bg
+    disp0 = S.display_for(3.0, 0.1, f_aa=0.0)
+    sc = H.flat_scene([((0, 0, 3.0), (1.5, 1.0), 0.2, 0.7, (0.9, 0.5, 0.1))])
+    bg = (0.2, 0.3, 0.4)
+    out = orc.render(scene=sc, camera=cam, display=disp0, views=S.ViewSet(3, 1, False, bg), N=1,
+                     binning="quantile")
+    r = out["ref"]
+    m = sc.means[0].astype(np.float64)
+    q = sc.quats[0].astype(np.float64)
+    ang = 2 * math.atan2(q[3], q[0])
+    x0, y0, x1, y1 = out["rect"][0]
+    for y in range(r.H):
+        for x in range(r.W):
+            if not (x0 <= x <= x1 and y0 <= y <= y1):
+                continue
+            o, d = H.ref_pixel_ray(r, x, y)
+            a = H.flat_gauss_alpha(H.hit_plane_z(o, d, m[2]), m, H.rot2(ang), sc.scales[0, :2].astype(np.float64),
+                                   float(sc.opacity[0]))
+            want = [a * float(sc.rgb[0, ch]) + (1 - a) * bg[ch] for ch in range(3)] + [a]
+            for k in range(3):
+                assert np.allclose(out["views"][k, y, x], want, atol=1e-12)

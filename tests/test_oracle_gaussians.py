@@ -184,14 +184,20 @@ def test_culling(orc):
     cam = S.identity_camera(64, 50.0)
     disp = S.display_for(3.0, 0.1)
     r = orc.make_ref(cam, disp)
-    sc = _rand_scene(4, 7)
+    sc = _rand_scene(6, 7)
     sc.means[0] = [0.0, 0.0, 0.1]       # behind the near plane (after D_forward)
     sc.means[1] = [50.0, 0.0, 3.0]      # far outside the frustum
     sc.means[2] = [0.0, 0.0, 3.0]       # centre
     sc.means[3] = [0.0, 0.0, -2.0]      # behind the camera
+    # in front of the reference camera but nearer than z_near (0.2): culled;
+    # just past z_near: kept
+    sc.means[4] = [0.0, 0.0, r.D_forward + 0.15]
+    sc.means[5] = [0.0, 0.0, r.D_forward + 0.25]
+    sc.scales[4:6] = 0.001
     z, valid, rect = orc.gauss_decide(r, sc)
-    assert valid.tolist() == [0, 0, 1, 0]
+    assert valid.tolist() == [0, 0, 1, 0, 0, 1]
     assert z[2] == pytest.approx(3.0 - r.D_forward, rel=1e-15)
+    assert 0.0 < z[4] < disp.z_near < z[5]
 
 
 def test_depth_order_and_ties(orc):

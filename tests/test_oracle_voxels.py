@@ -153,6 +153,26 @@ def test_voxel_depth_is_centre_depth(orc):
         assert z[v] == pytest.approx(c[2] - r.D_forward, rel=1e-15)
 
 
+def test_voxel_near_plane_culling(orc):
+    # a voxel is kept only if its whole cube lies past z_near (0.2) on
+    # reference depth: a cube straddling z_near, or one between the
+    # reference camera and z_near, is culled; one just beyond is kept
+    cam = S.identity_camera(32)
+    disp = S.display_for(3.0, 0.1)
+    r = orc.make_ref(cam, disp)
+    side = 0.05
+    lows = [r.D_forward + 0.18, r.D_forward + 0.05, r.D_forward + 0.21, 1.0]   # cube low z (base frame)
+    ijk = np.array([[-1, -1, 0]] * len(lows), np.int32)
+    rng = np.random.default_rng(3)
+    dens = rng.uniform(0, 6, (len(lows), 8)).astype(np.float32)
+    rgb = rng.uniform(0, 1, (len(lows), 3)).astype(np.float32)
+    valid = []
+    for zlo, d8, c in zip(lows, dens, rgb):
+        sc = S.VoxelScene(ijk[:1], np.zeros(1, np.uint8), np.array([0.0, 0.0, zlo]), side, d8[None], c[None])
+        valid.append(int(orc.voxel_decide(r, sc)[1][0]))
+    assert valid == [0, 0, 1, 1]
+
+
 def test_generated_sparse_grid(orc):
     # small version of the 3-level sparse grid workload
     sc = S.sparse_voxels(20_000, 0, base_res=64)
