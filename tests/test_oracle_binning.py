@@ -34,6 +34,10 @@ def test_quantile_partition_and_median(orc, n, N):
     nz = count[count > 0]
     assert nz.max() - nz.min() <= 1
     assert np.all(np.diff(chunk[order]) >= 0)
+    # chunk k begins at rank ceil(k M / N): rank r belongs to chunk k exactly
+    # when k M <= r N < (k + 1) M (the reading chunk = floor(r N / M))
+    starts = np.concatenate([[0], np.cumsum(count)[:-1]])
+    assert [int(x) for x in starts] == [-(-k * M // N) for k in range(N)]
     # plane distance = median member depth (base frame: + D_forward)
     for k in range(N):
         if count[k]:
