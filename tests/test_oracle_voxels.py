@@ -81,7 +81,9 @@ def _cameras():
     R = np.array([[math.cos(a), 0, math.sin(a)], [0, 1, 0], [-math.sin(a), 0, math.cos(a)]])
     c2 = S.identity_camera(32, 50.0, t=(0.1, 0.0, 0.4))
     c2.R = R
-    return [S.identity_camera(32, 50.0), c2]
+    # non-square: different focal lengths along x and y
+    c3 = S.Camera(np.eye(3), np.zeros(3), math.radians(50.0), math.radians(34.0), 40, 24)
+    return [S.identity_camera(32, 50.0), c2, c3]
 
 
 def _ref_ray_world(r, cam, x, y):
@@ -96,7 +98,7 @@ def _ref_ray_world(r, cam, x, y):
     return o, d / np.linalg.norm(d)
 
 
-@pytest.mark.parametrize("ci", [0, 1])
+@pytest.mark.parametrize("ci", [0, 1, 2])
 def test_voxel_footprint_contains_every_hitting_ray(orc, ci):
     cam = _cameras()[ci]
     disp = S.display_for(3.0, 0.1)
@@ -119,7 +121,7 @@ def test_voxel_footprint_contains_every_hitting_ray(orc, ci):
     assert n_hit > 40
 
 
-@pytest.mark.parametrize("ci", [0, 1])
+@pytest.mark.parametrize("ci", [0, 1, 2])
 def test_single_voxel_plane_is_its_opacity(orc, ci):
     cam = _cameras()[ci]
     disp = S.display_for(3.0, 0.1)
@@ -139,6 +141,25 @@ def test_single_voxel_plane_is_its_opacity(orc, ci):
             a, _ = orc.voxel_alpha(lo, s, sc.density8[0], o, d)
             assert P[y, x, 3] == pytest.approx(a, abs=1e-12)
             assert np.allclose(P[y, x, :3], a * sc.rgb[0], atol=1e-12)
+
+
+def test_two_voxels_compose_front_to_back(orc):
+    # two overlapping voxels in one chunk blend with the "over" operator:
+    # colour C_front + (1 - A_front) C_back, opacity 1 - (1 - A_front)(1 - A_back),
+    # where each single-voxel plane is rendered alone
+    cam = S.identity_camera(32, 50.0)
+    disp = S.display_for(3.0, 0.1)
+    rng = np.random.default_rng(21)
+    ijk = np.array([[-1, -1, 0], [-1, -1, 1]], np.int32)
+    sc = S.VoxelScene(ijk, np.zeros(2, np.uint8), np.array([0.1, 0.05, 3.0]), 0.4,
+                      rng.uniform(0.5, 3.0, (2, 8)).astype(np.float32), rng.uniform(0, 1, (2, 3)).astype(np.float32))
+    args = dict(camera=cam, display=disp, views=S.ViewSet(1), N=1, binning="quantile", with_views=False)
+    both = orc.render(scene=sc, **args)["planes"][0]
+    front = orc.render(scene=sc.subset([0]), **args)["planes"][0]
+    back = orc.render(scene=sc.subset([1]), **args)["planes"][0]
+    assert ((front[..., 3] > 0.05) & (back[..., 3] > 0.05)).sum() >= 10
+    assert np.allclose(both[..., :3], front[..., :3] + (1 - front[..., 3:]) * back[..., :3], atol=1e-12)
+    assert np.allclose(1 - both[..., 3], (1 - front[..., 3]) * (1 - back[..., 3]), atol=1e-12)
 
 
 def test_voxel_depth_is_centre_depth(orc):
