@@ -193,6 +193,40 @@ def test_bilinear_at_texel_centres_equals_nearest(orc):
     assert np.allclose(a["views"], b["views"], atol=1e-9)
 
 
+def test_bilinear_taps_outside_the_plane_are_transparent(orc):
+    # reading: a bilinear tap outside the plane contributes a transparent
+    # zero. With one fully opaque white plane, every view pixel's opacity is
+    # the summed weight of its in-plane taps, computed here from the sample
+    # position of Eq. (u_prime) (pixels whose samples leave the plane at the
+    # outer views' edges get less than 1)
+    cam = S.identity_camera(24)
+    disp = S.display_for(3.0, 0.3)
+    r = orc.make_ref(cam, disp)
+    N = 1
+    d = np.array([2.2])          # off the focal plane: views shift against the plane
+    planes = np.ones((N, r.H, r.W, 4))
+    count = np.array([1], np.int64)
+    Vx = 5
+    v = orc.composite(r, planes, d, count, Vx, 1, True)
+    dx, dy = orc.view_offsets(r, Vx, 1)
+    partial = 0
+    for j in range(Vx):
+        for y in range(r.cam.Ny):
+            Y = orc.plane_pixel(r, 1, dy[0], d[0], y)
+            for x in range(r.cam.Nx):
+                X = orc.plane_pixel(r, 0, dx[j], d[0], x)
+                x0, y0 = math.floor(X), math.floor(Y)
+                wx, wy = X - x0, Y - y0
+                w_in = 0.0
+                for ty, wty in ((y0, 1 - wy), (y0 + 1, wy)):
+                    for tx, wtx in ((x0, 1 - wx), (x0 + 1, wx)):
+                        if 0 <= tx < r.W and 0 <= ty < r.H:
+                            w_in += wtx * wty
+                assert v[j, y, x, 3] == pytest.approx(w_in, abs=1e-12)
+                partial += w_in < 1 - 1e-9
+    assert partial > 10
+
+
 def test_background_and_empty(orc):
     cam = S.identity_camera(16)
     disp = S.display_for(3.0, 0.1)

@@ -306,6 +306,49 @@ def test_3dgs_blend_single_gaussian_alpha_cutoff(orc):
     assert kept > 20 and cut > 20
 
 
+def test_3dgs_near_mask_marks_both_threshold_events(orc):
+    # The near-threshold mask flags a texel whose trace passes within 1e-6 of
+    # a cut-off. Opacities are set from the closed form so that, at the
+    # centre pixel, (a) a lone flat Gaussian's alpha is 1/255 + 5e-7, and (b)
+    # two wide layers leave T (1 - alpha) = 1e-4 + 5e-7 (0.99, then the
+    # second layer's exact complement): both texels are flagged, and both
+    # are still blended (neither value crosses its cut-off).
+    cam = S.identity_camera(16, 50.0)
+    disp = S.display_for(3.0, 0.1, f_aa=0.0)
+    args = dict(camera=cam, display=disp, views=S.ViewSet(1), N=1, binning="quantile", with_views=False)
+    r = orc.make_ref(cam, disp)
+    yc, xc = r.H // 2, r.W // 2
+    o_, d_ = H.ref_pixel_ray(r, xc, yc)
+
+    def unit_alpha(mean, sig):
+        # exp(-q/2) of an axis-aligned flat Gaussian at the centre pixel's ray hit (no clamp)
+        m = np.asarray(mean, np.float64)
+        dd = H.hit_plane_z(o_, d_, m[2])[:2] - m[:2]
+        return math.exp(-0.5 * float(np.sum((dd / np.asarray(sig, np.float64)) ** 2)))
+
+    # (a) alpha event
+    mean, sig = (0.05, 0.02, 3.0), (0.3, 0.25)
+    o_a = (1.0 / 255.0 + 5e-7) / unit_alpha(mean, sig)
+    sc = H.flat_scene([(mean, sig, 0.0, o_a, (1, 1, 1))])
+    sc.opacity[0] = np.float32(o_a)
+    out = orc.render(scene=sc, blend="3dgs", **args)
+    a_pix = float(sc.opacity[0]) * unit_alpha(sc.means[0], sc.scales[0, :2])      # the stored FP32 inputs
+    assert abs(a_pix - 1.0 / 255.0) < 1e-6 and a_pix >= 1.0 / 255.0
+    assert out["near"][0, yc, xc] == 1
+    assert out["planes"][0, yc, xc, 3] == pytest.approx(a_pix, abs=1e-12)
+    # (b) transmittance event: the front layer is clamped to 0.99
+    m1, m2, big = (0.0, 0.0, 2.5), (0.0, 0.0, 3.0), (3.0, 3.0)
+    a2 = 1.0 - (1e-4 + 5e-7) / 0.01
+    o_b = a2 / unit_alpha(m2, big)
+    sc = H.flat_scene([(m1, big, 0.0, 0.9999, (1, 0, 0)), (m2, big, 0.0, o_b, (0, 1, 0))])
+    out = orc.render(scene=sc, blend="3dgs", **args)
+    a2_pix = float(sc.opacity[1]) * unit_alpha(sc.means[1], sc.scales[1, :2])
+    t_after = 0.01 * (1.0 - a2_pix)
+    assert abs(t_after - 1e-4) < 1e-6 and t_after >= 1e-4
+    assert out["near"][0, yc, xc] == 1
+    assert out["planes"][0, yc, xc, 3] == pytest.approx(1.0 - t_after, abs=1e-12)
+
+
 def _layer_scene(n_layers, seed):
     # wide flat fronto-parallel layers on the optical axis, front to back at
     # z = 2, 2.25, ...; opacity 0.8 except a faint last layer (0.3), which a

@@ -78,6 +78,15 @@ def test_view_offsets(orc):
     assert np.all(dy == 0.0)
     dx1, _ = orc.view_offsets(r, 1, 1)
     assert dx1[0] == 0.0
+    # a vertical row of views with its own viewing angle: the outermost
+    # vertical offsets equal the vertical baseline (tan(phi_y/2) = b_y / D_f)
+    b_y = 0.05
+    disp = S.display_for(2.6087, 0.15, phi_y=2.0 * math.atan(b_y / 2.6087))
+    r2 = orc.make_ref(S.identity_camera(128, 50.0), disp)
+    dx2, dy2 = orc.view_offsets(r2, 5, 3)
+    assert dy2[0] == pytest.approx(-b_y, rel=1e-13) and dy2[-1] == pytest.approx(b_y, rel=1e-13)
+    assert dy2[1] == 0.0
+    assert dx2[0] == pytest.approx(-0.15, rel=1e-13)
 
 
 def test_u_prime_matches_ray_geometry(orc):
