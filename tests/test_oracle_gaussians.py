@@ -200,6 +200,23 @@ def test_culling(orc):
     assert 0.0 < z[4] < disp.z_near < z[5]
 
 
+def test_degenerate_projection_is_culled(orc):
+    # without the dilation (f = 0) a Gaussian whose projected covariance is
+    # singular (all scales 0, or a flat Gaussian seen exactly edge-on) has
+    # det(Sigma_2) = 0 and is culled; the same Gaussians with f > 0 are kept
+    cam = S.identity_camera(32, 50.0)
+    sc = _rand_scene(3, 12)
+    sc.means[:] = [[0.0, 0.0, 3.0], [0.2, 0.1, 3.5], [-0.2, 0.0, 4.0]]
+    sc.scales[0] = 0.0
+    sc.scales[1] = [0.2, 0.0, 0.0]                    # a line segment: rank-1 covariance
+    sc.quats[:] = [1.0, 0.0, 0.0, 0.0]
+    sc.scales[2] = [0.1, 0.1, 0.05]                   # regular
+    for f_aa, want in ((0.0, [0, 0, 1]), (0.3, [1, 1, 1])):
+        r = orc.make_ref(cam, S.display_for(3.0, 0.1, f_aa=f_aa))
+        z, valid, rect = orc.gauss_decide(r, sc)
+        assert valid.tolist() == want, f_aa
+
+
 def test_depth_order_and_ties(orc):
     # Front-to-back within a chunk: the nearer opaque Gaussian dominates;
     # equal depths are ordered by index.
