@@ -90,7 +90,7 @@ def _build(verbose: bool) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [nvcc, ARCH, "-shared", "-o", tmp] + objs
+    cmd = [nvcc, ARCH, "-shared", "-o", tmp] + objs + ["-ldl"]   # NVTX loads a profiler's hooks with dlopen
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -13,6 +13,8 @@
 
 #include "lf_internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>   // header-only; ranges are no-ops unless a profiler is attached
+
 namespace lf {
 
 static thread_local std::string g_last_error;
@@ -42,8 +44,16 @@ static cudaEvent_t pool_event()
     return e;
 }
 
+// one NVTX range per stage on the calling thread (named like the stage), so
+// a timeline profiler shows the pipeline's steps; a range left open by an
+// early error return is closed by the next stage
+static thread_local int g_nvtx_open = 0;
+
 void trace_begin(const char* stage, cudaStream_t s)
 {
+    if (g_nvtx_open) nvtxRangePop();
+    nvtxRangePushA(stage);
+    g_nvtx_open = 1;
     if (!g_trace_on) return;
     TraceRec r{stage, pool_event(), pool_event()};
     cudaEventRecord(r.a, s);
@@ -53,6 +63,10 @@ void trace_begin(const char* stage, cudaStream_t s)
 
 void trace_end(cudaStream_t s)
 {
+    if (g_nvtx_open) {
+        nvtxRangePop();
+        g_nvtx_open = 0;
+    }
     if (!g_trace_on || g_trace_open < 0) return;
     cudaEventRecord(g_trace[g_trace_open].b, s);
     g_trace_open = -1;
