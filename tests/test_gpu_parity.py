@@ -125,6 +125,25 @@ def test_chunk_counts_and_few_primitives(orc, N):
     _compare(gpu, o, o["ref"].W, o["ref"].H, N, "f32")
 
 
+def test_non_finite_inputs_are_culled(orc):
+    # host-side fault injection: Gaussians with a NaN position, scale or
+    # rotation, or an infinite scale, are culled by the same comparisons as
+    # in the oracle (every comparison with NaN is false) before any of their
+    # values is used as an index; the rest of the scene renders as usual
+    w = S.workload_tiny(seed=3)
+    sc = w.scene.subset(np.arange(2000))
+    sc.means[0, 0] = np.nan
+    sc.means[1, 2] = np.nan
+    sc.scales[2, 1] = np.nan
+    sc.quats[3, :] = np.nan
+    sc.scales[4] = np.inf
+    o = orc.render(scene=sc, camera=w.camera, display=w.display, views=w.views, N=w.N, binning=w.binning)
+    assert o["valid"][:5].tolist() == [0] * 5
+    gpu = G.run_gpu(sc, w.camera, w.display, w.views, w.N, w.binning, "f32")
+    _compare(gpu, o, o["ref"].W, o["ref"].H, w.N, "f32")
+    assert np.isfinite(gpu["planes"]).all() and np.isfinite(gpu["views"]).all()
+
+
 def test_everything_culled(orc):
     w = S.workload_tiny()
     sc = S.uniform_gaussians(500, 3)

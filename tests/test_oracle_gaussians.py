@@ -217,6 +217,28 @@ def test_degenerate_projection_is_culled(orc):
         assert valid.tolist() == want, f_aa
 
 
+def test_non_finite_geometry_is_culled(orc):
+    # host-side fault injection: a Gaussian whose position, scale or
+    # rotation is NaN, or whose scale is infinite, fails the culling tests
+    # (every comparison with NaN is false) and never reaches a plane; the
+    # rest of the scene renders as without it
+    w = S.workload_tiny(seed=3)
+    sc = w.scene.subset(np.arange(500))
+    bad = sc.subset(np.arange(500))
+    bad.means[0, 0] = np.nan
+    bad.means[1, 2] = np.nan
+    bad.scales[2, 1] = np.nan
+    bad.quats[3, :] = np.nan
+    bad.scales[4] = np.inf
+    args = dict(camera=w.camera, display=w.display, views=w.views, N=w.N, binning=w.binning)
+    out = orc.render(scene=bad, **args)
+    assert out["valid"][:5].tolist() == [0] * 5
+    assert np.isfinite(out["planes"]).all() and np.isfinite(out["views"]).all()
+    ref = orc.render(scene=sc.subset(np.arange(5, 500)), **args)
+    assert out["M"] == ref["M"]
+    assert np.allclose(out["views"], ref["views"], atol=1e-12)
+
+
 def test_depth_order_and_ties(orc):
     # Front-to-back within a chunk: the nearer opaque Gaussian dominates;
     # equal depths are ordered by index.
