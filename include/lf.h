@@ -217,7 +217,8 @@ lf_status lf_build_mpi_gaussians(const lf_gaussians* g, const lf_ref_camera* ref
  * culled unless the whole cube lies past z_near; footprint = bounding box of
  * the 8 projected corners; alpha = 1 - exp(-integral of the trilinear
  * density over the pixel's reference-ray segment in the cube) (exact
- * Simpson rule). Arguments and errors as lf_build_mpi_gaussians. */
+ * Simpson rule). Arguments and errors as lf_build_mpi_gaussians, except that
+ * a binning carrying LF_BLEND_3DGS fails with LF_ERR_UNSUPPORTED. */
 lf_status lf_build_mpi_voxels(const lf_voxels* v, const lf_ref_camera* ref, int32_t N, int32_t binning,
                               void* ws, size_t ws_bytes, lf_planes* out, cudaStream_t stream);
 
