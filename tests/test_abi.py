@@ -114,3 +114,11 @@ def test_workspace_sizes(L):
     b = api.lf_build_mpi_workspace_size(ref, 1_000_000, 64, 20_000_000)
     assert 0 < a < b
     assert api.lf_composite_workspace_size(64, S.ViewSet(45)) > 0
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # there is no CPU fallback: without liblf.so the binding raises
+    from paper_2508_18540_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="liblf.so not found"):
+        _lib.load(str(tmp_path / "liblf.so"))
