@@ -366,7 +366,8 @@ typedef struct {
  *  views_per_thread  composite views per thread: 3, 5 or 9;
  *  tile_x            composite CTA tile width (columns): 128, 256 or 512
  *                    (the tile is tile_x x 512/tile_x pixels);
- *  raster_ppt        raster pixels per thread: 2 or 4;
+ *  raster_ppt        raster pixels per thread: 4 or 8 (warp strips of 8 x 16
+ *                    or 8 x 32 pixels);
  *  schedule          0: items in scene order; 1: largest scenes first;
  *                    2: no persistent launches -- every scene's own
  *                    lf_build_mpi_gaussians + lf_composite on a stream of its

@@ -140,6 +140,14 @@ size_t build_ws_layout(int64_t n, int32_t N, int32_t W, int32_t H, int64_t cap, 
     w.entB = carve<uint32_t>(base, off, cc);
     w.seg = carve<int2>(base, off, (size_t)S);
     w.g2d = carve<float>(base, off, 12 * nn);
+    // partial-result slots of split raster lists: enough that a frame of cap
+    // pairs needs no more than kRasterSegMin entries per part, up to a cap
+    long long slots = 2 * (long long)cc / kRasterSegMin + 2;
+    slots = slots < 16 ? 16 : slots > kRasterSlotsMax ? kRasterSlotsMax : slots;
+    w.r_nslots = slots;
+    w.r_items = carve<int4>(base, off, (size_t)slots);
+    w.r_arrive = carve<int>(base, off, (size_t)S);
+    w.r_part = carve<float4>(base, off, (size_t)slots * kSuper * kSuper);
     w.bytes = align_up(off, 256);
     w.nb_sort = nb;
     w.nb_dup = nbd;
@@ -242,6 +250,7 @@ static void fill_raster_params(const lf_ref_camera* r, int32_t N, int32_t dtype,
     p->tiles_x = (r->W + kTile - 1) / kTile;
     p->tiles_y = (r->H + kTile - 1) / kTile;
     p->supers_x = (r->W + kSuper - 1) / kSuper;
+    p->supers_y = (r->H + kSuper - 1) / kSuper;
     p->dtype = dtype;
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) p->Rt[3 * i + j] = (float)r->base.R[3 * j + i];

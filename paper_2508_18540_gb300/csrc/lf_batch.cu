@@ -19,7 +19,7 @@ using namespace lf;
 
 struct lf_batch {
     std::vector<lf_batch_scene> sc;
-    lf_batch_plan plan{9, 512, 2, 1};
+    lf_batch_plan plan{9, 512, 4, 1};
     int dtype = LF_F32;
     int bilinear = 0;
     bool prepared = false;
@@ -30,10 +30,10 @@ struct lf_batch {
     // host copies (kept alive: the uploads read them)
     std::vector<RasterScene> rhost;
     std::vector<CompScene> chost;
-    long long r_total = 0, c_total = 0;
+    long long r_heavy = 0, r_total = 0, c_total = 0;   // raster grid: split-part CTAs, all CTAs
     size_t max_stage = 0;
     int maxN = 0;
-    int r_ctas = 0, c_ctas = 0;
+    int c_ctas = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long graph_kernels = 0;              // kernels in one launch of the graph
@@ -97,9 +97,9 @@ size_t lf_batch_workspace_size(const lf_batch* b) { return b ? batch_ws_bytes((i
 lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, size_t ws_bytes, cudaStream_t stream)
 {
     if (!b) return fail(LF_ERR_INVALID_ARG, "batch is NULL");
-    const lf_batch_plan pl = plan ? *plan : lf_batch_plan{9, 512, 2, 1};
+    const lf_batch_plan pl = plan ? *plan : lf_batch_plan{9, 512, 4, 1};
     if ((pl.views_per_thread != 3 && pl.views_per_thread != 5 && pl.views_per_thread != 9) ||
-        (pl.tile_x != 128 && pl.tile_x != 256 && pl.tile_x != 512) || (pl.raster_ppt != 2 && pl.raster_ppt != 4) ||
+        (pl.tile_x != 128 && pl.tile_x != 256 && pl.tile_x != 512) || (pl.raster_ppt != 4 && pl.raster_ppt != 8) ||
         (pl.schedule < 0 || pl.schedule > 2))
         return fail(LF_ERR_INVALID_ARG, "lf_batch_prepare: plan out of range");
     if (pl.schedule == 2 && b->side.empty()) {
@@ -165,18 +165,23 @@ lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, siz
     }
     b->rhost.resize(n);
     b->chost.resize(n);
-    long long rt = 0, ct = 0;
+    long long ct = 0, hb = 0, lb = 0;
     for (int q = 0; q < n; ++q) {
         RasterScene R = r[ro[q]];
-        R.base = rt;
-        rt += (long long)R.p.tiles_x * R.p.tiles_y * R.p.N;
+        R.pbase = hb;
+        hb += raster_part_ctas(R.w);
         b->rhost[q] = R;
         CompScene C = c[co[q]];
         C.base = ct;
         ct += (long long)C.G.groups_x * C.p.Vy * C.nby * C.nbz;
         b->chost[q] = C;
     }
-    b->r_total = rt;
+    for (int q = 0; q < n; ++q) {
+        b->rhost[q].lbase = hb + lb;
+        lb += (long long)b->rhost[q].p.supers_x * b->rhost[q].p.supers_y * b->rhost[q].p.N;
+    }
+    b->r_heavy = hb;
+    b->r_total = hb + lb;
     b->c_total = ct;
     b->max_stage = max_stage;
     b->maxN = maxN;
@@ -184,7 +189,6 @@ lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, siz
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                   cudaSuccess)
         return check_launch("device query");
-    b->r_ctas = sms * raster_batched_ctas_per_sm(pl.raster_ppt);
     const size_t smem = composite_batched_smem(max_stage, maxN, pl.views_per_thread);
     b->c_ctas = sms * ((2 * (smem + 1024) <= 228 * 1024) ? 2 : 1);
     if (cudaMemcpyAsync(b->rtab, b->rhost.data(), sizeof(RasterScene) * n, cudaMemcpyHostToDevice, stream) !=
@@ -229,10 +233,12 @@ lf_status lf_batch_render(lf_batch* b, cudaStream_t stream)
         const uint32_t* ranks = nullptr;
         st = build_gaussians_prefix(&s.g, &s.ref, s.N, s.binning, s.ws, s.ws_bytes, &s.planes, stream, &w, &ranks);
         if (st != LF_OK) return st;
+        RasterParams rp;
+        raster_params(&s.ref, s.N, s.planes.dtype, &rp);
+        launch_raster_plan(w, rp, false, stream);
     }
     trace_begin("raster_batched", stream);
-    launch_raster_gauss_batched(b->rtab, (int)b->sc.size(), b->r_total, b->dtype, b->plan.raster_ppt, b->counters,
-                                b->r_ctas, stream);
+    launch_raster_gauss_batched(b->rtab, (int)b->sc.size(), b->dtype, b->r_heavy, b->r_total, stream);
     trace_end(stream);
     if ((st = check_launch("batched raster")) != LF_OK) return st;
     trace_begin("comp_coeffs", stream);
@@ -322,7 +328,7 @@ lf_status lf_batch_autotune(lf_batch* b, void* ws, size_t ws_bytes, int32_t reps
         *ms = t / reps;
         return LF_OK;
     };
-    lf_batch_plan cur{9, 512, 2, 1};
+    lf_batch_plan cur{9, 512, 4, 1};
     float cur_ms = 3.4e38f;
     lf_status st = LF_OK;
     const int vgs[3] = {3, 5, 9}, txs[3] = {128, 256, 512};
@@ -338,7 +344,7 @@ lf_status lf_batch_autotune(lf_batch* b, void* ws, size_t ws_bytes, int32_t reps
             if (st == LF_OK && ms < cur_ms) cur_ms = ms, cur = pl;
         }
     lf_batch_plan comp = cur;
-    for (int ppt = 2; ppt <= 4 && st == LF_OK; ppt += 2)
+    for (int ppt = 4; ppt <= 8 && st == LF_OK; ppt += 4)
         for (int sch = 0; sch <= 1 && st == LF_OK; ++sch) {
             lf_batch_plan pl{comp.views_per_thread, comp.tile_x, ppt, sch};
             if (pl.raster_ppt == comp.raster_ppt && pl.schedule == comp.schedule) continue;

@@ -39,7 +39,8 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
-inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args)
+inline void launch_pdl_attr(bool programmatic, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t s, Args&&... args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
@@ -50,12 +51,28 @@ inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
+    cfg.numAttrs = programmatic ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args)
+{
     // a CUDA graph already hides the launch gaps (measured: programmatic
     // edges only add a few microseconds per frame there), so a launch that is
     // being captured is an ordinary one
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cfg.numAttrs = (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, kern, static_cast<Args&&>(args)...);
+    const bool pdl = cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+    launch_pdl_attr(pdl, kern, grid, block, smem, s, static_cast<Args&&>(args)...);
+}
+
+// The same with a programmatic edge in a captured graph as well: for a
+// kernel that must run alongside its predecessor, not after it.
+template <typename... KArgs, typename... Args>
+inline void launch_overlapped(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args)
+{
+    launch_pdl_attr(true, kern, grid, block, smem, s, static_cast<Args&&>(args)...);
 }
 #endif
 
@@ -118,7 +135,18 @@ struct WsHeader {
     long long dup_capacity;
     int N, W, H, tiles_x, tiles_y, supers_x, supers_y;
     int binning;
+    // Gaussian raster (k_raster_plan): lists longer than r_seg entries are
+    // split into parts
+    unsigned int r_heavy;         // parts of split lists
+    int r_seg;                    // entries per part (0x7fffffff: no list is split)
 };
+
+// Split lists of the Gaussian raster: a list of L > r_seg entries is cut into
+// ceil(L / r_seg) parts, each with a partial (C, T) slot of one super-tile
+// (kSuper^2 texels); r_seg is at least kRasterSegMin and large enough that
+// the parts of a frame never need more than the workspace's slots.
+constexpr int kRasterSegMin = 1024;
+constexpr long long kRasterSlotsMax = 4096;
 
 // Carved build workspace (all device pointers).
 struct BuildWs {
@@ -146,6 +174,10 @@ struct BuildWs {
     uint32_t* entB;
     int2* seg;                    // [supers * N] (start, end) of every (super-tile, chunk) list
     float* g2d;                   // [n][12] per-rank gradient accumulators of the backward pass
+    int4* r_items;                // [slots] parts of split lists: {list, part, parts, slot}
+    float4* r_part;               // [slots][kSuper^2] partial (C, T) of every part
+    int* r_arrive;                // [lists] parts of a split list finished
+    long long r_nslots;           // partial-result slots
     size_t bytes;
     long long nb_sort, nb_dup;
 };
@@ -173,7 +205,7 @@ struct ProjParams {
 };
 
 struct RasterParams {
-    int W, H, N, tiles_x, tiles_y, supers_x, dtype;
+    int W, H, N, tiles_x, tiles_y, supers_x, supers_y, dtype;
     // voxels: world-frame reference rays
     float Rt[9];                    // R^T row-major (camera -> world)
     float fx, fy, cx, cy;
@@ -221,11 +253,19 @@ struct RasterScene {
     RasterParams p;
     const uint32_t* ranks;
     void* planes;
-    long long base;     // first global item of this scene (tiles * N items)
+    long long pbase;        // its first split-part CTA in the batch grid (raster_part_ctas of them)
+    long long lbase;        // its first list CTA in the batch grid
 };
-void launch_raster_gauss_batched(const RasterScene* scenes_dev, int n_sc, long long total, int dtype, int ppt,
-                                 unsigned long long* counter, int n_ctas, cudaStream_t s);
-int raster_batched_ctas_per_sm(int ppt);
+// CTAs a raster reserves for the parts of split lists
+long long raster_part_ctas(const BuildWs& ws);
+// the split parts of one Gaussian raster into ws.r_items; blend3dgs splits
+// no list
+void launch_raster_plan(const BuildWs& ws, const RasterParams& p, bool blend3dgs, cudaStream_t s);
+// raster of several scenes (their plans made) in one grid of total CTAs: the
+// split-part CTAs of every scene first (parts_total of them), then the list
+// CTAs
+void launch_raster_gauss_batched(const RasterScene* scenes_dev, int n_sc, int dtype, long long parts_total,
+                                 long long total, cudaStream_t s);
 
 // backward: raster adjoints accumulate into ws.g2d (zeroed by the caller),
 // then the per-rank chain rule / scatter writes the parameter gradients

@@ -81,79 +81,148 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// Gaussians: 256 / PPT threads; thread t shades the PPT pixels of column
-// t % 16 in rows PPT (t / 16) ... PPT (t / 16) + PPT - 1, so warp w owns the
-// 2 PPT x 16 strip of rows 2 PPT w ... Each batch of list entries is staged
-// as three 16-byte words {mean x, mean y, A, B}, {C, o, x0 | y0 << 16,
-// (x1 - x0) | (y1 - y0) << 16}, {r, g, b, -}, with the conic pre-scaled so
-// that alpha = min(0.99, o 2^(A dx^2 + B dx dy + C dy^2)),
-// A = -log2(e)/2 a, B = -log2(e) b, C = -log2(e)/2 c. Every warp ballots which
-// entries touch its strip and visits only those, in list order, so the
-// blending order of every pixel is unchanged.
-template <int PPT>
+// explicit shared-space accesses through 32-bit shared addresses
+__device__ __forceinline__ float4 lds4(uint32_t a)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ int2 lds2i(uint32_t a)
+{
+    int2 v;
+    asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ void sts4(uint32_t a, float4 v)
+{
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// Gaussians. A CTA rasterises one (32 x 32 super-tile, chunk) list, or one
+// part of a long one, with 8 warps. Warp w owns the 8-column x 16-row strip
+// at column group w % 4 and row group w / 4 of the super-tile; lane l shades
+// column l % 8 in rows l / 8 + 4 s, s = 0 .. 3, so the lanes' s-th pixels
+// form the 8 x 4 sub-block s of the strip, and a footprint that misses a
+// sub-block costs the warp nothing there (sub-blocks of 32 pixels fit the
+// footprint sizes better than wide strips). Each batch of list entries is
+// staged as three 16-byte words {mean x, mean y, A, B},
+// {C, log2 o, x0 | y0 << 16, (x1 - x0) | (y1 - y0) << 16}, {r, g, b, -},
+// with the conic pre-scaled so that
+//   alpha = min(0.99, 2^(A dx^2 + B dx dy + C dy^2 + log2 o)),
+// A = -log2(e)/2 a, B = -log2(e) b, C = -log2(e)/2 c. Per visited entry a lane
+// forms g1 = B dx and g0 = A dx^2 + log2 o for its column once; each of its
+// rows inside the footprint then costs the Horner form (C dy + g1) dy + g0,
+// one ex2 and the blend. Every warp ballots which entries touch its strip and
+// visits only those, in list order, so each pixel blends its members front
+// to back. Two staging buffers alternate: one CTA barrier per batch.
+//
+// Load balance. The work of a list grows with its length, and dense regions
+// of the scene make a few lists far longer than the rest. k_raster_plan cuts
+// every list longer than r_seg entries into parts of r_seg entries, and
+// k_raster_gauss_parts rasterises the parts: each blends its entries into a
+// partial (C, T) started from (0, 1) and stores it in its slot, and the CTA
+// that finishes a list's last part composes the partials in part order,
+// C += T C_q, T *= T_q (the "over" operator is associative), and writes the
+// texels. k_raster_gauss rasterises the other lists, one CTA each, and is
+// launched right behind the parts kernel with programmatic dependent launch,
+// so the long lists' parts start first and the short lists fill the machine
+// around them. The 3DGS cut-offs are not associative (the stop depends on
+// the running transmittance), so that mode splits no list.
+constexpr int kPlanThreads = 256;
+constexpr int kGaussNS = 4;                       // pixels per thread
+constexpr int kGaussThreads = 32 * 4 * (8 / kGaussNS);
+
 struct GaussSmem {
-    static constexpr int NT = kTilePix / PPT;
-    float4 e0[NT];
-    float4 e1[NT];
-    float4 rgb[NT];
-    int wc[NT / 32];
+    float4 e0[2][kGaussThreads];
+    float4 e1[2][kGaussThreads];
+    float4 rgb[2][kGaussThreads];
 };
 
-// One (tile t, chunk k) work item; every thread of the CTA calls it. G3
-// adds the two cut-offs of the 3DGS rasteriser: a member with alpha < 1/255
-// is skipped, and a pixel whose next blend would take T (1 - alpha) below
-// 1e-4 stops blending (bit r of `stopped`).
-template <int DT, int PPT, bool G3 = false>
-__device__ __forceinline__ void raster_gauss_tile(const BuildWs& w, const RasterParams& p,
-                                                  const uint32_t* __restrict__ ranks, void* planes, int t, int k,
-                                                  GaussSmem<PPT>& sm)
+// Split parts of one raster (one thread per (super-tile, chunk) list): a list
+// of L > r_seg entries takes P = ceil(L / r_seg) consecutive partial slots;
+// its parts become items [0, r_heavy) of the form {list, part, P, slot}.
+__global__ void __launch_bounds__(kPlanThreads) k_raster_plan(BuildWs w, int lists, int split)
 {
-    constexpr int NT = kTilePix / PPT;
+    pdl_wait();
+    pdl_trigger();
+    const long long total = (long long)w.hdr->tile_n;
+    int S = 0x7fffffff;
+    if (split) {
+        long long need = (2 * total + w.r_nslots - 1) / w.r_nslots;   // keeps the parts within the slots
+        need = (need + 255) / 256 * 256;
+        S = (int)(need > kRasterSegMin ? need : kRasterSegMin);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) w.hdr->r_seg = S;
+    for (int id = blockIdx.x * kPlanThreads + threadIdx.x; id < lists; id += gridDim.x * kPlanThreads) {
+        const int2 sg = w.seg[id];
+        const int L = sg.y - sg.x;
+        if (L <= S) continue;
+        const int P = (int)(((long long)L + S - 1) / S);
+        const unsigned int pos = atomicAdd(&w.hdr->r_heavy, (unsigned int)P);
+        w.r_arrive[id] = 0;
+        for (int q = 0; q < P; ++q)   // pos + P <= r_nslots, by the choice of S
+            w.r_items[pos + q] = make_int4(id, q, P, (int)(pos + q));
+    }
+}
+
+// List (st, k): the whole list (SPLIT false), or part `part` of P with
+// partial slot `slot`, S entries per part (SPLIT true). Every thread of the
+// CTA calls it. G3 adds the two cut-offs of the 3DGS rasteriser: a member
+// with alpha < 1/255 is skipped, and a pixel whose next blend would take
+// T (1 - alpha) below 1e-4 stops blending (bit s of `stopped`).
+template <int DT, bool G3, bool SPLIT>
+__device__ __forceinline__ void raster_gauss_list(const BuildWs& w, const RasterParams& p,
+                                                  const uint32_t* __restrict__ ranks, void* planes, int st, int k,
+                                                  GaussSmem& sm, int part, int P, int slot, int S, int* s_last)
+{
+    constexpr int NS = kGaussNS;
+    constexpr int NT = kGaussThreads;
     constexpr float kL2E = 1.4426950408889634f;
-    float4* s_e0 = sm.e0;
-    float4* s_e1 = sm.e1;
-    float4* s_rgb = sm.rgb;
-    int* s_wc = sm.wc;
-    const int tx = t % p.tiles_x, ty = t / p.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py0 = ty * kTile + (threadIdx.x / kTile) * PPT;
-    const int sx0 = tx * kTile, sx1 = sx0 + kTile - 1;                // warp strip bounds
-    const int sy0 = ty * kTile + 2 * PPT * warp, sy1 = sy0 + 2 * PPT - 1;
-    const int st = (ty / kTilesPerSuper) * p.supers_x + tx / kTilesPerSuper;
+    const int SX = (st % p.supers_x) * kSuper, SY = (st / p.supers_x) * kSuper;
+    const int sx0 = SX + 8 * (warp & 3), sx1 = sx0 + 7;                  // warp strip bounds
+    const int sy0 = SY + 4 * NS * (warp >> 2), sy1 = sy0 + 4 * NS - 1;
+    const int px = sx0 + (lane & 7);
+    const int py0 = sy0 + (lane >> 3);                                    // slot s: row py0 + 4 s
     const int2 sg = w.seg[(size_t)st * p.N + k];
-    const int L = sg.y - sg.x;
+    const int beg = SPLIT ? sg.x + part * S : sg.x;
+    const int L = SPLIT ? min(sg.y - beg, S) : sg.y - sg.x;
     const float fpx = (float)px;
-    float C[PPT][3], T[PPT];
+    float C[NS][3], T[NS];
     uint32_t stopped = 0u;
 #pragma unroll
-    for (int r = 0; r < PPT; ++r) C[r][0] = C[r][1] = C[r][2] = 0.f, T[r] = 1.f;
-    for (int base = 0; base < L; base += NT) {
+    for (int s = 0; s < NS; ++s) C[s][0] = C[s][1] = C[s][2] = 0.f, T[s] = 1.f;
+    int buf = 0;
+    for (int base = 0; base < L; base += NT, buf ^= 1) {
         const int i = base + threadIdx.x;
-        uint32_t rk = 0;
-        int4 r = make_int4(0, 0, -1, -1);
         if (i < L) {
-            rk = ranks[sg.x + i];
-            r = w.r_rect[rk];
-        }
-        const bool hit = i < L && meets_tile(r, sx0, ty * kTile);
-        int cnt;
-        const int slot = compact_slot<NT>(hit, s_wc, &cnt);
-        if (hit) {
+            const uint32_t rk = ranks[beg + i];
+            const int4 r = w.r_rect[rk];
             const float4 geo = w.r_geo[rk];
             const float4 c = w.r_con[rk];
-            s_e0[slot] = make_float4(geo.x, geo.y, -0.5f * kL2E * c.x, -kL2E * c.y);
-            s_e1[slot] = make_float4(-0.5f * kL2E * c.z, c.w, __int_as_float((r.x & 0xffff) | (r.y << 16)),
-                                     __int_as_float(((r.z - r.x) & 0xffff) | ((r.w - r.y) << 16)));
-            s_rgb[slot] = w.r_rgb[rk];
+            sm.e0[buf][threadIdx.x] = make_float4(geo.x, geo.y, -0.5f * kL2E * c.x, -kL2E * c.y);
+            sm.e1[buf][threadIdx.x] =
+                make_float4(-0.5f * kL2E * c.z, __log2f(c.w), __int_as_float((r.x & 0xffff) | (r.y << 16)),
+                            __int_as_float(((r.z - r.x) & 0xffff) | ((r.w - r.y) << 16)));
+            sm.rgb[buf][threadIdx.x] = w.r_rgb[rk];
         }
+        // orders this batch's staging before its walk, and every warp's walk
+        // of the batch before last before this staging overwrote its buffer
         __syncthreads();
+        const int cnt = min(NT, L - base);
+        const float4* s_e0 = sm.e0[buf];
+        const float4* s_e1 = sm.e1[buf];
+        const float4* s_rgb = sm.rgb[buf];
         for (int m0 = 0; m0 < cnt; m0 += 32) {
             const int jl = m0 + lane;
             bool hit = false;
             if (jl < cnt) {
-                const float4 e1 = s_e1[jl];
-                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
+                const float2 rc = *reinterpret_cast<const float2*>(&s_e1[jl].z);
+                const int xy = __float_as_int(rc.x), wh = __float_as_int(rc.y);
                 const int rx0 = xy & 0xffff, ry0 = xy >> 16;
                 hit = rx0 <= sx1 && rx0 + (wh & 0xffff) >= sx0 && ry0 <= sy1 && ry0 + (wh >> 16) >= sy0;
             }
@@ -161,83 +230,144 @@ __device__ __forceinline__ void raster_gauss_tile(const BuildWs& w, const Raster
             while (mask) {
                 const int j = m0 + __ffs(mask) - 1;
                 mask &= mask - 1;
-                const float4 e1 = s_e1[j];
-                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
-                if ((uint32_t)(px - (xy & 0xffff)) > (uint32_t)(wh & 0xffff)) continue;
                 const float4 e0 = s_e0[j];
+                const float4 e1 = s_e1[j];
                 const float4 col = s_rgb[j];
+                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
+                // rows of slot 0 below the footprint's top row; a column
+                // outside the footprint fails every row test
+                const int rt = (uint32_t)(px - (xy & 0xffff)) <= (uint32_t)(wh & 0xffff) ? py0 - (xy >> 16)
+                                                                                        : 0x40000000;
+                const uint32_t rh = (uint32_t)(wh >> 16);
                 const float dx = fpx - e0.x;
-                const float adx = e0.z * dx;
-                const int ry0 = xy >> 16, rh = wh >> 16;
+                const float g1 = e0.w * dx;
+                const float g0 = fmaf(e0.z * dx, dx, e1.y);
 #pragma unroll
-                for (int r = 0; r < PPT; ++r) {
-                    if ((uint32_t)(py0 + r - ry0) <= (uint32_t)rh) {
-                        const float dy = (float)(py0 + r) - e0.y;
-                        const float pw = fmaf(dx, fmaf(e0.w, dy, adx), e1.x * dy * dy);
-                        const float al = fminf(0.99f, e1.y * ex2_approx(pw));
-                        const float tn = fmaf(-T[r], al, T[r]);
+                for (int s = 0; s < NS; ++s) {
+                    if ((uint32_t)(rt + 4 * s) <= rh) {
+                        const float dy = (float)(py0 + 4 * s) - e0.y;
+                        const float pw = fmaf(fmaf(e1.x, dy, g1), dy, g0);
+                        const float al = fminf(0.99f, ex2_approx(pw));
+                        const float tn = fmaf(-T[s], al, T[s]);
                         if (G3) {
-                            if ((stopped >> r) & 1u) continue;
+                            if ((stopped >> s) & 1u) continue;
                             if (al < 1.0f / 255.0f) continue;
                             if (tn < 1e-4f) {
-                                stopped |= 1u << r;
+                                stopped |= 1u << s;
                                 continue;
                             }
                         }
-                        const float ta = T[r] * al;
-                        C[r][0] = fmaf(ta, col.x, C[r][0]);
-                        C[r][1] = fmaf(ta, col.y, C[r][1]);
-                        C[r][2] = fmaf(ta, col.z, C[r][2]);
-                        T[r] = tn;
+                        const float ta = T[s] * al;
+                        C[s][0] = fmaf(ta, col.x, C[s][0]);
+                        C[s][1] = fmaf(ta, col.y, C[s][1]);
+                        C[s][2] = fmaf(ta, col.z, C[s][2]);
+                        T[s] = tn;
                     }
                 }
             }
         }
-        // no barrier here: the next batch's compaction barrier already
-        // waits for every warp to finish walking this batch before any
-        // staged entry is overwritten, and the staging barrier above orders
-        // the reads of s_wc before its next write
+    }
+    if (SPLIT) {
+        // publish the partial; the last part of the list to finish composes
+        // all of them, this one included, read back through L2 in order
+        const int slot0 = slot - part;
+        float4* mine = w.r_part + (size_t)slot * (kSuper * kSuper);
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+            __stcg(mine + (warp * NS + s) * 32 + lane, make_float4(C[s][0], C[s][1], C[s][2], T[s]));
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) *s_last = atomicAdd(&w.r_arrive[st * p.N + k], 1) == P - 1;
+        __syncthreads();
+        if (!*s_last) return;
+        __threadfence();
+#pragma unroll
+        for (int s = 0; s < NS; ++s) C[s][0] = C[s][1] = C[s][2] = 0.f, T[s] = 1.f;
+        for (int q = 0; q < P; ++q) {
+            const float4* src = w.r_part + (size_t)(slot0 + q) * (kSuper * kSuper);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const float4 v = __ldcg(src + (warp * NS + s) * 32 + lane);
+                C[s][0] = fmaf(T[s], v.x, C[s][0]);
+                C[s][1] = fmaf(T[s], v.y, C[s][1]);
+                C[s][2] = fmaf(T[s], v.z, C[s][2]);
+                T[s] *= v.w;
+            }
+        }
     }
     if (px < p.W) {
 #pragma unroll
-        for (int r = 0; r < PPT; ++r)
-            if (py0 + r < p.H)
-                store_texel<DT>(planes, ((size_t)k * p.H + py0 + r) * p.W + px, C[r][0], C[r][1], C[r][2],
-                                1.0f - T[r]);
+        for (int s = 0; s < NS; ++s)
+            if (py0 + 4 * s < p.H)
+                store_texel<DT>(planes, ((size_t)k * p.H + py0 + 4 * s) * p.W + px, C[s][0], C[s][1], C[s][2],
+                                1.0f - T[s]);
     }
 }
 
-template <int DT, int PPT, bool G3>
-__global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss(BuildWs w, RasterParams p,
-                                                                 const uint32_t* __restrict__ ranks, void* planes)
+// Lists no longer than r_seg entries: one CTA per (super-tile x, chunk y).
+// Launched behind the parts kernel, it does not wait for it to start;
+// CTA (0, 0) waits for it to finish before exiting, so this grid completes
+// after every part's texels are written and work ordered after it sees them.
+template <int DT, bool G3>
+__global__ void __launch_bounds__(kGaussThreads) k_raster_gauss(BuildWs w, RasterParams p,
+                                                               const uint32_t* __restrict__ ranks, void* planes)
 {
-    __shared__ GaussSmem<PPT> sm;
-    raster_gauss_tile<DT, PPT, G3>(w, p, ranks, planes, blockIdx.x, blockIdx.y, sm);
+    __shared__ GaussSmem sm;
+    const int st = blockIdx.x, k = blockIdx.y;
+    const int2 sg = w.seg[(size_t)st * p.N + k];
+    if (sg.y - sg.x <= w.hdr->r_seg)   // longer lists: k_raster_gauss_parts
+        raster_gauss_list<DT, G3, false>(w, p, ranks, planes, st, k, sm, 0, 1, -1, 0, nullptr);
+    if (st == 0 && k == 0) pdl_wait();
 }
 
-// Persistent form over the (tile, chunk) items of several scenes: CTAs take
-// items from a global counter in the order of the item table (scenes
-// concatenated in the order the schedule chose, tiles fastest within a
-// chunk) until it is exhausted.
-template <int DT, int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss_batched(const RasterScene* __restrict__ sc, int n_sc,
-                                                                         long long total,
-                                                                         unsigned long long* __restrict__ counter)
+// The parts of the split lists: CTA b takes item b (CTAs past r_heavy exit).
+// It lets the list kernel launch at once: that kernel reads nothing the
+// parts write.
+template <int DT>
+__global__ void __launch_bounds__(kGaussThreads) k_raster_gauss_parts(BuildWs w, RasterParams p,
+                                                                     const uint32_t* __restrict__ ranks, void* planes)
 {
-    __shared__ GaussSmem<PPT> sm;
-    __shared__ long long s_item;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
-        __syncthreads();
-        const long long it = s_item;
-        __syncthreads();
-        if (it >= total) return;
-        int s = 0;
-        while (s + 1 < n_sc && it >= sc[s + 1].base) ++s;
-        const RasterScene& S = sc[s];
-        const long long li = it - S.base;
-        const int tiles = S.p.tiles_x * S.p.tiles_y;
-        raster_gauss_tile<DT, PPT>(S.w, S.p, S.ranks, S.planes, (int)(li % tiles), (int)(li / tiles), sm);
+    __shared__ GaussSmem sm;
+    __shared__ int s_last;
+    pdl_wait();
+    pdl_trigger();
+    if (blockIdx.x >= w.hdr->r_heavy) return;
+    const int4 it = w.r_items[blockIdx.x];
+    const int st = it.x / p.N;
+    raster_gauss_list<DT, false, true>(w, p, ranks, planes, st, it.x - st * p.N, sm, it.y, it.z, it.w,
+                                       w.hdr->r_seg, &s_last);
+}
+
+// Several scenes in one grid: CTA b < parts_total takes a split part (scene s
+// from pbase), the others a list (scene s from lbase), in scene-table order.
+template <int DT>
+__global__ void __launch_bounds__(kGaussThreads) k_raster_gauss_batched(const RasterScene* __restrict__ sc, int n_sc,
+                                                                       long long parts_total)
+{
+    __shared__ GaussSmem sm;
+    __shared__ int s_last;
+    const long long b = blockIdx.x;
+    const bool part = b < parts_total;
+    int lo = 0, hi = n_sc - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((part ? sc[mid].pbase : sc[mid].lbase) <= b) lo = mid; else hi = mid - 1;
+    }
+    const RasterScene& S = sc[lo];
+    if (part) {
+        const long long q = b - S.pbase;
+        if (q >= (long long)S.w.hdr->r_heavy) return;
+        const int4 it = S.w.r_items[q];
+        const int st = it.x / S.p.N;
+        raster_gauss_list<DT, false, true>(S.w, S.p, S.ranks, S.planes, st, it.x - st * S.p.N, sm, it.y, it.z, it.w,
+                                           S.w.hdr->r_seg, &s_last);
+    } else {
+        const int supers = S.p.supers_x * S.p.supers_y;
+        const int li = (int)(b - S.lbase);
+        const int k = li / supers, st = li - k * supers;
+        const int2 sg = S.w.seg[(size_t)st * S.p.N + k];
+        if (sg.y - sg.x > S.w.hdr->r_seg) return;
+        raster_gauss_list<DT, false, false>(S.w, S.p, S.ranks, S.planes, st, k, sm, 0, 1, -1, 0, nullptr);
     }
 }
 
@@ -928,56 +1058,61 @@ void launch_raster_voxels_bwd(const BuildWs& ws, const RasterParams& p, const ui
     note_launches(1);
 }
 
-template <bool G3>
-static void launch_raster_gaussians_mode(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks,
-                                         void* planes, cudaStream_t s)
+long long raster_part_ctas(const BuildWs& ws) { return ws.r_nslots; }
+
+void launch_raster_plan(const BuildWs& ws, const RasterParams& p, bool blend3dgs, cudaStream_t s)
 {
-    const dim3 grid((unsigned)(p.tiles_x * p.tiles_y), (unsigned)p.N);
-    constexpr int kPPT = 2;   // pixels per thread
-    constexpr int kThreads = kTilePix / kPPT;
-    switch (p.dtype) {
-    case LF_F32: k_raster_gauss<LF_F32, kPPT, G3><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
-    case LF_F16: k_raster_gauss<LF_F16, kPPT, G3><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
-    case LF_U8: k_raster_gauss<LF_U8, kPPT, G3><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
-    default: k_raster_gauss<LF_BF16, kPPT, G3><<<grid, kThreads, 0, s>>>(ws, p, ranks, planes); break;
+    const int lists = p.supers_x * p.supers_y * p.N;
+    int blocks = (lists + kPlanThreads - 1) / kPlanThreads;
+    blocks = blocks < 1 ? 1 : blocks > 1024 ? 1024 : blocks;
+    launch_pdl(k_raster_plan, dim3(blocks), dim3(kPlanThreads), 0, s, ws, lists, blend3dgs ? 0 : 1);
+    note_launches(1);
+}
+
+template <int DT, bool G3>
+static void launch_raster_gauss_dt(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
+                                   cudaStream_t s)
+{
+    const dim3 grid((unsigned)(p.supers_x * p.supers_y), (unsigned)p.N);
+    if (!G3) {
+        launch_overlapped(k_raster_gauss_parts<DT>, dim3((unsigned)raster_part_ctas(ws)), dim3(kGaussThreads), 0, s,
+                          ws, p, ranks, planes);
+        launch_overlapped(k_raster_gauss<DT, G3>, grid, dim3(kGaussThreads), 0, s, ws, p, ranks, planes);
+        note_launches(2);
+    } else {
+        launch_pdl(k_raster_gauss<DT, G3>, grid, dim3(kGaussThreads), 0, s, ws, p, ranks, planes);
+        note_launches(1);
     }
 }
 
 void launch_raster_gaussians(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,
                              bool blend3dgs, cudaStream_t s)
 {
-    if (blend3dgs)
-        launch_raster_gaussians_mode<true>(ws, p, ranks, planes, s);
-    else
-        launch_raster_gaussians_mode<false>(ws, p, ranks, planes, s);
-    note_launches(1);
-}
-
-void launch_raster_gauss_batched(const RasterScene* scenes_dev, int n_sc, long long total, int dtype, int ppt,
-                                 unsigned long long* counter, int n_ctas, cudaStream_t s)
-{
-    if (total <= 0) return;
-#define LF_RB(DT_, PPT_)                                                                                  \
-    k_raster_gauss_batched<DT_, PPT_><<<n_ctas, kTilePix / PPT_, 0, s>>>(scenes_dev, n_sc, total, counter)
-    if (ppt == 4) {
-        if (dtype == LF_F32) LF_RB(LF_F32, 4); else if (dtype == LF_F16) LF_RB(LF_F16, 4);
-        else if (dtype == LF_U8) LF_RB(LF_U8, 4); else LF_RB(LF_BF16, 4);
-    } else {
-        if (dtype == LF_F32) LF_RB(LF_F32, 2); else if (dtype == LF_F16) LF_RB(LF_F16, 2);
-        else if (dtype == LF_U8) LF_RB(LF_U8, 2); else LF_RB(LF_BF16, 2);
+    launch_raster_plan(ws, p, blend3dgs, s);
+    switch (p.dtype) {
+    case LF_F32: blend3dgs ? launch_raster_gauss_dt<LF_F32, true>(ws, p, ranks, planes, s)
+                           : launch_raster_gauss_dt<LF_F32, false>(ws, p, ranks, planes, s); break;
+    case LF_F16: blend3dgs ? launch_raster_gauss_dt<LF_F16, true>(ws, p, ranks, planes, s)
+                           : launch_raster_gauss_dt<LF_F16, false>(ws, p, ranks, planes, s); break;
+    case LF_U8: blend3dgs ? launch_raster_gauss_dt<LF_U8, true>(ws, p, ranks, planes, s)
+                          : launch_raster_gauss_dt<LF_U8, false>(ws, p, ranks, planes, s); break;
+    default: blend3dgs ? launch_raster_gauss_dt<LF_BF16, true>(ws, p, ranks, planes, s)
+                       : launch_raster_gauss_dt<LF_BF16, false>(ws, p, ranks, planes, s); break;
     }
-#undef LF_RB
-    note_launches(1);
 }
 
-int raster_batched_ctas_per_sm(int ppt)
+void launch_raster_gauss_batched(const RasterScene* scenes_dev, int n_sc, int dtype, long long parts_total,
+                                 long long total, cudaStream_t s)
 {
-    int n = 0;
-    if (ppt == 4)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_gauss_batched<LF_F16, 4>, kTilePix / 4, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_gauss_batched<LF_F16, 2>, kTilePix / 2, 0);
-    return n > 0 ? n : 1;
+    if (n_sc <= 0 || total <= 0) return;
+    const unsigned g = (unsigned)total;
+    switch (dtype) {
+    case LF_F32: k_raster_gauss_batched<LF_F32><<<g, kGaussThreads, 0, s>>>(scenes_dev, n_sc, parts_total); break;
+    case LF_F16: k_raster_gauss_batched<LF_F16><<<g, kGaussThreads, 0, s>>>(scenes_dev, n_sc, parts_total); break;
+    case LF_U8: k_raster_gauss_batched<LF_U8><<<g, kGaussThreads, 0, s>>>(scenes_dev, n_sc, parts_total); break;
+    default: k_raster_gauss_batched<LF_BF16><<<g, kGaussThreads, 0, s>>>(scenes_dev, n_sc, parts_total); break;
+    }
+    note_launches(1);
 }
 
 void launch_raster_voxels(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, void* planes,

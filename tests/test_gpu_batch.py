@@ -64,7 +64,7 @@ def test_every_plan_gives_the_same_result():
     ref = [o.clone() for o in b.outputs]
     for vg in (3, 5, 9):
         for tx in (128, 256, 512):
-            for ppt, sch in ((2, 0), (4, 1), (2, 2)):
+            for ppt, sch in ((4, 0), (8, 1), (4, 2)):
                 b.prepare({"views_per_thread": vg, "tile_x": tx, "raster_ppt": ppt, "schedule": sch})
                 for o in b.outputs:
                     o.fill_(float("nan"))
@@ -79,7 +79,7 @@ def test_every_plan_gives_the_same_result():
 def test_graph_capture_replays_and_sees_new_inputs(schedule):
     wls = _scenes()
     b = api.BatchRenderer(wls, "f16")
-    b.prepare({"views_per_thread": 9, "tile_x": 512, "raster_ppt": 2, "schedule": schedule})
+    b.prepare({"views_per_thread": 9, "tile_x": 512, "raster_ppt": 4, "schedule": schedule})
     b.capture()
     for _ in range(2):
         for o in b.outputs:
@@ -109,7 +109,7 @@ def test_autotune_picks_a_valid_plan():
     b = api.BatchRenderer(wls, "f16")
     plan, ms = b.autotune(reps=1)
     assert plan["views_per_thread"] in (3, 5, 9) and plan["tile_x"] in (128, 256, 512)
-    assert plan["raster_ppt"] in (2, 4) and plan["schedule"] in (0, 1, 2)
+    assert plan["raster_ppt"] in (4, 8) and plan["schedule"] in (0, 1, 2)
     assert ms > 0
     b.render()
     _check_equal(b, wls, "f16")
