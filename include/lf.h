@@ -273,21 +273,36 @@ lf_status lf_composite(const lf_planes* planes, const lf_ref_camera* ref, const 
 lf_status lf_composite_status(int32_t N, const lf_view_set* views, const void* cws, cudaStream_t stream);
 
 /* Allocation-free form of lf_composite (the paper has no counterpart): the
- * same computation and result, with its scratch in a static device array of
+ * same kernels and the same result, with the composite scratch (coefficient
+ * tables and the error word) in a static device array of
  * lf_composite_noalloc_max_bytes() bytes (1 MiB) inside the library instead
- * of a caller workspace, for callers that cannot provide device memory (for
- * example a display runtime's per-frame present callback that must not call
- * a device allocator). The scratch address is looked up once per device with
- * that device current (the first call on a device does it). Requests whose
- * scratch (lf_composite_workspace_size) exceeds the limit fail with
- * LF_ERR_WORKSPACE and a message. Calls that overlap in time share the one
- * scratch array and race: the caller must serialise them. Other arguments
- * and errors as lf_composite. */
+ * of a caller workspace. It is for callers that cannot hand the library device
+ * memory, for example a display runtime's per-frame present callback, which
+ * runs where calling a device allocator is not allowed (it may synchronise
+ * the device or stall the frame). Every GPU that loads the library holds the
+ * array until the process exits. Each call looks up the array's device
+ * address on the calling thread's current device (cudaGetSymbolAddress, no
+ * allocation); the first call on a device may load the library's device code
+ * there, so make it before any stream capture. Requests whose scratch
+ * (lf_composite_workspace_size) exceeds the limit fail with LF_ERR_WORKSPACE
+ * and a message, before any device work. Every call shares the one array and
+ * it keeps the last call's contents (the error word is cleared by each
+ * call): calls that overlap on the GPU race, so the caller must serialise
+ * them. A bounded device wait that gives up is reported by
+ * lf_composite_noalloc_status, not by this call. Other arguments and
+ * argument errors as lf_composite. */
 lf_status lf_composite_noalloc(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
                                float* out, cudaStream_t stream);
 
 /* Size in bytes of lf_composite_noalloc's static scratch. */
 size_t lf_composite_noalloc_max_bytes(void);
+
+/* Status of the last lf_composite_noalloc for N planes and views, read from
+ * the static scratch after synchronising stream (the paper has no
+ * counterpart): LF_ERR_TIMEOUT if one of its bounded device waits gave up
+ * (its views are then not valid), else LF_OK. LF_ERR_INVALID_ARG for a
+ * request lf_composite_noalloc would refuse. */
+lf_status lf_composite_noalloc_status(int32_t N, const lf_view_set* views, cudaStream_t stream);
 
 /* ---- differentiation ------------------------------------------------------ */
 /*

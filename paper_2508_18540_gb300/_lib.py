@@ -103,6 +103,7 @@ SIGNATURES = [
     ("lf_composite_noalloc", ctypes.c_int, [ctypes.POINTER(LfPlanes), ctypes.POINTER(LfRefCamera),
                                             ctypes.POINTER(LfViewSet), _P, _P]),
     ("lf_composite_noalloc_max_bytes", ctypes.c_size_t, []),
+    ("lf_composite_noalloc_status", ctypes.c_int, [_I32, ctypes.POINTER(LfViewSet), _P]),
     ("lf_composite_backward", ctypes.c_int, [ctypes.POINTER(LfPlanes), ctypes.POINTER(LfRefCamera),
                                              ctypes.POINTER(LfViewSet), _P, _P, _P, ctypes.c_size_t, _P]),
     ("lf_build_mpi_backward_gaussians", ctypes.c_int, [ctypes.POINTER(LfGaussians), ctypes.POINTER(LfRefCamera),

@@ -274,6 +274,13 @@ def lf_composite_noalloc_max_bytes() -> int:
     return int(load().lf_composite_noalloc_max_bytes())
 
 
+def lf_composite_noalloc_status(N: int, views, stream=None) -> int:
+    """Status of the last lf_composite_noalloc for N planes and these views:
+    LF_ERR_TIMEOUT if a bounded device wait gave up, else LF_OK."""
+    vs = view_set(views)
+    return int(load().lf_composite_noalloc_status(int(N), ctypes.byref(vs), _stream_ptr(stream)))
+
+
 # ---------------------------------------------------------------------------
 # differentiation
 # ---------------------------------------------------------------------------

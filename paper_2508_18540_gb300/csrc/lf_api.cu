@@ -863,29 +863,19 @@ namespace lf {
 constexpr size_t kStaticCompBytes = 1u << 20;   // 1 MiB: e.g. N = 512 planes x 128 views
 static __device__ __align__(256) unsigned char g_comp_scratch[kStaticCompBytes];
 
-// device address of g_comp_scratch per device, looked up once per device
-// with that device current
-static std::mutex g_scratch_mu;
-static std::map<int, void*> g_scratch_addr;
-
+// Device address of g_comp_scratch on the calling thread's current device.
+// In host code the array's name is only a host-side stand-in, so every call
+// asks the runtime for the address (no allocation, and no address cached
+// across a device reset that could move the module).
 static lf_status static_scratch(void** out)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return check_launch("cudaGetDevice");
-    std::lock_guard<std::mutex> lk(g_scratch_mu);
-    auto it = g_scratch_addr.find(dev);
-    if (it != g_scratch_addr.end()) {
-        *out = it->second;
-        return LF_OK;
-    }
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_comp_scratch);
-    if (e != cudaSuccess) {
+    if (e != cudaSuccess || !p) {
         cudaGetLastError();
         return fail(LF_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") +
                                      cudaGetErrorString(e));
     }
-    g_scratch_addr[dev] = p;
     *out = p;
     return LF_OK;
 }
@@ -917,10 +907,25 @@ lf_status lf_composite_noalloc(const lf_planes* planes, const lf_ref_camera* ref
     fill_comp_params(planes, ref, views, &p);
     if (cudaMemsetAsync(cw.err, 0, sizeof(int) * (1 + (size_t)planes->N), stream) != cudaSuccess)
         return check_launch("composite reset");
+    trace_begin("comp_coeffs", stream);
     launch_comp_coeffs(p, planes->d, planes->count, cw, stream);
+    trace_end(stream);
     if ((st = check_launch("composite coefficients")) != LF_OK) return st;
+    trace_begin("composite", stream);
     launch_composite(p, planes->rgba, planes->count, cw, out, stream);
+    trace_end(stream);
     return check_launch("composite");
+}
+
+lf_status lf_composite_noalloc_status(int32_t N, const lf_view_set* views, cudaStream_t stream)
+{
+    if (!views || N < 1 || views->Vx < 1 || views->Vy < 1) return fail(LF_ERR_INVALID_ARG, "bad argument");
+    if (comp_ws_layout(N, views->Vx, views->Vy, nullptr, nullptr) > lf::kStaticCompBytes)
+        return fail(LF_ERR_INVALID_ARG, "N and views exceed what lf_composite_noalloc accepts");
+    void* scratch = nullptr;
+    const lf_status st = lf::static_scratch(&scratch);
+    if (st != LF_OK) return st;
+    return lf_composite_status(N, views, scratch, stream);
 }
 
 }  // extern "C"

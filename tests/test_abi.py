@@ -103,6 +103,8 @@ def test_invalid_arguments_are_rejected(L):
     vs = L.LfViewSet(5, 1, 0)
     assert lib.lf_composite_status(0, ctypes.byref(vs), ctypes.c_void_p(256), None) == L.LF_ERR_INVALID_ARG
     assert lib.lf_composite_status(4, ctypes.byref(vs), None, None) == L.LF_ERR_INVALID_ARG
+    assert lib.lf_composite_noalloc_status(0, ctypes.byref(vs), None) == L.LF_ERR_INVALID_ARG
+    assert lib.lf_composite_noalloc_status(1 << 20, ctypes.byref(vs), None) == L.LF_ERR_INVALID_ARG
     assert lib.lf_selftest_bounded_wait(0, None) == L.LF_ERR_INVALID_ARG
     assert lib.lf_selftest_bounded_wait(20000, None) == L.LF_ERR_INVALID_ARG
 
