@@ -29,6 +29,19 @@ WORKLOAD = dict(n=1_000_000, res=512, N=64, V=45, seed=2)
 METRIC = "LF frames/s (45 views, 512p, 1M Gaussians) FP16 vs FP32 planes; % HBM roofline"
 UNIT = "LF frames/s"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
+FIT_TARGET_SEED = 6                 # perturbation of the fit's target scene
+
+
+_VOXEL_WL = []
+
+
+def _voxel_workload():
+    """The 2M-voxel V2LF workload, generated once per process (both the GPU
+    section and the oracle baseline use it)."""
+    from paper_2508_18540_gb300 import synth as S
+    if not _VOXEL_WL:
+        _VOXEL_WL.append(S.workload_voxels())
+    return _VOXEL_WL[0]
 
 
 def _env_rank():
@@ -349,7 +362,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         line["v2lf"] = run_v2lf(args, dev)
         torch.cuda.empty_cache()
-        line["differentiable"] = run_differentiable(args, dev)
+        line["differentiable"] = run_differentiable(args, dev, getattr(args, "fit_target", None))
         torch.cuda.empty_cache()
         line["batched"] = run_batched(args, dev)
         torch.cuda.empty_cache()
@@ -387,7 +400,7 @@ def run_v2lf(args, dev):
     import torch
     from paper_2508_18540_gb300 import api
     from paper_2508_18540_gb300 import synth as S
-    wl = S.workload_voxels()
+    wl = _voxel_workload()
     v = api.DeviceVoxels.from_scene(wl.scene, device=dev)
     r = api.LightFieldRenderer(wl.camera, wl.display, wl.views, wl.N, wl.binning, "f32", device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -419,12 +432,16 @@ def run_v2lf(args, dev):
                                   "ms_per_step": round(ms_f, 4), "plane_filter_ms": f_ms}}
 
 
-def run_differentiable(args, dev):
+def run_differentiable(args, dev, fit_target=None):
     """Differentiable G2LF: 300k Gaussians, 512^2, N 64, 45 views: forward
     (build + composite) and backward (composite adjoint, splat adjoint,
-    projection chain rule) per step, FP32."""
+    projection chain rule) per step, FP32; then a fit of all five parameter
+    groups (means, scales, quaternions, opacities, colours) by Adam against
+    target views of a perturbed copy of the scene (means + N(0, 0.01),
+    opacities + N(0, 0.05)) rendered by the FP64 oracle, with its loss curve."""
     import torch
     from paper_2508_18540_gb300 import api
+    from paper_2508_18540_gb300 import autograd as AG
     from paper_2508_18540_gb300 import synth as S
     wl = S.workload_fit()
     g = api.DeviceGaussians.from_scene(wl.scene, device=dev)
@@ -441,9 +458,57 @@ def run_differentiable(args, dev):
     torch.cuda.synchronize()
     api.lf_trace_enable(False)
     stages = {k: round(t / c, 4) for k, (t, c) in api.lf_trace_collect().items()}
-    return {"workload": wl.name, "gaussians": wl.scene.n, "forward_ms": round(fwd, 4), "backward_ms": round(bwd, 4),
-            "steps_per_s": round(1000.0 / (fwd + bwd), 2), "stages_ms": stages,
-            "gradient_check": "tests/test_gpu_grad.py (finite differences of the FP64 oracle)"}
+    out = {"workload": wl.name, "gaussians": wl.scene.n, "forward_ms": round(fwd, 4), "backward_ms": round(bwd, 4),
+           "steps_per_s": round(1000.0 / (fwd + bwd), 2), "stages_ms": stages,
+           "gradient_check": "tests/test_gpu_grad.py (finite differences of the FP64 oracle)"}
+    # the fit: target views from the oracle (the CPU-baseline leg renders
+    # them) or, without that leg, from this renderer on the perturbed scene
+    if fit_target is None:
+        tgt = api.LightFieldRenderer(wl.camera, wl.display, wl.views, wl.N, wl.binning, "f32", device=dev)
+        target = tgt.render(api.DeviceGaussians.from_scene(S.perturbed(wl.scene, FIT_TARGET_SEED), device=dev)).clone()
+        source = "GPU render of the perturbed scene (oracle leg not run)"
+        del tgt
+    else:
+        target = torch.as_tensor(fit_target, dtype=torch.float32).to(dev)
+        source = "FP64 oracle render of the perturbed scene"
+    params = [t.clone().requires_grad_(True) for t in (g.means, g.scales, g.quats, g.opacity, g.rgb)]
+    lrs = [1e-3, 1e-4, 1e-3, 1e-2, 1e-2]
+    opt = torch.optim.Adam([{"params": [p], "lr": lr} for p, lr in zip(params, lrs)])
+    n_steps = 40
+    losses = []
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(n_steps):
+        opt.zero_grad(set_to_none=True)
+        v = AG.render_gaussians(r, *params)
+        loss = ((v - target) ** 2).sum()
+        loss.backward()
+        opt.step()
+        with torch.no_grad():
+            params[1].clamp_(min=1e-6)
+            params[3].clamp_(0.01, 0.99)
+        losses.append(loss.detach())
+    e1.record(st)
+    e1.synchronize()
+    fit_ms = e0.elapsed_time(e1) / n_steps
+    curve = [float(x) for x in torch.stack(losses).cpu()]
+    out["fit"] = {"target": source, "parameters": ["means", "scales", "quats", "opacity", "rgb"],
+                  "optimizer": "Adam (torch), lr %s" % lrs, "loss": "sum of squared view differences",
+                  "steps": n_steps, "ms_per_step": round(fit_ms, 3), "steps_per_s": round(1000.0 / fit_ms, 2),
+                  "loss_first": curve[0], "loss_last": curve[-1], "loss_curve": [round(x, 3) for x in curve]}
+    return out
+
+
+def oracle_fit_target():
+    """Target views of the differentiable fit: the FP64 oracle's render of the
+    perturbed copy of the 300k-Gaussian scene (part of the oracle leg)."""
+    import oracle
+    from paper_2508_18540_gb300 import synth as S
+    wl = S.workload_fit()
+    o = oracle.render(scene=S.perturbed(wl.scene, FIT_TARGET_SEED), camera=wl.camera, display=wl.display,
+                      views=wl.views, N=wl.N, binning=wl.binning)
+    return o["views"].astype(np.float32)
 
 
 def run_batched(args, dev):
@@ -574,27 +639,55 @@ def run_profile_grad(args):
     print("profile grad: composite status %d" % r.composite_status(), flush=True)
 
 
-def cpu_baseline(min_seconds=10.0, max_frames=40):
-    """The FP64 oracle, as it stands, on the host cores: full LF frames of
-    the same workload (all 1M Gaussians splatted into 64 planes, 45 views
-    composited), repeated until about min_seconds of CPU work."""
+def _oracle_rate(wl, min_seconds, max_frames):
+    """Full LF frames of the oracle on wl, repeated until about min_seconds
+    (at least one frame); returns (frames/s, frames, seconds, last result)."""
     import oracle
-    from paper_2508_18540_gb300 import synth as S
-    wl = S.workload_display(seed=WORKLOAD["seed"], n=WORKLOAD["n"], res=WORKLOAD["res"], N=WORKLOAD["N"],
-                            V=WORKLOAD["V"])
-    oracle.lib()
     t0 = time.perf_counter()
-    n_frames = 0
-    last = None
+    n_frames, last = 0, None
     while n_frames < max_frames:
         last = oracle.render(wl)
         n_frames += 1
         if time.perf_counter() - t0 >= min_seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": round(n_frames / dt, 4), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    return n_frames / dt, n_frames, dt, last
+
+
+def cpu_baseline(min_seconds=10.0, max_frames=40):
+    """The FP64 oracle, as it stands, on the host cores: full LF frames of
+    the same workload (all 1M Gaussians splatted into 64 planes, 45 views
+    composited), repeated until about min_seconds of CPU work, with every
+    core; beside it one frame on one thread, the 10k-Gaussian workload in
+    full on one thread and on every core, and the 2M-voxel V2LF workload in
+    full on every core."""
+    import oracle
+    from paper_2508_18540_gb300 import synth as S
+    wl = S.workload_display(seed=WORKLOAD["seed"], n=WORKLOAD["n"], res=WORKLOAD["res"], N=WORKLOAD["N"],
+                            V=WORKLOAD["V"])
+    oracle.lib()
+    oracle.set_num_threads(0)
+    cores = oracle.num_threads()
+    rate, n_frames, dt, last = _oracle_rate(wl, min_seconds, max_frames)
+    by_config = {}
+    oracle.set_num_threads(1)
+    r1, n1, t1, _ = _oracle_rate(wl, 0.0, 1)
+    by_config["g2lf_display_1M_512px_N64_45v"] = {
+        "all_cores": {"value": round(rate, 4), "threads": cores, "frames": n_frames, "seconds": round(dt, 2)},
+        "one_thread": {"value": round(r1, 4), "threads": 1, "frames": n1, "seconds": round(t1, 2)}}
+    tiny = S.workload_tiny()
+    r1, n1, t1, _ = _oracle_rate(tiny, 1.0, 200)
+    oracle.set_num_threads(0)
+    ra, na, ta, _ = _oracle_rate(tiny, 1.0, 200)
+    by_config[tiny.name] = {"all_cores": {"value": round(ra, 3), "threads": cores, "frames": na, "seconds": round(ta, 2)},
+                            "one_thread": {"value": round(r1, 3), "threads": 1, "frames": n1, "seconds": round(t1, 2)}}
+    vw = _voxel_workload()
+    rv, nv, tv, _ = _oracle_rate(vw, 0.0, 1)
+    by_config[vw.name] = {"all_cores": {"value": round(rv, 4), "threads": cores, "frames": nv, "seconds": round(tv, 2)}}
+    return {"value": round(rate, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d full LF frame(s) of the 1M-Gaussian 512px N64 45-view workload, FP64, OpenMP" % n_frames,
-            "seconds": round(dt, 2), "host": _host()}, last["views"]
+            "seconds": round(dt, 2), "host": _host(), "by_config": by_config,
+            "by_config_unit": "LF frames/s (full frames: splat + composite)"}, last["views"]
 
 
 def _host():
@@ -679,6 +772,11 @@ def main():
     else:
         import __graft_entry__
         __graft_entry__.build()
+        rank, world, _ = _env_rank()
+        if world == 1 and not args.no_cpu_baseline and not args.no_extras:
+            from oracle import build as obuild
+            obuild.build()
+            args.fit_target = oracle_fit_target()
         line = run_ours(args)
         rank, world, _ = _env_rank()
         views_host = line.pop("_views_host", None) if line is not None else None

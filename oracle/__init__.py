@@ -88,6 +88,8 @@ def lib():
                                         ctypes.c_int32]
         L.orc_num_threads.argtypes = []
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
+        L.orc_set_num_threads.restype = None
         L.orc_composite.argtypes = [ctypes.POINTER(OrcRef), ctypes.c_int32, _P, _P, _P, ctypes.c_int32,
                                     ctypes.c_int32, ctypes.c_int32, _P, _P]
         _lib = L
@@ -97,6 +99,11 @@ def lib():
 def num_threads() -> int:
     """Threads the oracle's OpenMP loops use."""
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Sets the threads of the oracle's OpenMP loops (n <= 0: one per processor)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def _ptr(a: np.ndarray):

@@ -156,6 +156,9 @@ void orc_composite(const orc_ref* r, int32_t N, const double* planes, const doub
 /* Threads the oracle's OpenMP loops run on (omp_get_max_threads). */
 int orc_num_threads(void);
 
+/* Sets that thread count (n <= 0: one per processor). */
+void orc_set_num_threads(int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -202,6 +202,11 @@ void orc_composite(const orc_ref* r, int32_t N, const double* planes, const doub
     free(dy);
 }
 
+void orc_set_num_threads(int n)
+{
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+}
+
 int orc_num_threads(void)
 {
     return omp_get_max_threads();

@@ -378,6 +378,17 @@ def test_display_scale_workload(orc, dtype):
     _compare(gpu, o, o["ref"].W, o["ref"].H, w.N, dtype, check_lists=False)
 
 
+def test_v2lf_display_scale_workload(orc):
+    # the bench's V2LF workload and launch configuration (2M sparse voxels,
+    # 512^2, N = 64, 45 views, FP32 planes): culling, rectangles, depth
+    # order, chunks and plane depths bit-exact; planes and all views within
+    # the FP32 tolerance
+    w = S.workload_voxels()
+    o = orc.render(w)
+    gpu = G.run_gpu(w.scene, w.camera, w.display, w.views, w.N, w.binning, "f32")
+    _compare(gpu, o, o["ref"].W, o["ref"].H, w.N, "f32", check_lists=False)
+
+
 def test_renderer_graph_replay():
     # one CUDA graph per frame: replays equal a plain render, and read the
     # scene buffers in place (new colours show up in the next replay)
