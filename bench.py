@@ -513,17 +513,25 @@ def oracle_fit_target():
 
 def run_batched(args, dev):
     """Six uneven G2LF scenes (50k..3M Gaussians, 9..128 views, 256^2..1024^2,
-    N 64..512, FP16 planes): autotuned plan, one CUDA-graph launch per frame,
-    against the same scenes rendered one by one."""
+    N 64..512, FP16 planes): autotuned plan (views per thread, composite
+    tile, chunk groups, scene schedule), one CUDA-graph launch per frame,
+    against the same scenes rendered one by one; beside it the frame time of
+    1, 2 and 4 chunk groups with the tuned composite layout."""
     import torch
     from paper_2508_18540_gb300 import api
     from paper_2508_18540_gb300 import synth as S
     wls = S.workloads_batched()
-    b = api.BatchRenderer(wls, "f16", device=dev)
+    b = api.BatchRenderer(wls, "f16", device=dev, max_chunk_groups=4)
     plan, tune_ms = b.autotune(reps=1)
-    b.capture()
     s = b.stream
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    by_groups = {}
+    for gr in (1, 2, 4):
+        pl = dict(plan, chunk_groups=gr, schedule=plan["schedule"] if plan["schedule"] != 2 else 1)
+        b.prepare(pl)
+        by_groups[str(gr)] = round(_event_ms(b.render, max(3, args.steps // 4), 2, s, flush), 3)
+    b.prepare(plan)
+    b.capture()
     k0 = api.lf_launch_count()
     g_ms = _event_ms(b.launch, args.steps, args.warmup, s, flush)
     launches = (api.lf_launch_count() - k0) // max(1, args.steps + args.warmup)
@@ -544,7 +552,9 @@ def run_batched(args, dev):
             "planes": "f16", "status": status, "plan": plan, "autotune_ms": round(tune_ms, 3),
             "graph_ms_per_frame": round(g_ms, 3), "batch_frames_per_s": round(1000.0 / g_ms, 2),
             "views_per_s": round(views * 1000.0 / g_ms, 1), "kernels_per_frame": int(launches),
-            "one_by_one_ms_per_frame": round(s_ms, 3)}
+            "one_by_one_ms_per_frame": round(s_ms, 3),
+            "chunk_groups_ms_per_frame": by_groups,
+            "chunk_groups_note": "persistent schedule (tuned composite layout), plain launches, L2 flushed"}
 
 
 def run_sweeps(args, dev):

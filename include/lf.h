@@ -348,13 +348,19 @@ lf_status lf_build_mpi_backward_voxels(const lf_voxels* v, const lf_ref_camera* 
  * Several G2LF scenes of uneven sizes, view counts, resolutions and N
  * rendered together: each scene's build runs up to its tile lists, then ONE
  * persistent raster launch covers the (tile, chunk) items of every scene and
- * ONE persistent staged-composite launch covers the (view group, row band,
- * column tile) items of every scene, CTAs pulling items from a global
- * counter; or (schedule 2) every scene's single-scene pipeline runs on a
- * stream of its own, all in parallel. The whole batch can be captured once
- * into a CUDA graph and relaunched per frame. An autotuner times candidate
- * plans (views per thread, composite tile shape, raster pixels per thread,
- * scene schedule) on the batch itself. Results are identical for every plan.
+ * ONE persistent staged-composite launch covers the (chunk group, view
+ * group, row band, column tile) items of every scene, CTAs pulling items
+ * from a global counter; or (schedule 2) every scene's single-scene pipeline
+ * runs on a stream of its own, all in parallel. With chunk groups G > 1 a
+ * scene's non-empty planes are cut into G contiguous shares composited
+ * separately into partial (Q, T) per view pixel and then composed front to
+ * back, Q = Q_f + T_f Q_b, T = T_f T_b (the over operator of Eq.
+ * alpha_blend is associative). The whole batch can be captured once into a
+ * CUDA graph and relaunched per frame. An autotuner times candidate plans
+ * (views per thread, composite tile shape, chunk groups, scene schedule) on
+ * the batch itself. Integer results (chunks, rectangles, lists) are
+ * identical for every plan, and so are the views for G = 1; G > 1 changes
+ * only the rounding order of the composite.
  */
 
 /* One scene of a batch. Every pointer is device memory the caller owns and
@@ -378,11 +384,14 @@ typedef struct {
 } lf_batch_scene;
 
 /* Launch plan of a batch:
- *  views_per_thread  composite views per thread: 3, 5 or 9;
+ *  views_per_thread  composite views per thread: 3, 5, 9 or 15 (15: one
+ *                    CTA per SM, the others two);
  *  tile_x            composite CTA tile width (columns): 128, 256 or 512
  *                    (the tile is tile_x x 512/tile_x pixels);
- *  raster_ppt        raster pixels per thread: 4 or 8 (warp strips of 8 x 16
- *                    or 8 x 32 pixels);
+ *  chunk_groups      1, 2 or 4: the contiguous shares of every scene's
+ *                    non-empty planes that are composited as separate items
+ *                    and composed in order (partial buffers in the batch
+ *                    workspace: lf_batch_plan_workspace_size);
  *  schedule          0: items in scene order; 1: largest scenes first;
  *                    2: no persistent launches -- every scene's own
  *                    lf_build_mpi_gaussians + lf_composite on a stream of its
@@ -391,7 +400,7 @@ typedef struct {
 typedef struct {
     int32_t views_per_thread;
     int32_t tile_x;
-    int32_t raster_ppt;
+    int32_t chunk_groups;
     int32_t schedule;
 } lf_batch_plan;
 
@@ -402,12 +411,19 @@ typedef struct lf_batch lf_batch;   /* opaque host-side batch object */
  * LF_ERR_UNSUPPORTED (a plane row that is not a multiple of 16 bytes). */
 lf_status lf_batch_create(const lf_batch_scene* scenes, int32_t n_scenes, lf_batch** out);
 
-/* Device bytes of the batch workspace (scene tables and work counters). */
+/* Device bytes of the batch workspace for plans with one chunk group (scene
+ * tables and work counters). */
 size_t lf_batch_workspace_size(const lf_batch* b);
 
-/* Sets the plan (NULL = default {9, 512, 2, 1}) and uploads the scene tables
- * into ws (device, ws_bytes, 256-byte aligned) on stream. Must be called
- * before lf_batch_render and again after a plan change; not during capture. */
+/* Device bytes of the batch workspace for plan (NULL = default): the tables
+ * plus, for chunk_groups G > 1, G - 1 partial buffers of every scene's
+ * views (16 bytes per view pixel each). 0 for an invalid plan. */
+size_t lf_batch_plan_workspace_size(const lf_batch* b, const lf_batch_plan* plan);
+
+/* Sets the plan (NULL = default {9, 512, 1, 1}) and uploads the scene tables
+ * into ws (device, ws_bytes >= lf_batch_plan_workspace_size, 256-byte
+ * aligned) on stream. Must be called before lf_batch_render and again after
+ * a plan change; not during capture. */
 lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /* Enqueues one frame of the whole batch on stream (builds, persistent
@@ -423,8 +439,8 @@ lf_status lf_batch_capture(lf_batch* b, cudaStream_t stream);
 lf_status lf_batch_launch(lf_batch* b, cudaStream_t stream);
 
 /* Times every candidate plan (coordinate search: composite views per thread
- * x tile width, then raster pixels per thread x schedules 0 and 1, then
- * schedule 2), reps frames each
+ * {3, 5, 9, 15} x tile width, then chunk groups x schedules 0 and 1 -- the group counts
+ * whose partial buffers fit in ws_bytes -- then schedule 2), reps frames each
  * after one warm-up frame, with CUDA events on stream; leaves b prepared with
  * the fastest plan and returns it in *best (host) and its mean frame time in
  * *best_ms (host, may be NULL). Synchronises the stream. */

@@ -82,7 +82,7 @@ class LfBatchScene(ctypes.Structure):
 
 
 class LfBatchPlan(ctypes.Structure):
-    _fields_ = [("views_per_thread", _I32), ("tile_x", _I32), ("raster_ppt", _I32), ("schedule", _I32)]
+    _fields_ = [("views_per_thread", _I32), ("tile_x", _I32), ("chunk_groups", _I32), ("schedule", _I32)]
 
 
 # (name, restype, argtypes) of every exported symbol declared in include/lf.h
@@ -114,6 +114,7 @@ SIGNATURES = [
                                                     _P, ctypes.c_size_t, _P]),
     ("lf_batch_create", ctypes.c_int, [ctypes.POINTER(LfBatchScene), _I32, ctypes.POINTER(_P)]),
     ("lf_batch_workspace_size", ctypes.c_size_t, [_P]),
+    ("lf_batch_plan_workspace_size", ctypes.c_size_t, [_P, ctypes.POINTER(LfBatchPlan)]),
     ("lf_batch_prepare", ctypes.c_int, [_P, ctypes.POINTER(LfBatchPlan), _P, ctypes.c_size_t, _P]),
     ("lf_batch_render", ctypes.c_int, [_P, _P]),
     ("lf_batch_capture", ctypes.c_int, [_P, _P]),

@@ -546,7 +546,8 @@ class BatchRenderer:
     Scene data is copied to the device once (update it in place through
     .prims[i] tensors; the captured graph reads the same buffers)."""
 
-    def __init__(self, workloads, dtype: str = "f16", device="cuda", stream: Optional[torch.cuda.Stream] = None):
+    def __init__(self, workloads, dtype: str = "f16", device="cuda", stream: Optional[torch.cuda.Stream] = None,
+                 max_chunk_groups: int = 1):
         self.device = device
         self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
         self.parts = []
@@ -570,7 +571,12 @@ class BatchRenderer:
         h = ctypes.c_void_p()
         check(load().lf_batch_create(scenes, len(workloads), ctypes.byref(h)))
         self.handle = h
-        self.ws = alloc_workspace(int(load().lf_batch_workspace_size(h)), device)
+        # workspace for plans of up to max_chunk_groups chunk groups (1, 2 or 4)
+        biggest = L.LfBatchPlan(9, 512, int(max_chunk_groups), 0)
+        nbytes = int(load().lf_batch_plan_workspace_size(h, ctypes.byref(biggest)))
+        if nbytes == 0:
+            raise ValueError("max_chunk_groups must be 1, 2 or 4")
+        self.ws = alloc_workspace(nbytes, device)
         self.plan = None
         self.prepare()
 
@@ -589,7 +595,7 @@ class BatchRenderer:
     def prepare(self, plan: Optional[dict] = None):
         p = None
         if plan is not None:
-            p = L.LfBatchPlan(plan["views_per_thread"], plan["tile_x"], plan["raster_ppt"], plan["schedule"])
+            p = L.LfBatchPlan(plan["views_per_thread"], plan["tile_x"], plan.get("chunk_groups", 1), plan["schedule"])
         check(load().lf_batch_prepare(self.handle, ctypes.byref(p) if p is not None else None, _ptr(self.ws),
                                       self.ws.numel(), ctypes.c_void_p(self.stream.cuda_stream)))
         self.plan = plan
@@ -609,7 +615,7 @@ class BatchRenderer:
         check(load().lf_batch_autotune(self.handle, _ptr(self.ws), self.ws.numel(), int(reps),
                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(best), ctypes.byref(ms)))
         self.plan = {"views_per_thread": best.views_per_thread, "tile_x": best.tile_x,
-                     "raster_ppt": best.raster_ppt, "schedule": best.schedule}
+                     "chunk_groups": best.chunk_groups, "schedule": best.schedule}
         return self.plan, float(ms.value)
 
     def status(self):

@@ -19,7 +19,7 @@ using namespace lf;
 
 struct lf_batch {
     std::vector<lf_batch_scene> sc;
-    lf_batch_plan plan{9, 512, 4, 1};
+    lf_batch_plan plan{9, 512, 1, 1};
     int dtype = LF_F32;
     int bilinear = 0;
     bool prepared = false;
@@ -47,7 +47,33 @@ namespace {
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-size_t batch_ws_bytes(int n) { return align256(16) + align256(sizeof(RasterScene) * n) + align256(sizeof(CompScene) * n); }
+size_t batch_tables_bytes(int n)
+{
+    return align256(16) + align256(sizeof(RasterScene) * n) + align256(sizeof(CompScene) * n);
+}
+
+// bytes of one scene's chunk-group partials (groups 1 .. groups - 1)
+size_t scene_part_bytes(const lf_batch_scene& s, int groups)
+{
+    if (groups <= 1) return 0;
+    return align256((size_t)(groups - 1) * s.views.Vx * s.views.Vy * s.ref.base.Nx * s.ref.base.Ny * sizeof(float4));
+}
+
+size_t batch_ws_bytes(const lf_batch* b, int groups)
+{
+    size_t t = batch_tables_bytes((int)b->sc.size());
+    for (const lf_batch_scene& s : b->sc) t += scene_part_bytes(s, groups);
+    return t;
+}
+
+bool plan_valid(const lf_batch_plan& pl)
+{
+    return (pl.views_per_thread == 3 || pl.views_per_thread == 5 || pl.views_per_thread == 9 ||
+            pl.views_per_thread == 15) &&
+           (pl.tile_x == 128 || pl.tile_x == 256 || pl.tile_x == 512) &&
+           (pl.chunk_groups == 1 || pl.chunk_groups == 2 || pl.chunk_groups == kMaxChunkGroups) &&
+           pl.schedule >= 0 && pl.schedule <= 2;
+}
 
 lf_status check_scene(const lf_batch_scene& s, int i)
 {
@@ -92,16 +118,22 @@ lf_status lf_batch_create(const lf_batch_scene* scenes, int32_t n_scenes, lf_bat
     return LF_OK;
 }
 
-size_t lf_batch_workspace_size(const lf_batch* b) { return b ? batch_ws_bytes((int)b->sc.size()) : 0; }
+size_t lf_batch_workspace_size(const lf_batch* b) { return b ? batch_ws_bytes(b, 1) : 0; }
+
+size_t lf_batch_plan_workspace_size(const lf_batch* b, const lf_batch_plan* plan)
+{
+    if (!b) return 0;
+    const lf_batch_plan pl = plan ? *plan : lf_batch_plan{9, 512, 1, 1};
+    if (!plan_valid(pl)) return 0;
+    return batch_ws_bytes(b, pl.schedule == 2 ? 1 : pl.chunk_groups);
+}
 
 lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, size_t ws_bytes, cudaStream_t stream)
 {
     if (!b) return fail(LF_ERR_INVALID_ARG, "batch is NULL");
-    const lf_batch_plan pl = plan ? *plan : lf_batch_plan{9, 512, 4, 1};
-    if ((pl.views_per_thread != 3 && pl.views_per_thread != 5 && pl.views_per_thread != 9) ||
-        (pl.tile_x != 128 && pl.tile_x != 256 && pl.tile_x != 512) || (pl.raster_ppt != 4 && pl.raster_ppt != 8) ||
-        (pl.schedule < 0 || pl.schedule > 2))
-        return fail(LF_ERR_INVALID_ARG, "lf_batch_prepare: plan out of range");
+    const lf_batch_plan pl = plan ? *plan : lf_batch_plan{9, 512, 1, 1};
+    if (!plan_valid(pl)) return fail(LF_ERR_INVALID_ARG, "lf_batch_prepare: plan out of range");
+    const int groups = pl.schedule == 2 ? 1 : pl.chunk_groups;
     if (pl.schedule == 2 && b->side.empty()) {
         b->side.resize(b->sc.size(), nullptr);
         b->done.resize(b->sc.size(), nullptr);
@@ -114,7 +146,8 @@ lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, siz
     }
     const int n = (int)b->sc.size();
     if (!ws || ((uintptr_t)ws) % 256) return fail(LF_ERR_WORKSPACE, "batch workspace NULL or not 256-byte aligned");
-    if (ws_bytes < batch_ws_bytes(n)) return fail(LF_ERR_WORKSPACE, "batch workspace too small");
+    if (ws_bytes < batch_ws_bytes(b, groups))
+        return fail(LF_ERR_WORKSPACE, "batch workspace too small for this plan (lf_batch_plan_workspace_size)");
     char* base = static_cast<char*>(ws);
     b->counters = reinterpret_cast<unsigned long long*>(base);
     b->rtab = reinterpret_cast<RasterScene*>(base + align256(16));
@@ -149,6 +182,8 @@ lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, siz
         c[i].out = s.out;
         c[i].nby = (cp.Ny + c[i].G.BY - 1) / c[i].G.BY;
         c[i].nbz = (cp.Nx + c[i].G.TX - 1) / c[i].G.TX;
+        c[i].groups = groups;
+        c[i].part = nullptr;
         cwork[i] = (double)cp.Vx * cp.Vy * cp.Nx * cp.Ny * cp.N;
         max_stage = std::max(max_stage, c[i].G.stage_bytes);
         maxN = std::max(maxN, s.N);
@@ -173,7 +208,7 @@ lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, siz
         b->rhost[q] = R;
         CompScene C = c[co[q]];
         C.base = ct;
-        ct += (long long)C.G.groups_x * C.p.Vy * C.nby * C.nbz;
+        ct += (long long)C.G.groups_x * C.p.Vy * C.nby * C.nbz * C.groups;
         b->chost[q] = C;
     }
     for (int q = 0; q < n; ++q) {
@@ -183,6 +218,16 @@ lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, siz
     b->r_heavy = hb;
     b->r_total = hb + lb;
     b->c_total = ct;
+    {
+        char* part = base + batch_tables_bytes(n);
+        for (int q = 0; q < n; ++q) {
+            if (groups > 1) {
+                const lf_batch_scene& sc = b->sc[co[q]];
+                b->chost[q].part = reinterpret_cast<float4*>(part);
+                part += scene_part_bytes(sc, groups);
+            }
+        }
+    }
     b->max_stage = max_stage;
     b->maxN = maxN;
     int dev = 0, sms = 0;
@@ -190,7 +235,8 @@ lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, siz
                                                   cudaSuccess)
         return check_launch("device query");
     const size_t smem = composite_batched_smem(max_stage, maxN, pl.views_per_thread);
-    b->c_ctas = sms * ((2 * (smem + 1024) <= 228 * 1024) ? 2 : 1);
+    // views per thread above kTwoCtaViews take up to 96 registers: one CTA per SM
+    b->c_ctas = sms * ((pl.views_per_thread <= kTwoCtaViews && 2 * (smem + 1024) <= 228 * 1024) ? 2 : 1);
     if (cudaMemcpyAsync(b->rtab, b->rhost.data(), sizeof(RasterScene) * n, cudaMemcpyHostToDevice, stream) !=
             cudaSuccess ||
         cudaMemcpyAsync(b->ctab, b->chost.data(), sizeof(CompScene) * n, cudaMemcpyHostToDevice, stream) !=
@@ -260,7 +306,14 @@ lf_status lf_batch_render(lf_batch* b, cudaStream_t stream)
                                              b->c_ctas, stream);
     trace_end(stream);
     if (!ok) return fail(LF_ERR_UNSUPPORTED, "batched composite layout does not fit shared memory");
-    return check_launch("batched composite");
+    if ((st = check_launch("batched composite")) != LF_OK) return st;
+    if (b->plan.chunk_groups > 1) {
+        trace_begin("merge_chunk_groups", stream);
+        for (const CompScene& C : b->chost) launch_merge_chunk_groups(C.p, C.groups, C.part, C.out, stream);
+        trace_end(stream);
+        return check_launch("chunk-group merge");
+    }
+    return LF_OK;
 }
 
 lf_status lf_batch_capture(lf_batch* b, cudaStream_t stream)
@@ -328,13 +381,13 @@ lf_status lf_batch_autotune(lf_batch* b, void* ws, size_t ws_bytes, int32_t reps
         *ms = t / reps;
         return LF_OK;
     };
-    lf_batch_plan cur{9, 512, 4, 1};
+    lf_batch_plan cur{9, 512, 1, 1};
     float cur_ms = 3.4e38f;
     lf_status st = LF_OK;
-    const int vgs[3] = {3, 5, 9}, txs[3] = {128, 256, 512};
-    for (int a = 0; a < 3 && st == LF_OK; ++a)
+    const int vgs[4] = {3, 5, 9, 15}, txs[3] = {128, 256, 512};
+    for (int a = 0; a < 4 && st == LF_OK; ++a)
         for (int c = 0; c < 3 && st == LF_OK; ++c) {
-            lf_batch_plan pl{vgs[a], txs[c], cur.raster_ppt, cur.schedule};
+            lf_batch_plan pl{vgs[a], txs[c], cur.chunk_groups, cur.schedule};
             float ms = 0.f;
             st = time_plan(pl, &ms);
             if (st == LF_ERR_UNSUPPORTED) {   // layout too large for this plan: skip it
@@ -343,17 +396,25 @@ lf_status lf_batch_autotune(lf_batch* b, void* ws, size_t ws_bytes, int32_t reps
             }
             if (st == LF_OK && ms < cur_ms) cur_ms = ms, cur = pl;
         }
+    // chunk groups x scene order, for the composite layout found above; only
+    // the group counts whose partial buffers fit the workspace
     lf_batch_plan comp = cur;
-    for (int ppt = 4; ppt <= 8 && st == LF_OK; ppt += 4)
+    const int gs[3] = {1, 2, kMaxChunkGroups};
+    for (int gi = 0; gi < 3 && st == LF_OK; ++gi)
         for (int sch = 0; sch <= 1 && st == LF_OK; ++sch) {
-            lf_batch_plan pl{comp.views_per_thread, comp.tile_x, ppt, sch};
-            if (pl.raster_ppt == comp.raster_ppt && pl.schedule == comp.schedule) continue;
+            lf_batch_plan pl{comp.views_per_thread, comp.tile_x, gs[gi], sch};
+            if (pl.chunk_groups == comp.chunk_groups && pl.schedule == comp.schedule) continue;
+            if (batch_ws_bytes(b, pl.chunk_groups) > ws_bytes) continue;
             float ms = 0.f;
             st = time_plan(pl, &ms);
+            if (st == LF_ERR_UNSUPPORTED) {
+                st = LF_OK;
+                continue;
+            }
             if (st == LF_OK && ms < cur_ms) cur_ms = ms, cur = pl;
         }
     if (st == LF_OK) {   // concurrent single-scene pipelines
-        lf_batch_plan pl{cur.views_per_thread, cur.tile_x, cur.raster_ppt, 2};
+        lf_batch_plan pl{cur.views_per_thread, cur.tile_x, 1, 2};
         float ms = 0.f;
         st = time_plan(pl, &ms);
         if (st == LF_OK && ms < cur_ms) cur_ms = ms, cur = pl;

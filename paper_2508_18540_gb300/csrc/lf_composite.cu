@@ -834,7 +834,7 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_com
 // stops taking items.
 // ---------------------------------------------------------------------------
 template <int DT, bool BILINEAR, int VG>
-__global__ void __launch_bounds__(kStagedBlock, 2) k_composite_batched(const CompScene* __restrict__ scs, int n_sc,
+__global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_composite_batched(const CompScene* __restrict__ scs, int n_sc,
                                                                          long long total,
                                                                          unsigned long long* __restrict__ counter,
                                                                          size_t max_stage_bytes, int maxN)
@@ -877,7 +877,10 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_batched(const Com
         const CompWs w = scs[si].w;
         const char* planes = scs[si].planes;
         const int nby = scs[si].nby;
-        const long long li = it - scs[si].base;
+        const long long li0 = it - scs[si].base;
+        const int cgs = scs[si].groups;
+        const int cg = (int)(li0 % cgs);              // chunk group
+        const long long li = li0 / cgs;
         const int ng = G.groups_x * p.Vy;
         const int vgroup = (int)(li % ng);
         const long long rest = li / ng;
@@ -890,9 +893,11 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_batched(const Com
         }
         if (si != prev) zero_pads<DT>(p, G, stage_base, max_stage_bytes, kStages);
         __syncthreads();
-        load_coefs<BILINEAR, VG>(p, w, plist, s_nplanes, vi, j0, coef);
+        // chunk group cg takes the non-empty planes [q0, q1) of the list
+        const int q0 = (int)((long long)s_nplanes * cg / cgs), q1 = (int)((long long)s_nplanes * (cg + 1) / cgs);
+        load_coefs<BILINEAR, VG>(p, w, plist + q0, q1 - q0, vi, j0, coef);
         __syncthreads();
-        const int P = s_nplanes;
+        const int P = q1 - q0;
 
         if (tid >= kStagedThreads) {
             if (tid == kStagedThreads) {
@@ -905,7 +910,7 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_batched(const Com
                         s_abort = 1;
                         break;
                     }
-                    produce_rows<DT>(p, G, planes, plist[q], coef + (size_t)q * CW, Y0,
+                    produce_rows<DT>(p, G, planes, plist[q0 + q], coef + (size_t)q * CW, Y0,
                                      stage_base + (size_t)st * max_stage_bytes, smem_addr(&full[st]));
                     if (++st == kStages) st = 0, ph ^= 1u, wr = true;
                 }
@@ -953,9 +958,19 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_batched(const Com
                     if (j >= p.Vx) break;
                     const int v = vi * p.Vx + j;
                     const float T = acc[jj][3];
-                    reinterpret_cast<float4*>(out)[view_pixel(p, v, x, y)] =
-                        make_float4(fmaf(T, p.bg[0], acc[jj][0]), fmaf(T, p.bg[1], acc[jj][1]),
-                                    fmaf(T, p.bg[2], acc[jj][2]), 1.0f - T);
+                    if (cgs == 1) {
+                        reinterpret_cast<float4*>(out)[view_pixel(p, v, x, y)] =
+                            make_float4(fmaf(T, p.bg[0], acc[jj][0]), fmaf(T, p.bg[1], acc[jj][1]),
+                                        fmaf(T, p.bg[2], acc[jj][2]), 1.0f - T);
+                    } else {
+                        // partial (Q, T) of this chunk group: group 0 in the
+                        // view buffer, group c > 0 in partial buffer c - 1
+                        const float4 qt = make_float4(acc[jj][0], acc[jj][1], acc[jj][2], T);
+                        if (cg == 0)
+                            reinterpret_cast<float4*>(out)[view_pixel(p, v, x, y)] = qt;
+                        else
+                            scs[si].part[(((size_t)(cg - 1) * p.Vx * p.Vy + v) * p.Ny + y) * p.Nx + x] = qt;
+                    }
                 }
             }
         }
@@ -1573,7 +1588,9 @@ template <int DT, bool BILINEAR>
 void launch_batched_vg(int VG, const CompScene* scs, int n_sc, long long total, size_t mx, int maxN,
                        unsigned long long* counter, int n_ctas, size_t smem, cudaStream_t s)
 {
-    if (VG == 9)
+    if (VG == 15)
+        launch_batched_t<DT, BILINEAR, 15>(scs, n_sc, total, mx, maxN, counter, n_ctas, smem, s);
+    else if (VG == 9)
         launch_batched_t<DT, BILINEAR, 9>(scs, n_sc, total, mx, maxN, counter, n_ctas, smem, s);
     else if (VG == 5)
         launch_batched_t<DT, BILINEAR, 5>(scs, n_sc, total, mx, maxN, counter, n_ctas, smem, s);
@@ -1617,6 +1634,44 @@ bool launch_composite_batched(const CompScene* scenes_dev, int n_sc, long long t
                                    s);
     note_launches(1);
     return true;
+}
+
+namespace {
+
+// Composition of a batch scene's chunk groups, front to back (the "over"
+// operator is associative): Q = Q_0 + T_0 Q_1 + T_0 T_1 Q_2 ..., T = T_0 T_1
+// ...; then the views (Q + T bg, 1 - T).
+__global__ void k_merge_chunk_groups(CompParams p, int groups, const float4* __restrict__ part, float* out)
+{
+    const long long per = (long long)p.Nx * p.Ny;
+    const long long total = per * p.Vx * p.Vy;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(e / per);
+        const long long pix = e - (long long)v * per;
+        const int y = (int)(pix / p.Nx), x = (int)(pix - (long long)y * p.Nx);
+        float4* dst = reinterpret_cast<float4*>(out) + view_pixel(p, v, x, y);
+        float4 a = *dst;
+        for (int c = 1; c < groups; ++c) {
+            const float4 b = __ldcs(part + ((size_t)(c - 1) * p.Vx * p.Vy * per + e));
+            a.x = fmaf(a.w, b.x, a.x);
+            a.y = fmaf(a.w, b.y, a.y);
+            a.z = fmaf(a.w, b.z, a.z);
+            a.w *= b.w;
+        }
+        *dst = make_float4(fmaf(a.w, p.bg[0], a.x), fmaf(a.w, p.bg[1], a.y), fmaf(a.w, p.bg[2], a.z), 1.0f - a.w);
+    }
+}
+
+}  // namespace
+
+void launch_merge_chunk_groups(const CompParams& p, int groups, const float4* part, float* out, cudaStream_t s)
+{
+    const long long total = (long long)p.Nx * p.Ny * p.Vx * p.Vy;
+    const long long want = (total + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 152 * 32 ? want : 152 * 32);
+    k_merge_chunk_groups<<<blocks, 256, 0, s>>>(p, groups, part, out);
+    note_launches(1);
 }
 
 void launch_wait_selftest(unsigned long long limit_ns, int* result, cudaStream_t s)

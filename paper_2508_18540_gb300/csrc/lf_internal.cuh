@@ -327,8 +327,8 @@ struct StagedGeom {
 StagedGeom staged_geom(const CompParams& p, int texel_bytes, bool bilinear, int VG, int tx_max);
 
 // batched (several scenes, one persistent launch): per-scene item table;
-// item li of a scene: view group li % (groups_x Vy), then row band, then
-// column tile
+// item li of a scene: chunk group li % groups, then view group, then row
+// band, then column tile
 struct CompScene {
     CompParams p;
     StagedGeom G;
@@ -338,7 +338,13 @@ struct CompScene {
     float* out;
     long long base;     // first global item of this scene
     int nby, nbz;       // row bands, column tiles
+    int groups;         // chunk groups: contiguous shares of the non-empty planes
+    float4* part;       // groups > 1: [groups - 1][V][Ny][Nx] partial (Q, T) of groups 1.. (group 0 in out)
 };
+constexpr int kMaxChunkGroups = 4;
+// groups > 1: composes the partials (group 0 in out, the others in part)
+// front to back into out's final views
+void launch_merge_chunk_groups(const CompParams& p, int groups, const float4* part, float* out, cudaStream_t s);
 void launch_comp_coeffs(const CompParams& p, const double* d, const int32_t* count, const CompWs& ws,
                         cudaStream_t s);
 // smem_bytes: the largest staged layout of the batch (its stage size, N)
