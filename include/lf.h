@@ -310,8 +310,11 @@ lf_status lf_composite_noalloc_status(int32_t N, const lf_view_set* views, cudaS
  * target light-field views. The integer structure of the forward pass
  * (culling, chunk membership, plane depths d_k, footprint rectangles, tile
  * lists, nearest indices) is held fixed: it is piecewise constant in the
- * parameters and receives no gradient. Transmittance is recomputed inside
- * the adjoint kernels, never stored by the forward pass. The clamp
+ * parameters and receives no gradient. The composite adjoint either
+ * recomputes each view pixel's transmittance with a front-to-back walk of
+ * its own (lf_composite_backward), or starts from 16 bytes per view pixel
+ * that the saving forward (lf_composite_save) wrote and walks the planes
+ * once (lf_composite_backward_saved). The clamp
  * alpha = min(0.99, .) passes no gradient where it is active. Gradients are
  * accumulated in FP32 with atomics, so their last bits depend on scheduling.
  */
@@ -324,6 +327,37 @@ lf_status lf_composite_noalloc_status(int32_t N, const lf_view_set* views, cudaS
  * lf_composite. */
 lf_status lf_composite_backward(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
                                 const float* dviews, float* dplanes, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Bytes of the saved composite state for these views of ref's output
+ * resolution (ref->base.Nx x ref->base.Ny): 16 per view pixel,
+ * Vy*Vx*Ny*Nx*16 (0 for a NULL argument or an empty view set). */
+size_t lf_composite_state_size(const lf_ref_camera* ref, const lf_view_set* views);
+
+/* lf_composite (Sec. 4.3, Eq. alpha_blend) in its saving form: each view
+ * pixel's walk stops at the first plane k behind which T would fall below
+ * 2^-64 (to 0 behind a plane with A = 1); plane k still blends, the colour
+ * of the planes behind it (below 2^-64 each) is dropped and the output's
+ * T is 0. Otherwise the same views as lf_composite. Per view pixel it also
+ * writes the state the adjoint starts from to state [Vy*Vx][Ny][Nx] of four
+ * 32-bit words (device, 16-byte aligned, state_bytes >=
+ * lf_composite_state_size(ref, views); separate-views order, also when out
+ * is an atlas): T_k (FP32) and k (int32), the transmittance in front of the
+ * stop plane k; or, when the walk never stops, T behind the last plane and
+ * k = N; then two zero words. The state is owned by the caller and stays
+ * valid while planes, ref and views are unchanged. Errors as lf_composite,
+ * and LF_ERR_INVALID_ARG for a NULL, misaligned or short state. */
+lf_status lf_composite_save(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views, float* out,
+                            float* state, size_t state_bytes, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* lf_composite_backward from the state lf_composite_save wrote for the same
+ * planes, ref and views: one back-to-front walk over the planes instead of
+ * two. The planes behind a pixel's stop plane get no gradient from it (their
+ * T, below 2^-64, is taken as 0); otherwise the same gradients up to FP32
+ * rounding. Same contract and errors as lf_composite_backward, and
+ * LF_ERR_INVALID_ARG for a NULL, misaligned or short state. */
+lf_status lf_composite_backward_saved(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
+                                      const float* dviews, const float* state, size_t state_bytes, float* dplanes,
+                                      void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /* Adjoint of lf_build_mpi_gaussians: given dplanes = dL/d(planes.rgba)
  * [N][H][W][4] FP32 device, writes the parameter gradients into grad (every

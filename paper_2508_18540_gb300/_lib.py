@@ -106,6 +106,13 @@ SIGNATURES = [
     ("lf_composite_noalloc_status", ctypes.c_int, [_I32, ctypes.POINTER(LfViewSet), _P]),
     ("lf_composite_backward", ctypes.c_int, [ctypes.POINTER(LfPlanes), ctypes.POINTER(LfRefCamera),
                                              ctypes.POINTER(LfViewSet), _P, _P, _P, ctypes.c_size_t, _P]),
+    ("lf_composite_state_size", ctypes.c_size_t, [ctypes.POINTER(LfRefCamera), ctypes.POINTER(LfViewSet)]),
+    ("lf_composite_save", ctypes.c_int, [ctypes.POINTER(LfPlanes), ctypes.POINTER(LfRefCamera),
+                                         ctypes.POINTER(LfViewSet), _P, _P, ctypes.c_size_t, _P, ctypes.c_size_t,
+                                         _P]),
+    ("lf_composite_backward_saved", ctypes.c_int, [ctypes.POINTER(LfPlanes), ctypes.POINTER(LfRefCamera),
+                                                   ctypes.POINTER(LfViewSet), _P, _P, ctypes.c_size_t, _P, _P,
+                                                   ctypes.c_size_t, _P]),
     ("lf_build_mpi_backward_gaussians", ctypes.c_int, [ctypes.POINTER(LfGaussians), ctypes.POINTER(LfRefCamera),
                                                        ctypes.POINTER(LfPlanes), _P, ctypes.POINTER(LfGaussiansGrad),
                                                        _P, ctypes.c_size_t, _P]),

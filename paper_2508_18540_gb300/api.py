@@ -260,6 +260,13 @@ def lf_composite(planes: Planes, ref: L.LfRefCamera, views, out: torch.Tensor, w
                               ws.numel(), _stream_ptr(stream)))
 
 
+def lf_composite_status(N: int, views, ws: torch.Tensor, stream=None) -> int:
+    """Status of the last composite (or adjoint) on workspace ws:
+    LF_ERR_TIMEOUT if a bounded device wait gave up, else LF_OK."""
+    vs = view_set(views)
+    return int(load().lf_composite_status(int(N), ctypes.byref(vs), _ptr(ws), _stream_ptr(stream)))
+
+
 def lf_composite_noalloc(planes: Planes, ref: L.LfRefCamera, views, out: torch.Tensor, stream=None):
     """lf_composite with the library's static scratch instead of a workspace
     (calls must not overlap in time)."""
@@ -335,6 +342,43 @@ def lf_composite_backward(planes: Planes, ref: L.LfRefCamera, views, dviews: tor
                                        _ptr(dplanes), _ptr(ws), ws.numel(), _stream_ptr(stream)))
 
 
+def lf_composite_state_size(ref: L.LfRefCamera, views) -> int:
+    vs = view_set(views)
+    return int(load().lf_composite_state_size(ctypes.byref(ref), ctypes.byref(vs)))
+
+
+def composite_state_shape(ref: L.LfRefCamera, views):
+    """Shape of the saved composite state: [Vy*Vx][Ny][Nx][4] 32-bit words."""
+    vs = view_set(views)
+    return (vs.Vx * vs.Vy, ref.base.Ny, ref.base.Nx, 4)
+
+
+def lf_composite_save(planes: Planes, ref: L.LfRefCamera, views, out: torch.Tensor, state: torch.Tensor,
+                      ws: torch.Tensor, stream=None):
+    """lf_composite that also writes the adjoint's starting state (16 bytes per
+    view pixel) into state (asynchronous)."""
+    vs = view_set(views)
+    _need(out, views_shape(views, ref.base.Nx, ref.base.Ny), torch.float32, "views")
+    _need(state, composite_state_shape(ref, views), torch.float32, "state")
+    ps = planes.c_struct()
+    check(load().lf_composite_save(ctypes.byref(ps), ctypes.byref(ref), ctypes.byref(vs), _ptr(out), _ptr(state),
+                                   state.numel() * 4, _ptr(ws), ws.numel(), _stream_ptr(stream)))
+
+
+def lf_composite_backward_saved(planes: Planes, ref: L.LfRefCamera, views, dviews: torch.Tensor,
+                                state: torch.Tensor, dplanes: torch.Tensor, ws: torch.Tensor, stream=None):
+    """Adjoint of lf_composite_save from its state: one back-to-front plane
+    walk (asynchronous)."""
+    vs = view_set(views)
+    _need(dviews, (vs.Vx * vs.Vy, ref.base.Ny, ref.base.Nx, 4), torch.float32, "dviews")
+    _need(state, composite_state_shape(ref, views), torch.float32, "state")
+    _need(dplanes, (planes.N, ref.H, ref.W, 4), torch.float32, "dplanes")
+    ps = planes.c_struct()
+    check(load().lf_composite_backward_saved(ctypes.byref(ps), ctypes.byref(ref), ctypes.byref(vs), _ptr(dviews),
+                                             _ptr(state), state.numel() * 4, _ptr(dplanes), _ptr(ws), ws.numel(),
+                                             _stream_ptr(stream)))
+
+
 def lf_build_mpi_backward_gaussians(g: DeviceGaussians, ref: L.LfRefCamera, planes: Planes, dplanes: torch.Tensor,
                                     grads: GaussianGrads, ws: torch.Tensor, stream=None):
     """Adjoint of lf_build_mpi_gaussians (ws: the forward's workspace, unchanged)."""
@@ -365,7 +409,7 @@ class LightFieldRenderer:
 
     def __init__(self, camera, display, views, N: int, binning: str = "quantile", dtype: str = "f32",
                  n_capacity: int = 0, dup_capacity: int = 0, device="cuda", plane_filter: float = 0.0,
-                 blend: str = "exact"):
+                 blend: str = "exact", save_state: bool = False):
         if blend not in BLEND:
             raise ValueError("blend must be one of %s" % sorted(BLEND))
         self.camera, self.display, self.views = camera, display, views
@@ -380,6 +424,14 @@ class LightFieldRenderer:
         self.ws = None
         self.cws = alloc_workspace(lf_composite_workspace_size(self.N, views), device)
         self.out = torch.empty(views_shape(views, camera.Nx, camera.Ny), dtype=torch.float32, device=device)
+        # save_state: composite() runs the saving form (lf_composite_save) and
+        # backward() starts the composite adjoint from its state (one plane
+        # walk instead of two); 16 bytes per view pixel
+        self.save_state = bool(save_state)
+        self.state = (torch.empty(composite_state_shape(self.ref, views), dtype=torch.float32, device=device)
+                      if self.save_state else None)
+        self.state_generation = -1
+        self.generation = 0
 
     def _ensure(self, n: int):
         if self.planes is None or n > self.n_capacity:
@@ -391,7 +443,7 @@ class LightFieldRenderer:
 
     def build(self, prims, stream=None):
         self._ensure(prims.n)
-        self.generation = getattr(self, "generation", 0) + 1
+        self.generation += 1
         pl = self.planes
         view = Planes(pl.rgba, pl.d, pl.count, pl.chunk[: max(prims.n, 1)], pl.rect[: max(prims.n, 1)], pl.dtype_code)
         if isinstance(prims, DeviceGaussians):
@@ -406,7 +458,11 @@ class LightFieldRenderer:
 
     def composite(self, stream=None, out: Optional[torch.Tensor] = None):
         out = self.out if out is None else out
-        lf_composite(self.planes, self.ref, self.views, out, self.cws, stream)
+        if self.save_state:
+            lf_composite_save(self.planes, self.ref, self.views, out, self.state, self.cws, stream)
+            self.state_generation = self.generation
+        else:
+            lf_composite(self.planes, self.ref, self.views, out, self.cws, stream)
         return out
 
     def render(self, prims, stream=None):
@@ -453,7 +509,11 @@ class LightFieldRenderer:
         if self.blend != "exact":
             raise ValueError("the adjoint differentiates exact blending; this renderer uses %r" % self.blend)
         dplanes = torch.empty((self.N, self.ref.H, self.ref.W, 4), dtype=torch.float32, device=self.device)
-        lf_composite_backward(self.planes, self.ref, self.views, dviews, dplanes, self.cws, stream)
+        if self.save_state and self.state_generation == self.generation:
+            lf_composite_backward_saved(self.planes, self.ref, self.views, dviews, self.state, dplanes, self.cws,
+                                        stream)
+        else:
+            lf_composite_backward(self.planes, self.ref, self.views, dviews, dplanes, self.cws, stream)
         view = self.planes_view(prims.n)
         if isinstance(prims, DeviceGaussians):
             grads = GaussianGrads.empty(prims.n, self.device)

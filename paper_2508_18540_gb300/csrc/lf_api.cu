@@ -299,6 +299,9 @@ static lf_status check_composite_args(const lf_planes* planes, const lf_ref_came
         return fail(LF_ERR_INVALID_ARG, "plane array shape does not match the reference camera");
     if (planes->dtype < LF_F32 || planes->dtype > LF_U8) return fail(LF_ERR_INVALID_ARG, "unknown plane dtype");
     if (!planes->rgba || !planes->d || !planes->count) return fail(LF_ERR_INVALID_ARG, "plane pointer is NULL");
+    // texels are read whole (16, 8 or 4 bytes)
+    const uintptr_t texel = planes->dtype == LF_F32 ? 16 : (planes->dtype == LF_U8 ? 4 : 8);
+    if (((uintptr_t)planes->rgba) % texel) return fail(LF_ERR_INVALID_ARG, "planes->rgba is not texel-aligned");
     if (views->Vx < 1 || views->Vy < 1 || views->Vx > 65535 || views->Vy > 65535)
         return fail(LF_ERR_INVALID_ARG, "view counts must be in 1..65535");
     if (views->atlas_cols < 0) return fail(LF_ERR_INVALID_ARG, "atlas_cols must be >= 0");
@@ -737,12 +740,54 @@ lf_status lf_composite(const lf_planes* planes, const lf_ref_camera* ref, const 
     return check_launch("composite");
 }
 
-lf_status lf_composite_backward(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
-                                const float* dviews, float* dplanes, void* ws, size_t ws_bytes, cudaStream_t stream)
+size_t lf_composite_state_size(const lf_ref_camera* ref, const lf_view_set* views)
+{
+    if (!ref || !views || views->Vx < 1 || views->Vy < 1 || ref->base.Nx < 1 || ref->base.Ny < 1) return 0;
+    return (size_t)16 * views->Vx * views->Vy * ref->base.Nx * ref->base.Ny;
+}
+
+// after check_composite_args (ref and views valid)
+static lf_status check_state(const lf_ref_camera* ref, const lf_view_set* views, const void* state,
+                             size_t state_bytes)
+{
+    if (!state) return fail(LF_ERR_INVALID_ARG, "state is NULL");
+    if (((uintptr_t)state) % 16) return fail(LF_ERR_INVALID_ARG, "state must be 16-byte aligned");
+    if (state_bytes < lf_composite_state_size(ref, views))
+        return fail(LF_ERR_INVALID_ARG, "state is smaller than lf_composite_state_size(ref, views)");
+    return LF_OK;
+}
+
+lf_status lf_composite_save(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views, float* out,
+                            float* state, size_t state_bytes, void* ws, size_t ws_bytes, cudaStream_t stream)
+{
+    CompWs cw;
+    lf_status st = check_composite_args(planes, ref, views, out, ws, ws_bytes, &cw);
+    if (st != LF_OK) return st;
+    if ((st = check_state(ref, views, state, state_bytes)) != LF_OK) return st;
+    CompParams p;
+    fill_comp_params(planes, ref, views, &p);
+    if (cudaMemsetAsync(cw.err, 0, sizeof(int) * (1 + (size_t)planes->N), stream) != cudaSuccess)
+        return check_launch("composite reset");
+    trace_begin("comp_coeffs", stream);
+    launch_comp_coeffs(p, planes->d, planes->count, cw, stream);
+    trace_end(stream);
+    if ((st = check_launch("composite coefficients")) != LF_OK) return st;
+    trace_begin("composite_save", stream);
+    launch_composite(p, planes->rgba, planes->count, cw, out, stream, reinterpret_cast<float4*>(state));
+    trace_end(stream);
+    return check_launch("composite (saving form)");
+}
+
+// state: NULL (two walks) or the saving forward's state
+static lf_status composite_backward_impl(const lf_planes* planes, const lf_ref_camera* ref,
+                                         const lf_view_set* views, const float* dviews, const float* state,
+                                         size_t state_bytes, float* dplanes, void* ws, size_t ws_bytes,
+                                         cudaStream_t stream)
 {
     CompWs cw;
     lf_status st = check_composite_args(planes, ref, views, dviews, ws, ws_bytes, &cw);
     if (st != LF_OK) return st;
+    if (state && (st = check_state(ref, views, state, state_bytes)) != LF_OK) return st;
     if (!dplanes) return fail(LF_ERR_INVALID_ARG, "dplanes is NULL");
     if (views->atlas_cols > 0) return fail(LF_ERR_UNSUPPORTED, "the composite adjoint takes separate views only");
     if (((uintptr_t)dviews) % 16 || ((uintptr_t)dplanes) % 16)
@@ -757,10 +802,25 @@ lf_status lf_composite_backward(const lf_planes* planes, const lf_ref_camera* re
     launch_comp_coeffs(p, planes->d, planes->count, cw, stream);
     trace_end(stream);
     if ((st = check_launch("composite coefficients")) != LF_OK) return st;
-    trace_begin("composite_bwd", stream);
-    launch_composite_bwd(p, planes->rgba, planes->count, cw, dviews, dplanes, stream);
+    trace_begin(state ? "composite_bwd_saved" : "composite_bwd", stream);
+    launch_composite_bwd(p, planes->rgba, planes->count, cw, dviews, dplanes, stream,
+                         reinterpret_cast<const float4*>(state));
     trace_end(stream);
     return check_launch("composite backward");
+}
+
+lf_status lf_composite_backward(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
+                                const float* dviews, float* dplanes, void* ws, size_t ws_bytes, cudaStream_t stream)
+{
+    return composite_backward_impl(planes, ref, views, dviews, nullptr, 0, dplanes, ws, ws_bytes, stream);
+}
+
+lf_status lf_composite_backward_saved(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
+                                      const float* dviews, const float* state, size_t state_bytes, float* dplanes,
+                                      void* ws, size_t ws_bytes, cudaStream_t stream)
+{
+    if (!state) return fail(LF_ERR_INVALID_ARG, "state is NULL");
+    return composite_backward_impl(planes, ref, views, dviews, state, state_bytes, dplanes, ws, ws_bytes, stream);
 }
 
 // Common part of the two splat adjoints: argument checks, the forward's

@@ -115,14 +115,25 @@ __device__ __forceinline__ int nearest_index(int P_s, int x, float gm, float hn)
     return P_s * x + (int)f;
 }
 
+// Transmittance carried as m 2^-e (e a multiple of 64) so that no product of
+// many (1 - A) underflows: when m falls below 2^-64 it is scaled up by 2^64.
+constexpr float kUpB = 18446744073709551616.0f;       // 2^64
+constexpr float kDownB = 5.42101086242752217e-20f;    // 2^-64
+constexpr float kBigB = 4294967296.0f;                // 2^32
+__device__ __forceinline__ float scaled_t(float m, int e) { return e == 0 ? m : (e == 64 ? m * kDownB : 0.0f); }
+
+// saving forms: a walk stops once T would fall below this (taken as 0)
+constexpr float kTStop = 5.42101086242752217e-20f;   // 2^-64
 constexpr int kCompBX = 32, kCompBY = 8;
 
 // Unstaged fallback (planes read through L1/L2), used when the staged kernel's
 // shared-memory layout does not fit or rows are not 16-byte aligned.
-template <int DT, bool BILINEAR>
+// SAVE: T carried as m 2^-e and the adjoint's starting state written, as in
+// the staged kernel's saving form.
+template <int DT, bool BILINEAR, bool SAVE = false>
 __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, const void* __restrict__ planes,
                                                                const int32_t* __restrict__ count, CompWs w,
-                                                               float* __restrict__ out)
+                                                               float* __restrict__ out, float4* __restrict__ state)
 {
     extern __shared__ float s_coef[];  // [N][6]: x (gm, hn, hb), y (gm, hn, hb); count in [N] ints after
     int* s_cnt = reinterpret_cast<int*>(s_coef + 6 * p.N);
@@ -146,6 +157,7 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
     if (x >= p.Nx || y >= p.Ny) return;
     const size_t plane_sz = (size_t)p.W * p.H;
     float Q0 = 0.f, Q1 = 0.f, Q2 = 0.f, T = 1.f;
+    int kq = -1;   // saving form: the plane the walk stopped at (blend_texel)
     for (int k = 0; k < p.N; ++k) {
         if (s_cnt[k] == 0) continue;
         const float* c = s_coef + 6 * k;
@@ -181,13 +193,29 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
                 }
             }
         }
-        Q0 = fmaf(T, tx.x, Q0);
-        Q1 = fmaf(T, tx.y, Q1);
-        Q2 = fmaf(T, tx.z, Q2);
-        T = T * (1.0f - tx.w);
+        if (!SAVE) {
+            Q0 = fmaf(T, tx.x, Q0);
+            Q1 = fmaf(T, tx.y, Q1);
+            Q2 = fmaf(T, tx.z, Q2);
+            T = T * (1.0f - tx.w);
+        } else {
+            // the staged saving form's stop rule: T_k frozen at the stop plane
+            Q0 = fmaf(T, tx.x, Q0);
+            Q1 = fmaf(T, tx.y, Q1);
+            Q2 = fmaf(T, tx.z, Q2);
+            const float nt = T * (1.0f - tx.w);
+            if (nt < kTStop) {
+                kq = k;
+                break;
+            }
+            T = nt;
+        }
     }
+    const float Tn = SAVE && kq >= 0 ? 0.0f : T;
     reinterpret_cast<float4*>(out)[view_pixel(p, v, x, y)] =
-        make_float4(fmaf(T, p.bg[0], Q0), fmaf(T, p.bg[1], Q1), fmaf(T, p.bg[2], Q2), 1.0f - T);
+        make_float4(fmaf(Tn, p.bg[0], Q0), fmaf(Tn, p.bg[1], Q1), fmaf(Tn, p.bg[2], Q2), 1.0f - Tn);
+    if (SAVE)
+        state[((size_t)v * p.Ny + y) * p.Nx + x] = make_float4(T, __int_as_float(kq < 0 ? p.N : kq), 0.0f, 0.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -215,70 +243,8 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
 
 constexpr int kStagedWarps = kStagedThreads / 32;     // consumer warps
 constexpr int kStagedBlock = kStagedThreads + 32;     // + one producer warp
-constexpr long long kSpinLimit = 1ll << 26;
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s: a staged wait that long has failed
 constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Waits for the phase with the given parity; gives up (false) after about
-// limit_ns of wall time (the clock is read every 4096 failed tries, from the
-// first such read on) or kSpinLimit tries, whichever comes first. One plain
-// loop: the common case (first try succeeds) costs what an unbounded wait does.
-__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, unsigned long long limit_ns)
-{
-    unsigned long long t0 = 0;
-    for (long long it = 0; it < kSpinLimit; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 4095) == 4095) {
-            const unsigned long long t = global_ns();
-            if (t0 == 0)
-                t0 = t;
-            else if (t - t0 > limit_ns)
-                return false;
-        }
-    }
-    return false;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
-{
-    return mbar_wait_for(bar, parity, kWaitLimitNs);
-}
 
 __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
 {
@@ -429,11 +395,64 @@ __device__ __forceinline__ ThreadGeom thread_geom(const CompParams& p, const Sta
     return t;
 }
 
+// Saving form. A view's walk stops at the first list entry q behind which
+// T would fall below kTStop (0 behind a plane with A = 1): plane q still
+// blends with its T_q, q goes to the thread's stop slot of the view in
+// shared memory (stop_a + 4 jj kStagedThreads), and a[3] = -T_q marks the
+// view as stopped (T_q >= kTStop > 0; T = 0 from there on, the colour the
+// plain form would still add being below 2^-64 per plane). The kernel
+// stores the state at the end of its walk.
+// store q to view J's stop slot ([stop_a + immediate]: no address register
+// per view)
+template <int J>
+__device__ __forceinline__ void st_stop(uint32_t stop_a, int q, bool on)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.shared.u32 [%0+%3], %1;\n\t}"
+                 ::"r"(stop_a), "r"(q), "r"((uint32_t)on), "n"(4 * J * kStagedThreads));
+}
+
+template <bool SAVE>
+__device__ __forceinline__ void blend_texel(float (&a)[4], float4 t, uint32_t stop_a, int jj, int q)
+{
+    if (!SAVE) {
+        const float T = a[3];
+        a[0] = fmaf(T, t.x, a[0]);
+        a[1] = fmaf(T, t.y, a[1]);
+        a[2] = fmaf(T, t.z, a[2]);
+        a[3] = fmaf(-T, t.w, T);
+    } else {
+        const float T = fmaxf(a[3], 0.0f);
+        a[0] = fmaf(T, t.x, a[0]);
+        a[1] = fmaf(T, t.y, a[1]);
+        a[2] = fmaf(T, t.z, a[2]);
+        const float nt = fmaf(-T, t.w, T);
+        const bool stop = a[3] > 0.0f && nt < kTStop;   // branch-free: a predicated store
+        switch (jj) {   // jj is a constant in every (unrolled) caller
+        case 0: st_stop<0>(stop_a, q, stop); break;
+        case 1: st_stop<1>(stop_a, q, stop); break;
+        case 2: st_stop<2>(stop_a, q, stop); break;
+        case 3: st_stop<3>(stop_a, q, stop); break;
+        case 4: st_stop<4>(stop_a, q, stop); break;
+        case 5: st_stop<5>(stop_a, q, stop); break;
+        case 6: st_stop<6>(stop_a, q, stop); break;
+        case 7: st_stop<7>(stop_a, q, stop); break;
+        case 8: st_stop<8>(stop_a, q, stop); break;
+        case 9: st_stop<9>(stop_a, q, stop); break;
+        case 10: st_stop<10>(stop_a, q, stop); break;
+        case 11: st_stop<11>(stop_a, q, stop); break;
+        case 12: st_stop<12>(stop_a, q, stop); break;
+        case 13: st_stop<13>(stop_a, q, stop); break;
+        default: st_stop<14>(stop_a, q, stop); break;
+        }
+        a[3] = stop ? -T : (a[3] > 0.0f ? nt : a[3]);
+    }
+}
+
 // hdr: (gm_x, gm_y, h_y, -); ca: shared address of the plane's coefficient
 // block; sb: shared address of the stage holding the plane's rows
-template <int DT, bool BILINEAR, int VG, bool CLAMP>
+template <int DT, bool BILINEAR, int VG, bool CLAMP, bool SAVE = false>
 __device__ __forceinline__ void blend_plane(float (&acc)[VG][4], float4 hdr, uint32_t ca, uint32_t sb,
-                                            const ThreadGeom& tg)
+                                            const ThreadGeom& tg, uint32_t stop_a, int q)
 {
     using TX_ = Texel<DT>;
     const uint32_t maxi = tg.maxi;
@@ -460,7 +479,7 @@ __device__ __forceinline__ void blend_plane(float (&acc)[VG][4], float4 hdr, uin
         for (int jj = 0; jj < VG; ++jj) {
             const int ix = __float_as_int(floor_magic<CLAMP>(gmx, xf, c[3 + jj])) + base_x;
             const float T = acc[jj][3];
-            if constexpr (DT == LF_U8) {
+            if constexpr (DT == LF_U8 && !SAVE) {
                 // colour bytes scale by 1/255 through T (one multiply per
                 // texel instead of three); alpha keeps A = byte / 255
                 constexpr float s = 1.0f / 255.0f;
@@ -472,10 +491,7 @@ __device__ __forceinline__ void blend_plane(float (&acc)[VG][4], float4 hdr, uin
                 acc[jj][3] = fmaf(-T, u8_byte<3>(u) * s, T);
             } else {
                 const float4 t = TX_::load(row, min((uint32_t)ix, maxi));
-                acc[jj][0] = fmaf(T, t.x, acc[jj][0]);
-                acc[jj][1] = fmaf(T, t.y, acc[jj][1]);
-                acc[jj][2] = fmaf(T, t.z, acc[jj][2]);
-                acc[jj][3] = fmaf(-T, t.w, T);
+                blend_texel<SAVE>(acc[jj], t, stop_a, jj, q);
             }
         }
     } else {
@@ -512,20 +528,16 @@ __device__ __forceinline__ void blend_plane(float (&acc)[VG][4], float4 hdr, uin
                 t.z = fmaf(w1, fmaf(wa, ta.z, wx * tb.z), t.z);
                 t.w = fmaf(w1, fmaf(wa, ta.w, wx * tb.w), t.w);
             }
-            const float T = acc[jj][3];
-            acc[jj][0] = fmaf(T, t.x, acc[jj][0]);
-            acc[jj][1] = fmaf(T, t.y, acc[jj][1]);
-            acc[jj][2] = fmaf(T, t.z, acc[jj][2]);
-            acc[jj][3] = fmaf(-T, t.w, T);
+            blend_texel<SAVE>(acc[jj], t, stop_a, jj, q);
         }
     }
 }
 
 // Bilinear horizontal taps from a vertically pre-blended FP32 row (shared
 // address ba, same texel layout as a staged row).
-template <int VG, bool CLAMP>
+template <int VG, bool CLAMP, bool SAVE = false>
 __device__ __forceinline__ void blend_blended_row(float (&acc)[VG][4], float4 hdr, uint32_t ca, uint32_t ba,
-                                                  const ThreadGeom& tg)
+                                                  const ThreadGeom& tg, uint32_t stop_a, int q)
 {
     float c[4 * ((VG + 3) / 4)];
 #pragma unroll
@@ -545,23 +557,22 @@ __device__ __forceinline__ void blend_blended_row(float (&acc)[VG][4], float4 hd
         const int i0 = __float_as_int(tm) + tg.base_x;
         const uint32_t a0 = min((uint32_t)i0, tg.maxi), a1 = min((uint32_t)(i0 + 1), tg.maxi);
         const float4 ta = lds_f4(ba + a0 * 16u), tb = lds_f4(ba + a1 * 16u);
-        const float T = acc[jj][3];
-        acc[jj][0] = fmaf(T, fmaf(wa, ta.x, wx * tb.x), acc[jj][0]);
-        acc[jj][1] = fmaf(T, fmaf(wa, ta.y, wx * tb.y), acc[jj][1]);
-        acc[jj][2] = fmaf(T, fmaf(wa, ta.z, wx * tb.z), acc[jj][2]);
-        acc[jj][3] = fmaf(-T, fmaf(wa, ta.w, wx * tb.w), T);
+        const float4 t = make_float4(fmaf(wa, ta.x, wx * tb.x), fmaf(wa, ta.y, wx * tb.y), fmaf(wa, ta.z, wx * tb.z),
+                                     fmaf(wa, ta.w, wx * tb.w));
+        blend_texel<SAVE>(acc[jj], t, stop_a, jj, q);
     }
 }
 
 // Every view of this thread has T == 0 exactly (or the thread is idle).
 // T never leaves 0 (T <- T - T A), and behind it a plane adds T c = 0 to Q
 // and leaves T = 0, so skipping such planes changes no bit of the output.
-template <int VG>
+// (Saving form: every view has stopped, a[3] < 0.)
+template <int VG, bool SAVE = false>
 __device__ __forceinline__ bool saturated(const float (&acc)[VG][4], bool live)
 {
     bool s = true;
 #pragma unroll
-    for (int jj = 0; jj < VG; ++jj) s = s && acc[jj][3] == 0.0f;
+    for (int jj = 0; jj < VG; ++jj) s = s && (SAVE ? acc[jj][3] < 0.0f : acc[jj][3] == 0.0f);
     return s || !live;
 }
 
@@ -654,15 +665,22 @@ __device__ __forceinline__ void zero_pads(const CompParams& p, const StagedGeom&
     }
 }
 
-template <int DT, bool BILINEAR, int VG>
+// SAVE: also writes, per view pixel, the state the adjoint's back-to-front
+// walk starts from, state[(v Ny + y) Nx + x] = {T_k, bits of k, 0, 0}: k the
+// plane behind which T falls below 2^-64 (and is taken as 0), T_k the
+// transmittance in front of it; or k = N and the transmittance behind the
+// last plane (see blend_texel).
+template <int DT, bool BILINEAR, int VG, bool SAVE = false>
 __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_composite_staged(CompParams p, StagedGeom G,
                                                                         const char* __restrict__ planes,
                                                                         const int32_t* __restrict__ count, CompWs w,
-                                                                        float* __restrict__ out)
+                                                                        float* __restrict__ out,
+                                                                        float4* __restrict__ state)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     // [stages][rows][row_bytes] | bilinear: [2][BY][row_texels] float4 |
-    // full[kStages] | empty[kStages] | coef [N][CW] | plist [N]
+    // full[kStages] | empty[kStages] | coef [N][CW] | plist [N] | saving
+    // form: stop slots [VG][kStagedThreads]
     constexpr int CW = CoefBlock<VG>::kFloats;
     unsigned char* stage_base = smem;
     // bilinear: the two staged rows of an output row are blended vertically
@@ -738,6 +756,8 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_com
     float acc[VG][4];
 #pragma unroll
     for (int jj = 0; jj < VG; ++jj) acc[jj][0] = acc[jj][1] = acc[jj][2] = 0.f, acc[jj][3] = 1.f;
+    // saving form: the stop slots [VG][kStagedThreads] follow plist
+    const uint32_t stop_a = smem_addr(plist + p.N) + 4u * (uint32_t)tid;
     const uint32_t stage_a = smem_addr(stage_base), coef_a = smem_addr(coef);
     const bool live = ty < G.BY && x < p.Nx && y < p.Ny;   // threads past BY rows idle
     const ThreadGeom tg = thread_geom(p, G, x, y, ty);
@@ -753,7 +773,7 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_com
             // bilinear: keep meeting the per-plane CTA barrier (results discarded)
             if (!BILINEAR) break;
         }
-        if ((q & 3) == 0 && q > 0 && !warp_sat) warp_sat = __all_sync(0xffffffffu, saturated<VG>(acc, live));
+        if ((q & 3) == 0 && q > 0 && !warp_sat) warp_sat = __all_sync(0xffffffffu, saturated<VG, SAVE>(acc, live));
         if constexpr (BILINEAR) {
             // the threads of an output row blend interior texels tx, tx + TX,
             // ... of its two staged rows into the FP32 row buffer
@@ -790,9 +810,9 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_com
             if (live && !warp_sat) {
                 const uint32_t ba = smem_addr(brow);
                 if (__float_as_int(hdr.w))
-                    blend_blended_row<VG, true>(acc, hdr, ca, ba, tg);
+                    blend_blended_row<VG, true, SAVE>(acc, hdr, ca, ba, tg, stop_a, q);
                 else
-                    blend_blended_row<VG, false>(acc, hdr, ca, ba, tg);
+                    blend_blended_row<VG, false, SAVE>(acc, hdr, ca, ba, tg, stop_a, q);
             }
         } else {
             if (live && !warp_sat) {
@@ -800,9 +820,9 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_com
                 const uint32_t sb = stage_a + (uint32_t)(s * G.stage_bytes);
                 const float4 hdr = lds_f4(ca);
                 if (__float_as_int(hdr.w))
-                    blend_plane<DT, BILINEAR, VG, true>(acc, hdr, ca, sb, tg);
+                    blend_plane<DT, BILINEAR, VG, true, SAVE>(acc, hdr, ca, sb, tg, stop_a, q);
                 else
-                    blend_plane<DT, BILINEAR, VG, false>(acc, hdr, ca, sb, tg);
+                    blend_plane<DT, BILINEAR, VG, false, SAVE>(acc, hdr, ca, sb, tg, stop_a, q);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
@@ -814,9 +834,16 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_com
         const int j = j0 + jj;
         if (j >= p.Vx) break;
         const int v = vi * p.Vx + j;
-        const float T = acc[jj][3];
+        const float T = SAVE ? fmaxf(acc[jj][3], 0.0f) : acc[jj][3];
         reinterpret_cast<float4*>(out)[view_pixel(p, v, x, y)] = make_float4(
             fmaf(T, p.bg[0], acc[jj][0]), fmaf(T, p.bg[1], acc[jj][1]), fmaf(T, p.bg[2], acc[jj][2]), 1.0f - T);
+        if (SAVE) {
+            // stopped: {T_k, k} of the stop plane; else {T behind the last plane, N}
+            const bool stopped = acc[jj][3] < 0.0f;
+            const int k = stopped ? plist[lds_u32(stop_a + 4u * (uint32_t)(jj * kStagedThreads))] : p.N;
+            state[((size_t)v * p.Ny + y) * p.Nx + x] =
+                make_float4(fabsf(acc[jj][3]), __int_as_float(k), 0.0f, 0.0f);
+        }
     }
 }
 
@@ -921,6 +948,7 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_com
             const bool live = ty < G.BY && x < p.Nx && y < p.Ny;
             const ThreadGeom tg = thread_geom(p, G, x, y, ty);
             float acc[VG][4];
+            const uint32_t stop_a = 0;   // unused: the batch blends in the plain form
 #pragma unroll
             for (int jj = 0; jj < VG; ++jj) acc[jj][0] = acc[jj][1] = acc[jj][2] = 0.f, acc[jj][3] = 1.f;
             bool ok = true;
@@ -942,9 +970,9 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_com
                     const uint32_t sb = stage_a + (uint32_t)st * stage_stride;
                     const float4 hdr = lds_f4(ca);
                     if (__float_as_int(hdr.w))
-                        blend_plane<DT, BILINEAR, VG, true>(acc, hdr, ca, sb, tg);
+                        blend_plane<DT, BILINEAR, VG, true>(acc, hdr, ca, sb, tg, stop_a, q);
                     else
-                        blend_plane<DT, BILINEAR, VG, false>(acc, hdr, ca, sb, tg);
+                        blend_plane<DT, BILINEAR, VG, false>(acc, hdr, ca, sb, tg, stop_a, q);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_addr(&empty[st]));
@@ -984,21 +1012,22 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_com
     }
 }
 
-template <int DT, bool BILINEAR, int VG>
+template <int DT, bool BILINEAR, int VG, bool SAVE = false>
 bool launch_staged_vg(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
-                      cudaStream_t s)
+                      cudaStream_t s, float4* state = nullptr)
 {
     constexpr int TB = Texel<DT>::kBytes;
-    const StagedGeom G = staged_geom(p, TB, BILINEAR, VG, 512);
+    StagedGeom G = staged_geom(p, TB, BILINEAR, VG, 512);
+    if (SAVE) G.smem_bytes += sizeof(int) * (size_t)VG * kStagedThreads;   // stop slots
     if (G.smem_bytes > 200 * 1024) return false;
     // bulk copies need 16-byte aligned rows: plane base and row pitch
     if (((uintptr_t)planes) % 16 != 0 || ((size_t)p.W * TB) % 16 != 0) return false;
-    auto kern = k_composite_staged<DT, BILINEAR, VG>;
+    auto kern = k_composite_staged<DT, BILINEAR, VG, SAVE>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem_bytes) != cudaSuccess)
         return false;
     const dim3 grid((unsigned)(G.groups_x * p.Vy), (unsigned)((p.Ny + G.BY - 1) / G.BY),
                     (unsigned)((p.Nx + G.TX - 1) / G.TX));
-    kern<<<grid, kStagedBlock, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, out);
+    kern<<<grid, kStagedBlock, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, out, state);
     note_launches(1);
     return true;
 }
@@ -1011,54 +1040,59 @@ bool launch_staged_vg(const CompParams& p, const void* planes, const int32_t* co
 // FP32 (four-channel FP32 taps) spills more, so it skips 9. Measured on 45
 // views of 512^2, N 64: 15 beats 9 by 4 % (FP32) to 8 % (FP16) nearest and
 // 7-15 % bilinear.
-inline int staged_views_per_thread(int Vx, bool no9)
+// The saving form (two more live words per view) takes 5 at most: wider
+// groups spill.
+inline int staged_views_per_thread(int Vx, bool no9, int max_vg = 15)
 {
     int best = 3;
     long long best_cost = -1;
     for (int vg : {15, 9, 5, 3}) {
-        if ((vg > Vx && vg != 3) || (no9 && vg == 9)) continue;
+        if ((vg > Vx && vg != 3) || (no9 && vg == 9) || vg > max_vg) continue;
         const long long cost = (long long)((Vx + vg - 1) / vg) * (vg + 3);
         if (best_cost < 0 || cost < best_cost) best_cost = cost, best = vg;
     }
     return best;
 }
 
-template <int DT, bool BILINEAR>
+template <int DT, bool BILINEAR, bool SAVE>
 bool launch_staged(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
-                   cudaStream_t s)
+                   cudaStream_t s, float4* state)
 {
     switch (staged_views_per_thread(p.Vx, BILINEAR && DT == LF_F32)) {
-    case 15: return launch_staged_vg<DT, BILINEAR, 15>(p, planes, count, ws, out, s);
-    case 9: return launch_staged_vg<DT, BILINEAR, 9>(p, planes, count, ws, out, s);
-    case 5: return launch_staged_vg<DT, BILINEAR, 5>(p, planes, count, ws, out, s);
-    default: return launch_staged_vg<DT, BILINEAR, 3>(p, planes, count, ws, out, s);
+    case 15: return launch_staged_vg<DT, BILINEAR, 15, SAVE>(p, planes, count, ws, out, s, state);
+    case 9: return launch_staged_vg<DT, BILINEAR, 9, SAVE>(p, planes, count, ws, out, s, state);
+    case 5: return launch_staged_vg<DT, BILINEAR, 5, SAVE>(p, planes, count, ws, out, s, state);
+    default: return launch_staged_vg<DT, BILINEAR, 3, SAVE>(p, planes, count, ws, out, s, state);
     }
 }
 
-template <int DT>
-void launch_composite_t(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
-                        cudaStream_t s)
+template <int DT, bool BILINEAR, bool SAVE>
+void launch_unstaged(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
+                     cudaStream_t s, float4* state)
 {
-    if (p.N <= 4096) {
-        const bool ok = p.bilinear ? launch_staged<DT, true>(p, planes, count, ws, out, s)
-                                   : launch_staged<DT, false>(p, planes, count, ws, out, s);
-        if (ok) return;
-    }
     const dim3 block(kCompBX, kCompBY);
     const dim3 grid((unsigned)(p.Vx * p.Vy), (unsigned)((p.Nx + kCompBX - 1) / kCompBX),
                     (unsigned)((p.Ny + kCompBY - 1) / kCompBY));
     const size_t smem = sizeof(float) * 6 * p.N + sizeof(int) * p.N;
-    if (p.bilinear) {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_composite<DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_composite<DT, true><<<grid, block, smem, s>>>(p, planes, count, ws, out);
-        note_launches(1);
-    } else {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_composite<DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_composite<DT, false><<<grid, block, smem, s>>>(p, planes, count, ws, out);
-        note_launches(1);
+    auto kern = k_composite<DT, BILINEAR, SAVE>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, block, smem, s>>>(p, planes, count, ws, out, state);
+    note_launches(1);
+}
+
+template <int DT, bool SAVE>
+void launch_composite_t(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
+                        cudaStream_t s, float4* state)
+{
+    if (p.N <= 4096) {
+        const bool ok = p.bilinear ? launch_staged<DT, true, SAVE>(p, planes, count, ws, out, s, state)
+                                   : launch_staged<DT, false, SAVE>(p, planes, count, ws, out, s, state);
+        if (ok) return;
     }
+    if (p.bilinear)
+        launch_unstaged<DT, true, SAVE>(p, planes, count, ws, out, s, state);
+    else
+        launch_unstaged<DT, false, SAVE>(p, planes, count, ws, out, s, state);
 }
 
 // ---------------------------------------------------------------------------
@@ -1073,20 +1107,22 @@ void launch_composite_t(const CompParams& p, const void* planes, const int32_t* 
 // can be exactly 1 (T_{k+1} = 0); the forward walk keeps T before the first
 // such plane, and every plane behind it gets T = 0. The texel gradients are
 // scattered with FP32 vector atomics into dplanes (nearest: the sampled
-// texel; bilinear: the in-plane taps with their weights). Per-chunk
-// transmittance is recomputed, never stored.
+// texel; bilinear: the in-plane taps with their weights). The adjoint either
+// recomputes the far-end transmittance with a front-to-back walk of its own,
+// or starts from the 16 bytes per view pixel (m, e, first opaque plane) that
+// the saving forward composite wrote, and walks the planes once.
 // ---------------------------------------------------------------------------
 
 constexpr int kBwdViews = 3;                          // views per thread of the staged adjoint
-constexpr float kUpB = 18446744073709551616.0f;       // 2^64
-constexpr float kDownB = 5.42101086242752217e-20f;    // 2^-64
-constexpr float kBigB = 4294967296.0f;                // 2^32
 
-template <int DT, bool BILINEAR>
+// FS: the front-to-back walk is skipped and the pixel's transmittance taken
+// from the state the saving forward wrote (as the staged adjoint's FS form).
+template <int DT, bool BILINEAR, bool FS = false>
 __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite_bwd(CompParams p, const void* __restrict__ planes,
                                                                    const int32_t* __restrict__ count, CompWs w,
                                                                    const float4* __restrict__ dviews,
-                                                                   float4* __restrict__ dplanes)
+                                                                   float4* __restrict__ dplanes,
+                                                                   const float4* __restrict__ state)
 {
     extern __shared__ float s_coef[];  // as k_composite
     int* s_cnt = reinterpret_cast<int*>(s_coef + 6 * p.N);
@@ -1163,7 +1199,17 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite_bwd(CompParams p
 
     float Tm = 1.f, oTm = 0.f;
     int Te = 0, oTe = 0, ok = -1;
-    for (int k = 0; k < p.N; ++k) {
+    if (FS) {
+        // state {T_k, k}: T in front of plane k, 0 behind it; k = N: T
+        // behind the last plane
+        const float4 sv = state[((size_t)v * p.Ny + y) * p.Nx + x];
+        const int kq = __float_as_int(sv.y);
+        if (kq < p.N)
+            Tm = 0.f, oTm = sv.x, ok = kq;
+        else
+            Tm = sv.x;
+    }
+    for (int k = 0; k < (FS ? 0 : p.N); ++k) {
         if (s_cnt[k] == 0) continue;
         const float4 tx = sample(k, taps(k));
         const float oma = 1.0f - tx.w;
@@ -1248,15 +1294,19 @@ __device__ __forceinline__ float texel_alpha<LF_U8>(uint32_t row, uint32_t i)
 }
 
 // T = m 2^-e (e a multiple of 64): m, m 2^-64, or below 2^-96 (taken as 0)
-__device__ __forceinline__ float scaled_t(float m, int e) { return e == 0 ? m : (e == 64 ? m * kDownB : 0.0f); }
 
-template <int DT, bool BILINEAR, int VG>
+// FS (from state): the front-to-back walk is skipped; each view pixel's
+// transmittance behind the last plane, or in front of the first opaque one,
+// comes from the state the saving forward composite wrote, and the ring
+// carries only the back-to-front planes.
+template <int DT, bool BILINEAR, int VG, bool FS = false>
 __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_bwd_staged(CompParams p, StagedGeom G,
                                                                             const char* __restrict__ planes,
                                                                             const int32_t* __restrict__ count,
                                                                             CompWs w,
                                                                             const float4* __restrict__ dviews,
-                                                                            float4* __restrict__ dplanes)
+                                                                            float4* __restrict__ dplanes,
+                                                                            const float4* __restrict__ state)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     // [kStages][rows][row_bytes] | full[kStages] | empty[kStages] | coef [N][CW] | plist [N]
@@ -1295,15 +1345,19 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_bwd_staged(CompPa
     }
     __syncthreads();
     const int P = s_nplanes;
-    // ring slot q < P holds list entry q, slot q >= P list entry 2P - 1 - q
+    // walk step q < P visits list entry q, step q >= P list entry 2P - 1 - q;
+    // step q uses ring position r = q - q0 (q0 = P when the first walk is
+    // skipped)
     auto entry = [&](int q) { return q < P ? q : 2 * P - 1 - q; };
+    const int q0 = FS ? P : 0;
 
     if (tid >= kStagedThreads) {
         if (tid == kStagedThreads) {
-            for (int q = 0; q < 2 * P; ++q) {
-                const int st = q % kStages;
-                if (q >= kStages &&
-                    !mbar_wait_bounded(smem_addr(&empty[st]), (uint32_t)(((q / kStages) - 1) & 1))) {
+            for (int q = q0; q < 2 * P; ++q) {
+                const int r = q - q0;
+                const int st = r % kStages;
+                if (r >= kStages &&
+                    !mbar_wait_bounded(smem_addr(&empty[st]), (uint32_t)(((r / kStages) - 1) & 1))) {
                     atomicExch(w.err, 1);
                     break;
                 }
@@ -1347,11 +1401,25 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_bwd_staged(CompPa
     int Te[VG], oTe[VG], okq[VG];
 #pragma unroll
     for (int jj = 0; jj < VG; ++jj) Tm[jj] = 1.f, oTm[jj] = 0.f, Te[jj] = 0, oTe[jj] = 0, okq[jj] = -1;
-    int q = 0;
+    if (FS && live) {
+        // state {T_k, k}: T in front of plane k, 0 behind it (the saving
+        // forward stopped there); k = N: T behind the last plane
+#pragma unroll
+        for (int jj = 0; jj < VG; ++jj) {
+            if (j0 + jj >= p.Vx) break;
+            const float4 sv = state[((size_t)(vi * p.Vx + j0 + jj) * p.Ny + y) * p.Nx + x];
+            const int kq = __float_as_int(sv.y);
+            if (kq < p.N)
+                Tm[jj] = 0.f, oTm[jj] = sv.x, okq[jj] = kq;
+            else
+                Tm[jj] = sv.x;
+        }
+    }
+    int q = q0;
     // front to back: transmittance at the far end, and T before the first
     // opaque plane (alpha only)
     for (; q < P; ++q) {
-        const int st = q % kStages;
+        const int st = q % kStages;   // q0 == 0 here
         if (!mbar_wait_bounded(smem_addr(&full[st]), (uint32_t)((q / kStages) & 1))) {
             atomicExch(w.err, 1);
             return;
@@ -1382,19 +1450,21 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_bwd_staged(CompPa
                 if (!BILINEAR) {
                     if (rv && (uint32_t)ip - padl < Wu) a = texel_alpha<DT>(sb, (uint32_t)ip);
                 } else {
+                    // vertical pair first, then the horizontal pair: the
+                    // forward's rounding order (its blended rows)
                     const bool c0 = (uint32_t)ip - padl < Wu, c1 = (uint32_t)ip + 1u - padl < Wu;
                     const float wa = 1.0f - wx;
+                    float u0 = 0.f, u1 = 0.f;
                     if (w0 != 0.0f) {
-                        const float a0 = c0 ? texel_alpha<DT>(sb, (uint32_t)ip) : 0.f;
-                        const float a1 = c1 ? texel_alpha<DT>(sb, (uint32_t)ip + 1u) : 0.f;
-                        a = w0 * fmaf(wa, a0, wx * a1);
+                        u0 = w0 * (c0 ? texel_alpha<DT>(sb, (uint32_t)ip) : 0.f);
+                        u1 = w0 * (c1 ? texel_alpha<DT>(sb, (uint32_t)ip + 1u) : 0.f);
                     }
                     if (w1 != 0.0f) {
                         const uint32_t r1 = sb + tg.row_bytes;
-                        const float a0 = c0 ? texel_alpha<DT>(r1, (uint32_t)ip) : 0.f;
-                        const float a1 = c1 ? texel_alpha<DT>(r1, (uint32_t)ip + 1u) : 0.f;
-                        a = fmaf(w1, fmaf(wa, a0, wx * a1), a);
+                        u0 = fmaf(w1, c0 ? texel_alpha<DT>(r1, (uint32_t)ip) : 0.f, u0);
+                        u1 = fmaf(w1, c1 ? texel_alpha<DT>(r1, (uint32_t)ip + 1u) : 0.f, u1);
                     }
+                    a = fmaf(wa, u0, wx * u1);
                 }
                 const float oma = 1.0f - a;
                 if (!(oma > 0.0f) && Tm[jj] > 0.0f && okq[jj] < 0) {
@@ -1422,8 +1492,9 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_bwd_staged(CompPa
     }
     // back to front: T recovered by division, texel gradients, B recurrence
     for (; q < 2 * P; ++q) {
-        const int st = q % kStages;
-        if (!mbar_wait_bounded(smem_addr(&full[st]), (uint32_t)((q / kStages) & 1))) {
+        const int r = q - q0;
+        const int st = r % kStages;
+        if (!mbar_wait_bounded(smem_addr(&full[st]), (uint32_t)((r / kStages) & 1))) {
             atomicExch(w.err, 1);
             return;
         }
@@ -1460,26 +1531,30 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_bwd_staged(CompPa
                 if (!BILINEAR) {
                     if (rv && c0) t = TX_::load(sb, (uint32_t)ip);
                 } else {
+                    // vertical pairs first (u0 at column ip, u1 at ip + 1),
+                    // then the horizontal pair: the forward's rounding order
+                    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 u0 = z, u1 = z;
                     if (w0 != 0.0f) {
-                        const float4 t0 = c0 ? TX_::load(sb, (uint32_t)ip) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        const float4 t1 = c1 ? TX_::load(sb, (uint32_t)ip + 1u) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        t.x = w0 * fmaf(wa, t0.x, wx * t1.x);
-                        t.y = w0 * fmaf(wa, t0.y, wx * t1.y);
-                        t.z = w0 * fmaf(wa, t0.z, wx * t1.z);
-                        t.w = w0 * fmaf(wa, t0.w, wx * t1.w);
+                        const float4 t0 = c0 ? TX_::load(sb, (uint32_t)ip) : z;
+                        const float4 t1 = c1 ? TX_::load(sb, (uint32_t)ip + 1u) : z;
+                        u0 = make_float4(w0 * t0.x, w0 * t0.y, w0 * t0.z, w0 * t0.w);
+                        u1 = make_float4(w0 * t1.x, w0 * t1.y, w0 * t1.z, w0 * t1.w);
                     }
                     if (w1 != 0.0f) {
                         const uint32_t r1 = sb + tg.row_bytes;
-                        const float4 t0 = c0 ? TX_::load(r1, (uint32_t)ip) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        const float4 t1 = c1 ? TX_::load(r1, (uint32_t)ip + 1u) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        t.x = fmaf(w1, fmaf(wa, t0.x, wx * t1.x), t.x);
-                        t.y = fmaf(w1, fmaf(wa, t0.y, wx * t1.y), t.y);
-                        t.z = fmaf(w1, fmaf(wa, t0.z, wx * t1.z), t.z);
-                        t.w = fmaf(w1, fmaf(wa, t0.w, wx * t1.w), t.w);
+                        const float4 t0 = c0 ? TX_::load(r1, (uint32_t)ip) : z;
+                        const float4 t1 = c1 ? TX_::load(r1, (uint32_t)ip + 1u) : z;
+                        u0 = make_float4(fmaf(w1, t0.x, u0.x), fmaf(w1, t0.y, u0.y), fmaf(w1, t0.z, u0.z),
+                                         fmaf(w1, t0.w, u0.w));
+                        u1 = make_float4(fmaf(w1, t1.x, u1.x), fmaf(w1, t1.y, u1.y), fmaf(w1, t1.z, u1.z),
+                                         fmaf(w1, t1.w, u1.w));
                     }
+                    t = make_float4(fmaf(wa, u0.x, wx * u1.x), fmaf(wa, u0.y, wx * u1.y), fmaf(wa, u0.z, wx * u1.z),
+                                    fmaf(wa, u0.w, wx * u1.w));
                 }
                 const float oma = 1.0f - t.w;
-                if (e == okq[jj]) {
+                if ((FS ? plist[e] : e) == okq[jj]) {
                     Tm[jj] = oTm[jj];
                     Te[jj] = oTe[jj];
                 } else if (oma > 0.0f) {
@@ -1512,9 +1587,9 @@ __global__ void __launch_bounds__(kStagedBlock, 2) k_composite_bwd_staged(CompPa
     }
 }
 
-template <int DT, bool BILINEAR, int VG>
+template <int DT, bool BILINEAR, int VG, bool FS = false>
 bool launch_bwd_staged_vg(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
-                          const float4* dviews, float4* dplanes, cudaStream_t s)
+                          const float4* dviews, float4* dplanes, cudaStream_t s, const float4* state = nullptr)
 {
     constexpr int TB = Texel<DT>::kBytes;
     StagedGeom G = staged_geom(p, TB, BILINEAR, VG, 512);
@@ -1525,12 +1600,13 @@ bool launch_bwd_staged_vg(const CompParams& p, const void* planes, const int32_t
                    sizeof(int) * (size_t)p.N;
     if (G.smem_bytes > 200 * 1024) return false;
     if (((uintptr_t)planes) % 16 != 0 || ((size_t)p.W * TB) % 16 != 0) return false;
-    auto kern = k_composite_bwd_staged<DT, BILINEAR, VG>;
+    auto kern = k_composite_bwd_staged<DT, BILINEAR, VG, FS>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem_bytes) != cudaSuccess)
         return false;
     const dim3 grid((unsigned)(G.groups_x * p.Vy), (unsigned)((p.Ny + G.BY - 1) / G.BY),
                     (unsigned)((p.Nx + G.TX - 1) / G.TX));
-    kern<<<grid, kStagedBlock, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, dviews, dplanes);
+    kern<<<grid, kStagedBlock, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, dviews, dplanes,
+                                                  state);
     note_launches(1);
     return true;
 }
@@ -1548,9 +1624,9 @@ __global__ void k_wait_selftest(unsigned long long limit_ns, int* result)
     *result = mbar_wait_for(b, 0u, limit_ns) ? 2 : 1;
 }
 
-template <int DT>
+template <int DT, bool FS>
 void launch_composite_bwd_t(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
-                            const float* dviews, float* dplanes, cudaStream_t s)
+                            const float* dviews, float* dplanes, cudaStream_t s, const float4* state)
 {
     const dim3 block(kCompBX, kCompBY);
     const dim3 grid((unsigned)(p.Vx * p.Vy), (unsigned)((p.Nx + kCompBX - 1) / kCompBX),
@@ -1559,19 +1635,14 @@ void launch_composite_bwd_t(const CompParams& p, const void* planes, const int32
     const float4* dv = reinterpret_cast<const float4*>(dviews);
     float4* dp = reinterpret_cast<float4*>(dplanes);
     if (p.N <= 4096) {
-        const bool ok = p.bilinear ? launch_bwd_staged_vg<DT, true, kBwdViews>(p, planes, count, ws, dv, dp, s)
-                                   : launch_bwd_staged_vg<DT, false, kBwdViews>(p, planes, count, ws, dv, dp, s);
+        const bool ok = p.bilinear
+                            ? launch_bwd_staged_vg<DT, true, kBwdViews, FS>(p, planes, count, ws, dv, dp, s, state)
+                            : launch_bwd_staged_vg<DT, false, kBwdViews, FS>(p, planes, count, ws, dv, dp, s, state);
         if (ok) return;
     }
-    if (p.bilinear) {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_composite_bwd<DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_composite_bwd<DT, true><<<grid, block, smem, s>>>(p, planes, count, ws, dv, dp);
-    } else {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_composite_bwd<DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_composite_bwd<DT, false><<<grid, block, smem, s>>>(p, planes, count, ws, dv, dp);
-    }
+    auto kern = p.bilinear ? k_composite_bwd<DT, true, FS> : k_composite_bwd<DT, false, FS>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, block, smem, s>>>(p, planes, count, ws, dv, dp, state);
     note_launches(1);
 }
 
@@ -1680,16 +1751,25 @@ void launch_wait_selftest(unsigned long long limit_ns, int* result, cudaStream_t
     note_launches(1);
 }
 
-void launch_composite_bwd(
-const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
-                          const float* dviews, float* dplanes, cudaStream_t s)
+template <bool FS>
+void launch_composite_bwd_dt(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
+                             const float* dviews, float* dplanes, const float4* state, cudaStream_t s)
 {
     switch (p.dtype) {
-    case LF_F32: launch_composite_bwd_t<LF_F32>(p, planes, count, ws, dviews, dplanes, s); break;
-    case LF_F16: launch_composite_bwd_t<LF_F16>(p, planes, count, ws, dviews, dplanes, s); break;
-    case LF_U8: launch_composite_bwd_t<LF_U8>(p, planes, count, ws, dviews, dplanes, s); break;
-    default: launch_composite_bwd_t<LF_BF16>(p, planes, count, ws, dviews, dplanes, s); break;
+    case LF_F32: launch_composite_bwd_t<LF_F32, FS>(p, planes, count, ws, dviews, dplanes, s, state); break;
+    case LF_F16: launch_composite_bwd_t<LF_F16, FS>(p, planes, count, ws, dviews, dplanes, s, state); break;
+    case LF_U8: launch_composite_bwd_t<LF_U8, FS>(p, planes, count, ws, dviews, dplanes, s, state); break;
+    default: launch_composite_bwd_t<LF_BF16, FS>(p, planes, count, ws, dviews, dplanes, s, state); break;
     }
+}
+
+void launch_composite_bwd(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
+                          const float* dviews, float* dplanes, cudaStream_t s, const float4* state)
+{
+    if (state)
+        launch_composite_bwd_dt<true>(p, planes, count, ws, dviews, dplanes, state, s);
+    else
+        launch_composite_bwd_dt<false>(p, planes, count, ws, dviews, dplanes, nullptr, s);
 }
 
 void launch_comp_coeffs(const CompParams& p, const double* d, const int32_t* count, const CompWs& ws, cudaStream_t s)
@@ -1699,15 +1779,25 @@ void launch_comp_coeffs(const CompParams& p, const double* d, const int32_t* cou
     note_launches(1);
 }
 
-void launch_composite(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
-                      cudaStream_t s)
+template <bool SAVE>
+void launch_composite_dt(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
+                         float4* state, cudaStream_t s)
 {
     switch (p.dtype) {
-    case LF_F32: launch_composite_t<LF_F32>(p, planes, count, ws, out, s); break;
-    case LF_F16: launch_composite_t<LF_F16>(p, planes, count, ws, out, s); break;
-    case LF_U8: launch_composite_t<LF_U8>(p, planes, count, ws, out, s); break;
-    default: launch_composite_t<LF_BF16>(p, planes, count, ws, out, s); break;
+    case LF_F32: launch_composite_t<LF_F32, SAVE>(p, planes, count, ws, out, s, state); break;
+    case LF_F16: launch_composite_t<LF_F16, SAVE>(p, planes, count, ws, out, s, state); break;
+    case LF_U8: launch_composite_t<LF_U8, SAVE>(p, planes, count, ws, out, s, state); break;
+    default: launch_composite_t<LF_BF16, SAVE>(p, planes, count, ws, out, s, state); break;
     }
+}
+
+void launch_composite(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
+                      cudaStream_t s, float4* state)
+{
+    if (state)
+        launch_composite_dt<true>(p, planes, count, ws, out, state, s);
+    else
+        launch_composite_dt<false>(p, planes, count, ws, out, nullptr, s);
 }
 
 }  // namespace lf

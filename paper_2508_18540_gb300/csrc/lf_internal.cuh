@@ -76,6 +76,74 @@ inline void launch_overlapped(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
 }
 #endif
 
+// ---- mbarriers with bounded waits (shared by the staged kernels) ---------
+// Every device-side wait of the library gives up after about kWaitLimitNs of
+// wall time or kSpinLimit tries; its caller then records an error word.
+constexpr long long kSpinLimit = 1ll << 26;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s: a wait that long has failed
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase with the given parity; gives up (false) after about
+// limit_ns of wall time (the clock is read every 4096 failed tries, from the
+// first such read on) or kSpinLimit tries, whichever comes first. One plain
+// loop: the common case (first try succeeds) costs what an unbounded wait does.
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, unsigned long long limit_ns)
+{
+    unsigned long long t0 = 0;
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 4095) == 4095) {
+            const unsigned long long t = global_ns();
+            if (t0 == 0)
+                t0 = t;
+            else if (t - t0 > limit_ns)
+                return false;
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    return mbar_wait_for(bar, parity, kWaitLimitNs);
+}
+
+#endif
+
 // ---- RGBA8 unorm codec (exact, no conversion-unit instructions) -------------
 // decode: byte k of u placed under the exponent of 2^23 reads 2^23 + byte;
 //         subtracting 2^23 leaves the byte as an exact FP32 integer.
@@ -355,10 +423,13 @@ size_t composite_batched_smem(size_t max_stage_bytes, int maxN, int VG);
 // argument checks and parameters of one composite (lf_api.cu)
 lf_status composite_args(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,
                          const float* out, void* ws, size_t ws_bytes, CompWs* cw, CompParams* p);
+// state != null: the saving form, which also writes the adjoint's starting
+// state ([V][Ny][Nx] float4, separate views order)
 void launch_composite(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
-                      float* out, cudaStream_t s);
+                      float* out, cudaStream_t s, float4* state = nullptr);
 void launch_wait_selftest(unsigned long long limit_ns, int* result, cudaStream_t s);
+// state != null: start from the saving forward's state (one plane walk)
 void launch_composite_bwd(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws,
-                          const float* dviews, float* dplanes, cudaStream_t s);
+                          const float* dviews, float* dplanes, cudaStream_t s, const float4* state = nullptr);
 
 }  // namespace lf

@@ -107,6 +107,23 @@ def test_invalid_arguments_are_rejected(L):
     assert lib.lf_composite_noalloc_status(1 << 20, ctypes.byref(vs), None) == L.LF_ERR_INVALID_ARG
     assert lib.lf_selftest_bounded_wait(0, None) == L.LF_ERR_INVALID_ARG
     assert lib.lf_selftest_bounded_wait(20000, None) == L.LF_ERR_INVALID_ARG
+    # the saving composite and its adjoint check the state buffer on the host
+    sb = lib.lf_composite_state_size(ctypes.byref(ref), ctypes.byref(vs))
+    assert sb == 16 * 5 * ref.base.Nx * ref.base.Ny
+    assert lib.lf_composite_state_size(None, ctypes.byref(vs)) == 0
+    pl16 = L.LfPlanes(4, ref.H, ref.W, 0, 256, 1, 1, 1, 1)   # FP32 texels: rgba 16-byte aligned
+    for state, nbytes, what in ((None, sb, b"NULL"), (8, sb, b"aligned"), (16, sb - 16, b"smaller")):
+        st = lib.lf_composite_save(ctypes.byref(pl16), ctypes.byref(ref), ctypes.byref(vs), ctypes.c_void_p(16),
+                                   ctypes.c_void_p(state), nbytes, ctypes.c_void_p(256), 1 << 20, None)
+        assert st == L.LF_ERR_INVALID_ARG and what in lib.lf_last_error(), what
+        st = lib.lf_composite_backward_saved(ctypes.byref(pl16), ctypes.byref(ref), ctypes.byref(vs),
+                                             ctypes.c_void_p(16), ctypes.c_void_p(state), nbytes,
+                                             ctypes.c_void_p(16), ctypes.c_void_p(256), 1 << 20, None)
+        assert st == L.LF_ERR_INVALID_ARG and what in lib.lf_last_error(), what
+    # texels are read whole: an FP32 plane array off a 16-byte boundary is refused
+    st = lib.lf_composite(ctypes.byref(planes), ctypes.byref(ref), ctypes.byref(vs), ctypes.c_void_p(16),
+                          ctypes.c_void_p(256), 1 << 20, None)
+    assert st == L.LF_ERR_INVALID_ARG and b"texel-aligned" in lib.lf_last_error()
 
 
 def test_workspace_sizes(L):

@@ -93,8 +93,8 @@ class _OracleLoss:
         return (lp - lm) / (2 * h)
 
 
-def _gpu_grads(w, W, dtype="f32"):
-    r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, dtype)
+def _gpu_grads(w, W, dtype="f32", save_state=False):
+    r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, dtype, save_state=save_state)
     g = api.DeviceGaussians.from_scene(w.scene)
     r.render(g)
     grads, dplanes = r.backward(g, torch.from_numpy(W.astype(np.float32)).cuda())
@@ -156,15 +156,17 @@ def test_culled_gaussians_get_zero_gradient(fd_case):
         assert np.all(g[key][out] == 0.0), key
 
 
-def test_composite_adjoint_against_fd(orc):
-    # dplanes of the composite alone, on random texels, nearest and bilinear
+@pytest.mark.parametrize("save_state", [False, True])
+def test_composite_adjoint_against_fd(orc, save_state):
+    # dplanes of the composite alone, on random texels, nearest and bilinear;
+    # the adjoint's own two walks, or one walk from the saving forward's state
     for bilinear in (False, True):
         w = _fd_scene(seed=6, n=1500)
         w = S.Workload(w.name, w.scene, w.camera, w.display, S.ViewSet(5, 1, bilinear, (0.2, 0.1, 0.3)), w.N,
                        w.binning)
         rng = np.random.default_rng(14)
         W = rng.normal(size=(5, w.camera.Ny, w.camera.Nx, 4))
-        _, dplanes, r = _gpu_grads(w, W)
+        _, dplanes, r = _gpu_grads(w, W, save_state=save_state)
         dp = dplanes.cpu().numpy().astype(np.float64)
         o = orc.render(w)
         planes = o["planes"].copy()
@@ -246,14 +248,15 @@ def test_voxel_gradients_against_fd(orc):
         assert _rel(np.array(an), np.array(fd)) <= REL_TOL, key
 
 
-def test_autograd_function_and_fit_step():
+@pytest.mark.parametrize("save_state", [False, True])
+def test_autograd_function_and_fit_step(save_state):
     # torch.autograd path: gradients equal the direct adjoint call, and a few
     # gradient steps on opacities reduce the L2 loss against target views
     w = _fd_scene(seed=8, n=3000)
     tgt_scene = S.perturbed(w.scene, 9, mean_std=0.0)
     r_t = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f32")
     target = r_t.render(api.DeviceGaussians.from_scene(tgt_scene)).clone()
-    r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f32")
+    r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f32", save_state=save_state)
     g = api.DeviceGaussians.from_scene(w.scene)
     params = [t.clone().requires_grad_(True) for t in (g.means, g.scales, g.quats, g.opacity, g.rgb)]
     views = AG.render_gaussians(r, *params)
@@ -307,3 +310,107 @@ def test_staged_and_unstaged_composite_adjoints_agree(dtype, bilinear):
     scale = float(dp_staged.abs().max())
     assert scale > 0.0
     assert float((dp_staged - dp_unstaged).abs().max()) <= 2e-5 * scale
+
+
+def _opaque_planes(dtype, seed=21):
+    # rendered planes with the alpha of 4 x 4 texel blocks (3 % of them) set
+    # to 1 exactly (A = 1: T is 0 behind such a texel, as dense FP16 / U8
+    # planes reach by rounding); bilinear samples inside a block get A = 1 or
+    # 1 - a few ulp
+    w = _fd_scene(seed=seed, n=3000, res=64, N=8)
+    r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, dtype)
+    r.render(api.DeviceGaussians.from_scene(w.scene))
+    rgba = r.planes.rgba
+    N, H, W = rgba.shape[:3]
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    blocks = torch.rand((N, (H + 3) // 4, (W + 3) // 4), device="cuda", generator=gen) < 0.03
+    hit = blocks.repeat_interleave(4, 1).repeat_interleave(4, 2)[:, :H, :W]
+    rgba[..., 3][hit] = 255 if dtype == "u8" else 1.0
+    assert int(hit.sum()) > 50
+    return w, r
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16", "u8"])
+@pytest.mark.parametrize("bilinear", [False, True])
+def test_saved_state_adjoint_matches_two_walks(dtype, bilinear):
+    # lf_composite_save gives the views of lf_composite up to the colour
+    # behind the plane where T falls below 2^-64, and
+    # lf_composite_backward_saved the dplanes of lf_composite_backward up to
+    # FP32 rounding (atomic order), with opaque texels (A = 1) in the planes;
+    # the state names the stop plane of every pixel that has one. Staged
+    # kernels, and the unstaged ones on a copy of the planes one texel off
+    # the 16-byte boundary.
+    w, r = _opaque_planes(dtype)
+    views = S.ViewSet(7, 1, bilinear, (0.2, 0.1, 0.3))
+    pl = r.planes
+    V, Ny, Nx = 7, w.camera.Ny, w.camera.Nx
+    cws = api.alloc_workspace(api.lf_composite_workspace_size(w.N, views), "cuda")
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    dv = torch.randn((V, Ny, Nx, 4), device="cuda", generator=gen)
+    shape = tuple(pl.rgba.shape)
+    cases = [pl]
+    if dtype != "f32":
+        # one texel off: rows no longer start on 16-byte boundaries (FP32
+        # texels are 16 bytes, so FP32 planes always stage)
+        flat = torch.empty((shape[0] * shape[1] * shape[2] + 1, 4), dtype=pl.rgba.dtype, device="cuda")
+        moved = flat[1:].view(shape)
+        moved.copy_(pl.rgba)
+        assert moved.data_ptr() % 16 != 0
+        cases.append(api.Planes(moved, pl.d, pl.count, pl.chunk, pl.rect, pl.dtype_code))
+    results = []
+    for P in cases:
+        plain = torch.empty((V, Ny, Nx, 4), device="cuda")
+        saved = torch.full((V, Ny, Nx, 4), float("nan"), device="cuda")
+        state = torch.full(api.composite_state_shape(r.ref, views), float("nan"), device="cuda")
+        api.lf_composite(P, r.ref, views, plain, cws)
+        api.lf_composite_save(P, r.ref, views, saved, state, cws)
+        d2 = torch.empty(shape, dtype=torch.float32, device="cuda")
+        d1 = torch.empty(shape, dtype=torch.float32, device="cuda")
+        api.lf_composite_backward(P, r.ref, views, dv, d2, cws)
+        api.lf_composite_backward_saved(P, r.ref, views, dv, state, d1, cws)
+        assert api.lf_composite_status(w.N, views, cws) == 0
+        assert float((saved - plain).abs().max()) <= 2e-6
+        scale = float(d2.abs().max())
+        assert scale > 0.0
+        assert float((d1 - d2).abs().max()) <= 2e-5 * scale
+        results.append((saved, state, d1))
+    # the state's plane index: N where T never falls below 2^-64, else the
+    # stop plane; staged and unstaged agree on it exactly
+    # (bilinear: staged and unstaged round A differently, so a sample may be
+    # exactly opaque in one and 1 - ulp in the other)
+    k_st = results[0][1][..., 1].view(torch.int32)
+    opq = k_st < w.N
+    assert int((~opq).sum()) > 0 and bool((k_st >= 0).all())
+    if not bilinear:
+        assert int(opq.sum()) > 0
+    if int(opq.sum()) > 0:
+        alpha_opaque = results[0][0][..., 3][opq]
+        assert float((alpha_opaque - 1.0).abs().max()) == 0.0      # T = 0 behind an opaque plane
+    if len(results) == 2 and not bilinear:
+        assert torch.equal(k_st, results[1][1][..., 1].view(torch.int32))
+        assert float((results[0][0] - results[1][0]).abs().max()) <= 2e-6
+        scale = float(results[0][2].abs().max())
+        assert float((results[0][2] - results[1][2]).abs().max()) <= 2e-5 * scale
+
+
+def test_saved_state_renderer_matches_oracle(orc):
+    # the saving forward's views against the FP64 oracle (the display parity
+    # bar), and the renderer falls back to the two-walk adjoint once it has
+    # rebuilt without compositing
+    w = _fd_scene(seed=12, n=3000, res=64, N=8)
+    r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f32", save_state=True)
+    g = api.DeviceGaussians.from_scene(w.scene)
+    v = r.render(g).cpu().numpy().astype(np.float64)
+    o = orc.render(w)
+    assert np.abs(v - o["views"]).max() <= 1e-4
+    assert r.state_generation == r.generation
+    r.build(g)
+    assert r.state_generation != r.generation
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    dv = torch.randn((w.views.Vx, w.camera.Ny, w.camera.Nx, 4), device="cuda", generator=gen)
+    _, dp_two = r.backward(g, dv)
+    r.composite()
+    _, dp_one = r.backward(g, dv)
+    torch.cuda.synchronize()
+    scale = float(dp_two.abs().max())
+    assert float((dp_one - dp_two).abs().max()) <= 2e-5 * scale
