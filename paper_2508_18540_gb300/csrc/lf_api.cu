@@ -836,6 +836,10 @@ static lf_status splat_backward_common(int64_t n, const lf_ref_camera* ref, cons
     if (planes->N < 1 || planes->N > 65535 || planes->W != ref->W || planes->H != ref->H)
         return fail(LF_ERR_INVALID_ARG, "plane array shape does not match the reference camera");
     if (((uintptr_t)dplanes) % 16) return fail(LF_ERR_INVALID_ARG, "dplanes must be 16-byte aligned");
+    if (planes->dtype < LF_F32 || planes->dtype > LF_U8) return fail(LF_ERR_INVALID_ARG, "unknown plane dtype");
+    // the Gaussian adjoint reads FP32 texels (C_end, 1 - T_end) of the forward
+    if (kind == 0 && planes->dtype == LF_F32 && (!planes->rgba || ((uintptr_t)planes->rgba) % 16))
+        return fail(LF_ERR_INVALID_ARG, "FP32 planes->rgba must be non-NULL and 16-byte aligned");
     if (n < 0 || n > (int64_t)0x7fffffff) return fail(LF_ERR_INVALID_ARG, "primitive count out of range");
     if (!ws) return fail(LF_ERR_WORKSPACE, "workspace is NULL");
     if (((uintptr_t)ws) % 256) return fail(LF_ERR_WORKSPACE, "workspace must be 256-byte aligned");
@@ -845,12 +849,12 @@ static lf_status splat_backward_common(int64_t n, const lf_ref_camera* ref, cons
     if (n > 0 && cudaMemsetAsync(w->g2d, 0, sizeof(float) * 12 * (size_t)n, stream) != cudaSuccess)
         return check_launch("gradient accumulator reset");
     RasterParams rp;
-    fill_raster_params(ref, planes->N, LF_F32, &rp);
+    fill_raster_params(ref, planes->N, planes->dtype, &rp);
     const int n_supers = ((ref->W + kSuper - 1) / kSuper) * ((ref->H + kSuper - 1) / kSuper);
     const uint32_t* ranks = tile_sort_passes(tile_bits_for(n_supers)) % 2 ? w->entB : w->entA;
     trace_begin(kind == 0 ? "raster_gaussians_bwd" : "raster_voxels_bwd", stream);
     if (kind == 0)
-        launch_raster_gaussians_bwd(*w, rp, ranks, dplanes, stream);
+        launch_raster_gaussians_bwd(*w, rp, ranks, planes->rgba, dplanes, stream);
     else
         launch_raster_voxels_bwd(*w, rp, ranks, dplanes, stream);
     trace_end(stream);

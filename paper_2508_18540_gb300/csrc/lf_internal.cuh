@@ -337,8 +337,9 @@ void launch_raster_gauss_batched(const RasterScene* scenes_dev, int n_sc, int dt
 
 // backward: raster adjoints accumulate into ws.g2d (zeroed by the caller),
 // then the per-rank chain rule / scatter writes the parameter gradients
+// planes: the forward's plane texels (p.dtype), read for K with FP32 planes
 void launch_raster_gaussians_bwd(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks,
-                                 const float* dplanes, cudaStream_t s);
+                                 const void* planes, const float* dplanes, cudaStream_t s);
 void launch_raster_voxels_bwd(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, const float* dplanes,
                               cudaStream_t s);
 void launch_gauss_chain(const lf_gaussians& g, const ProjParams& p, const BuildWs& ws, const lf_gaussians_grad& out,

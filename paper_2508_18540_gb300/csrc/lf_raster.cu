@@ -613,14 +613,14 @@ __global__ void __launch_bounds__(kTilePix, 5) k_raster_voxel(BuildWs w, RasterP
 // w_i = c_i . dC + dA (because 1 - T_end = sum_i T_i a_i):
 //   dL/dc_i = T_i a_i dC,   dL/da_i = T_i (w_i - S_i),
 //   S_i = sum_{j>i} (T_j / T_{i+1}) a_j w_j,  S_{i-1} = a_i w_i + (1 - a_i) S_i.
-// The kernels first recompute T_end per pixel (front to back, the forward's
-// operation order), then walk the list back to front recovering
-// T_i = T_{i+1} / (1 - a_i); a_i <= 0.99 (Gaussians) keeps every divisor
-// >= 0.01. Transmittance is carried as m 2^-e (e a multiple of 64) so that a
-// long list cannot underflow it before the reverse walk. Nothing per entry is
-// stored: the per-chunk transmittance is recomputed, not kept.
-// Per entry each warp sums its pixels' contributions with shuffles and adds
-// them to the primitive's accumulator (rank order) with one vector atomic.
+// The voxel kernel first recomputes T_end per pixel (front to back, the
+// forward's operation order), then walks the list back to front recovering
+// T_i = T_{i+1} / (1 - a_i), with the transmittance carried as m 2^-e (e a
+// multiple of 64) so that a long list cannot underflow it before the reverse
+// walk. The Gaussian kernel walks front to back once (below). Nothing per
+// entry is stored. Per entry each warp sums its pixels' contributions with
+// shuffles and adds them to the primitive's accumulator (rank order) with
+// vector atomics.
 // ---------------------------------------------------------------------------
 
 constexpr float kUp = 18446744073709551616.0f;        // 2^64
@@ -661,175 +661,309 @@ __device__ __forceinline__ float4 load_grad(const float4* __restrict__ dplanes, 
     return make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Gaussians. Same CTA shape and list walk as k_raster_gauss. Accumulator of
-// rank r: g2d[3 r .. 3 r + 2] = {d mean x, d mean y, d a, d b}, {d c, d o,
-// d r, d g}, {d b(lue), 0, 0, 0} with (a, b, c) the conic, q = a dx^2 +
-// 2 b dx dy + c dy^2, alpha = min(0.99, o exp(-q/2)); a clamped alpha passes
-// no gradient to o or q.
-template <int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT) k_raster_gauss_bwd(BuildWs w, RasterParams p,
-                                                                     const uint32_t* __restrict__ ranks,
-                                                                     const float4* __restrict__ dplanes,
-                                                                     float4* __restrict__ g2d)
-{
-    constexpr int NT = kTilePix / PPT;
-    constexpr float kL2E = 1.4426950408889634f;
-    __shared__ float4 s_e0[NT];
-    __shared__ float4 s_e1[NT];
-    __shared__ float4 s_rgb[NT];
-    __shared__ float4 s_abc[NT];
-    __shared__ int s_wc[NT / 32];
-    if (w.hdr->overflow) return;
-    const int t = blockIdx.x, k = blockIdx.y;
-    const int tx = t % p.tiles_x, ty = t / p.tiles_x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py0 = ty * kTile + (threadIdx.x / kTile) * PPT;
-    const int sx0 = tx * kTile, sx1 = sx0 + kTile - 1;
-    const int sy0 = ty * kTile + 2 * PPT * warp, sy1 = sy0 + 2 * PPT - 1;
-    const int st = (ty / kTilesPerSuper) * p.supers_x + tx / kTilesPerSuper;
-    const int2 sg = w.seg[(size_t)st * p.N + k];
-    const int L = sg.y - sg.x;
-    const float fpx = (float)px;
-    float Tm[PPT], S[PPT], dC[PPT][3], dA[PPT];
-    int Te[PPT];
-#pragma unroll
-    for (int r = 0; r < PPT; ++r) {
-        const float4 g = load_grad(dplanes, k, px, py0 + r, p.W, p.H);
-        dC[r][0] = g.x, dC[r][1] = g.y, dC[r][2] = g.z, dA[r] = g.w;
-        Tm[r] = 1.f, Te[r] = 0, S[r] = 0.f;
-    }
-    if (L == 0) return;
-    const int nbatch = (L + NT - 1) / NT;
+// Gaussians, front to back. For the pixel's entries i of a list, with
+// w_i = c_i . dC + dA and R_i the part of C . dC + A dA = sum_j T_j a_j w_j
+// behind entry i,
+//   R_i = sum_{j>i} T_j a_j w_j = K - C_{i+1} . dC + T_{i+1} dA,
+//   K = C_end . dC - T_end dA,
+//   dL/dc_i = T_i a_i dC,   dL/da_i = T_i w_i - R_i / (1 - a_i),
+// (the T_j, j > i, carry the factor 1 - a_i) where C_{i+1}, T_{i+1} are the
+// running colour and transmittance behind entry i: one walk in the forward's
+// order and arithmetic gives every term, with no division chain and no
+// rescaling (1 - a_i >= 0.01). K comes from the forward's texel (FP32 planes:
+// C_end exact, T_end = 1 - A within 2^-24), from the split list's partials
+// (composed as the forward composed them), or, for the other plane types,
+// from a first walk that recomputes (C_end, T_end).
+// CTA layout, staging and list walk as k_raster_gauss (one (super-tile,
+// chunk) list, or one part of a split list, per CTA; 8 warps of 8 x 16
+// pixel strips, lane rows l / 8 + 4 s). A part starts from the composition
+// of the partials in front of it. Per entry each warp adds its pixels'
+// terms: Su = sum u, Sv = sum v (u = dq dx, v = dq dy, dq = -a_i dL/da_i / 2),
+// Saa = sum u dx, Sbb = sum u dy, Scc = sum v dy, So = sum dL/da_i G, and the
+// colour terms; eight of them are reduced by a butterfly that halves the
+// values each step (9 shuffles), and
+//   d mean = -2 (a Su + b Sv, b Su + c Sv), d(a, b, c) = (Saa, 2 Sbb, Scc)
+// (q = a dx^2 + 2 b dx dy + c dy^2, alpha = min(0.99, o exp(-q/2)); a clamped
+// alpha passes no gradient to o or q). Accumulator of rank r:
+// g2d[3 r .. 3 r + 2] = {d mean x, d mean y, d a, d b}, {d c, d o, d r,
+// d g}, {d b(lue), 0, 0, 0}.
+constexpr int kGaussBwdThreads = kGaussThreads;
 
-    // stages batch b: compacted entries of the tile in list order; returns the count
-    auto stage = [&](int b) -> int {
-        const int i = b * NT + threadIdx.x;
-        uint32_t rk = 0;
-        int4 r = make_int4(0, 0, -1, -1);
-        if (i < L) {
-            rk = ranks[sg.x + i];
-            r = w.r_rect[rk];
+struct GaussBwdSmem {
+    float4 e0[2][kGaussBwdThreads];
+    float4 e1[2][kGaussBwdThreads];
+    float4 rgb[2][kGaussBwdThreads];   // {r, g, b, 1 / o}
+    uint32_t rank[2][kGaussBwdThreads];
+};
+
+// v[0..7] summed over the warp; lane l ends with the sum of v[(l >> 2) & 7]
+__device__ __forceinline__ float warp_reduce_scatter8(float (&v)[8], int lane)
+{
+    float h[4];
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b4 ? v[i] : v[i + 4], keep = b4 ? v[i + 4] : v[i];
+        h[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float q[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b3 ? h[i] : h[i + 2], keep = b3 ? h[i + 2] : h[i];
+        q[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const float send = b2 ? q[0] : q[1], keep = b2 ? q[1] : q[0];
+    float r = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    r += __shfl_xor_sync(0xffffffffu, r, 2);
+    r += __shfl_xor_sync(0xffffffffu, r, 1);
+    return r;
+}
+
+// One list (SPLIT false) or one part of a split list (SPLIT true).
+template <int DT, bool SPLIT>
+__device__ __forceinline__ void raster_gauss_bwd_list(const BuildWs& w, const RasterParams& p,
+                                                      const uint32_t* __restrict__ ranks,
+                                                      const void* __restrict__ planes,
+                                                      const float4* __restrict__ dplanes, float4* __restrict__ g2d,
+                                                      int st, int k, GaussBwdSmem& sm, int part, int P, int slot,
+                                                      int S)
+{
+    constexpr int NS = kGaussNS;
+    constexpr int NT = kGaussBwdThreads;
+    constexpr float kL2E = 1.4426950408889634f;
+    // K from a first walk: unsplit lists whose planes are not FP32
+    constexpr bool WALK1 = !SPLIT && DT != LF_F32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int SX = (st % p.supers_x) * kSuper, SY = (st / p.supers_x) * kSuper;
+    const int sx0 = SX + 8 * (warp & 3), sx1 = sx0 + 7;
+    const int sy0 = SY + 4 * NS * (warp >> 2), sy1 = sy0 + 4 * NS - 1;
+    const int px = sx0 + (lane & 7);
+    const int py0 = sy0 + (lane >> 3);
+    const int2 sg = w.seg[(size_t)st * p.N + k];
+    const int beg = SPLIT ? sg.x + part * S : sg.x;
+    const int L = SPLIT ? min(sg.y - beg, S) : sg.y - sg.x;
+    const float fpx = (float)px;
+
+    float C[NS][3], T[NS], dC[NS][3], dA[NS], K[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int py = py0 + 4 * s;
+        const bool in = px < p.W && py < p.H;
+        const size_t idx = ((size_t)k * p.H + py) * p.W + px;
+        const float4 g = in ? __ldg(dplanes + idx) : make_float4(0.f, 0.f, 0.f, 0.f);
+        dC[s][0] = g.x, dC[s][1] = g.y, dC[s][2] = g.z, dA[s] = g.w;
+        C[s][0] = C[s][1] = C[s][2] = 0.f, T[s] = 1.f;
+        K[s] = 0.f;
+        if (SPLIT) {
+            // (C, T) in front of this part and at the list's end: the
+            // partials composed in part order, as the forward composed them
+            float ce0 = 0.f, ce1 = 0.f, ce2 = 0.f, te = 1.f;
+            const int slot0 = slot - part;
+            for (int q = 0; q < P; ++q) {
+                if (q == part) C[s][0] = ce0, C[s][1] = ce1, C[s][2] = ce2, T[s] = te;
+                const float4 v = __ldcg(w.r_part + (size_t)(slot0 + q) * (kSuper * kSuper) + (warp * NS + s) * 32 + lane);
+                ce0 = fmaf(te, v.x, ce0);
+                ce1 = fmaf(te, v.y, ce1);
+                ce2 = fmaf(te, v.z, ce2);
+                te *= v.w;
+            }
+            K[s] = fmaf(ce0, dC[s][0], fmaf(ce1, dC[s][1], fmaf(ce2, dC[s][2], -te * dA[s])));
+        } else if (DT == LF_F32) {
+            const float4 t = in ? __ldg(reinterpret_cast<const float4*>(planes) + idx) : make_float4(0.f, 0.f, 0.f, 1.f);
+            K[s] = fmaf(t.x, dC[s][0], fmaf(t.y, dC[s][1], fmaf(t.z, dC[s][2], -(1.0f - t.w) * dA[s])));
         }
-        const bool hit = i < L && meets_tile(r, sx0, ty * kTile);
-        int cnt;
-        const int slot = compact_slot<NT>(hit, s_wc, &cnt);
-        if (hit) {
+    }
+
+    // stages batch `base` of the list into buffer buf
+    auto stage = [&](int base, int buf) {
+        const int i = base + threadIdx.x;
+        if (i < L) {
+            const uint32_t rk = ranks[beg + i];
+            const int4 r = w.r_rect[rk];
             const float4 geo = w.r_geo[rk];
             const float4 c = w.r_con[rk];
-            s_e0[slot] = make_float4(geo.x, geo.y, -0.5f * kL2E * c.x, -kL2E * c.y);
-            s_e1[slot] = make_float4(-0.5f * kL2E * c.z, c.w, __int_as_float((r.x & 0xffff) | (r.y << 16)),
-                                     __int_as_float(((r.z - r.x) & 0xffff) | ((r.w - r.y) << 16)));
-            s_rgb[slot] = w.r_rgb[rk];
-            s_abc[slot] = make_float4(c.x, c.y, c.z, __uint_as_float(rk));
+            const float4 rgb = w.r_rgb[rk];
+            sm.e0[buf][threadIdx.x] = make_float4(geo.x, geo.y, -0.5f * kL2E * c.x, -kL2E * c.y);
+            sm.e1[buf][threadIdx.x] =
+                make_float4(-0.5f * kL2E * c.z, __log2f(c.w), __int_as_float((r.x & 0xffff) | (r.y << 16)),
+                            __int_as_float(((r.z - r.x) & 0xffff) | ((r.w - r.y) << 16)));
+            sm.rgb[buf][threadIdx.x] = make_float4(rgb.x, rgb.y, rgb.z, 1.0f / c.w);
+            sm.rank[buf][threadIdx.x] = rk;
         }
-        __syncthreads();
-        return cnt;
     };
-    auto strip_hit = [&](int jl, int cnt) -> bool {
-        if (jl >= cnt) return false;
-        const float4 e1 = s_e1[jl];
-        const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
-        const int rx0 = xy & 0xffff, ry0 = xy >> 16;
-        return rx0 <= sx1 && rx0 + (wh & 0xffff) >= sx0 && ry0 <= sy1 && ry0 + (wh >> 16) >= sy0;
+    auto strip_mask = [&](const float4* s_e1, int m0, int cnt) -> uint32_t {
+        const int jl = m0 + lane;
+        bool hit = false;
+        if (jl < cnt) {
+            const float2 rc = *reinterpret_cast<const float2*>(&s_e1[jl].z);
+            const int xy = __float_as_int(rc.x), wh = __float_as_int(rc.y);
+            const int rx0 = xy & 0xffff, ry0 = xy >> 16;
+            hit = rx0 <= sx1 && rx0 + (wh & 0xffff) >= sx0 && ry0 <= sy1 && ry0 + (wh >> 16) >= sy0;
+        }
+        return __ballot_sync(0xffffffffu, hit);
     };
 
-    // 1) forward: T_end per pixel
-    for (int b = 0; b < nbatch; ++b) {
-        const int cnt = stage(b);
-        for (int m0 = 0; m0 < cnt; m0 += 32) {
-            uint32_t mask = __ballot_sync(0xffffffffu, strip_hit(m0 + lane, cnt));
-            while (mask) {
-                const int j = m0 + __ffs(mask) - 1;
-                mask &= mask - 1;
-                const float4 e1 = s_e1[j];
-                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
-                if ((uint32_t)(px - (xy & 0xffff)) > (uint32_t)(wh & 0xffff)) continue;
-                const float4 e0 = s_e0[j];
-                const float dx = fpx - e0.x;
-                const float adx = e0.z * dx;
-                const int ry0 = xy >> 16, rh = wh >> 16;
+    if (WALK1) {
+        // (C_end, T_end) in the forward's arithmetic
+        int buf = 0;
+        for (int base = 0; base < L; base += NT, buf ^= 1) {
+            stage(base, buf);
+            __syncthreads();
+            const int cnt = min(NT, L - base);
+            const float4* s_e0 = sm.e0[buf];
+            const float4* s_e1 = sm.e1[buf];
+            const float4* s_rgb = sm.rgb[buf];
+            for (int m0 = 0; m0 < cnt; m0 += 32) {
+                uint32_t mask = strip_mask(s_e1, m0, cnt);
+                while (mask) {
+                    const int j = m0 + __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const float4 e0 = s_e0[j];
+                    const float4 e1 = s_e1[j];
+                    const float4 col = s_rgb[j];
+                    const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
+                    const int rt = (uint32_t)(px - (xy & 0xffff)) <= (uint32_t)(wh & 0xffff) ? py0 - (xy >> 16)
+                                                                                            : 0x40000000;
+                    const uint32_t rh = (uint32_t)(wh >> 16);
+                    const float dx = fpx - e0.x;
+                    const float g1 = e0.w * dx;
+                    const float g0 = fmaf(e0.z * dx, dx, e1.y);
 #pragma unroll
-                for (int r = 0; r < PPT; ++r) {
-                    if ((uint32_t)(py0 + r - ry0) <= (uint32_t)rh) {
-                        const float dy = (float)(py0 + r) - e0.y;
-                        const float pw = fmaf(dx, fmaf(e0.w, dy, adx), e1.x * dy * dy);
-                        const float al = fminf(0.99f, e1.y * ex2_approx(pw));
-                        t_forward(Tm[r], Te[r], al);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
-
-    // 2) reverse: back to front through the batches and the entries
-    for (int b = nbatch - 1; b >= 0; --b) {
-        const int cnt = stage(b);
-        for (int m0 = ((cnt - 1) / 32) * 32; m0 >= 0; m0 -= 32) {
-            uint32_t mask = __ballot_sync(0xffffffffu, strip_hit(m0 + lane, cnt));
-            while (mask) {
-                const int bit = 31 - __clz(mask);
-                mask &= ~(1u << bit);
-                const int j = m0 + bit;
-                const float4 e1 = s_e1[j];
-                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
-                const bool colin = (uint32_t)(px - (xy & 0xffff)) <= (uint32_t)(wh & 0xffff);
-                const float4 e0 = s_e0[j];
-                const float4 abc = s_abc[j];
-                const float4 col = s_rgb[j];
-                const float dx = fpx - e0.x;
-                const float adx = e0.z * dx;
-                const int ry0 = xy >> 16, rh = wh >> 16;
-                float g_mx = 0.f, g_my = 0.f, g_a = 0.f, g_b = 0.f, g_c = 0.f, g_o = 0.f;
-                float g_r = 0.f, g_g = 0.f, g_bl = 0.f;
-#pragma unroll
-                for (int r = 0; r < PPT; ++r) {
-                    if (colin && (uint32_t)(py0 + r - ry0) <= (uint32_t)rh) {
-                        const float dy = (float)(py0 + r) - e0.y;
-                        const float pw = fmaf(dx, fmaf(e0.w, dy, adx), e1.x * dy * dy);
-                        const float G = ex2_approx(pw);
-                        const float araw = e1.y * G;
-                        const float al = fminf(0.99f, araw);
-                        const float oma = 1.0f - al;
-                        t_reverse(Tm[r], Te[r], oma);
-                        const float Ti = t_value(Tm[r], Te[r]);
-                        const float wv = fmaf(col.x, dC[r][0], fmaf(col.y, dC[r][1], fmaf(col.z, dC[r][2], dA[r])));
-                        const float dal = Ti * (wv - S[r]);
-                        S[r] = fmaf(al, wv, oma * S[r]);
-                        const float ta = Ti * al;
-                        g_r = fmaf(ta, dC[r][0], g_r);
-                        g_g = fmaf(ta, dC[r][1], g_g);
-                        g_bl = fmaf(ta, dC[r][2], g_bl);
-                        if (araw < 0.99f) {
-                            g_o = fmaf(dal, G, g_o);
-                            const float dq = -0.5f * dal * al;
-                            g_a = fmaf(dq, dx * dx, g_a);
-                            g_b = fmaf(dq, 2.0f * dx * dy, g_b);
-                            g_c = fmaf(dq, dy * dy, g_c);
-                            g_mx = fmaf(dq, -2.0f * fmaf(abc.x, dx, abc.y * dy), g_mx);
-                            g_my = fmaf(dq, -2.0f * fmaf(abc.y, dx, abc.z * dy), g_my);
+                    for (int s = 0; s < NS; ++s) {
+                        if ((uint32_t)(rt + 4 * s) <= rh) {
+                            const float dy = (float)(py0 + 4 * s) - e0.y;
+                            const float pw = fmaf(fmaf(e1.x, dy, g1), dy, g0);
+                            const float al = fminf(0.99f, ex2_approx(pw));
+                            const float ta = T[s] * al;
+                            C[s][0] = fmaf(ta, col.x, C[s][0]);
+                            C[s][1] = fmaf(ta, col.y, C[s][1]);
+                            C[s][2] = fmaf(ta, col.z, C[s][2]);
+                            T[s] = fmaf(-T[s], al, T[s]);
                         }
                     }
                 }
-                g_mx = warp_sum(g_mx);
-                g_my = warp_sum(g_my);
-                g_a = warp_sum(g_a);
-                g_b = warp_sum(g_b);
-                g_c = warp_sum(g_c);
-                g_o = warp_sum(g_o);
-                g_r = warp_sum(g_r);
-                g_g = warp_sum(g_g);
-                g_bl = warp_sum(g_bl);
-                if (lane == 0) {
-                    float4* acc = g2d + 3 * (size_t)__float_as_uint(abc.w);
-                    atomicAdd(acc, make_float4(g_mx, g_my, g_a, g_b));
-                    atomicAdd(acc + 1, make_float4(g_c, g_o, g_r, g_g));
-                    atomicAdd(&acc[2].x, g_bl);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            K[s] = fmaf(C[s][0], dC[s][0], fmaf(C[s][1], dC[s][1], fmaf(C[s][2], dC[s][2], -T[s] * dA[s])));
+            C[s][0] = C[s][1] = C[s][2] = 0.f, T[s] = 1.f;
+        }
+        __syncthreads();   // the walk's last reads before the buffers are staged again
+    }
+
+    int buf = 0;
+    for (int base = 0; base < L; base += NT, buf ^= 1) {
+        stage(base, buf);
+        // orders this batch's staging before its walk, and every warp's walk
+        // of the batch before last before this staging overwrote its buffer
+        __syncthreads();
+        const int cnt = min(NT, L - base);
+        const float4* s_e0 = sm.e0[buf];
+        const float4* s_e1 = sm.e1[buf];
+        const float4* s_rgb = sm.rgb[buf];
+        const uint32_t* s_rank = sm.rank[buf];
+        for (int m0 = 0; m0 < cnt; m0 += 32) {
+            uint32_t mask = strip_mask(s_e1, m0, cnt);
+            while (mask) {
+                const int j = m0 + __ffs(mask) - 1;
+                mask &= mask - 1;
+                const float4 e0 = s_e0[j];
+                const float4 e1 = s_e1[j];
+                const float4 col = s_rgb[j];
+                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
+                const int rt = (uint32_t)(px - (xy & 0xffff)) <= (uint32_t)(wh & 0xffff) ? py0 - (xy >> 16)
+                                                                                        : 0x40000000;
+                const uint32_t rh = (uint32_t)(wh >> 16);
+                const float dx = fpx - e0.x;
+                const float g1 = e0.w * dx;
+                const float g0 = fmaf(e0.z * dx, dx, e1.y);
+                // v: Su, Sv, Saa, Sbb, Scc, So, Sr, Sg; sbl: blue
+                float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float sbl = 0.f;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    if ((uint32_t)(rt + 4 * s) <= rh) {
+                        const float dy = (float)(py0 + 4 * s) - e0.y;
+                        const float pw = fmaf(fmaf(e1.x, dy, g1), dy, g0);
+                        const float araw = ex2_approx(pw);
+                        const float al = fminf(0.99f, araw);
+                        const float Ti = T[s];
+                        const float ta = Ti * al;
+                        const float wv = fmaf(col.x, dC[s][0], fmaf(col.y, dC[s][1], fmaf(col.z, dC[s][2], dA[s])));
+                        C[s][0] = fmaf(ta, col.x, C[s][0]);
+                        C[s][1] = fmaf(ta, col.y, C[s][1]);
+                        C[s][2] = fmaf(ta, col.z, C[s][2]);
+                        T[s] = fmaf(-Ti, al, Ti);
+                        v[6] = fmaf(ta, dC[s][0], v[6]);
+                        v[7] = fmaf(ta, dC[s][1], v[7]);
+                        sbl = fmaf(ta, dC[s][2], sbl);
+                        if (araw < 0.99f) {
+                            const float R = fmaf(T[s], dA[s],
+                                                 K[s] - fmaf(C[s][0], dC[s][0],
+                                                             fmaf(C[s][1], dC[s][1], C[s][2] * dC[s][2])));
+                            const float dal = fmaf(Ti, wv, -R * __frcp_rn(1.0f - al));
+                            v[5] = fmaf(dal, araw * col.w, v[5]);     // G = alpha / o
+                            const float dq = -0.5f * dal * al;
+                            const float u = dq * dx, vv = dq * dy;
+                            v[0] += u;
+                            v[1] += vv;
+                            v[2] = fmaf(u, dx, v[2]);
+                            v[3] = fmaf(u, dy, v[3]);
+                            v[4] = fmaf(vv, dy, v[4]);
+                        }
+                    }
+                }
+                const float r = warp_reduce_scatter8(v, lane);
+                sbl = warp_sum(sbl);
+                // lane 0: Su .. Sbb; lane 16: Scc, So, Sr, Sg
+                const float r1 = __shfl_down_sync(0xffffffffu, r, 4);
+                const float r2 = __shfl_down_sync(0xffffffffu, r, 8);
+                const float r3 = __shfl_down_sync(0xffffffffu, r, 12);
+                if ((lane & 15) == 0) {
+                    float4* acc = g2d + 3 * (size_t)s_rank[j];
+                    if (lane == 0) {
+                        // raw conic from the staged (A, B, C) = -log2(e) (a/2, b, c/2)
+                        const float ca = e0.z * (-2.0f / kL2E), cb = e0.w * (-1.0f / kL2E),
+                                    cc = e1.x * (-2.0f / kL2E);
+                        atomicAdd(acc, make_float4(-2.0f * fmaf(ca, r, cb * r1), -2.0f * fmaf(cb, r, cc * r1), r2,
+                                                   2.0f * r3));
+                        atomicAdd(&acc[2].x, sbl);
+                    } else {
+                        atomicAdd(acc + 1, make_float4(r, r1, r2, r3));
+                    }
                 }
             }
         }
-        __syncthreads();
+    }
+}
+
+// Lists no longer than r_seg and the parts of the longer ones, one grid:
+// CTA b < r_nslots takes part item b (CTAs past r_heavy exit), the others
+// the list (b - r_nslots) of (super-tile, chunk) order, longer lists exiting.
+template <int DT>
+__global__ void __launch_bounds__(kGaussBwdThreads) k_raster_gauss_bwd(BuildWs w, RasterParams p,
+                                                                      const uint32_t* __restrict__ ranks,
+                                                                      const void* __restrict__ planes,
+                                                                      const float4* __restrict__ dplanes,
+                                                                      float4* __restrict__ g2d)
+{
+    __shared__ GaussBwdSmem sm;
+    if (w.hdr->overflow) return;
+    const long long b = blockIdx.x;
+    if (b < w.r_nslots) {
+        if (b >= (long long)w.hdr->r_heavy) return;
+        const int4 it = w.r_items[b];
+        const int st = it.x / p.N;
+        raster_gauss_bwd_list<DT, true>(w, p, ranks, planes, dplanes, g2d, st, it.x - st * p.N, sm, it.y, it.z, it.w,
+                                        w.hdr->r_seg);
+    } else {
+        const int supers = p.supers_x * p.supers_y;
+        const int li = (int)(b - w.r_nslots);
+        const int st = li % supers, k = li / supers;
+        const int2 sg = w.seg[(size_t)st * p.N + k];
+        if (sg.y - sg.x > w.hdr->r_seg || sg.y == sg.x) return;
+        raster_gauss_bwd_list<DT, false>(w, p, ranks, planes, dplanes, g2d, st, k, sm, 0, 1, -1, 0);
     }
 }
 
@@ -1040,12 +1174,18 @@ __global__ void __launch_bounds__(kTilePix) k_raster_voxel_bwd(BuildWs w, Raster
 }  // namespace
 
 void launch_raster_gaussians_bwd(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks,
-                                 const float* dplanes, cudaStream_t s)
+                                 const void* planes, const float* dplanes, cudaStream_t s)
 {
-    const dim3 grid((unsigned)(p.tiles_x * p.tiles_y), (unsigned)p.N);
-    constexpr int kPPT = 2;
-    k_raster_gauss_bwd<kPPT><<<grid, kTilePix / kPPT, 0, s>>>(ws, p, ranks, reinterpret_cast<const float4*>(dplanes),
-                                                             reinterpret_cast<float4*>(ws.g2d));
+    const long long ctas = ws.r_nslots + (long long)p.supers_x * p.supers_y * p.N;
+    const dim3 grid((unsigned)ctas);
+    const float4* dp = reinterpret_cast<const float4*>(dplanes);
+    float4* g = reinterpret_cast<float4*>(ws.g2d);
+    switch (p.dtype) {
+    case LF_F32: k_raster_gauss_bwd<LF_F32><<<grid, kGaussBwdThreads, 0, s>>>(ws, p, ranks, planes, dp, g); break;
+    case LF_F16: k_raster_gauss_bwd<LF_F16><<<grid, kGaussBwdThreads, 0, s>>>(ws, p, ranks, planes, dp, g); break;
+    case LF_U8: k_raster_gauss_bwd<LF_U8><<<grid, kGaussBwdThreads, 0, s>>>(ws, p, ranks, planes, dp, g); break;
+    default: k_raster_gauss_bwd<LF_BF16><<<grid, kGaussBwdThreads, 0, s>>>(ws, p, ranks, planes, dp, g); break;
+    }
     note_launches(1);
 }
 

@@ -71,3 +71,18 @@ def small_rotated_camera(Nx=100, Ny=70):
     Rx = np.array([[1, 0, 0], [0, np.cos(b), -np.sin(b)], [0, np.sin(b), np.cos(b)]])
     cam = S.Camera(Rx @ Ry, np.array([0.1, -0.05, 0.3]), np.radians(50.0), np.radians(38.0), Nx, Ny)
     return cam
+
+
+def longest_super_tile_list(o, N):
+    """Longest (32 x 32 super-tile, chunk) list of an oracle render: the
+    culled-in primitives whose rectangle meets the super-tile, per chunk."""
+    v = o["valid"].astype(bool)
+    r = o["rect"][v].astype(np.int64)
+    ch = o["chunk"][v].astype(np.int64)
+    W, H = o["ref"].W, o["ref"].H
+    sx_n, sy_n = (W + 31) // 32, (H + 31) // 32
+    counts = np.zeros((sy_n, sx_n, N), np.int64)
+    for i in range(r.shape[0]):
+        x0, y0, x1, y1 = r[i]
+        counts[y0 // 32:y1 // 32 + 1, x0 // 32:x1 // 32 + 1, ch[i]] += 1
+    return int(counts.max())

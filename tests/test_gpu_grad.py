@@ -148,6 +148,37 @@ def test_gaussian_gradients_directional(fd_case):
             assert abs(an - fd) <= REL_TOL * max(abs(fd), 1e-12) + 1e-9, (key, an, fd)
 
 
+def test_gaussian_gradients_with_split_lists(orc):
+    # 20,000 faint Gaussians in a 128^2 frame, one chunk: (super-tile,
+    # chunk) lists of thousands of entries, which the raster cuts into parts;
+    # the adjoint walks every part from the composition of the partials in
+    # front of it. FP32 planes against finite differences of the FP64
+    # oracle; FP16 planes track FP32
+    from tests import gpu_util as G
+    sc = S.uniform_gaussians(20_000, 23, opacity=(0.02, 0.3))
+    t = S.workload_tiny()
+    w = S.Workload("split_fd", sc, t.camera, t.display, S.ViewSet(3), 1, "quantile")
+    o = orc.render(w)
+    assert G.longest_super_tile_list(o, 1) > 2 * 1024   # three parts or more
+    rng = np.random.default_rng(17)
+    W = rng.normal(size=(3, w.camera.Ny, w.camera.Nx, 4))
+    loss = _OracleLoss(orc, w, W)
+    g, _, _ = _gpu_grads(w, W)
+    for key in ("means", "scales", "opacity", "rgb"):
+        for _ in range(2):
+            u = rng.normal(size=loss.p[key].shape)
+            u /= np.linalg.norm(u)
+            fd = loss.fd_direction(key, u, float(np.abs(loss.p[key]).max()))
+            an = float(np.sum(g[key] * u))
+            assert abs(an - fd) <= REL_TOL * max(abs(fd), 1e-12) + 1e-9, (key, an, fd)
+    # isotropic Gaussians: a rotation changes nothing, the quaternion
+    # gradient is zero up to rounding
+    assert np.linalg.norm(g["quats"]) <= 1e-5 * np.linalg.norm(g["means"])
+    g16, _, _ = _gpu_grads(w, W, "f16")
+    for key in ("means", "scales", "opacity", "rgb"):
+        assert _rel(g16[key], g[key]) <= 2e-2, key
+
+
 def test_culled_gaussians_get_zero_gradient(fd_case):
     w, W, loss, g = fd_case
     out = loss.chunk < 0

@@ -125,21 +125,6 @@ def test_chunk_counts_and_few_primitives(orc, N):
     _compare(gpu, o, o["ref"].W, o["ref"].H, N, "f32")
 
 
-def _longest_super_tile_list(o, N):
-    """Longest (32 x 32 super-tile, chunk) list of an oracle render: the
-    culled-in primitives whose rectangle meets the super-tile, per chunk."""
-    v = o["valid"].astype(bool)
-    r = o["rect"][v].astype(np.int64)
-    ch = o["chunk"][v].astype(np.int64)
-    W, H = o["ref"].W, o["ref"].H
-    sx_n, sy_n = (W + 31) // 32, (H + 31) // 32
-    counts = np.zeros((sy_n, sx_n, N), np.int64)
-    for i in range(r.shape[0]):
-        x0, y0, x1, y1 = r[i]
-        counts[y0 // 32:y1 // 32 + 1, x0 // 32:x1 // 32 + 1, ch[i]] += 1
-    return int(counts.max())
-
-
 @pytest.mark.parametrize("N,dtype", [(1, "f32"), (2, "f32"), (2, "f16"), (3, "bf16")])
 def test_long_lists_are_split_and_merged(orc, N, dtype):
     # 30,000 Gaussians in a 128^2 frame with few chunks: (super-tile, chunk)
@@ -149,7 +134,7 @@ def test_long_lists_are_split_and_merged(orc, N, dtype):
     sc = S.uniform_gaussians(30_000, 21)
     w = S.workload_tiny()
     o = orc.render(scene=sc, camera=w.camera, display=w.display, views=w.views, N=N, binning="quantile")
-    assert _longest_super_tile_list(o, N) > 2 * 1024   # at least three parts
+    assert G.longest_super_tile_list(o, N) > 2 * 1024   # at least three parts
     gpu = G.run_gpu(sc, w.camera, w.display, w.views, N, "quantile", dtype)
     _compare(gpu, o, o["ref"].W, o["ref"].H, N, dtype, check_lists=False)
 
