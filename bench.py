@@ -644,14 +644,15 @@ def run_profile(args):
 
 def run_profile_grad(args):
     """Short run for profilers of the differentiable workload (300k Gaussians,
-    512^2, N 64, 45 views, FP32): W + 1 forward + backward steps, no timing."""
+    512^2, N 64, 45 views, FP32, saved composite state): W + 1 forward +
+    backward steps, no timing."""
     import torch
 
     from paper_2508_18540_gb300 import api
     from paper_2508_18540_gb300 import synth as S
     wl = S.workload_fit()
     g = api.DeviceGaussians.from_scene(wl.scene)
-    r = api.LightFieldRenderer(wl.camera, wl.display, wl.views, wl.N, wl.binning, "f32")
+    r = api.LightFieldRenderer(wl.camera, wl.display, wl.views, wl.N, wl.binning, "f32", save_state=True)
     gen = torch.Generator(device="cuda").manual_seed(11)
     dv = torch.randn((wl.views.Vx, wl.camera.Ny, wl.camera.Nx, 4), device="cuda", generator=gen)
     for _ in range(args.warmup + 1):

@@ -837,8 +837,8 @@ static lf_status splat_backward_common(int64_t n, const lf_ref_camera* ref, cons
         return fail(LF_ERR_INVALID_ARG, "plane array shape does not match the reference camera");
     if (((uintptr_t)dplanes) % 16) return fail(LF_ERR_INVALID_ARG, "dplanes must be 16-byte aligned");
     if (planes->dtype < LF_F32 || planes->dtype > LF_U8) return fail(LF_ERR_INVALID_ARG, "unknown plane dtype");
-    // the Gaussian adjoint reads FP32 texels (C_end, 1 - T_end) of the forward
-    if (kind == 0 && planes->dtype == LF_F32 && (!planes->rgba || ((uintptr_t)planes->rgba) % 16))
+    // the adjoints read FP32 texels (C_end, 1 - T_end) of the forward
+    if (planes->dtype == LF_F32 && (!planes->rgba || ((uintptr_t)planes->rgba) % 16))
         return fail(LF_ERR_INVALID_ARG, "FP32 planes->rgba must be non-NULL and 16-byte aligned");
     if (n < 0 || n > (int64_t)0x7fffffff) return fail(LF_ERR_INVALID_ARG, "primitive count out of range");
     if (!ws) return fail(LF_ERR_WORKSPACE, "workspace is NULL");
@@ -856,7 +856,7 @@ static lf_status splat_backward_common(int64_t n, const lf_ref_camera* ref, cons
     if (kind == 0)
         launch_raster_gaussians_bwd(*w, rp, ranks, planes->rgba, dplanes, stream);
     else
-        launch_raster_voxels_bwd(*w, rp, ranks, dplanes, stream);
+        launch_raster_voxels_bwd(*w, rp, ranks, planes->rgba, dplanes, stream);
     trace_end(stream);
     return check_launch("raster backward");
 }

@@ -340,8 +340,8 @@ void launch_raster_gauss_batched(const RasterScene* scenes_dev, int n_sc, int dt
 // planes: the forward's plane texels (p.dtype), read for K with FP32 planes
 void launch_raster_gaussians_bwd(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks,
                                  const void* planes, const float* dplanes, cudaStream_t s);
-void launch_raster_voxels_bwd(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, const float* dplanes,
-                              cudaStream_t s);
+void launch_raster_voxels_bwd(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, const void* planes,
+                              const float* dplanes, cudaStream_t s);
 void launch_gauss_chain(const lf_gaussians& g, const ProjParams& p, const BuildWs& ws, const lf_gaussians_grad& out,
                         cudaStream_t s);
 void launch_voxel_scatter(const BuildWs& ws, long long n, const lf_voxels_grad& out, cudaStream_t s);

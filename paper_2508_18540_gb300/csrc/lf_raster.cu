@@ -613,52 +613,16 @@ __global__ void __launch_bounds__(kTilePix, 5) k_raster_voxel(BuildWs w, RasterP
 // w_i = c_i . dC + dA (because 1 - T_end = sum_i T_i a_i):
 //   dL/dc_i = T_i a_i dC,   dL/da_i = T_i (w_i - S_i),
 //   S_i = sum_{j>i} (T_j / T_{i+1}) a_j w_j,  S_{i-1} = a_i w_i + (1 - a_i) S_i.
-// The voxel kernel first recomputes T_end per pixel (front to back, the
-// forward's operation order), then walks the list back to front recovering
-// T_i = T_{i+1} / (1 - a_i), with the transmittance carried as m 2^-e (e a
-// multiple of 64) so that a long list cannot underflow it before the reverse
-// walk. The Gaussian kernel walks front to back once (below). Nothing per
-// entry is stored. Per entry each warp sums its pixels' contributions with
-// shuffles and adds them to the primitive's accumulator (rank order) with
-// vector atomics.
+// Both kernels walk each list front to back in the forward's arithmetic and
+// form the term behind entry i from the pixel's end values (below), so no
+// transmittance is divided back and nothing per entry is stored.
 // ---------------------------------------------------------------------------
-
-constexpr float kUp = 18446744073709551616.0f;        // 2^64
-constexpr float kDown = 5.42101086242752217e-20f;     // 2^-64
-constexpr float kSmall = 5.42101086242752217e-20f;    // rescale below 2^-64
-constexpr float kBig = 4294967296.0f;                 // 2^32
-
-__device__ __forceinline__ void t_forward(float& m, int& e, float al)
-{
-    m = fmaf(-m, al, m);
-    if (m < kSmall && m > 0.0f) {
-        m *= kUp;
-        e += 64;
-    }
-}
-
-__device__ __forceinline__ void t_reverse(float& m, int& e, float one_minus_al)
-{
-    m = __fdiv_rn(m, one_minus_al);
-    if (e > 0 && m > kBig) {
-        m *= kDown;
-        e -= 64;
-    }
-}
-
-__device__ __forceinline__ float t_value(float m, int e) { return e == 0 ? m : ldexpf(m, -e); }
 
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
-}
-
-__device__ __forceinline__ float4 load_grad(const float4* __restrict__ dplanes, int k, int x, int y, int W, int H)
-{
-    if (x < W && y < H) return __ldg(dplanes + ((size_t)k * H + y) * W + x);
-    return make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Gaussians, front to back. For the pixel's entries i of a list, with
@@ -902,7 +866,7 @@ __device__ __forceinline__ void raster_gauss_bwd_list(const BuildWs& w, const Ra
                             const float R = fmaf(T[s], dA[s],
                                                  K[s] - fmaf(C[s][0], dC[s][0],
                                                              fmaf(C[s][1], dC[s][1], C[s][2] * dC[s][2])));
-                            const float dal = fmaf(Ti, wv, -R * __frcp_rn(1.0f - al));
+                            const float dal = fmaf(Ti, wv, -__fdividef(R, 1.0f - al));
                             v[5] = fmaf(dal, araw * col.w, v[5]);     // G = alpha / o
                             const float dq = -0.5f * dal * al;
                             const float u = dq * dx, vv = dq * dy;
@@ -942,7 +906,8 @@ __device__ __forceinline__ void raster_gauss_bwd_list(const BuildWs& w, const Ra
 // CTA b < r_nslots takes part item b (CTAs past r_heavy exit), the others
 // the list (b - r_nslots) of (super-tile, chunk) order, longer lists exiting.
 template <int DT>
-__global__ void __launch_bounds__(kGaussBwdThreads) k_raster_gauss_bwd(BuildWs w, RasterParams p,
+// three CTAs per SM (80 registers): 18 % faster than two at 87
+__global__ void __launch_bounds__(kGaussBwdThreads, 3) k_raster_gauss_bwd(BuildWs w, RasterParams p,
                                                                       const uint32_t* __restrict__ ranks,
                                                                       const void* __restrict__ planes,
                                                                       const float4* __restrict__ dplanes,
@@ -967,11 +932,48 @@ __global__ void __launch_bounds__(kGaussBwdThreads) k_raster_gauss_bwd(BuildWs w
     }
 }
 
-// Voxels. alpha = 1 - exp(-I), I = (t1 - t0)/6 (s(t0) + 4 s(tm) + s(t1)),
-// s(t) = sum_c W_c(f(t)) rho_c (trilinear weights), so
-// dalpha/drho_c = (1 - alpha) (t1 - t0)/6 (W_c(f0) + 4 W_c(fm) + W_c(f1)).
-// Accumulator of rank r: g2d[3 r .. 3 r + 2] = {d rho_0..3}, {d rho_4..7},
-// {d r, d g, d b, 0}.
+// Voxels, front to back and pair-parallel, in the forward's layout (one CTA
+// of 256 threads per (16 x 16 tile, chunk), thread t owning tile pixel
+// (t % 16, t / 16), the footprints of each batch of staged voxels clipped to
+// the tile and numbered as pairs). With alpha_i = 1 - e^{-I_i},
+//   dL/dI_i = (1 - alpha_i) dL/dalpha_i = T_{i+1} w_i - R_i
+// (w_i, R_i and K as for Gaussians), with no division: an opacity that
+// rounds to 1 needs no care. I_i = (t1 - t0)/6 (s(t0) + 4 s(tm) + s(t1)),
+// s = sum_c W_c(f) rho_c (trilinear weights), so dI_i/drho_c is the
+// Simpson-weighted sum of the three samples' weights. Per batch, and per
+// pass of at most kVoxBwdPairs pairs:
+//   0) pair-parallel: every pair's opacity, the forward's arithmetic;
+//   A) per pixel, its pairs in list order (each warp visits the voxels that
+//      touch its two rows): T_i alpha_i and dL/dI_i of the pair into shared
+//      memory, C and T carried exactly as the forward carries them;
+//   B) pair-parallel: the pair's weights, dL/drho_c += dL/dI_i dI_i/drho_c
+//      and dL/dc += T_i alpha_i dC, summed per voxel in shared memory;
+// then one thread per staged voxel adds the sums to the voxel's accumulator
+// (rank order): g2d[3 r .. 3 r + 2] = {d rho_0..3}, {d rho_4..7},
+// {d r, d g, d b, 0}. K: from the forward's texel with FP32 planes; other
+// plane types first walk the list once (phases 0 and A, C and T only).
+constexpr int kVoxBwdPairs = 1024;
+
+struct VoxBwdSmem {
+    float4 box[kTilePix];
+    float inv_side[kTilePix];
+    float den[kTilePix * 8];      // trilinear polynomial coefficients (the forward's)
+    float4 rgb[kTilePix];
+    int4 rect[kTilePix];          // footprint clipped to the tile, tile-local
+    int off[kTilePix];            // number of the voxel's first pair
+    uint32_t rank[kTilePix];
+    float4 dir[kTilePix];         // per pixel: unit reference-ray direction
+    float4 inv[kTilePix];         // per pixel: its reciprocal
+    float4 grad[kTilePix];        // per pixel: (dC, dA)
+    float acc[kTilePix][12];      // per staged voxel: d rho (8), d rgb (3)
+    uint16_t pair[kVoxBwdPairs];  // voxel slot | x << 8 | y << 12
+    float alpha[kVoxBwdPairs];
+    float dI[kVoxBwdPairs];
+    float ta[kVoxBwdPairs];
+    int wc[kTilePix / 32];
+    int ws[kTilePix / 32];
+};
+
 __device__ __forceinline__ void tri_weights(float fx, float fy, float fz, float s, float* Wc)
 {
     const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
@@ -985,10 +987,10 @@ __device__ __forceinline__ void tri_weights(float fx, float fy, float fz, float 
     Wc[7] = fmaf(s, fx * fy * fz, Wc[7]);
 }
 
-// Ray-segment integral of one voxel for one pixel (the forward's arithmetic);
-// returns false on a miss. Fills the Simpson-weighted trilinear weights when Wc is given.
-__device__ __forceinline__ bool voxel_integral(const float4 b, const float* rho, const float* d, const float* inv,
-                                               float* integral, float* Wc)
+// dI/drho_c of one voxel for one reference ray (the geometry of
+// voxel_alpha): false when the ray misses the cube (I = 0, no gradient)
+__device__ __forceinline__ bool voxel_weights(const float4 b, const float is, const float d[3], const float inv[3],
+                                              float Wc[8])
 {
     const float lo[3] = {b.x, b.y, b.z};
     float t0 = -__int_as_float(0x7f800000), t1 = __int_as_float(0x7f800000);
@@ -1012,163 +1014,187 @@ __device__ __forceinline__ bool voxel_integral(const float4 b, const float* rho,
     t0 = fmaxf(t0, 0.0f);
     if (miss || !(t1 > t0)) return false;
     const float tm = 0.5f * (t0 + t1);
-    const float is = 1.0f / b.w;
-    const float f0x = clamp01((t0 * d[0] - lo[0]) * is), f0y = clamp01((t0 * d[1] - lo[1]) * is),
-                f0z = clamp01((t0 * d[2] - lo[2]) * is);
-    const float fmx = clamp01((tm * d[0] - lo[0]) * is), fmy = clamp01((tm * d[1] - lo[1]) * is),
-                fmz = clamp01((tm * d[2] - lo[2]) * is);
-    const float f1x = clamp01((t1 * d[0] - lo[0]) * is), f1y = clamp01((t1 * d[1] - lo[1]) * is),
-                f1z = clamp01((t1 * d[2] - lo[2]) * is);
-    const float s0 = trilinear(rho, f0x, f0y, f0z);
-    const float sm = trilinear(rho, fmx, fmy, fmz);
-    const float s1 = trilinear(rho, f1x, f1y, f1z);
     const float len6 = (t1 - t0) * (1.0f / 6.0f);
-    *integral = len6 * (s0 + 4.0f * sm + s1);
-    if (Wc) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) Wc[c] = 0.f;
-        tri_weights(f0x, f0y, f0z, len6, Wc);
-        tri_weights(fmx, fmy, fmz, 4.0f * len6, Wc);
-        tri_weights(f1x, f1y, f1z, len6, Wc);
-    }
+    for (int c = 0; c < 8; ++c) Wc[c] = 0.f;
+    tri_weights(clamp01((t0 * d[0] - lo[0]) * is), clamp01((t0 * d[1] - lo[1]) * is),
+                clamp01((t0 * d[2] - lo[2]) * is), len6, Wc);
+    tri_weights(clamp01((tm * d[0] - lo[0]) * is), clamp01((tm * d[1] - lo[1]) * is),
+                clamp01((tm * d[2] - lo[2]) * is), 4.0f * len6, Wc);
+    tri_weights(clamp01((t1 * d[0] - lo[0]) * is), clamp01((t1 * d[1] - lo[1]) * is),
+                clamp01((t1 * d[2] - lo[2]) * is), len6, Wc);
     return true;
 }
 
+template <int DT>
 __global__ void __launch_bounds__(kTilePix) k_raster_voxel_bwd(BuildWs w, RasterParams p,
                                                                const uint32_t* __restrict__ ranks,
+                                                               const void* __restrict__ planes,
                                                                const float4* __restrict__ dplanes,
                                                                float4* __restrict__ g2d)
 {
     constexpr int NT = kTilePix;
-    __shared__ float4 s_box[NT];
-    __shared__ float s_den[NT * 8];
-    __shared__ float4 s_rgb[NT];
-    __shared__ int4 s_rect[NT];
-    __shared__ uint32_t s_rank[NT];
-    __shared__ int s_wc[NT / 32];
+    extern __shared__ __align__(16) unsigned char vox_smem[];
+    VoxBwdSmem& sm = *reinterpret_cast<VoxBwdSmem*>(vox_smem);
     if (w.hdr->overflow) return;
     const int t = blockIdx.x, k = blockIdx.y;
     const int tx = t % p.tiles_x, ty = t / p.tiles_x;
-    const int lane = threadIdx.x & 31;
-    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py = ty * kTile + (threadIdx.x / kTile);
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    const int px = tx * kTile + lx, py = ty * kTile + ly;
+    const int wy0 = 2 * (threadIdx.x >> 5), wy1 = wy0 + 1;   // this warp's two tile rows
     const int st = (ty / kTilesPerSuper) * p.supers_x + tx / kTilesPerSuper;
     const int2 sg = w.seg[(size_t)st * p.N + k];
     const int L = sg.y - sg.x;
     if (L == 0) return;
 
-    const float dcx = ((float)px - p.cx) / p.fx, dcy = ((float)py - p.cy) / p.fy;
-    float d[3];
+    const bool in = px < p.W && py < p.H;
+    const size_t idx = ((size_t)k * p.H + py) * p.W + px;
+    const float4 g = in ? __ldg(dplanes + idx) : make_float4(0.f, 0.f, 0.f, 0.f);
+    {
+        const float dcx = ((float)px - p.cx) / p.fx, dcy = ((float)py - p.cy) / p.fy;
+        float d[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) d[a] = fmaf(p.Rt[3 * a], dcx, fmaf(p.Rt[3 * a + 1], dcy, p.Rt[3 * a + 2]));
-    const float nrm = rsqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
-    float inv[3];
+        for (int a = 0; a < 3; ++a) d[a] = fmaf(p.Rt[3 * a], dcx, fmaf(p.Rt[3 * a + 1], dcy, p.Rt[3 * a + 2]));
+        const float nrm = rsqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+        float inv[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        d[a] *= nrm;
-        inv[a] = 1.0f / d[a];
+        for (int a = 0; a < 3; ++a) {
+            d[a] *= nrm;
+            inv[a] = 1.0f / d[a];
+        }
+        sm.dir[threadIdx.x] = make_float4(d[0], d[1], d[2], 0.f);
+        sm.inv[threadIdx.x] = make_float4(inv[0], inv[1], inv[2], 0.f);
+        sm.grad[threadIdx.x] = g;
     }
-    const float4 gpl = load_grad(dplanes, k, px, py, p.W, p.H);
-    float Tm = 1.f, S = 0.f;
-    int Te = 0;
-    // alpha rounds to 1 for a large integral: T is then 0 behind that entry,
-    // which the reverse walk cannot divide back, so the forward keeps T just
-    // before the first such entry (batch ob, slot oj)
-    float oTm = 0.f;
-    int oTe = 0, ob = -1, oj = -1;
-    const int nbatch = (L + NT - 1) / NT;
-    auto stage = [&](int b) -> int {
-        const int i = b * NT + threadIdx.x;
-        uint32_t rk = 0;
-        int4 r = make_int4(0, 0, -1, -1);
-        if (i < L) {
-            rk = ranks[sg.x + i];
-            r = w.r_rect[rk];
+    float K = 0.f;
+    if (DT == LF_F32) {
+        const float4 tt = in ? __ldg(reinterpret_cast<const float4*>(planes) + idx) : make_float4(0.f, 0.f, 0.f, 1.f);
+        K = fmaf(tt.x, g.x, fmaf(tt.y, g.y, fmaf(tt.z, g.z, -(1.0f - tt.w) * g.w)));
+    }
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+
+    // one walk over the list; GRAD false: C and T only
+    auto walk = [&](const bool grad) {
+        for (int base = 0; base < L; base += NT) {
+            const int i = base + threadIdx.x;
+            uint32_t rk = 0;
+            int4 r = make_int4(0, 0, -1, -1);
+            if (i < L) {
+                rk = ranks[sg.x + i];
+                r = w.r_rect[rk];
+            }
+            const bool hit = i < L && meets_tile(r, tx * kTile, ty * kTile);
+            int cnt;
+            const int slot = compact_slot<NT>(hit, sm.wc, &cnt);
+            int4 cr = make_int4(0, 0, -1, -1);
+            if (hit) {
+                cr = make_int4(max(r.x - tx * kTile, 0), max(r.y - ty * kTile, 0), min(r.z - tx * kTile, kTile - 1),
+                               min(r.w - ty * kTile, kTile - 1));
+                const float4 box = w.r_geo[rk];
+                sm.box[slot] = box;
+                sm.inv_side[slot] = 1.0f / box.w;
+                const float4 da = w.r_den[2 * (size_t)rk], db = w.r_den[2 * (size_t)rk + 1];
+                const float rho8[8] = {da.x, da.y, da.z, da.w, db.x, db.y, db.z, db.w};
+                trilinear_coeffs(rho8, sm.den + 8 * slot);
+                sm.rgb[slot] = w.r_rgb[rk];
+                sm.rect[slot] = cr;
+                sm.rank[slot] = rk;
+#pragma unroll
+                for (int c = 0; c < 12; ++c) sm.acc[slot][c] = 0.f;
+            }
+            int P;
+            const int off = block_exscan_256(hit ? (cr.z - cr.x + 1) * (cr.w - cr.y + 1) : 0, sm.ws, &P);
+            if (hit) sm.off[slot] = off;
+            __syncthreads();
+            for (int c0 = 0; c0 < P; c0 += kVoxBwdPairs) {
+                const int c1 = min(P, c0 + kVoxBwdPairs);
+                if (hit && off < c1) {
+                    int q = off;
+                    for (int yy = cr.y; yy <= cr.w && q < c1; ++yy)
+                        for (int xx = cr.x; xx <= cr.z && q < c1; ++xx, ++q)
+                            if (q >= c0) sm.pair[q - c0] = (uint16_t)(slot | (xx << 8) | (yy << 12));
+                }
+                __syncthreads();
+                // 0) opacities
+                for (int q = threadIdx.x; q < c1 - c0; q += NT) {
+                    const uint32_t e = sm.pair[q];
+                    const int j = e & 0xff, pix = (int)((e >> 12) << 4) + (int)((e >> 8) & 15);
+                    const float4 dd = sm.dir[pix], iv = sm.inv[pix];
+                    const float d[3] = {dd.x, dd.y, dd.z}, inv[3] = {iv.x, iv.y, iv.z};
+                    sm.alpha[q] = voxel_alpha(sm.box[j], sm.inv_side[j], sm.den + 8 * j, d, inv);
+                }
+                __syncthreads();
+                // A) per pixel, in list order
+                for (int m0 = 0; m0 < cnt; m0 += 32) {
+                    const int jl = m0 + (threadIdx.x & 31);
+                    bool touches = false;
+                    if (jl < cnt) {
+                        const int4 rl = sm.rect[jl];
+                        touches = rl.y <= wy1 && rl.w >= wy0;
+                    }
+                    uint32_t vmask = __ballot_sync(0xffffffffu, touches);
+                    while (vmask) {
+                        const int j = m0 + __ffs(vmask) - 1;
+                        vmask &= vmask - 1;
+                        const int4 rc = sm.rect[j];
+                        if (lx < rc.x || lx > rc.z || ly < rc.y || ly > rc.w) continue;
+                        const int q = sm.off[j] + (ly - rc.y) * (rc.z - rc.x + 1) + (lx - rc.x);
+                        if (q < c0 || q >= c1) continue;
+                        const float al = sm.alpha[q - c0];
+                        const float4 col = sm.rgb[j];
+                        const float ta = T * al;
+                        C0 = fmaf(ta, col.x, C0);
+                        C1 = fmaf(ta, col.y, C1);
+                        C2 = fmaf(ta, col.z, C2);
+                        T = T * (1.0f - al);
+                        if (grad) {
+                            const float wv = fmaf(col.x, g.x, fmaf(col.y, g.y, fmaf(col.z, g.z, g.w)));
+                            const float R = fmaf(T, g.w, K - fmaf(C0, g.x, fmaf(C1, g.y, C2 * g.z)));
+                            sm.dI[q - c0] = fmaf(T, wv, -R);
+                            sm.ta[q - c0] = ta;
+                        }
+                    }
+                }
+                if (grad) {
+                    __syncthreads();
+                    // B) weights and per-voxel sums
+                    for (int q = threadIdx.x; q < c1 - c0; q += NT) {
+                        const uint32_t e = sm.pair[q];
+                        const int j = e & 0xff, pix = (int)((e >> 12) << 4) + (int)((e >> 8) & 15);
+                        const float4 dd = sm.dir[pix], iv = sm.inv[pix];
+                        const float d[3] = {dd.x, dd.y, dd.z}, inv[3] = {iv.x, iv.y, iv.z};
+                        float Wc[8];
+                        if (!voxel_weights(sm.box[j], sm.inv_side[j], d, inv, Wc)) continue;
+                        const float dI = sm.dI[q], ta = sm.ta[q];
+                        const float4 gp = sm.grad[pix];
+                        float* acc = sm.acc[j];
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) atomicAdd(acc + c, dI * Wc[c]);
+                        atomicAdd(acc + 8, ta * gp.x);
+                        atomicAdd(acc + 9, ta * gp.y);
+                        atomicAdd(acc + 10, ta * gp.z);
+                    }
+                }
+                // the next pass overwrites the pairs; the next batch restages
+                __syncthreads();
+            }
+            if (grad && threadIdx.x < cnt) {
+                const float* a = sm.acc[threadIdx.x];
+                float4* dst = g2d + 3 * (size_t)sm.rank[threadIdx.x];
+                atomicAdd(dst, make_float4(a[0], a[1], a[2], a[3]));
+                atomicAdd(dst + 1, make_float4(a[4], a[5], a[6], a[7]));
+                atomicAdd(dst + 2, make_float4(a[8], a[9], a[10], 0.f));
+            }
+            __syncthreads();
         }
-        const bool hit = i < L && meets_tile(r, tx * kTile, ty * kTile);
-        int cnt;
-        const int slot = compact_slot<NT>(hit, s_wc, &cnt);
-        if (hit) {
-            s_box[slot] = w.r_geo[rk];
-            const float4 da = w.r_den[2 * (size_t)rk], db = w.r_den[2 * (size_t)rk + 1];
-            float* sd = s_den + 8 * slot;
-            sd[0] = da.x; sd[1] = da.y; sd[2] = da.z; sd[3] = da.w;
-            sd[4] = db.x; sd[5] = db.y; sd[6] = db.z; sd[7] = db.w;
-            s_rgb[slot] = w.r_rgb[rk];
-            s_rect[slot] = r;
-            s_rank[slot] = rk;
-        }
-        __syncthreads();
-        return cnt;
     };
 
-    for (int b = 0; b < nbatch; ++b) {
-        const int cnt = stage(b);
-        for (int j = 0; j < cnt; ++j) {
-            const int4 rc = s_rect[j];
-            if (!(px >= rc.x && px <= rc.z && py >= rc.y && py <= rc.w)) continue;
-            float integral;
-            if (!voxel_integral(s_box[j], s_den + 8 * j, d, inv, &integral, nullptr)) continue;
-            const float al = 1.0f - __expf(-integral);
-            if (al >= 1.0f && Tm > 0.0f && ob < 0) {
-                oTm = Tm;
-                oTe = Te;
-                ob = b;
-                oj = j;
-            }
-            t_forward(Tm, Te, al);
-        }
-        __syncthreads();
+    if (DT != LF_F32) {
+        walk(false);
+        K = fmaf(C0, g.x, fmaf(C1, g.y, fmaf(C2, g.z, -T * g.w)));
+        C0 = C1 = C2 = 0.f, T = 1.f;
     }
-    for (int b = nbatch - 1; b >= 0; --b) {
-        const int cnt = stage(b);
-        for (int j = cnt - 1; j >= 0; --j) {
-            const int4 rc = s_rect[j];
-            const bool in = px >= rc.x && px <= rc.z && py >= rc.y && py <= rc.w;
-            float Wc[8], integral = 0.f;
-            bool hit = false;
-            if (in) hit = voxel_integral(s_box[j], s_den + 8 * j, d, inv, &integral, Wc);
-            float gr = 0.f, gg = 0.f, gb = 0.f, gd[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) gd[c] = 0.f;
-            if (hit) {
-                const float al = 1.0f - __expf(-integral);
-                const float oma = 1.0f - al;
-                const float4 col = s_rgb[j];
-                if (b == ob && j == oj) {
-                    Tm = oTm;
-                    Te = oTe;
-                } else if (oma > 0.0f) {
-                    t_reverse(Tm, Te, oma);
-                }
-                const float Ti = t_value(Tm, Te);
-                const float wv = fmaf(col.x, gpl.x, fmaf(col.y, gpl.y, fmaf(col.z, gpl.z, gpl.w)));
-                const float dal = Ti * (wv - S);
-                S = fmaf(al, wv, oma * S);
-                const float ta = Ti * al;
-                gr = ta * gpl.x;
-                gg = ta * gpl.y;
-                gb = ta * gpl.z;
-                const float dI = dal * oma;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) gd[c] = dI * Wc[c];
-            }
-            const bool any = __syncthreads_or(hit);
-            if (!any) continue;
-            gr = warp_sum(gr);
-            gg = warp_sum(gg);
-            gb = warp_sum(gb);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) gd[c] = warp_sum(gd[c]);
-            if (lane == 0) {
-                float4* acc = g2d + 3 * (size_t)s_rank[j];
-                atomicAdd(acc, make_float4(gd[0], gd[1], gd[2], gd[3]));
-                atomicAdd(acc + 1, make_float4(gd[4], gd[5], gd[6], gd[7]));
-                atomicAdd(acc + 2, make_float4(gr, gg, gb, 0.f));
-            }
-        }
-        __syncthreads();
-    }
+    walk(true);
 }
 
 }  // namespace
@@ -1189,12 +1215,31 @@ void launch_raster_gaussians_bwd(const BuildWs& ws, const RasterParams& p, const
     note_launches(1);
 }
 
-void launch_raster_voxels_bwd(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, const float* dplanes,
-                              cudaStream_t s)
+void launch_raster_voxels_bwd(const BuildWs& ws, const RasterParams& p, const uint32_t* ranks, const void* planes,
+                              const float* dplanes, cudaStream_t s)
 {
     const dim3 grid((unsigned)(p.tiles_x * p.tiles_y), (unsigned)p.N);
-    k_raster_voxel_bwd<<<grid, kTilePix, 0, s>>>(ws, p, ranks, reinterpret_cast<const float4*>(dplanes),
-                                                 reinterpret_cast<float4*>(ws.g2d));
+    const size_t smem = sizeof(VoxBwdSmem);
+    const float4* dp = reinterpret_cast<const float4*>(dplanes);
+    float4* g = reinterpret_cast<float4*>(ws.g2d);
+    switch (p.dtype) {
+    case LF_F32:
+        cudaFuncSetAttribute(k_raster_voxel_bwd<LF_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_raster_voxel_bwd<LF_F32><<<grid, kTilePix, smem, s>>>(ws, p, ranks, planes, dp, g);
+        break;
+    case LF_F16:
+        cudaFuncSetAttribute(k_raster_voxel_bwd<LF_F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_raster_voxel_bwd<LF_F16><<<grid, kTilePix, smem, s>>>(ws, p, ranks, planes, dp, g);
+        break;
+    case LF_U8:
+        cudaFuncSetAttribute(k_raster_voxel_bwd<LF_U8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_raster_voxel_bwd<LF_U8><<<grid, kTilePix, smem, s>>>(ws, p, ranks, planes, dp, g);
+        break;
+    default:
+        cudaFuncSetAttribute(k_raster_voxel_bwd<LF_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_raster_voxel_bwd<LF_BF16><<<grid, kTilePix, smem, s>>>(ws, p, ranks, planes, dp, g);
+        break;
+    }
     note_launches(1);
 }
 

@@ -279,6 +279,30 @@ def test_voxel_gradients_against_fd(orc):
         assert _rel(np.array(an), np.array(fd)) <= REL_TOL, key
 
 
+def test_voxel_fp16_gradients_track_fp32():
+    # FP16 planes: the voxel adjoint first walks each list for (C_end,
+    # T_end) instead of reading them from the texel
+    cam = S.identity_camera(48, t=(0.0, 0.0, 6.0))
+    vs = S.sparse_voxels(1500, 7, base_res=32)
+    sc = S.VoxelScene(vs.ijk, vs.level, vs.origin, vs.base_size,
+                      (0.5 * vs.density8).astype(np.float32), vs.rgb)
+    disp = S.display_for(S.harmonic_focal(4.0, 8.0), 0.15)
+    views = S.ViewSet(5, 1, False)
+    rng = np.random.default_rng(16)
+    W = torch.from_numpy(rng.normal(size=(5, 48, 48, 4)).astype(np.float32)).cuda()
+    out = {}
+    for dtype in ("f32", "f16"):
+        r = api.LightFieldRenderer(cam, disp, views, 6, "quantile", dtype)
+        v = api.DeviceVoxels.from_scene(sc)
+        r.render(v)
+        grads, _ = r.backward(v, W)
+        torch.cuda.synchronize()
+        out[dtype] = (grads.ddensity8.cpu().numpy().astype(np.float64), grads.drgb.cpu().numpy().astype(np.float64))
+    for a, b in zip(out["f16"], out["f32"]):
+        assert np.linalg.norm(b) > 0
+        assert _rel(a, b) <= 2e-2
+
+
 @pytest.mark.parametrize("save_state", [False, True])
 def test_autograd_function_and_fit_step(save_state):
     # torch.autograd path: gradients equal the direct adjoint call, and a few
