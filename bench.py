@@ -66,9 +66,9 @@ def _config(extra=None):
 # with them.
 NCU_TRAFFIC = {
     # the raster stage's two kernels: the parts of split lists and the lists
-    "raster_gaussians": (71_478_016 + 11_970_560 + 207_899_136, ("lf_raster.cu", "lf_internal.cuh"),
-                         "5173da5cabd3e411"),
-    "composite": (253_311_232 + 153_777_408, ("lf_composite.cu", "lf_internal.cuh"), "b94e072075d79b80"),
+    "raster_gaussians": (11_974_656 + 0 + 71_355_904 + 204_294_144, ("lf_raster.cu", "lf_internal.cuh"),
+                         "108b044d1ac58be0"),
+    "composite": (252_995_328 + 149_867_520, ("lf_composite.cu", "lf_internal.cuh"), "db9544c42571e6ad"),
 }
 
 
@@ -440,7 +440,8 @@ def run_differentiable(args, dev, fit_target=None):
     projection chain rule) per step, FP32; then a fit of all five parameter
     groups (means, scales, quaternions, opacities, colours) by Adam against
     target views of a perturbed copy of the scene (means + N(0, 0.01),
-    opacities + N(0, 0.05)) rendered by the FP64 oracle, with its loss curve."""
+    opacities + N(0, 0.05)) rendered by the FP64 oracle, with its loss curve;
+    then forward and backward of the 2M-voxel V2LF workload (FP32 planes)."""
     import torch
     from paper_2508_18540_gb300 import api
     from paper_2508_18540_gb300 import autograd as AG
@@ -483,32 +484,60 @@ def run_differentiable(args, dev, fit_target=None):
     else:
         target = torch.as_tensor(fit_target, dtype=torch.float32).to(dev)
         source = "FP64 oracle render of the perturbed scene"
-    params = [t.clone().requires_grad_(True) for t in (g.means, g.scales, g.quats, g.opacity, g.rgb)]
     lrs = [1e-3, 1e-4, 1e-3, 1e-2, 1e-2]
-    opt = torch.optim.Adam([{"params": [p], "lr": lr} for p, lr in zip(params, lrs)])
+
+    def fit(n_steps):
+        params = [t.clone().requires_grad_(True) for t in (g.means, g.scales, g.quats, g.opacity, g.rgb)]
+        opt = torch.optim.Adam([{"params": [p], "lr": lr} for p, lr in zip(params, lrs)])
+        losses = []
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(n_steps):
+            opt.zero_grad(set_to_none=True)
+            v = AG.render_gaussians(r, *params)
+            loss = ((v - target) ** 2).sum()
+            loss.backward()
+            opt.step()
+            with torch.no_grad():
+                params[1].clamp_(min=1e-6)
+                params[3].clamp_(0.01, 0.99)
+            losses.append(loss.detach())
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / n_steps, losses
+
+    # warm-up steps from the same start, not kept: the first optimizer step
+    # and the first backward pass through torch.autograd load their Python
+    # modules and start autograd's device thread (seconds on a cold host)
+    fit(max(3, args.warmup))
     n_steps = 40
-    losses = []
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(n_steps):
-        opt.zero_grad(set_to_none=True)
-        v = AG.render_gaussians(r, *params)
-        loss = ((v - target) ** 2).sum()
-        loss.backward()
-        opt.step()
-        with torch.no_grad():
-            params[1].clamp_(min=1e-6)
-            params[3].clamp_(0.01, 0.99)
-        losses.append(loss.detach())
-    e1.record(st)
-    e1.synchronize()
-    fit_ms = e0.elapsed_time(e1) / n_steps
+    fit_ms, losses = fit(n_steps)
     curve = [float(x) for x in torch.stack(losses).cpu()]
     out["fit"] = {"target": source, "parameters": ["means", "scales", "quats", "opacity", "rgb"],
                   "optimizer": "Adam (torch), lr %s" % lrs, "loss": "sum of squared view differences",
                   "steps": n_steps, "ms_per_step": round(fit_ms, 3), "steps_per_s": round(1000.0 / fit_ms, 2),
                   "loss_first": curve[0], "loss_last": curve[-1], "loss_curve": [round(x, 3) for x in curve]}
+    del r
+    # the voxel model's adjoint: the V2LF workload (2M voxels), FP32 planes
+    vw = _voxel_workload()
+    vv = api.DeviceVoxels.from_scene(vw.scene, device=dev)
+    rv = api.LightFieldRenderer(vw.camera, vw.display, vw.views, vw.N, vw.binning, "f32", device=dev,
+                                save_state=True)
+    dvv = torch.randn((vw.views.Vx, vw.camera.Ny, vw.camera.Nx, 4), device=dev)
+    n_v = max(3, args.steps // 4)
+    vf = _event_ms(lambda: rv.render(vv), n_v, 2, st)
+    vb = _event_ms(lambda: rv.backward(vv, dvv), n_v, 2, st)
+    api.lf_trace_collect()
+    api.lf_trace_enable(True)
+    rv.render(vv)
+    rv.backward(vv, dvv)
+    torch.cuda.synchronize()
+    api.lf_trace_enable(False)
+    out["voxels"] = {"workload": vw.name, "voxels": vw.scene.n, "forward_ms": round(vf, 4),
+                     "backward_ms": round(vb, 4),
+                     "stages_ms": {k: round(t / c, 4) for k, (t, c) in api.lf_trace_collect().items()},
+                     "gradient_check": "tests/test_gpu_grad.py (finite differences of the FP64 oracle)"}
     return out
 
 
@@ -643,9 +672,9 @@ def run_profile(args):
 
 
 def run_profile_grad(args):
-    """Short run for profilers of the differentiable workload (300k Gaussians,
-    512^2, N 64, 45 views, FP32, saved composite state): W + 1 forward +
-    backward steps, no timing."""
+    """Short run for profilers of the differentiable workloads (300k Gaussians,
+    then 2M voxels; 512^2, N 64, 45 views, FP32, saved composite state): W + 1
+    forward + backward steps of each, no timing."""
     import torch
 
     from paper_2508_18540_gb300 import api
@@ -660,6 +689,17 @@ def run_profile_grad(args):
         r.backward(g, dv)
     torch.cuda.synchronize()
     print("profile grad: composite status %d" % r.composite_status(), flush=True)
+    del r
+    # then the 2M-voxel V2LF workload, FP32 planes
+    vw = _voxel_workload()
+    v = api.DeviceVoxels.from_scene(vw.scene)
+    rv = api.LightFieldRenderer(vw.camera, vw.display, vw.views, vw.N, vw.binning, "f32", save_state=True)
+    dvv = torch.randn((vw.views.Vx, vw.camera.Ny, vw.camera.Nx, 4), device="cuda", generator=gen)
+    for _ in range(args.warmup + 1):
+        rv.render(v)
+        rv.backward(v, dvv)
+    torch.cuda.synchronize()
+    print("profile grad voxels: composite status %d" % rv.composite_status(), flush=True)
 
 
 def _oracle_rate(wl, min_seconds, max_frames):
