@@ -365,7 +365,10 @@ lf_status lf_composite_backward_saved(const lf_planes* planes, const lf_ref_came
  * of the forward call and ws (ws_bytes) the workspace that call used,
  * unchanged since: the adjoint reads the forward's depth order, rank-ordered
  * records and tile lists from it. After an overflowed build the gradients are
- * all 0 (lf_mpi_status reports the overflow). Errors: LF_ERR_INVALID_ARG,
+ * all 0 (lf_mpi_status reports the overflow). The adjoint is that of exact
+ * blending; after a forward with LF_BLEND_3DGS it returns the exact-blending
+ * gradient of the same structure. With FP32 planes it reads the forward's
+ * texels (planes->rgba, 16-byte aligned). Errors: LF_ERR_INVALID_ARG,
  * LF_ERR_WORKSPACE, LF_ERR_CUDA. */
 lf_status lf_build_mpi_backward_gaussians(const lf_gaussians* g, const lf_ref_camera* ref, const lf_planes* planes,
                                           const float* dplanes, lf_gaussians_grad* grad, void* ws, size_t ws_bytes,
