@@ -122,6 +122,8 @@ constexpr float kDownB = 5.42101086242752217e-20f;    // 2^-64
 constexpr float kBigB = 4294967296.0f;                // 2^32
 __device__ __forceinline__ float scaled_t(float m, int e) { return e == 0 ? m : (e == 64 ? m * kDownB : 0.0f); }
 
+// plain forms: T below this is taken as 0 at every fourth non-empty plane
+constexpr float kTFlush = 5.9604644775390625e-8f;   // 2^-24
 // saving forms: a walk stops once T would fall below this (taken as 0)
 constexpr float kTStop = 5.42101086242752217e-20f;   // 2^-64
 constexpr int kCompBX = 32, kCompBY = 8;
@@ -158,8 +160,16 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
     const size_t plane_sz = (size_t)p.W * p.H;
     float Q0 = 0.f, Q1 = 0.f, Q2 = 0.f, T = 1.f;
     int kq = -1;   // saving form: the plane the walk stopped at (blend_texel)
+    int q = 0;     // non-empty planes so far
     for (int k = 0; k < p.N; ++k) {
         if (s_cnt[k] == 0) continue;
+        // plain form: the staged kernels' flush of T below 2^-24 (flush_tiny),
+        // at the same list positions
+        if (!SAVE && (q & 3) == 0 && q > 0 && T < kTFlush) {
+            T = 0.0f;
+            break;
+        }
+        ++q;
         const float* c = s_coef + 6 * k;
         float4 tx = make_float4(0.f, 0.f, 0.f, 0.f);
         if (!BILINEAR) {
@@ -563,6 +573,20 @@ __device__ __forceinline__ void blend_blended_row(float (&acc)[VG][4], float4 hd
     }
 }
 
+// Plain form, before every fourth non-empty plane of the list: a view whose
+// transmittance has fallen below kTFlush = 2^-24 (the FP32 spacing at 1)
+// takes T = 0, so the planes behind it add nothing; what they would still
+// add is below 2^-24 of a colour's range per channel, and the output's
+// 1 - T moves by less than 2^-24. The decision depends on the view pixel's
+// own walk and the list position only, so every layout of the work
+// (views per thread, tiles, batch plans) gives the same bits.
+template <int VG>
+__device__ __forceinline__ void flush_tiny(float (&acc)[VG][4])
+{
+#pragma unroll
+    for (int jj = 0; jj < VG; ++jj) acc[jj][3] = acc[jj][3] < kTFlush ? 0.0f : acc[jj][3];
+}
+
 // Every view of this thread has T == 0 exactly (or the thread is idle).
 // T never leaves 0 (T <- T - T A), and behind it a plane adds T c = 0 to Q
 // and leaves T = 0, so skipping such planes changes no bit of the output.
@@ -773,7 +797,10 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_com
             // bilinear: keep meeting the per-plane CTA barrier (results discarded)
             if (!BILINEAR) break;
         }
-        if ((q & 3) == 0 && q > 0 && !warp_sat) warp_sat = __all_sync(0xffffffffu, saturated<VG, SAVE>(acc, live));
+        if ((q & 3) == 0 && q > 0 && !warp_sat) {
+            if (!SAVE) flush_tiny<VG>(acc);
+            warp_sat = __all_sync(0xffffffffu, saturated<VG, SAVE>(acc, live));
+        }
         if constexpr (BILINEAR) {
             // the threads of an output row blend interior texels tx, tx + TX,
             // ... of its two staged rows into the FP32 row buffer
@@ -963,8 +990,10 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_com
                     ok = false;
                     break;
                 }
-                if ((q & 3) == 0 && q > 0 && !warp_sat)
+                if ((q & 3) == 0 && q > 0 && !warp_sat) {
+                    flush_tiny<VG>(acc);
                     warp_sat = __all_sync(0xffffffffu, saturated<VG>(acc, live));
+                }
                 if (live && !warp_sat) {
                     const uint32_t ca = coef_a + 4u * (uint32_t)(q * CW);
                     const uint32_t sb = stage_a + (uint32_t)st * stage_stride;
