@@ -68,7 +68,7 @@ NCU_TRAFFIC = {
     # the raster stage's two kernels: the parts of split lists and the lists
     "raster_gaussians": (11_974_656 + 0 + 71_355_904 + 204_294_144, ("lf_raster.cu", "lf_internal.cuh"),
                          "108b044d1ac58be0"),
-    "composite": (252_995_328 + 149_867_520, ("lf_composite.cu", "lf_internal.cuh"), "db9544c42571e6ad"),
+    "composite": (253_057_792 + 152_613_120, ("lf_composite.cu", "lf_internal.cuh"), "495c1e18b0bb95c0"),
 }
 
 
