@@ -335,8 +335,8 @@ size_t lf_composite_state_size(const lf_ref_camera* ref, const lf_view_set* view
 
 /* lf_composite (Sec. 4.3, Eq. alpha_blend) in its saving form: each view
  * pixel's walk stops at the first plane k behind which T would fall below
- * 2^-64 (to 0 behind a plane with A = 1); plane k still blends, the colour
- * of the planes behind it (below 2^-64 each) is dropped and the output's
+ * 2^-24 (to 0 behind a plane with A = 1); plane k still blends, the colour
+ * of the planes behind it (below 2^-24 each) is dropped and the output's
  * T is 0. Otherwise the same views as lf_composite. Per view pixel it also
  * writes the state the adjoint starts from to state [Vy*Vx][Ny][Nx] of four
  * 32-bit words (device, 16-byte aligned, state_bytes >=
@@ -352,7 +352,7 @@ lf_status lf_composite_save(const lf_planes* planes, const lf_ref_camera* ref, c
 /* lf_composite_backward from the state lf_composite_save wrote for the same
  * planes, ref and views: one back-to-front walk over the planes instead of
  * two. The planes behind a pixel's stop plane get no gradient from it (their
- * T, below 2^-64, is taken as 0); otherwise the same gradients up to FP32
+ * T, below 2^-24, is taken as 0); otherwise the same gradients up to FP32
  * rounding. Same contract and errors as lf_composite_backward, and
  * LF_ERR_INVALID_ARG for a NULL, misaligned or short state. */
 lf_status lf_composite_backward_saved(const lf_planes* planes, const lf_ref_camera* ref, const lf_view_set* views,

@@ -124,8 +124,9 @@ __device__ __forceinline__ float scaled_t(float m, int e) { return e == 0 ? m : 
 
 // plain forms: T below this is taken as 0 at every fourth non-empty plane
 constexpr float kTFlush = 5.9604644775390625e-8f;   // 2^-24
-// saving forms: a walk stops once T would fall below this (taken as 0)
-constexpr float kTStop = 5.42101086242752217e-20f;   // 2^-64
+// saving forms: a walk stops once T would fall below this (taken as 0), the
+// plain forms' flush threshold
+constexpr float kTStop = kTFlush;
 constexpr int kCompBX = 32, kCompBY = 8;
 
 // Unstaged fallback (planes read through L1/L2), used when the staged kernel's
@@ -410,7 +411,7 @@ __device__ __forceinline__ ThreadGeom thread_geom(const CompParams& p, const Sta
 // blends with its T_q, q goes to the thread's stop slot of the view in
 // shared memory (stop_a + 4 jj kStagedThreads), and a[3] = -T_q marks the
 // view as stopped (T_q >= kTStop > 0; T = 0 from there on, the colour the
-// plain form would still add being below 2^-64 per plane). The kernel
+// plain form would still add being below 2^-24 per plane). The kernel
 // stores the state at the end of its walk.
 // store q to view J's stop slot ([stop_a + immediate]: no address register
 // per view)
@@ -691,7 +692,7 @@ __device__ __forceinline__ void zero_pads(const CompParams& p, const StagedGeom&
 
 // SAVE: also writes, per view pixel, the state the adjoint's back-to-front
 // walk starts from, state[(v Ny + y) Nx + x] = {T_k, bits of k, 0, 0}: k the
-// plane behind which T falls below 2^-64 (and is taken as 0), T_k the
+// plane behind which T falls below 2^-24 (and is taken as 0), T_k the
 // transmittance in front of it; or k = N and the transmittance behind the
 // last plane (see blend_texel).
 template <int DT, bool BILINEAR, int VG, bool SAVE = false>
@@ -1522,6 +1523,17 @@ __global__ void __launch_bounds__(kStagedBlock, VG > 5 ? 1 : 2) k_composite_bwd_
         g[jj] = vv ? dviews[view_pixel(p, vi * p.Vx + j0 + jj, x, y)] : make_float4(0.f, 0.f, 0.f, 0.f);
         B[jj] = fmaf(g[jj].x, p.bg[0], fmaf(g[jj].y, p.bg[1], fmaf(g[jj].z, p.bg[2], -g[jj].w)));
     }
+    // from the state: the planes behind the last stop plane of the warp's
+    // views carry T = 0 for all of them, and their share of B is scaled by a
+    // transmittance below the stop threshold; the warp walks from there
+    int kmax = -1;
+    if (FS) {
+        int km = -1;
+#pragma unroll
+        for (int jj = 0; jj < VG; ++jj)
+            if (live && j0 + jj < p.Vx) km = max(km, okq[jj] >= 0 ? okq[jj] : p.N);
+        kmax = __reduce_max_sync(0xffffffffu, km);
+    }
     // back to front: T recovered by division, texel gradients, B recurrence
     for (; q < 2 * P; ++q) {
         const int r = q - q0;
@@ -1530,7 +1542,7 @@ __global__ void __launch_bounds__(kStagedBlock, VG > 5 ? 1 : 2) k_composite_bwd_
             atomicExch(w.err, 1);
             return;
         }
-        if (live) {
+        if (live && (!FS || plist[entry(q)] <= kmax)) {
             const int e = entry(q);
             const uint32_t sb = stage_a + (uint32_t)(st * G.stage_bytes) + tg.row0;
             const float4 hdr = lds_f4(coef_a + 4u * (uint32_t)(e * CW));
@@ -1587,7 +1599,7 @@ __global__ void __launch_bounds__(kStagedBlock, VG > 5 ? 1 : 2) k_composite_bwd_
                 }
                 const float oma = 1.0f - t.w;
                 if constexpr (FS) {
-                    // T in [2^-64, 1] from the stop plane on, 0 behind it: no scaling
+                    // T in [2^-24, 1] from the stop plane on, 0 behind it: no scaling
                     if (plist[e] == okq[jj])
                         Tm[jj] = oTm[jj];
                     else if (oma > 0.0f)
