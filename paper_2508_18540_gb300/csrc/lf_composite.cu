@@ -1242,8 +1242,17 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite_bwd(CompParams p
         else
             Tm = sv.x;
     }
+    int nq = 0;   // non-empty planes so far (the forward's flush positions)
     for (int k = 0; k < (FS ? 0 : p.N); ++k) {
         if (s_cnt[k] == 0) continue;
+        if ((nq & 3) == 0 && nq > 0 && ok < 0 && (Te == 0 ? Tm : ldexpf(Tm, -Te)) < kTFlush) {
+            // the plain composite's flush: T is 0 from this plane on
+            oTm = Tm;
+            oTe = Te;
+            ok = k;
+            Tm = 0.0f;
+        }
+        ++nq;
         const float4 tx = sample(k, taps(k));
         const float oma = 1.0f - tx.w;
         if (!(oma > 0.0f) && Tm > 0.0f && ok < 0) {
@@ -1449,15 +1458,33 @@ __global__ void __launch_bounds__(kStagedBlock, VG > 5 ? 1 : 2) k_composite_bwd_
         }
     }
     int q = q0;
+    bool walk_done = false;   // two walks: every view of the warp has stopped (warp-uniform)
     // front to back: transmittance at the far end, and T before the first
-    // opaque plane (alpha only)
+    // opaque plane (alpha only). The plain composite's flush (flush_tiny) is
+    // followed too: at the same list positions a view whose T has fallen
+    // below 2^-24 stops there, as before an opaque plane, and a warp whose
+    // views have all stopped walks no further
     for (; q < P; ++q) {
         const int st = q % kStages;   // q0 == 0 here
         if (!mbar_wait_bounded(smem_addr(&full[st]), (uint32_t)((q / kStages) & 1))) {
             atomicExch(w.err, 1);
             return;
         }
-        if (live) {
+        if ((q & 3) == 0 && q > 0 && !walk_done) {
+            bool all = true;
+#pragma unroll
+            for (int jj = 0; jj < VG; ++jj) {
+                if (okq[jj] < 0 && scaled_t(Tm[jj], Te[jj]) < kTFlush) {
+                    oTm[jj] = Tm[jj];
+                    oTe[jj] = Te[jj];
+                    okq[jj] = q;
+                    Tm[jj] = 0.0f;
+                }
+                all = all && (okq[jj] >= 0 || j0 + jj >= p.Vx);
+            }
+            walk_done = __all_sync(0xffffffffu, all || !live);
+        }
+        if (live && !walk_done) {
             const uint32_t sb = stage_a + (uint32_t)(st * G.stage_bytes) + tg.row0;
             const float4 hdr = lds_f4(coef_a + 4u * (uint32_t)(q * CW));
             float c[NC];
@@ -1526,14 +1553,12 @@ __global__ void __launch_bounds__(kStagedBlock, VG > 5 ? 1 : 2) k_composite_bwd_
     // from the state: the planes behind the last stop plane of the warp's
     // views carry T = 0 for all of them, and their share of B is scaled by a
     // transmittance below the stop threshold; the warp walks from there
-    int kmax = -1;
-    if (FS) {
-        int km = -1;
+    // (two walks: the same for the list entries behind the last stop)
+    int km = -1;
 #pragma unroll
-        for (int jj = 0; jj < VG; ++jj)
-            if (live && j0 + jj < p.Vx) km = max(km, okq[jj] >= 0 ? okq[jj] : p.N);
-        kmax = __reduce_max_sync(0xffffffffu, km);
-    }
+    for (int jj = 0; jj < VG; ++jj)
+        if (live && j0 + jj < p.Vx) km = max(km, okq[jj] >= 0 ? okq[jj] : (FS ? p.N : P));
+    const int kmax = __reduce_max_sync(0xffffffffu, km);
     // back to front: T recovered by division, texel gradients, B recurrence
     for (; q < 2 * P; ++q) {
         const int r = q - q0;
@@ -1542,7 +1567,7 @@ __global__ void __launch_bounds__(kStagedBlock, VG > 5 ? 1 : 2) k_composite_bwd_
             atomicExch(w.err, 1);
             return;
         }
-        if (live && (!FS || plist[entry(q)] <= kmax)) {
+        if (live && (FS ? plist[entry(q)] : entry(q)) <= kmax) {
             const int e = entry(q);
             const uint32_t sb = stage_a + (uint32_t)(st * G.stage_bytes) + tg.row0;
             const float4 hdr = lds_f4(coef_a + 4u * (uint32_t)(e * CW));
