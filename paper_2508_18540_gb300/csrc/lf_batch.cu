@@ -235,8 +235,11 @@ lf_status lf_batch_prepare(lf_batch* b, const lf_batch_plan* plan, void* ws, siz
                                                   cudaSuccess)
         return check_launch("device query");
     const size_t smem = composite_batched_smem(max_stage, maxN, pl.views_per_thread);
-    // views per thread above kTwoCtaViews take up to 96 registers: one CTA per SM
-    b->c_ctas = sms * ((pl.views_per_thread <= kTwoCtaViews && 2 * (smem + 1024) <= 228 * 1024) ? 2 : 1);
+    // CTAs per SM: the composite's launch bounds aim at four (views per
+    // thread up to kTwoCtaViews) or two, as shared memory allows
+    int per_sm = pl.views_per_thread <= kTwoCtaViews ? 4 : 2;
+    while (per_sm > 1 && (size_t)per_sm * (smem + 1024) > (size_t)228 * 1024) --per_sm;
+    b->c_ctas = sms * per_sm;
     if (cudaMemcpyAsync(b->rtab, b->rhost.data(), sizeof(RasterScene) * n, cudaMemcpyHostToDevice, stream) !=
             cudaSuccess ||
         cudaMemcpyAsync(b->ctab, b->chost.data(), sizeof(CompScene) * n, cudaMemcpyHostToDevice, stream) !=

@@ -254,6 +254,8 @@ __global__ void __launch_bounds__(kCompBX* kCompBY) k_composite(CompParams p, co
 
 constexpr int kStagedWarps = kStagedThreads / 32;     // consumer warps
 constexpr int kStagedBlock = kStagedThreads + 32;     // + one producer warp
+constexpr int kBwdWarps = kBwdStagedThreads / 32;     // the adjoint's
+constexpr int kBwdBlock = kBwdStagedThreads + 32;
 constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
 
@@ -352,13 +354,15 @@ inline size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 }  // namespace
 
 // Staged layout of one composite: TX columns x BY rows per CTA (TX a
-// multiple of 32 not above tx_max, BY = 512 / TX), VG views per thread.
-StagedGeom staged_geom(const CompParams& p, int texel_bytes, bool bilinear, int VG, int tx_max)
+// multiple of 32 not above tx_max or the consumer threads, BY = threads /
+// TX), VG views per thread.
+StagedGeom staged_geom(const CompParams& p, int texel_bytes, bool bilinear, int VG, int tx_max, int threads)
 {
     StagedGeom G;
     const int nx32 = (p.Nx + 31) / 32 * 32;
     G.TX = nx32 < tx_max ? nx32 : tx_max;
-    G.BY = kStagedThreads / G.TX;
+    if (G.TX > threads) G.TX = threads;
+    G.BY = threads / G.TX;
     G.VG = VG;
     G.rows_per_y = bilinear ? 2 : 1;
     G.padl = 16 / texel_bytes;
@@ -370,10 +374,10 @@ StagedGeom staged_geom(const CompParams& p, int texel_bytes, bool bilinear, int 
     const size_t fixed = G.blend_bytes + 2 * kStages * 8 + sizeof(float) * (size_t)p.N * (4 + 4 * ((VG + 3) / 4)) +
                          sizeof(int) * (size_t)p.N;
     // a bilinear stage is released once its rows are blended, so a shallower
-    // ring suffices; keep two CTAs per SM where the blend rows would not fit
-    // (view groups wider than kTwoCtaViews run one CTA per SM: no such limit)
+    // ring suffices: keep the CTAs per SM the launch bounds aim at (two for
+    // view groups wider than kTwoCtaViews, four below) where they fit
     G.stages = kStages;
-    const size_t budget = VG > kTwoCtaViews ? (size_t)200 * 1024 : kTwoCtaSmem;
+    const size_t budget = VG > kTwoCtaViews ? kTwoCtaSmem : kTwoCtaSmem / 2;
     while (bilinear && G.stages > 3 && G.stages * G.stage_bytes + fixed > budget) --G.stages;
     G.smem_bytes = G.stages * G.stage_bytes + fixed;
     return G;
@@ -696,7 +700,7 @@ __device__ __forceinline__ void zero_pads(const CompParams& p, const StagedGeom&
 // transmittance in front of it; or k = N and the transmittance behind the
 // last plane (see blend_texel).
 template <int DT, bool BILINEAR, int VG, bool SAVE = false>
-__global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_composite_staged(CompParams p, StagedGeom G,
+__global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 2 : 4) k_composite_staged(CompParams p, StagedGeom G,
                                                                         const char* __restrict__ planes,
                                                                         const int32_t* __restrict__ count, CompWs w,
                                                                         float* __restrict__ out,
@@ -889,7 +893,7 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_com
 // stops taking items.
 // ---------------------------------------------------------------------------
 template <int DT, bool BILINEAR, int VG>
-__global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 1 : 2) k_composite_batched(const CompScene* __restrict__ scs, int n_sc,
+__global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 2 : 4) k_composite_batched(const CompScene* __restrict__ scs, int n_sc,
                                                                          long long total,
                                                                          unsigned long long* __restrict__ counter,
                                                                          size_t max_stage_bytes, int maxN)
@@ -1065,19 +1069,17 @@ bool launch_staged_vg(const CompParams& p, const void* planes, const int32_t* co
 // Views per thread of the staged composite, from {15, 9, 5, 3} (at most Vx,
 // or 3): the one with the least padded work, ceil(Vx / VG) (VG + 3) -- a view
 // group's fixed cost (plane list, coefficient block, staging every plane's
-// rows) measured worth about three views. Groups of 15 run one CTA per SM at
-// up to 96 registers; 9 at two CTAs per SM spills a little, and bilinear
-// FP32 (four-channel FP32 taps) spills more, so it skips 9. Measured on 45
-// views of 512^2, N 64: 15 beats 9 by 4 % (FP32) to 8 % (FP16) nearest and
-// 7-15 % bilinear.
-// The saving form (two more live words per view) takes 5 at most: wider
-// groups spill.
-inline int staged_views_per_thread(int Vx, bool no9, int max_vg = 15)
+// rows) measured worth about three views. Groups of 15 run two CTAs of 256
+// consumer threads per SM; 9 at four spills a little, and bilinear FP32
+// (four-channel FP32 taps) spills more, so it skips 9. Measured on 45 views
+// of 512^2, N 64 (one CTA of 512 threads per SM then): 15 beat 9 by 4 %
+// (FP32) to 8 % (FP16) nearest and 7-15 % bilinear.
+inline int staged_views_per_thread(int Vx, bool no9)
 {
     int best = 3;
     long long best_cost = -1;
     for (int vg : {15, 9, 5, 3}) {
-        if ((vg > Vx && vg != 3) || (no9 && vg == 9) || vg > max_vg) continue;
+        if ((vg > Vx && vg != 3) || (no9 && vg == 9)) continue;
         const long long cost = (long long)((Vx + vg - 1) / vg) * (vg + 3);
         if (best_cost < 0 || cost < best_cost) best_cost = cost, best = vg;
     }
@@ -1342,7 +1344,7 @@ __device__ __forceinline__ float texel_alpha<LF_U8>(uint32_t row, uint32_t i)
 // comes from the state the saving forward composite wrote, and the ring
 // carries only the back-to-front planes.
 template <int DT, bool BILINEAR, int VG, bool FS = false>
-__global__ void __launch_bounds__(kStagedBlock, VG > 5 ? 1 : 2) k_composite_bwd_staged(CompParams p, StagedGeom G,
+__global__ void __launch_bounds__(kBwdBlock, VG > 5 ? 1 : 2) k_composite_bwd_staged(CompParams p, StagedGeom G,
                                                                             const char* __restrict__ planes,
                                                                             const int32_t* __restrict__ count,
                                                                             CompWs w,
@@ -1381,7 +1383,7 @@ __global__ void __launch_bounds__(kStagedBlock, VG > 5 ? 1 : 2) k_composite_bwd_
     if (tid == 0) {
         for (int st = 0; st < kStages; ++st) {
             mbar_init(smem_addr(&full[st]), 1);
-            mbar_init(smem_addr(&empty[st]), kStagedWarps);
+            mbar_init(smem_addr(&empty[st]), kBwdWarps);
         }
         fence_proxy_async();
     }
@@ -1393,8 +1395,8 @@ __global__ void __launch_bounds__(kStagedBlock, VG > 5 ? 1 : 2) k_composite_bwd_
     auto entry = [&](int q) { return q < P ? q : 2 * P - 1 - q; };
     const int q0 = FS ? P : 0;
 
-    if (tid >= kStagedThreads) {
-        if (tid == kStagedThreads) {
+    if (tid >= kBwdStagedThreads) {
+        if (tid == kBwdStagedThreads) {
             for (int q = q0; q < 2 * P; ++q) {
                 const int r = q - q0;
                 const int st = r % kStages;
@@ -1669,7 +1671,7 @@ bool launch_bwd_staged_vg(const CompParams& p, const void* planes, const int32_t
                           const float4* dviews, float4* dplanes, cudaStream_t s, const float4* state = nullptr)
 {
     constexpr int TB = Texel<DT>::kBytes;
-    StagedGeom G = staged_geom(p, TB, BILINEAR, VG, 512);
+    StagedGeom G = staged_geom(p, TB, BILINEAR, VG, 512, kBwdStagedThreads);
     // no blended rows here: the full ring
     G.blend_bytes = 0;
     G.stages = kStages;
@@ -1682,7 +1684,7 @@ bool launch_bwd_staged_vg(const CompParams& p, const void* planes, const int32_t
         return false;
     const dim3 grid((unsigned)(G.groups_x * p.Vy), (unsigned)((p.Ny + G.BY - 1) / G.BY),
                     (unsigned)((p.Nx + G.TX - 1) / G.TX));
-    kern<<<grid, kStagedBlock, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, dviews, dplanes,
+    kern<<<grid, kBwdBlock, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, dviews, dplanes,
                                                   state);
     note_launches(1);
     return true;

@@ -380,10 +380,15 @@ struct CompParams {
 };
 
 // staged composite layout (see lf_composite.cu)
-constexpr int kStagedThreads = 512;   // consumer threads of a staged-composite CTA
+// Consumer threads of a staged-composite CTA (plus one producer warp): 256
+// for the forward kernels (two CTAs per SM at up to 15 views per thread,
+// four at 9 or fewer: an SM keeps working on one CTA's planes while the
+// other's warps wait at its ring), 512 for the adjoint (two CTAs per SM).
+constexpr int kStagedThreads = 256;
+constexpr int kBwdStagedThreads = 512;
 constexpr int kStages = 6;            // depth of its plane-row ring
 constexpr size_t kTwoCtaSmem = 112 * 1024;   // dynamic shared memory that still lets two CTAs share an SM
-constexpr int kTwoCtaViews = 9;               // widest view group run at two CTAs per SM
+constexpr int kTwoCtaViews = 9;               // widest view group run at the higher CTA count per SM
 struct StagedGeom {
     int TX, BY, VG, rows_per_y;    // rows_per_y: 1 nearest, 2 bilinear
     int padl;                      // zero texels left of every staged row (16 bytes)
@@ -393,7 +398,8 @@ struct StagedGeom {
     int stages;                    // ring depth of the single-scene kernel (<= kStages)
     size_t blend_bytes;            // bilinear: two FP32 row buffers per output row (single-scene kernel)
 };
-StagedGeom staged_geom(const CompParams& p, int texel_bytes, bool bilinear, int VG, int tx_max);
+StagedGeom staged_geom(const CompParams& p, int texel_bytes, bool bilinear, int VG, int tx_max,
+                       int threads = kStagedThreads);
 
 // batched (several scenes, one persistent launch): per-scene item table;
 // item li of a scene: chunk group li % groups, then view group, then row
