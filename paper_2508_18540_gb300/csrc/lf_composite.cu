@@ -374,10 +374,12 @@ StagedGeom staged_geom(const CompParams& p, int texel_bytes, bool bilinear, int 
     const size_t fixed = G.blend_bytes + 2 * kStages * 8 + sizeof(float) * (size_t)p.N * (4 + 4 * ((VG + 3) / 4)) +
                          sizeof(int) * (size_t)p.N;
     // a bilinear stage is released once its rows are blended, so a shallower
-    // ring suffices: keep the CTAs per SM the launch bounds aim at (two for
-    // view groups wider than kTwoCtaViews, four below) where they fit
+    // ring suffices: keep the CTAs per SM the launch bounds aim at (256
+    // threads: two for view groups wider than kTwoCtaViews, four below; 512:
+    // one and two) where they fit
     G.stages = kStages;
-    const size_t budget = VG > kTwoCtaViews ? kTwoCtaSmem : kTwoCtaSmem / 2;
+    const size_t budget = threads == 256 ? (VG > kTwoCtaViews ? kTwoCtaSmem : kTwoCtaSmem / 2)
+                                         : (VG > kTwoCtaViews ? (size_t)200 * 1024 : kTwoCtaSmem);
     while (bilinear && G.stages > 3 && G.stages * G.stage_bytes + fixed > budget) --G.stages;
     G.smem_bytes = G.stages * G.stage_bytes + fixed;
     return G;
@@ -413,7 +415,7 @@ __device__ __forceinline__ ThreadGeom thread_geom(const CompParams& p, const Sta
 // Saving form. A view's walk stops at the first list entry q behind which
 // T would fall below kTStop (0 behind a plane with A = 1): plane q still
 // blends with its T_q, q goes to the thread's stop slot of the view in
-// shared memory (stop_a + 4 jj kStagedThreads), and a[3] = -T_q marks the
+// shared memory (stop_a + 4 jj, the thread's VG slots), and a[3] = -T_q marks the
 // view as stopped (T_q >= kTStop > 0; T = 0 from there on, the colour the
 // plain form would still add being below 2^-24 per plane). The kernel
 // stores the state at the end of its walk.
@@ -423,7 +425,7 @@ template <int J>
 __device__ __forceinline__ void st_stop(uint32_t stop_a, int q, bool on)
 {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.shared.u32 [%0+%3], %1;\n\t}"
-                 ::"r"(stop_a), "r"(q), "r"((uint32_t)on), "n"(4 * J * kStagedThreads));
+                 ::"r"(stop_a), "r"(q), "r"((uint32_t)on), "n"(4 * J));
 }
 
 template <bool SAVE>
@@ -699,8 +701,12 @@ __device__ __forceinline__ void zero_pads(const CompParams& p, const StagedGeom&
 // plane behind which T falls below 2^-24 (and is taken as 0), T_k the
 // transmittance in front of it; or k = N and the transmittance behind the
 // last plane (see blend_texel).
-template <int DT, bool BILINEAR, int VG, bool SAVE = false>
-__global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 2 : 4) k_composite_staged(CompParams p, StagedGeom G,
+// NT consumer threads (256: two CTAs per SM at up to 15 views per thread,
+// four below; 512 where two CTAs of 256 would not fit their shared memory on
+// an SM: one CTA of 16 consumer warps then, two below).
+template <int DT, bool BILINEAR, int VG, bool SAVE = false, int NT = kStagedThreads>
+__global__ void __launch_bounds__(NT + 32, NT == 256 ? (VG > kTwoCtaViews ? 2 : 4) : (VG > kTwoCtaViews ? 1 : 2))
+    k_composite_staged(CompParams p, StagedGeom G,
                                                                         const char* __restrict__ planes,
                                                                         const int32_t* __restrict__ count, CompWs w,
                                                                         float* __restrict__ out,
@@ -709,7 +715,7 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 2 : 4) k_com
     extern __shared__ __align__(128) unsigned char smem[];
     // [stages][rows][row_bytes] | bilinear: [2][BY][row_texels] float4 |
     // full[kStages] | empty[kStages] | coef [N][CW] | plist [N] | saving
-    // form: stop slots [VG][kStagedThreads]
+    // form: stop slots [NT][VG]
     constexpr int CW = CoefBlock<VG>::kFloats;
     unsigned char* stage_base = smem;
     // bilinear: the two staged rows of an output row are blended vertically
@@ -753,7 +759,7 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 2 : 4) k_com
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(smem_addr(&full[s]), 1);
-            mbar_init(smem_addr(&empty[s]), kStagedWarps);
+            mbar_init(smem_addr(&empty[s]), (NT / 32));
         }
         fence_proxy_async();
     }
@@ -766,10 +772,10 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 2 : 4) k_com
                          stage_base + (size_t)(q % NS) * G.stage_bytes, smem_addr(&full[q % NS]));
     };
 
-    if (tid >= kStagedThreads) {
+    if (tid >= NT) {
         // producer warp: one lane streams the planes through the stage ring,
         // refilling a stage as soon as every consumer warp has released it
-        if (tid == kStagedThreads) {
+        if (tid == NT) {
             for (int q = 0; q < P; ++q) {
                 const int s = q % NS;
                 if (q >= NS && !mbar_wait_bounded(smem_addr(&empty[s]), (uint32_t)(((q / NS) - 1) & 1))) {
@@ -785,8 +791,8 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 2 : 4) k_com
     float acc[VG][4];
 #pragma unroll
     for (int jj = 0; jj < VG; ++jj) acc[jj][0] = acc[jj][1] = acc[jj][2] = 0.f, acc[jj][3] = 1.f;
-    // saving form: the stop slots [VG][kStagedThreads] follow plist
-    const uint32_t stop_a = smem_addr(plist + p.N) + 4u * (uint32_t)tid;
+    // saving form: the stop slots [NT][VG] follow plist
+    const uint32_t stop_a = smem_addr(plist + p.N) + 4u * (uint32_t)(tid * VG);
     const uint32_t stage_a = smem_addr(stage_base), coef_a = smem_addr(coef);
     const bool live = ty < G.BY && x < p.Nx && y < p.Ny;   // threads past BY rows idle
     const ThreadGeom tg = thread_geom(p, G, x, y, ty);
@@ -835,7 +841,7 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 2 : 4) k_com
                     brow[i] = t;
                 }
             }
-            asm volatile("bar.sync 1, %0;" ::"r"(kStagedThreads) : "memory");
+            asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
             // the staged rows are no longer needed: release the stage now
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
@@ -872,7 +878,7 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 2 : 4) k_com
         if (SAVE) {
             // stopped: {T_k, k} of the stop plane; else {T behind the last plane, N}
             const bool stopped = acc[jj][3] < 0.0f;
-            const int k = stopped ? plist[lds_u32(stop_a + 4u * (uint32_t)(jj * kStagedThreads))] : p.N;
+            const int k = stopped ? plist[lds_u32(stop_a + 4u * (uint32_t)jj)] : p.N;
             state[((size_t)v * p.Ny + y) * p.Nx + x] =
                 make_float4(fabsf(acc[jj][3]), __int_as_float(k), 0.0f, 0.0f);
         }
@@ -1046,24 +1052,37 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 2 : 4) k_com
     }
 }
 
+template <int DT, bool BILINEAR, int VG, bool SAVE, int NT>
+bool launch_staged_nt(const CompParams& p, const StagedGeom& G, const void* planes, const int32_t* count,
+                      const CompWs& ws, float* out, cudaStream_t s, float4* state)
+{
+    auto kern = k_composite_staged<DT, BILINEAR, VG, SAVE, NT>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem_bytes) != cudaSuccess)
+        return false;
+    const dim3 grid((unsigned)(G.groups_x * p.Vy), (unsigned)((p.Ny + G.BY - 1) / G.BY),
+                    (unsigned)((p.Nx + G.TX - 1) / G.TX));
+    kern<<<grid, NT + 32, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, out, state);
+    note_launches(1);
+    return true;
+}
+
+// 256 consumer threads where two such CTAs fit an SM's shared memory, else
+// 512 (one CTA of 16 consumer warps keeps the SM as busy as two of 8)
 template <int DT, bool BILINEAR, int VG, bool SAVE = false>
 bool launch_staged_vg(const CompParams& p, const void* planes, const int32_t* count, const CompWs& ws, float* out,
                       cudaStream_t s, float4* state = nullptr)
 {
     constexpr int TB = Texel<DT>::kBytes;
-    StagedGeom G = staged_geom(p, TB, BILINEAR, VG, 512);
-    if (SAVE) G.smem_bytes += sizeof(int) * (size_t)VG * kStagedThreads;   // stop slots
-    if (G.smem_bytes > 200 * 1024) return false;
     // bulk copies need 16-byte aligned rows: plane base and row pitch
     if (((uintptr_t)planes) % 16 != 0 || ((size_t)p.W * TB) % 16 != 0) return false;
-    auto kern = k_composite_staged<DT, BILINEAR, VG, SAVE>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem_bytes) != cudaSuccess)
-        return false;
-    const dim3 grid((unsigned)(G.groups_x * p.Vy), (unsigned)((p.Ny + G.BY - 1) / G.BY),
-                    (unsigned)((p.Nx + G.TX - 1) / G.TX));
-    kern<<<grid, kStagedBlock, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, out, state);
-    note_launches(1);
-    return true;
+    StagedGeom G = staged_geom(p, TB, BILINEAR, VG, 512, 256);
+    if (SAVE) G.smem_bytes += sizeof(int) * (size_t)VG * 256;   // stop slots
+    if (2 * (G.smem_bytes + 1024) <= (size_t)228 * 1024)
+        return launch_staged_nt<DT, BILINEAR, VG, SAVE, 256>(p, G, planes, count, ws, out, s, state);
+    G = staged_geom(p, TB, BILINEAR, VG, 512, 512);
+    if (SAVE) G.smem_bytes += sizeof(int) * (size_t)VG * 512;
+    if (G.smem_bytes > 200 * 1024) return false;
+    return launch_staged_nt<DT, BILINEAR, VG, SAVE, 512>(p, G, planes, count, ws, out, s, state);
 }
 
 // Views per thread of the staged composite, from {15, 9, 5, 3} (at most Vx,
