@@ -66,9 +66,9 @@ def _config(extra=None):
 # with them.
 NCU_TRAFFIC = {
     # the raster stage's two kernels: the parts of split lists and the lists
-    "raster_gaussians": (11_974_656 + 0 + 71_355_904 + 204_294_144, ("lf_raster.cu", "lf_internal.cuh"),
-                         "108b044d1ac58be0"),
-    "composite": (253_057_792 + 152_613_120, ("lf_composite.cu", "lf_internal.cuh"), "495c1e18b0bb95c0"),
+    "raster_gaussians": (11_973_888 + 0 + 71_340_800 + 204_708_608, ("lf_raster.cu", "lf_internal.cuh"),
+                         "b1bfb8379a0ee06e"),
+    "composite": (253_054_976 + 156_040_960, ("lf_composite.cu", "lf_internal.cuh"), "1f168023239401ed"),
 }
 
 

@@ -731,11 +731,15 @@ __global__ void __launch_bounds__(NT + 32, NT == 256 ? (VG > kTwoCtaViews ? 2 : 
     __shared__ int s_nplanes;
 
     const int tid = threadIdx.x, lane = tid & 31;
-    const int vgroup = blockIdx.x;                 // fastest: neighbouring CTAs share plane rows in L2
+    // fastest: the view groups, then the column tiles of one row band, so
+    // that the CTAs reading the same plane rows run together (rows read from
+    // DRAM once, then from L2)
+    const int nvg = G.groups_x * p.Vy;
+    const int vgroup = blockIdx.x % nvg;
     const int vi = vgroup / G.groups_x;            // view row
     const int j0 = (vgroup % G.groups_x) * VG;     // first view column of the group
     const int Y0 = blockIdx.y * G.BY;
-    const int X0 = blockIdx.z * G.TX;
+    const int X0 = (blockIdx.x / nvg) * G.TX;
     const int tx = tid % G.TX, ty = tid / G.TX;
     const int x = X0 + tx, y = Y0 + ty;
 
@@ -941,7 +945,6 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 2 : 4) k_com
         const StagedGeom G = scs[si].G;
         const CompWs w = scs[si].w;
         const char* planes = scs[si].planes;
-        const int nby = scs[si].nby;
         const long long li0 = it - scs[si].base;
         const int cgs = scs[si].groups;
         const int cg = (int)(li0 % cgs);              // chunk group
@@ -950,7 +953,10 @@ __global__ void __launch_bounds__(kStagedBlock, VG > kTwoCtaViews ? 2 : 4) k_com
         const int vgroup = (int)(li % ng);
         const long long rest = li / ng;
         const int vi = vgroup / G.groups_x, j0 = (vgroup % G.groups_x) * VG;
-        const int Y0 = (int)(rest % nby) * G.BY, X0 = (int)(rest / nby) * G.TX;
+        // column tiles before row bands: the items reading the same plane
+        // rows are taken together
+        const int ntx = scs[si].nbz;
+        const int X0 = (int)(rest % ntx) * G.TX, Y0 = (int)(rest / ntx) * G.BY;
 
         if (tid < 32) {
             const int n = plane_list(p, scs[si].count, plist);
@@ -1059,8 +1065,7 @@ bool launch_staged_nt(const CompParams& p, const StagedGeom& G, const void* plan
     auto kern = k_composite_staged<DT, BILINEAR, VG, SAVE, NT>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem_bytes) != cudaSuccess)
         return false;
-    const dim3 grid((unsigned)(G.groups_x * p.Vy), (unsigned)((p.Ny + G.BY - 1) / G.BY),
-                    (unsigned)((p.Nx + G.TX - 1) / G.TX));
+    const dim3 grid((unsigned)(G.groups_x * p.Vy * ((p.Nx + G.TX - 1) / G.TX)), (unsigned)((p.Ny + G.BY - 1) / G.BY));
     kern<<<grid, NT + 32, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, out, state);
     note_launches(1);
     return true;
@@ -1384,11 +1389,12 @@ __global__ void __launch_bounds__(kBwdBlock, VG > 5 ? 1 : 2) k_composite_bwd_sta
     __shared__ int s_nplanes;
 
     const int tid = threadIdx.x, lane = tid & 31;
-    const int vgroup = blockIdx.x;
+    const int nvg = G.groups_x * p.Vy;   // view groups, then column tiles (as the forward)
+    const int vgroup = blockIdx.x % nvg;
     const int vi = vgroup / G.groups_x;
     const int j0 = (vgroup % G.groups_x) * VG;
     const int Y0 = blockIdx.y * G.BY;
-    const int X0 = blockIdx.z * G.TX;
+    const int X0 = (blockIdx.x / nvg) * G.TX;
     const int tx = tid % G.TX, ty = tid / G.TX;
     const int x = X0 + tx, y = Y0 + ty;
 
@@ -1701,8 +1707,7 @@ bool launch_bwd_staged_vg(const CompParams& p, const void* planes, const int32_t
     auto kern = k_composite_bwd_staged<DT, BILINEAR, VG, FS>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem_bytes) != cudaSuccess)
         return false;
-    const dim3 grid((unsigned)(G.groups_x * p.Vy), (unsigned)((p.Ny + G.BY - 1) / G.BY),
-                    (unsigned)((p.Nx + G.TX - 1) / G.TX));
+    const dim3 grid((unsigned)(G.groups_x * p.Vy * ((p.Nx + G.TX - 1) / G.TX)), (unsigned)((p.Ny + G.BY - 1) / G.BY));
     kern<<<grid, kBwdBlock, G.smem_bytes, s>>>(p, G, static_cast<const char*>(planes), count, ws, dviews, dplanes,
                                                   state);
     note_launches(1);

@@ -402,8 +402,8 @@ StagedGeom staged_geom(const CompParams& p, int texel_bytes, bool bilinear, int 
                        int threads = kStagedThreads);
 
 // batched (several scenes, one persistent launch): per-scene item table;
-// item li of a scene: chunk group li % groups, then view group, then row
-// band, then column tile
+// item li of a scene: chunk group li % groups, then view group, then column
+// tile, then row band
 struct CompScene {
     CompParams p;
     StagedGeom G;
