@@ -246,8 +246,38 @@ def run_ours(args):
         barrier()
         return R.max_over_ranks(sum(a.elapsed_time(b) for a, b in evg) / steps, world, dev)
 
+    # a render loop with two frames in flight: two renderers (workspace,
+    # planes, views each), one graph and one stream each, frames alternating;
+    # K frames timed from the first frame's start to the last one's end (each
+    # frame streams > 0.7 GB through the 129 MB L2, so no flush)
+    pair_streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+
+    def timed_in_flight(rr, steps, warmup):
+        for i in range(2 * warmup):
+            with torch.cuda.stream(pair_streams[i & 1]):
+                rr[i & 1].replay()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(pair_streams[0])
+        pair_streams[1].wait_event(e0)
+        for i in range(steps):
+            with torch.cuda.stream(pair_streams[i & 1]):
+                rr[i & 1].replay()
+        pair_streams[0].wait_stream(pair_streams[1])
+        e1.record(pair_streams[0])
+        e1.synchronize()
+        barrier()
+        return R.max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
+
     r32 = res["f32"]["renderer"]
     graph_kernels = r32.capture(g)
+    for d in res:
+        r2 = api.LightFieldRenderer(wl.camera, wl.display, wl.views, wl.N, wl.binning, d, device=dev)
+        if d != "f32":
+            res[d]["renderer"].capture(g)
+        r2.capture(g)
+        res[d]["pair"] = [res[d]["renderer"], r2]
     # the sampler runs from half a second of back-to-back replays (the GPU at
     # its working clock) through the end of the timed replays
     clocks.start()
@@ -257,11 +287,14 @@ def run_ours(args):
             r32.replay()
         torch.cuda.synchronize()
     g_ms = timed_graph(r32, args.steps, args.warmup)
+    f_ms = timed_in_flight(res["f32"]["pair"], args.steps, args.warmup)
     clk = clocks.stop()
     clk["window"] = "0.5 s of back-to-back graph replays, then the timed replays"
     for d in ("f16", "bf16", "u8"):
-        res[d]["renderer"].capture(g)
         res[d]["graph_ms"] = timed_graph(res[d]["renderer"], args.steps, args.warmup)
+        res[d]["flight_ms"] = timed_in_flight(res[d]["pair"], args.steps, args.warmup)
+    for d in res:
+        res[d]["pair"] = None
 
     # end to end through the public API with host buffers (pinned), f32 planes
     host_in = api.DeviceGaussians.from_scene(wl.scene, pin=True)
@@ -328,26 +361,35 @@ def run_ours(args):
 
     line = None
     if rank == 0:
-        # the frame as a render loop runs it: one CUDA-graph replay per frame
-        fps = R.job_rate(g_ms, world)
+        # the frame as a render loop runs it: one CUDA-graph replay per frame,
+        # two frames in flight; the one-frame-at-a-time figure beside it
+        fps = R.job_rate(f_ms, world)
         line = {
             "metric": METRIC, "value": round(fps, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(g_ms, 4), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": round(f_ms, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": _config({"planes": "f32", "parallelism": "replicas" if world > 1 else "single",
-                               "launch": "one CUDA-graph replay per frame (%d kernels)" % graph_kernels}),
+                               "launch": "one CUDA-graph replay per frame (%d kernels), two frames in flight "
+                                         "(two renderers, two streams)" % graph_kernels,
+                               "l2": "not flushed: each frame streams > 0.7 GB (planes, views, workspace) "
+                                     "through the 129 MB L2"}),
             "views_per_s": round(fps * WORKLOAD["V"], 1),
+            "one_frame_at_a_time": {"value": round(R.job_rate(g_ms, world), 2), "ms_per_step": round(g_ms, 4),
+                                    "l2": "flushed between frames (512 MB write)",
+                                    "note": "frame latency: one graph replay, the next frame starting after it"},
             "plain_launches": {"value": round(R.job_rate(res["f32"]["ms"], world), 2),
                                "ms_per_step": round(res["f32"]["ms"], 4)},
-            "variants": {d: {"planes": d, "value": round(R.job_rate(res[d]["graph_ms"], world), 2),
-                             "ms_per_step": round(res[d]["graph_ms"], 4),
+            "variants": {d: {"planes": d, "value": round(R.job_rate(res[d]["flight_ms"], world), 2),
+                             "ms_per_step": round(res[d]["flight_ms"], 4),
+                             "one_frame_at_a_time_value": round(R.job_rate(res[d]["graph_ms"], world), 2),
                              "plain_launches_value": round(R.job_rate(res[d]["ms"], world), 2), "roofline": roofs[d]}
                          for d in ("f16", "bf16", "u8")},
             "stages_ms": {d: {k: round(v[0] / v[1], 4) for k, v in res[d]["stages"].items()} for d in res},
             "e2e": {"value": round(R.job_rate(e_ms, world), 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(e_ms, 4),
-                    "api": "HostPipeline.submit (pinned host Gaussians in, pinned host views out, "
-                           "copies overlapped with neighbouring frames, one CUDA-graph replay per frame)",
+                    "api": "HostPipeline.submit (pinned host Gaussians in, pinned host views out, two "
+                           "frames in flight: a renderer and compute stream per slot, copies overlapped with "
+                           "the neighbouring frames, one CUDA-graph replay per frame)",
                     "l2": "not flushed between steps: each step streams > 0.7 GB (planes, views, workspace) "
                           "through the 129 MB L2"},
             "gpu_launches": graph_kernels * args.steps,

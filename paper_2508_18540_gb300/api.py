@@ -530,21 +530,28 @@ class LightFieldRenderer:
 
 class HostPipeline:
     """Renders frames whose Gaussians live in (pinned) host memory and whose
-    views go back to (pinned) host memory. Two device input slots and two
-    device view slots let frame i's host-to-device copy (copy stream) and
-    frame i-1's device-to-host copy (second copy stream) run while frame i-1
-    or i is computed, ordered by CUDA events. submit() returns the event that
-    marks frame i's views in host memory."""
+    views go back to (pinned) host memory, two frames in flight. Each of the
+    two slots has its own device inputs, renderer (workspace, planes, views)
+    and compute stream, so frame i is computed while frame i-1 is, and frame
+    i's host-to-device copy (copy stream) and frame i-1's device-to-host copy
+    (second copy stream) run beside them, ordered by CUDA events. submit()
+    returns the event that marks frame i's views in host memory."""
 
     def __init__(self, renderer: "LightFieldRenderer", n: int, device="cuda", graphs: bool = True):
         self.r = renderer
+        r2 = LightFieldRenderer(renderer.camera, renderer.display, renderer.views, renderer.N, renderer.binning,
+                                renderer.dtype, n_capacity=max(n, renderer.n_capacity),
+                                dup_capacity=renderer.dup_capacity, device=device,
+                                plane_filter=renderer.plane_filter, blend=renderer.blend)
+        self.renderers = [renderer, r2]
         f = dict(dtype=torch.float32, device=device)
         # zero Gaussians sit at the world origin, in front of no reference camera
         # that sees them from z_near on, so warm-up and capture renders cull them
         self.slots = [DeviceGaussians(torch.zeros((n, 3), **f), torch.zeros((n, 3), **f), torch.zeros((n, 4), **f),
                                       torch.zeros((n,), **f), torch.zeros((n, 3), **f)) for _ in range(2)]
         self.outs = [torch.empty_like(renderer.out) for _ in range(2)]
-        self.s_in, self.s_comp, self.s_out = (torch.cuda.Stream(device=device) for _ in range(3))
+        self.s_in, self.s_out = torch.cuda.Stream(device=device), torch.cuda.Stream(device=device)
+        self.s_comp = [torch.cuda.Stream(device=device) for _ in range(2)]
         E = torch.cuda.Event
         self.in_ready, self.in_free = [E(), E()], [E(), E()]
         self.out_ready, self.out_free = [E(), E()], [E(), E()]
@@ -554,36 +561,37 @@ class HostPipeline:
         if graphs:
             self.graphs = []
             for k in range(2):
-                renderer.build(self.slots[k])
-                renderer.composite(out=self.outs[k])
+                rk = self.renderers[k]
+                rk.build(self.slots[k])
+                rk.composite(out=self.outs[k])
                 torch.cuda.synchronize()
                 gk = torch.cuda.CUDAGraph()
                 lf_trace_enable(False)
                 with torch.cuda.graph(gk):
                     st = torch.cuda.current_stream()
-                    renderer.build(self.slots[k], st)
-                    renderer.composite(st, out=self.outs[k])
+                    rk.build(self.slots[k], st)
+                    rk.composite(st, out=self.outs[k])
                 self.graphs.append(gk)
 
     def submit(self, host: DeviceGaussians, host_out: torch.Tensor) -> torch.cuda.Event:
         k = self.i % 2
-        dev = self.slots[k]
+        dev, rk, sc = self.slots[k], self.renderers[k], self.s_comp[k]
         self.s_in.wait_event(self.in_free[k])          # frame i-2 no longer reads this slot
         with torch.cuda.stream(self.s_in):
             for dst, src in ((dev.means, host.means), (dev.scales, host.scales), (dev.quats, host.quats),
                              (dev.opacity, host.opacity), (dev.rgb, host.rgb)):
                 dst.copy_(src, non_blocking=True)
         self.in_ready[k].record(self.s_in)
-        self.s_comp.wait_event(self.in_ready[k])
-        self.s_comp.wait_event(self.out_free[k])       # frame i-2's views have left this slot
+        sc.wait_event(self.in_ready[k])
+        sc.wait_event(self.out_free[k])       # frame i-2's views have left this slot
         if self.graphs is not None:
-            with torch.cuda.stream(self.s_comp):
+            with torch.cuda.stream(sc):
                 self.graphs[k].replay()
         else:
-            self.r.build(dev, self.s_comp)
-            self.r.composite(self.s_comp, out=self.outs[k])
-        self.in_free[k].record(self.s_comp)
-        self.out_ready[k].record(self.s_comp)
+            rk.build(dev, sc)
+            rk.composite(sc, out=self.outs[k])
+        self.in_free[k].record(sc)
+        self.out_ready[k].record(sc)
         self.s_out.wait_event(self.out_ready[k])
         with torch.cuda.stream(self.s_out):
             host_out.copy_(self.outs[k], non_blocking=True)
