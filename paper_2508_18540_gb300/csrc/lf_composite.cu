@@ -412,15 +412,8 @@ __device__ __forceinline__ ThreadGeom thread_geom(const CompParams& p, const Sta
     return t;
 }
 
-// Saving form. A view's walk stops at the first list entry q behind which
-// T would fall below kTStop (0 behind a plane with A = 1): plane q still
-// blends with its T_q, q goes to the thread's stop slot of the view in
-// shared memory (stop_a + 4 jj, the thread's VG slots), and a[3] = -T_q marks the
-// view as stopped (T_q >= kTStop > 0; T = 0 from there on, the colour the
-// plain form would still add being below 2^-24 per plane). The kernel
-// stores the state at the end of its walk.
-// store q to view J's stop slot ([stop_a + immediate]: no address register
-// per view)
+// Stores q to view J's stop slot when on ([stop_a + immediate]: no address
+// register per view, no branch).
 template <int J>
 __device__ __forceinline__ void st_stop(uint32_t stop_a, int q, bool on)
 {
@@ -428,6 +421,15 @@ __device__ __forceinline__ void st_stop(uint32_t stop_a, int q, bool on)
                  ::"r"(stop_a), "r"(q), "r"((uint32_t)on), "n"(4 * J));
 }
 
+// One view's blend of one texel t at plane list entry q (view jj of the
+// thread's group). Plain form: Q += T c, T <- T - T A. Saving form: the
+// view's walk stops at the first list entry q behind which T would fall
+// below kTStop (0 behind a plane with A = 1): plane q still blends with its
+// T_q, q goes to the view's stop slot in shared memory (stop_a + 4 jj, the
+// thread's VG slots), and a[3] = -T_q marks the view as stopped (T_q >=
+// kTStop > 0; T = 0 from there on, the colour the plain form would still
+// add being below 2^-24 per plane). The kernel stores the state at the end
+// of its walk.
 template <bool SAVE>
 __device__ __forceinline__ void blend_texel(float (&a)[4], float4 t, uint32_t stop_a, int jj, int q)
 {
