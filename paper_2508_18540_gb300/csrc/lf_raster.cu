@@ -1,11 +1,13 @@
 // lf_raster.cu -- 3D-tiled rasterisation of every chunk into its sweeping
 // plane (the per-chunk rendering step of Algorithm 1, all chunks in parallel).
 //
-// One CTA per (16x16 tile, chunk). It walks the (32x32 super-tile, chunk)
-// list holding its tile (ranks in depth order) in batches, keeps the entries
-// whose footprint meets its tile (order-preserving compaction), stages those
-// primitives (rank-ordered copies) in shared memory, and every thread blends
-// its pixels front to back:
+// Every (32x32 super-tile, chunk) list holds the ranks, in depth order, of
+// the primitives whose footprint meets the super-tile. Gaussians: one CTA
+// per list (long lists cut into parts, composed with the "over" operator;
+// see below). Voxels: one CTA per (16x16 tile, chunk), keeping the entries of
+// its super-tile's list that meet its tile (order-preserving compaction).
+// The CTA stages the primitives (rank-ordered copies) in shared memory in
+// batches, and every thread blends its pixels front to back:
 //   Gaussians (Sec. 4.4, 3DGS model): alpha = min(0.99, o exp(-q/2)),
 //     q = d^T Sigma_2^{-1} d inside the primitive's footprint rectangle;
 //   voxels (Sec. 4.5, SVR model): alpha = 1 - exp(-integral of the trilinear
@@ -81,27 +83,6 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// explicit shared-space accesses through 32-bit shared addresses
-__device__ __forceinline__ float4 lds4(uint32_t a)
-{
-    float4 v;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
-    return v;
-}
-
-__device__ __forceinline__ int2 lds2i(uint32_t a)
-{
-    int2 v;
-    asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
-    return v;
-}
-
-__device__ __forceinline__ void sts4(uint32_t a, float4 v)
-{
-    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-                 : "memory");
-}
-
 // Gaussians. A CTA rasterises one (32 x 32 super-tile, chunk) list, or one
 // part of a long one, with 8 warps. Warp w owns the 8-column x 16-row strip
 // at column group w % 4 and row group w / 4 of the super-tile; lane l shades
@@ -109,16 +90,19 @@ __device__ __forceinline__ void sts4(uint32_t a, float4 v)
 // form the 8 x 4 sub-block s of the strip, and a footprint that misses a
 // sub-block costs the warp nothing there (sub-blocks of 32 pixels fit the
 // footprint sizes better than wide strips). Each batch of list entries is
-// staged as three 16-byte words {mean x, mean y, A, B},
-// {C, log2 o, x0 | y0 << 16, (x1 - x0) | (y1 - y0) << 16}, {r, g, b, -},
-// with the conic pre-scaled so that
+// staged as three 16-byte words {mean x, mean y, A, B}, {C, log2 o, cm, rm},
+// {r, g, b, wm}, with the conic pre-scaled so that
 //   alpha = min(0.99, 2^(A dx^2 + B dx dy + C dy^2 + log2 o)),
-// A = -log2(e)/2 a, B = -log2(e) b, C = -log2(e)/2 c. Per visited entry a lane
-// forms g1 = B dx and g0 = A dx^2 + log2 o for its column once; each of its
-// rows inside the footprint then costs the Horner form (C dy + g1) dy + g0,
-// one ex2 and the blend. Every warp ballots which entries touch its strip and
-// visits only those, in list order, so each pixel blends its members front
-// to back. Two staging buffers alternate: one CTA barrier per batch.
+// A = -log2(e)/2 a, B = -log2(e) b, C = -log2(e)/2 c, and the footprint
+// rectangle as bit masks over the super-tile: bit c of cm for column c, bit r
+// of rm for row r, bit w of wm for the warps whose strips it meets (computed
+// once per entry and CTA, so a warp's visit tests bits instead of bounds).
+// Per visited entry a lane forms g1 = B dx and g0 = A dx^2 + log2 o for its
+// column once; each of its rows inside the footprint then costs the Horner
+// form (C dy + g1) dy + g0, one ex2 and the blend. Every warp ballots which
+// entries touch its strip and visits only those, in list order, so each
+// pixel blends its members front to back. Two staging buffers alternate: one
+// CTA barrier per batch.
 //
 // Load balance. The work of a list grows with its length, and dense regions
 // of the scene make a few lists far longer than the rest. k_raster_plan cuts
@@ -184,14 +168,16 @@ __device__ __forceinline__ void raster_gauss_list(const BuildWs& w, const Raster
     constexpr float kL2E = 1.4426950408889634f;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int SX = (st % p.supers_x) * kSuper, SY = (st / p.supers_x) * kSuper;
-    const int sx0 = SX + 8 * (warp & 3), sx1 = sx0 + 7;                  // warp strip bounds
-    const int sy0 = SY + 4 * NS * (warp >> 2), sy1 = sy0 + 4 * NS - 1;
+    const int sx0 = SX + 8 * (warp & 3);                                  // warp strip origin
+    const int sy0 = SY + 4 * NS * (warp >> 2);
     const int px = sx0 + (lane & 7);
     const int py0 = sy0 + (lane >> 3);                                    // slot s: row py0 + 4 s
     const int2 sg = w.seg[(size_t)st * p.N + k];
     const int beg = SPLIT ? sg.x + part * S : sg.x;
     const int L = SPLIT ? min(sg.y - beg, S) : sg.y - sg.x;
     const float fpx = (float)px;
+    // bit of this lane's column in cm, of its slot-0 row in rm
+    const int csh = px - SX, rsh = py0 - SY;
     float C[NS][3], T[NS];
     uint32_t stopped = 0u;
 #pragma unroll
@@ -205,10 +191,20 @@ __device__ __forceinline__ void raster_gauss_list(const BuildWs& w, const Raster
             const float4 geo = w.r_geo[rk];
             const float4 c = w.r_con[rk];
             sm.e0[buf][threadIdx.x] = make_float4(geo.x, geo.y, -0.5f * kL2E * c.x, -kL2E * c.y);
+            // footprint columns / rows of the super-tile as bit masks, and
+            // the warps whose 8 x 16 strips it meets
+            const int cl = max(r.x - SX, 0), ch = min(r.z - SX, kSuper - 1);
+            const int rl = max(r.y - SY, 0), rh = min(r.w - SY, kSuper - 1);
+            const uint32_t cm = cl <= ch ? (0xffffffffu >> (31 - ch)) & (0xffffffffu << cl) : 0u;
+            const uint32_t rm = rl <= rh ? (0xffffffffu >> (31 - rh)) & (0xffffffffu << rl) : 0u;
+            uint32_t wm = 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                wm |= ((cm >> (8 * (q & 3))) & 0xffu) && ((rm >> (16 * (q >> 2))) & 0xffffu) ? 1u << q : 0u;
             sm.e1[buf][threadIdx.x] =
-                make_float4(-0.5f * kL2E * c.z, __log2f(c.w), __int_as_float((r.x & 0xffff) | (r.y << 16)),
-                            __int_as_float(((r.z - r.x) & 0xffff) | ((r.w - r.y) << 16)));
-            sm.rgb[buf][threadIdx.x] = w.r_rgb[rk];
+                make_float4(-0.5f * kL2E * c.z, __log2f(c.w), __uint_as_float(cm), __uint_as_float(rm));
+            const float4 rgb = w.r_rgb[rk];
+            sm.rgb[buf][threadIdx.x] = make_float4(rgb.x, rgb.y, rgb.z, __uint_as_float(wm));
         }
         // orders this batch's staging before its walk, and every warp's walk
         // of the batch before last before this staging overwrote its buffer
@@ -219,13 +215,7 @@ __device__ __forceinline__ void raster_gauss_list(const BuildWs& w, const Raster
         const float4* s_rgb = sm.rgb[buf];
         for (int m0 = 0; m0 < cnt; m0 += 32) {
             const int jl = m0 + lane;
-            bool hit = false;
-            if (jl < cnt) {
-                const float2 rc = *reinterpret_cast<const float2*>(&s_e1[jl].z);
-                const int xy = __float_as_int(rc.x), wh = __float_as_int(rc.y);
-                const int rx0 = xy & 0xffff, ry0 = xy >> 16;
-                hit = rx0 <= sx1 && rx0 + (wh & 0xffff) >= sx0 && ry0 <= sy1 && ry0 + (wh >> 16) >= sy0;
-            }
+            const bool hit = jl < cnt && ((__float_as_uint(s_rgb[jl].w) >> warp) & 1u);
             uint32_t mask = __ballot_sync(0xffffffffu, hit);
             while (mask) {
                 const int j = m0 + __ffs(mask) - 1;
@@ -233,18 +223,14 @@ __device__ __forceinline__ void raster_gauss_list(const BuildWs& w, const Raster
                 const float4 e0 = s_e0[j];
                 const float4 e1 = s_e1[j];
                 const float4 col = s_rgb[j];
-                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
-                // rows of slot 0 below the footprint's top row; a column
-                // outside the footprint fails every row test
-                const int rt = (uint32_t)(px - (xy & 0xffff)) <= (uint32_t)(wh & 0xffff) ? py0 - (xy >> 16)
-                                                                                        : 0x40000000;
-                const uint32_t rh = (uint32_t)(wh >> 16);
+                // slot s of this lane lies in the footprint iff bit 4 s of m is set
+                const uint32_t m = (__float_as_uint(e1.z) >> csh) & 1u ? __float_as_uint(e1.w) >> rsh : 0u;
                 const float dx = fpx - e0.x;
                 const float g1 = e0.w * dx;
                 const float g0 = fmaf(e0.z * dx, dx, e1.y);
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
-                    if ((uint32_t)(rt + 4 * s) <= rh) {
+                    if (m & (1u << (4 * s))) {
                         const float dy = (float)(py0 + 4 * s) - e0.y;
                         const float pw = fmaf(fmaf(e1.x, dy, g1), dy, g0);
                         const float al = fminf(0.99f, ex2_approx(pw));
@@ -305,11 +291,12 @@ __device__ __forceinline__ void raster_gauss_list(const BuildWs& w, const Raster
 }
 
 // Lists no longer than r_seg entries: one CTA per (super-tile x, chunk y).
+// Five CTAs (40 warps) per SM: 48 registers.
 // Launched behind the parts kernel, it does not wait for it to start;
 // CTA (0, 0) waits for it to finish before exiting, so this grid completes
 // after every part's texels are written and work ordered after it sees them.
 template <int DT, bool G3>
-__global__ void __launch_bounds__(kGaussThreads) k_raster_gauss(BuildWs w, RasterParams p,
+__global__ void __launch_bounds__(kGaussThreads, 5) k_raster_gauss(BuildWs w, RasterParams p,
                                                                const uint32_t* __restrict__ ranks, void* planes)
 {
     __shared__ GaussSmem sm;
@@ -369,15 +356,6 @@ __global__ void __launch_bounds__(kGaussThreads) k_raster_gauss_batched(const Ra
         if (sg.y - sg.x > S.w.hdr->r_seg) return;
         raster_gauss_list<DT, false, false>(S.w, S.p, S.ranks, S.planes, st, k, sm, 0, 1, -1, 0, nullptr);
     }
-}
-
-__device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
-
-__device__ __forceinline__ float trilinear(const float* rho, float fx, float fy, float fz)
-{
-    const float c00 = lerpf(rho[0], rho[1], fx), c10 = lerpf(rho[2], rho[3], fx);
-    const float c01 = lerpf(rho[4], rho[5], fx), c11 = lerpf(rho[6], rho[7], fx);
-    return lerpf(lerpf(c00, c10, fy), lerpf(c01, c11, fy), fz);
 }
 
 // clamp to [0, 1] (NaN -> 0) in one saturating operation
