@@ -318,8 +318,13 @@ def test_autograd_function_and_fit_step(save_state):
     loss = ((views - target) ** 2).sum()
     loss.backward()
     grads, _ = r.backward(g, (2.0 * (views.detach() - target)).contiguous())
+    # the adjoints sum with float atomics (dplanes over views, the per-primitive
+    # sums over pixels), so two calls agree up to the order of those sums: an
+    # element that cancels can move by more than 1e-4 of itself, the tensor by
+    # a few FP32 rounding steps of its norm
     for p, ref_g in zip(params, (grads.dmeans, grads.dscales, grads.dquats, grads.dopacity, grads.drgb)):
-        assert torch.allclose(p.grad, ref_g, rtol=1e-4, atol=1e-6)
+        a, b = p.grad.double().cpu().numpy(), ref_g.double().cpu().numpy()
+        assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b) + 1e-9, _rel(a, b)
     opa = params[3].detach().clone().requires_grad_(True)
     opt = torch.optim.Adam([opa], lr=0.01)
     losses = []
