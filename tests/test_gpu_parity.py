@@ -237,15 +237,16 @@ def test_voxels_rotated(orc):
     _compare(gpu, o, o["ref"].W, o["ref"].H, 6, "f32")
 
 
-@pytest.mark.parametrize("graphs", [True, False])
-def test_host_pipeline_frames_match_synchronous_renders(graphs):
+@pytest.mark.parametrize("graphs,depth", [(True, 3), (False, 3), (True, 2), (True, 1)])
+def test_host_pipeline_frames_match_synchronous_renders(graphs, depth):
     # api.HostPipeline overlaps copies with compute across frames; every
     # frame's host views must equal a plain synchronous render of its input
+    # (five frames: every slot is reused at least once)
     from paper_2508_18540_gb300 import api
     w = S.workload_tiny()
-    scenes = [w.scene, S.perturbed(w.scene, 3), S.perturbed(w.scene, 4), S.perturbed(w.scene, 5)]
+    scenes = [w.scene] + [S.perturbed(w.scene, s) for s in (3, 4, 5, 6)]
     r = api.LightFieldRenderer(w.camera, w.display, w.views, w.N, w.binning, "f32")
-    pipe = api.HostPipeline(r, w.scene.n, graphs=graphs)
+    pipe = api.HostPipeline(r, w.scene.n, graphs=graphs, depth=depth)
     outs, evs = [], []
     hosts = [api.DeviceGaussians.from_scene(sc, pin=True) for sc in scenes]
     for h in hosts:
