@@ -639,6 +639,7 @@ struct GaussBwdSmem {
     float4 e1[2][kGaussBwdThreads];
     float4 rgb[2][kGaussBwdThreads];   // {r, g, b, 1 / o}
     uint32_t rank[2][kGaussBwdThreads];
+    uint32_t wm[2][kGaussBwdThreads];  // warps whose strips the footprint meets
 };
 
 // v[0..7] summed over the warp; lane l ends with the sum of v[(l >> 2) & 7]
@@ -680,10 +681,10 @@ __device__ __forceinline__ void raster_gauss_bwd_list(const BuildWs& w, const Ra
     constexpr bool WALK1 = !SPLIT && DT != LF_F32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int SX = (st % p.supers_x) * kSuper, SY = (st / p.supers_x) * kSuper;
-    const int sx0 = SX + 8 * (warp & 3), sx1 = sx0 + 7;
-    const int sy0 = SY + 4 * NS * (warp >> 2), sy1 = sy0 + 4 * NS - 1;
-    const int px = sx0 + (lane & 7);
-    const int py0 = sy0 + (lane >> 3);
+    const int px = SX + 8 * (warp & 3) + (lane & 7);
+    const int py0 = SY + 4 * NS * (warp >> 2) + (lane >> 3);
+    // bit of this lane's column in cm, of its slot-0 row in rm
+    const int csh = px - SX, rsh = py0 - SY;
     const int2 sg = w.seg[(size_t)st * p.N + k];
     const int beg = SPLIT ? sg.x + part * S : sg.x;
     const int L = SPLIT ? min(sg.y - beg, S) : sg.y - sg.x;
@@ -729,23 +730,25 @@ __device__ __forceinline__ void raster_gauss_bwd_list(const BuildWs& w, const Ra
             const float4 c = w.r_con[rk];
             const float4 rgb = w.r_rgb[rk];
             sm.e0[buf][threadIdx.x] = make_float4(geo.x, geo.y, -0.5f * kL2E * c.x, -kL2E * c.y);
+            // the footprint as bit masks over the super-tile, as in the forward
+            const int cl = max(r.x - SX, 0), ch = min(r.z - SX, kSuper - 1);
+            const int rl = max(r.y - SY, 0), rh = min(r.w - SY, kSuper - 1);
+            const uint32_t cm = cl <= ch ? (0xffffffffu >> (31 - ch)) & (0xffffffffu << cl) : 0u;
+            const uint32_t rm = rl <= rh ? (0xffffffffu >> (31 - rh)) & (0xffffffffu << rl) : 0u;
+            uint32_t wm = 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                wm |= ((cm >> (8 * (q & 3))) & 0xffu) && ((rm >> (16 * (q >> 2))) & 0xffffu) ? 1u << q : 0u;
             sm.e1[buf][threadIdx.x] =
-                make_float4(-0.5f * kL2E * c.z, __log2f(c.w), __int_as_float((r.x & 0xffff) | (r.y << 16)),
-                            __int_as_float(((r.z - r.x) & 0xffff) | ((r.w - r.y) << 16)));
+                make_float4(-0.5f * kL2E * c.z, __log2f(c.w), __uint_as_float(cm), __uint_as_float(rm));
             sm.rgb[buf][threadIdx.x] = make_float4(rgb.x, rgb.y, rgb.z, 1.0f / c.w);
             sm.rank[buf][threadIdx.x] = rk;
+            sm.wm[buf][threadIdx.x] = wm;
         }
     };
-    auto strip_mask = [&](const float4* s_e1, int m0, int cnt) -> uint32_t {
+    auto strip_mask = [&](const uint32_t* s_wm, int m0, int cnt) -> uint32_t {
         const int jl = m0 + lane;
-        bool hit = false;
-        if (jl < cnt) {
-            const float2 rc = *reinterpret_cast<const float2*>(&s_e1[jl].z);
-            const int xy = __float_as_int(rc.x), wh = __float_as_int(rc.y);
-            const int rx0 = xy & 0xffff, ry0 = xy >> 16;
-            hit = rx0 <= sx1 && rx0 + (wh & 0xffff) >= sx0 && ry0 <= sy1 && ry0 + (wh >> 16) >= sy0;
-        }
-        return __ballot_sync(0xffffffffu, hit);
+        return __ballot_sync(0xffffffffu, jl < cnt && ((s_wm[jl] >> warp) & 1u));
     };
 
     if (WALK1) {
@@ -759,23 +762,20 @@ __device__ __forceinline__ void raster_gauss_bwd_list(const BuildWs& w, const Ra
             const float4* s_e1 = sm.e1[buf];
             const float4* s_rgb = sm.rgb[buf];
             for (int m0 = 0; m0 < cnt; m0 += 32) {
-                uint32_t mask = strip_mask(s_e1, m0, cnt);
+                uint32_t mask = strip_mask(sm.wm[buf], m0, cnt);
                 while (mask) {
                     const int j = m0 + __ffs(mask) - 1;
                     mask &= mask - 1;
                     const float4 e0 = s_e0[j];
                     const float4 e1 = s_e1[j];
                     const float4 col = s_rgb[j];
-                    const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
-                    const int rt = (uint32_t)(px - (xy & 0xffff)) <= (uint32_t)(wh & 0xffff) ? py0 - (xy >> 16)
-                                                                                            : 0x40000000;
-                    const uint32_t rh = (uint32_t)(wh >> 16);
+                    const uint32_t m = (__float_as_uint(e1.z) >> csh) & 1u ? __float_as_uint(e1.w) >> rsh : 0u;
                     const float dx = fpx - e0.x;
                     const float g1 = e0.w * dx;
                     const float g0 = fmaf(e0.z * dx, dx, e1.y);
 #pragma unroll
                     for (int s = 0; s < NS; ++s) {
-                        if ((uint32_t)(rt + 4 * s) <= rh) {
+                        if (m & (1u << (4 * s))) {
                             const float dy = (float)(py0 + 4 * s) - e0.y;
                             const float pw = fmaf(fmaf(e1.x, dy, g1), dy, g0);
                             const float al = fminf(0.99f, ex2_approx(pw));
@@ -809,17 +809,15 @@ __device__ __forceinline__ void raster_gauss_bwd_list(const BuildWs& w, const Ra
         const float4* s_rgb = sm.rgb[buf];
         const uint32_t* s_rank = sm.rank[buf];
         for (int m0 = 0; m0 < cnt; m0 += 32) {
-            uint32_t mask = strip_mask(s_e1, m0, cnt);
+            uint32_t mask = strip_mask(sm.wm[buf], m0, cnt);
             while (mask) {
                 const int j = m0 + __ffs(mask) - 1;
                 mask &= mask - 1;
                 const float4 e0 = s_e0[j];
                 const float4 e1 = s_e1[j];
                 const float4 col = s_rgb[j];
-                const int xy = __float_as_int(e1.z), wh = __float_as_int(e1.w);
-                const int rt = (uint32_t)(px - (xy & 0xffff)) <= (uint32_t)(wh & 0xffff) ? py0 - (xy >> 16)
-                                                                                        : 0x40000000;
-                const uint32_t rh = (uint32_t)(wh >> 16);
+                // slot s of this lane lies in the footprint iff bit 4 s of m is set
+                const uint32_t m = (__float_as_uint(e1.z) >> csh) & 1u ? __float_as_uint(e1.w) >> rsh : 0u;
                 const float dx = fpx - e0.x;
                 const float g1 = e0.w * dx;
                 const float g0 = fmaf(e0.z * dx, dx, e1.y);
@@ -828,7 +826,7 @@ __device__ __forceinline__ void raster_gauss_bwd_list(const BuildWs& w, const Ra
                 float sbl = 0.f;
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
-                    if ((uint32_t)(rt + 4 * s) <= rh) {
+                    if (m & (1u << (4 * s))) {
                         const float dy = (float)(py0 + 4 * s) - e0.y;
                         const float pw = fmaf(fmaf(e1.x, dy, g1), dy, g0);
                         const float araw = ex2_approx(pw);
