@@ -292,12 +292,13 @@ __device__ __forceinline__ void raster_gauss_list(const BuildWs& w, const Raster
 
 // Lists no longer than r_seg entries: one CTA per (super-tile x, chunk y).
 // The FP32 form takes 48 registers: five CTAs (40 warps) per SM. (A
-// minimum-blocks bound of five, same register count, measured 8 % slower.)
+// minimum-blocks bound of five, same register count, measured 8 % slower;
+// only the 3DGS form, 58 registers unbounded, gains from it.)
 // Launched behind the parts kernel, it does not wait for it to start;
 // CTA (0, 0) waits for it to finish before exiting, so this grid completes
 // after every part's texels are written and work ordered after it sees them.
 template <int DT, bool G3>
-__global__ void __launch_bounds__(kGaussThreads) k_raster_gauss(BuildWs w, RasterParams p,
+__global__ void __launch_bounds__(kGaussThreads, G3 ? 5 : 0) k_raster_gauss(BuildWs w, RasterParams p,
                                                                const uint32_t* __restrict__ ranks, void* planes)
 {
     __shared__ GaussSmem sm;
