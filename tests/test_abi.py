@@ -141,3 +141,10 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="liblf.so not found"):
         _lib.load(str(tmp_path / "liblf.so"))
+
+
+def test_host_pipeline_rejects_no_slots():
+    # the frame count in flight is checked before any device work
+    from paper_2508_18540_gb300 import api
+    with pytest.raises(ValueError, match="depth"):
+        api.HostPipeline(None, 1, depth=0)
