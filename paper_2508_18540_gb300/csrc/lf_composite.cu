@@ -751,7 +751,11 @@ __global__ void __launch_bounds__(NT + 32, NT == 256 ? (VG > kTwoCtaViews ? 2 : 
     const int vgroup = blockIdx.x % nvg;
     const int vi = vgroup / G.groups_x;            // view row
     const int j0 = (vgroup % G.groups_x) * VG;     // first view column of the group
-    const int Y0 = blockIdx.y * G.BY;
+    // row bands from both edges inward: the bands whose views rarely reach
+    // T = 0 (the scene's borders) start first, the cheap centre ones last
+    const int by = (int)blockIdx.y;
+    const int band = (by & 1) ? (int)gridDim.y - 1 - (by >> 1) : (by >> 1);
+    const int Y0 = band * G.BY;
     const int X0 = (blockIdx.x / nvg) * G.TX;
     const int tx = tid % G.TX, ty = tid / G.TX;
     const int x = X0 + tx, y = Y0 + ty;
