@@ -68,7 +68,7 @@ NCU_TRAFFIC = {
     # the raster stage's two kernels: the parts of split lists and the lists
     "raster_gaussians": (11_979_008 + 0 + 71_470_848 + 204_340_480, ("lf_raster.cu", "lf_internal.cuh"),
                          "3e0cef0f8f9d1f2b"),
-    "composite": (252_993_792 + 156_311_552, ("lf_composite.cu", "lf_internal.cuh"), "71b9c829af766851"),
+    "composite": (252_981_760 + 156_500_736, ("lf_composite.cu", "lf_internal.cuh"), "d93198e445d327bc"),
 }
 
 
